@@ -1,0 +1,335 @@
+"""Benchmark: SPH particle-updates/s of the leapfrog step on one GB300.
+
+Workload: 3D Sedov-Taylor blast, 128^3 = 2,097,152 particles on a jittered
+lattice (the seeded generator in paper_1909_07439_gb300.inputs).  One bench
+step is one full sph_step: kick/drift, Morton-key tree build (keys, radix
+sort, permutation, chop), group walk + h-rho Newton density solve, force
+pass, closing kick and Courant step, all on the device.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on a bounded sample of the same workload instead (the CPU baseline
+arm).  Multi-GPU runs are independent replicas (the step is a single problem
+and is not sharded), launched one process per GPU by torchrun.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SPH particle-updates/s & pair-interactions/s (1 GB300); batched/adjoint vs plain"
+UNIT = "particle-updates/s"
+SIDE = 128
+# Algorithmic FP32 operations per pair (FMA = 2, add/mul = 1; sqrt, rcp and
+# divide are special-function ops, not counted), from the plain definition:
+#  density sweep pair: distance 8, kernel f and f' 9, sums 7            = 24
+#  force pair: distance 8, two kernel gradients 14, v_ij.rhat 9,
+#  signal speed 2, pressure/viscosity coefficient 9, acceleration 7,
+#  pressure work 3, conduction 11, P_j 2 (viscous branch not counted)   = 65
+FLOP_DENSITY_PAIR = 24
+FLOP_FORCE_PAIR = 65
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r for r in csv.reader(io.StringIO(out)) if len(r) >= 9]
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if r[5 + k].strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(mx)) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    from paper_1909_07439_gb300 import DeviceState, build, inputs, native
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    build.build()
+    native.load()
+    w = inputs.sedov_lattice(args.side)
+    n = w.n
+    ctx = native.sph_create(n, local)
+    s = DeviceState.from_arrays(w.pos, w.vel, w.h, device=f"cuda:{local}")
+    p = native.sph_params_default()
+    stream = torch.cuda.current_stream()
+    d_dt = torch.zeros(1, dtype=torch.float32, device="cuda")
+    d_t = torch.zeros(1, dtype=torch.float64, device="cuda")
+    # initial evaluation (untimed): tree, density, force, Courant step
+    native.sph_build_tree(ctx, s.c, p)
+    native.sph_density(ctx, s.c, p)
+    native.sph_force(ctx, s.c, p)
+    native.sph_timestep(ctx, s.c, p, d_dt)
+    native.sph_sync(ctx)
+    for _ in range(args.warmup):
+        native.sph_step(ctx, s.c, p, d_dt, d_t)
+    native.sph_sync(ctx)
+    native.sph_get_stats(ctx)          # reset counters
+    native.sph_get_timing(ctx)         # reset stage timers
+    native.sph_set_timing(ctx, True)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        flush.zero_()                  # L2 flushed between timed steps (outside the events)
+        evs[k][0].record(stream)
+        native.sph_step(ctx, s.c, p, d_dt, d_t)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if ws > 1:
+        torch.distributed.barrier()
+    native.sph_sync(ctx)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = float(sum(step_ms))
+    stage_ms, launches = native.sph_get_timing(ctx)
+    native.sph_set_timing(ctx, False)
+    stats = native.sph_get_stats(ctx)
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = n * args.steps * ws / (total_ms / 1e3)
+    pairs = stats["density_pairs"] + stats["force_pairs"]
+    pair_rate = pairs * ws / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (ALU-bound pair passes)
+    pk, pk_kind = peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak_tflops = 2 * 128 * sms * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    dens_flop = stats["density_pairs"] * FLOP_DENSITY_PAIR
+    force_flop = stats["force_pairs"] * FLOP_FORCE_PAIR
+    if stage_ms["force"] >= stage_ms["density"]:
+        dom, dflop, dms = "force_kernel", force_flop, stage_ms["force"]
+    else:
+        dom, dflop, dms = "density_kernel", dens_flop, stage_ms["density"]
+    achieved = dflop / args.steps / (dms / args.steps / 1e3) / 1e12
+    roof = {"kernel": dom, "bound": "alu", "achieved": round(achieved, 3),
+            "peak": round(peak_tflops, 2), "unit": "TFLOP/s",
+            "frac": round(achieved / peak_tflops, 4), "traffic": None,
+            "peak_basis": f"FP32 FMA 2 x 128 lanes x {sms} SMs x {pk.get('sm_max_mhz', 2070.0)} MHz "
+                          f"(sm_max_mhz {pk_kind})",
+            "launch_ms": round(dms / args.steps, 4)}
+
+    e2e = run_e2e(native, ctx, s, p, n, args, stream) if rank == 0 else None
+    out = None
+    if rank == 0:
+        cpu = run_cpu_baseline(w, args.cpu_seconds) if args.cpu_seconds > 0 else None
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded Sedov lattice; no dataset)",
+            "config": {"workload": f"sedov_blast_lattice_{args.side}^3", "n_particles": n,
+                       "step": "sph_step: KDK + tree build + density Newton + force + Courant dt",
+                       "kernel": "M4", "n_leaf": p.n_leaf, "n_group": p.n_group,
+                       "hfact": round(p.hfact, 4), "l2": "flushed between timed steps",
+                       "parallelism": f"replicas x{ws}"},
+            "pair_interactions_per_s": pair_rate,
+            "clocks": clk,
+            "e2e": e2e,
+            "gpu_launches": int(sum(launches.values())),
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "stage_ms_per_step": {k: round(v / args.steps, 4) for k, v in stage_ms.items()},
+            "work_per_step": {k: v / args.steps for k, v in stats.items()
+                              if k not in ("n_nodes", "n_groups")},
+            "tree": {"n_nodes": stats["n_nodes"], "n_groups": stats["n_groups"]},
+            "sim_time": float(d_t.item()),
+        }
+    native.sph_destroy(ctx)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return out
+
+
+def run_e2e(native, ctx, s, p, n, args, stream):
+    """Same metric through the C ABI with the state in pinned HOST memory:
+    every step copies the inputs in and the whole state back."""
+    import ctypes
+    import torch
+    host = {k: getattr(s, k)[:n].cpu().pin_memory() for k in s.FIELDS4 + s.FIELDS1 + ("perm", "keys")}
+    hs = native.sph_state()
+    hs.n = n
+    for k, t in host.items():
+        setattr(hs, k, t.data_ptr())
+    dt = ctypes.c_float(1e-6)
+    d = torch.zeros(1, dtype=torch.float32, device="cuda")
+    native.sph_timestep(ctx, s.c, p, d)
+    dt.value = d.item()
+    native.sph_step_host(ctx, hs, p, 1, dt)  # first call allocates the mirror
+    k = max(1, min(args.steps, 10))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(k):
+        native.sph_step_host(ctx, hs, p, 1, dt)
+    t1 = time.perf_counter()
+    h2d = n * (16 * 3 + 4 + 4) + 4
+    d2h = n * (16 * 3 + 4 * 5 + 4 + 8) + 4
+    return {"value": n * k / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "steps": k,
+            "note": "sph_step_host: pinned host state, H2D + step + D2H inside the timed region"}
+
+
+# ------------------------------------------------------------ CPU baseline
+def oracle_sample_rate(w, target_seconds, seed=12345):
+    """Time the FP64 oracle's per-particle work on a sample of targets:
+    the h-rho solve (brute force over all n) plus the force pass (brute force
+    over all n).  The force leg uses the generator's h and unit rho, Omega for
+    the non-sampled particles; its cost is the O(n) pair scan per target."""
+    import oracle
+    oracle.build()
+    x = w.pos[:, :3].astype(np.float64)
+    v = w.vel[:, :3].astype(np.float64)
+    m = w.pos[:, 3].astype(np.float64)
+    u = w.vel[:, 3].astype(np.float64)
+    h0 = w.h.astype(np.float64)
+    rng = np.random.default_rng(seed)
+
+    def run(k):
+        t = np.sort(rng.choice(w.n, size=k, replace=False))
+        t0 = time.perf_counter()
+        d = oracle.density(x, v, m, h0, targets=t)
+        hh, rr, oo = h0.copy(), np.ones(w.n), np.ones(w.n)
+        hh[t], rr[t], oo[t] = d.h, d.rho, d.omega
+        oracle.force(x, v, m, u, hh, rr, oo, targets=t)
+        return time.perf_counter() - t0
+
+    k = 16
+    dt = run(k)
+    while dt < 0.5 and k < 1 << 16:
+        k *= 2
+        dt = run(k)
+    k = max(1, int(k * target_seconds / max(dt, 1e-9)))
+    dt = run(k)
+    return k, dt
+
+
+def run_cpu_baseline(w, seconds):
+    k, dt = oracle_sample_rate(w, seconds)
+    return {"value": k / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{k} seeded target particles of the {w.n}-particle workload: FP64 h-rho "
+                      f"Newton solve + force, each brute force over all {w.n} particles "
+                      f"({dt:.1f} s)"}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return None
+    from paper_1909_07439_gb300 import inputs
+    w = inputs.sedov_lattice(args.side)
+    per_step = max(1.0, min(10.0, 120.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample_rate(w, per_step / 4)
+    total_k, total_t = 0, 0.0
+    for _ in range(args.steps):
+        k, dt = oracle_sample_rate(w, per_step)
+        total_k += k
+        total_t += dt
+    value = total_k / total_t
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * w.n / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Sedov lattice)",
+            "config": {"workload": f"sedov_blast_lattice_{args.side}^3", "n_particles": w.n},
+            "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "value": value,
+                             "unit": UNIT,
+                             "sample": f"{total_k} target particles over {args.steps} steps, "
+                                       f"each brute force over all {w.n} particles"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "note": "FP64 brute-force CPU oracle (the reference arm); per-particle rate"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--side", type=int, default=SIDE)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/*
+ * sph.h - C ABI of the GB300 (sm_103a) SPH neighbour-sum library.
+ *
+ * The library implements the per-step hot path of Bonsai-SPH
+ * (arXiv 1909.07439): space-filling-curve octree build (Sect. 3.1), the
+ * group-wise tree walk (Sect. 3.2), the smoothing-length / density solve
+ * (Sect. 2.2, Eqs. 1-4), the hydro force with artificial viscosity and
+ * conductivity (Sect. 2.4-2.6, Eqs. 9-15) and the leapfrog step with the
+ * Courant time step (Sect. 2.4, Eqs. 5-8), for the M4 cubic spline
+ * (Sect. 2.3).  Self-gravity is not part of this library.
+ *
+ * Conventions for every entry point:
+ *  - All array pointers in sph_state are DEVICE pointers (unless an entry
+ *    point says otherwise), owned by the caller, 16-byte aligned, and must
+ *    stay valid until the work enqueued on `stream` has finished.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - Calls are asynchronous.  Argument errors are returned synchronously.
+ *    Conditions found on the device (non-finite input, a density solve that
+ *    did not converge, a scratch overflow, negative internal energy) are
+ *    recorded in the context's device error word and returned by the next
+ *    sph_sync(); sph_last_error() gives the text.
+ *  - A context owns all scratch memory, allocated once by sph_create for at
+ *    most max_n particles; no later call allocates device memory, except
+ *    sph_step_host (host-buffer mirror, allocated on its first call).
+ *  - A context is not thread-safe; use one context per host thread/stream.
+ */
+#ifndef SPH_H
+#define SPH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sph_ctx sph_ctx;
+
+typedef enum {
+    SPH_OK = 0,
+    SPH_ERR_INVALID_ARG = 1,   /* bad pointer, size, or parameter                    */
+    SPH_ERR_CUDA = 2,          /* a CUDA runtime call failed                         */
+    SPH_ERR_NOMEM = 3,         /* allocation failed, or tree capacity exceeded       */
+    SPH_ERR_NOT_CONVERGED = 4, /* h-rho Newton did not reach h_tol in max_h_iter     */
+    SPH_ERR_TILE_OVERFLOW = 5, /* a tree-walk list overflowed its shared-memory tile */
+    SPH_ERR_NONFINITE = 6,     /* non-finite position, velocity, mass or h; m<=0; h<=0 */
+    SPH_ERR_NEGATIVE_U = 7,    /* internal energy became negative                    */
+    SPH_ERR_TIMEOUT = 8        /* a bounded device-side wait gave up                 */
+} sph_status;
+
+/* Method parameters.  Defaults (sph_params_default) are the paper's
+ * (Sect. 4: gamma = 5/3, alpha_AV = 1, beta_AV = 2, alpha_u = 1, C_cour = 0.3,
+ * M4 kernel; Sect. 4.6: N_leaf = 16, N_crit = N_group = 8) and hfact = 1.2. */
+typedef struct {
+    float gamma;         /* adiabatic index; P = (gamma-1) rho u                       */
+    float hfact;         /* h = hfact (m/rho)^(1/3)  (Eq. 2)                            */
+    float alpha_av;      /* alpha^AV  (Eq. 12)                                          */
+    float beta_av;       /* beta^AV   (Eq. 12)                                          */
+    float alpha_u;       /* alpha_u, artificial conductivity (Eq. 13)                   */
+    float c_cour;        /* Courant factor (Eq. 8)                                      */
+    float h_tol;         /* Newton stops when |dh|/h < h_tol (checked in FP64)          */
+    int32_t kernel;      /* smoothing kernel: 0 = M4 cubic spline (the only one built)  */
+    int32_t n_leaf;      /* max particles per tree leaf  (1..64)                        */
+    int32_t n_group;     /* max particles per walk group (1..32)                        */
+    int32_t tile;        /* per-target neighbour-list capacity, 0 = default (96)       */
+    int32_t max_h_iter;  /* Newton iteration cap (>= 1)                                 */
+    int32_t density_iters; /* 0: iterate to h_tol; k > 0: exactly k updates (Sect. 3.2.1) */
+} sph_params;
+
+/* Particle state, structure of arrays, n particles, device memory.
+ * After sph_build_tree the arrays are in space-filling-curve order and
+ * perm[k] is the caller's original index of slot k. */
+typedef struct {
+    int64_t n;
+    float *pos;      /* [n][4]  x, y, z, m                                   in    */
+    float *vel;      /* [n][4]  vx, vy, vz, u                                in    */
+    float *acc;      /* [n][4]  ax, ay, az, du/dt                            out   */
+    float *h;        /* [n]     smoothing length                             in/out */
+    float *rho;      /* [n]     density                                      out   */
+    float *omega;    /* [n]     grad-h term Omega (Eq. 4)                    out   */
+    float *drhodt;   /* [n]     drho/dt (Eq. 3)                              out   */
+    float *vsigmax;  /* [n]     max signal speed (Eq. 8)                     out   */
+    uint32_t *perm;  /* [n]     original index of each slot                  in/out */
+    uint64_t *keys;  /* [n]     63-bit Morton key of each slot               out   */
+} sph_state;
+
+/* Fill *p with the defaults listed above. */
+void sph_params_default(sph_params *p);
+
+/* Create a context on CUDA device `device` for up to max_n particles
+ * (max_n >= 1, < 2^31).  All scratch is allocated here.
+ * Errors: SPH_ERR_INVALID_ARG, SPH_ERR_CUDA, SPH_ERR_NOMEM. */
+sph_status sph_create(sph_ctx **out, int64_t max_n, int device);
+
+/* Release a context and its scratch (synchronises its device first). */
+void sph_destroy(sph_ctx *ctx);
+
+/* Tree build (Sect. 3.1): bounding box, 63-bit Morton keys (21 bits per axis,
+ * canonical FP32 quantisation), stable LSD radix sort of (key, slot), in-place
+ * permutation of pos, vel, acc, h, rho, omega, drhodt, vsigmax and perm into
+ * curve order, octree chop (nodes of at most n_leaf particles) and group chop
+ * (groups of at most n_group particles), with node/group bounding boxes.
+ * The caller initialises perm once (identity for "original order").
+ * Validates inputs: non-finite pos/h, m <= 0 or h <= 0 set SPH_ERR_NONFINITE. */
+sph_status sph_build_tree(sph_ctx *ctx, sph_state *s, const sph_params *p, void *stream);
+
+/* Density pass (Eqs. 1-4): for every particle, Newton iteration on
+ * g(h) = sum_j m_j W(r_ij, h) - m (hfact/h)^3 from the input h, over the
+ * group walk of the tree built by the last sph_build_tree on this state.
+ * Writes h, rho = m (hfact/h)^3, omega (Eq. 4) and drhodt (Eq. 3, with vel). */
+sph_status sph_density(sph_ctx *ctx, sph_state *s, const sph_params *p, void *stream);
+
+/* Hydro force pass (Eqs. 9-15), no gravity: writes acc (xyz and du/dt) and
+ * vsigmax.  Needs h, rho, omega from sph_density and the current vel.
+ * A pair interacts if r < 2 max(h_i, h_j) (Sect. 3.2). */
+sph_status sph_force(sph_ctx *ctx, sph_state *s, const sph_params *p, void *stream);
+
+/* Courant step (Eq. 8): *d_dt = c_cour * min_i h_i / vsigmax_i (device float). */
+sph_status sph_timestep(sph_ctx *ctx, const sph_state *s, const sph_params *p, float *d_dt,
+                        void *stream);
+
+/* One leapfrog step (Eqs. 5-7 in kick-drift-kick form) with dt = *d_dt:
+ * kick/drift with the acc already in the state, tree build, density and force
+ * at the new positions with predicted v and u, closing kick, then the next
+ * Courant step is written to *d_dt.  If d_time is not NULL, *d_time += dt
+ * (device double).  Nothing returns to the host inside the call. */
+sph_status sph_step(sph_ctx *ctx, sph_state *s, const sph_params *p, float *d_dt,
+                    double *d_time, void *stream);
+
+/* Same step for a state held in HOST memory (pinned for best speed): copies
+ * the state in, runs n_steps steps, copies it back; *h_dt (host) is read as
+ * the first dt and receives the next one.  Allocates a device mirror on the
+ * first call.  Synchronous. */
+sph_status sph_step_host(sph_ctx *ctx, sph_state *host_state, const sph_params *p, int n_steps,
+                         float *h_dt, void *stream);
+
+/* FP64 conserved quantities (Sect. 4.5, Eq. 16), deterministic reduction:
+ * d_out8 = { E_kin, E_th, px, py, pz, Lx, Ly, Lz } (device doubles). */
+sph_status sph_conserved(sph_ctx *ctx, const sph_state *s, double *d_out8, void *stream);
+
+/* Neighbour sets of the current tree/state (Sect. 3.2), for testing.
+ * mode 0: density set {j : r2 < (2 h_i)^2} (includes i);
+ * mode 1: force set {j != i : r2 < (2 max(h_i, h_j))^2};
+ * r2 = (dx*dx + dy*dy) + dz*dz in FP32, round-to-nearest, no fusion.
+ * d_off: device int64 [n+1] row offsets (always written);
+ * d_idx: device int32 [cap] slot indices (written if non-NULL and total <= cap).
+ * *h_total receives the total (host).  Synchronous. */
+sph_status sph_neighbours(sph_ctx *ctx, const sph_state *s, const sph_params *p, int mode,
+                          int64_t *d_off, int32_t *d_idx, int64_t cap, int64_t *h_total,
+                          void *stream);
+
+/* Copy the tree and groups of the last sph_build_tree to HOST arrays, for
+ * testing.  Nodes are in level-major order (first particle order inside a
+ * level): level, first particle, particle count, number of children, and the
+ * index of the first child (-1 for a leaf; children are contiguous).  Groups:
+ * first particle and count.  *n_nodes / *n_groups receive the counts; the
+ * arrays are filled only when the counts fit node_cap / group_cap (any array
+ * may be NULL).  Synchronous. */
+sph_status sph_get_tree(sph_ctx *ctx, int32_t *h_level, int32_t *h_first, int32_t *h_count,
+                        int32_t *h_nchild, int32_t *h_child, int64_t node_cap,
+                        int32_t *h_gfirst, int32_t *h_gcount, int64_t group_cap,
+                        int64_t *n_nodes, int64_t *n_groups);
+
+/* Work counters accumulated since the last call (then reset).  Synchronous. */
+typedef struct {
+    uint64_t density_pairs;       /* true-neighbour pairs summed, all Newton sweeps   */
+    uint64_t density_candidates;  /* particle-pair distance tests in density walks     */
+    uint64_t force_pairs;         /* pairs in the force sets                           */
+    uint64_t force_candidates;    /* particle-pair distance tests in the force walk    */
+    uint64_t newton_iters;        /* Newton updates summed over particles              */
+    uint64_t density_rewalks;     /* group walks repeated because h outgrew its pad    */
+    uint64_t streamed_groups;     /* groups whose lists overflowed the tile            */
+    uint64_t n_nodes;             /* tree nodes of the last build                      */
+    uint64_t n_groups;            /* groups of the last build                          */
+} sph_stats;
+sph_status sph_get_stats(sph_ctx *ctx, sph_stats *out);
+
+/* Per-stage device timing (CUDA events on the launching stream).
+ * Stages: 0 tree build, 1 density kernel, 2 force kernel, 3 reductions
+ * (dt, conserved), 4 leapfrog kicks/drift, 5 force preparation (per-particle
+ * sound speed and node/group h_max).  sph_get_timing synchronises and returns
+ * the milliseconds summed since the last call, and the number of kernels
+ * launched per stage (also counted when timing is off). */
+#define SPH_N_STAGES 6
+sph_status sph_set_timing(sph_ctx *ctx, int enable);
+sph_status sph_get_timing(sph_ctx *ctx, double *ms_by_stage, int64_t *launches_by_stage);
+
+/* Synchronise `stream` and return (then clear) the device error word. */
+sph_status sph_sync(sph_ctx *ctx, void *stream);
+
+/* Text of the last error on this context (never NULL). */
+const char *sph_last_error(sph_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPH_H */

@@ -1,0 +1,267 @@
+// Hydro force pass (Sect. 2.4-2.6, Eqs. 9-15), no gravity.
+//
+// One warp per group (up to 8 targets at a time).  The walk opens a node if
+// its box is within 2 max(h_max(group), h_max(node)) of the group box, so a
+// pair is found whenever either particle reaches the other (Sect. 3.2).  Each
+// candidate chunk is tested against every target with the canonical FP32
+// distance; hits are compacted with ballots into per-target lists in shared
+// memory.  The pair arithmetic then runs over the lists with L lanes per
+// target, so the expensive part executes with full warps and no divergence
+// from the neighbour test; lists are flushed whenever one could overflow.
+#include "walk.cuh"
+
+namespace sph {
+
+constexpr int kFTB = 8;          // targets per batch
+constexpr int kForceWarps = 4;   // warps per block
+
+template <int CAP>
+struct ForceSmem {
+    WalkSmem w;
+    float4 tp[kFTB];   // x, y, z, m
+    float4 tv[kFTB];   // vx, vy, vz, u
+    float4 tq[kFTB];   // h, rho, 1/(rho Omega), c
+    int tlen[kFTB];
+    int ej[kFTB][CAP];
+};
+
+struct ForceArgs {
+    const float4 *pos, *vel, *prop;
+    float4 *acc;
+    float *vsigmax;
+    const int2 *grp_ref;
+    const float4 *grp_lo, *grp_hi;
+    const int *sizes;
+    int *work;
+    WalkTree tree;
+    float gm1, alpha, beta, alpha_u;
+    int *err;
+    unsigned long long *counters;
+};
+
+__device__ __forceinline__ float m4_df(float q)
+{
+    if (q < 1.f) return q * (-3.f + 2.25f * q);
+    if (q < 2.f) {
+        float t = 2.f - q;
+        return -0.75f * t * t;
+    }
+    return 0.f;
+}
+
+template <int CAP>
+__global__ void __launch_bounds__(kForceWarps * 32) force_kernel(ForceArgs a)
+{
+    extern __shared__ __align__(16) unsigned char fsm_raw[];
+    ForceSmem<CAP> &sm = reinterpret_cast<ForceSmem<CAP> *>(fsm_raw)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lane_lt();
+    const int ng = a.sizes[SZ_GROUPS];
+    unsigned long long n_pairs = 0, n_cand = 0;
+
+    while (true) {
+        int g = 0;
+        if (lane == 0) g = atomicAdd(a.work, 1);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g >= ng) break;
+        const int2 gr = a.grp_ref[g];
+        const float4 glo = a.grp_lo[g], ghi = a.grp_hi[g];
+        for (int b0 = 0; b0 < gr.y; b0 += kFTB) {
+            const int nt = min(kFTB, gr.y - b0);
+            const int L = nt > 4 ? 4 : nt > 2 ? 8 : nt > 1 ? 16 : 32;
+            const int t = lane / L, sub = lane % L;
+            const bool act = t < nt;
+            const int i0 = gr.x + b0;
+            if (lane < nt) {
+                sm.tp[lane] = a.pos[i0 + lane];
+                sm.tv[lane] = a.vel[i0 + lane];
+                sm.tq[lane] = a.prop[i0 + lane];
+                sm.tlen[lane] = 0;
+            }
+            __syncwarp();
+            // per-target constants in registers of the target's lanes
+            const float4 xi = sm.tp[act ? t : 0], vi = sm.tv[act ? t : 0], qi = sm.tq[act ? t : 0];
+            const float hinv_i = 1.f / qi.x;
+            const float hinv4_i = hinv_i * hinv_i * hinv_i * hinv_i;
+            const float Ai = qi.z, ci = qi.w;
+            const float Pi = a.gm1 * qi.y * vi.w;
+            const float pres_i = a.gm1 * vi.w;  // P_i / rho_i
+            float ax = 0.f, ay = 0.f, az = 0.f, dup = 0.f, duav = 0.f, duc = 0.f;
+            float vsmax = a.alpha * ci;
+            int cnt = 0;
+
+            auto flush = [&]() {
+                if (act) {
+                    const int len = sm.tlen[t];
+                    for (int e = sub; e < len; e += L) {
+                        const int j = sm.ej[t][e];
+                        const float4 pj = __ldg(&a.pos[j]);
+                        const float4 vj = __ldg(&a.vel[j]);
+                        const float4 qj = __ldg(&a.prop[j]);
+                        const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
+                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        const float r = sqrtf(r2);
+                        const float rinv = r > 0.f ? 1.f / r : 0.f;
+                        const float hinv_j = 1.f / qj.x;
+                        const float Fi = kCNorm * m4_df(r * hinv_i) * hinv4_i;
+                        const float hinv2_j = hinv_j * hinv_j;
+                        const float Fj = kCNorm * m4_df(r * hinv_j) * hinv2_j * hinv2_j;
+                        const float vr = ((vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz) * rinv;
+                        const float avr = fabsf(vr);
+                        const float vsi = a.alpha * ci + a.beta * avr;
+                        float avi = 0.f, avj = 0.f;
+                        if (vr < 0.f) {
+                            avi = -0.5f * vsi * vr;
+                            avj = -0.5f * (a.alpha * qj.w + a.beta * avr) * vr;
+                            duav += pj.w * vsi * vr * vr * Fi;
+                        }
+                        const float Aj = qj.z;
+                        const float coef = pj.w * (Ai * (pres_i + avi) * Fi + Aj * (a.gm1 * vj.w + avj) * Fj);
+                        ax -= coef * dx * rinv;
+                        ay -= coef * dy * rinv;
+                        az -= coef * dz * rinv;
+                        dup += pj.w * vr * Fi;
+                        const float Pj = a.gm1 * qj.y * vj.w;
+                        const float vsu = sqrtf(fabsf(Pi - Pj) / (0.5f * (qi.y + qj.y)));
+                        duc += pj.w * vsu * (vi.w - vj.w) * (Fi * Ai + Fj * Aj);
+                        vsmax = fmaxf(vsmax, vsi);
+                        ++cnt;
+                    }
+                }
+                __syncwarp();
+                if (lane < nt) sm.tlen[lane] = 0;
+                __syncwarp();
+            };
+            auto chunk = [&](int j) {
+                bool full = lane < nt && sm.tlen[lane] > CAP - 32;
+                if (__any_sync(0xffffffffu, full)) flush();
+                float4 pj = j >= 0 ? __ldg(&a.pos[j]) : make_float4(0, 0, 0, 0);
+                float hj = j >= 0 ? __ldg(&a.prop[j].x) : 0.f;
+                for (int tt = 0; tt < nt; ++tt) {
+                    float4 tp = sm.tp[tt];
+                    float ht = sm.tq[tt].x;
+                    float r2 = canon_r2(tp.x, tp.y, tp.z, pj.x, pj.y, pj.z);
+                    float R = 2.0f * fmaxf(ht, hj);
+                    bool hit = j >= 0 && j != i0 + tt && r2 < R * R;
+                    unsigned b = __ballot_sync(0xffffffffu, hit);
+                    int base = sm.tlen[tt];
+                    if (hit) sm.ej[tt][base + __popc(b & lt)] = j;
+                    __syncwarp();
+                    if (lane == 0) sm.tlen[tt] = base + __popc(b);
+                    __syncwarp();
+                }
+                n_cand += (unsigned long long)nt;
+            };
+            bool ok = walk_group(a.tree, glo, ghi, 0.f, true, glo.w, sm.w, chunk);
+            if (!ok && lane == 0) raise_error(a.err, SPH_ERR_TILE_OVERFLOW);
+            flush();
+            // reduce over the L lanes of each target
+            for (int o = L >> 1; o > 0; o >>= 1) {
+                ax += __shfl_xor_sync(0xffffffffu, ax, o);
+                ay += __shfl_xor_sync(0xffffffffu, ay, o);
+                az += __shfl_xor_sync(0xffffffffu, az, o);
+                dup += __shfl_xor_sync(0xffffffffu, dup, o);
+                duav += __shfl_xor_sync(0xffffffffu, duav, o);
+                duc += __shfl_xor_sync(0xffffffffu, duc, o);
+                vsmax = fmaxf(vsmax, __shfl_xor_sync(0xffffffffu, vsmax, o));
+            }
+            if (act && sub == 0) {
+                float du = pres_i * Ai * dup - 0.5f * Ai * duav + 0.5f * a.alpha_u * duc;
+                a.acc[i0 + t] = make_float4(ax, ay, az, du);
+                a.vsigmax[i0 + t] = vsmax;
+            }
+            n_pairs += cnt;
+            __syncwarp();
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        n_pairs += __shfl_xor_sync(0xffffffffu, n_pairs, o);
+        n_cand += __shfl_xor_sync(0xffffffffu, n_cand, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&a.counters[C_FORCE_PAIRS], n_pairs);
+        atomicAdd(&a.counters[C_FORCE_CAND], n_cand);  // sum over lanes = 32 per chunk-target
+    }
+}
+
+// prop = (h, rho, 1/(rho Omega), c_s) from the state; checks vel and u
+__global__ void force_prep_kernel(const float4 *__restrict__ vel, const float *__restrict__ h,
+                                  const float *__restrict__ rho, const float *__restrict__ omega,
+                                  float4 *__restrict__ prop, int n, float gamma, int *err)
+{
+    bool bad = false, neg = false;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float4 v = vel[i];
+        float r = rho[i], o = omega[i];
+        bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w) && isfinite(r) &&
+                 isfinite(o));
+        neg |= v.w < 0.f;
+        float cs = sqrtf(fmaxf(gamma * (gamma - 1.f) * v.w, 0.f));
+        prop[i] = make_float4(h[i], r, 1.f / (r * o), cs);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) raise_error(err, SPH_ERR_NONFINITE);
+    if (__any_sync(0xffffffffu, neg) && (threadIdx.x & 31) == 0) raise_error(err, SPH_ERR_NEGATIVE_U);
+}
+
+template <int CAP>
+static cudaError_t launch_force(Ctx &c, const ForceArgs &a, cudaStream_t st)
+{
+    size_t smem = sizeof(ForceSmem<CAP>) * kForceWarps;
+    static bool configured = false;
+    static int blocks = 1;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(force_kernel<CAP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_kernel<CAP>, kForceWarps * 32, smem);
+        if (e != cudaSuccess) return e;
+        blocks = nb > 0 ? nb : 1;
+        configured = true;
+    }
+    force_kernel<CAP><<<c.num_sms * blocks, kForceWarps * 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t force_prep(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st)
+{
+    const int n = (int)s.n;
+    int grid = (n + 255) / 256;
+    if (grid > c.num_sms * 16) grid = c.num_sms * 16;
+    force_prep_kernel<<<grid, 256, 0, st>>>((const float4 *)s.vel, s.h, s.rho, s.omega, c.prop, n,
+                                            p.gamma, c.d_err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return update_hmax(c, s, p, st);
+}
+
+cudaError_t force_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st)
+{
+    cudaError_t e;
+    ForceArgs a{};
+    a.pos = (const float4 *)s.pos;
+    a.vel = (const float4 *)s.vel;
+    a.prop = c.prop;
+    a.acc = (float4 *)s.acc;
+    a.vsigmax = s.vsigmax;
+    a.grp_ref = c.tree.grp_ref;
+    a.grp_lo = c.tree.grp_lo;
+    a.grp_hi = c.tree.grp_hi;
+    a.sizes = c.d_sizes;
+    a.work = c.d_sizes + 3;
+    a.tree = WalkTree{c.tree.node_lo, c.tree.node_hi, c.tree.node_ref};
+    a.gm1 = p.gamma - 1.f;
+    a.alpha = p.alpha_av;
+    a.beta = p.beta_av;
+    a.alpha_u = p.alpha_u;
+    a.err = c.d_err;
+    a.counters = c.d_counters;
+    e = cudaMemsetAsync(a.work, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    int cap = p.tile > 0 ? p.tile : 96;
+    if (cap <= 64) return launch_force<64>(c, a, st);
+    if (cap <= 96) return launch_force<96>(c, a, st);
+    return launch_force<128>(c, a, st);
+}
+
+}  // namespace sph

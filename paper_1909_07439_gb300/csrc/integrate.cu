@@ -1,0 +1,154 @@
+// Particle integration (Sect. 3.3): one thread per particle.
+// Leapfrog of Eqs. 5-7 in kick-drift-kick form, the Courant step (Eq. 8) and
+// the FP64 conserved quantities used for the energy error (Eq. 16).
+#include "sph_internal.cuh"
+
+namespace sph {
+
+static int grid_n(const Ctx &c, int64_t n, int block)
+{
+    int64_t g = (n + block - 1) / block;
+    int64_t cap = (int64_t)c.num_sms * 16;
+    if (g > cap) g = cap;
+    return g < 1 ? 1 : (int)g;
+}
+
+// v_half = v + a dt/2, u_half = u + du dt/2 (kept in vhalf);
+// predicted v1p = v + a dt, u1p = u + du dt (Eq. 6) into vel;
+// r1 = r + v_half dt = r + v dt + a dt^2/2 (Eq. 5).
+__global__ void kick_drift_kernel(float4 *__restrict__ pos, float4 *__restrict__ vel,
+                                  const float4 *__restrict__ acc, float4 *__restrict__ vhalf,
+                                  int n, const float *d_dt)
+{
+    const float dt = *d_dt, hdt = 0.5f * dt;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float4 v = vel[i], a = acc[i], p = pos[i];
+        float4 vh = make_float4(v.x + hdt * a.x, v.y + hdt * a.y, v.z + hdt * a.z, v.w + hdt * a.w);
+        vhalf[i] = vh;
+        vel[i] = make_float4(v.x + dt * a.x, v.y + dt * a.y, v.z + dt * a.z, v.w + dt * a.w);
+        pos[i] = make_float4(p.x + dt * vh.x, p.y + dt * vh.y, p.z + dt * vh.z, p.w);
+    }
+}
+
+// v1 = v_half + a1 dt/2 (equal to Eq. 7 applied to the Eq. 6 prediction)
+__global__ void kick_close_kernel(float4 *__restrict__ vel, const float4 *__restrict__ acc,
+                                  const float4 *__restrict__ vhalf, int n, const float *d_dt,
+                                  double *d_time, int *err)
+{
+    const float dt = *d_dt, hdt = 0.5f * dt;
+    bool neg = false;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float4 vh = vhalf[i], a = acc[i];
+        float4 v = make_float4(vh.x + hdt * a.x, vh.y + hdt * a.y, vh.z + hdt * a.z, vh.w + hdt * a.w);
+        neg |= !(v.w >= 0.f);
+        vel[i] = v;
+    }
+    if (__any_sync(0xffffffffu, neg) && (threadIdx.x & 31) == 0) raise_error(err, SPH_ERR_NEGATIVE_U);
+    if (d_time && blockIdx.x == 0 && threadIdx.x == 0) *d_time += (double)dt;
+}
+
+// block minima of h / vsigmax
+__global__ void __launch_bounds__(256) dt_block_kernel(const float *__restrict__ h,
+                                                       const float *__restrict__ vs, int n,
+                                                       float *blockmin)
+{
+    __shared__ float sm[8];
+    float m = INFINITY;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        m = fminf(m, h[i] / vs[i]);
+    for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float r = sm[0];
+        for (int w = 1; w < 8; ++w) r = fminf(r, sm[w]);
+        blockmin[blockIdx.x] = r;
+    }
+}
+
+__global__ void dt_final_kernel(const float *blockmin, int nb, float c_cour, float *d_dt)
+{
+    float m = INFINITY;
+    for (int b = threadIdx.x; b < nb; b += 32) m = fminf(m, blockmin[b]);
+    for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) *d_dt = c_cour * m;
+}
+
+// FP64 sums in a fixed order: each thread owns a fixed strided subset, the
+// block combines by a fixed tree, the final kernel adds block sums in order.
+__global__ void __launch_bounds__(256) conserved_block_kernel(const float4 *__restrict__ pos,
+                                                              const float4 *__restrict__ vel, int n,
+                                                              double *part, int nb)
+{
+    __shared__ double sm[8][256];
+    double e[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float4 p = pos[i], v = vel[i];
+        double m = p.w, x = p.x, y = p.y, z = p.z, vx = v.x, vy = v.y, vz = v.z;
+        e[0] += 0.5 * m * (vx * vx + vy * vy + vz * vz);
+        e[1] += m * (double)v.w;
+        e[2] += m * vx;
+        e[3] += m * vy;
+        e[4] += m * vz;
+        e[5] += m * (y * vz - z * vy);
+        e[6] += m * (z * vx - x * vz);
+        e[7] += m * (x * vy - y * vx);
+    }
+    for (int k = 0; k < 8; ++k) sm[k][threadIdx.x] = e[k];
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+            for (int k = 0; k < 8; ++k) sm[k][threadIdx.x] += sm[k][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x < 8) part[threadIdx.x * nb + blockIdx.x] = sm[threadIdx.x][0];
+}
+
+__global__ void conserved_final_kernel(const double *part, int nb, double *out8)
+{
+    int k = threadIdx.x;
+    if (k < 8) {
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) s += part[k * nb + b];
+        out8[k] = s;
+    }
+}
+
+cudaError_t kick_drift(Ctx &c, const sph_state &s, const float *d_dt, cudaStream_t st)
+{
+    int n = (int)s.n;
+    kick_drift_kernel<<<grid_n(c, n, 256), 256, 0, st>>>((float4 *)s.pos, (float4 *)s.vel,
+                                                         (const float4 *)s.acc, c.vhalf, n, d_dt);
+    return cudaGetLastError();
+}
+
+cudaError_t kick_close(Ctx &c, const sph_state &s, const float *d_dt, double *d_time,
+                       cudaStream_t st)
+{
+    int n = (int)s.n;
+    kick_close_kernel<<<grid_n(c, n, 256), 256, 0, st>>>((float4 *)s.vel, (const float4 *)s.acc,
+                                                         c.vhalf, n, d_dt, d_time, c.d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t courant_dt(Ctx &c, const sph_state &s, const sph_params &p, float *d_dt,
+                       cudaStream_t st)
+{
+    int n = (int)s.n;
+    int nb = grid_n(c, n, 256);
+    dt_block_kernel<<<nb, 256, 0, st>>>(s.h, s.vsigmax, n, c.red_f);
+    dt_final_kernel<<<1, 32, 0, st>>>(c.red_f, nb, p.c_cour, d_dt);
+    return cudaGetLastError();
+}
+
+cudaError_t conserved(Ctx &c, const sph_state &s, double *d_out8, cudaStream_t st)
+{
+    int n = (int)s.n;
+    int nb = grid_n(c, n, 256);
+    conserved_block_kernel<<<nb, 256, 0, st>>>((const float4 *)s.pos, (const float4 *)s.vel, n,
+                                               c.red_d, nb);
+    conserved_final_kernel<<<1, 32, 0, st>>>(c.red_d, nb, d_out8);
+    return cudaGetLastError();
+}
+
+}  // namespace sph

@@ -1,0 +1,561 @@
+// C ABI entry points (include/sph.h): context, argument checks, stage timing,
+// error word, and the step driver.
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "sph_internal.cuh"
+
+using namespace sph;
+
+namespace {
+
+const char *status_text(sph_status s)
+{
+    switch (s) {
+    case SPH_OK: return "ok";
+    case SPH_ERR_INVALID_ARG: return "invalid argument";
+    case SPH_ERR_CUDA: return "CUDA error";
+    case SPH_ERR_NOMEM: return "out of memory or tree capacity exceeded";
+    case SPH_ERR_NOT_CONVERGED: return "h-rho Newton iteration did not converge";
+    case SPH_ERR_TILE_OVERFLOW: return "tree-walk stack overflow";
+    case SPH_ERR_NONFINITE: return "non-finite or non-positive input (pos, vel, m, h)";
+    case SPH_ERR_NEGATIVE_U: return "negative internal energy";
+    case SPH_ERR_TIMEOUT: return "device wait timed out";
+    }
+    return "unknown";
+}
+
+sph_status fail(Ctx &c, sph_status s, const char *what)
+{
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s: %s", status_text(s), what);
+    c.last_error = buf;
+    return s;
+}
+
+sph_status cuda_fail(Ctx &c, cudaError_t e, const char *what)
+{
+    char buf[320];
+    snprintf(buf, sizeof(buf), "CUDA error in %s: %s", what, cudaGetErrorString(e));
+    c.last_error = buf;
+    return SPH_ERR_CUDA;
+}
+
+template <class T>
+cudaError_t dalloc(T *&p, size_t count)
+{
+    return cudaMalloc((void **)&p, sizeof(T) * (count > 0 ? count : 1));
+}
+
+struct StageScope {
+    Ctx &c;
+    int stage;
+    cudaStream_t st;
+    Ctx::EvPair ev{};
+    bool on = false;
+    StageScope(Ctx &c_, int stage_, cudaStream_t st_, int launches) : c(c_), stage(stage_), st(st_)
+    {
+        c.pending_launches[stage] += launches;
+        if (!c.timing) return;
+        if (c.ev_free.empty()) {
+            Ctx::EvPair p{};
+            if (cudaEventCreate(&p.a) != cudaSuccess) return;
+            if (cudaEventCreate(&p.b) != cudaSuccess) return;
+            c.ev_free.push_back(p);
+        }
+        ev = c.ev_free.back();
+        c.ev_free.pop_back();
+        ev.stage = stage;
+        on = cudaEventRecord(ev.a, st) == cudaSuccess;
+    }
+    ~StageScope()
+    {
+        if (!on) return;
+        cudaEventRecord(ev.b, st);
+        c.ev_pending.push_back(ev);
+    }
+};
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+sph_status check_state(Ctx &c, const sph_state *s, bool need_outputs)
+{
+    if (!s) return fail(c, SPH_ERR_INVALID_ARG, "state is NULL");
+    if (s->n < 0 || s->n > c.max_n) return fail(c, SPH_ERR_INVALID_ARG, "n out of range [0, max_n]");
+    if (s->n == 0) return SPH_OK;
+    if (!s->pos || !s->vel || !s->h || !s->perm || !s->keys)
+        return fail(c, SPH_ERR_INVALID_ARG, "NULL state array");
+    if (need_outputs && (!s->acc || !s->rho || !s->omega || !s->drhodt || !s->vsigmax))
+        return fail(c, SPH_ERR_INVALID_ARG, "NULL output array");
+    if (!aligned16(s->pos) || !aligned16(s->vel) || (s->acc && !aligned16(s->acc)))
+        return fail(c, SPH_ERR_INVALID_ARG, "pos/vel/acc must be 16-byte aligned");
+    return SPH_OK;
+}
+
+sph_status check_params(Ctx &c, const sph_params *p)
+{
+    if (!p) return fail(c, SPH_ERR_INVALID_ARG, "params is NULL");
+    if (!(p->gamma > 1.f) || !(p->hfact > 0.f) || !(p->h_tol > 0.f) || !(p->c_cour > 0.f) ||
+        !(p->alpha_av >= 0.f) || !(p->beta_av >= 0.f) || !(p->alpha_u >= 0.f))
+        return fail(c, SPH_ERR_INVALID_ARG, "parameter out of range");
+    if (p->kernel != 0) return fail(c, SPH_ERR_INVALID_ARG, "only the M4 kernel (0) is built");
+    if (p->n_leaf < 1 || p->n_leaf > 64 || p->n_group < 1 || p->n_group > 32)
+        return fail(c, SPH_ERR_INVALID_ARG, "n_leaf must be 1..64 and n_group 1..32");
+    if (p->tile < 0 || p->tile > 128 || p->max_h_iter < 1 || p->density_iters < 0)
+        return fail(c, SPH_ERR_INVALID_ARG, "tile 0..128, max_h_iter >= 1, density_iters >= 0");
+    return SPH_OK;
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+constexpr int kTreeLaunches = 50;
+constexpr int kPrepLaunches = 3;
+
+sph_status do_density(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st)
+{
+    StageScope sc(c, ST_DENSITY, st, 1);
+    CK(density_pass(c, s, p, st), "density");
+    return SPH_OK;
+}
+
+sph_status do_force(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st)
+{
+    {
+        StageScope sc(c, ST_PREP, st, kPrepLaunches);
+        CK(force_prep(c, s, p, st), "force_prep");
+    }
+    StageScope sc(c, ST_FORCE, st, 1);
+    CK(force_pass(c, s, p, st), "force");
+    return SPH_OK;
+}
+
+sph_status do_tree(Ctx &c, const sph_state &s, const sph_params &p, bool full, cudaStream_t st)
+{
+    StageScope sc(c, ST_TREE, st, kTreeLaunches);
+    CK(build_tree(c, s, p, full, st), "build_tree");
+    return SPH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sph_params_default(sph_params *p)
+{
+    if (!p) return;
+    p->gamma = 5.0f / 3.0f;
+    p->hfact = 1.2f;
+    p->alpha_av = 1.0f;
+    p->beta_av = 2.0f;
+    p->alpha_u = 1.0f;
+    p->c_cour = 0.3f;
+    p->h_tol = 1e-6f;
+    p->kernel = 0;
+    p->n_leaf = 16;
+    p->n_group = 8;
+    p->tile = 0;
+    p->max_h_iter = 50;
+    p->density_iters = 0;
+}
+
+sph_status sph_create(sph_ctx **out, int64_t max_n, int device)
+{
+    if (!out) return SPH_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (max_n < 1 || max_n >= (int64_t)1 << 31) return SPH_ERR_INVALID_ARG;
+    sph_ctx *h = new (std::nothrow) sph_ctx();
+    if (!h) return SPH_ERR_NOMEM;
+    Ctx &c = h->impl;
+    c.device = device;
+    c.max_n = max_n;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        delete h;
+        return SPH_ERR_CUDA;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        delete h;
+        return SPH_ERR_CUDA;
+    }
+    c.num_sms = prop.multiProcessorCount;
+    const size_t n = (size_t)max_n;
+    c.ntiles_cap = div_up(max_n, 2048);
+    int nbchop = div_up(max_n, kChopBlock);
+    int64_t scan_n = max_n > (int64_t)kLevels * nbchop ? max_n : (int64_t)kLevels * nbchop;
+    c.scan_part_cap = div_up(scan_n, 2048) + 16;
+    c.red_cap = c.num_sms * 16;
+    Tree &t = c.tree;
+    t.cap_nodes = (int)(2 * n + 1024 < (size_t)INT32_MAX ? 2 * n + 1024 : INT32_MAX);
+    t.cap_groups = (int)n;
+    cudaError_t e = cudaSuccess;
+    auto A = [&](cudaError_t r) { if (e == cudaSuccess) e = r; };
+    A(dalloc(c.keys_alt, n));
+    A(dalloc(c.idx_a, n));
+    A(dalloc(c.idx_b, n));
+    A(dalloc(c.hist, (size_t)256 * c.ntiles_cap));
+    A(dalloc(c.dtotal, 256));
+    for (int k = 0; k < 4; ++k) A(dalloc(c.tmp4[k], n));
+    for (int k = 0; k < 5; ++k) A(dalloc(c.tmp1[k], n));
+    A(dalloc(c.tmp_perm, n));
+    A(dalloc(t.node_first, t.cap_nodes));
+    A(dalloc(t.node_count, t.cap_nodes));
+    A(dalloc(t.node_level, t.cap_nodes));
+    A(dalloc(t.node_child, t.cap_nodes));
+    A(dalloc(t.node_nchild, t.cap_nodes));
+    A(dalloc(t.node_parent, t.cap_nodes));
+    A(dalloc(t.node_arrive, t.cap_nodes));
+    A(dalloc(t.node_lo, t.cap_nodes));
+    A(dalloc(t.node_hi, t.cap_nodes));
+    A(dalloc(t.node_ref, t.cap_nodes));
+    A(dalloc(t.level_start, kLevels + 1));
+    A(dalloc(t.grp_ref, t.cap_groups));
+    A(dalloc(t.grp_lo, t.cap_groups));
+    A(dalloc(t.grp_hi, t.cap_groups));
+    A(dalloc(t.lv_tree, n));
+    A(dalloc(t.lv_grp, n));
+    A(dalloc(t.blk_cnt, (size_t)kLevels * nbchop));
+    A(dalloc(c.prop, n));
+    A(dalloc(c.vhalf, n));
+    A(dalloc(c.bbox, 8));
+    A(dalloc(c.scan_part, c.scan_part_cap));
+    A(dalloc(c.red_f, c.red_cap));
+    A(dalloc(c.red_d, (size_t)8 * c.red_cap));
+    A(dalloc(c.d_err, 1));
+    A(dalloc(c.d_counters, C_N));
+    A(dalloc(c.d_sizes, SZ_N));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&c.h_pinned, 64);
+    if (e == cudaSuccess) e = cudaMemset(c.d_err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c.d_counters, 0, sizeof(unsigned long long) * C_N);
+    if (e == cudaSuccess) e = cudaMemset(c.d_sizes, 0, sizeof(int) * SZ_N);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        sph_destroy(h);
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? SPH_ERR_NOMEM : SPH_ERR_CUDA;
+    }
+    *out = h;
+    return SPH_OK;
+}
+
+void sph_destroy(sph_ctx *h)
+{
+    if (!h) return;
+    Ctx &c = h->impl;
+    cudaSetDevice(c.device);
+    cudaDeviceSynchronize();
+    void *ptrs[] = {c.keys_alt, c.idx_a, c.idx_b, c.hist, c.dtotal, c.tmp4[0], c.tmp4[1], c.tmp4[2],
+                    c.tmp4[3], c.tmp1[0], c.tmp1[1], c.tmp1[2], c.tmp1[3], c.tmp1[4], c.tmp_perm,
+                    c.tree.node_first, c.tree.node_count, c.tree.node_level, c.tree.node_child,
+                    c.tree.node_nchild, c.tree.node_parent, c.tree.node_arrive, c.tree.node_lo,
+                    c.tree.node_hi, c.tree.node_ref, c.tree.level_start, c.tree.grp_ref,
+                    c.tree.grp_lo, c.tree.grp_hi, c.tree.lv_tree, c.tree.lv_grp, c.tree.blk_cnt,
+                    c.prop, c.vhalf, c.bbox, c.scan_part, c.red_f, c.red_d, c.d_err, c.d_counters,
+                    c.d_sizes, c.mirror.pos, c.mirror.vel, c.mirror.acc, c.mirror.h, c.mirror.rho,
+                    c.mirror.omega, c.mirror.drhodt, c.mirror.vsigmax, c.mirror.perm,
+                    c.mirror.keys, c.mirror_dt};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (c.h_pinned) cudaFreeHost(c.h_pinned);
+    for (auto &p : c.ev_free) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (auto &p : c.ev_pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    delete h;
+}
+
+sph_status sph_build_tree(sph_ctx *h, sph_state *s, const sph_params *p, void *stream)
+{
+    if (!h) return SPH_ERR_INVALID_ARG;
+    Ctx &c = h->impl;
+    sph_status r = check_state(c, s, true);
+    if (r != SPH_OK) return r;
+    if ((r = check_params(c, p)) != SPH_OK) return r;
+    if (s->n == 0) return SPH_OK;
+    return do_tree(c, *s, *p, true, (cudaStream_t)stream);
+}
+
+sph_status sph_density(sph_ctx *h, sph_state *s, const sph_params *p, void *stream)
+{
+    if (!h) return SPH_ERR_INVALID_ARG;
+    Ctx &c = h->impl;
+    sph_status r = check_state(c, s, true);
+    if (r != SPH_OK) return r;
+    if ((r = check_params(c, p)) != SPH_OK) return r;
+    if (s->n == 0) return SPH_OK;
+    return do_density(c, *s, *p, (cudaStream_t)stream);
+}
+
+sph_status sph_force(sph_ctx *h, sph_state *s, const sph_params *p, void *stream)
+{
+    if (!h) return SPH_ERR_INVALID_ARG;
+    Ctx &c = h->impl;
+    sph_status r = check_state(c, s, true);
+    if (r != SPH_OK) return r;
+    if ((r = check_params(c, p)) != SPH_OK) return r;
+    if (s->n == 0) return SPH_OK;
+    return do_force(c, *s, *p, (cudaStream_t)stream);
+}
+
+sph_status sph_timestep(sph_ctx *h, const sph_state *s, const sph_params *p, float *d_dt,
+                        void *stream)
+{
+    if (!h) return SPH_ERR_INVALID_ARG;
+    Ctx &c = h->impl;
+    sph_status r = check_state(c, s, true);
+    if (r != SPH_OK) return r;
+    if ((r = check_params(c, p)) != SPH_OK) return r;
+    if (!d_dt) return fail(c, SPH_ERR_INVALID_ARG, "d_dt is NULL");
+    if (s->n == 0) return SPH_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    StageScope sc(c, ST_REDUCE, st, 2);
+    CK(courant_dt(c, *s, *p, d_dt, st), "timestep");
+    return SPH_OK;
+}
+
+sph_status sph_step(sph_ctx *h, sph_state *s, const sph_params *p, float *d_dt, double *d_time,
+                    void *stream)
+{
+    if (!h) return SPH_ERR_INVALID_ARG;
+    Ctx &c = h->impl;
+    sph_status r = check_state(c, s, true);
+    if (r != SPH_OK) return r;
+    if ((r = check_params(c, p)) != SPH_OK) return r;
+    if (!d_dt) return fail(c, SPH_ERR_INVALID_ARG, "d_dt is NULL");
+    if (s->n == 0) return SPH_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    {
+        StageScope sc(c, ST_LEAPFROG, st, 1);
+        CK(kick_drift(c, *s, d_dt, st), "kick_drift");
+    }
+    if ((r = do_tree(c, *s, *p, false, st)) != SPH_OK) return r;
+    if ((r = do_density(c, *s, *p, st)) != SPH_OK) return r;
+    if ((r = do_force(c, *s, *p, st)) != SPH_OK) return r;
+    {
+        StageScope sc(c, ST_LEAPFROG, st, 1);
+        CK(kick_close(c, *s, d_dt, d_time, st), "kick_close");
+    }
+    {
+        StageScope sc(c, ST_REDUCE, st, 2);
+        CK(courant_dt(c, *s, *p, d_dt, st), "timestep");
+    }
+    return SPH_OK;
+}
+
+sph_status sph_step_host(sph_ctx *h, sph_state *hs, const sph_params *p, int n_steps, float *h_dt,
+                         void *stream)
+{
+    if (!h) return SPH_ERR_INVALID_ARG;
+    Ctx &c = h->impl;
+    if (!hs || !h_dt || n_steps < 0) return fail(c, SPH_ERR_INVALID_ARG, "NULL argument");
+    sph_status r = check_params(c, p);
+    if (r != SPH_OK) return r;
+    if (hs->n < 0 || hs->n > c.max_n) return fail(c, SPH_ERR_INVALID_ARG, "n out of range");
+    const int64_t n = hs->n;
+    if (n == 0) return SPH_OK;
+    if (!hs->pos || !hs->vel || !hs->acc || !hs->h || !hs->rho || !hs->omega || !hs->drhodt ||
+        !hs->vsigmax || !hs->perm || !hs->keys)
+        return fail(c, SPH_ERR_INVALID_ARG, "NULL host array");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (c.mirror_n < n) {
+        sph_state &m = c.mirror;
+        void *old[] = {m.pos, m.vel, m.acc, m.h, m.rho, m.omega, m.drhodt, m.vsigmax, m.perm, m.keys};
+        for (void *q : old)
+            if (q) cudaFree(q);
+        m = sph_state{};
+        cudaError_t e = cudaSuccess;
+        auto A = [&](cudaError_t x) { if (e == cudaSuccess) e = x; };
+        size_t nn = (size_t)c.max_n;
+        A(cudaMalloc((void **)&m.pos, nn * 16));
+        A(cudaMalloc((void **)&m.vel, nn * 16));
+        A(cudaMalloc((void **)&m.acc, nn * 16));
+        A(cudaMalloc((void **)&m.h, nn * 4));
+        A(cudaMalloc((void **)&m.rho, nn * 4));
+        A(cudaMalloc((void **)&m.omega, nn * 4));
+        A(cudaMalloc((void **)&m.drhodt, nn * 4));
+        A(cudaMalloc((void **)&m.vsigmax, nn * 4));
+        A(cudaMalloc((void **)&m.perm, nn * 4));
+        A(cudaMalloc((void **)&m.keys, nn * 8));
+        if (!c.mirror_dt) A(cudaMalloc((void **)&c.mirror_dt, sizeof(float)));
+        if (e != cudaSuccess) return cuda_fail(c, e, "step_host mirror allocation");
+        c.mirror_n = c.max_n;
+    }
+    sph_state d = c.mirror;
+    d.n = n;
+    const cudaMemcpyKind H2D = cudaMemcpyHostToDevice, D2H = cudaMemcpyDeviceToHost;
+    CK(cudaMemcpyAsync(d.pos, hs->pos, n * 16, H2D, st), "H2D pos");
+    CK(cudaMemcpyAsync(d.vel, hs->vel, n * 16, H2D, st), "H2D vel");
+    CK(cudaMemcpyAsync(d.acc, hs->acc, n * 16, H2D, st), "H2D acc");
+    CK(cudaMemcpyAsync(d.h, hs->h, n * 4, H2D, st), "H2D h");
+    CK(cudaMemcpyAsync(d.perm, hs->perm, n * 4, H2D, st), "H2D perm");
+    CK(cudaMemcpyAsync(c.mirror_dt, h_dt, sizeof(float), H2D, st), "H2D dt");
+    for (int k = 0; k < n_steps; ++k)
+        if ((r = sph_step(h, &d, p, c.mirror_dt, nullptr, stream)) != SPH_OK) return r;
+    CK(cudaMemcpyAsync(hs->pos, d.pos, n * 16, D2H, st), "D2H pos");
+    CK(cudaMemcpyAsync(hs->vel, d.vel, n * 16, D2H, st), "D2H vel");
+    CK(cudaMemcpyAsync(hs->acc, d.acc, n * 16, D2H, st), "D2H acc");
+    CK(cudaMemcpyAsync(hs->h, d.h, n * 4, D2H, st), "D2H h");
+    CK(cudaMemcpyAsync(hs->rho, d.rho, n * 4, D2H, st), "D2H rho");
+    CK(cudaMemcpyAsync(hs->omega, d.omega, n * 4, D2H, st), "D2H omega");
+    CK(cudaMemcpyAsync(hs->drhodt, d.drhodt, n * 4, D2H, st), "D2H drhodt");
+    CK(cudaMemcpyAsync(hs->vsigmax, d.vsigmax, n * 4, D2H, st), "D2H vsigmax");
+    CK(cudaMemcpyAsync(hs->perm, d.perm, n * 4, D2H, st), "D2H perm");
+    CK(cudaMemcpyAsync(hs->keys, d.keys, n * 8, D2H, st), "D2H keys");
+    CK(cudaMemcpyAsync(h_dt, c.mirror_dt, sizeof(float), D2H, st), "D2H dt");
+    return sph_sync(h, stream);
+}
+
+sph_status sph_conserved(sph_ctx *h, const sph_state *s, double *d_out8, void *stream)
+{
+    if (!h) return SPH_ERR_INVALID_ARG;
+    Ctx &c = h->impl;
+    sph_status r = check_state(c, s, false);
+    if (r != SPH_OK) return r;
+    if (!d_out8) return fail(c, SPH_ERR_INVALID_ARG, "d_out8 is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (s->n == 0) {
+        CK(cudaMemsetAsync(d_out8, 0, 8 * sizeof(double), st), "memset");
+        return SPH_OK;
+    }
+    StageScope sc(c, ST_REDUCE, st, 2);
+    CK(conserved(c, *s, d_out8, st), "conserved");
+    return SPH_OK;
+}
+
+sph_status sph_neighbours(sph_ctx *h, const sph_state *s, const sph_params *p, int mode,
+                          int64_t *d_off, int32_t *d_idx, int64_t cap, int64_t *h_total,
+                          void *stream)
+{
+    if (!h) return SPH_ERR_INVALID_ARG;
+    Ctx &c = h->impl;
+    sph_status r = check_state(c, s, false);
+    if (r != SPH_OK) return r;
+    if ((r = check_params(c, p)) != SPH_OK) return r;
+    if ((mode != 0 && mode != 1) || !d_off || !h_total)
+        return fail(c, SPH_ERR_INVALID_ARG, "mode must be 0 or 1; d_off and h_total required");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (s->n == 0) {
+        *h_total = 0;
+        CK(cudaMemsetAsync(d_off, 0, sizeof(int64_t), st), "memset");
+        return sph_sync(h, stream);
+    }
+    // the force set needs the current h in the node/group bounds
+    CK(update_hmax(c, *s, *p, st), "update_hmax");
+    CK(neighbour_lists(c, *s, *p, mode, d_off, d_idx, cap, h_total, st), "neighbours");
+    return sph_sync(h, stream);
+}
+
+sph_status sph_get_tree(sph_ctx *h, int32_t *h_level, int32_t *h_first, int32_t *h_count,
+                        int32_t *h_nchild, int32_t *h_child, int64_t node_cap,
+                        int32_t *h_gfirst, int32_t *h_gcount, int64_t group_cap,
+                        int64_t *n_nodes, int64_t *n_groups)
+{
+    if (!h || !n_nodes || !n_groups) return SPH_ERR_INVALID_ARG;
+    Ctx &c = h->impl;
+    int sz[SZ_N];
+    CK(cudaDeviceSynchronize(), "tree sync");
+    CK(cudaMemcpy(sz, c.d_sizes, sizeof(sz), cudaMemcpyDeviceToHost), "sizes copy");
+    *n_nodes = sz[SZ_NODES];
+    *n_groups = sz[SZ_GROUPS];
+    const Tree &t = c.tree;
+    if (sz[SZ_NODES] <= node_cap) {
+        size_t b = sizeof(int32_t) * (size_t)sz[SZ_NODES];
+        if (h_level) CK(cudaMemcpy(h_level, t.node_level, b, cudaMemcpyDeviceToHost), "copy");
+        if (h_first) CK(cudaMemcpy(h_first, t.node_first, b, cudaMemcpyDeviceToHost), "copy");
+        if (h_count) CK(cudaMemcpy(h_count, t.node_count, b, cudaMemcpyDeviceToHost), "copy");
+        if (h_nchild) CK(cudaMemcpy(h_nchild, t.node_nchild, b, cudaMemcpyDeviceToHost), "copy");
+        if (h_child) CK(cudaMemcpy(h_child, t.node_child, b, cudaMemcpyDeviceToHost), "copy");
+    }
+    if (sz[SZ_GROUPS] <= group_cap && sz[SZ_GROUPS] > 0) {
+        std::vector<int2> g((size_t)sz[SZ_GROUPS]);
+        CK(cudaMemcpy(g.data(), t.grp_ref, sizeof(int2) * g.size(), cudaMemcpyDeviceToHost), "copy");
+        for (size_t k = 0; k < g.size(); ++k) {
+            if (h_gfirst) h_gfirst[k] = g[k].x;
+            if (h_gcount) h_gcount[k] = g[k].y;
+        }
+    }
+    return SPH_OK;
+}
+
+sph_status sph_get_stats(sph_ctx *h, sph_stats *out)
+{
+    if (!h || !out) return SPH_ERR_INVALID_ARG;
+    Ctx &c = h->impl;
+    unsigned long long v[C_N];
+    int sz[SZ_N];
+    CK(cudaDeviceSynchronize(), "stats sync");
+    CK(cudaMemcpy(v, c.d_counters, sizeof(v), cudaMemcpyDeviceToHost), "stats copy");
+    CK(cudaMemcpy(sz, c.d_sizes, sizeof(sz), cudaMemcpyDeviceToHost), "sizes copy");
+    CK(cudaMemset(c.d_counters, 0, sizeof(v)), "stats reset");
+    out->density_pairs = v[C_DENS_PAIRS];
+    out->density_candidates = v[C_DENS_CAND];
+    out->force_pairs = v[C_FORCE_PAIRS];
+    out->force_candidates = v[C_FORCE_CAND];
+    out->newton_iters = v[C_NEWTON];
+    out->density_rewalks = v[C_REWALK];
+    out->streamed_groups = v[C_STREAMED];
+    out->n_nodes = (uint64_t)sz[SZ_NODES];
+    out->n_groups = (uint64_t)sz[SZ_GROUPS];
+    return SPH_OK;
+}
+
+sph_status sph_set_timing(sph_ctx *h, int enable)
+{
+    if (!h) return SPH_ERR_INVALID_ARG;
+    h->impl.timing = enable != 0;
+    return SPH_OK;
+}
+
+sph_status sph_get_timing(sph_ctx *h, double *ms, int64_t *launches)
+{
+    if (!h) return SPH_ERR_INVALID_ARG;
+    Ctx &c = h->impl;
+    for (auto &p : c.ev_pending) {
+        CK(cudaEventSynchronize(p.b), "timing sync");
+        float t = 0.f;
+        CK(cudaEventElapsedTime(&t, p.a, p.b), "timing elapsed");
+        c.stage_ms[p.stage] += t;
+        c.ev_free.push_back(p);
+    }
+    c.ev_pending.clear();
+    for (int k = 0; k < ST_N; ++k) {
+        if (ms) ms[k] = c.stage_ms[k];
+        if (launches) launches[k] = c.pending_launches[k];
+        c.stage_ms[k] = 0;
+        c.pending_launches[k] = 0;
+    }
+    return SPH_OK;
+}
+
+sph_status sph_sync(sph_ctx *h, void *stream)
+{
+    if (!h) return SPH_ERR_INVALID_ARG;
+    Ctx &c = h->impl;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaStreamSynchronize(st), "sync");
+    CK(cudaMemcpy(c.h_pinned, c.d_err, sizeof(int), cudaMemcpyDeviceToHost), "error word");
+    int w = c.h_pinned[0];
+    if (w == 0) return SPH_OK;
+    CK(cudaMemset(c.d_err, 0, sizeof(int)), "error reset");
+    std::string msg = "device reported:";
+    sph_status first = SPH_OK;
+    for (int k = 1; k <= (int)SPH_ERR_TIMEOUT; ++k)
+        if (w & (1 << k)) {
+            msg += " ";
+            msg += status_text((sph_status)k);
+            msg += ";";
+            if (first == SPH_OK) first = (sph_status)k;
+        }
+    c.last_error = msg;
+    return first;
+}
+
+const char *sph_last_error(sph_ctx *h)
+{
+    if (!h) return "NULL context";
+    return h->impl.last_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,152 @@
+// Internal definitions shared by the library's translation units.
+// Not part of the public ABI (include/sph.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "sph.h"
+
+namespace sph {
+
+constexpr int kMaxLevel = 21;        // 21 bits per axis, 63-bit keys
+constexpr int kLevels = 22;          // levels 0..21
+constexpr int kWarp = 32;
+constexpr float kCNorm = 0.318309886183790671538f;  // M4, 3D: 1/pi
+
+// stage ids for the per-stage timers
+enum Stage { ST_TREE = 0, ST_DENSITY = 1, ST_FORCE = 2, ST_REDUCE = 3, ST_LEAPFROG = 4, ST_PREP = 5, ST_N = 6 };
+
+// device error word: bit (1 << status) per condition seen
+__device__ __forceinline__ void raise_error(int *err, sph_status code)
+{
+    atomicOr(err, 1 << (int)code);
+}
+
+// device counters (indices into Ctx::d_counters)
+enum Counter {
+    C_DENS_PAIRS = 0,
+    C_DENS_CAND = 1,
+    C_FORCE_PAIRS = 2,
+    C_FORCE_CAND = 3,
+    C_NEWTON = 4,
+    C_REWALK = 5,
+    C_STREAMED = 6,
+    C_N = 8
+};
+
+// tree-size scalars on the device (Ctx::d_sizes)
+enum Size { SZ_NODES = 0, SZ_GROUPS = 1, SZ_N = 4 };
+
+struct Tree {
+    int cap_nodes = 0;
+    int cap_groups = 0;
+    // nodes, level-major, first-particle order inside a level
+    int *node_first = nullptr, *node_count = nullptr, *node_level = nullptr;
+    int *node_child = nullptr, *node_nchild = nullptr, *node_parent = nullptr;
+    int *node_arrive = nullptr;
+    float4 *node_lo = nullptr;   // x, y, z, h_max
+    float4 *node_hi = nullptr;   // x, y, z, unused
+    int2 *node_ref = nullptr;    // leaf: (first, count); internal: (child_first, -nchild)
+    int *level_start = nullptr;  // [kLevels + 1]
+    // groups: terminal nodes of the n_group chop
+    int2 *grp_ref = nullptr;     // (first, count)
+    float4 *grp_lo = nullptr;    // x, y, z, h_max
+    float4 *grp_hi = nullptr;
+    // chop scratch
+    int *lv_tree = nullptr, *lv_grp = nullptr;
+    int *blk_cnt = nullptr;      // [kLevels][nb]
+};
+
+struct Ctx {
+    int device = 0;
+    int64_t max_n = 0;
+    int num_sms = 0;
+    std::string last_error;
+
+    // sort scratch
+    uint64_t *keys_alt = nullptr;
+    uint32_t *idx_a = nullptr, *idx_b = nullptr;
+    uint32_t *hist = nullptr;    // [256][ntiles]
+    uint32_t *dtotal = nullptr;  // [256]
+    int ntiles_cap = 0;
+
+    // gather scratch
+    float4 *tmp4[4] = {nullptr, nullptr, nullptr, nullptr};
+    float *tmp1[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    uint32_t *tmp_perm = nullptr;
+
+    Tree tree;
+
+    // per-particle scratch
+    float4 *prop = nullptr;   // h, rho, 1/(rho Omega), c_s
+    float4 *vhalf = nullptr;  // half-step v, u of the leapfrog
+    float *bbox = nullptr;    // [8]: lo xyz, size, then scratch
+
+    // scan scratch
+    int *scan_part = nullptr;
+    int scan_part_cap = 0;
+
+    // reductions
+    float *red_f = nullptr;     // block minima
+    double *red_d = nullptr;    // block partial sums [8][nb]
+    int red_cap = 0;
+
+    int *d_err = nullptr;
+    unsigned long long *d_counters = nullptr;
+    int *d_sizes = nullptr;
+    int *h_pinned = nullptr;  // small pinned host buffer
+
+    // host-buffer mirror (sph_step_host)
+    sph_state mirror{};
+    float *mirror_dt = nullptr;
+    int64_t mirror_n = 0;
+
+    // timing
+    bool timing = false;
+    struct EvPair { cudaEvent_t a, b; int stage; };
+    std::vector<EvPair> ev_free, ev_pending;
+    double stage_ms[ST_N] = {0, 0, 0, 0, 0, 0};
+    int64_t stage_launches[ST_N] = {0, 0, 0, 0, 0, 0};
+    int64_t pending_launches[ST_N] = {0, 0, 0, 0, 0, 0};
+};
+
+// ---------------------------------------------------------------------------
+// launchers (host functions) implemented in the .cu files
+// ---------------------------------------------------------------------------
+// tree.cu
+cudaError_t build_tree(Ctx &c, const sph_state &s, const sph_params &p, bool full_permute,
+                       cudaStream_t st);
+cudaError_t update_hmax(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st);
+cudaError_t scan_exclusive_int(Ctx &c, const int *in, int *out, int n, int *total_dev,
+                               cudaStream_t st);
+// density.cu
+cudaError_t density_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st);
+cudaError_t neighbour_lists(Ctx &c, const sph_state &s, const sph_params &p, int mode,
+                            int64_t *d_off, int32_t *d_idx, int64_t cap, int64_t *h_total,
+                            cudaStream_t st);
+// force.cu
+cudaError_t force_prep(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st);
+cudaError_t force_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st);
+// integrate.cu
+cudaError_t kick_drift(Ctx &c, const sph_state &s, const float *d_dt, cudaStream_t st);
+cudaError_t kick_close(Ctx &c, const sph_state &s, const float *d_dt, double *d_time,
+                       cudaStream_t st);
+cudaError_t courant_dt(Ctx &c, const sph_state &s, const sph_params &p, float *d_dt,
+                       cudaStream_t st);
+cudaError_t conserved(Ctx &c, const sph_state &s, double *d_out8, cudaStream_t st);
+
+// helpers
+inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// number of blocks used by the chop's per-block counting (1024 particles each)
+constexpr int kChopBlock = 1024;
+
+}  // namespace sph
+
+struct sph_ctx {
+    sph::Ctx impl;
+};

@@ -1,0 +1,679 @@
+// Tree build (Sect. 3.1): bounding box, Morton keys, radix sort, in-place
+// permutation into curve order, octree chop and group chop, node bounds.
+//
+// Chop: the paper builds the tree level by level, splitting every curve
+// section with more than N_leaf particles.  Here the same node set is found
+// with O(1) work per particle instead of one pass per level.  With d(s) the
+// first level at which key[s] differs from key[s-1] (s starts a run at every
+// level >= d(s)), the nodes that start at particle s are the levels
+// d(s) .. Lmax(s), provided the run containing s at level d(s)-1 holds more
+// than T particles; Lmax(s) = max(d(s), min(c + 1, 21)), where c is the number
+// of leading 3-bit digits key[s] shares with key[s+T] (the run starting at s
+// holds more than T particles exactly at the levels <= c).  A node is terminal
+// at Lmax(s), so the terminal nodes (the groups, for T = N_group) start at the
+// particles with any node at all.  Nodes are numbered level by level and by
+// first particle inside a level, the order of the level-by-level chop.
+#include "sph_internal.cuh"
+
+namespace sph {
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ int ord_of(float f)
+{
+    int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float float_of(int o)
+{
+    return __int_as_float(o >= 0 ? o : o ^ 0x7fffffff);
+}
+
+// number of equal leading 3-bit digits of two 63-bit keys (0..21)
+__device__ __forceinline__ int common_digits(uint64_t a, uint64_t b)
+{
+    uint64_t x = a ^ b;
+    if (x == 0) return kMaxLevel;
+    int hb = 63 - __clzll((long long)x);
+    return (62 - hb) / 3;
+}
+
+__device__ __forceinline__ uint64_t spread21(uint32_t v)
+{
+    uint64_t x = v & 0x1fffffu;
+    x = (x | x << 32) & 0x1f00000000ffffull;
+    x = (x | x << 16) & 0x1f0000ff0000ffull;
+    x = (x | x << 8) & 0x100f00f00f00f00full;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+    x = (x | x << 2) & 0x1249249249249249ull;
+    return x;
+}
+
+// ------------------------------------------------------------ bbox + checks
+__global__ void bbox_init_kernel(int *bb)
+{
+    if (threadIdx.x < 3) bb[threadIdx.x] = 0x7fffffff;           // min of ordered ints
+    else if (threadIdx.x < 6) bb[threadIdx.x] = (int)0x80000000; // max
+}
+
+__global__ void bbox_kernel(const float4 *__restrict__ pos, const float *__restrict__ h, int n,
+                            int *bb, int *err)
+{
+    int mn[3] = {0x7fffffff, 0x7fffffff, 0x7fffffff};
+    int mx[3] = {(int)0x80000000, (int)0x80000000, (int)0x80000000};
+    bool bad = false;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float4 p = pos[i];
+        float hh = h[i];
+        bad |= !(isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && isfinite(p.w) &&
+                 isfinite(hh) && p.w > 0.f && hh > 0.f);
+        int o0 = ord_of(p.x), o1 = ord_of(p.y), o2 = ord_of(p.z);
+        mn[0] = min(mn[0], o0); mx[0] = max(mx[0], o0);
+        mn[1] = min(mn[1], o1); mx[1] = max(mx[1], o1);
+        mn[2] = min(mn[2], o2); mx[2] = max(mx[2], o2);
+    }
+    for (int o = 16; o > 0; o >>= 1)
+        for (int a = 0; a < 3; ++a) {
+            mn[a] = min(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+            mx[a] = max(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+        }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) raise_error(err, SPH_ERR_NONFINITE);
+    if ((threadIdx.x & 31) == 0)
+        for (int a = 0; a < 3; ++a) {
+            atomicMin(bb + a, mn[a]);
+            atomicMax(bb + 3 + a, mx[a]);
+        }
+}
+
+// canonical FP32 quantisation, see include/sph.h
+__global__ void morton_kernel(const float4 *__restrict__ pos, int n, const int *bb,
+                              uint64_t *__restrict__ keys, uint32_t *__restrict__ idx)
+{
+    float lo[3], size = 0.f;
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = float_of(bb[a]);
+        float e = __fsub_rn(float_of(bb[3 + a]), lo[a]);
+        size = e > size ? e : size;
+    }
+    float s = size > 0.f ? __fdiv_rn(2097152.0f, size) : 0.f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        float4 p = pos[i];
+        float x[3] = {p.x, p.y, p.z};
+        uint32_t c[3];
+        for (int a = 0; a < 3; ++a) {
+            float t = __fmul_rn(__fsub_rn(x[a], lo[a]), s);
+            uint32_t v = (uint32_t)floorf(t);
+            c[a] = v > 2097151u ? 2097151u : v;
+        }
+        keys[i] = (spread21(c[0]) << 2) | (spread21(c[1]) << 1) | spread21(c[2]);
+        idx[i] = (uint32_t)i;
+    }
+}
+
+// ------------------------------------------------------------- radix sort
+// Stable LSD radix sort of (key, index), 8-bit digits, 8 passes over the
+// 64-bit word.  Per pass: tile histograms, per-digit scan over tiles, digit
+// bases, then a scatter that ranks equal digits inside a tile in input order
+// (warp match + per-warp counts), which keeps the sort stable.
+constexpr int RS_T = 256, RS_I = 8, RS_TILE = RS_T * RS_I;
+
+__global__ void __launch_bounds__(RS_T) rs_hist_kernel(const uint64_t *__restrict__ keys, int n,
+                                                       int shift, uint32_t *hist, int ntiles)
+{
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int base = blockIdx.x * RS_TILE;
+#pragma unroll
+    for (int i = 0; i < RS_I; ++i) {
+        int s = base + i * RS_T + threadIdx.x;
+        if (s < n) atomicAdd(&h[(keys[s] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// block-wide exclusive scan helper for 256 threads, returns the block total
+__device__ __forceinline__ uint32_t block_scan_256(uint32_t v, uint32_t &excl, uint32_t *ws)
+{
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t t = lane < 8 ? ws[lane] : 0;
+        for (int o = 1; o < 8; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < 8) ws[lane] = t;
+    }
+    __syncthreads();
+    uint32_t wbase = w > 0 ? ws[w - 1] : 0;
+    uint32_t total = ws[7];
+    excl = wbase + x - v;
+    __syncthreads();
+    return total;
+}
+
+__global__ void __launch_bounds__(256) rs_scan_rows_kernel(uint32_t *hist, int ntiles,
+                                                           uint32_t *dtotal)
+{
+    __shared__ uint32_t ws[8];
+    uint32_t *row = hist + (size_t)blockIdx.x * ntiles;
+    uint32_t carry = 0;
+    for (int b = 0; b < ntiles; b += 256) {
+        int i = b + threadIdx.x;
+        uint32_t v = i < ntiles ? row[i] : 0, ex;
+        uint32_t tot = block_scan_256(v, ex, ws);
+        if (i < ntiles) row[i] = carry + ex;
+        carry += tot;
+    }
+    if (threadIdx.x == 0) dtotal[blockIdx.x] = carry;
+}
+
+__global__ void __launch_bounds__(256) rs_digit_base_kernel(uint32_t *dtotal)
+{
+    __shared__ uint32_t ws[8];
+    uint32_t v = dtotal[threadIdx.x], ex;
+    block_scan_256(v, ex, ws);
+    dtotal[threadIdx.x] = ex;
+}
+
+__global__ void __launch_bounds__(RS_T) rs_scatter_kernel(
+    const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
+    uint32_t *__restrict__ vout, int n, int shift, const uint32_t *__restrict__ hist,
+    const uint32_t *__restrict__ dbase, int ntiles)
+{
+    __shared__ uint32_t base[256];
+    __shared__ uint32_t run[256];
+    __shared__ uint32_t wcnt[8][256];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    base[tid] = hist[tid * ntiles + blockIdx.x] + dbase[tid];
+    run[tid] = 0;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int tile0 = blockIdx.x * RS_TILE;
+    for (int r = 0; r < RS_I; ++r) {
+        uint32_t *flat = &wcnt[0][0];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) flat[tid * 8 + k] = 0;
+        __syncthreads();
+        int s = tile0 + r * RS_T + tid;
+        bool valid = s < n;
+        uint64_t key = valid ? kin[s] : 0;
+        uint32_t val = valid ? vin[s] : 0;
+        uint32_t d = valid ? (uint32_t)((key >> shift) & 255u) : 256u + lane;
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t rank = __popc(peers & lt);
+        if (valid && rank == 0) wcnt[w][d] = __popc(peers);
+        __syncthreads();
+        {
+            uint32_t acc = run[tid];
+#pragma unroll
+            for (int ww = 0; ww < 8; ++ww) {
+                uint32_t c = wcnt[ww][tid];
+                wcnt[ww][tid] = acc;
+                acc += c;
+            }
+            run[tid] = acc;
+        }
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = base[d] + wcnt[w][d] + rank;
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ gather
+struct GatherArgs {
+    const uint32_t *order;
+    float4 *a4[4];
+    float4 *t4[4];
+    float *a1[5];
+    float *t1[5];
+    uint32_t *perm, *tperm;
+    int n4, n1;
+};
+
+__global__ void gather_kernel(GatherArgs g, int n)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        uint32_t o = g.order[k];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+            if (a < g.n4) g.t4[a][k] = g.a4[a][o];
+#pragma unroll
+        for (int a = 0; a < 5; ++a)
+            if (a < g.n1) g.t1[a][k] = g.a1[a][o];
+        g.tperm[k] = g.perm[o];
+    }
+}
+
+// -------------------------------------------------------------------- scan
+constexpr int SC_T = 256, SC_I = 8, SC_CHUNK = SC_T * SC_I;
+
+__device__ __forceinline__ int scan_in(const int *in, int i, int n, int mode)
+{
+    if (i >= n) return 0;
+    int v = in[i];
+    return mode == 0 ? v : (v >= 0 ? 1 : 0);
+}
+
+__global__ void __launch_bounds__(SC_T) scan_reduce_kernel(const int *in, int n, int mode, int *part)
+{
+    __shared__ uint32_t ws[8];
+    int base = blockIdx.x * SC_CHUNK + threadIdx.x * SC_I;
+    int s = 0;
+#pragma unroll
+    for (int k = 0; k < SC_I; ++k) s += scan_in(in, base + k, n, mode);
+    uint32_t ex;
+    uint32_t tot = block_scan_256((uint32_t)s, ex, ws);
+    if (threadIdx.x == 0) part[blockIdx.x] = (int)tot;
+}
+
+__global__ void __launch_bounds__(SC_T) scan_part_kernel(int *part, int nb, int *total)
+{
+    __shared__ uint32_t ws[8];
+    uint32_t carry = 0;
+    for (int b = 0; b < nb; b += SC_T) {
+        int i = b + threadIdx.x;
+        uint32_t v = i < nb ? (uint32_t)part[i] : 0, ex;
+        uint32_t tot = block_scan_256(v, ex, ws);
+        if (i < nb) part[i] = (int)(carry + ex);
+        carry += tot;
+    }
+    if (threadIdx.x == 0 && total) *total = (int)carry;
+}
+
+__global__ void __launch_bounds__(SC_T) scan_down_kernel(const int *in, int *out, int n, int mode,
+                                                         const int *part)
+{
+    __shared__ uint32_t ws[8];
+    int base = blockIdx.x * SC_CHUNK + threadIdx.x * SC_I;
+    int v[SC_I], s = 0;
+#pragma unroll
+    for (int k = 0; k < SC_I; ++k) { v[k] = scan_in(in, base + k, n, mode); s += v[k]; }
+    uint32_t ex;
+    block_scan_256((uint32_t)s, ex, ws);
+    int run = part[blockIdx.x] + (int)ex;
+#pragma unroll
+    for (int k = 0; k < SC_I; ++k)
+        if (base + k < n) { out[base + k] = run; run += v[k]; }
+}
+
+// mode 0: out[i] = sum_{k<i} in[k]; mode 1: counts in[k] >= 0
+static cudaError_t scan_mode(Ctx &c, const int *in, int *out, int n, int mode, int *total_dev,
+                             cudaStream_t st)
+{
+    int nb = div_up(n, SC_CHUNK);
+    if (nb < 1) nb = 1;
+    if (nb > c.scan_part_cap) return cudaErrorInvalidValue;
+    scan_reduce_kernel<<<nb, SC_T, 0, st>>>(in, n, mode, c.scan_part);
+    scan_part_kernel<<<1, SC_T, 0, st>>>(c.scan_part, nb, total_dev);
+    scan_down_kernel<<<nb, SC_T, 0, st>>>(in, out, n, mode, c.scan_part);
+    return cudaGetLastError();
+}
+
+cudaError_t scan_exclusive_int(Ctx &c, const int *in, int *out, int n, int *total_dev,
+                               cudaStream_t st)
+{
+    return scan_mode(c, in, out, n, 0, total_dev, st);
+}
+
+// -------------------------------------------------------------------- chop
+// lv[s] = d | (Lmax << 8) if nodes start at s, else -1 (for threshold T)
+__device__ __forceinline__ int chop_levels(const uint64_t *__restrict__ keys, int n, int s, int T)
+{
+    int d;
+    uint64_t ks = keys[s];
+    if (s == 0) {
+        d = 0;
+    } else {
+        int c = common_digits(ks, keys[s - 1]);
+        if (c == kMaxLevel) return -1;  // same key as the previous particle
+        d = c + 1;
+        int l = d - 1;
+        int lo = max(0, s - T), hi = s;
+        while (lo < hi) {
+            int mid = (lo + hi) >> 1;
+            if (common_digits(keys[mid], ks) >= l) hi = mid; else lo = mid + 1;
+        }
+        if (!(lo + T <= n - 1 && common_digits(keys[lo + T], ks) >= l)) return -1;
+    }
+    int c2 = (s + T <= n - 1) ? common_digits(ks, keys[s + T]) : -1;
+    int lmax = max(d, min(c2 + 1, kMaxLevel));
+    return d | (lmax << 8);
+}
+
+__global__ void chop_flags_kernel(const uint64_t *__restrict__ keys, int n, int t_leaf,
+                                  int t_group, int *lv_tree, int *lv_grp)
+{
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        lv_tree[s] = chop_levels(keys, n, s, t_leaf);
+        lv_grp[s] = chop_levels(keys, n, s, t_group);
+    }
+}
+
+// per block of kChopBlock particles: number of nodes per level
+__global__ void __launch_bounds__(256) chop_count_kernel(const int *__restrict__ lv, int n,
+                                                         int *blk_cnt, int nb)
+{
+    __shared__ int cnt[kLevels];
+    if (threadIdx.x < kLevels) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (int r = 0; r < kChopBlock / 256; ++r) {
+        int s = blockIdx.x * kChopBlock + r * 256 + threadIdx.x;
+        if (s < n) {
+            int v = lv[s];
+            if (v >= 0)
+                for (int L = v & 0xff; L <= (v >> 8); ++L) atomicAdd(&cnt[L], 1);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < kLevels) blk_cnt[threadIdx.x * nb + blockIdx.x] = cnt[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(256) chop_write_kernel(const int *__restrict__ lv, int n,
+                                                         const int *__restrict__ blk_off, int nb,
+                                                         Tree t, int *err)
+{
+    __shared__ int wcnt[kLevels][8];
+    __shared__ int run[kLevels];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x < kLevels) run[threadIdx.x] = blk_off[threadIdx.x * nb + blockIdx.x];
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    for (int r = 0; r < kChopBlock / 256; ++r) {
+        int s = blockIdx.x * kChopBlock + r * 256 + threadIdx.x;
+        int v = s < n ? lv[s] : -1;
+        int d = v >= 0 ? (v & 0xff) : 99, lm = v >= 0 ? (v >> 8) : -1;
+        unsigned ranks[kLevels];
+#pragma unroll
+        for (int L = 0; L < kLevels; ++L) {
+            unsigned b = __ballot_sync(0xffffffffu, d <= L && L <= lm);
+            ranks[L] = __popc(b & lt);
+            if (lane == 0) wcnt[L][w] = __popc(b);
+        }
+        __syncthreads();
+        if (threadIdx.x < kLevels) {
+            int acc = run[threadIdx.x];
+            for (int ww = 0; ww < 8; ++ww) {
+                int cc = wcnt[threadIdx.x][ww];
+                wcnt[threadIdx.x][ww] = acc;
+                acc += cc;
+            }
+            run[threadIdx.x] = acc;
+        }
+        __syncthreads();
+        for (int L = d; L <= lm; ++L) {
+            int idx = wcnt[L][w] + (int)ranks[L];
+            if (idx < t.cap_nodes) {
+                t.node_first[idx] = s;
+                t.node_level[idx] = L;
+                t.node_arrive[idx] = 0;
+            } else {
+                raise_error(err, SPH_ERR_NOMEM);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void level_start_kernel(const int *blk_off, int nb, const int *total, Tree t,
+                                   int *sizes)
+{
+    int L = threadIdx.x;
+    if (L < kLevels) t.level_start[L] = blk_off[L * nb];
+    if (L == kLevels) {
+        t.level_start[kLevels] = *total;
+        sizes[SZ_NODES] = min(*total, t.cap_nodes);
+    }
+}
+
+// end of the run at level L that starts at s (galloping search)
+__device__ int run_end(const uint64_t *__restrict__ keys, int n, int s, int L)
+{
+    if (L == 0) return n;
+    uint64_t ks = keys[s];
+    int step = 1, lo = s;  // keys[lo] in run
+    while (s + step < n && common_digits(keys[s + step], ks) >= L) {
+        lo = s + step;
+        step <<= 1;
+    }
+    int hi = min(s + step, n);  // keys[hi] not in run (or hi == n)
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (common_digits(keys[mid], ks) >= L) lo = mid; else hi = mid;
+    }
+    return hi;
+}
+
+__global__ void node_finish_kernel(const uint64_t *__restrict__ keys, int n, int T, Tree t,
+                                   const int *sizes)
+{
+    int nn = sizes[SZ_NODES];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nn; k += gridDim.x * blockDim.x) {
+        int L = t.node_level[k], s = t.node_first[k];
+        int cnt = run_end(keys, n, s, L) - s;
+        t.node_count[k] = cnt;
+        if (k == 0) t.node_parent[0] = -1;
+        int cf = -1, nc = 0;
+        if (cnt > T && L < kMaxLevel) {
+            int lo = t.level_start[L + 1], hi = min(t.level_start[L + 2], nn);
+            while (lo < hi) {
+                int mid = (lo + hi) >> 1;
+                if (t.node_first[mid] < s) lo = mid + 1; else hi = mid;
+            }
+            cf = lo;
+            int e = min(t.level_start[L + 2], nn);
+            while (cf + nc < e && t.node_first[cf + nc] < s + cnt) {
+                t.node_parent[cf + nc] = k;
+                ++nc;
+            }
+        }
+        t.node_child[k] = cf;
+        t.node_nchild[k] = nc;
+        t.node_ref[k] = nc > 0 ? make_int2(cf, -nc) : make_int2(s, cnt);
+    }
+}
+
+// Bottom-up bounds: leaves from particles, parents from children; the last
+// child to finish (arrival counter) computes its parent.  what = 0: AABB of
+// positions; what = 1: h_max.
+__global__ void node_bounds_kernel(const float4 *__restrict__ pos, const float *__restrict__ h,
+                                   Tree t, const int *sizes, int what)
+{
+    int nn = sizes[SZ_NODES];
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nn; k += gridDim.x * blockDim.x) {
+        if (t.node_nchild[k] != 0) continue;
+        int s = t.node_first[k], e = s + t.node_count[k];
+        if (what == 0) {
+            float3 lo = make_float3(INFINITY, INFINITY, INFINITY);
+            float3 hi = make_float3(-INFINITY, -INFINITY, -INFINITY);
+            for (int i = s; i < e; ++i) {
+                float4 p = pos[i];
+                lo.x = fminf(lo.x, p.x); lo.y = fminf(lo.y, p.y); lo.z = fminf(lo.z, p.z);
+                hi.x = fmaxf(hi.x, p.x); hi.y = fmaxf(hi.y, p.y); hi.z = fmaxf(hi.z, p.z);
+            }
+            t.node_lo[k] = make_float4(lo.x, lo.y, lo.z, 0.f);
+            t.node_hi[k] = make_float4(hi.x, hi.y, hi.z, 0.f);
+        } else {
+            float hm = 0.f;
+            for (int i = s; i < e; ++i) hm = fmaxf(hm, h[i]);
+            t.node_lo[k].w = hm;
+        }
+        int cur = k;
+        while (true) {
+            int p = t.node_parent[cur];
+            if (p < 0) break;
+            __threadfence();
+            int old = atomicAdd(&t.node_arrive[p], 1);
+            if (old != t.node_nchild[p] - 1) break;
+            __threadfence();
+            int cf = t.node_child[p], nc = t.node_nchild[p];
+            if (what == 0) {
+                float3 lo = make_float3(INFINITY, INFINITY, INFINITY);
+                float3 hi = make_float3(-INFINITY, -INFINITY, -INFINITY);
+                for (int q = cf; q < cf + nc; ++q) {
+                    float4 a = __ldcg(&t.node_lo[q]), b = __ldcg(&t.node_hi[q]);
+                    lo.x = fminf(lo.x, a.x); lo.y = fminf(lo.y, a.y); lo.z = fminf(lo.z, a.z);
+                    hi.x = fmaxf(hi.x, b.x); hi.y = fmaxf(hi.y, b.y); hi.z = fmaxf(hi.z, b.z);
+                }
+                __stcg(&t.node_lo[p], make_float4(lo.x, lo.y, lo.z, 0.f));
+                __stcg(&t.node_hi[p], make_float4(hi.x, hi.y, hi.z, 0.f));
+            } else {
+                float hm = 0.f;
+                for (int q = cf; q < cf + nc; ++q) hm = fmaxf(hm, __ldcg(&t.node_lo[q].w));
+                __stcg(&t.node_lo[p].w, hm);
+            }
+            cur = p;
+        }
+    }
+}
+
+// groups: first particle of each terminal node of the group chop
+__global__ void group_write_kernel(const int *__restrict__ lv_grp, const int *__restrict__ gidx,
+                                   int n, Tree t)
+{
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
+        if (lv_grp[s] >= 0) t.grp_ref[gidx[s]] = make_int2(s, 0);
+}
+
+// what = 0: count + AABB (h_max too); what = 1: h_max only
+__global__ void group_bounds_kernel(const float4 *__restrict__ pos, const float *__restrict__ h,
+                                    int n, Tree t, const int *sizes, int what)
+{
+    int ng = sizes[SZ_GROUPS];
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
+        int s = t.grp_ref[g].x;
+        int e = g + 1 < ng ? t.grp_ref[g + 1].x : n;
+        float hm = 0.f;
+        if (what == 0) {
+            float3 lo = make_float3(INFINITY, INFINITY, INFINITY);
+            float3 hi = make_float3(-INFINITY, -INFINITY, -INFINITY);
+            for (int i = s; i < e; ++i) {
+                float4 p = pos[i];
+                lo.x = fminf(lo.x, p.x); lo.y = fminf(lo.y, p.y); lo.z = fminf(lo.z, p.z);
+                hi.x = fmaxf(hi.x, p.x); hi.y = fmaxf(hi.y, p.y); hi.z = fmaxf(hi.z, p.z);
+                hm = fmaxf(hm, h[i]);
+            }
+            t.grp_ref[g].y = e - s;
+            t.grp_lo[g] = make_float4(lo.x, lo.y, lo.z, hm);
+            t.grp_hi[g] = make_float4(hi.x, hi.y, hi.z, 0.f);
+        } else {
+            for (int i = s; i < e; ++i) hm = fmaxf(hm, h[i]);
+            t.grp_lo[g].w = hm;
+        }
+    }
+}
+
+__global__ void copy_int_kernel(const int *src, int *dst) { *dst = *src; }
+
+// ------------------------------------------------------------- host driver
+static int grid_for(const Ctx &c, int64_t n, int block)
+{
+    int64_t g = (n + block - 1) / block;
+    int64_t cap = (int64_t)c.num_sms * 16;
+    if (g > cap) g = cap;
+    return g < 1 ? 1 : (int)g;
+}
+
+#define SPH_TRY(x)                                  \
+    do {                                            \
+        cudaError_t e_ = (x);                       \
+        if (e_ != cudaSuccess) return e_;           \
+    } while (0)
+
+cudaError_t build_tree(Ctx &c, const sph_state &s, const sph_params &p, bool full_permute,
+                       cudaStream_t st)
+{
+    const int n = (int)s.n;
+    Tree &t = c.tree;
+    float4 *pos = (float4 *)s.pos;
+    int *bb = (int *)c.bbox;
+    // 1. bounding box and input checks
+    bbox_init_kernel<<<1, 32, 0, st>>>(bb);
+    bbox_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(pos, s.h, n, bb, c.d_err);
+    // 2. keys
+    morton_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(pos, n, bb, s.keys, c.idx_a);
+    // 3. radix sort (key, slot)
+    int ntiles = div_up(n, RS_TILE);
+    uint64_t *kin = s.keys, *kout = c.keys_alt;
+    uint32_t *vin = c.idx_a, *vout = c.idx_b;
+    for (int pass = 0; pass < 8; ++pass) {
+        int shift = 8 * pass;
+        rs_hist_kernel<<<ntiles, RS_T, 0, st>>>(kin, n, shift, c.hist, ntiles);
+        rs_scan_rows_kernel<<<256, 256, 0, st>>>(c.hist, ntiles, c.dtotal);
+        rs_digit_base_kernel<<<1, 256, 0, st>>>(c.dtotal);
+        rs_scatter_kernel<<<ntiles, RS_T, 0, st>>>(kin, vin, kout, vout, n, shift, c.hist, c.dtotal,
+                                                   ntiles);
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+    }
+    // after 8 passes the sorted (key, slot) pairs are back in (s.keys, idx_a)
+    // 4. permute the state into curve order
+    GatherArgs g{};
+    g.order = c.idx_a;
+    int n4 = 0, n1 = 0;
+    float4 *arr4[4] = {(float4 *)s.pos, (float4 *)s.vel, nullptr, nullptr};
+    n4 = 2;
+    if (full_permute) {
+        arr4[n4++] = (float4 *)s.acc;
+    } else {
+        arr4[n4++] = c.vhalf;
+    }
+    float *arr1[5] = {s.h, s.rho, s.omega, s.drhodt, s.vsigmax};
+    n1 = full_permute ? 5 : 1;
+    for (int a = 0; a < n4; ++a) { g.a4[a] = arr4[a]; g.t4[a] = c.tmp4[a]; }
+    for (int a = 0; a < n1; ++a) { g.a1[a] = arr1[a]; g.t1[a] = c.tmp1[a]; }
+    g.perm = s.perm;
+    g.tperm = c.tmp_perm;
+    g.n4 = n4;
+    g.n1 = n1;
+    gather_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(g, n);
+    for (int a = 0; a < n4; ++a)
+        SPH_TRY(cudaMemcpyAsync(arr4[a], c.tmp4[a], (size_t)n * 16, cudaMemcpyDeviceToDevice, st));
+    for (int a = 0; a < n1; ++a)
+        SPH_TRY(cudaMemcpyAsync(arr1[a], c.tmp1[a], (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
+    SPH_TRY(cudaMemcpyAsync(s.perm, c.tmp_perm, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
+    // 5. chop: tree (n_leaf) and groups (n_group)
+    chop_flags_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(s.keys, n, p.n_leaf, p.n_group,
+                                                            t.lv_tree, t.lv_grp);
+    // groups
+    int *gidx = (int *)c.tmp1[1];  // scratch: tmp1[1..] are free once copied back
+    SPH_TRY(scan_mode(c, t.lv_grp, gidx, n, 1, c.d_sizes + SZ_GROUPS, st));
+    group_write_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(t.lv_grp, gidx, n, t);
+    group_bounds_kernel<<<grid_for(c, n, 128), 128, 0, st>>>(pos, s.h, n, t, c.d_sizes, 0);
+    // nodes
+    int nb = div_up(n, kChopBlock);
+    int *blk_off = (int *)c.tmp1[2];
+    int *ntotal = c.d_sizes + 2;
+    chop_count_kernel<<<nb, 256, 0, st>>>(t.lv_tree, n, t.blk_cnt, nb);
+    SPH_TRY(scan_mode(c, t.blk_cnt, blk_off, kLevels * nb, 0, ntotal, st));
+    chop_write_kernel<<<nb, 256, 0, st>>>(t.lv_tree, n, blk_off, nb, t, c.d_err);
+    level_start_kernel<<<1, 32, 0, st>>>(blk_off, nb, ntotal, t, c.d_sizes);
+    node_finish_kernel<<<grid_for(c, t.cap_nodes, 256), 256, 0, st>>>(s.keys, n, p.n_leaf, t,
+                                                                       c.d_sizes);
+    node_bounds_kernel<<<grid_for(c, t.cap_nodes, 128), 128, 0, st>>>(pos, s.h, t, c.d_sizes, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t update_hmax(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st)
+{
+    (void)p;
+    Tree &t = c.tree;
+    SPH_TRY(cudaMemsetAsync(t.node_arrive, 0, sizeof(int) * (size_t)t.cap_nodes, st));
+    node_bounds_kernel<<<grid_for(c, t.cap_nodes, 128), 128, 0, st>>>((const float4 *)s.pos, s.h, t,
+                                                                       c.d_sizes, 1);
+    group_bounds_kernel<<<grid_for(c, s.n, 128), 128, 0, st>>>((const float4 *)s.pos, s.h,
+                                                               (int)s.n, t, c.d_sizes, 1);
+    return cudaGetLastError();
+}
+
+}  // namespace sph

@@ -1,0 +1,335 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Bars: keys, sort order, tree, groups and neighbour sets bit-exact; rho within
+1e-5 relative; accelerations and du/dt within 1e-4 of max|.|.  All inputs
+come from the seeded generators; every expected value from the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1909_07439_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+RHO_TOL = 1e-5
+ACC_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def sph():
+    import torch
+    from paper_1909_07439_gb300 import build, native
+    build.build()
+    native.load()
+    ctx = native.sph_create(1 << 18, 0)
+    yield native, ctx, torch
+    native.sph_destroy(ctx)
+
+
+def upload(native, w):
+    from paper_1909_07439_gb300 import DeviceState
+    return DeviceState.from_arrays(w.pos, w.vel, w.h)
+
+
+def f64(w):
+    return (w.pos[:, :3].astype(np.float64), w.vel[:, :3].astype(np.float64),
+            w.pos[:, 3].astype(np.float64), w.vel[:, 3].astype(np.float64))
+
+
+def small_cases():
+    a = inputs.unit_sphere(8192, seed=1)                      # C1: N = 8192 unit sphere
+    b = inputs.unit_sphere(3001, seed=7, sigma_v=0.3)         # ragged, several tiles
+    rng = np.random.default_rng(7)
+    b.pos[:, 3] *= rng.uniform(0.5, 1.5, b.n).astype(np.float32)   # unequal masses
+    b.vel[:, 3] *= rng.uniform(0.5, 2.0, b.n).astype(np.float32)   # pressure gradients
+    return {"c1_8192": a, "ragged_3001": b}
+
+
+CASES = small_cases()
+
+
+def evaluate_gpu(native, ctx, w, **pk):
+    s = upload(native, w)
+    p = native.sph_params_default(**pk)
+    native.sph_build_tree(ctx, s.c, p)
+    native.sph_density(ctx, s.c, p)
+    native.sph_force(ctx, s.c, p)
+    native.sph_sync(ctx)
+    return s, p
+
+
+_oracle_cache = {}
+
+
+def oracle_eval(name, w):
+    if name not in _oracle_cache:
+        x, v, m, u = f64(w)
+        d = oracle.density(x, v, m, w.h)
+        assert d.failures == 0
+        f = oracle.force(x, v, m, u, d.h, d.rho, d.omega)
+        _oracle_cache[name] = (d, f)
+    return _oracle_cache[name]
+
+
+# ------------------------------------------------------------ keys / sort / tree
+@pytest.mark.parametrize("n", [1, 2, 37, 1000, 8192])
+def test_keys_sort_perm_bit_exact(sph, n):
+    native, ctx, torch = sph
+    w = inputs.unit_sphere(n, seed=n)
+    s = upload(native, w)
+    p = native.sph_params_default()
+    native.sph_build_tree(ctx, s.c, p)
+    native.sph_sync(ctx)
+    keys_o = oracle.morton_keys(w.pos)
+    order = oracle.sort_order(keys_o)
+    assert np.array_equal(s.numpy("perm").astype(np.int64), order)
+    assert np.array_equal(s.numpy("keys").view(np.uint64), keys_o[order])
+    assert np.array_equal(s.numpy("pos"), w.pos[order])     # permuted, bit for bit
+    assert np.array_equal(s.numpy("h"), w.h[order])
+
+
+def _clustered(n=20000):
+    w = inputs.plummer(n, seed=11)
+    # a block of exact duplicates exercises identical keys (depth-21 leaves)
+    w.pos[100:160] = w.pos[100]
+    return w
+
+
+@pytest.mark.parametrize("case", ["c1", "plummer_dups", "tiny"])
+def test_tree_and_groups_exact(sph, case):
+    native, ctx, torch = sph
+    w = {"c1": CASES["c1_8192"], "plummer_dups": _clustered(), "tiny": inputs.unit_sphere(5)}[case]
+    s = upload(native, w)
+    p = native.sph_params_default()
+    native.sph_build_tree(ctx, s.c, p)
+    native.sph_sync(ctx)
+    nodes, groups = native.sph_get_tree(ctx)
+    sk = oracle.morton_keys(w.pos)
+    sk = sk[oracle.sort_order(sk)]
+    ch = oracle.chop(sk, p.n_leaf)
+    assert np.array_equal(nodes["level"], ch.level)
+    assert np.array_equal(nodes["first"], ch.first)
+    assert np.array_equal(nodes["count"], ch.count)
+    assert np.array_equal(nodes["nchild"], ch.nchild)
+    assert np.array_equal(np.where(ch.nchild > 0, nodes["child"], -1),
+                          np.where(ch.nchild > 0, ch.child_first, -1))
+    cg = oracle.chop(sk, p.n_group)
+    term = cg.nchild == 0
+    assert np.array_equal(groups["first"], np.sort(cg.first[term]))
+    assert np.array_equal(groups["count"], cg.count[term][np.argsort(cg.first[term])])
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("case", ["c1_8192", "ragged_3001"])
+def test_neighbour_sets_bit_exact(sph, mode, case):
+    native, ctx, torch = sph
+    w = CASES[case]
+    rng = np.random.default_rng(mode + 17)
+    h = (w.h * rng.uniform(0.7, 1.4, w.n)).astype(np.float32)   # same h array on both sides
+    s = upload(native, inputs.Workload("x", w.pos, w.vel, h))
+    p = native.sph_params_default()
+    native.sph_build_tree(ctx, s.c, p)
+    off = torch.zeros(w.n + 1, dtype=torch.int64, device="cuda")
+    total = native.sph_neighbours(ctx, s.c, p, mode, off)
+    idx = torch.zeros(total, dtype=torch.int32, device="cuda")
+    native.sph_neighbours(ctx, s.c, p, mode, off, idx, total)
+    off, idx = off.cpu().numpy(), idx.cpu().numpy()
+    perm = s.numpy("perm").astype(np.int64)
+    oo, oi = oracle.neighbours(w.pos, h, mode)
+    assert total == oo[-1]
+    for slot in range(w.n):
+        i = perm[slot]
+        got = np.sort(perm[idx[off[slot]:off[slot + 1]]])
+        assert np.array_equal(got, oi[oo[i]:oo[i + 1]]), (slot, i)
+
+
+# ------------------------------------------------------------------ density
+@pytest.mark.parametrize("case", ["c1_8192", "ragged_3001"])
+def test_density_parity(sph, case):
+    native, ctx, torch = sph
+    w = CASES[case]
+    s, p = evaluate_gpu(native, ctx, w)
+    d, _ = oracle_eval(case, w)
+    rho = s.in_original_order("rho")
+    h = s.in_original_order("h")
+    om = s.in_original_order("omega")
+    dr = s.in_original_order("drhodt")
+    assert np.max(np.abs(rho / d.rho - 1)) <= RHO_TOL
+    assert np.max(np.abs(h / d.h - 1)) <= RHO_TOL / 3
+    assert np.max(np.abs(om - d.omega)) <= 1e-5 * np.max(np.abs(d.omega))
+    assert np.max(np.abs(dr - d.drhodt)) <= ACC_TOL * np.max(np.abs(d.drhodt))
+
+
+def test_density_fixed_iterations(sph):
+    native, ctx, torch = sph
+    w = CASES["ragged_3001"]
+    s, p = evaluate_gpu(native, ctx, w, density_iters=3)
+    x, v, m, u = f64(w)
+    d3 = oracle.density(x, v, m, w.h, fixed_iters=3)
+    h = s.in_original_order("h")
+    # three Newton updates from the same h0; both sides take the same branch
+    rel = np.abs(h / d3.h - 1)
+    assert np.quantile(rel, 0.999) <= 1e-5
+
+
+# -------------------------------------------------------------------- force
+@pytest.mark.parametrize("case", ["c1_8192", "ragged_3001"])
+def test_force_parity(sph, case):
+    native, ctx, torch = sph
+    w = CASES[case]
+    s, p = evaluate_gpu(native, ctx, w)
+    d, f = oracle_eval(case, w)
+    acc = s.in_original_order("acc")
+    amax = np.max(np.abs(f.acc))
+    assert np.max(np.abs(acc[:, :3] - f.acc)) <= ACC_TOL * amax
+    assert np.max(np.abs(acc[:, 3] - f.dudt)) <= ACC_TOL * np.max(np.abs(f.dudt))
+    # vsigmax is a max over a set: bracket it by the sets at radius (1 -/+ 1e-4)
+    x, v, m, u = f64(w)
+    lo = oracle.force(x, v, m, u, d.h, d.rho, d.omega, vsig_scale=1 - 1e-4).vsigmax
+    hi = oracle.force(x, v, m, u, d.h, d.rho, d.omega, vsig_scale=1 + 1e-4).vsigmax
+    vs = s.in_original_order("vsigmax")
+    assert np.all(vs >= lo * (1 - 1e-5)) and np.all(vs <= hi * (1 + 1e-5))
+
+
+def test_force_invariants(sph):
+    native, ctx, torch = sph
+    w = CASES["ragged_3001"]
+    s, p = evaluate_gpu(native, ctx, w)
+    acc = s.in_original_order("acc").astype(np.float64)
+    x, v, m, u = f64(w)
+    ma = m[:, None] * acc[:, :3]
+    assert np.max(np.abs(ma.sum(0))) <= 2e-6 * np.sum(np.abs(ma))
+    de = m * (np.sum(v * acc[:, :3], 1) + acc[:, 3])
+    assert abs(de.sum()) <= 2e-6 * np.sum(np.abs(m * np.sum(v * acc[:, :3], 1)) + np.abs(m * acc[:, 3]))
+
+
+# ---------------------------------------------------------- step / reductions
+def test_timestep_and_step_parity(sph):
+    native, ctx, torch = sph
+    w = CASES["ragged_3001"]
+    s, p = evaluate_gpu(native, ctx, w)
+    d, f = oracle_eval("ragged_3001", w)
+    x, v, m, u = f64(w)
+    st = oracle.SphState(x=x, v=v, u=u, m=m, h=d.h, rho=d.rho, omega=d.omega, drhodt=d.drhodt,
+                         acc=f.acc, dudt=f.dudt, vsigmax=f.vsigmax)
+    dt_o = oracle.courant_dt(st)
+    d_dt = torch.zeros(1, dtype=torch.float32, device="cuda")
+    native.sph_timestep(ctx, s.c, p, d_dt)
+    assert abs(d_dt.item() / dt_o - 1) <= 1e-4
+    d_dt.fill_(dt_o)
+    d_t = torch.zeros(1, dtype=torch.float64, device="cuda")
+    native.sph_step(ctx, s.c, p, d_dt, d_t)
+    native.sph_sync(ctx)
+    assert abs(d_t.item() - np.float32(dt_o)) <= 1e-12
+    n1 = oracle.kdk_step(st, float(np.float32(dt_o)))
+    pos = s.in_original_order("pos")
+    vel = s.in_original_order("vel")
+    rho = s.in_original_order("rho")
+    acc = s.in_original_order("acc")
+    assert np.max(np.abs(pos[:, :3] - n1.x)) <= 1e-6
+    vscale = np.max(np.abs(n1.v))
+    assert np.max(np.abs(vel[:, :3] - n1.v)) <= 1e-5 * vscale
+    assert np.max(np.abs(vel[:, 3] / n1.u - 1)) <= 1e-5
+    assert np.max(np.abs(rho / n1.rho - 1)) <= RHO_TOL
+    assert np.max(np.abs(acc[:, :3] - n1.acc)) <= ACC_TOL * np.max(np.abs(n1.acc))
+    assert np.max(np.abs(acc[:, 3] - n1.dudt)) <= ACC_TOL * np.max(np.abs(n1.dudt))
+    # the step wrote the next Courant dt
+    n1.vsigmax = n1.vsigmax
+    assert abs(d_dt.item() / oracle.courant_dt(n1) - 1) <= 1e-3
+
+
+def test_conserved_fp64(sph):
+    native, ctx, torch = sph
+    w = CASES["c1_8192"]
+    s = upload(native, w)
+    out = torch.zeros(8, dtype=torch.float64, device="cuda")
+    native.sph_conserved(ctx, s.c, out)
+    ref = oracle.conserved(*f64(w))
+    got = out.cpu().numpy()
+    scale = np.array([ref[0], ref[1]] + [np.sum(np.abs(w.vel[:, :3]) * w.pos[:, 3:4])] * 3 +
+                     [np.sum(np.abs(ref[5:]))] * 3)
+    assert np.all(np.abs(got - ref) <= 1e-12 * np.maximum(scale, 1e-30))
+
+
+def test_step_host_matches_device_step(sph):
+    import ctypes
+    native, ctx, torch = sph
+    w = CASES["ragged_3001"]
+    s, p = evaluate_gpu(native, ctx, w)
+    d_dt = torch.zeros(1, dtype=torch.float32, device="cuda")
+    native.sph_timestep(ctx, s.c, p, d_dt)
+    dt0 = d_dt.item()
+    host = {k: getattr(s, k).cpu().pin_memory() for k in s.FIELDS4 + s.FIELDS1 + ("perm", "keys")}
+    hs = native.sph_state()
+    hs.n = s.n
+    for k, t in host.items():
+        setattr(hs, k, t.data_ptr())
+    native.sph_step(ctx, s.c, p, d_dt)
+    native.sph_sync(ctx)
+    hdt = ctypes.c_float(dt0)
+    native.sph_step_host(ctx, hs, p, 1, hdt)
+    for k in ("pos", "vel", "acc", "h", "rho"):
+        assert torch.equal(host[k][: s.n], getattr(s, k)[: s.n].cpu()), k
+    assert hdt.value == d_dt.item()
+
+
+# ------------------------------------------------------------------ edge cases
+def test_empty_is_noop(sph):
+    native, ctx, torch = sph
+    from paper_1909_07439_gb300 import DeviceState
+    s = DeviceState(0)
+    p = native.sph_params_default()
+    for fn in (native.sph_build_tree, native.sph_density, native.sph_force):
+        fn(ctx, s.c, p)
+    native.sph_sync(ctx)
+
+
+def test_too_few_particles_has_no_root(sph):
+    # with fewer than ~6 particles sum_j m W(r, h) never reaches m (hfact/h)^3:
+    # the fixed point does not exist and the solve must say so
+    native, ctx, torch = sph
+    w = inputs.unit_sphere(3, seed=2)
+    s = upload(native, w)
+    p = native.sph_params_default(max_h_iter=20)
+    native.sph_build_tree(ctx, s.c, p)
+    native.sph_density(ctx, s.c, p)
+    with pytest.raises(native.SphError) as e:
+        native.sph_sync(ctx)
+    assert e.value.status == 4
+
+
+def test_nonfinite_input_is_rejected(sph):
+    native, ctx, torch = sph
+    w = inputs.unit_sphere(500, seed=3)
+    w.pos[17, 1] = np.nan
+    s = upload(native, w)
+    p = native.sph_params_default()
+    native.sph_build_tree(ctx, s.c, p)
+    with pytest.raises(native.SphError) as e:
+        native.sph_sync(ctx)
+    assert e.value.status == 6
+
+
+def test_invalid_arguments(sph):
+    native, ctx, torch = sph
+    s = upload(native, inputs.unit_sphere(64))
+    with pytest.raises(native.SphError):
+        native.sph_build_tree(ctx, s.c, native.sph_params_default(n_group=0))
+    big = s.c
+    big.n = 1 << 20
+    with pytest.raises(native.SphError):
+        native.sph_build_tree(ctx, big, native.sph_params_default())
+
+
+def test_coincident_particles(sph):
+    native, ctx, torch = sph
+    w = inputs.unit_sphere(2000, seed=9)
+    w.pos[500:520, :3] = w.pos[500, :3]   # 20 particles at one point
+    s, p = evaluate_gpu(native, ctx, w)
+    x, v, m, u = f64(w)
+    d = oracle.density(x, v, m, w.h)
+    f = oracle.force(x, v, m, u, d.h, d.rho, d.omega)
+    assert np.max(np.abs(s.in_original_order("rho") / d.rho - 1)) <= RHO_TOL
+    acc = s.in_original_order("acc")
+    assert np.max(np.abs(acc[:, :3] - f.acc)) <= ACC_TOL * np.max(np.abs(f.acc))
