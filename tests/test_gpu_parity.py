@@ -325,11 +325,30 @@ def test_invalid_arguments(sph):
 def test_coincident_particles(sph):
     native, ctx, torch = sph
     w = inputs.unit_sphere(2000, seed=9)
-    w.pos[500:520, :3] = w.pos[500, :3]   # 20 particles at one point
+    w.pos[500:504, :3] = w.pos[500, :3]   # 4 particles at one point (r = 0 pairs)
     s, p = evaluate_gpu(native, ctx, w)
     x, v, m, u = f64(w)
     d = oracle.density(x, v, m, w.h)
+    assert d.failures == 0
     f = oracle.force(x, v, m, u, d.h, d.rho, d.omega)
     assert np.max(np.abs(s.in_original_order("rho") / d.rho - 1)) <= RHO_TOL
     acc = s.in_original_order("acc")
     assert np.max(np.abs(acc[:, :3] - f.acc)) <= ACC_TOL * np.max(np.abs(f.acc))
+
+
+def test_point_mass_cluster_has_no_root(sph):
+    # k coincident particles give sum_j m W(0, h) = k m C / h^3 > m hfact^3 / h^3
+    # once k C > hfact^3 (k >= 6 for the M4 kernel): g(h) > 0 for every h, so
+    # the h-rho fixed point does not exist; the oracle and the GPU both report it
+    native, ctx, torch = sph
+    w = inputs.unit_sphere(2000, seed=9)
+    w.pos[500:520, :3] = w.pos[500, :3]
+    x, v, m, u = f64(w)
+    assert oracle.density(x, v, m, w.h, targets=[500], max_iter=60).failures == 1
+    s = upload(native, w)
+    p = native.sph_params_default()
+    native.sph_build_tree(ctx, s.c, p)
+    native.sph_density(ctx, s.c, p)
+    with pytest.raises(native.SphError) as e:
+        native.sph_sync(ctx)
+    assert e.value.status == 4
