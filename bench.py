@@ -185,7 +185,7 @@ def run_ours(args):
                           f"(sm_max_mhz {pk_kind})",
             "launch_ms": round(dms / args.steps, 4)}
 
-    e2e = run_e2e(native, ctx, s, p, n, args, stream) if rank == 0 else None
+    e2e = run_e2e(native, ctx, s, p, n, args, stream) if rank == 0 and not args.skip_e2e else None
     out = None
     if rank == 0:
         cpu = run_cpu_baseline(w, args.cpu_seconds) if args.cpu_seconds > 0 else None
@@ -323,6 +323,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--side", type=int, default=SIDE)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--skip-e2e", action="store_true", help="profiling runs: no host-buffer leg")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -21,7 +21,7 @@ namespace sph {
 
 constexpr int kTB = 8;           // targets per batch
 constexpr int kDensWarps = 4;    // warps per block
-constexpr float kPad = 0.08f;    // padded list radius, relative to h
+constexpr float kPad = 0.05f;    // padded list radius, relative to h
 
 template <int CAP>
 struct DensSmem {
@@ -160,29 +160,39 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_kernel(DensArgs a)
                     __syncwarp();
                     bool overflow = false;
                     auto chunk = [&](int j) {
-                        // flush when a list could overflow during this chunk
-                        bool full = lane < nt && sm.tlen[lane] > CAP - 32;
-                        if (__any_sync(0xffffffffu, full)) {
+                        float4 pj = j >= 0 ? __ldg(&a.pos[j]) : make_float4(0, 0, 0, 0);
+                        float r2s[kTB];
+                        unsigned bs[kTB];
+                        bool over = false;
+#pragma unroll
+                        for (int tt = 0; tt < kTB; ++tt) {
+                            if (tt < nt) {
+                                float4 tq = sm.tp[tt];
+                                r2s[tt] = canon_r2(tq.x, tq.y, tq.z, pj.x, pj.y, pj.z);
+                                bs[tt] = __ballot_sync(0xffffffffu, j >= 0 && r2s[tt] < sm.tr2[tt]);
+                                over |= sm.tlen[tt] + __popc(bs[tt]) > CAP;
+                            }
+                        }
+                        // a list would overflow: sum what is there at the current h, start over
+                        if (over) {
                             overflow = true;
                             list_sums();
                             if (lane < nt) sm.tlen[lane] = 0;
                             __syncwarp();
                         }
-                        float4 pj = j >= 0 ? __ldg(&a.pos[j]) : make_float4(0, 0, 0, 0);
-                        for (int tt = 0; tt < nt; ++tt) {
-                            float4 tq = sm.tp[tt];
-                            float r2 = canon_r2(tq.x, tq.y, tq.z, pj.x, pj.y, pj.z);
-                            bool hit = j >= 0 && r2 < sm.tr2[tt];
-                            unsigned b = __ballot_sync(0xffffffffu, hit);
-                            int base = sm.tlen[tt];
-                            if (hit) {
-                                int p = base + __popc(b & lt);
-                                sm.erm[tt][p] = make_float2(r2, pj.w);
-                                sm.ej[tt][p] = j;
+#pragma unroll
+                        for (int tt = 0; tt < kTB; ++tt) {
+                            if (tt < nt) {
+                                int base = sm.tlen[tt];
+                                if ((bs[tt] >> lane) & 1u) {
+                                    int p = base + __popc(bs[tt] & lt);
+                                    sm.erm[tt][p] = make_float2(r2s[tt], pj.w);
+                                    sm.ej[tt][p] = j;
+                                }
+                                __syncwarp();
+                                if (lane == 0) sm.tlen[tt] = base + __popc(bs[tt]);
+                                __syncwarp();
                             }
-                            __syncwarp();
-                            if (lane == 0) sm.tlen[tt] = base + __popc(b);
-                            __syncwarp();
                         }
                         n_cand += (unsigned long long)nt * 32;
                     };

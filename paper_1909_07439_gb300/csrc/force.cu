@@ -133,22 +133,31 @@ __global__ void __launch_bounds__(kForceWarps * 32) force_kernel(ForceArgs a)
                 __syncwarp();
             };
             auto chunk = [&](int j) {
-                bool full = lane < nt && sm.tlen[lane] > CAP - 32;
-                if (__any_sync(0xffffffffu, full)) flush();
                 float4 pj = j >= 0 ? __ldg(&a.pos[j]) : make_float4(0, 0, 0, 0);
                 float hj = j >= 0 ? __ldg(&a.prop[j].x) : 0.f;
-                for (int tt = 0; tt < nt; ++tt) {
-                    float4 tp = sm.tp[tt];
-                    float ht = sm.tq[tt].x;
-                    float r2 = canon_r2(tp.x, tp.y, tp.z, pj.x, pj.y, pj.z);
-                    float R = 2.0f * fmaxf(ht, hj);
-                    bool hit = j >= 0 && j != i0 + tt && r2 < R * R;
-                    unsigned b = __ballot_sync(0xffffffffu, hit);
-                    int base = sm.tlen[tt];
-                    if (hit) sm.ej[tt][base + __popc(b & lt)] = j;
-                    __syncwarp();
-                    if (lane == 0) sm.tlen[tt] = base + __popc(b);
-                    __syncwarp();
+                unsigned bs[kFTB];
+                bool over = false;
+#pragma unroll
+                for (int tt = 0; tt < kFTB; ++tt) {
+                    if (tt < nt) {
+                        float4 tp = sm.tp[tt];
+                        float ht = sm.tq[tt].x;
+                        float r2 = canon_r2(tp.x, tp.y, tp.z, pj.x, pj.y, pj.z);
+                        float R = 2.0f * fmaxf(ht, hj);
+                        bs[tt] = __ballot_sync(0xffffffffu, j >= 0 && j != i0 + tt && r2 < R * R);
+                        over |= sm.tlen[tt] + __popc(bs[tt]) > CAP;
+                    }
+                }
+                if (over) flush();  // run the pairs listed so far, then start over
+#pragma unroll
+                for (int tt = 0; tt < kFTB; ++tt) {
+                    if (tt < nt) {
+                        int base = sm.tlen[tt];
+                        if ((bs[tt] >> lane) & 1u) sm.ej[tt][base + __popc(bs[tt] & lt)] = j;
+                        __syncwarp();
+                        if (lane == 0) sm.tlen[tt] = base + __popc(bs[tt]);
+                        __syncwarp();
+                    }
                 }
                 n_cand += (unsigned long long)nt;
             };
