@@ -137,6 +137,29 @@ sph_status sph_step_host(sph_ctx *ctx, sph_state *host_state, const sph_params *
  * d_out8 = { E_kin, E_th, px, py, pz, Lx, Ly, Lz } (device doubles). */
 sph_status sph_conserved(sph_ctx *ctx, const sph_state *s, double *d_out8, void *stream);
 
+/* Conserved quantities for callers that cannot allocate device memory.
+ * The paper has no counterpart; this is a library convenience.
+ * Same result as sph_conserved (FP64 {E_kin, E_th, px, py, pz, Lx, Ly, Lz},
+ * summation order differs, so values agree to FP64 rounding), but it needs
+ * no context: sph_create allocates, and some callers cannot call cudaMalloc
+ * (a host framework that owns all device memory and only lends its particle
+ * arrays, or code that must not risk the device-wide synchronisation an
+ * allocation can cause).  d_pos, d_vel: device [n][4] float arrays as in
+ * sph_state, 16-byte aligned; d_out8: device double[8]; stream as above.
+ * Its scratch is a fixed 256 KB array inside the library, held on every GPU
+ * that loads the library until the process exits; no call allocates.
+ * The first call on each device looks up that array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's partial sums: calls
+ * whose kernels overlap on the GPU (unordered streams) race; calls ordered on
+ * one stream are safe.  Returns SPH_ERR_INVALID_ARG if n < 0 or
+ * n > SPH_CONSERVED_NOALLOC_MAX_N, for NULL or misaligned pointers, or a
+ * current device index >= 64; SPH_ERR_CUDA if a launch or the address
+ * lookup fails.  Asynchronous otherwise. */
+#define SPH_CONSERVED_NOALLOC_MAX_N 16777216
+sph_status sph_conserved_noalloc(int64_t n, const float *d_pos, const float *d_vel,
+                                 double *d_out8, void *stream);
+
 /* Neighbour sets of the current tree/state (Sect. 3.2), for testing.
  * mode 0: density set {j : r2 < (2 h_i)^2} (includes i);
  * mode 1: force set {j != i : r2 < (2 max(h_i, h_j))^2};

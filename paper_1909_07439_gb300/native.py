@@ -56,6 +56,7 @@ class sph_stats(ctypes.Structure):
 _lib = None
 EXPORTS = ("sph_params_default", "sph_create", "sph_destroy", "sph_build_tree", "sph_density",
            "sph_force", "sph_timestep", "sph_step", "sph_step_host", "sph_conserved",
+           "sph_conserved_noalloc",
            "sph_neighbours", "sph_get_tree", "sph_get_stats", "sph_set_timing", "sph_get_timing", "sph_sync",
            "sph_last_error")
 
@@ -82,6 +83,7 @@ def load():
     lib.sph_step_host.argtypes = [P, POINTER(sph_state), POINTER(sph_params), c_int,
                                   POINTER(c_float), P]
     lib.sph_conserved.argtypes = [P, POINTER(sph_state), P, P]
+    lib.sph_conserved_noalloc.argtypes = [c_int64, P, P, P, P]
     lib.sph_neighbours.argtypes = [P, POINTER(sph_state), POINTER(sph_params), c_int, P, P,
                                    c_int64, POINTER(c_int64), P]
     lib.sph_get_tree.argtypes = [P, P, P, P, P, P, c_int64, P, P, c_int64, POINTER(c_int64),
@@ -178,6 +180,20 @@ def sph_step_host(ctx, host_state, params, n_steps, h_dt: c_float, stream=None):
 def sph_conserved(ctx, state, d_out8, stream=None):
     return _check(ctx, load().sph_conserved(ctx, ctypes.byref(state), _ptr(d_out8),
                                             _stream(stream)))
+
+
+CONSERVED_NOALLOC_MAX_N = 16777216
+
+
+def sph_conserved_noalloc(n, d_pos, d_vel, d_out8, stream=None):
+    """Context-free conserved sums for callers that cannot allocate device
+    memory (see include/sph.h); scratch is a fixed array inside the library."""
+    st = load().sph_conserved_noalloc(int(n), _ptr(d_pos), _ptr(d_vel), _ptr(d_out8),
+                                      _stream(stream))
+    if st != SPH_OK:
+        raise SphError(st, f"sph_conserved_noalloc rejected the call (n = {n}, "
+                           f"limit {CONSERVED_NOALLOC_MAX_N})")
+    return st
 
 
 def sph_neighbours(ctx, state, params, mode, d_off, d_idx=None, cap=0, stream=None):
