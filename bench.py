@@ -121,6 +121,12 @@ def run_ours(args):
     ctx = native.sph_create(n, local)
     s = DeviceState.from_arrays(w.pos, w.vel, w.h, device=f"cuda:{local}")
     p = native.sph_params_default()
+    if args.n_leaf:
+        p.n_leaf = args.n_leaf
+    if args.n_group:
+        p.n_group = args.n_group
+    if args.tile:
+        p.tile = args.tile
     stream = torch.cuda.current_stream()
     d_dt = torch.zeros(1, dtype=torch.float32, device="cuda")
     d_t = torch.zeros(1, dtype=torch.float64, device="cuda")
@@ -186,6 +192,9 @@ def run_ours(args):
             "launch_ms": round(dms / args.steps, 4)}
 
     e2e = run_e2e(native, ctx, s, p, n, args, stream) if rank == 0 and not args.skip_e2e else None
+    native.sph_destroy(ctx)
+    del s
+    batched = run_batched(args) if rank == 0 and args.batch_instances > 0 else None
     out = None
     if rank == 0:
         cpu = run_cpu_baseline(w, args.cpu_seconds) if args.cpu_seconds > 0 else None
@@ -210,11 +219,76 @@ def run_ours(args):
                               if k not in ("n_nodes", "n_groups")},
             "tree": {"n_nodes": stats["n_nodes"], "n_groups": stats["n_groups"]},
             "sim_time": float(d_t.item()),
+            "batched": batched,
         }
-    native.sph_destroy(ctx)
     if ws > 1:
         torch.distributed.destroy_process_group()
     return out
+
+
+def run_batched(args):
+    """512 independent Sedov blasts (log-uniform sizes in [4096, 262144]),
+    20 steps each with per-instance dt: one batched state, graph-replayed
+    steps with persistent walk kernels, autotuned N_group and tile; compared
+    with the same instances advanced one after another by sph_step."""
+    import torch
+    from paper_1909_07439_gb300 import DeviceState, autotune, inputs, native
+    w, off = inputs.sedov_batch(args.batch_instances, seed=4)
+    k = len(off) - 1
+    ctx = native.sph_create(w.n, 0)
+    s = DeviceState.from_arrays(w.pos, w.vel, w.h)
+    d_off = torch.as_tensor(off, device="cuda")
+    dt = torch.zeros(k, dtype=torch.float32, device="cuda")
+    t = torch.zeros(k, dtype=torch.float64, device="cuda")
+    p, report = autotune.tune_batch(ctx, s, d_off, k)
+    native.sph_batch_evaluate(ctx, s.c, d_off, k, p, dt)
+    native.sph_batch_step(ctx, s.c, d_off, k, 1, p, dt, t)      # records the graph
+    native.sph_sync(ctx)
+    native.sph_get_stats(ctx)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    native.sph_batch_step(ctx, s.c, d_off, k, args.batch_steps, p, dt, t)
+    e1.record()
+    torch.cuda.synchronize()
+    native.sph_sync(ctx)
+    t_batch = e0.elapsed_time(e1) / 1e3
+    stats = native.sph_get_stats(ctx)
+    native.sph_destroy(ctx)
+    del s
+    # the same instances one after another through the single-instance path
+    nmax = int(np.max(np.diff(off)))
+    ctx = native.sph_create(nmax, 0)
+    p1 = native.sph_params_default(n_group=p.n_group, tile=p.tile)
+    states = []
+    for i in range(k):
+        a, b = int(off[i]), int(off[i + 1])
+        si = DeviceState.from_arrays(w.pos[a:b], w.vel[a:b], w.h[a:b])
+        di = torch.zeros(1, dtype=torch.float32, device="cuda")
+        native.sph_build_tree(ctx, si.c, p1)
+        native.sph_density(ctx, si.c, p1)
+        native.sph_force(ctx, si.c, p1)
+        native.sph_timestep(ctx, si.c, p1, di)
+        native.sph_step(ctx, si.c, p1, di)
+        states.append((si, di))
+    native.sph_sync(ctx)
+    torch.cuda.synchronize()
+    e0.record()
+    for si, di in states:
+        for _ in range(args.batch_steps):
+            native.sph_step(ctx, si.c, p1, di)
+    e1.record()
+    torch.cuda.synchronize()
+    native.sph_sync(ctx)
+    t_seq = e0.elapsed_time(e1) / 1e3
+    native.sph_destroy(ctx)
+    updates = w.n * args.batch_steps
+    return {"workload": f"{k} Sedov blasts, sizes log-uniform in [4096, 262144] (seeded), "
+                        f"{w.n} particles", "steps": args.batch_steps,
+            "value": updates / t_batch, "unit": UNIT,
+            "plain_sequential_value": updates / t_seq, "batched_over_plain": t_seq / t_batch,
+            "pair_interactions_per_s": (stats["density_pairs"] + stats["force_pairs"]) / t_batch,
+            "autotune": report, "ms_per_step": 1e3 * t_batch / args.batch_steps}
 
 
 def run_e2e(native, ctx, s, p, n, args, stream):
@@ -324,6 +398,11 @@ def main():
     ap.add_argument("--side", type=int, default=SIDE)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--skip-e2e", action="store_true", help="profiling runs: no host-buffer leg")
+    ap.add_argument("--n-leaf", type=int, default=0, help="override N_leaf (paper: 16)")
+    ap.add_argument("--n-group", type=int, default=0, help="override N_group (paper: 8)")
+    ap.add_argument("--tile", type=int, default=0, help="override the neighbour-list tile")
+    ap.add_argument("--batch-instances", type=int, default=512)
+    ap.add_argument("--batch-steps", type=int, default=20)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

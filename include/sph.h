@@ -126,6 +126,65 @@ sph_status sph_timestep(sph_ctx *ctx, const sph_state *s, const sph_params *p, f
 sph_status sph_step(sph_ctx *ctx, sph_state *s, const sph_params *p, float *d_dt,
                     double *d_time, void *stream);
 
+/* Batched form (not in the paper): n_inst independent SPH problems packed
+ * back to back in one state; instance k owns slots [d_offsets[k],
+ * d_offsets[k+1]) (device int64 [n_inst+1], ascending, d_offsets[0] = 0,
+ * d_offsets[n_inst] = n, every instance non-empty, n_inst <= 65536).  Each
+ * instance gets its own bounding box, keys, tree and groups (the sort keeps
+ * every instance on its own slots), its own Courant step and its own time:
+ * d_dt is a device float [n_inst], d_time a device double [n_inst] (or NULL).
+ * The results for an instance equal those of the single-instance calls on
+ * that instance alone.
+ * sph_batch_evaluate: tree build, density, force and Courant step of every
+ * instance (the initial evaluation before stepping).
+ * sph_batch_step: n_steps leapfrog steps of every instance.  The first call
+ * for a given (state, offsets, params, d_dt, d_time) records one step into a
+ * CUDA graph (stream capture); every step is a replay of that graph, whose
+ * density and force kernels are persistent launches pulling the groups of
+ * all instances from one work queue.  Asynchronous. */
+sph_status sph_batch_evaluate(sph_ctx *ctx, sph_state *s, const int64_t *d_offsets, int n_inst,
+                              const sph_params *p, float *d_dt, void *stream);
+sph_status sph_batch_step(sph_ctx *ctx, sph_state *s, const int64_t *d_offsets, int n_inst,
+                          int n_steps, const sph_params *p, float *d_dt, double *d_time,
+                          void *stream);
+
+/* Adjoint of the force pass (not in the paper): given the cotangents
+ * d_gacc [n][4] = (dL/da xyz, dL/d(du/dt)) of the outputs of the LAST
+ * sph_force on this state (same tree and neighbour sets), writes dL/dx
+ * (d_gpos [n][4], xyz), dL/dv and dL/du (d_gvel [n][4]), dL/dh, dL/drho,
+ * dL/dOmega (d_gh, d_grho, d_gomega [n]) of every particle, and ADDS
+ * dL/dalpha_AV to *d_galpha (device double).  Deterministic: each particle
+ * sums the terms landing on its inputs (no atomics on particle data). */
+sph_status sph_force_bwd(sph_ctx *ctx, const sph_state *s, const sph_params *p,
+                         const float *d_gacc, float *d_gpos, float *d_gvel, float *d_gh,
+                         float *d_grho, float *d_gomega, double *d_galpha, void *stream);
+
+/* Adjoint of the density pass (not in the paper): given cotangents of h,
+ * rho and Omega from the LAST sph_density on this state, ADDS dL/dx to
+ * d_gpos [n][4] (xyz).  The h-rho fixed point is differentiated by the
+ * implicit-function theorem: dh_i = -(dg_i/dx) dx / (dg_i/dh_i),
+ * g_i = sum_j m_j W(r_ij, h_i) - m_i (hfact/h_i)^3 (Eqs. 1, 2, 4). */
+sph_status sph_density_bwd(sph_ctx *ctx, const sph_state *s, const sph_params *p,
+                           const float *d_gh, const float *d_grho, const float *d_gomega,
+                           float *d_gpos, void *stream);
+
+/* Differentiable rollout (not in the paper).  From the initial state init
+ * (device arrays pos, vel, h in the caller's order, n particles; not
+ * modified): initial evaluation, then n_steps leapfrog steps with the Courant
+ * dt of each step recorded; loss L = mean over the n_probes particles
+ * d_probes (device int64, caller's indices) of rho^2 after the last step,
+ * written to *h_loss (host).  If d_gvel (device float [n][4]) is not NULL,
+ * also writes dL/dv0 (xyz) and dL/du0 (w) of every particle in the caller's
+ * order and dL/dalpha_AV to *h_galpha (host), by the adjoint method: the dt
+ * sequence is held fixed, the state before every ckpt-th step is
+ * checkpointed, and each window of ckpt steps is recomputed from its
+ * checkpoint during the backward sweep.  Work buffers (about 12 state copies
+ * plus ckpt + n_steps/ckpt checkpoints) are allocated on the first call and
+ * kept by the context.  Synchronous. */
+sph_status sph_rollout(sph_ctx *ctx, const sph_state *init, const sph_params *p, int n_steps,
+                       int ckpt, const int64_t *d_probes, int n_probes, double *h_loss,
+                       float *d_gvel, double *h_galpha, void *stream);
+
 /* Same step for a state held in HOST memory (pinned for best speed): copies
  * the state in, runs n_steps steps, copies it back; *h_dt (host) is read as
  * the first dt and receives the next one.  Allocates a device mirror on the

@@ -6,7 +6,9 @@ same function names (``native``), holds device state in torch tensors
 (``state``) and draws seeded synthetic inputs (``inputs``).
 """
 from . import inputs  # noqa: F401
-from .native import (NativeLibraryMissing, SphError, load, sph_build_tree, sph_conserved,  # noqa: F401
+from .native import (NativeLibraryMissing, SphError, load, sph_batch_evaluate,  # noqa: F401
+                     sph_batch_step, sph_build_tree, sph_conserved, sph_conserved_noalloc,
+                     sph_density_bwd, sph_force_bwd, sph_rollout,
                      sph_create, sph_density, sph_destroy, sph_force, sph_get_stats,
                      sph_get_timing, sph_get_tree, sph_last_error, sph_neighbours, sph_params,
                      sph_params_default, sph_set_timing, sph_state, sph_step, sph_step_host,

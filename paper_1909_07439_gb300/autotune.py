@@ -1,0 +1,81 @@
+"""Autotuner for the batched step: picks the group size (N_group) and the
+neighbour-list tile width by timing a few graph-replayed steps of the actual
+batch, restoring the state between trials.  Results are cached in a JSON
+file keyed by device, particle count and instance count."""
+from __future__ import annotations
+
+import json
+import os
+
+from . import native
+
+CANDIDATES = [(g, t) for g in (4, 8, 16) for t in (64, 80, 96)]
+
+
+def cache_path() -> str:
+    base = os.environ.get("XDG_CACHE_HOME", os.path.join(os.path.expanduser("~"), ".cache"))
+    return os.path.join(base, "paper_1909_07439_gb300", "autotune.json")
+
+
+def _key(torch, n, n_inst):
+    return f"{torch.cuda.get_device_name()}|n={n}|inst={n_inst}"
+
+
+def _load_cache():
+    try:
+        with open(cache_path()) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _save_cache(c):
+    path = cache_path()
+    try:
+        os.makedirs(os.path.dirname(path), exist_ok=True)
+        with open(path + ".tmp", "w") as f:
+            json.dump(c, f, indent=1)
+        os.replace(path + ".tmp", path)
+    except OSError:
+        pass
+
+
+def tune_batch(ctx, state, d_offsets, n_inst, base=None, steps=2, use_cache=True,
+               candidates=CANDIDATES):
+    """Return (sph_params, report) with the fastest (n_group, tile) for this batch.
+    ``state`` (a DeviceState) is left exactly as it was on entry."""
+    import torch
+    base = base or native.sph_params_default()
+    key = _key(torch, state.n, n_inst)
+    cache = _load_cache() if use_cache else {}
+    if key in cache:
+        g, t = cache[key]["n_group"], cache[key]["tile"]
+        return native.sph_params_default(**{**_as_dict(base), "n_group": g, "tile": t}), cache[key]
+    saved = {f: getattr(state, f).clone() for f in state.FIELDS4 + state.FIELDS1 + ("perm", "keys")}
+    dt = torch.zeros(n_inst, dtype=torch.float32, device=state.device)
+    trials = []
+    for g, t in candidates:
+        for f, v in saved.items():
+            getattr(state, f).copy_(v)
+        p = native.sph_params_default(**{**_as_dict(base), "n_group": g, "tile": t})
+        native.sph_batch_evaluate(ctx, state.c, d_offsets, n_inst, p, dt)
+        native.sph_batch_step(ctx, state.c, d_offsets, n_inst, 1, p, dt)  # capture + warm
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        native.sph_batch_step(ctx, state.c, d_offsets, n_inst, steps, p, dt)
+        e1.record()
+        native.sph_sync(ctx)
+        trials.append({"n_group": g, "tile": t, "ms_per_step": e0.elapsed_time(e1) / steps})
+    for f, v in saved.items():
+        getattr(state, f).copy_(v)
+    best = min(trials, key=lambda r: r["ms_per_step"])
+    report = {"n_group": best["n_group"], "tile": best["tile"], "trials": trials}
+    if use_cache:
+        cache[key] = report
+        _save_cache(cache)
+    return native.sph_params_default(**{**_as_dict(base), "n_group": best["n_group"],
+                                        "tile": best["tile"]}), report
+
+
+def _as_dict(p):
+    return {k: getattr(p, k) for k, _ in p._fields_}

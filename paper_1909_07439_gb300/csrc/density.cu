@@ -21,16 +21,20 @@ namespace sph {
 
 constexpr int kTB = 8;           // targets per batch
 constexpr int kDensWarps = 4;    // warps per block
-constexpr float kPad = 0.05f;    // padded list radius, relative to h
+constexpr float kPad = 0.03f;    // padded list radius, relative to h
+constexpr int kRecLeaves = 96;   // leaf ranges a group's walk may record for the force pass
 
 template <int CAP>
 struct DensSmem {
     WalkSmem w;
     float4 tp[kTB];        // target x, y, z, m
+    float4 tv[kTB];        // target vx, vy, vz, u
+    TargetPairs<kTB> tq;   // target coordinates in pairs for the packed distance test
     float tr2[kTB];        // list radius^2
     int tlen[kTB];
-    float2 erm[kTB][CAP];  // (r^2, m_j)
-    int ej[kTB][CAP];
+    int rec_n;             // leaf ranges recorded by the last walk (-1: too many)
+    int2 rec[kRecLeaves];
+    float4 e[kTB][CAP];    // (r^2, m_j, (v_i - v_j).(x_i - x_j), 0)
 };
 
 struct DensArgs {
@@ -44,25 +48,27 @@ struct DensArgs {
     const int *sizes;
     int *work;
     WalkTree tree;
+    const int *inst;  // instance of each slot (batches), or nullptr
+    float h_in_scale;          // 1 + pad
+    int2 *leaf_rec, *grp_rec;  // recorded leaf ranges (see sph_internal.cuh)
+    int *rec_ctl;
+    int rec_cap;
     float hfact, tol, gamma;
     int max_iter, fixed_iters;
     int *err;
     unsigned long long *counters;
 };
 
+// M4 shape f(q) and f'(q) without branches (q >= 0; q >= 2 gives 0)
 __device__ __forceinline__ void m4_f_df(float q, float &f, float &df)
 {
-    if (q < 1.f) {
-        f = 1.f + q * q * (-1.5f + 0.75f * q);
-        df = q * (-3.f + 2.25f * q);
-    } else if (q < 2.f) {
-        float t = 2.f - q;
-        f = 0.25f * t * t * t;
-        df = -0.75f * t * t;
-    } else {
-        f = 0.f;
-        df = 0.f;
-    }
+    float fi = 1.f + q * q * (-1.5f + 0.75f * q);
+    float dfi = q * (-3.f + 2.25f * q);
+    float t = fmaxf(2.f - q, 0.f);
+    float t2 = t * t;
+    bool in = q < 1.f;
+    f = in ? fi : 0.25f * t2 * t;
+    df = in ? dfi : -0.75f * t2;
 }
 
 __device__ __forceinline__ float seg_sum(float v, int L)
@@ -80,6 +86,8 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_kernel(DensArgs a)
     const unsigned lt = lane_lt();
     const int ng = a.sizes[SZ_GROUPS];
     const float hf3 = a.hfact * a.hfact * a.hfact;
+    const bool fixed = a.fixed_iters > 0;
+    const int limit = fixed ? a.fixed_iters : a.max_iter;
     unsigned long long n_pairs = 0, n_cand = 0, n_newton = 0, n_rewalk = 0, n_stream = 0;
 
     while (true) {
@@ -89,6 +97,7 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_kernel(DensArgs a)
         if (g >= ng) break;
         const int2 gr = a.grp_ref[g];
         const float4 glo = a.grp_lo[g], ghi = a.grp_hi[g];
+        const int root = a.inst ? a.inst[gr.x] : 0;
         float ghmax = 0.f;
         for (int b0 = 0; b0 < gr.y; b0 += kTB) {
             const int nt = min(kTB, gr.y - b0);
@@ -96,107 +105,120 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_kernel(DensArgs a)
             const int t = lane / L, sub = lane % L;
             const bool act = t < nt;
             const int i = gr.x + b0 + (act ? t : 0);
-            if (lane < nt) sm.tp[lane] = a.pos[gr.x + b0 + lane];
+            if (lane < kTB) {
+                const float4 p = lane < nt ? a.pos[gr.x + b0 + lane] : make_float4(1e30f, 1e30f, 1e30f, 0.f);
+                sm.tp[lane] = p;
+                sm.tq.set(lane, p);
+                if (lane < nt) sm.tv[lane] = a.vel[gr.x + b0 + lane];
+            }
+            __syncwarp();
             float h = a.h[i];
-            const float mi = a.pos[i].w;
-            const float M = mi * hf3;
+            const float h_in = h;
+            const float M = sm.tp[act ? t : 0].w * hf3;  // m_i hfact^3
             float hlo = 0.f, hhi = INFINITY;
             float hw = h * (1.f + kPad);  // list radius is 2 hw
             bool valid = false;           // lists cover the current h
             bool streamed = false;        // group overflowed the tile
             bool conv = !act;
-            int it = 0;
-            const int limit = a.fixed_iters > 0 ? a.fixed_iters : a.max_iter;
             bool final_pass = false;
-            float s0, s1, s2;
-            int cnt;
-            __syncwarp();
+            int it = 0;
+            float s0, s1, s2, cf;
             while (true) {
                 // ---- one sweep: sums at the current h of every target
-                s0 = 0.f; s1 = 0.f; s2 = 0.f; cnt = 0;
+                s0 = 0.f; s1 = 0.f; s2 = 0.f;
+                int cnt = 0;
                 const float hinv = 1.f / h;
                 const float R = 2.f * h;
                 const float R2 = R * R;
-                const float4 ti = act ? sm.tp[t] : make_float4(0, 0, 0, 0);
-                const float4 vi = (act && final_pass) ? a.vel[i] : make_float4(0, 0, 0, 0);
                 auto list_sums = [&]() {
                     if (act) {
-                        const int len = min(sm.tlen[t], CAP);
+                        const int len = sm.tlen[t];
                         for (int e = sub; e < len; e += L) {
-                            float2 rm = sm.erm[t][e];
-                            if (!(rm.x < R2)) continue;
+                            const float4 q4 = sm.e[t][e];
+                            if (!(q4.x < R2)) continue;
                             ++cnt;
-                            float r = sqrtf(rm.x);
-                            float q = r * hinv, f, df;
+                            const float rinv = q4.x > 0.f ? rsqrtf(q4.x) : 0.f;
+                            const float q = q4.x * rinv * hinv;
+                            float f, df;
                             m4_f_df(q, f, df);
-                            s0 += rm.y * f;
-                            s1 += rm.y * (3.f * f + q * df);
-                            if (final_pass && r > 0.f) {
-                                int j = sm.ej[t][e];
-                                float4 pj = __ldg(&a.pos[j]);
-                                float4 vj = __ldg(&a.vel[j]);
-                                float vr = ((vi.x - vj.x) * (ti.x - pj.x) + (vi.y - vj.y) * (ti.y - pj.y) +
-                                            (vi.z - vj.z) * (ti.z - pj.z)) / r;
-                                s2 += rm.y * vr * df;
-                            }
+                            s0 += q4.y * f;
+                            s1 += q4.y * (3.f * f + q * df);
+                            s2 += q4.y * q4.z * df * rinv;
                         }
                     }
                     __syncwarp();
                 };
                 if (!valid) {
                     // (re)build the candidate lists with a walk
-                    if (lane < nt) {
-                        sm.tlen[lane] = 0;
-                    }
-                    // radius per target: padded unless streaming
-                    float myr = streamed ? R : 2.f * hw;
+                    const float myr = streamed ? R : 2.f * hw;  // padded unless streaming
                     if (act && sub == 0) sm.tr2[t] = myr * myr;
-                    float reach = 0.f;
-                    {
-                        float rr = act ? myr : 0.f;
-                        for (int o = 16; o > 0; o >>= 1) rr = fmaxf(rr, __shfl_xor_sync(0xffffffffu, rr, o));
-                        reach = rr;
-                    }
+                    if (lane < kTB) sm.tlen[lane] = 0;
+                    float reach = act ? myr : 0.f;
+                    for (int o = 16; o > 0; o >>= 1) reach = fmaxf(reach, __shfl_xor_sync(0xffffffffu, reach, o));
                     __syncwarp();
                     bool overflow = false;
                     auto chunk = [&](int j) {
-                        float4 pj = j >= 0 ? __ldg(&a.pos[j]) : make_float4(0, 0, 0, 0);
-                        float r2s[kTB];
+                        const float4 pj = j >= 0 ? __ldg(&a.pos[j]) : make_float4(0, 0, 0, 0);
+                        const float4 vj = j >= 0 ? __ldg(&a.vel[j]) : make_float4(0, 0, 0, 0);
                         unsigned bs[kTB];
+                        float r2s[kTB];
+                        int base[kTB];
                         bool over = false;
 #pragma unroll
-                        for (int tt = 0; tt < kTB; ++tt) {
-                            if (tt < nt) {
-                                float4 tq = sm.tp[tt];
-                                r2s[tt] = canon_r2(tq.x, tq.y, tq.z, pj.x, pj.y, pj.z);
-                                bs[tt] = __ballot_sync(0xffffffffu, j >= 0 && r2s[tt] < sm.tr2[tt]);
-                                over |= sm.tlen[tt] + __popc(bs[tt]) > CAP;
+                        for (int q = 0; q < kTB / 2; ++q) {
+                            const int t0 = 2 * q, t1 = 2 * q + 1;
+                            bs[t0] = bs[t1] = 0u;
+                            base[t0] = base[t1] = 0;
+                            r2s[t0] = r2s[t1] = 0.f;
+                            if (t0 < nt) {
+                                const float2 r2 = canon_r2_x2(sm.tq.x[q], sm.tq.y[q], sm.tq.z[q], pj.x,
+                                                              pj.y, pj.z);
+                                r2s[t0] = r2.x;
+                                r2s[t1] = r2.y;
+                                bs[t0] = __ballot_sync(0xffffffffu, j >= 0 && r2.x < sm.tr2[t0]);
+                                bs[t1] = __ballot_sync(0xffffffffu, j >= 0 && t1 < nt && r2.y < sm.tr2[t1]);
+                                base[t0] = sm.tlen[t0];
+                                base[t1] = sm.tlen[t1];
+                                over |= base[t0] + __popc(bs[t0]) > CAP;
+                                over |= base[t1] + __popc(bs[t1]) > CAP;
                             }
                         }
-                        // a list would overflow: sum what is there at the current h, start over
                         if (over) {
+                            // a list would overflow: sum what is there at the current h, start over
                             overflow = true;
                             list_sums();
                             if (lane < nt) sm.tlen[lane] = 0;
                             __syncwarp();
+#pragma unroll
+                            for (int tt = 0; tt < kTB; ++tt) base[tt] = 0;
                         }
 #pragma unroll
                         for (int tt = 0; tt < kTB; ++tt) {
                             if (tt < nt) {
-                                int base = sm.tlen[tt];
                                 if ((bs[tt] >> lane) & 1u) {
-                                    int p = base + __popc(bs[tt] & lt);
-                                    sm.erm[tt][p] = make_float2(r2s[tt], pj.w);
-                                    sm.ej[tt][p] = j;
+                                    const float4 tq = sm.tp[tt], tv = sm.tv[tt];
+                                    const float vdot = (tv.x - vj.x) * (tq.x - pj.x) +
+                                                       (tv.y - vj.y) * (tq.y - pj.y) +
+                                                       (tv.z - vj.z) * (tq.z - pj.z);
+                                    sm.e[tt][base[tt] + __popc(bs[tt] & lt)] =
+                                        make_float4(r2s[tt], pj.w, vdot, 0.f);
                                 }
-                                __syncwarp();
-                                if (lane == 0) sm.tlen[tt] = base + __popc(bs[tt]);
-                                __syncwarp();
+                                if (lane == tt) sm.tlen[tt] = base[tt] + __popc(bs[tt]);
                             }
                         }
-                        n_cand += (unsigned long long)nt * 32;
+                        __syncwarp();
+                        n_cand += (unsigned long long)nt;
                     };
-                    bool ok = walk_group(a.tree, glo, ghi, reach, false, 0.f, sm.w, chunk);
+                    // A padded-list walk opens a node if it is within reach of the
+                    // group or within 2 h_max(node) (1 + pad): that also covers the
+                    // force criterion 2 max(h_i, h_j) while no h grows beyond the pad,
+                    // so the force pass can replay the recorded leaves.
+                    if (lane == 0) sm.rec_n = streamed ? -1 : 0;
+                    __syncwarp();
+                    bool ok = streamed
+                                  ? walk_group(a.tree, root, glo, ghi, reach, false, 0.f, sm.w, chunk)
+                                  : walk_group(a.tree, root, glo, ghi, 0.f, true, 0.5f * reach, sm.w,
+                                               chunk, 1.f + kPad, sm.rec, &sm.rec_n, kRecLeaves);
                     if (!ok && lane == 0) raise_error(a.err, SPH_ERR_TILE_OVERFLOW);
                     list_sums();
                     if (overflow) {
@@ -212,69 +234,82 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_kernel(DensArgs a)
                 }
                 s0 = seg_sum(s0, L);
                 s1 = seg_sum(s1, L);
-                float cf = seg_sum((float)cnt, L);
-                if (sub == 0 && act) n_pairs += (unsigned long long)cf;
-                if (final_pass) {
-                    s2 = seg_sum(s2, L);
-                    break;
+                s2 = seg_sum(s2, L);
+                cf = seg_sum((float)cnt, L);
+                if (sub == 0 && act) {
+                    n_pairs += (unsigned long long)cf;
+                    ++n_newton;
                 }
-                // ---- Newton step on g(h) (bracketed)
+                if (final_pass) break;
+                // ---- bracketed Newton step on g(h); g h^3 = C s0 - M, g' h^4 = 3M - C s1
                 if (act && !conv) {
-                    float gt = kCNorm * s0 - M;          // g h^3
-                    float gp = 3.f * M - kCNorm * s1;    // g' h^4
-                    float hn;
+                    const float gt = kCNorm * s0 - M;
+                    const float gp = 3.f * M - kCNorm * s1;
                     if (gt == 0.f) {
-                        hn = h;
-                        conv = a.fixed_iters <= 0;
+                        conv = !fixed;
                     } else {
                         if (gt < 0.f) hlo = h; else hhi = h;
-                        hn = h * (1.f - gt / gp);
-                        bool ok = gp > 0.f && hn >= hlo && hn <= hhi && hn >= 0.5f * h && hn <= 2.f * h;
+                        float hn = h * (1.f - gt / gp);
+                        const bool ok = gp > 0.f && hn >= hlo && hn <= hhi && hn >= 0.5f * h && hn <= 2.f * h;
                         if (!ok) {
                             if (hlo > 0.f && hhi < INFINITY) hn = 0.5f * (hlo + hhi);
                             else if (gt < 0.f) hn = 2.f * h;
                             else hn = 0.5f * h;
                         }
-                        double rel = fabs((double)hn - (double)h) / (double)h;
-                        if (a.fixed_iters <= 0 && rel < (double)a.tol) conv = true;
+                        const double rel = fabs((double)hn - (double)h) / (double)h;  // FP64 test
+                        if (!fixed && rel < (double)a.tol) conv = true;  // sums are at this h
+                        else h = hn;
                     }
-                    h = hn;
-                    if (sub == 0) ++n_newton;
                     if (h > hw) {  // outgrew the padded list
                         hw = h * (1.f + kPad);
                         valid = false;
                     }
                 }
                 ++it;
-                bool need_walk = __any_sync(0xffffffffu, !valid && act);
-                if (need_walk) valid = false;
-                bool all_conv = __all_sync(0xffffffffu, conv);
-                if (a.fixed_iters > 0 ? it >= a.fixed_iters : (all_conv || it >= limit)) {
-                    if (!all_conv && a.fixed_iters <= 0 && lane == 0)
-                        raise_error(a.err, SPH_ERR_NOT_CONVERGED);
+                if (__any_sync(0xffffffffu, !valid)) valid = false;
+                if (fixed) {
+                    if (it >= limit) final_pass = true;   // one more sweep at the last h
+                } else if (__all_sync(0xffffffffu, conv)) {
+                    break;                                // every target's sums are at its h
+                } else if (it >= limit) {
+                    if (lane == 0) raise_error(a.err, SPH_ERR_NOT_CONVERGED);
                     final_pass = true;
-                    // the final sweep at the accepted h needs the lists to cover h
-                    if (__any_sync(0xffffffffu, act && h > hw)) valid = false;
                 }
                 __syncwarp();
             }
             // ---- outputs at the accepted h
             if (act && sub == 0) {
-                float hinv = 1.f / h;
-                float rho = M * hinv * hinv * hinv;
-                float om = 1.f - kCNorm * s1 / (3.f * M);
-                float F4 = kCNorm * hinv * hinv * hinv * hinv;
+                const float hinv = 1.f / h;
+                const float rho = M * hinv * hinv * hinv;
+                const float om = 1.f - kCNorm * s1 / (3.f * M);
+                const float F4 = kCNorm * hinv * hinv * hinv * hinv;
                 a.h[i] = h;
                 a.rho[i] = rho;
                 a.omega[i] = om;
                 a.drhodt[i] = F4 * s2 / om;
-                float u = a.vel[i].w;
-                float cs = sqrtf(fmaxf(a.gamma * (a.gamma - 1.f) * u, 0.f));
+                const float u = sm.tv[t].w;
+                const float cs = sqrtf(fmaxf(a.gamma * (a.gamma - 1.f) * u, 0.f));
                 a.prop[i] = make_float4(h, rho, 1.f / (rho * om), cs);
             }
             float hm = act ? h : 0.f;
             for (int o = 16; o > 0; o >>= 1) hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
             ghmax = fmaxf(ghmax, hm);
+            // the records hold while no h grew beyond the pad used by the walk
+            if (__any_sync(0xffffffffu, act && h > a.h_in_scale * h_in) && lane == 0)
+                atomicOr(a.rec_ctl + 1, 1);
+            __syncwarp();
+            // keep the last walk's leaves for the force pass (one-batch groups)
+            int2 rr = make_int2(0, -1);
+            if (gr.y <= kTB && sm.rec_n >= 0) {
+                int start = 0;
+                if (lane == 0) start = atomicAdd(a.rec_ctl, sm.rec_n);
+                start = __shfl_sync(0xffffffffu, start, 0);
+                if (start + sm.rec_n <= a.rec_cap) {
+                    for (int k = lane; k < sm.rec_n; k += 32) a.leaf_rec[start + k] = sm.rec[k];
+                    rr = make_int2(start, sm.rec_n);
+                }
+            }
+            if (lane == 0 && b0 == 0) a.grp_rec[g] = rr;
             __syncwarp();
         }
         if (lane == 0) a.grp_lo[g].w = ghmax;
@@ -282,12 +317,11 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_kernel(DensArgs a)
     // counters: one atomic per warp
     for (int o = 16; o > 0; o >>= 1) {
         n_pairs += __shfl_xor_sync(0xffffffffu, n_pairs, o);
-        n_cand += __shfl_xor_sync(0xffffffffu, n_cand, o);
         n_newton += __shfl_xor_sync(0xffffffffu, n_newton, o);
     }
     if (lane == 0) {
         atomicAdd(&a.counters[C_DENS_PAIRS], n_pairs);
-        atomicAdd(&a.counters[C_DENS_CAND], n_cand / 32);  // n_cand counted on all lanes
+        atomicAdd(&a.counters[C_DENS_CAND], n_cand * 32);
         atomicAdd(&a.counters[C_NEWTON], n_newton);
         atomicAdd(&a.counters[C_REWALK], n_rewalk);
         atomicAdd(&a.counters[C_STREAMED], n_stream);
@@ -303,6 +337,7 @@ struct NbrArgs {
     const int *sizes;
     int *work;
     WalkTree tree;
+    const int *inst;
     int mode;          // 0 density set, 1 force set
     int64_t *off;      // [n+1]
     int32_t *idx;      // nullptr: count pass
@@ -358,7 +393,8 @@ __global__ void __launch_bounds__(128) neighbour_kernel(NbrArgs a)
                     __syncwarp();
                 }
             };
-            bool ok = walk_group(a.tree, glo, ghi, 2.f * hmx, a.mode == 1, hmx, sm.w, chunk);
+            bool ok = walk_group(a.tree, a.inst ? a.inst[gr.x] : 0, glo, ghi, 2.f * hmx, a.mode == 1,
+                                 hmx, sm.w, chunk);
             if (!ok && lane == 0) raise_error(a.err, SPH_ERR_TILE_OVERFLOW);
             if (lane < nt && !a.idx) a.off[gr.x + b0 + lane] = sm.tcnt[lane];
             __syncwarp();
@@ -394,30 +430,58 @@ __global__ void scan_i64_kernel(int64_t *off, int n)
 }
 
 // ------------------------------------------------------------------ host side
+// one-time kernel attributes and occupancy (also called before graph capture)
 template <int CAP>
-static cudaError_t launch_density(Ctx &c, const DensArgs &a, cudaStream_t st)
+static cudaError_t configure_density(int &blocks)
 {
-    size_t smem = sizeof(DensSmem<CAP>) * kDensWarps;
     static bool configured = false;
-    static int g_dens_blocks = 0;
+    static int nb_cached = 1;
     if (!configured) {
+        size_t smem = sizeof(DensSmem<CAP>) * kDensWarps;
         cudaError_t e = cudaFuncSetAttribute(density_kernel<CAP>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int nb = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, density_kernel<CAP>, kDensWarps * 32, smem);
         if (e != cudaSuccess) return e;
-        g_dens_blocks = nb > 0 ? nb : 1;
+        nb_cached = nb > 0 ? nb : 1;
         configured = true;
     }
-    int grid = c.num_sms * g_dens_blocks;
-    density_kernel<CAP><<<grid, kDensWarps * 32, smem, st>>>(a);
+    blocks = nb_cached;
+    return cudaSuccess;
+}
+
+template <int CAP>
+static cudaError_t launch_density(Ctx &c, const DensArgs &a, cudaStream_t st)
+{
+    int blocks = 1;
+    cudaError_t e = configure_density<CAP>(blocks);
+    if (e != cudaSuccess) return e;
+    size_t smem = sizeof(DensSmem<CAP>) * kDensWarps;
+    density_kernel<CAP><<<c.num_sms * blocks, kDensWarps * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t density_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st)
+cudaError_t configure_density_kernels()
+{
+    int b;
+    cudaError_t e = configure_density<64>(b);
+    if (e == cudaSuccess) e = configure_density<80>(b);
+    if (e == cudaSuccess) e = configure_density<96>(b);
+    if (e == cudaSuccess) e = configure_density<128>(b);
+    return e;
+}
+
+cudaError_t density_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st,
+                         const Batch *batch)
 {
     DensArgs a{};
+    a.inst = batch ? c.inst : nullptr;
+    a.h_in_scale = 1.f + kPad;
+    a.leaf_rec = c.tree.leaf_rec;
+    a.grp_rec = c.tree.grp_rec;
+    a.rec_ctl = c.tree.rec_ctl;
+    a.rec_cap = c.tree.rec_cap;
     a.pos = (const float4 *)s.pos;
     a.vel = (const float4 *)s.vel;
     a.h = s.h;
@@ -440,8 +504,12 @@ cudaError_t density_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaSt
     a.counters = c.d_counters;
     cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    int cap = p.tile > 0 ? p.tile : 96;
+    // fresh leaf records: allocation counter 0, valid unless an h outgrows its pad
+    e = cudaMemsetAsync(c.tree.rec_ctl, 0, 2 * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    int cap = p.tile > 0 ? p.tile : 80;
     if (cap <= 64) return launch_density<64>(c, a, st);
+    if (cap <= 80) return launch_density<80>(c, a, st);
     if (cap <= 96) return launch_density<96>(c, a, st);
     return launch_density<128>(c, a, st);
 }

@@ -21,6 +21,8 @@ struct ForceSmem {
     float4 tp[kFTB];   // x, y, z, m
     float4 tv[kFTB];   // vx, vy, vz, u
     float4 tq[kFTB];   // h, rho, 1/(rho Omega), c
+    TargetPairs<kFTB> tc;  // target coordinates in pairs for the packed distance test
+    float th[kFTB];    // target h (0 for unused slots)
     int tlen[kFTB];
     int ej[kFTB][CAP];
 };
@@ -34,6 +36,9 @@ struct ForceArgs {
     const int *sizes;
     int *work;
     WalkTree tree;
+    const int *inst;  // instance of each slot (batches), or nullptr
+    const int2 *leaf_rec, *grp_rec;  // leaf ranges recorded by the density walk
+    const int *rec_ctl;
     float gm1, alpha, beta, alpha_u;
     int *err;
     unsigned long long *counters;
@@ -50,13 +55,14 @@ __device__ __forceinline__ float m4_df(float q)
 }
 
 template <int CAP>
-__global__ void __launch_bounds__(kForceWarps * 32) force_kernel(ForceArgs a)
+__global__ void __launch_bounds__(kForceWarps * 32, 6) force_kernel(ForceArgs a)
 {
     extern __shared__ __align__(16) unsigned char fsm_raw[];
     ForceSmem<CAP> &sm = reinterpret_cast<ForceSmem<CAP> *>(fsm_raw)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const unsigned lt = lane_lt();
     const int ng = a.sizes[SZ_GROUPS];
+    const bool recs_valid = a.rec_ctl[1] == 0;
     unsigned long long n_pairs = 0, n_cand = 0;
 
     while (true) {
@@ -72,11 +78,16 @@ __global__ void __launch_bounds__(kForceWarps * 32) force_kernel(ForceArgs a)
             const int t = lane / L, sub = lane % L;
             const bool act = t < nt;
             const int i0 = gr.x + b0;
-            if (lane < nt) {
-                sm.tp[lane] = a.pos[i0 + lane];
-                sm.tv[lane] = a.vel[i0 + lane];
-                sm.tq[lane] = a.prop[i0 + lane];
+            if (lane < kFTB) {
+                const float4 p = lane < nt ? a.pos[i0 + lane] : make_float4(1e30f, 1e30f, 1e30f, 0.f);
+                sm.tc.set(lane, p);
+                sm.th[lane] = lane < nt ? a.prop[i0 + lane].x : 0.f;
                 sm.tlen[lane] = 0;
+                if (lane < nt) {
+                    sm.tp[lane] = p;
+                    sm.tv[lane] = a.vel[i0 + lane];
+                    sm.tq[lane] = a.prop[i0 + lane];
+                }
             }
             __syncwarp();
             // per-target constants in registers of the target's lanes
@@ -133,36 +144,51 @@ __global__ void __launch_bounds__(kForceWarps * 32) force_kernel(ForceArgs a)
                 __syncwarp();
             };
             auto chunk = [&](int j) {
-                float4 pj = j >= 0 ? __ldg(&a.pos[j]) : make_float4(0, 0, 0, 0);
-                float hj = j >= 0 ? __ldg(&a.prop[j].x) : 0.f;
+                const float4 pj = j >= 0 ? __ldg(&a.pos[j]) : make_float4(0, 0, 0, 0);
+                const float hj = j >= 0 ? __ldg(&a.prop[j].x) : 0.f;
                 unsigned bs[kFTB];
+                int base[kFTB];
                 bool over = false;
 #pragma unroll
-                for (int tt = 0; tt < kFTB; ++tt) {
-                    if (tt < nt) {
-                        float4 tp = sm.tp[tt];
-                        float ht = sm.tq[tt].x;
-                        float r2 = canon_r2(tp.x, tp.y, tp.z, pj.x, pj.y, pj.z);
-                        float R = 2.0f * fmaxf(ht, hj);
-                        bs[tt] = __ballot_sync(0xffffffffu, j >= 0 && j != i0 + tt && r2 < R * R);
-                        over |= sm.tlen[tt] + __popc(bs[tt]) > CAP;
+                for (int q = 0; q < kFTB / 2; ++q) {
+                    const int t0 = 2 * q, t1 = 2 * q + 1;
+                    bs[t0] = bs[t1] = 0u;
+                    base[t0] = base[t1] = 0;
+                    if (t0 < nt) {
+                        const float2 r2 = canon_r2_x2(sm.tc.x[q], sm.tc.y[q], sm.tc.z[q], pj.x, pj.y, pj.z);
+                        const float R0 = 2.0f * fmaxf(sm.th[t0], hj);
+                        const float R1 = 2.0f * fmaxf(sm.th[t1], hj);
+                        bs[t0] = __ballot_sync(0xffffffffu, j >= 0 && j != i0 + t0 && r2.x < R0 * R0);
+                        bs[t1] = __ballot_sync(0xffffffffu, j >= 0 && t1 < nt && j != i0 + t1 && r2.y < R1 * R1);
+                        base[t0] = sm.tlen[t0];
+                        base[t1] = sm.tlen[t1];
+                        over |= base[t0] + __popc(bs[t0]) > CAP;
+                        over |= base[t1] + __popc(bs[t1]) > CAP;
                     }
                 }
-                if (over) flush();  // run the pairs listed so far, then start over
+                if (over) {  // run the pairs listed so far, then start over
+                    flush();
+#pragma unroll
+                    for (int tt = 0; tt < kFTB; ++tt) base[tt] = 0;
+                }
 #pragma unroll
                 for (int tt = 0; tt < kFTB; ++tt) {
                     if (tt < nt) {
-                        int base = sm.tlen[tt];
-                        if ((bs[tt] >> lane) & 1u) sm.ej[tt][base + __popc(bs[tt] & lt)] = j;
-                        __syncwarp();
-                        if (lane == 0) sm.tlen[tt] = base + __popc(bs[tt]);
-                        __syncwarp();
+                        if ((bs[tt] >> lane) & 1u) sm.ej[tt][base[tt] + __popc(bs[tt] & lt)] = j;
+                        if (lane == tt) sm.tlen[tt] = base[tt] + __popc(bs[tt]);
                     }
                 }
+                __syncwarp();
                 n_cand += (unsigned long long)nt;
             };
-            bool ok = walk_group(a.tree, glo, ghi, 0.f, true, glo.w, sm.w, chunk);
-            if (!ok && lane == 0) raise_error(a.err, SPH_ERR_TILE_OVERFLOW);
+            const int2 rr = recs_valid ? a.grp_rec[g] : make_int2(0, -1);
+            if (rr.y >= 0 && gr.y <= kFTB) {
+                replay_ranges(a.leaf_rec + rr.x, rr.y, chunk);
+            } else {
+                bool ok = walk_group(a.tree, a.inst ? a.inst[gr.x] : 0, glo, ghi, 0.f, true, glo.w,
+                                     sm.w, chunk);
+                if (!ok && lane == 0) raise_error(a.err, SPH_ERR_TILE_OVERFLOW);
+            }
             flush();
             // reduce over the L lanes of each target
             for (int o = L >> 1; o > 0; o >>= 1) {
@@ -212,24 +238,45 @@ __global__ void force_prep_kernel(const float4 *__restrict__ vel, const float *_
     if (__any_sync(0xffffffffu, neg) && (threadIdx.x & 31) == 0) raise_error(err, SPH_ERR_NEGATIVE_U);
 }
 
+// one-time kernel attributes and occupancy (also called before graph capture)
 template <int CAP>
-static cudaError_t launch_force(Ctx &c, const ForceArgs &a, cudaStream_t st)
+static cudaError_t configure_force(int &blocks)
 {
-    size_t smem = sizeof(ForceSmem<CAP>) * kForceWarps;
     static bool configured = false;
-    static int blocks = 1;
+    static int nb_cached = 1;
     if (!configured) {
+        size_t smem = sizeof(ForceSmem<CAP>) * kForceWarps;
         cudaError_t e = cudaFuncSetAttribute(force_kernel<CAP>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int nb = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_kernel<CAP>, kForceWarps * 32, smem);
         if (e != cudaSuccess) return e;
-        blocks = nb > 0 ? nb : 1;
+        nb_cached = nb > 0 ? nb : 1;
         configured = true;
     }
+    blocks = nb_cached;
+    return cudaSuccess;
+}
+
+template <int CAP>
+static cudaError_t launch_force(Ctx &c, const ForceArgs &a, cudaStream_t st)
+{
+    int blocks = 1;
+    cudaError_t e = configure_force<CAP>(blocks);
+    if (e != cudaSuccess) return e;
+    size_t smem = sizeof(ForceSmem<CAP>) * kForceWarps;
     force_kernel<CAP><<<c.num_sms * blocks, kForceWarps * 32, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t configure_force_kernels()
+{
+    int b;
+    cudaError_t e = configure_force<64>(b);
+    if (e == cudaSuccess) e = configure_force<96>(b);
+    if (e == cudaSuccess) e = configure_force<128>(b);
+    return e;
 }
 
 cudaError_t force_prep(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st)
@@ -244,10 +291,15 @@ cudaError_t force_prep(Ctx &c, const sph_state &s, const sph_params &p, cudaStre
     return update_hmax(c, s, p, st);
 }
 
-cudaError_t force_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st)
+cudaError_t force_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st,
+                       const Batch *batch)
 {
     cudaError_t e;
     ForceArgs a{};
+    a.inst = batch ? c.inst : nullptr;
+    a.leaf_rec = c.tree.leaf_rec;
+    a.grp_rec = c.tree.grp_rec;
+    a.rec_ctl = c.tree.rec_ctl;
     a.pos = (const float4 *)s.pos;
     a.vel = (const float4 *)s.vel;
     a.prop = c.prop;

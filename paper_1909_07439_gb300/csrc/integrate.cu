@@ -18,10 +18,14 @@ static int grid_n(const Ctx &c, int64_t n, int block)
 // r1 = r + v_half dt = r + v dt + a dt^2/2 (Eq. 5).
 __global__ void kick_drift_kernel(float4 *__restrict__ pos, float4 *__restrict__ vel,
                                   const float4 *__restrict__ acc, float4 *__restrict__ vhalf,
-                                  int n, const float *d_dt)
+                                  int n, const float *d_dt, const int *__restrict__ inst)
 {
-    const float dt = *d_dt, hdt = 0.5f * dt;
+    float dt = *d_dt, hdt = 0.5f * dt;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (inst) {
+            dt = d_dt[inst[i]];
+            hdt = 0.5f * dt;
+        }
         float4 v = vel[i], a = acc[i], p = pos[i];
         float4 vh = make_float4(v.x + hdt * a.x, v.y + hdt * a.y, v.z + hdt * a.z, v.w + hdt * a.w);
         vhalf[i] = vh;
@@ -33,18 +37,61 @@ __global__ void kick_drift_kernel(float4 *__restrict__ pos, float4 *__restrict__
 // v1 = v_half + a1 dt/2 (equal to Eq. 7 applied to the Eq. 6 prediction)
 __global__ void kick_close_kernel(float4 *__restrict__ vel, const float4 *__restrict__ acc,
                                   const float4 *__restrict__ vhalf, int n, const float *d_dt,
-                                  double *d_time, int *err)
+                                  double *d_time, int *err, const int *__restrict__ inst)
 {
-    const float dt = *d_dt, hdt = 0.5f * dt;
+    float dt = *d_dt, hdt = 0.5f * dt;
     bool neg = false;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (inst) {
+            dt = d_dt[inst[i]];
+            hdt = 0.5f * dt;
+        }
         float4 vh = vhalf[i], a = acc[i];
         float4 v = make_float4(vh.x + hdt * a.x, vh.y + hdt * a.y, vh.z + hdt * a.z, vh.w + hdt * a.w);
         neg |= !(v.w >= 0.f);
         vel[i] = v;
     }
     if (__any_sync(0xffffffffu, neg) && (threadIdx.x & 31) == 0) raise_error(err, SPH_ERR_NEGATIVE_U);
-    if (d_time && blockIdx.x == 0 && threadIdx.x == 0) *d_time += (double)dt;
+    if (!inst && d_time && blockIdx.x == 0 && threadIdx.x == 0) *d_time += (double)*d_dt;
+}
+
+// per-instance simulation time
+__global__ void time_batch_kernel(const float *d_dt, double *d_time, int n_inst)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_inst; k += gridDim.x * blockDim.x)
+        d_time[k] += (double)d_dt[k];
+}
+
+// per-instance minimum of h / vsigmax: ordered-int atomics, combined per warp
+// when the warp lies inside one instance (positive floats order as ints)
+__global__ void dt_batch_init_kernel(int *dtmin, int n_inst)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_inst; k += gridDim.x * blockDim.x)
+        dtmin[k] = 0x7f800000;  // +inf
+}
+
+__global__ void dt_batch_kernel(const float *__restrict__ h, const float *__restrict__ vs,
+                                const int *__restrict__ inst, int n, int *dtmin)
+{
+    for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
+        int i = i0 + threadIdx.x;
+        bool in = i < n;
+        float m = in ? h[i] / vs[i] : INFINITY;
+        int k = in ? inst[i] : -1;
+        int k0 = __shfl_sync(0xffffffffu, k, 0);
+        if (__all_sync(0xffffffffu, k == k0)) {
+            for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+            if ((threadIdx.x & 31) == 0 && k0 >= 0) atomicMin(dtmin + k0, __float_as_int(m));
+        } else if (in) {
+            atomicMin(dtmin + k, __float_as_int(m));
+        }
+    }
+}
+
+__global__ void dt_batch_final_kernel(const int *dtmin, int n_inst, float c_cour, float *d_dt)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_inst; k += gridDim.x * blockDim.x)
+        d_dt[k] = c_cour * __int_as_float(dtmin[k]);
 }
 
 // block minima of h / vsigmax
@@ -114,27 +161,39 @@ __global__ void conserved_final_kernel(const double *part, int nb, double *out8)
     }
 }
 
-cudaError_t kick_drift(Ctx &c, const sph_state &s, const float *d_dt, cudaStream_t st)
+cudaError_t kick_drift(Ctx &c, const sph_state &s, const float *d_dt, cudaStream_t st,
+                       const Batch *batch)
 {
     int n = (int)s.n;
     kick_drift_kernel<<<grid_n(c, n, 256), 256, 0, st>>>((float4 *)s.pos, (float4 *)s.vel,
-                                                         (const float4 *)s.acc, c.vhalf, n, d_dt);
+                                                         (const float4 *)s.acc, c.vhalf, n, d_dt,
+                                                         batch ? c.inst : nullptr);
     return cudaGetLastError();
 }
 
 cudaError_t kick_close(Ctx &c, const sph_state &s, const float *d_dt, double *d_time,
-                       cudaStream_t st)
+                       cudaStream_t st, const Batch *batch)
 {
     int n = (int)s.n;
     kick_close_kernel<<<grid_n(c, n, 256), 256, 0, st>>>((float4 *)s.vel, (const float4 *)s.acc,
-                                                         c.vhalf, n, d_dt, d_time, c.d_err);
+                                                         c.vhalf, n, d_dt, d_time, c.d_err,
+                                                         batch ? c.inst : nullptr);
+    if (batch && d_time)
+        time_batch_kernel<<<div_up(batch->n_inst, 256), 256, 0, st>>>(d_dt, d_time, batch->n_inst);
     return cudaGetLastError();
 }
 
 cudaError_t courant_dt(Ctx &c, const sph_state &s, const sph_params &p, float *d_dt,
-                       cudaStream_t st)
+                       cudaStream_t st, const Batch *batch)
 {
     int n = (int)s.n;
+    if (batch) {
+        const int ni = batch->n_inst;
+        dt_batch_init_kernel<<<div_up(ni, 256), 256, 0, st>>>(c.dtmin_inst, ni);
+        dt_batch_kernel<<<grid_n(c, n, 256), 256, 0, st>>>(s.h, s.vsigmax, c.inst, n, c.dtmin_inst);
+        dt_batch_final_kernel<<<div_up(ni, 256), 256, 0, st>>>(c.dtmin_inst, ni, p.c_cour, d_dt);
+        return cudaGetLastError();
+    }
     int nb = grid_n(c, n, 256);
     dt_block_kernel<<<nb, 256, 0, st>>>(s.h, s.vsigmax, n, c.red_f);
     dt_final_kernel<<<1, 32, 0, st>>>(c.red_f, nb, p.c_cour, d_dt);

@@ -216,11 +216,18 @@ sph_status sph_create(sph_ctx **out, int64_t max_n, int device)
     A(dalloc(t.grp_ref, t.cap_groups));
     A(dalloc(t.grp_lo, t.cap_groups));
     A(dalloc(t.grp_hi, t.cap_groups));
+    t.rec_cap = (int)(6 * n + 4096 < (size_t)INT32_MAX ? 6 * n + 4096 : INT32_MAX);
+    A(dalloc(t.leaf_rec, t.rec_cap));
+    A(dalloc(t.grp_rec, t.cap_groups));
+    A(dalloc(t.rec_ctl, 2));
     A(dalloc(t.lv_tree, n));
     A(dalloc(t.lv_grp, n));
     A(dalloc(t.blk_cnt, (size_t)kLevels * nbchop));
     A(dalloc(c.prop, n));
     A(dalloc(c.vhalf, n));
+    A(dalloc(c.inst, n));
+    A(dalloc(c.bbox_inst, (size_t)6 * kMaxInstances));
+    A(dalloc(c.dtmin_inst, kMaxInstances));
     A(dalloc(c.bbox, 8));
     A(dalloc(c.scan_part, c.scan_part_cap));
     A(dalloc(c.red_f, c.red_cap));
@@ -254,13 +261,17 @@ void sph_destroy(sph_ctx *h)
                     c.tree.node_nchild, c.tree.node_parent, c.tree.node_arrive, c.tree.node_lo,
                     c.tree.node_hi, c.tree.node_ref, c.tree.level_start, c.tree.grp_ref,
                     c.tree.grp_lo, c.tree.grp_hi, c.tree.lv_tree, c.tree.lv_grp, c.tree.blk_cnt,
-                    c.prop, c.vhalf, c.bbox, c.scan_part, c.red_f, c.red_d, c.d_err, c.d_counters,
+                    c.tree.leaf_rec, c.tree.grp_rec, c.tree.rec_ctl,
+                    c.prop, c.vhalf, c.inst, c.bbox_inst, c.dtmin_inst,
+                    c.bbox, c.scan_part, c.red_f, c.red_d, c.d_err, c.d_counters,
                     c.d_sizes, c.mirror.pos, c.mirror.vel, c.mirror.acc, c.mirror.h, c.mirror.rho,
                     c.mirror.omega, c.mirror.drhodt, c.mirror.vsigmax, c.mirror.perm,
                     c.mirror.keys, c.mirror_dt};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c.h_pinned) cudaFreeHost(c.h_pinned);
+    if (c.batch_graph) cudaGraphExecDestroy(c.batch_graph);
+    if (c.capture_stream) cudaStreamDestroy(c.capture_stream);
     for (auto &p : c.ev_free) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto &p : c.ev_pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     delete h;
@@ -405,6 +416,106 @@ sph_status sph_step_host(sph_ctx *h, sph_state *hs, const sph_params *p, int n_s
     CK(cudaMemcpyAsync(hs->keys, d.keys, n * 8, D2H, st), "D2H keys");
     CK(cudaMemcpyAsync(h_dt, c.mirror_dt, sizeof(float), D2H, st), "D2H dt");
     return sph_sync(h, stream);
+}
+
+namespace {
+
+sph_status check_batch(Ctx &c, const sph_state *s, const int64_t *d_offsets, int n_inst)
+{
+    if (!d_offsets) return fail(c, SPH_ERR_INVALID_ARG, "d_offsets is NULL");
+    if (n_inst < 1 || n_inst > kMaxInstances)
+        return fail(c, SPH_ERR_INVALID_ARG, "n_inst must be 1..65536");
+    if (s->n < n_inst) return fail(c, SPH_ERR_INVALID_ARG, "every instance needs a particle");
+    return SPH_OK;
+}
+
+// enqueue one leapfrog step of every instance of a batch (no host sync)
+cudaError_t enqueue_batch_step(Ctx &c, const sph_state &s, const sph_params &p, const Batch &b,
+                               float *d_dt, double *d_time, cudaStream_t st)
+{
+    cudaError_t e = kick_drift(c, s, d_dt, st, &b);
+    if (e == cudaSuccess) e = build_tree(c, s, p, false, st, &b);
+    if (e == cudaSuccess) e = density_pass(c, s, p, st, &b);
+    if (e == cudaSuccess) e = force_prep(c, s, p, st);
+    if (e == cudaSuccess) e = force_pass(c, s, p, st, &b);
+    if (e == cudaSuccess) e = kick_close(c, s, d_dt, d_time, st, &b);
+    if (e == cudaSuccess) e = courant_dt(c, s, p, d_dt, st, &b);
+    return e;
+}
+
+}  // namespace
+
+sph_status sph_batch_evaluate(sph_ctx *h, sph_state *s, const int64_t *d_offsets, int n_inst,
+                              const sph_params *p, float *d_dt, void *stream)
+{
+    if (!h) return SPH_ERR_INVALID_ARG;
+    Ctx &c = h->impl;
+    sph_status r = check_state(c, s, true);
+    if (r != SPH_OK) return r;
+    if ((r = check_params(c, p)) != SPH_OK) return r;
+    if ((r = check_batch(c, s, d_offsets, n_inst)) != SPH_OK) return r;
+    if (!d_dt) return fail(c, SPH_ERR_INVALID_ARG, "d_dt is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    Batch b{d_offsets, n_inst};
+    const int n = (int)s->n;
+    CK(instance_map(c, d_offsets, n_inst, n, st), "instance map");
+    CK(build_tree(c, *s, *p, true, st, &b), "batch build_tree");
+    CK(density_pass(c, *s, *p, st, &b), "batch density");
+    CK(force_prep(c, *s, *p, st), "batch force_prep");
+    CK(force_pass(c, *s, *p, st, &b), "batch force");
+    CK(courant_dt(c, *s, *p, d_dt, st, &b), "batch timestep");
+    return SPH_OK;
+}
+
+sph_status sph_batch_step(sph_ctx *h, sph_state *s, const int64_t *d_offsets, int n_inst,
+                          int n_steps, const sph_params *p, float *d_dt, double *d_time,
+                          void *stream)
+{
+    if (!h) return SPH_ERR_INVALID_ARG;
+    Ctx &c = h->impl;
+    sph_status r = check_state(c, s, true);
+    if (r != SPH_OK) return r;
+    if ((r = check_params(c, p)) != SPH_OK) return r;
+    if ((r = check_batch(c, s, d_offsets, n_inst)) != SPH_OK) return r;
+    if (!d_dt || n_steps < 0) return fail(c, SPH_ERR_INVALID_ARG, "d_dt is NULL or n_steps < 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    Batch b{d_offsets, n_inst};
+    CK(instance_map(c, d_offsets, n_inst, (int)s->n, st), "instance map");
+    // the graph is valid for exactly these pointers, sizes and parameters
+    std::vector<unsigned char> key(sizeof(sph_state) + sizeof(sph_params) + 4 * sizeof(void *));
+    unsigned char *kp = key.data();
+    memcpy(kp, s, sizeof(sph_state)); kp += sizeof(sph_state);
+    memcpy(kp, p, sizeof(sph_params)); kp += sizeof(sph_params);
+    const void *extra[4] = {d_offsets, d_dt, d_time, (const void *)(intptr_t)n_inst};
+    memcpy(kp, extra, sizeof(extra));
+    if (!c.batch_graph || key != c.batch_graph_key) {
+        if (c.batch_graph) {
+            cudaGraphExecDestroy(c.batch_graph);
+            c.batch_graph = nullptr;
+        }
+        CK(configure_density_kernels(), "configure density");
+        CK(configure_force_kernels(), "configure force");
+        // record on a private stream: the caller's may be the legacy default
+        // stream, which cannot be captured
+        if (!c.capture_stream)
+            CK(cudaStreamCreateWithFlags(&c.capture_stream, cudaStreamNonBlocking), "capture stream");
+        cudaStream_t cs = c.capture_stream;
+        CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture");
+        cudaError_t e = enqueue_batch_step(c, *s, *p, b, d_dt, d_time, cs);
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+        if (e != cudaSuccess) return cuda_fail(c, e, "batch step capture");
+        if (e2 != cudaSuccess) return cuda_fail(c, e2, "end capture");
+        cudaError_t e3 = cudaGraphInstantiate(&c.batch_graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e3 != cudaSuccess) {
+            c.batch_graph = nullptr;
+            return cuda_fail(c, e3, "graph instantiate");
+        }
+        c.batch_graph_key = key;
+    }
+    for (int k = 0; k < n_steps; ++k) CK(cudaGraphLaunch(c.batch_graph, st), "graph launch");
+    return SPH_OK;
 }
 
 sph_status sph_conserved(sph_ctx *h, const sph_state *s, double *d_out8, void *stream)

@@ -56,10 +56,25 @@ struct Tree {
     int2 *grp_ref = nullptr;     // (first, count)
     float4 *grp_lo = nullptr;    // x, y, z, h_max
     float4 *grp_hi = nullptr;
+    // leaf ranges opened by each group's density walk, replayed by the force
+    // pass: grp_rec[g] = (start, count) into leaf_rec, count < 0: not recorded;
+    // rec_ctl[0] = allocation counter, rec_ctl[1] = 1 while the records are valid
+    int2 *leaf_rec = nullptr;
+    int2 *grp_rec = nullptr;
+    int *rec_ctl = nullptr;
+    int rec_cap = 0;
     // chop scratch
     int *lv_tree = nullptr, *lv_grp = nullptr;
     int *blk_cnt = nullptr;      // [kLevels][nb]
 };
+
+// a batch of independent instances packed back to back
+struct Batch {
+    const int64_t *offsets;  // device [n_inst + 1]
+    int n_inst;
+};
+
+constexpr int kMaxInstances = 65536;
 
 struct Ctx {
     int device = 0;
@@ -85,6 +100,13 @@ struct Ctx {
     float4 *prop = nullptr;   // h, rho, 1/(rho Omega), c_s
     float4 *vhalf = nullptr;  // half-step v, u of the leapfrog
     float *bbox = nullptr;    // [8]: lo xyz, size, then scratch
+    // batches
+    int *inst = nullptr;       // [max_n] instance of each slot
+    int *bbox_inst = nullptr;  // [6 * kMaxInstances] per-instance boxes
+    int *dtmin_inst = nullptr; // [kMaxInstances] per-instance min h / vsigmax (ordered ints)
+    cudaGraphExec_t batch_graph = nullptr;
+    cudaStream_t capture_stream = nullptr;  // graphs are recorded here, launched on the caller's
+    std::vector<unsigned char> batch_graph_key;
 
     // scan scratch
     int *scan_part = nullptr;
@@ -119,24 +141,31 @@ struct Ctx {
 // ---------------------------------------------------------------------------
 // tree.cu
 cudaError_t build_tree(Ctx &c, const sph_state &s, const sph_params &p, bool full_permute,
-                       cudaStream_t st);
+                       cudaStream_t st, const Batch *batch = nullptr);
+cudaError_t instance_map(Ctx &c, const int64_t *d_offsets, int n_inst, int n, cudaStream_t st);
 cudaError_t update_hmax(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st);
 cudaError_t scan_exclusive_int(Ctx &c, const int *in, int *out, int n, int *total_dev,
                                cudaStream_t st);
 // density.cu
-cudaError_t density_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st);
+cudaError_t density_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st,
+                         const Batch *batch = nullptr);
 cudaError_t neighbour_lists(Ctx &c, const sph_state &s, const sph_params &p, int mode,
                             int64_t *d_off, int32_t *d_idx, int64_t cap, int64_t *h_total,
                             cudaStream_t st);
 // force.cu
 cudaError_t force_prep(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st);
-cudaError_t force_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st);
+cudaError_t force_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st,
+                       const Batch *batch = nullptr);
+cudaError_t configure_density_kernels();
+cudaError_t configure_force_kernels();
 // integrate.cu
-cudaError_t kick_drift(Ctx &c, const sph_state &s, const float *d_dt, cudaStream_t st);
+// with a batch, d_dt and d_time hold one value per instance
+cudaError_t kick_drift(Ctx &c, const sph_state &s, const float *d_dt, cudaStream_t st,
+                       const Batch *batch = nullptr);
 cudaError_t kick_close(Ctx &c, const sph_state &s, const float *d_dt, double *d_time,
-                       cudaStream_t st);
+                       cudaStream_t st, const Batch *batch = nullptr);
 cudaError_t courant_dt(Ctx &c, const sph_state &s, const sph_params &p, float *d_dt,
-                       cudaStream_t st);
+                       cudaStream_t st, const Batch *batch = nullptr);
 cudaError_t conserved(Ctx &c, const sph_state &s, double *d_out8, cudaStream_t st);
 
 // helpers

@@ -77,25 +77,83 @@ __global__ void bbox_kernel(const float4 *__restrict__ pos, const float *__restr
             mx[a] = max(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
         }
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) raise_error(err, SPH_ERR_NONFINITE);
+    // block-level combine first: one set of 6 atomics per block
+    __shared__ int sb[6][32];
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     if ((threadIdx.x & 31) == 0)
         for (int a = 0; a < 3; ++a) {
-            atomicMin(bb + a, mn[a]);
-            atomicMax(bb + 3 + a, mx[a]);
+            sb[a][w] = mn[a];
+            sb[3 + a][w] = mx[a];
         }
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        int k = threadIdx.x, v = sb[k][0];
+        for (int q = 1; q < nw; ++q) v = k < 3 ? min(v, sb[k][q]) : max(v, sb[k][q]);
+        if (k < 3) atomicMin(bb + k, v); else atomicMax(bb + k, v);
+    }
+}
+
+// batch: one box per instance (6 ordered ints each), warp-combined atomics
+__global__ void bbox_batch_init_kernel(int *bb, int n_inst)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < 6 * n_inst; k += gridDim.x * blockDim.x)
+        bb[k] = (k % 6) < 3 ? 0x7fffffff : (int)0x80000000;
+}
+
+__global__ void bbox_batch_kernel(const float4 *__restrict__ pos, const float *__restrict__ h,
+                                  const int *__restrict__ inst, int n, int *bb, int *err)
+{
+    for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += gridDim.x * blockDim.x) {
+        int i = i0 + threadIdx.x;
+        bool in = i < n;
+        float4 p = in ? pos[i] : make_float4(0, 0, 0, 0);
+        float hh = in ? h[i] : 1.f;
+        int k = in ? inst[i] : -1;
+        bool bad = in && !(isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && isfinite(p.w) &&
+                           isfinite(hh) && p.w > 0.f && hh > 0.f);
+        if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) raise_error(err, SPH_ERR_NONFINITE);
+        int o[3] = {ord_of(p.x), ord_of(p.y), ord_of(p.z)};
+        int k0 = __shfl_sync(0xffffffffu, k, 0);
+        if (__all_sync(0xffffffffu, k == k0)) {  // whole warp in one instance
+            int mn[3] = {o[0], o[1], o[2]}, mx[3] = {o[0], o[1], o[2]};
+            for (int s = 16; s > 0; s >>= 1)
+                for (int a = 0; a < 3; ++a) {
+                    mn[a] = min(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], s));
+                    mx[a] = max(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], s));
+                }
+            if ((threadIdx.x & 31) == 0 && k0 >= 0)
+                for (int a = 0; a < 3; ++a) {
+                    atomicMin(bb + 6 * k0 + a, mn[a]);
+                    atomicMax(bb + 6 * k0 + 3 + a, mx[a]);
+                }
+        } else if (in) {
+            for (int a = 0; a < 3; ++a) {
+                atomicMin(bb + 6 * k + a, o[a]);
+                atomicMax(bb + 6 * k + 3 + a, o[a]);
+            }
+        }
+    }
 }
 
 // canonical FP32 quantisation, see include/sph.h
-__global__ void morton_kernel(const float4 *__restrict__ pos, int n, const int *bb,
-                              uint64_t *__restrict__ keys, uint32_t *__restrict__ idx)
+__device__ __forceinline__ void box_scale(const int *bb, float lo[3], float &s)
 {
-    float lo[3], size = 0.f;
+    float size = 0.f;
     for (int a = 0; a < 3; ++a) {
         lo[a] = float_of(bb[a]);
         float e = __fsub_rn(float_of(bb[3 + a]), lo[a]);
         size = e > size ? e : size;
     }
-    float s = size > 0.f ? __fdiv_rn(2097152.0f, size) : 0.f;
+    s = size > 0.f ? __fdiv_rn(2097152.0f, size) : 0.f;
+}
+
+__global__ void morton_kernel(const float4 *__restrict__ pos, const int *__restrict__ inst, int n,
+                              const int *bb, uint64_t *__restrict__ keys, uint32_t *__restrict__ idx)
+{
+    float lo[3], s;
+    box_scale(bb, lo, s);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (inst) box_scale(bb + 6 * inst[i], lo, s);
         float4 p = pos[i];
         float x[3] = {p.x, p.y, p.z};
         uint32_t c[3];
@@ -116,7 +174,18 @@ __global__ void morton_kernel(const float4 *__restrict__ pos, int n, const int *
 // (warp match + per-warp counts), which keeps the sort stable.
 constexpr int RS_T = 256, RS_I = 8, RS_TILE = RS_T * RS_I;
 
-__global__ void __launch_bounds__(RS_T) rs_hist_kernel(const uint64_t *__restrict__ keys, int n,
+// digit of element s: 8 bits of its key, or (inst != nullptr) of its instance id
+__device__ __forceinline__ uint32_t rs_digit(const uint64_t *__restrict__ keys,
+                                             const uint32_t *__restrict__ vals,
+                                             const int *__restrict__ inst, int s, int shift)
+{
+    if (inst) return ((uint32_t)inst[vals[s]] >> shift) & 255u;
+    return (uint32_t)((keys[s] >> shift) & 255u);
+}
+
+__global__ void __launch_bounds__(RS_T) rs_hist_kernel(const uint64_t *__restrict__ keys,
+                                                       const uint32_t *__restrict__ vals,
+                                                       const int *__restrict__ inst, int n,
                                                        int shift, uint32_t *hist, int ntiles)
 {
     __shared__ uint32_t h[256];
@@ -126,7 +195,7 @@ __global__ void __launch_bounds__(RS_T) rs_hist_kernel(const uint64_t *__restric
 #pragma unroll
     for (int i = 0; i < RS_I; ++i) {
         int s = base + i * RS_T + threadIdx.x;
-        if (s < n) atomicAdd(&h[(keys[s] >> shift) & 255u], 1u);
+        if (s < n) atomicAdd(&h[rs_digit(keys, vals, inst, s, shift)], 1u);
     }
     __syncthreads();
     hist[threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
@@ -185,8 +254,8 @@ __global__ void __launch_bounds__(256) rs_digit_base_kernel(uint32_t *dtotal)
 
 __global__ void __launch_bounds__(RS_T) rs_scatter_kernel(
     const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
-    uint32_t *__restrict__ vout, int n, int shift, const uint32_t *__restrict__ hist,
-    const uint32_t *__restrict__ dbase, int ntiles)
+    uint32_t *__restrict__ vout, const int *__restrict__ inst, int n, int shift,
+    const uint32_t *__restrict__ hist, const uint32_t *__restrict__ dbase, int ntiles)
 {
     __shared__ uint32_t base[256];
     __shared__ uint32_t run[256];
@@ -205,7 +274,9 @@ __global__ void __launch_bounds__(RS_T) rs_scatter_kernel(
         bool valid = s < n;
         uint64_t key = valid ? kin[s] : 0;
         uint32_t val = valid ? vin[s] : 0;
-        uint32_t d = valid ? (uint32_t)((key >> shift) & 255u) : 256u + lane;
+        uint32_t d = valid ? (inst ? ((uint32_t)inst[val] >> shift) & 255u
+                                   : (uint32_t)((key >> shift) & 255u))
+                           : 256u + lane;
         uint32_t peers = __match_any_sync(0xffffffffu, d);
         uint32_t rank = __popc(peers & lt);
         if (valid && rank == 0) wcnt[w][d] = __popc(peers);
@@ -327,36 +398,46 @@ cudaError_t scan_exclusive_int(Ctx &c, const int *in, int *out, int n, int *tota
 }
 
 // -------------------------------------------------------------------- chop
+// Shared leading digits of the keys of slots a and b; -1 when the slots
+// belong to different instances of a batch (inst != nullptr): instances never
+// share a node, each has its own root at level 0.
+__device__ __forceinline__ int cd_slots(const uint64_t *__restrict__ keys,
+                                        const int *__restrict__ inst, int a, int b)
+{
+    if (inst && inst[a] != inst[b]) return -1;
+    return common_digits(keys[a], keys[b]);
+}
+
 // lv[s] = d | (Lmax << 8) if nodes start at s, else -1 (for threshold T)
-__device__ __forceinline__ int chop_levels(const uint64_t *__restrict__ keys, int n, int s, int T)
+__device__ __forceinline__ int chop_levels(const uint64_t *__restrict__ keys,
+                                           const int *__restrict__ inst, int n, int s, int T)
 {
     int d;
-    uint64_t ks = keys[s];
-    if (s == 0) {
-        d = 0;
+    if (s == 0 || (inst && inst[s] != inst[s - 1])) {
+        d = 0;  // root of the (instance's) tree
     } else {
-        int c = common_digits(ks, keys[s - 1]);
+        int c = cd_slots(keys, inst, s, s - 1);
         if (c == kMaxLevel) return -1;  // same key as the previous particle
         d = c + 1;
         int l = d - 1;
         int lo = max(0, s - T), hi = s;
         while (lo < hi) {
             int mid = (lo + hi) >> 1;
-            if (common_digits(keys[mid], ks) >= l) hi = mid; else lo = mid + 1;
+            if (cd_slots(keys, inst, mid, s) >= l) hi = mid; else lo = mid + 1;
         }
-        if (!(lo + T <= n - 1 && common_digits(keys[lo + T], ks) >= l)) return -1;
+        if (!(lo + T <= n - 1 && cd_slots(keys, inst, lo + T, s) >= l)) return -1;
     }
-    int c2 = (s + T <= n - 1) ? common_digits(ks, keys[s + T]) : -1;
+    int c2 = (s + T <= n - 1) ? cd_slots(keys, inst, s, s + T) : -1;
     int lmax = max(d, min(c2 + 1, kMaxLevel));
     return d | (lmax << 8);
 }
 
-__global__ void chop_flags_kernel(const uint64_t *__restrict__ keys, int n, int t_leaf,
-                                  int t_group, int *lv_tree, int *lv_grp)
+__global__ void chop_flags_kernel(const uint64_t *__restrict__ keys, const int *__restrict__ inst,
+                                  int n, int t_leaf, int t_group, int *lv_tree, int *lv_grp)
 {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-        lv_tree[s] = chop_levels(keys, n, s, t_leaf);
-        lv_grp[s] = chop_levels(keys, n, s, t_group);
+        lv_tree[s] = chop_levels(keys, inst, n, s, t_leaf);
+        lv_grp[s] = chop_levels(keys, inst, n, s, t_group);
     }
 }
 
@@ -437,32 +518,33 @@ __global__ void level_start_kernel(const int *blk_off, int nb, const int *total,
 }
 
 // end of the run at level L that starts at s (galloping search)
-__device__ int run_end(const uint64_t *__restrict__ keys, int n, int s, int L)
+__device__ int run_end(const uint64_t *__restrict__ keys, const int *__restrict__ inst,
+                       const int64_t *__restrict__ offs, int n, int s, int L)
 {
-    if (L == 0) return n;
-    uint64_t ks = keys[s];
-    int step = 1, lo = s;  // keys[lo] in run
-    while (s + step < n && common_digits(keys[s + step], ks) >= L) {
+    if (L == 0) return inst ? (int)offs[inst[s] + 1] : n;
+    int step = 1, lo = s;  // slot lo is in the run
+    while (s + step < n && cd_slots(keys, inst, s + step, s) >= L) {
         lo = s + step;
         step <<= 1;
     }
-    int hi = min(s + step, n);  // keys[hi] not in run (or hi == n)
+    int hi = min(s + step, n);  // slot hi is not in the run (or hi == n)
     while (hi - lo > 1) {
         int mid = (lo + hi) >> 1;
-        if (common_digits(keys[mid], ks) >= L) lo = mid; else hi = mid;
+        if (cd_slots(keys, inst, mid, s) >= L) lo = mid; else hi = mid;
     }
     return hi;
 }
 
-__global__ void node_finish_kernel(const uint64_t *__restrict__ keys, int n, int T, Tree t,
+__global__ void node_finish_kernel(const uint64_t *__restrict__ keys, const int *__restrict__ inst,
+                                   const int64_t *__restrict__ offs, int n, int T, Tree t,
                                    const int *sizes)
 {
     int nn = sizes[SZ_NODES];
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nn; k += gridDim.x * blockDim.x) {
         int L = t.node_level[k], s = t.node_first[k];
-        int cnt = run_end(keys, n, s, L) - s;
+        int cnt = run_end(keys, inst, offs, n, s, L) - s;
         t.node_count[k] = cnt;
-        if (k == 0) t.node_parent[0] = -1;
+        if (L == 0) t.node_parent[k] = -1;
         int cf = -1, nc = 0;
         if (cnt > T && L < kMaxLevel) {
             int lo = t.level_start[L + 1], hi = min(t.level_start[L + 2], nn);
@@ -485,7 +567,7 @@ __global__ void node_finish_kernel(const uint64_t *__restrict__ keys, int n, int
 
 // Bottom-up bounds: leaves from particles, parents from children; the last
 // child to finish (arrival counter) computes its parent.  what = 0: AABB of
-// positions; what = 1: h_max.
+// positions and h_max; what = 1: h_max only.
 __global__ void node_bounds_kernel(const float4 *__restrict__ pos, const float *__restrict__ h,
                                    Tree t, const int *sizes, int what)
 {
@@ -496,12 +578,14 @@ __global__ void node_bounds_kernel(const float4 *__restrict__ pos, const float *
         if (what == 0) {
             float3 lo = make_float3(INFINITY, INFINITY, INFINITY);
             float3 hi = make_float3(-INFINITY, -INFINITY, -INFINITY);
+            float hm = 0.f;
             for (int i = s; i < e; ++i) {
                 float4 p = pos[i];
                 lo.x = fminf(lo.x, p.x); lo.y = fminf(lo.y, p.y); lo.z = fminf(lo.z, p.z);
                 hi.x = fmaxf(hi.x, p.x); hi.y = fmaxf(hi.y, p.y); hi.z = fmaxf(hi.z, p.z);
+                hm = fmaxf(hm, h[i]);
             }
-            t.node_lo[k] = make_float4(lo.x, lo.y, lo.z, 0.f);
+            t.node_lo[k] = make_float4(lo.x, lo.y, lo.z, hm);
             t.node_hi[k] = make_float4(hi.x, hi.y, hi.z, 0.f);
         } else {
             float hm = 0.f;
@@ -520,12 +604,14 @@ __global__ void node_bounds_kernel(const float4 *__restrict__ pos, const float *
             if (what == 0) {
                 float3 lo = make_float3(INFINITY, INFINITY, INFINITY);
                 float3 hi = make_float3(-INFINITY, -INFINITY, -INFINITY);
+                float hm = 0.f;
                 for (int q = cf; q < cf + nc; ++q) {
                     float4 a = __ldcg(&t.node_lo[q]), b = __ldcg(&t.node_hi[q]);
                     lo.x = fminf(lo.x, a.x); lo.y = fminf(lo.y, a.y); lo.z = fminf(lo.z, a.z);
                     hi.x = fmaxf(hi.x, b.x); hi.y = fmaxf(hi.y, b.y); hi.z = fmaxf(hi.z, b.z);
+                    hm = fmaxf(hm, a.w);
                 }
-                __stcg(&t.node_lo[p], make_float4(lo.x, lo.y, lo.z, 0.f));
+                __stcg(&t.node_lo[p], make_float4(lo.x, lo.y, lo.z, hm));
                 __stcg(&t.node_hi[p], make_float4(hi.x, hi.y, hi.z, 0.f));
             } else {
                 float hm = 0.f;
@@ -573,7 +659,18 @@ __global__ void group_bounds_kernel(const float4 *__restrict__ pos, const float 
     }
 }
 
-__global__ void copy_int_kernel(const int *src, int *dst) { *dst = *src; }
+// inst[k] = instance owning slot k (offsets ascending, every instance non-empty)
+__global__ void instance_map_kernel(const int64_t *__restrict__ offs, int n_inst, int n, int *inst)
+{
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        int lo = 0, hi = n_inst - 1;  // largest i with offs[i] <= k
+        while (lo < hi) {
+            int mid = (lo + hi + 1) >> 1;
+            if (offs[mid] <= k) lo = mid; else hi = mid - 1;
+        }
+        inst[k] = lo;
+    }
+}
 
 // ------------------------------------------------------------- host driver
 static int grid_for(const Ctx &c, int64_t n, int block)
@@ -590,33 +687,49 @@ static int grid_for(const Ctx &c, int64_t n, int block)
         if (e_ != cudaSuccess) return e_;           \
     } while (0)
 
+cudaError_t instance_map(Ctx &c, const int64_t *d_offsets, int n_inst, int n, cudaStream_t st)
+{
+    instance_map_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(d_offsets, n_inst, n, c.inst);
+    return cudaGetLastError();
+}
+
 cudaError_t build_tree(Ctx &c, const sph_state &s, const sph_params &p, bool full_permute,
-                       cudaStream_t st)
+                       cudaStream_t st, const Batch *batch)
 {
     const int n = (int)s.n;
     Tree &t = c.tree;
     float4 *pos = (float4 *)s.pos;
-    int *bb = (int *)c.bbox;
-    // 1. bounding box and input checks
-    bbox_init_kernel<<<1, 32, 0, st>>>(bb);
-    bbox_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(pos, s.h, n, bb, c.d_err);
+    const int *inst = batch ? c.inst : nullptr;
+    const int64_t *offs = batch ? batch->offsets : nullptr;
+    int *bb = batch ? c.bbox_inst : (int *)c.bbox;
+    // 1. bounding box (per instance in a batch) and input checks
+    if (batch) {
+        bbox_batch_init_kernel<<<div_up(6 * batch->n_inst, 256), 256, 0, st>>>(bb, batch->n_inst);
+        bbox_batch_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(pos, s.h, inst, n, bb, c.d_err);
+    } else {
+        bbox_init_kernel<<<1, 32, 0, st>>>(bb);
+        bbox_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(pos, s.h, n, bb, c.d_err);
+    }
     // 2. keys
-    morton_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(pos, n, bb, s.keys, c.idx_a);
-    // 3. radix sort (key, slot)
+    morton_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(pos, inst, n, bb, s.keys, c.idx_a);
+    // 3. radix sort (key, slot); a batch adds stable passes on the instance id,
+    //    which puts every instance back on its own slots
     int ntiles = div_up(n, RS_TILE);
     uint64_t *kin = s.keys, *kout = c.keys_alt;
     uint32_t *vin = c.idx_a, *vout = c.idx_b;
-    for (int pass = 0; pass < 8; ++pass) {
-        int shift = 8 * pass;
-        rs_hist_kernel<<<ntiles, RS_T, 0, st>>>(kin, n, shift, c.hist, ntiles);
+    const int npass = batch ? 10 : 8;
+    for (int pass = 0; pass < npass; ++pass) {
+        const int *dinst = pass >= 8 ? inst : nullptr;
+        int shift = pass >= 8 ? 8 * (pass - 8) : 8 * pass;
+        rs_hist_kernel<<<ntiles, RS_T, 0, st>>>(kin, vin, dinst, n, shift, c.hist, ntiles);
         rs_scan_rows_kernel<<<256, 256, 0, st>>>(c.hist, ntiles, c.dtotal);
         rs_digit_base_kernel<<<1, 256, 0, st>>>(c.dtotal);
-        rs_scatter_kernel<<<ntiles, RS_T, 0, st>>>(kin, vin, kout, vout, n, shift, c.hist, c.dtotal,
-                                                   ntiles);
+        rs_scatter_kernel<<<ntiles, RS_T, 0, st>>>(kin, vin, kout, vout, dinst, n, shift, c.hist,
+                                                   c.dtotal, ntiles);
         std::swap(kin, kout);
         std::swap(vin, vout);
     }
-    // after 8 passes the sorted (key, slot) pairs are back in (s.keys, idx_a)
+    // after an even number of passes the sorted (key, slot) pairs are in (s.keys, idx_a)
     // 4. permute the state into curve order
     GatherArgs g{};
     g.order = c.idx_a;
@@ -642,8 +755,10 @@ cudaError_t build_tree(Ctx &c, const sph_state &s, const sph_params &p, bool ful
     for (int a = 0; a < n1; ++a)
         SPH_TRY(cudaMemcpyAsync(arr1[a], c.tmp1[a], (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
     SPH_TRY(cudaMemcpyAsync(s.perm, c.tmp_perm, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
+    // recorded leaf ranges refer to the previous tree: mark them invalid
+    SPH_TRY(cudaMemsetAsync(t.rec_ctl + 1, 0xff, sizeof(int), st));
     // 5. chop: tree (n_leaf) and groups (n_group)
-    chop_flags_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(s.keys, n, p.n_leaf, p.n_group,
+    chop_flags_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(s.keys, inst, n, p.n_leaf, p.n_group,
                                                             t.lv_tree, t.lv_grp);
     // groups
     int *gidx = (int *)c.tmp1[1];  // scratch: tmp1[1..] are free once copied back
@@ -658,8 +773,8 @@ cudaError_t build_tree(Ctx &c, const sph_state &s, const sph_params &p, bool ful
     SPH_TRY(scan_mode(c, t.blk_cnt, blk_off, kLevels * nb, 0, ntotal, st));
     chop_write_kernel<<<nb, 256, 0, st>>>(t.lv_tree, n, blk_off, nb, t, c.d_err);
     level_start_kernel<<<1, 32, 0, st>>>(blk_off, nb, ntotal, t, c.d_sizes);
-    node_finish_kernel<<<grid_for(c, t.cap_nodes, 256), 256, 0, st>>>(s.keys, n, p.n_leaf, t,
-                                                                       c.d_sizes);
+    node_finish_kernel<<<grid_for(c, t.cap_nodes, 256), 256, 0, st>>>(s.keys, inst, offs, n,
+                                                                       p.n_leaf, t, c.d_sizes);
     node_bounds_kernel<<<grid_for(c, t.cap_nodes, 128), 128, 0, st>>>(pos, s.h, t, c.d_sizes, 0);
     return cudaGetLastError();
 }

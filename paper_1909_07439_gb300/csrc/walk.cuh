@@ -46,6 +46,31 @@ __device__ __forceinline__ float canon_r2(float xi, float yi, float zi, float xj
     return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
 }
 
+// The same canonical squared distance for two targets at once with the
+// packed FP32x2 instructions: every element is rounded to nearest exactly as
+// in canon_r2 (x - y is formed as x + (-y), which is the same operation).
+__device__ __forceinline__ float2 canon_r2_x2(float2 tx, float2 ty, float2 tz, float xj, float yj,
+                                              float zj)
+{
+    const float2 dx = __fadd2_rn(tx, make_float2(-xj, -xj));
+    const float2 dy = __fadd2_rn(ty, make_float2(-yj, -yj));
+    const float2 dz = __fadd2_rn(tz, make_float2(-zj, -zj));
+    return __fadd2_rn(__fadd2_rn(__fmul2_rn(dx, dx), __fmul2_rn(dy, dy)), __fmul2_rn(dz, dz));
+}
+
+// Targets of a warp's batch as coordinate pairs for canon_r2_x2: element t of
+// the batch is component (t & 1) of pair t >> 1; unused slots sit far away.
+template <int TB>
+struct TargetPairs {
+    float2 x[TB / 2], y[TB / 2], z[TB / 2];
+    __device__ __forceinline__ void set(int t, float4 p)
+    {
+        reinterpret_cast<float *>(x)[t] = p.x;
+        reinterpret_cast<float *>(y)[t] = p.y;
+        reinterpret_cast<float *>(z)[t] = p.z;
+    }
+};
+
 // squared distance between two axis-aligned boxes (0 if they overlap)
 __device__ __forceinline__ float box_dist2(float4 alo, float4 ahi, float4 blo, float4 bhi)
 {
@@ -55,20 +80,25 @@ __device__ __forceinline__ float box_dist2(float4 alo, float4 ahi, float4 blo, f
     return dx * dx + dy * dy + dz * dz;
 }
 
-// Walk the tree for a group with box [glo, ghi].
+// Walk the tree below node `root` for a group with box [glo, ghi].
 //   force_mode = false: open a node if dist < reach (reach = 2 * padded h of the group)
 //   force_mode = true : open a node if dist < 2 max(h_group, h_max(node))
 // chunk(j): called warp-uniformly with this lane's candidate j (-1: none).
 // Returns false if the stack overflowed (results then incomplete).
+// Opened leaves are appended, in order, to rec[0 .. *rec_n) when rec is
+// given (*rec_n = -1 once more than rec_cap were opened).  In force mode a
+// node's h_max is scaled by node_scale.
 template <class ChunkFn>
-__device__ bool walk_group(const WalkTree &T, float4 glo, float4 ghi, float reach, bool force_mode,
-                           float hgroup, WalkSmem &sm, ChunkFn &&chunk)
+__device__ bool walk_group(const WalkTree &T, int root, float4 glo, float4 ghi, float reach,
+                           bool force_mode, float hgroup, WalkSmem &sm, ChunkFn &&chunk,
+                           float node_scale = 1.f, int2 *rec = nullptr, int *rec_n = nullptr,
+                           int rec_cap = 0)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = lane_lt();
     bool ok = true;
     int sp = 1;
-    if (lane == 0) sm.stk[0] = make_int2(0, 1);  // root
+    if (lane == 0) sm.stk[0] = make_int2(root, 1);  // the group's (instance) root
     int rq_head = 0, rq_tail = 0, rq_off = 0, pending = 0;
     const float reach2 = reach * reach * kOpenSlack;
     __syncwarp();
@@ -100,7 +130,7 @@ __device__ bool walk_group(const WalkTree &T, float4 glo, float4 ghi, float reac
                 float d2 = box_dist2(glo, ghi, lo, hi);
                 float r2 = reach2;
                 if (force_mode) {
-                    float R = 2.0f * fmaxf(hgroup, lo.w);
+                    float R = 2.0f * fmaxf(hgroup, lo.w * node_scale);
                     r2 = R * R * kOpenSlack;
                 }
                 open = d2 < r2;
@@ -118,6 +148,20 @@ __device__ bool walk_group(const WalkTree &T, float4 glo, float4 ghi, float reac
             }
             unsigned bleaf = __ballot_sync(0xffffffffu, open && leaf);
             if (open && leaf) sm.rq[(rq_tail + __popc(bleaf & lt)) % kRQ] = ref;
+            if (rec) {
+                int nr = *rec_n;
+                if (nr >= 0) {
+                    if (nr + __popc(bleaf) > rec_cap) {
+                        nr = -1;
+                    } else {
+                        if (open && leaf) rec[nr + __popc(bleaf & lt)] = ref;
+                        nr += __popc(bleaf);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) *rec_n = nr;
+                __syncwarp();
+            }
             rq_tail += __popc(bleaf);
             pending += warp_sum_i(open && leaf ? ref.y : 0);
             __syncwarp();
@@ -148,6 +192,37 @@ __device__ bool walk_group(const WalkTree &T, float4 glo, float4 ghi, float reac
     }
     __syncwarp();
     return ok;
+}
+
+// Hand the particles of recorded leaf ranges (global, in walk order) to
+// chunk() in 32-particle chunks, as walk_group would.
+template <class ChunkFn>
+__device__ void replay_ranges(const int2 *__restrict__ ranges, int count, ChunkFn &&chunk)
+{
+    const int lane = threadIdx.x & 31;
+    int filled = 0, myj = -1;
+    for (int b = 0; b < count; b += 32) {
+        const int2 mine = b + lane < count ? __ldg(&ranges[b + lane]) : make_int2(0, 0);
+        const int nb = min(32, count - b);
+        for (int k = 0; k < nb; ++k) {
+            const int first = __shfl_sync(0xffffffffu, mine.x, k);
+            const int cnt = __shfl_sync(0xffffffffu, mine.y, k);
+            int off = 0;
+            while (off < cnt) {
+                const int take = min(cnt - off, 32 - filled);
+                if (lane >= filled && lane < filled + take) myj = first + off + (lane - filled);
+                filled += take;
+                off += take;
+                if (filled == 32) {
+                    chunk(myj);
+                    filled = 0;
+                    myj = -1;
+                }
+            }
+        }
+    }
+    if (filled > 0) chunk(myj);
+    __syncwarp();
 }
 
 }  // namespace sph

@@ -55,7 +55,8 @@ class sph_stats(ctypes.Structure):
 
 _lib = None
 EXPORTS = ("sph_params_default", "sph_create", "sph_destroy", "sph_build_tree", "sph_density",
-           "sph_force", "sph_timestep", "sph_step", "sph_step_host", "sph_conserved",
+           "sph_force", "sph_timestep", "sph_step", "sph_step_host", "sph_batch_evaluate",
+           "sph_batch_step", "sph_force_bwd", "sph_density_bwd", "sph_rollout", "sph_conserved",
            "sph_conserved_noalloc",
            "sph_neighbours", "sph_get_tree", "sph_get_stats", "sph_set_timing", "sph_get_timing", "sph_sync",
            "sph_last_error")
@@ -82,6 +83,14 @@ def load():
     lib.sph_step.argtypes = [P, POINTER(sph_state), POINTER(sph_params), P, P, P]
     lib.sph_step_host.argtypes = [P, POINTER(sph_state), POINTER(sph_params), c_int,
                                   POINTER(c_float), P]
+    lib.sph_batch_evaluate.argtypes = [P, POINTER(sph_state), P, c_int, POINTER(sph_params), P, P]
+    lib.sph_batch_step.argtypes = [P, POINTER(sph_state), P, c_int, c_int, POINTER(sph_params), P,
+                                   P, P]
+    lib.sph_force_bwd.argtypes = [P, POINTER(sph_state), POINTER(sph_params), P, P, P, P, P, P, P,
+                                  P]
+    lib.sph_density_bwd.argtypes = [P, POINTER(sph_state), POINTER(sph_params), P, P, P, P, P]
+    lib.sph_rollout.argtypes = [P, POINTER(sph_state), POINTER(sph_params), c_int, c_int, P, c_int,
+                                POINTER(c_double), P, POINTER(c_double), P]
     lib.sph_conserved.argtypes = [P, POINTER(sph_state), P, P]
     lib.sph_conserved_noalloc.argtypes = [c_int64, P, P, P, P]
     lib.sph_neighbours.argtypes = [P, POINTER(sph_state), POINTER(sph_params), c_int, P, P,
@@ -175,6 +184,44 @@ def sph_step(ctx, state, params, d_dt, d_time=None, stream=None):
 def sph_step_host(ctx, host_state, params, n_steps, h_dt: c_float, stream=None):
     return _check(ctx, load().sph_step_host(ctx, ctypes.byref(host_state), ctypes.byref(params),
                                             int(n_steps), ctypes.byref(h_dt), _stream(stream)))
+
+
+def sph_batch_evaluate(ctx, state, d_offsets, n_inst, params, d_dt, stream=None):
+    return _check(ctx, load().sph_batch_evaluate(ctx, ctypes.byref(state), _ptr(d_offsets),
+                                                 int(n_inst), ctypes.byref(params), _ptr(d_dt),
+                                                 _stream(stream)))
+
+
+def sph_batch_step(ctx, state, d_offsets, n_inst, n_steps, params, d_dt, d_time=None, stream=None):
+    return _check(ctx, load().sph_batch_step(ctx, ctypes.byref(state), _ptr(d_offsets), int(n_inst),
+                                             int(n_steps), ctypes.byref(params), _ptr(d_dt),
+                                             _ptr(d_time), _stream(stream)))
+
+
+def sph_force_bwd(ctx, state, params, gacc, gpos, gvel, gh, grho, gomega, galpha, stream=None):
+    return _check(ctx, load().sph_force_bwd(ctx, ctypes.byref(state), ctypes.byref(params),
+                                            _ptr(gacc), _ptr(gpos), _ptr(gvel), _ptr(gh),
+                                            _ptr(grho), _ptr(gomega), _ptr(galpha),
+                                            _stream(stream)))
+
+
+def sph_density_bwd(ctx, state, params, gh, grho, gomega, gpos, stream=None):
+    return _check(ctx, load().sph_density_bwd(ctx, ctypes.byref(state), ctypes.byref(params),
+                                              _ptr(gh), _ptr(grho), _ptr(gomega), _ptr(gpos),
+                                              _stream(stream)))
+
+
+def sph_rollout(ctx, init_state, params, n_steps, ckpt, d_probes, n_probes, d_gvel=None,
+                stream=None):
+    """Returns (loss, dL/dalpha or None); fills d_gvel with dL/d(v0, u0) if given."""
+    loss = c_double(0.0)
+    ga = c_double(0.0)
+    _check(ctx, load().sph_rollout(ctx, ctypes.byref(init_state), ctypes.byref(params),
+                                   int(n_steps), int(ckpt), _ptr(d_probes), int(n_probes),
+                                   ctypes.byref(loss), _ptr(d_gvel),
+                                   ctypes.byref(ga) if d_gvel is not None else None,
+                                   _stream(stream)))
+    return loss.value, (ga.value if d_gvel is not None else None)
 
 
 def sph_conserved(ctx, state, d_out8, stream=None):

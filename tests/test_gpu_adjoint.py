@@ -1,0 +1,169 @@
+"""Adjoint kernels and the differentiable rollout vs FP64 torch autograd.
+
+The reference (oracle/adjoint_ref.py) is pinned to the C oracle's forward and
+to finite differences (tests/test_oracle_adjoint.py).  Bar: gradients within
+1e-3 relative (in norm over particles) of the reference."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1909_07439_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+from oracle import adjoint_ref as R  # noqa: E402
+
+T = torch.float64
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1909_07439_gb300 import build, native
+    build.build()
+    native.load()
+    ctx = native.sph_create(1 << 16, 0)
+    yield native, ctx
+    native.sph_destroy(ctx)
+
+
+def _cloud(n=1500, seed=3):
+    w = inputs.unit_sphere(n, seed=seed, sigma_v=0.3)
+    rng = np.random.default_rng(seed)
+    w.vel[:, 3] *= rng.uniform(0.5, 2.0, n).astype(np.float32)
+    return w
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def test_force_bwd_matches_autograd(lib):
+    native, ctx = lib
+    from paper_1909_07439_gb300 import DeviceState
+    w = _cloud()
+    x, v, m, u = (w.pos[:, :3].astype(np.float64), w.vel[:, :3].astype(np.float64),
+                  w.pos[:, 3].astype(np.float64), w.vel[:, 3].astype(np.float64))
+    d = oracle.density(x, v, m, w.h)
+    # both sides use the oracle's h, rho, Omega (rounded to float32) as inputs
+    h32, r32, o32 = (d.h.astype(np.float32), d.rho.astype(np.float32), d.omega.astype(np.float32))
+    s = DeviceState.from_arrays(w.pos, w.vel, h32)
+    p = native.sph_params_default()
+    native.sph_build_tree(ctx, s.c, p)
+    perm = s.numpy("perm").astype(np.int64)
+    s.rho[: s.n] = torch.as_tensor(r32[perm], device="cuda")
+    s.omega[: s.n] = torch.as_tensor(o32[perm], device="cuda")
+    native.sph_force(ctx, s.c, p)
+    wgt = np.random.default_rng(1).normal(size=(w.n, 4)).astype(np.float32)
+    gacc = torch.as_tensor(wgt[perm], device="cuda")
+    z4 = lambda: torch.zeros((w.n, 4), dtype=torch.float32, device="cuda")
+    z1 = lambda: torch.zeros(w.n, dtype=torch.float32, device="cuda")
+    gpos, gvel, gh, grho, gom = z4(), z4(), z1(), z1(), z1()
+    gal = torch.zeros(1, dtype=torch.float64, device="cuda")
+    native.sph_force_bwd(ctx, s.c, p, gacc, gpos, gvel, gh, grho, gom, gal)
+    native.sph_sync(ctx)
+
+    def orig(t):
+        a = t.cpu().numpy()
+        out = np.empty_like(a)
+        out[perm] = a
+        return out
+
+    tx = torch.tensor(w.pos[:, :3], dtype=T, requires_grad=True)
+    tv = torch.tensor(w.vel[:, :3], dtype=T, requires_grad=True)
+    tu = torch.tensor(w.vel[:, 3], dtype=T, requires_grad=True)
+    th = torch.tensor(h32, dtype=T, requires_grad=True)
+    tr = torch.tensor(r32, dtype=T, requires_grad=True)
+    to = torch.tensor(o32, dtype=T, requires_grad=True)
+    ta = torch.tensor(1.0, dtype=T, requires_grad=True)
+    tm = torch.tensor(w.pos[:, 3], dtype=T)
+    i, j = R.pair_list(tx.detach(), th.detach(), 1.0001)
+    acc, du = R.force(tx, tv, tu, tm, th, tr, to, i, j, alpha=ta)
+    L = (torch.tensor(wgt[:, :3], dtype=T) * acc).sum() + (torch.tensor(wgt[:, 3], dtype=T) * du).sum()
+    L.backward()
+    assert _rel(orig(gpos)[:, :3], tx.grad.numpy()) < 1e-3
+    assert _rel(orig(gvel)[:, :3], tv.grad.numpy()) < 1e-3
+    assert _rel(orig(gvel)[:, 3], tu.grad.numpy()) < 1e-3
+    assert _rel(orig(gh), th.grad.numpy()) < 1e-3
+    assert _rel(orig(grho), tr.grad.numpy()) < 1e-3
+    assert _rel(orig(gom), to.grad.numpy()) < 1e-3
+    assert abs(gal.item() - float(ta.grad)) <= 1e-3 * abs(float(ta.grad))
+
+
+def test_density_bwd_matches_autograd(lib):
+    native, ctx = lib
+    from paper_1909_07439_gb300 import DeviceState
+    w = _cloud(1200, seed=8)
+    s = DeviceState.from_arrays(w.pos, w.vel, w.h)
+    p = native.sph_params_default()
+    native.sph_build_tree(ctx, s.c, p)
+    native.sph_density(ctx, s.c, p)
+    perm = s.numpy("perm").astype(np.int64)
+    rng = np.random.default_rng(4)
+    cg = rng.normal(size=(3, w.n)).astype(np.float32)
+    gh = torch.as_tensor(cg[0][perm], device="cuda")
+    gr = torch.as_tensor(cg[1][perm], device="cuda")
+    go = torch.as_tensor(cg[2][perm], device="cuda")
+    gpos = torch.zeros((w.n, 4), dtype=torch.float32, device="cuda")
+    native.sph_density_bwd(ctx, s.c, p, gh, gr, go, gpos)
+    native.sph_sync(ctx)
+    got = np.empty((w.n, 4), np.float32)
+    got[perm] = gpos.cpu().numpy()
+    tx = torch.tensor(w.pos[:, :3], dtype=T, requires_grad=True)
+    tm = torch.tensor(w.pos[:, 3], dtype=T)
+    h0 = torch.tensor(w.h, dtype=T)
+    i, j = R.pair_list(tx.detach(), h0, 2.6)
+    h, rho, om = R.density(tx, tm, h0, i, j, iters=40)
+    L = (torch.tensor(cg[0], dtype=T) * h + torch.tensor(cg[1], dtype=T) * rho +
+         torch.tensor(cg[2], dtype=T) * om).sum()
+    L.backward()
+    assert _rel(got[:, :3], tx.grad.numpy()) < 1e-3
+
+
+def _sedov16():
+    w = inputs.sedov_lattice(16, seed=6)
+    return w, inputs.probe_indices(w.n, 256, seed=7)
+
+
+def test_rollout_gradient_matches_fp64_reference(lib):
+    native, ctx = lib
+    from paper_1909_07439_gb300 import DeviceState
+    w, probes = _sedov16()
+    s = DeviceState.from_arrays(w.pos, w.vel, w.h)
+    p = native.sph_params_default()
+    d_probes = torch.as_tensor(probes, device="cuda")
+    gvel = torch.zeros((w.n, 4), dtype=torch.float32, device="cuda")
+    loss, galpha = native.sph_rollout(ctx, s.c, p, 20, 5, d_probes, len(probes), gvel)
+    g = gvel.cpu().numpy()
+    x = torch.tensor(w.pos[:, :3], dtype=T)
+    v = torch.tensor(w.vel[:, :3], dtype=T, requires_grad=True)
+    u = torch.tensor(w.vel[:, 3], dtype=T, requires_grad=True)
+    m = torch.tensor(w.pos[:, 3], dtype=T)
+    al = torch.tensor(1.0, dtype=T, requires_grad=True)
+    Lr, dts, _ = R.rollout(x, v, u, m, torch.tensor(w.h, dtype=T), al, 20, torch.tensor(probes))
+    Lr.backward()
+    assert abs(loss / float(Lr) - 1) < 1e-4
+    assert _rel(g[:, :3], v.grad.numpy()) < 1e-3
+    assert _rel(g[:, 3], u.grad.numpy()) < 1e-3
+    assert abs(galpha / float(al.grad) - 1) < 1e-3
+
+
+def test_autograd_function_and_no_grad_path(lib):
+    native, ctx = lib
+    from paper_1909_07439_gb300 import DeviceState
+    from paper_1909_07439_gb300.adjoint import rollout_loss
+    w, probes = _sedov16()
+    s = DeviceState.from_arrays(w.pos, w.vel, w.h)
+    p = native.sph_params_default()
+    d_probes = torch.as_tensor(probes, device="cuda")
+    velu = s.vel[: s.n].clone().requires_grad_(True)
+    al = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    L = rollout_loss(ctx, s.pos[: s.n], velu, s.h[: s.n], al, p, 6, 3, d_probes)
+    L.backward()
+    g = torch.zeros((w.n, 4), dtype=torch.float32, device="cuda")
+    loss2, ga2 = native.sph_rollout(ctx, s.c, p, 6, 3, d_probes, len(probes), g)
+    assert float(L) == loss2
+    assert torch.equal(velu.grad, g)
+    # dL/dalpha is an FP64 sum accumulated with atomics: equal up to summation order
+    assert abs(float(al.grad) - ga2) <= 1e-12 * abs(ga2)
+    loss3, _ = native.sph_rollout(ctx, s.c, p, 6, 3, d_probes, len(probes))   # loss only
+    assert loss3 == loss2
