@@ -40,6 +40,11 @@ SIDE = 128
 #  pressure work 3, conduction 11, P_j 2 (viscous branch not counted)   = 65
 FLOP_DENSITY_PAIR = 24
 FLOP_FORCE_PAIR = 65
+# DRAM bytes (read + write) per launch of the pair kernels from one ncu capture
+# of this workload (profiles/density_force_kernels_sedov128_ncu.md); to be
+# re-measured whenever those kernels change.
+NCU_TRAFFIC = {"density_kernel": 105.985536e6 + 68.234496e6,
+               "force_kernel": 149.596928e6 + 30.545664e6}
 
 
 def peaks():
@@ -95,6 +100,24 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": float(max(mx)) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def shard_instances(sizes, world_size):
+    """Split independent instances over ranks, balancing particle counts
+    (largest first onto the least-loaded rank); deterministic."""
+    load = [0] * world_size
+    parts = [[] for _ in range(world_size)]
+    for k in sorted(range(len(sizes)), key=lambda k: (-int(sizes[k]), k)):
+        r = min(range(world_size), key=lambda q: (load[q], q))
+        parts[r].append(k)
+        load[r] += int(sizes[k])
+    return [sorted(p) for p in parts]
+
+
+def aggregate(local_ms, units, world_size, all_reduce_max=None):
+    """Whole-job rate: units processed by all ranks over the slowest rank's time."""
+    ms = all_reduce_max(local_ms) if (all_reduce_max and world_size > 1) else local_ms
+    return units * world_size / (ms / 1e3), ms
 
 
 def dist_env():
@@ -165,11 +188,12 @@ def run_ours(args):
     stage_ms, launches = native.sph_get_timing(ctx)
     native.sph_set_timing(ctx, False)
     stats = native.sph_get_stats(ctx)
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda")
+    def _max(x):
+        t = torch.tensor([x], device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = n * args.steps * ws / (total_ms / 1e3)
+        return float(t.item())
+
+    value, total_ms = aggregate(total_ms, n * args.steps, ws, _max)
     pairs = stats["density_pairs"] + stats["force_pairs"]
     pair_rate = pairs * ws / (total_ms / 1e3)
 
@@ -186,7 +210,7 @@ def run_ours(args):
     achieved = dflop / args.steps / (dms / args.steps / 1e3) / 1e12
     roof = {"kernel": dom, "bound": "alu", "achieved": round(achieved, 3),
             "peak": round(peak_tflops, 2), "unit": "TFLOP/s",
-            "frac": round(achieved / peak_tflops, 4), "traffic": None,
+            "frac": round(achieved / peak_tflops, 4), "traffic": NCU_TRAFFIC.get(dom),
             "peak_basis": f"FP32 FMA 2 x 128 lanes x {sms} SMs x {pk.get('sm_max_mhz', 2070.0)} MHz "
                           f"(sm_max_mhz {pk_kind})",
             "launch_ms": round(dms / args.steps, 4)}
@@ -195,6 +219,8 @@ def run_ours(args):
     native.sph_destroy(ctx)
     del s
     batched = run_batched(args) if rank == 0 and args.batch_instances > 0 else None
+    adjoint = run_adjoint(args) if rank == 0 and args.adjoint_side > 0 else None
+    plummer = run_plummer(args) if rank == 0 and args.plummer_log2 > 0 else None
     out = None
     if rank == 0:
         cpu = run_cpu_baseline(w, args.cpu_seconds) if args.cpu_seconds > 0 else None
@@ -220,6 +246,8 @@ def run_ours(args):
             "tree": {"n_nodes": stats["n_nodes"], "n_groups": stats["n_groups"]},
             "sim_time": float(d_t.item()),
             "batched": batched,
+            "adjoint": adjoint,
+            "plummer": plummer,
         }
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -233,7 +261,10 @@ def run_batched(args):
     with the same instances advanced one after another by sph_step."""
     import torch
     from paper_1909_07439_gb300 import DeviceState, autotune, inputs, native
-    w, off = inputs.sedov_batch(args.batch_instances, seed=4)
+    ws, rank, _ = dist_env()
+    sides = inputs.batch_sizes(args.batch_instances, seed=4)
+    mine = shard_instances(sides ** 3, ws)[rank]   # this rank's instances, no exchange
+    w, off = inputs.sedov_batch(args.batch_instances, seed=4, only=mine)
     k = len(off) - 1
     ctx = native.sph_create(w.n, 0)
     s = DeviceState.from_arrays(w.pos, w.vel, w.h)
@@ -289,6 +320,75 @@ def run_batched(args):
             "plain_sequential_value": updates / t_seq, "batched_over_plain": t_seq / t_batch,
             "pair_interactions_per_s": (stats["density_pairs"] + stats["force_pairs"]) / t_batch,
             "autotune": report, "ms_per_step": 1e3 * t_batch / args.batch_steps}
+
+
+def run_adjoint(args):
+    """Differentiable form: 64^3 Sedov blast, 20-step rollout, loss = mean
+    rho^2 of 1024 seeded probes, gradients w.r.t. initial v, u and alpha_AV
+    with checkpoints every 5 steps; timed against the same rollout without
+    gradients."""
+    import torch
+    from paper_1909_07439_gb300 import DeviceState, inputs, native
+    w = inputs.sedov_lattice(args.adjoint_side)
+    probes = torch.as_tensor(inputs.probe_indices(w.n, 1024), device="cuda")
+    ctx = native.sph_create(w.n, 0)
+    s = DeviceState.from_arrays(w.pos, w.vel, w.h)
+    p = native.sph_params_default()
+    g = torch.zeros((w.n, 4), dtype=torch.float32, device="cuda")
+    native.sph_rollout(ctx, s.c, p, 20, 5, probes, 1024, g)       # allocates the work buffers
+    t0 = time.perf_counter()
+    loss_f, _ = native.sph_rollout(ctx, s.c, p, 20, 5, probes, 1024)
+    t1 = time.perf_counter()
+    loss_b, ga = native.sph_rollout(ctx, s.c, p, 20, 5, probes, 1024, g)
+    t2 = time.perf_counter()
+    native.sph_destroy(ctx)
+    n_upd = w.n * 20
+    return {"workload": f"Sedov lattice {args.adjoint_side}^3 ({w.n} particles), 20 KDK steps, "
+                        f"1024 probes, checkpoints every 5", "loss": loss_f,
+            "forward_value": n_upd / (t1 - t0), "forward_backward_value": n_upd / (t2 - t1),
+            "unit": UNIT, "adjoint_over_forward_time": (t2 - t1) / (t1 - t0),
+            "grad_norm_v": float(torch.linalg.vector_norm(g[:, :3])),
+            "grad_norm_u": float(torch.linalg.vector_norm(g[:, 3])), "dL_dalpha": ga}
+
+
+def run_plummer(args):
+    """Strongly inhomogeneous evaluation: 2^24-particle Plummer sphere,
+    tree build + density + force of one evaluation."""
+    import torch
+    from paper_1909_07439_gb300 import DeviceState, inputs, native
+    w = inputs.plummer(1 << args.plummer_log2)
+    ctx = native.sph_create(w.n, 0)
+    s = DeviceState.from_arrays(w.pos, w.vel, w.h)
+    p = native.sph_params_default()
+    native.sph_build_tree(ctx, s.c, p)
+    native.sph_density(ctx, s.c, p)      # converges h from the analytic-density guess
+    native.sph_force(ctx, s.c, p)
+    native.sph_sync(ctx)
+    native.sph_get_stats(ctx)
+    native.sph_get_timing(ctx)
+    native.sph_set_timing(ctx, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record()
+    for _ in range(reps):
+        native.sph_build_tree(ctx, s.c, p)
+        native.sph_density(ctx, s.c, p)
+        native.sph_force(ctx, s.c, p)
+    e1.record()
+    torch.cuda.synchronize()
+    native.sph_sync(ctx)
+    ms = e0.elapsed_time(e1) / reps
+    stage, _ = native.sph_get_timing(ctx)
+    stats = native.sph_get_stats(ctx)
+    native.sph_destroy(ctx)
+    hh = s.numpy("h")
+    return {"workload": f"Plummer sphere a = 0.1 truncated at r = 1, {w.n} particles",
+            "ms_per_evaluation": ms, "value": w.n / (ms / 1e3), "unit": UNIT,
+            "pair_interactions_per_s": (stats["density_pairs"] + stats["force_pairs"]) / reps / (ms / 1e3),
+            "stage_ms": {k: v / reps for k, v in stage.items()},
+            "h_range": [float(hh.min()), float(hh.max())],
+            "streamed_groups": stats["streamed_groups"] / reps,
+            "n_nodes": stats["n_nodes"], "n_groups": stats["n_groups"]}
 
 
 def run_e2e(native, ctx, s, p, n, args, stream):
@@ -403,6 +503,8 @@ def main():
     ap.add_argument("--tile", type=int, default=0, help="override the neighbour-list tile")
     ap.add_argument("--batch-instances", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--adjoint-side", type=int, default=64)
+    ap.add_argument("--plummer-log2", type=int, default=24)
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -22,7 +22,7 @@ namespace sph {
 constexpr int kTB = 8;           // targets per batch
 constexpr int kDensWarps = 4;    // warps per block
 constexpr float kPad = 0.03f;    // padded list radius, relative to h
-constexpr int kRecLeaves = 96;   // leaf ranges a group's walk may record for the force pass
+constexpr int kRecLeaves = 64;   // leaf ranges a group's walk may record for the force pass
 
 template <int CAP>
 struct DensSmem {
@@ -34,7 +34,10 @@ struct DensSmem {
     int tlen[kTB];
     int rec_n;             // leaf ranges recorded by the last walk (-1: too many)
     int2 rec[kRecLeaves];
-    float4 e[kTB][CAP];    // (r^2, m_j, (v_i - v_j).(x_i - x_j), 0)
+    // list entries: r^2, m_j, (v_i - v_j).(x_i - x_j)
+    float er2[kTB][CAP];
+    float em[kTB][CAP];
+    float evd[kTB][CAP];
 };
 
 struct DensArgs {
@@ -50,9 +53,9 @@ struct DensArgs {
     WalkTree tree;
     const int *inst;  // instance of each slot (batches), or nullptr
     float h_in_scale;          // 1 + pad
-    int2 *leaf_rec, *grp_rec;  // recorded leaf ranges (see sph_internal.cuh)
-    int *rec_ctl;
-    int rec_cap;
+    int2 *leaf_rec, *grp_rec;  // recorded particle runs (see sph_internal.cuh)
+    int *rec_ctl, *rec_bad;
+    int rec_slots;
     float hfact, tol, gamma;
     int max_iter, fixed_iters;
     int *err;
@@ -78,7 +81,7 @@ __device__ __forceinline__ float seg_sum(float v, int L)
 }
 
 template <int CAP>
-__global__ void __launch_bounds__(kDensWarps * 32) density_kernel(DensArgs a)
+__global__ void __launch_bounds__(kDensWarps * 32, 5) density_kernel(DensArgs a)
 {
     extern __shared__ __align__(16) unsigned char dsm_raw[];
     DensSmem<CAP> &sm = reinterpret_cast<DensSmem<CAP> *>(dsm_raw)[threadIdx.x >> 5];
@@ -134,16 +137,17 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_kernel(DensArgs a)
                     if (act) {
                         const int len = sm.tlen[t];
                         for (int e = sub; e < len; e += L) {
-                            const float4 q4 = sm.e[t][e];
-                            if (!(q4.x < R2)) continue;
+                            const float r2 = sm.er2[t][e];
+                            if (!(r2 < R2)) continue;
+                            const float mj = sm.em[t][e];
                             ++cnt;
-                            const float rinv = q4.x > 0.f ? rsqrtf(q4.x) : 0.f;
-                            const float q = q4.x * rinv * hinv;
+                            const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+                            const float q = r2 * rinv * hinv;
                             float f, df;
                             m4_f_df(q, f, df);
-                            s0 += q4.y * f;
-                            s1 += q4.y * (3.f * f + q * df);
-                            s2 += q4.y * q4.z * df * rinv;
+                            s0 += mj * f;
+                            s1 += mj * (3.f * f + q * df);
+                            s2 += mj * sm.evd[t][e] * df * rinv;
                         }
                     }
                     __syncwarp();
@@ -200,8 +204,10 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_kernel(DensArgs a)
                                     const float vdot = (tv.x - vj.x) * (tq.x - pj.x) +
                                                        (tv.y - vj.y) * (tq.y - pj.y) +
                                                        (tv.z - vj.z) * (tq.z - pj.z);
-                                    sm.e[tt][base[tt] + __popc(bs[tt] & lt)] =
-                                        make_float4(r2s[tt], pj.w, vdot, 0.f);
+                                    const int pe = base[tt] + __popc(bs[tt] & lt);
+                                    sm.er2[tt][pe] = r2s[tt];
+                                    sm.em[tt][pe] = pj.w;
+                                    sm.evd[tt][pe] = vdot;
                                 }
                                 if (lane == tt) sm.tlen[tt] = base[tt] + __popc(bs[tt]);
                             }
@@ -296,20 +302,41 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_kernel(DensArgs a)
             ghmax = fmaxf(ghmax, hm);
             // the records hold while no h grew beyond the pad used by the walk
             if (__any_sync(0xffffffffu, act && h > a.h_in_scale * h_in) && lane == 0)
-                atomicOr(a.rec_ctl + 1, 1);
+                atomicOr(a.rec_bad + root, 1);  // root = this group's instance
             __syncwarp();
-            // keep the last walk's leaves for the force pass (one-batch groups)
-            int2 rr = make_int2(0, -1);
-            if (gr.y <= kTB && sm.rec_n >= 0) {
-                int start = 0;
-                if (lane == 0) start = atomicAdd(a.rec_ctl, sm.rec_n);
-                start = __shfl_sync(0xffffffffu, start, 0);
-                if (start + sm.rec_n <= a.rec_cap) {
-                    for (int k = lane; k < sm.rec_n; k += 32) a.leaf_rec[start + k] = sm.rec[k];
-                    rr = make_int2(start, sm.rec_n);
+            // keep the last walk's leaves for the force pass (one-batch groups),
+            // merged into contiguous particle runs, in the group's own slot
+            if (b0 == 0) {
+                int nrun = -1;
+                const int nrec = sm.rec_n;
+                if (gr.y <= kTB && nrec >= 0 && g < a.rec_slots) {
+                    // warp-parallel merge: entry k starts a run unless it continues
+                    // entry k-1; runs gathered as (start, end) in the walk queue area
+                    int2 *runs = sm.w.rq;  // the walk is over
+                    int carry = 0;
+                    for (int b = 0; b < nrec; b += 32) {
+                        const int k = b + lane;
+                        const bool valid = k < nrec;
+                        const int2 e = valid ? sm.rec[k] : make_int2(0, 0);
+                        const bool starts =
+                            valid && (k == 0 || sm.rec[k - 1].x + sm.rec[k - 1].y != e.x);
+                        const bool ends =
+                            valid && (k + 1 == nrec || e.x + e.y != sm.rec[k + 1].x);
+                        const unsigned bst = __ballot_sync(0xffffffffu, starts);
+                        const int run = carry + __popc(bst & (lt | (1u << lane))) - 1;
+                        if (starts && run < kRecRuns) runs[run].x = e.x;
+                        if (ends && run < kRecRuns) runs[run].y = e.x + e.y;
+                        carry += __popc(bst);
+                    }
+                    __syncwarp();
+                    nrun = carry <= kRecRuns ? carry : -1;
+                    if (nrun > 0 && lane < nrun) {
+                        const int2 r = runs[lane];
+                        a.leaf_rec[(size_t)g * kRecRuns + lane] = make_int2(r.x, r.y - r.x);
+                    }
                 }
+                if (lane == 0) a.grp_rec[g] = make_int2(g * kRecRuns, nrun);
             }
-            if (lane == 0 && b0 == 0) a.grp_rec[g] = rr;
             __syncwarp();
         }
         if (lane == 0) a.grp_lo[g].w = ghmax;
@@ -481,7 +508,8 @@ cudaError_t density_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaSt
     a.leaf_rec = c.tree.leaf_rec;
     a.grp_rec = c.tree.grp_rec;
     a.rec_ctl = c.tree.rec_ctl;
-    a.rec_cap = c.tree.rec_cap;
+    a.rec_bad = c.tree.rec_bad;
+    a.rec_slots = c.tree.rec_slots;
     a.pos = (const float4 *)s.pos;
     a.vel = (const float4 *)s.vel;
     a.h = s.h;
@@ -504,8 +532,10 @@ cudaError_t density_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaSt
     a.counters = c.d_counters;
     cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    // fresh leaf records: allocation counter 0, valid unless an h outgrows its pad
+    // fresh records: valid unless an h outgrows its pad
     e = cudaMemsetAsync(c.tree.rec_ctl, 0, 2 * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(c.tree.rec_bad, 0, sizeof(int) * (batch ? batch->n_inst : 1), st);
     if (e != cudaSuccess) return e;
     int cap = p.tile > 0 ? p.tile : 80;
     if (cap <= 64) return launch_density<64>(c, a, st);

@@ -38,7 +38,7 @@ struct ForceArgs {
     WalkTree tree;
     const int *inst;  // instance of each slot (batches), or nullptr
     const int2 *leaf_rec, *grp_rec;  // leaf ranges recorded by the density walk
-    const int *rec_ctl;
+    const int *rec_ctl, *rec_bad;
     float gm1, alpha, beta, alpha_u;
     int *err;
     unsigned long long *counters;
@@ -181,12 +181,12 @@ __global__ void __launch_bounds__(kForceWarps * 32, 6) force_kernel(ForceArgs a)
                 __syncwarp();
                 n_cand += (unsigned long long)nt;
             };
-            const int2 rr = recs_valid ? a.grp_rec[g] : make_int2(0, -1);
+            const int root = a.inst ? a.inst[gr.x] : 0;
+            const int2 rr = recs_valid && a.rec_bad[root] == 0 ? a.grp_rec[g] : make_int2(0, -1);
             if (rr.y >= 0 && gr.y <= kFTB) {
                 replay_ranges(a.leaf_rec + rr.x, rr.y, chunk);
             } else {
-                bool ok = walk_group(a.tree, a.inst ? a.inst[gr.x] : 0, glo, ghi, 0.f, true, glo.w,
-                                     sm.w, chunk);
+                bool ok = walk_group(a.tree, root, glo, ghi, 0.f, true, glo.w, sm.w, chunk);
                 if (!ok && lane == 0) raise_error(a.err, SPH_ERR_TILE_OVERFLOW);
             }
             flush();
@@ -300,6 +300,7 @@ cudaError_t force_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStre
     a.leaf_rec = c.tree.leaf_rec;
     a.grp_rec = c.tree.grp_rec;
     a.rec_ctl = c.tree.rec_ctl;
+    a.rec_bad = c.tree.rec_bad;
     a.pos = (const float4 *)s.pos;
     a.vel = (const float4 *)s.vel;
     a.prop = c.prop;

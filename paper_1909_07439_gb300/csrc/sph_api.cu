@@ -113,7 +113,7 @@ sph_status check_params(Ctx &c, const sph_params *p)
         if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
     } while (0)
 
-constexpr int kTreeLaunches = 50;
+constexpr int kTreeLaunches = 42;
 constexpr int kPrepLaunches = 3;
 
 sph_status do_density(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st)
@@ -216,10 +216,11 @@ sph_status sph_create(sph_ctx **out, int64_t max_n, int device)
     A(dalloc(t.grp_ref, t.cap_groups));
     A(dalloc(t.grp_lo, t.cap_groups));
     A(dalloc(t.grp_hi, t.cap_groups));
-    t.rec_cap = (int)(6 * n + 4096 < (size_t)INT32_MAX ? 6 * n + 4096 : INT32_MAX);
-    A(dalloc(t.leaf_rec, t.rec_cap));
+    t.rec_slots = t.cap_groups;  // one slot per possible group (256 B per particle)
+    A(dalloc(t.leaf_rec, (size_t)t.rec_slots * kRecRuns));
     A(dalloc(t.grp_rec, t.cap_groups));
     A(dalloc(t.rec_ctl, 2));
+    A(dalloc(t.rec_bad, kMaxInstances));
     A(dalloc(t.lv_tree, n));
     A(dalloc(t.lv_grp, n));
     A(dalloc(t.blk_cnt, (size_t)kLevels * nbchop));
@@ -261,7 +262,7 @@ void sph_destroy(sph_ctx *h)
                     c.tree.node_nchild, c.tree.node_parent, c.tree.node_arrive, c.tree.node_lo,
                     c.tree.node_hi, c.tree.node_ref, c.tree.level_start, c.tree.grp_ref,
                     c.tree.grp_lo, c.tree.grp_hi, c.tree.lv_tree, c.tree.lv_grp, c.tree.blk_cnt,
-                    c.tree.leaf_rec, c.tree.grp_rec, c.tree.rec_ctl,
+                    c.tree.leaf_rec, c.tree.grp_rec, c.tree.rec_ctl, c.tree.rec_bad,
                     c.prop, c.vhalf, c.inst, c.bbox_inst, c.dtmin_inst,
                     c.bbox, c.scan_part, c.red_f, c.red_d, c.d_err, c.d_counters,
                     c.d_sizes, c.mirror.pos, c.mirror.vel, c.mirror.acc, c.mirror.h, c.mirror.rho,

@@ -15,6 +15,8 @@ namespace sph {
 constexpr int kMaxLevel = 21;        // 21 bits per axis, 63-bit keys
 constexpr int kLevels = 22;          // levels 0..21
 constexpr int kWarp = 32;
+constexpr int kMaxInstances = 65536;  // instances in one batch
+constexpr int kRecRuns = 32;          // recorded particle runs per group
 constexpr float kCNorm = 0.318309886183790671538f;  // M4, 3D: 1/pi
 
 // stage ids for the per-stage timers
@@ -56,13 +58,15 @@ struct Tree {
     int2 *grp_ref = nullptr;     // (first, count)
     float4 *grp_lo = nullptr;    // x, y, z, h_max
     float4 *grp_hi = nullptr;
-    // leaf ranges opened by each group's density walk, replayed by the force
-    // pass: grp_rec[g] = (start, count) into leaf_rec, count < 0: not recorded;
-    // rec_ctl[0] = allocation counter, rec_ctl[1] = 1 while the records are valid
+    // Particle runs opened by each group's density walk, replayed by the force
+    // pass.  Group g < rec_slots owns leaf_rec[g * kRecRuns ...]; grp_rec[g] =
+    // (g * kRecRuns, count), count < 0: not recorded (the force pass walks).
+    // rec_ctl[1] != 0: records stale (tree rebuilt since the density pass).
     int2 *leaf_rec = nullptr;
     int2 *grp_rec = nullptr;
     int *rec_ctl = nullptr;
-    int rec_cap = 0;
+    int *rec_bad = nullptr;  // per instance (index 0 without a batch): an h outgrew its pad
+    int rec_slots = 0;
     // chop scratch
     int *lv_tree = nullptr, *lv_grp = nullptr;
     int *blk_cnt = nullptr;      // [kLevels][nb]
@@ -73,8 +77,6 @@ struct Batch {
     const int64_t *offsets;  // device [n_inst + 1]
     int n_inst;
 };
-
-constexpr int kMaxInstances = 65536;
 
 struct Ctx {
     int device = 0;

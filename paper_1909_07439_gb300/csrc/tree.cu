@@ -169,9 +169,9 @@ __global__ void morton_kernel(const float4 *__restrict__ pos, const int *__restr
 
 // ------------------------------------------------------------- radix sort
 // Stable LSD radix sort of (key, index), 8-bit digits, 8 passes over the
-// 64-bit word.  Per pass: tile histograms, per-digit scan over tiles, digit
-// bases, then a scatter that ranks equal digits inside a tile in input order
-// (warp match + per-warp counts), which keeps the sort stable.
+// 64-bit word.  Per pass: tile histograms, per-digit scan over tiles, then a
+// scatter that scans the digit totals and ranks equal digits inside a tile in
+// input order (warp match + per-warp counts), which keeps the sort stable.
 constexpr int RS_T = 256, RS_I = 8, RS_TILE = RS_T * RS_I;
 
 // digit of element s: 8 bits of its key, or (inst != nullptr) of its instance id
@@ -244,60 +244,67 @@ __global__ void __launch_bounds__(256) rs_scan_rows_kernel(uint32_t *hist, int n
     if (threadIdx.x == 0) dtotal[blockIdx.x] = carry;
 }
 
-__global__ void __launch_bounds__(256) rs_digit_base_kernel(uint32_t *dtotal)
-{
-    __shared__ uint32_t ws[8];
-    uint32_t v = dtotal[threadIdx.x], ex;
-    block_scan_256(v, ex, ws);
-    dtotal[threadIdx.x] = ex;
-}
-
+// Stable scatter of one tile: warp w owns the contiguous keys
+// [w * 256, (w + 1) * 256) of the tile and ranks them in 8 rounds of 32 with
+// __match_any_sync and a warp-private digit counter row; one prefix over the
+// warps per digit then gives each warp's offset.  Tile order is
+// (warp, round, lane), so equal digits keep their input order.
 __global__ void __launch_bounds__(RS_T) rs_scatter_kernel(
     const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const int *__restrict__ inst, int n, int shift,
-    const uint32_t *__restrict__ hist, const uint32_t *__restrict__ dbase, int ntiles)
+    const uint32_t *__restrict__ hist, const uint32_t *__restrict__ dtotal, int ntiles)
 {
     __shared__ uint32_t base[256];
-    __shared__ uint32_t run[256];
     __shared__ uint32_t wcnt[8][256];
+    __shared__ uint32_t ws[8];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    base[tid] = hist[tid * ntiles + blockIdx.x] + dbase[tid];
-    run[tid] = 0;
+    uint32_t dstart;  // first output slot of digit tid: exclusive scan of the digit totals
+    block_scan_256(dtotal[tid], dstart, ws);
+    base[tid] = hist[tid * ntiles + blockIdx.x] + dstart;
+    uint32_t *flat = &wcnt[0][0];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) flat[k * 256 + tid] = 0;
+    __syncthreads();
     const uint32_t lt = (1u << lane) - 1u;
-    const int tile0 = blockIdx.x * RS_TILE;
+    const int wbase = blockIdx.x * RS_TILE + w * (RS_TILE / 8);
+    uint64_t key[RS_I];
+    uint32_t val[RS_I], dig[RS_I], rank[RS_I];
+#pragma unroll
     for (int r = 0; r < RS_I; ++r) {
-        uint32_t *flat = &wcnt[0][0];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) flat[tid * 8 + k] = 0;
-        __syncthreads();
-        int s = tile0 + r * RS_T + tid;
-        bool valid = s < n;
-        uint64_t key = valid ? kin[s] : 0;
-        uint32_t val = valid ? vin[s] : 0;
-        uint32_t d = valid ? (inst ? ((uint32_t)inst[val] >> shift) & 255u
-                                   : (uint32_t)((key >> shift) & 255u))
+        const int s = wbase + r * 32 + lane;
+        const bool valid = s < n;
+        key[r] = valid ? kin[s] : 0;
+        val[r] = valid ? vin[s] : 0;
+        uint32_t d = valid ? (inst ? ((uint32_t)inst[val[r]] >> shift) & 255u
+                                   : (uint32_t)((key[r] >> shift) & 255u))
                            : 256u + lane;
-        uint32_t peers = __match_any_sync(0xffffffffu, d);
-        uint32_t rank = __popc(peers & lt);
-        if (valid && rank == 0) wcnt[w][d] = __popc(peers);
-        __syncthreads();
-        {
-            uint32_t acc = run[tid];
+        dig[r] = d;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t old = valid ? wcnt[w][d] : 0u;
+        rank[r] = old + __popc(peers & lt);
+        __syncwarp();
+        if (valid && (peers & lt) == 0) wcnt[w][d] = old + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        uint32_t acc = 0;
 #pragma unroll
-            for (int ww = 0; ww < 8; ++ww) {
-                uint32_t c = wcnt[ww][tid];
-                wcnt[ww][tid] = acc;
-                acc += c;
-            }
-            run[tid] = acc;
+        for (int ww = 0; ww < 8; ++ww) {
+            const uint32_t c = wcnt[ww][tid];
+            wcnt[ww][tid] = acc;
+            acc += c;
         }
-        __syncthreads();
-        if (valid) {
-            uint32_t pos = base[d] + wcnt[w][d] + rank;
-            kout[pos] = key;
-            vout[pos] = val;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RS_I; ++r) {
+        if (wbase + r * 32 + lane < n) {
+            const uint32_t d = dig[r];
+            const uint32_t pos = base[d] + wcnt[w][d] + rank[r];
+            kout[pos] = key[r];
+            vout[pos] = val[r];
         }
-        __syncthreads();
     }
 }
 
@@ -723,7 +730,6 @@ cudaError_t build_tree(Ctx &c, const sph_state &s, const sph_params &p, bool ful
         int shift = pass >= 8 ? 8 * (pass - 8) : 8 * pass;
         rs_hist_kernel<<<ntiles, RS_T, 0, st>>>(kin, vin, dinst, n, shift, c.hist, ntiles);
         rs_scan_rows_kernel<<<256, 256, 0, st>>>(c.hist, ntiles, c.dtotal);
-        rs_digit_base_kernel<<<1, 256, 0, st>>>(c.dtotal);
         rs_scatter_kernel<<<ntiles, RS_T, 0, st>>>(kin, vin, kout, vout, dinst, n, shift, c.hist,
                                                    c.dtotal, ntiles);
         std::swap(kin, kout);

@@ -15,7 +15,7 @@
 
 namespace sph {
 
-constexpr int kStack = 256;  // node-range stack entries per warp
+constexpr int kStack = 224;  // node-range stack entries per warp
 constexpr int kRQ = 64;      // leaf-range queue entries per warp
 constexpr float kOpenSlack = 1.0f + 1e-5f;  // keeps FP32 box tests conservative
 

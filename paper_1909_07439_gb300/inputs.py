@@ -135,17 +135,19 @@ def batch_sizes(n_inst: int = 512, seed: int = 4, nmin: int = 4096, nmax: int = 
     return np.rint(nk ** (1.0 / 3.0)).astype(np.int64)
 
 
-def sedov_batch(n_inst: int = 512, seed: int = 4, **kw):
+def sedov_batch(n_inst: int = 512, seed: int = 4, only=None, **kw):
     """Independent Sedov blasts of uneven sizes, packed back to back.
-    Returns (Workload with all particles, offsets[n_inst + 1])."""
+    ``only``: indices of the instances to generate (a rank's share).
+    Returns (Workload with those particles, offsets[len + 1])."""
     sides = batch_sizes(n_inst, seed, **kw)
-    parts = [sedov_lattice(int(s), seed=seed * 100003 + k) for k, s in enumerate(sides)]
-    off = np.zeros(n_inst + 1, np.int64)
+    ks = range(n_inst) if only is None else only
+    parts = [sedov_lattice(int(sides[k]), seed=seed * 100003 + k) for k in ks]
+    off = np.zeros(len(parts) + 1, np.int64)
     off[1:] = np.cumsum([p.n for p in parts])
     pos = np.concatenate([p.pos for p in parts])
     vel = np.concatenate([p.vel for p in parts])
     h = np.concatenate([p.h for p in parts])
-    return Workload("sedov_batch", pos, vel, h, {"seed": seed, "sides": sides.tolist()}), off
+    return Workload("sedov_batch", pos, vel, h, {"seed": seed, "sides": [int(sides[k]) for k in ks]}), off
 
 
 def probe_indices(n: int, k: int = 1024, seed: int = 5) -> np.ndarray:
