@@ -247,26 +247,33 @@ __global__ void __launch_bounds__(256) rs_scan_rows_kernel(uint32_t *hist, int n
 // Stable scatter of one tile: warp w owns the contiguous keys
 // [w * 256, (w + 1) * 256) of the tile and ranks them in 8 rounds of 32 with
 // __match_any_sync and a warp-private digit counter row; one prefix over the
-// warps per digit then gives each warp's offset.  Tile order is
+// warps per digit then gives each key its place in a digit-ordered copy of
+// the tile in shared memory, which is written out digit run by digit run
+// (consecutive threads, consecutive addresses).  Tile order is
 // (warp, round, lane), so equal digits keep their input order.
 __global__ void __launch_bounds__(RS_T) rs_scatter_kernel(
     const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const int *__restrict__ inst, int n, int shift,
     const uint32_t *__restrict__ hist, const uint32_t *__restrict__ dtotal, int ntiles)
 {
-    __shared__ uint32_t base[256];
+    __shared__ uint32_t gbase[256];   // first output slot of (digit, this tile)
+    __shared__ uint32_t tstart[256];  // first slot of each digit in the sorted tile
     __shared__ uint32_t wcnt[8][256];
     __shared__ uint32_t ws[8];
+    __shared__ uint64_t skey[RS_TILE];
+    __shared__ uint32_t sval[RS_TILE];
+    __shared__ uint8_t sdig[RS_TILE];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    uint32_t dstart;  // first output slot of digit tid: exclusive scan of the digit totals
+    uint32_t dstart;  // exclusive scan of the digit totals
     block_scan_256(dtotal[tid], dstart, ws);
-    base[tid] = hist[tid * ntiles + blockIdx.x] + dstart;
+    gbase[tid] = hist[tid * ntiles + blockIdx.x] + dstart;
     uint32_t *flat = &wcnt[0][0];
 #pragma unroll
     for (int k = 0; k < 8; ++k) flat[k * 256 + tid] = 0;
     __syncthreads();
     const uint32_t lt = (1u << lane) - 1u;
-    const int wbase = blockIdx.x * RS_TILE + w * (RS_TILE / 8);
+    const int tile0 = blockIdx.x * RS_TILE;
+    const int wbase = tile0 + w * (RS_TILE / 8);
     uint64_t key[RS_I];
     uint32_t val[RS_I], dig[RS_I], rank[RS_I];
 #pragma unroll
@@ -288,6 +295,7 @@ __global__ void __launch_bounds__(RS_T) rs_scatter_kernel(
     }
     __syncthreads();
     {
+        // per digit: offsets of the warps inside the digit, and the tile count
         uint32_t acc = 0;
 #pragma unroll
         for (int ww = 0; ww < 8; ++ww) {
@@ -295,16 +303,28 @@ __global__ void __launch_bounds__(RS_T) rs_scatter_kernel(
             wcnt[ww][tid] = acc;
             acc += c;
         }
+        uint32_t ex;
+        block_scan_256(acc, ex, ws);  // digit starts inside the sorted tile
+        tstart[tid] = ex;
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < RS_I; ++r) {
         if (wbase + r * 32 + lane < n) {
             const uint32_t d = dig[r];
-            const uint32_t pos = base[d] + wcnt[w][d] + rank[r];
-            kout[pos] = key[r];
-            vout[pos] = val[r];
+            const uint32_t lp = tstart[d] + wcnt[w][d] + rank[r];
+            skey[lp] = key[r];
+            sval[lp] = val[r];
+            sdig[lp] = (uint8_t)d;
         }
+    }
+    __syncthreads();
+    const int valid_n = min(RS_TILE, n - tile0);
+    for (int i = tid; i < valid_n; i += RS_T) {
+        const uint32_t d = sdig[i];
+        const uint32_t pos = gbase[d] + (uint32_t)i - tstart[d];
+        kout[pos] = skey[i];
+        vout[pos] = sval[i];
     }
 }
 
