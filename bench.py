@@ -40,11 +40,12 @@ SIDE = 128
 #  pressure work 3, conduction 11, P_j 2 (viscous branch not counted)   = 65
 FLOP_DENSITY_PAIR = 24
 FLOP_FORCE_PAIR = 65
-# DRAM bytes (read + write) per launch of the pair kernels from one ncu capture
-# of this workload (profiles/density_force_kernels_sedov128_ncu.md); to be
-# re-measured whenever those kernels change.
-NCU_TRAFFIC = {"density_kernel": 105.985536e6 + 68.234496e6,
-               "force_kernel": 149.596928e6 + 30.545664e6}
+#  neighbour-list candidate test: canonical squared distance, 3 sub 3 mul 2 add = 8
+FLOP_TEST = 8
+# DRAM bytes (read + write) per launch of the dominant kernels from one ncu
+# capture of this workload (profiles/); None until measured for the current
+# kernels.
+NCU_TRAFFIC = {}
 
 
 def peaks():
@@ -201,12 +202,13 @@ def run_ours(args):
     pk, pk_kind = peaks()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     peak_tflops = 2 * 128 * sms * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    dens_flop = stats["density_pairs"] * FLOP_DENSITY_PAIR
-    force_flop = stats["force_pairs"] * FLOP_FORCE_PAIR
-    if stage_ms["force"] >= stage_ms["density"]:
-        dom, dflop, dms = "force_kernel", force_flop, stage_ms["force"]
-    else:
-        dom, dflop, dms = "density_kernel", dens_flop, stage_ms["density"]
+    # stage -> (its main kernel, algorithmic FLOPs); each of these stages is
+    # that kernel plus a fallback kernel with (normally) no work
+    work = {"lists": ("nlist_kernel", stats["density_candidates"] * FLOP_TEST),
+            "density": ("density_list_kernel", stats["density_pairs"] * FLOP_DENSITY_PAIR),
+            "force": ("force_list_kernel", stats["force_pairs"] * FLOP_FORCE_PAIR)}
+    dstage = max(work, key=lambda k: stage_ms[k])
+    (dom, dflop), dms = work[dstage], stage_ms[dstage]
     achieved = dflop / args.steps / (dms / args.steps / 1e3) / 1e12
     roof = {"kernel": dom, "bound": "alu", "achieved": round(achieved, 3),
             "peak": round(peak_tflops, 2), "unit": "TFLOP/s",

@@ -57,11 +57,12 @@ typedef struct {
     float beta_av;       /* beta^AV   (Eq. 12)                                          */
     float alpha_u;       /* alpha_u, artificial conductivity (Eq. 13)                   */
     float c_cour;        /* Courant factor (Eq. 8)                                      */
-    float h_tol;         /* Newton stops when |dh|/h < h_tol (checked in FP64)          */
+    float h_tol;         /* Newton stops when |dh| < h_tol h (decided exactly)         */
     int32_t kernel;      /* smoothing kernel: 0 = M4 cubic spline (the only one built)  */
     int32_t n_leaf;      /* max particles per tree leaf  (1..64)                        */
     int32_t n_group;     /* max particles per walk group (1..32)                        */
-    int32_t tile;        /* per-target neighbour-list capacity, 0 = default (96)       */
+    int32_t tile;        /* shared-memory list capacity per target of the walking
+                            fallback kernels, 0 = default (80 density, 96 force)     */
     int32_t max_h_iter;  /* Newton iteration cap (>= 1)                                 */
     int32_t density_iters; /* 0: iterate to h_tol; k > 0: exactly k updates (Sect. 3.2.1) */
 } sph_params;
@@ -245,24 +246,30 @@ sph_status sph_get_tree(sph_ctx *ctx, int32_t *h_level, int32_t *h_first, int32_
 /* Work counters accumulated since the last call (then reset).  Synchronous. */
 typedef struct {
     uint64_t density_pairs;       /* true-neighbour pairs summed, all Newton sweeps   */
-    uint64_t density_candidates;  /* particle-pair distance tests in density walks     */
+    uint64_t density_candidates;  /* particle-pair distance tests in list-building and
+                                     density walks                                     */
     uint64_t force_pairs;         /* pairs in the force sets                           */
-    uint64_t force_candidates;    /* particle-pair distance tests in the force walk    */
+    uint64_t force_candidates;    /* list entries scanned plus pair tests of force walks */
     uint64_t newton_iters;        /* Newton updates summed over particles              */
-    uint64_t density_rewalks;     /* group walks repeated because h outgrew its pad    */
-    uint64_t streamed_groups;     /* groups whose lists overflowed the tile            */
+    uint64_t density_rewalks;     /* target batches solved by the walking fallback
+                                     (an h outgrew the list pad or a list overflowed) */
+    uint64_t streamed_groups;     /* fallback batches whose lists overflowed the tile  */
     uint64_t n_nodes;             /* tree nodes of the last build                      */
     uint64_t n_groups;            /* groups of the last build                          */
+    uint64_t list_entries;        /* neighbour-list entries written                    */
+    uint64_t list_overflows;      /* particles whose list exceeded its capacity        */
 } sph_stats;
 sph_status sph_get_stats(sph_ctx *ctx, sph_stats *out);
 
 /* Per-stage device timing (CUDA events on the launching stream).
- * Stages: 0 tree build, 1 density kernel, 2 force kernel, 3 reductions
+ * Stages: 0 tree build, 1 density (h-rho solve), 2 force, 3 reductions
  * (dt, conserved), 4 leapfrog kicks/drift, 5 force preparation (per-particle
- * sound speed and node/group h_max).  sph_get_timing synchronises and returns
- * the milliseconds summed since the last call, and the number of kernels
- * launched per stage (also counted when timing is off). */
-#define SPH_N_STAGES 6
+ * sound speed and node/group h_max, also refreshed before the density pass),
+ * 6 neighbour lists (the list-building tree walk of the density pass).
+ * sph_get_timing synchronises and returns the milliseconds summed since the
+ * last call, and the number of kernels launched per stage (also counted when
+ * timing is off); both arrays hold SPH_N_STAGES entries. */
+#define SPH_N_STAGES 7
 sph_status sph_set_timing(sph_ctx *ctx, int enable);
 sph_status sph_get_timing(sph_ctx *ctx, double *ms_by_stage, int64_t *launches_by_stage);
 

@@ -509,7 +509,7 @@ static cudaError_t launch_pairwalk(Ctx &c, const sph_state &s, bool dens_set, co
     a.grp_lo = c.tree.grp_lo;
     a.grp_hi = c.tree.grp_hi;
     a.sizes = c.d_sizes;
-    a.work = c.d_sizes + 3;
+    a.work = c.d_sizes + SZ_WORK;
     a.tree = WalkTree{c.tree.node_lo, c.tree.node_hi, c.tree.node_ref};
     a.inst = batch ? c.inst : nullptr;
     a.dens_set = dens_set ? 1 : 0;

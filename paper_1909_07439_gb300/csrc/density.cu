@@ -1,15 +1,20 @@
 // Density pass (Sect. 2.2, Eqs. 1-4) with the smoothing-length solve.
 //
-// One warp per group of particles (up to 8 targets at a time).  The warp
-// walks the tree once with a padded search radius 2 h (1 + pad) per target
-// and keeps, per target, the list of candidates inside that radius in shared
-// memory as (r^2, m_j, j).  The Newton iterations on
+// The h-rho relation is solved per particle with a bracketed Newton iteration
+// on
 //     g(h) = sum_j m_j W(r_ij, h) - m_i (hfact / h)^3
-// then run over those lists only: r_ij does not depend on h, so an iteration
-// is a pure pair sum with no memory traffic.  If a target's h leaves its
-// padded radius the group is walked again; if a list would overflow the
-// shared-memory tile, the group falls back to walking the tree for every
-// sweep ("streamed"), accumulating partial sums as the tile fills.
+// (Sect. 3.2.1).  r_ij does not depend on h, so every sweep is a pure pair sum
+// over a candidate list.
+//
+// density_list_kernel: one warp per batch of up to 8 targets of a group, L
+// lanes per target, reading each target's neighbour list (built by
+// nlist_kernel at the starting h with a (1 + pad) margin).  A batch whose h
+// leaves that margin, or whose list overflowed, is handed to
+// density_walk_kernel, which starts the batch over: it walks the tree with a
+// padded search radius 2 h (1 + pad) per target and keeps the candidates as
+// (r^2, m_j, (v_i - v_j).(x_i - x_j)) in shared memory, walking again if h
+// leaves the pad and falling back to summing while walking ("streamed") if a
+// list would overflow the shared-memory tile.
 //
 // Lane layout for the sums: L = 32 / pow2ceil(targets) lanes per target,
 // lane = t * L + sub; partial sums are reduced across the L lanes with xor
@@ -22,7 +27,6 @@ namespace sph {
 constexpr int kTB = 8;           // targets per batch
 constexpr int kDensWarps = 4;    // warps per block
 constexpr float kPad = 0.03f;    // padded list radius, relative to h
-constexpr int kRecLeaves = 64;   // leaf ranges a group's walk may record for the force pass
 
 template <int CAP>
 struct DensSmem {
@@ -32,8 +36,6 @@ struct DensSmem {
     TargetPairs<kTB> tq;   // target coordinates in pairs for the packed distance test
     float tr2[kTB];        // list radius^2
     int tlen[kTB];
-    int rec_n;             // leaf ranges recorded by the last walk (-1: too many)
-    int2 rec[kRecLeaves];
     // list entries: r^2, m_j, (v_i - v_j).(x_i - x_j)
     float er2[kTB][CAP];
     float em[kTB][CAP];
@@ -46,16 +48,16 @@ struct DensArgs {
     float *h, *rho, *omega, *drhodt;
     float4 *prop;  // h, rho, 1/(rho Omega), c_s  (for the force pass)
     const int2 *grp_ref;
-    float4 *grp_lo;  // .w <- h_max of the group after the solve
-    const float4 *grp_hi;
+    const float4 *grp_lo, *grp_hi;
     const int *sizes;
-    int *work;
+    int *work, *work2;
     WalkTree tree;
     const int *inst;  // instance of each slot (batches), or nullptr
-    float h_in_scale;          // 1 + pad
-    int2 *leaf_rec, *grp_rec;  // recorded particle runs (see sph_internal.cuh)
-    int *rec_ctl, *rec_bad;
-    int rec_slots;
+    const int *nl_idx, *nl_len;
+    int2 *fallback;   // batches handed to the walking kernel
+    int *n_fallback;
+    int *rec_bad;     // per instance: an h outgrew the pad of the lists
+    float h_in_scale; // 1 + pad
     float hfact, tol, gamma;
     int max_iter, fixed_iters;
     int *err;
@@ -80,18 +82,78 @@ __device__ __forceinline__ float seg_sum(float v, int L)
     return v;
 }
 
-template <int CAP>
-__global__ void __launch_bounds__(kDensWarps * 32, 5) density_kernel(DensArgs a)
+// Sums of one pair at smoothing length 1/hinv:
+//   s0 += m_j f(q), s1 += m_j (3 f + q f'), s2 += m_j vd f' / r
+// (h^3 rho = C s0, -h^4 d(rho)/dh = C s1, Eq. 3 numerator x h^4 / C = s2).
+__device__ __forceinline__ void pair_sums(float r2, float mj, float vd, float hinv, float &s0,
+                                          float &s1, float &s2)
 {
-    extern __shared__ __align__(16) unsigned char dsm_raw[];
-    DensSmem<CAP> &sm = reinterpret_cast<DensSmem<CAP> *>(dsm_raw)[threadIdx.x >> 5];
+    const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+    const float q = r2 * rinv * hinv;
+    float f, df;
+    m4_f_df(q, f, df);
+    s0 += mj * f;
+    s1 += mj * (3.f * f + q * df);
+    s2 += mj * vd * df * rinv;
+}
+
+// One bracketed Newton update of h from the sums at h; g h^3 = C s0 - M,
+// g' h^4 = 3 M - C s1 with M = m_i hfact^3.  Convergence |h_new - h| < tol h
+// is decided exactly: h_new - h is exact in FP32 for h_new in [h/2, 2h] and
+// the rounding error of tol h is recovered with an FMA.
+__device__ __forceinline__ void newton_update(float &h, float &hlo, float &hhi, bool &conv,
+                                              float s0, float s1, float M, bool fixed, float tol)
+{
+    const float gt = kCNorm * s0 - M;
+    const float gp = 3.f * M - kCNorm * s1;
+    if (gt == 0.f) {
+        conv = !fixed;
+        return;
+    }
+    if (gt < 0.f) hlo = h; else hhi = h;
+    float hn = h * (1.f - gt / gp);
+    const bool ok = gp > 0.f && hn >= hlo && hn <= hhi && hn >= 0.5f * h && hn <= 2.f * h;
+    if (!ok) {
+        if (hlo > 0.f && hhi < INFINITY) hn = 0.5f * (hlo + hhi);
+        else if (gt < 0.f) hn = 2.f * h;
+        else hn = 0.5f * h;
+    }
+    const float d = fabsf(hn - h);
+    const float th = tol * h;
+    const float th_err = fmaf(tol, h, -th);  // tol h = th + th_err exactly
+    if (!fixed && (d < th || (d == th && th_err > 0.f))) conv = true;  // sums are at this h
+    else h = hn;
+}
+
+// outputs at the accepted h (Eqs. 1-4) and the force pass's per-particle terms
+__device__ __forceinline__ void density_outputs(const DensArgs &a, int i, float h, float M, float s1,
+                                                float s2, float u)
+{
+    const float hinv = 1.f / h;
+    const float rho = M * hinv * hinv * hinv;
+    const float om = 1.f - kCNorm * s1 / (3.f * M);
+    const float F4 = kCNorm * hinv * hinv * hinv * hinv;
+    a.h[i] = h;
+    a.rho[i] = rho;
+    a.omega[i] = om;
+    a.drhodt[i] = F4 * s2 / om;
+    const float cs = sqrtf(fmaxf(a.gamma * (a.gamma - 1.f) * u, 0.f));
+    a.prop[i] = make_float4(h, rho, 1.f / (rho * om), cs);
+}
+
+__device__ __forceinline__ void push_fallback(const DensArgs &a, int g, int b0)
+{
+    if ((threadIdx.x & 31) == 0) a.fallback[atomicAdd(a.n_fallback, 1)] = make_int2(g, b0);
+}
+
+__global__ void __launch_bounds__(kDensWarps * 32) density_list_kernel(DensArgs a)
+{
     const int lane = threadIdx.x & 31;
-    const unsigned lt = lane_lt();
     const int ng = a.sizes[SZ_GROUPS];
     const float hf3 = a.hfact * a.hfact * a.hfact;
     const bool fixed = a.fixed_iters > 0;
     const int limit = fixed ? a.fixed_iters : a.max_iter;
-    unsigned long long n_pairs = 0, n_cand = 0, n_newton = 0, n_rewalk = 0, n_stream = 0;
+    unsigned long long n_pairs = 0, n_newton = 0;
 
     while (true) {
         int g = 0;
@@ -99,10 +161,111 @@ __global__ void __launch_bounds__(kDensWarps * 32, 5) density_kernel(DensArgs a)
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= ng) break;
         const int2 gr = a.grp_ref[g];
+        for (int b0 = 0; b0 < gr.y; b0 += kTB) {
+            const int nt = min(kTB, gr.y - b0);
+            const int L = nt > 4 ? 4 : nt > 2 ? 8 : nt > 1 ? 16 : 32;
+            const int t = lane / L, sub = lane % L;
+            const bool act = t < nt;
+            const int i = gr.x + b0 + (act ? t : 0);
+            const int len = act ? a.nl_len[i] : 0;
+            if (__any_sync(0xffffffffu, len < 0)) {  // a list overflowed
+                push_fallback(a, g, b0);
+                continue;
+            }
+            const int *__restrict__ lst = a.nl_idx + (size_t)i * kNbrCap;
+            const float4 xi = a.pos[i], vi = a.vel[i];
+            float h = a.h[i];
+            const float hw = h * a.h_in_scale;  // the lists hold every pair with r < 2 hw
+            const float M = xi.w * hf3;
+            float hlo = 0.f, hhi = INFINITY;
+            bool conv = !act, outside = false, final_pass = false;
+            int it = 0;
+            float s0, s1, s2;
+            while (true) {
+                s0 = 0.f; s1 = 0.f; s2 = 0.f;
+                int cnt = 0;
+                const float hinv = 1.f / h;
+                const float R = 2.f * h;
+                const float R2 = R * R;
+                for (int e = sub; e < len; e += L) {
+                    const int j = __ldg(lst + e);
+                    const float4 pj = __ldg(&a.pos[j]);
+                    const float r2 = canon_r2(xi.x, xi.y, xi.z, pj.x, pj.y, pj.z);
+                    if (!(r2 < R2)) continue;
+                    const float4 vj = __ldg(&a.vel[j]);
+                    const float vd = (vi.x - vj.x) * (xi.x - pj.x) + (vi.y - vj.y) * (xi.y - pj.y) +
+                                     (vi.z - vj.z) * (xi.z - pj.z);
+                    ++cnt;
+                    pair_sums(r2, pj.w, vd, hinv, s0, s1, s2);
+                }
+                s0 = seg_sum(s0, L);
+                s1 = seg_sum(s1, L);
+                s2 = seg_sum(s2, L);
+                const float cf = seg_sum((float)cnt, L);
+                if (sub == 0 && act) {
+                    n_pairs += (unsigned long long)cf;
+                    ++n_newton;
+                }
+                if (final_pass) break;
+                if (act && !conv) {
+                    newton_update(h, hlo, hhi, conv, s0, s1, M, fixed, a.tol);
+                    outside = h > hw;
+                }
+                ++it;
+                if (__any_sync(0xffffffffu, outside)) break;  // the lists no longer cover h
+                if (fixed) {
+                    if (it >= limit) final_pass = true;   // one more sweep at the last h
+                } else if (__all_sync(0xffffffffu, conv)) {
+                    break;                                // every target's sums are at its h
+                } else if (it >= limit) {
+                    if (lane == 0) raise_error(a.err, SPH_ERR_NOT_CONVERGED);
+                    final_pass = true;
+                }
+            }
+            if (__any_sync(0xffffffffu, outside)) {  // start the batch over with walks
+                push_fallback(a, g, b0);
+                continue;
+            }
+            if (act && sub == 0) density_outputs(a, i, h, M, s1, s2, vi.w);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        n_pairs += __shfl_xor_sync(0xffffffffu, n_pairs, o);
+        n_newton += __shfl_xor_sync(0xffffffffu, n_newton, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&a.counters[C_DENS_PAIRS], n_pairs);
+        atomicAdd(&a.counters[C_NEWTON], n_newton);
+    }
+}
+
+// Batches the list kernel handed over, each solved from its starting h with
+// tree walks.
+template <int CAP>
+__global__ void __launch_bounds__(kDensWarps * 32) density_walk_kernel(DensArgs a)
+{
+    extern __shared__ __align__(16) unsigned char dsm_raw[];
+    DensSmem<CAP> &sm = reinterpret_cast<DensSmem<CAP> *>(dsm_raw)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lane_lt();
+    const int nfb = *a.n_fallback;
+    const float hf3 = a.hfact * a.hfact * a.hfact;
+    const bool fixed = a.fixed_iters > 0;
+    const int limit = fixed ? a.fixed_iters : a.max_iter;
+    unsigned long long n_pairs = 0, n_cand = 0, n_newton = 0, n_rewalk = 0, n_stream = 0;
+
+    while (true) {
+        int k = 0;
+        if (lane == 0) k = atomicAdd(a.work2, 1);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if (k >= nfb) break;
+        const int2 fb = a.fallback[k];
+        const int g = fb.x, b0 = fb.y;
+        const int2 gr = a.grp_ref[g];
         const float4 glo = a.grp_lo[g], ghi = a.grp_hi[g];
         const int root = a.inst ? a.inst[gr.x] : 0;
-        float ghmax = 0.f;
-        for (int b0 = 0; b0 < gr.y; b0 += kTB) {
+        ++n_rewalk;
+        {
             const int nt = min(kTB, gr.y - b0);
             const int L = nt > 4 ? 4 : nt > 2 ? 8 : nt > 1 ? 16 : 32;
             const int t = lane / L, sub = lane % L;
@@ -121,11 +284,11 @@ __global__ void __launch_bounds__(kDensWarps * 32, 5) density_kernel(DensArgs a)
             float hlo = 0.f, hhi = INFINITY;
             float hw = h * (1.f + kPad);  // list radius is 2 hw
             bool valid = false;           // lists cover the current h
-            bool streamed = false;        // group overflowed the tile
+            bool streamed = false;        // batch overflowed the tile
             bool conv = !act;
             bool final_pass = false;
             int it = 0;
-            float s0, s1, s2, cf;
+            float s0, s1, s2;
             while (true) {
                 // ---- one sweep: sums at the current h of every target
                 s0 = 0.f; s1 = 0.f; s2 = 0.f;
@@ -139,15 +302,8 @@ __global__ void __launch_bounds__(kDensWarps * 32, 5) density_kernel(DensArgs a)
                         for (int e = sub; e < len; e += L) {
                             const float r2 = sm.er2[t][e];
                             if (!(r2 < R2)) continue;
-                            const float mj = sm.em[t][e];
                             ++cnt;
-                            const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
-                            const float q = r2 * rinv * hinv;
-                            float f, df;
-                            m4_f_df(q, f, df);
-                            s0 += mj * f;
-                            s1 += mj * (3.f * f + q * df);
-                            s2 += mj * sm.evd[t][e] * df * rinv;
+                            pair_sums(r2, sm.em[t][e], sm.evd[t][e], hinv, s0, s1, s2);
                         }
                     }
                     __syncwarp();
@@ -215,16 +371,7 @@ __global__ void __launch_bounds__(kDensWarps * 32, 5) density_kernel(DensArgs a)
                         __syncwarp();
                         n_cand += (unsigned long long)nt;
                     };
-                    // A padded-list walk opens a node if it is within reach of the
-                    // group or within 2 h_max(node) (1 + pad): that also covers the
-                    // force criterion 2 max(h_i, h_j) while no h grows beyond the pad,
-                    // so the force pass can replay the recorded leaves.
-                    if (lane == 0) sm.rec_n = streamed ? -1 : 0;
-                    __syncwarp();
-                    bool ok = streamed
-                                  ? walk_group(a.tree, root, glo, ghi, reach, false, 0.f, sm.w, chunk)
-                                  : walk_group(a.tree, root, glo, ghi, 0.f, true, 0.5f * reach, sm.w,
-                                               chunk, 1.f + kPad, sm.rec, &sm.rec_n, kRecLeaves);
+                    bool ok = walk_group(a.tree, root, glo, ghi, reach, false, 0.f, sm.w, chunk);
                     if (!ok && lane == 0) raise_error(a.err, SPH_ERR_TILE_OVERFLOW);
                     list_sums();
                     if (overflow) {
@@ -233,7 +380,6 @@ __global__ void __launch_bounds__(kDensWarps * 32, 5) density_kernel(DensArgs a)
                         valid = false;
                     } else {
                         valid = !streamed;
-                        if (!streamed && it > 0) ++n_rewalk;
                     }
                 } else {
                     list_sums();
@@ -241,31 +387,14 @@ __global__ void __launch_bounds__(kDensWarps * 32, 5) density_kernel(DensArgs a)
                 s0 = seg_sum(s0, L);
                 s1 = seg_sum(s1, L);
                 s2 = seg_sum(s2, L);
-                cf = seg_sum((float)cnt, L);
+                const float cf = seg_sum((float)cnt, L);
                 if (sub == 0 && act) {
                     n_pairs += (unsigned long long)cf;
                     ++n_newton;
                 }
                 if (final_pass) break;
-                // ---- bracketed Newton step on g(h); g h^3 = C s0 - M, g' h^4 = 3M - C s1
                 if (act && !conv) {
-                    const float gt = kCNorm * s0 - M;
-                    const float gp = 3.f * M - kCNorm * s1;
-                    if (gt == 0.f) {
-                        conv = !fixed;
-                    } else {
-                        if (gt < 0.f) hlo = h; else hhi = h;
-                        float hn = h * (1.f - gt / gp);
-                        const bool ok = gp > 0.f && hn >= hlo && hn <= hhi && hn >= 0.5f * h && hn <= 2.f * h;
-                        if (!ok) {
-                            if (hlo > 0.f && hhi < INFINITY) hn = 0.5f * (hlo + hhi);
-                            else if (gt < 0.f) hn = 2.f * h;
-                            else hn = 0.5f * h;
-                        }
-                        const double rel = fabs((double)hn - (double)h) / (double)h;  // FP64 test
-                        if (!fixed && rel < (double)a.tol) conv = true;  // sums are at this h
-                        else h = hn;
-                    }
+                    newton_update(h, hlo, hhi, conv, s0, s1, M, fixed, a.tol);
                     if (h > hw) {  // outgrew the padded list
                         hw = h * (1.f + kPad);
                         valid = false;
@@ -283,63 +412,12 @@ __global__ void __launch_bounds__(kDensWarps * 32, 5) density_kernel(DensArgs a)
                 }
                 __syncwarp();
             }
-            // ---- outputs at the accepted h
-            if (act && sub == 0) {
-                const float hinv = 1.f / h;
-                const float rho = M * hinv * hinv * hinv;
-                const float om = 1.f - kCNorm * s1 / (3.f * M);
-                const float F4 = kCNorm * hinv * hinv * hinv * hinv;
-                a.h[i] = h;
-                a.rho[i] = rho;
-                a.omega[i] = om;
-                a.drhodt[i] = F4 * s2 / om;
-                const float u = sm.tv[t].w;
-                const float cs = sqrtf(fmaxf(a.gamma * (a.gamma - 1.f) * u, 0.f));
-                a.prop[i] = make_float4(h, rho, 1.f / (rho * om), cs);
-            }
-            float hm = act ? h : 0.f;
-            for (int o = 16; o > 0; o >>= 1) hm = fmaxf(hm, __shfl_xor_sync(0xffffffffu, hm, o));
-            ghmax = fmaxf(ghmax, hm);
-            // the records hold while no h grew beyond the pad used by the walk
+            if (act && sub == 0) density_outputs(a, i, h, M, s1, s2, sm.tv[t].w);
+            // the neighbour lists hold while no h grew beyond their pad
             if (__any_sync(0xffffffffu, act && h > a.h_in_scale * h_in) && lane == 0)
                 atomicOr(a.rec_bad + root, 1);  // root = this group's instance
             __syncwarp();
-            // keep the last walk's leaves for the force pass (one-batch groups),
-            // merged into contiguous particle runs, in the group's own slot
-            if (b0 == 0) {
-                int nrun = -1;
-                const int nrec = sm.rec_n;
-                if (gr.y <= kTB && nrec >= 0 && g < a.rec_slots) {
-                    // warp-parallel merge: entry k starts a run unless it continues
-                    // entry k-1; runs gathered as (start, end) in the walk queue area
-                    int2 *runs = sm.w.rq;  // the walk is over
-                    int carry = 0;
-                    for (int b = 0; b < nrec; b += 32) {
-                        const int k = b + lane;
-                        const bool valid = k < nrec;
-                        const int2 e = valid ? sm.rec[k] : make_int2(0, 0);
-                        const bool starts =
-                            valid && (k == 0 || sm.rec[k - 1].x + sm.rec[k - 1].y != e.x);
-                        const bool ends =
-                            valid && (k + 1 == nrec || e.x + e.y != sm.rec[k + 1].x);
-                        const unsigned bst = __ballot_sync(0xffffffffu, starts);
-                        const int run = carry + __popc(bst & (lt | (1u << lane))) - 1;
-                        if (starts && run < kRecRuns) runs[run].x = e.x;
-                        if (ends && run < kRecRuns) runs[run].y = e.x + e.y;
-                        carry += __popc(bst);
-                    }
-                    __syncwarp();
-                    nrun = carry <= kRecRuns ? carry : -1;
-                    if (nrun > 0 && lane < nrun) {
-                        const int2 r = runs[lane];
-                        a.leaf_rec[(size_t)g * kRecRuns + lane] = make_int2(r.x, r.y - r.x);
-                    }
-                }
-                if (lane == 0) a.grp_rec[g] = make_int2(g * kRecRuns, nrun);
-            }
-            __syncwarp();
         }
-        if (lane == 0) a.grp_lo[g].w = ghmax;
     }
     // counters: one atomic per warp
     for (int o = 16; o > 0; o >>= 1) {
@@ -465,11 +543,28 @@ static cudaError_t configure_density(int &blocks)
     static int nb_cached = 1;
     if (!configured) {
         size_t smem = sizeof(DensSmem<CAP>) * kDensWarps;
-        cudaError_t e = cudaFuncSetAttribute(density_kernel<CAP>,
+        cudaError_t e = cudaFuncSetAttribute(density_walk_kernel<CAP>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, density_kernel<CAP>, kDensWarps * 32, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, density_walk_kernel<CAP>, kDensWarps * 32,
+                                                          smem);
+        if (e != cudaSuccess) return e;
+        nb_cached = nb > 0 ? nb : 1;
+        configured = true;
+    }
+    blocks = nb_cached;
+    return cudaSuccess;
+}
+
+static cudaError_t configure_density_list(int &blocks)
+{
+    static bool configured = false;
+    static int nb_cached = 1;
+    if (!configured) {
+        int nb = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, density_list_kernel,
+                                                                      kDensWarps * 32, 0);
         if (e != cudaSuccess) return e;
         nb_cached = nb > 0 ? nb : 1;
         configured = true;
@@ -479,37 +574,53 @@ static cudaError_t configure_density(int &blocks)
 }
 
 template <int CAP>
-static cudaError_t launch_density(Ctx &c, const DensArgs &a, cudaStream_t st)
+static cudaError_t launch_density_walk(Ctx &c, const DensArgs &a, cudaStream_t st)
 {
     int blocks = 1;
     cudaError_t e = configure_density<CAP>(blocks);
     if (e != cudaSuccess) return e;
     size_t smem = sizeof(DensSmem<CAP>) * kDensWarps;
-    density_kernel<CAP><<<c.num_sms * blocks, kDensWarps * 32, smem, st>>>(a);
+    density_walk_kernel<CAP><<<c.num_sms * blocks, kDensWarps * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t configure_density_kernels()
 {
     int b;
-    cudaError_t e = configure_density<64>(b);
+    cudaError_t e = configure_density_list(b);
+    if (e == cudaSuccess) e = configure_density<64>(b);
     if (e == cudaSuccess) e = configure_density<80>(b);
     if (e == cudaSuccess) e = configure_density<96>(b);
     if (e == cudaSuccess) e = configure_density<128>(b);
     return e;
 }
 
-cudaError_t density_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st,
-                         const Batch *batch)
+cudaError_t density_lists(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st,
+                          const Batch *batch, bool refresh_hmax)
+{
+    cudaError_t e = cudaSuccess;
+    // node and group h_max of the starting h: the list walk's opening test needs them
+    if (refresh_hmax) e = update_hmax(c, s, p, st);
+    if (e != cudaSuccess) return e;
+    // fresh lists: valid unless an h outgrows its pad
+    e = cudaMemsetAsync(c.tree.rec_ctl, 0, 2 * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(c.tree.rec_bad, 0, sizeof(int) * (batch ? batch->n_inst : 1), st);
+    if (e != cudaSuccess) return e;
+    return nlist_pass(c, s, p, kPad, st, batch);
+}
+
+cudaError_t density_solve(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st,
+                          const Batch *batch)
 {
     DensArgs a{};
     a.inst = batch ? c.inst : nullptr;
     a.h_in_scale = 1.f + kPad;
-    a.leaf_rec = c.tree.leaf_rec;
-    a.grp_rec = c.tree.grp_rec;
-    a.rec_ctl = c.tree.rec_ctl;
+    a.nl_idx = c.nl_idx;
+    a.nl_len = c.nl_len;
+    a.fallback = c.fallback;
+    a.n_fallback = c.d_sizes + SZ_FALLBACK;
     a.rec_bad = c.tree.rec_bad;
-    a.rec_slots = c.tree.rec_slots;
     a.pos = (const float4 *)s.pos;
     a.vel = (const float4 *)s.vel;
     a.h = s.h;
@@ -521,7 +632,8 @@ cudaError_t density_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaSt
     a.grp_lo = c.tree.grp_lo;
     a.grp_hi = c.tree.grp_hi;
     a.sizes = c.d_sizes;
-    a.work = c.d_sizes + 3;
+    a.work = c.d_sizes + SZ_WORK;
+    a.work2 = c.d_sizes + SZ_WORK2;
     a.tree = WalkTree{c.tree.node_lo, c.tree.node_hi, c.tree.node_ref};
     a.hfact = p.hfact;
     a.tol = p.h_tol;
@@ -530,18 +642,28 @@ cudaError_t density_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaSt
     a.fixed_iters = p.density_iters;
     a.err = c.d_err;
     a.counters = c.d_counters;
-    cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(int), st);
+    static_assert(SZ_FALLBACK == SZ_WORK + 1 && SZ_WORK2 == SZ_WORK + 2, "work counters adjacent");
+    cudaError_t e = cudaMemsetAsync(a.work, 0, 3 * sizeof(int), st);
     if (e != cudaSuccess) return e;
-    // fresh records: valid unless an h outgrows its pad
-    e = cudaMemsetAsync(c.tree.rec_ctl, 0, 2 * sizeof(int), st);
+    int blocks = 1;
+    e = configure_density_list(blocks);
     if (e != cudaSuccess) return e;
-    e = cudaMemsetAsync(c.tree.rec_bad, 0, sizeof(int) * (batch ? batch->n_inst : 1), st);
+    density_list_kernel<<<c.num_sms * blocks, kDensWarps * 32, 0, st>>>(a);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     int cap = p.tile > 0 ? p.tile : 80;
-    if (cap <= 64) return launch_density<64>(c, a, st);
-    if (cap <= 80) return launch_density<80>(c, a, st);
-    if (cap <= 96) return launch_density<96>(c, a, st);
-    return launch_density<128>(c, a, st);
+    if (cap <= 64) return launch_density_walk<64>(c, a, st);
+    if (cap <= 80) return launch_density_walk<80>(c, a, st);
+    if (cap <= 96) return launch_density_walk<96>(c, a, st);
+    return launch_density_walk<128>(c, a, st);
+}
+
+cudaError_t density_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st,
+                         const Batch *batch)
+{
+    cudaError_t e = density_lists(c, s, p, st, batch);
+    if (e != cudaSuccess) return e;
+    return density_solve(c, s, p, st, batch);
 }
 
 cudaError_t neighbour_lists(Ctx &c, const sph_state &s, const sph_params &p, int mode,
@@ -556,7 +678,7 @@ cudaError_t neighbour_lists(Ctx &c, const sph_state &s, const sph_params &p, int
     a.grp_lo = c.tree.grp_lo;
     a.grp_hi = c.tree.grp_hi;
     a.sizes = c.d_sizes;
-    a.work = c.d_sizes + 3;
+    a.work = c.d_sizes + SZ_WORK;
     a.tree = WalkTree{c.tree.node_lo, c.tree.node_hi, c.tree.node_ref};
     a.mode = mode;
     a.off = d_off;

@@ -1,13 +1,19 @@
 // Hydro force pass (Sect. 2.4-2.6, Eqs. 9-15), no gravity.
 //
-// One warp per group (up to 8 targets at a time).  The walk opens a node if
-// its box is within 2 max(h_max(group), h_max(node)) of the group box, so a
-// pair is found whenever either particle reaches the other (Sect. 3.2).  Each
-// candidate chunk is tested against every target with the canonical FP32
-// distance; hits are compacted with ballots into per-target lists in shared
-// memory.  The pair arithmetic then runs over the lists with L lanes per
-// target, so the expensive part executes with full warps and no divergence
-// from the neighbour test; lists are flushed whenever one could overflow.
+// The pair set of a particle is every j with r_ij < 2 max(h_i, h_j): a pair is
+// found whenever either particle reaches the other (Sect. 3.2).
+//
+// force_list_kernel: one warp per batch of up to 8 targets of a group, L
+// lanes per target, reading each target's neighbour list from the density
+// pass (a superset of the pair set while no h outgrew the list pad) and
+// applying the exact test with the canonical FP32 distance.  Batches whose
+// lists are unusable (overflowed, stale, or an h of the instance outgrew the
+// pad) go to force_walk_kernel, which walks the tree: it opens a node if its
+// box is within 2 max(h_max(group), h_max(node)) of the group box, tests
+// each candidate chunk against every target and compacts the hits with
+// ballots into per-target lists in shared memory; the pair arithmetic then
+// runs over those lists with L lanes per target, flushing whenever a list
+// could overflow.
 #include "walk.cuh"
 
 namespace sph {
@@ -34,11 +40,13 @@ struct ForceArgs {
     const int2 *grp_ref;
     const float4 *grp_lo, *grp_hi;
     const int *sizes;
-    int *work;
+    int *work, *work2;
     WalkTree tree;
     const int *inst;  // instance of each slot (batches), or nullptr
-    const int2 *leaf_rec, *grp_rec;  // leaf ranges recorded by the density walk
+    const int *nl_idx, *nl_len;
     const int *rec_ctl, *rec_bad;
+    int2 *fallback;
+    int *n_fallback;
     float gm1, alpha, beta, alpha_u;
     int *err;
     unsigned long long *counters;
@@ -54,15 +62,86 @@ __device__ __forceinline__ float m4_df(float q)
     return 0.f;
 }
 
-template <int CAP>
-__global__ void __launch_bounds__(kForceWarps * 32, 6) force_kernel(ForceArgs a)
+// Per-target state of the pair sums: the target's constants and the
+// accumulated acceleration (Eq. 9 with Eq. 13), the three du/dt terms
+// (Eqs. 10, 14, 15) and the signal-velocity maximum (Eq. 12).
+struct ForceTarget {
+    float4 xi, vi, qi;  // x, m / v, u / h, rho, A = 1/(rho Omega), c
+    float hinv_i, hinv4_i, Pi, pres_i;
+    float ax, ay, az, dup, duav, duc, vsmax;
+    int cnt;
+
+    __device__ __forceinline__ void init(float4 x, float4 v, float4 q, const ForceArgs &a)
+    {
+        xi = x; vi = v; qi = q;
+        hinv_i = 1.f / qi.x;
+        hinv4_i = hinv_i * hinv_i * hinv_i * hinv_i;
+        Pi = a.gm1 * qi.y * vi.w;
+        pres_i = a.gm1 * vi.w;  // P_i / rho_i
+        ax = ay = az = dup = duav = duc = 0.f;
+        vsmax = a.alpha * qi.w;
+        cnt = 0;
+    }
+
+    __device__ __forceinline__ void pair(float4 pj, float4 vj, float4 qj, const ForceArgs &a)
+    {
+        const float Ai = qi.z, ci = qi.w;
+        const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float r = sqrtf(r2);
+        const float rinv = r > 0.f ? 1.f / r : 0.f;
+        const float hinv_j = 1.f / qj.x;
+        const float Fi = kCNorm * m4_df(r * hinv_i) * hinv4_i;
+        const float hinv2_j = hinv_j * hinv_j;
+        const float Fj = kCNorm * m4_df(r * hinv_j) * hinv2_j * hinv2_j;
+        const float vr = ((vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz) * rinv;
+        const float avr = fabsf(vr);
+        const float vsi = a.alpha * ci + a.beta * avr;
+        float avi = 0.f, avj = 0.f;
+        if (vr < 0.f) {
+            avi = -0.5f * vsi * vr;
+            avj = -0.5f * (a.alpha * qj.w + a.beta * avr) * vr;
+            duav += pj.w * vsi * vr * vr * Fi;
+        }
+        const float Aj = qj.z;
+        const float coef = pj.w * (Ai * (pres_i + avi) * Fi + Aj * (a.gm1 * vj.w + avj) * Fj);
+        ax -= coef * dx * rinv;
+        ay -= coef * dy * rinv;
+        az -= coef * dz * rinv;
+        dup += pj.w * vr * Fi;
+        const float Pj = a.gm1 * qj.y * vj.w;
+        const float vsu = sqrtf(fabsf(Pi - Pj) / (0.5f * (qi.y + qj.y)));
+        duc += pj.w * vsu * (vi.w - vj.w) * (Fi * Ai + Fj * Aj);
+        vsmax = fmaxf(vsmax, vsi);
+        ++cnt;
+    }
+
+    // reduce over the L lanes of each target; lane sub == 0 writes
+    __device__ __forceinline__ void finish(int L, bool write, int i, const ForceArgs &a)
+    {
+        for (int o = L >> 1; o > 0; o >>= 1) {
+            ax += __shfl_xor_sync(0xffffffffu, ax, o);
+            ay += __shfl_xor_sync(0xffffffffu, ay, o);
+            az += __shfl_xor_sync(0xffffffffu, az, o);
+            dup += __shfl_xor_sync(0xffffffffu, dup, o);
+            duav += __shfl_xor_sync(0xffffffffu, duav, o);
+            duc += __shfl_xor_sync(0xffffffffu, duc, o);
+            vsmax = fmaxf(vsmax, __shfl_xor_sync(0xffffffffu, vsmax, o));
+        }
+        if (write) {
+            const float Ai = qi.z;
+            const float du = pres_i * Ai * dup - 0.5f * Ai * duav + 0.5f * a.alpha_u * duc;
+            a.acc[i] = make_float4(ax, ay, az, du);
+            a.vsigmax[i] = vsmax;
+        }
+    }
+};
+
+__global__ void __launch_bounds__(kForceWarps * 32) force_list_kernel(ForceArgs a)
 {
-    extern __shared__ __align__(16) unsigned char fsm_raw[];
-    ForceSmem<CAP> &sm = reinterpret_cast<ForceSmem<CAP> *>(fsm_raw)[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
-    const unsigned lt = lane_lt();
     const int ng = a.sizes[SZ_GROUPS];
-    const bool recs_valid = a.rec_ctl[1] == 0;
+    const bool lists_fresh = a.rec_ctl[1] == 0;
     unsigned long long n_pairs = 0, n_cand = 0;
 
     while (true) {
@@ -71,8 +150,68 @@ __global__ void __launch_bounds__(kForceWarps * 32, 6) force_kernel(ForceArgs a)
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= ng) break;
         const int2 gr = a.grp_ref[g];
-        const float4 glo = a.grp_lo[g], ghi = a.grp_hi[g];
+        const int root = a.inst ? a.inst[gr.x] : 0;
+        const bool usable = lists_fresh && a.rec_bad[root] == 0;
         for (int b0 = 0; b0 < gr.y; b0 += kFTB) {
+            const int nt = min(kFTB, gr.y - b0);
+            const int L = nt > 4 ? 4 : nt > 2 ? 8 : nt > 1 ? 16 : 32;
+            const int t = lane / L, sub = lane % L;
+            const bool act = t < nt;
+            const int i = gr.x + b0 + (act ? t : 0);
+            const int len = usable && act ? a.nl_len[i] : 0;
+            if (!usable || __any_sync(0xffffffffu, len < 0)) {
+                if (lane == 0) a.fallback[atomicAdd(a.n_fallback, 1)] = make_int2(g, b0);
+                continue;
+            }
+            ForceTarget T;
+            T.init(a.pos[i], a.vel[i], a.prop[i], a);
+            const int *__restrict__ lst = a.nl_idx + (size_t)i * kNbrCap;
+            for (int e = sub; e < len; e += L) {
+                const int j = __ldg(lst + e);
+                if (j == i) continue;
+                const float4 pj = __ldg(&a.pos[j]);
+                const float4 qj = __ldg(&a.prop[j]);
+                const float r2 = canon_r2(T.xi.x, T.xi.y, T.xi.z, pj.x, pj.y, pj.z);
+                const float R = 2.0f * fmaxf(T.qi.x, qj.x);
+                if (!(r2 < R * R)) continue;
+                T.pair(pj, __ldg(&a.vel[j]), qj, a);
+            }
+            T.finish(L, act && sub == 0, i, a);
+            n_pairs += T.cnt;
+            n_cand += act ? (unsigned long long)((len - sub + L - 1) / L) : 0ull;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        n_pairs += __shfl_xor_sync(0xffffffffu, n_pairs, o);
+        n_cand += __shfl_xor_sync(0xffffffffu, n_cand, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&a.counters[C_FORCE_PAIRS], n_pairs);
+        atomicAdd(&a.counters[C_FORCE_CAND], n_cand);
+    }
+}
+
+// Batches the list kernel handed over, with tree walks.
+template <int CAP>
+__global__ void __launch_bounds__(kForceWarps * 32) force_walk_kernel(ForceArgs a)
+{
+    extern __shared__ __align__(16) unsigned char fsm_raw[];
+    ForceSmem<CAP> &sm = reinterpret_cast<ForceSmem<CAP> *>(fsm_raw)[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lane_lt();
+    const int nfb = *a.n_fallback;
+    unsigned long long n_pairs = 0, n_cand = 0;
+
+    while (true) {
+        int k = 0;
+        if (lane == 0) k = atomicAdd(a.work2, 1);
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if (k >= nfb) break;
+        const int2 fb = a.fallback[k];
+        const int g = fb.x, b0 = fb.y;
+        const int2 gr = a.grp_ref[g];
+        const float4 glo = a.grp_lo[g], ghi = a.grp_hi[g];
+        {
             const int nt = min(kFTB, gr.y - b0);
             const int L = nt > 4 ? 4 : nt > 2 ? 8 : nt > 1 ? 16 : 32;
             const int t = lane / L, sub = lane % L;
@@ -90,53 +229,15 @@ __global__ void __launch_bounds__(kForceWarps * 32, 6) force_kernel(ForceArgs a)
                 }
             }
             __syncwarp();
-            // per-target constants in registers of the target's lanes
-            const float4 xi = sm.tp[act ? t : 0], vi = sm.tv[act ? t : 0], qi = sm.tq[act ? t : 0];
-            const float hinv_i = 1.f / qi.x;
-            const float hinv4_i = hinv_i * hinv_i * hinv_i * hinv_i;
-            const float Ai = qi.z, ci = qi.w;
-            const float Pi = a.gm1 * qi.y * vi.w;
-            const float pres_i = a.gm1 * vi.w;  // P_i / rho_i
-            float ax = 0.f, ay = 0.f, az = 0.f, dup = 0.f, duav = 0.f, duc = 0.f;
-            float vsmax = a.alpha * ci;
-            int cnt = 0;
+            ForceTarget T;
+            T.init(sm.tp[act ? t : 0], sm.tv[act ? t : 0], sm.tq[act ? t : 0], a);
 
             auto flush = [&]() {
                 if (act) {
                     const int len = sm.tlen[t];
                     for (int e = sub; e < len; e += L) {
                         const int j = sm.ej[t][e];
-                        const float4 pj = __ldg(&a.pos[j]);
-                        const float4 vj = __ldg(&a.vel[j]);
-                        const float4 qj = __ldg(&a.prop[j]);
-                        const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
-                        const float r2 = dx * dx + dy * dy + dz * dz;
-                        const float r = sqrtf(r2);
-                        const float rinv = r > 0.f ? 1.f / r : 0.f;
-                        const float hinv_j = 1.f / qj.x;
-                        const float Fi = kCNorm * m4_df(r * hinv_i) * hinv4_i;
-                        const float hinv2_j = hinv_j * hinv_j;
-                        const float Fj = kCNorm * m4_df(r * hinv_j) * hinv2_j * hinv2_j;
-                        const float vr = ((vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz) * rinv;
-                        const float avr = fabsf(vr);
-                        const float vsi = a.alpha * ci + a.beta * avr;
-                        float avi = 0.f, avj = 0.f;
-                        if (vr < 0.f) {
-                            avi = -0.5f * vsi * vr;
-                            avj = -0.5f * (a.alpha * qj.w + a.beta * avr) * vr;
-                            duav += pj.w * vsi * vr * vr * Fi;
-                        }
-                        const float Aj = qj.z;
-                        const float coef = pj.w * (Ai * (pres_i + avi) * Fi + Aj * (a.gm1 * vj.w + avj) * Fj);
-                        ax -= coef * dx * rinv;
-                        ay -= coef * dy * rinv;
-                        az -= coef * dz * rinv;
-                        dup += pj.w * vr * Fi;
-                        const float Pj = a.gm1 * qj.y * vj.w;
-                        const float vsu = sqrtf(fabsf(Pi - Pj) / (0.5f * (qi.y + qj.y)));
-                        duc += pj.w * vsu * (vi.w - vj.w) * (Fi * Ai + Fj * Aj);
-                        vsmax = fmaxf(vsmax, vsi);
-                        ++cnt;
+                        T.pair(__ldg(&a.pos[j]), __ldg(&a.vel[j]), __ldg(&a.prop[j]), a);
                     }
                 }
                 __syncwarp();
@@ -182,40 +283,18 @@ __global__ void __launch_bounds__(kForceWarps * 32, 6) force_kernel(ForceArgs a)
                 n_cand += (unsigned long long)nt;
             };
             const int root = a.inst ? a.inst[gr.x] : 0;
-            const int2 rr = recs_valid && a.rec_bad[root] == 0 ? a.grp_rec[g] : make_int2(0, -1);
-            if (rr.y >= 0 && gr.y <= kFTB) {
-                replay_ranges(a.leaf_rec + rr.x, rr.y, chunk);
-            } else {
-                bool ok = walk_group(a.tree, root, glo, ghi, 0.f, true, glo.w, sm.w, chunk);
-                if (!ok && lane == 0) raise_error(a.err, SPH_ERR_TILE_OVERFLOW);
-            }
+            bool ok = walk_group(a.tree, root, glo, ghi, 0.f, true, glo.w, sm.w, chunk);
+            if (!ok && lane == 0) raise_error(a.err, SPH_ERR_TILE_OVERFLOW);
             flush();
-            // reduce over the L lanes of each target
-            for (int o = L >> 1; o > 0; o >>= 1) {
-                ax += __shfl_xor_sync(0xffffffffu, ax, o);
-                ay += __shfl_xor_sync(0xffffffffu, ay, o);
-                az += __shfl_xor_sync(0xffffffffu, az, o);
-                dup += __shfl_xor_sync(0xffffffffu, dup, o);
-                duav += __shfl_xor_sync(0xffffffffu, duav, o);
-                duc += __shfl_xor_sync(0xffffffffu, duc, o);
-                vsmax = fmaxf(vsmax, __shfl_xor_sync(0xffffffffu, vsmax, o));
-            }
-            if (act && sub == 0) {
-                float du = pres_i * Ai * dup - 0.5f * Ai * duav + 0.5f * a.alpha_u * duc;
-                a.acc[i0 + t] = make_float4(ax, ay, az, du);
-                a.vsigmax[i0 + t] = vsmax;
-            }
-            n_pairs += cnt;
+            T.finish(L, act && sub == 0, i0 + t, a);
+            n_pairs += T.cnt;
             __syncwarp();
         }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        n_pairs += __shfl_xor_sync(0xffffffffu, n_pairs, o);
-        n_cand += __shfl_xor_sync(0xffffffffu, n_cand, o);
-    }
+    for (int o = 16; o > 0; o >>= 1) n_pairs += __shfl_xor_sync(0xffffffffu, n_pairs, o);
     if (lane == 0) {
         atomicAdd(&a.counters[C_FORCE_PAIRS], n_pairs);
-        atomicAdd(&a.counters[C_FORCE_CAND], n_cand);  // sum over lanes = 32 per chunk-target
+        atomicAdd(&a.counters[C_FORCE_CAND], n_cand * 32);  // 32 lanes per chunk-target
     }
 }
 
@@ -246,11 +325,28 @@ static cudaError_t configure_force(int &blocks)
     static int nb_cached = 1;
     if (!configured) {
         size_t smem = sizeof(ForceSmem<CAP>) * kForceWarps;
-        cudaError_t e = cudaFuncSetAttribute(force_kernel<CAP>,
+        cudaError_t e = cudaFuncSetAttribute(force_walk_kernel<CAP>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_kernel<CAP>, kForceWarps * 32, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_walk_kernel<CAP>, kForceWarps * 32,
+                                                          smem);
+        if (e != cudaSuccess) return e;
+        nb_cached = nb > 0 ? nb : 1;
+        configured = true;
+    }
+    blocks = nb_cached;
+    return cudaSuccess;
+}
+
+static cudaError_t configure_force_list(int &blocks)
+{
+    static bool configured = false;
+    static int nb_cached = 1;
+    if (!configured) {
+        int nb = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_list_kernel,
+                                                                      kForceWarps * 32, 0);
         if (e != cudaSuccess) return e;
         nb_cached = nb > 0 ? nb : 1;
         configured = true;
@@ -260,20 +356,21 @@ static cudaError_t configure_force(int &blocks)
 }
 
 template <int CAP>
-static cudaError_t launch_force(Ctx &c, const ForceArgs &a, cudaStream_t st)
+static cudaError_t launch_force_walk(Ctx &c, const ForceArgs &a, cudaStream_t st)
 {
     int blocks = 1;
     cudaError_t e = configure_force<CAP>(blocks);
     if (e != cudaSuccess) return e;
     size_t smem = sizeof(ForceSmem<CAP>) * kForceWarps;
-    force_kernel<CAP><<<c.num_sms * blocks, kForceWarps * 32, smem, st>>>(a);
+    force_walk_kernel<CAP><<<c.num_sms * blocks, kForceWarps * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t configure_force_kernels()
 {
     int b;
-    cudaError_t e = configure_force<64>(b);
+    cudaError_t e = configure_force_list(b);
+    if (e == cudaSuccess) e = configure_force<64>(b);
     if (e == cudaSuccess) e = configure_force<96>(b);
     if (e == cudaSuccess) e = configure_force<128>(b);
     return e;
@@ -297,10 +394,12 @@ cudaError_t force_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStre
     cudaError_t e;
     ForceArgs a{};
     a.inst = batch ? c.inst : nullptr;
-    a.leaf_rec = c.tree.leaf_rec;
-    a.grp_rec = c.tree.grp_rec;
+    a.nl_idx = c.nl_idx;
+    a.nl_len = c.nl_len;
     a.rec_ctl = c.tree.rec_ctl;
     a.rec_bad = c.tree.rec_bad;
+    a.fallback = c.fallback;
+    a.n_fallback = c.d_sizes + SZ_FALLBACK;
     a.pos = (const float4 *)s.pos;
     a.vel = (const float4 *)s.vel;
     a.prop = c.prop;
@@ -310,7 +409,8 @@ cudaError_t force_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStre
     a.grp_lo = c.tree.grp_lo;
     a.grp_hi = c.tree.grp_hi;
     a.sizes = c.d_sizes;
-    a.work = c.d_sizes + 3;
+    a.work = c.d_sizes + SZ_WORK;
+    a.work2 = c.d_sizes + SZ_WORK2;
     a.tree = WalkTree{c.tree.node_lo, c.tree.node_hi, c.tree.node_ref};
     a.gm1 = p.gamma - 1.f;
     a.alpha = p.alpha_av;
@@ -318,12 +418,18 @@ cudaError_t force_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStre
     a.alpha_u = p.alpha_u;
     a.err = c.d_err;
     a.counters = c.d_counters;
-    e = cudaMemsetAsync(a.work, 0, sizeof(int), st);
+    e = cudaMemsetAsync(a.work, 0, 3 * sizeof(int), st);  // work, fallback count, work2
+    if (e != cudaSuccess) return e;
+    int blocks = 1;
+    e = configure_force_list(blocks);
+    if (e != cudaSuccess) return e;
+    force_list_kernel<<<c.num_sms * blocks, kForceWarps * 32, 0, st>>>(a);
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     int cap = p.tile > 0 ? p.tile : 96;
-    if (cap <= 64) return launch_force<64>(c, a, st);
-    if (cap <= 96) return launch_force<96>(c, a, st);
-    return launch_force<128>(c, a, st);
+    if (cap <= 64) return launch_force_walk<64>(c, a, st);
+    if (cap <= 96) return launch_force_walk<96>(c, a, st);
+    return launch_force_walk<128>(c, a, st);
 }
 
 }  // namespace sph

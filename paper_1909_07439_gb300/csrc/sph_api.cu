@@ -118,8 +118,17 @@ constexpr int kPrepLaunches = 3;
 
 sph_status do_density(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st)
 {
-    StageScope sc(c, ST_DENSITY, st, 1);
-    CK(density_pass(c, s, p, st), "density");
+    {
+        // node and group h_max of the starting h, for the list walk
+        StageScope sc(c, ST_PREP, st, 2);
+        CK(update_hmax(c, s, p, st), "update_hmax");
+    }
+    {
+        StageScope sc(c, ST_LISTS, st, 1);
+        CK(density_lists(c, s, p, st, nullptr, false), "neighbour lists");
+    }
+    StageScope sc(c, ST_DENSITY, st, 2);
+    CK(density_solve(c, s, p, st), "density");
     return SPH_OK;
 }
 
@@ -129,7 +138,7 @@ sph_status do_force(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_
         StageScope sc(c, ST_PREP, st, kPrepLaunches);
         CK(force_prep(c, s, p, st), "force_prep");
     }
-    StageScope sc(c, ST_FORCE, st, 1);
+    StageScope sc(c, ST_FORCE, st, 2);
     CK(force_pass(c, s, p, st), "force");
     return SPH_OK;
 }
@@ -216,10 +225,11 @@ sph_status sph_create(sph_ctx **out, int64_t max_n, int device)
     A(dalloc(t.grp_ref, t.cap_groups));
     A(dalloc(t.grp_lo, t.cap_groups));
     A(dalloc(t.grp_hi, t.cap_groups));
-    t.rec_slots = t.cap_groups;  // one slot per possible group (256 B per particle)
-    A(dalloc(t.leaf_rec, (size_t)t.rec_slots * kRecRuns));
-    A(dalloc(t.grp_rec, t.cap_groups));
+    A(dalloc(c.nl_idx, n * kNbrCap));  // 512 B per particle
+    A(dalloc(c.nl_len, n));
+    A(dalloc(c.fallback, n));
     A(dalloc(t.rec_ctl, 2));
+    if (e == cudaSuccess) e = cudaMemset(t.rec_ctl, 0xff, 2 * sizeof(int));  // no lists yet
     A(dalloc(t.rec_bad, kMaxInstances));
     A(dalloc(t.lv_tree, n));
     A(dalloc(t.lv_grp, n));
@@ -262,7 +272,7 @@ void sph_destroy(sph_ctx *h)
                     c.tree.node_nchild, c.tree.node_parent, c.tree.node_arrive, c.tree.node_lo,
                     c.tree.node_hi, c.tree.node_ref, c.tree.level_start, c.tree.grp_ref,
                     c.tree.grp_lo, c.tree.grp_hi, c.tree.lv_tree, c.tree.lv_grp, c.tree.blk_cnt,
-                    c.tree.leaf_rec, c.tree.grp_rec, c.tree.rec_ctl, c.tree.rec_bad,
+                    c.nl_idx, c.nl_len, c.fallback, c.tree.rec_ctl, c.tree.rec_bad,
                     c.prop, c.vhalf, c.inst, c.bbox_inst, c.dtmin_inst,
                     c.bbox, c.scan_part, c.red_f, c.red_d, c.d_err, c.d_counters,
                     c.d_sizes, c.mirror.pos, c.mirror.vel, c.mirror.acc, c.mirror.h, c.mirror.rho,
@@ -496,6 +506,7 @@ sph_status sph_batch_step(sph_ctx *h, sph_state *s, const int64_t *d_offsets, in
         }
         CK(configure_density_kernels(), "configure density");
         CK(configure_force_kernels(), "configure force");
+        CK(configure_nlist_kernels(), "configure lists");
         // record on a private stream: the caller's may be the legacy default
         // stream, which cannot be captured
         if (!c.capture_stream)
@@ -608,6 +619,8 @@ sph_status sph_get_stats(sph_ctx *h, sph_stats *out)
     out->newton_iters = v[C_NEWTON];
     out->density_rewalks = v[C_REWALK];
     out->streamed_groups = v[C_STREAMED];
+    out->list_entries = v[C_LIST_ENTRIES];
+    out->list_overflows = v[C_LIST_OVERFLOW];
     out->n_nodes = (uint64_t)sz[SZ_NODES];
     out->n_groups = (uint64_t)sz[SZ_GROUPS];
     return SPH_OK;

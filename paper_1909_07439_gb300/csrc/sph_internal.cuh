@@ -16,11 +16,14 @@ constexpr int kMaxLevel = 21;        // 21 bits per axis, 63-bit keys
 constexpr int kLevels = 22;          // levels 0..21
 constexpr int kWarp = 32;
 constexpr int kMaxInstances = 65536;  // instances in one batch
-constexpr int kRecRuns = 32;          // recorded particle runs per group
+constexpr int kNbrCap = 128;          // neighbour-list entries per particle
 constexpr float kCNorm = 0.318309886183790671538f;  // M4, 3D: 1/pi
 
 // stage ids for the per-stage timers
-enum Stage { ST_TREE = 0, ST_DENSITY = 1, ST_FORCE = 2, ST_REDUCE = 3, ST_LEAPFROG = 4, ST_PREP = 5, ST_N = 6 };
+enum Stage {
+    ST_TREE = 0, ST_DENSITY = 1, ST_FORCE = 2, ST_REDUCE = 3, ST_LEAPFROG = 4, ST_PREP = 5, ST_LISTS = 6,
+    ST_N = 7
+};
 
 // device error word: bit (1 << status) per condition seen
 __device__ __forceinline__ void raise_error(int *err, sph_status code)
@@ -37,11 +40,15 @@ enum Counter {
     C_NEWTON = 4,
     C_REWALK = 5,
     C_STREAMED = 6,
-    C_N = 8
+    C_LIST_ENTRIES = 7,
+    C_LIST_OVERFLOW = 8,
+    C_N = 12
 };
 
 // tree-size scalars on the device (Ctx::d_sizes)
-enum Size { SZ_NODES = 0, SZ_GROUPS = 1, SZ_N = 4 };
+// SZ_WORK / SZ_WORK2: work counters of the persistent kernels; SZ_FALLBACK:
+// entries in Ctx::fallback
+enum Size { SZ_NODES = 0, SZ_GROUPS = 1, SZ_WORK = 3, SZ_FALLBACK = 4, SZ_WORK2 = 5, SZ_N = 8 };
 
 struct Tree {
     int cap_nodes = 0;
@@ -58,15 +65,11 @@ struct Tree {
     int2 *grp_ref = nullptr;     // (first, count)
     float4 *grp_lo = nullptr;    // x, y, z, h_max
     float4 *grp_hi = nullptr;
-    // Particle runs opened by each group's density walk, replayed by the force
-    // pass.  Group g < rec_slots owns leaf_rec[g * kRecRuns ...]; grp_rec[g] =
-    // (g * kRecRuns, count), count < 0: not recorded (the force pass walks).
-    // rec_ctl[1] != 0: records stale (tree rebuilt since the density pass).
-    int2 *leaf_rec = nullptr;
-    int2 *grp_rec = nullptr;
+    // Validity of the neighbour lists built by the density pass:
+    // rec_ctl[1] != 0: lists stale (tree rebuilt since the density pass);
+    // rec_bad[k] != 0: an h of instance k (0 without a batch) outgrew its pad.
     int *rec_ctl = nullptr;
-    int *rec_bad = nullptr;  // per instance (index 0 without a batch): an h outgrew its pad
-    int rec_slots = 0;
+    int *rec_bad = nullptr;
     // chop scratch
     int *lv_tree = nullptr, *lv_grp = nullptr;
     int *blk_cnt = nullptr;      // [kLevels][nb]
@@ -97,6 +100,13 @@ struct Ctx {
     uint32_t *tmp_perm = nullptr;
 
     Tree tree;
+
+    // Neighbour lists (curve order): particle i owns nl_idx[i * kNbrCap ...],
+    // nl_len[i] entries, -1 if they did not fit.  Entry j is in i's list if
+    // r_ij < 2 (1 + pad) max(h_i, h_j) at the h the density pass started from.
+    int *nl_idx = nullptr;
+    int *nl_len = nullptr;
+    int2 *fallback = nullptr;  // (group, first batch slot) handed to the walk kernels
 
     // per-particle scratch
     float4 *prop = nullptr;   // h, rho, 1/(rho Omega), c_s
@@ -133,9 +143,9 @@ struct Ctx {
     bool timing = false;
     struct EvPair { cudaEvent_t a, b; int stage; };
     std::vector<EvPair> ev_free, ev_pending;
-    double stage_ms[ST_N] = {0, 0, 0, 0, 0, 0};
-    int64_t stage_launches[ST_N] = {0, 0, 0, 0, 0, 0};
-    int64_t pending_launches[ST_N] = {0, 0, 0, 0, 0, 0};
+    double stage_ms[ST_N] = {};
+    int64_t stage_launches[ST_N] = {};
+    int64_t pending_launches[ST_N] = {};
 };
 
 // ---------------------------------------------------------------------------
@@ -148,7 +158,15 @@ cudaError_t instance_map(Ctx &c, const int64_t *d_offsets, int n_inst, int n, cu
 cudaError_t update_hmax(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st);
 cudaError_t scan_exclusive_int(Ctx &c, const int *in, int *out, int n, int *total_dev,
                                cudaStream_t st);
-// density.cu
+// nlist.cu
+cudaError_t nlist_pass(Ctx &c, const sph_state &s, const sph_params &p, float pad,
+                       cudaStream_t st, const Batch *batch = nullptr);
+cudaError_t configure_nlist_kernels();
+// density.cu (density_pass = density_lists + density_solve)
+cudaError_t density_lists(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st,
+                          const Batch *batch = nullptr, bool refresh_hmax = true);
+cudaError_t density_solve(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st,
+                          const Batch *batch = nullptr);
 cudaError_t density_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st,
                          const Batch *batch = nullptr);
 cudaError_t neighbour_lists(Ctx &c, const sph_state &s, const sph_params &p, int mode,

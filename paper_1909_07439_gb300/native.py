@@ -17,7 +17,7 @@ SPH_OK = 0
 STATUS = {0: "SPH_OK", 1: "SPH_ERR_INVALID_ARG", 2: "SPH_ERR_CUDA", 3: "SPH_ERR_NOMEM",
           4: "SPH_ERR_NOT_CONVERGED", 5: "SPH_ERR_TILE_OVERFLOW", 6: "SPH_ERR_NONFINITE",
           7: "SPH_ERR_NEGATIVE_U", 8: "SPH_ERR_TIMEOUT"}
-STAGES = ("tree", "density", "force", "reduce", "leapfrog", "prep")
+STAGES = ("tree", "density", "force", "reduce", "leapfrog", "prep", "lists")
 
 
 class NativeLibraryMissing(RuntimeError):
@@ -47,7 +47,8 @@ class sph_state(ctypes.Structure):
 class sph_stats(ctypes.Structure):
     _fields_ = [(k, c_uint64) for k in (
         "density_pairs", "density_candidates", "force_pairs", "force_candidates",
-        "newton_iters", "density_rewalks", "streamed_groups", "n_nodes", "n_groups")]
+        "newton_iters", "density_rewalks", "streamed_groups", "n_nodes", "n_groups",
+        "list_entries", "list_overflows")]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
