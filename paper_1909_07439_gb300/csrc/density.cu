@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_list_kernel(DensArgs 
             const bool act = t < nt;
             const int i = gr.x + b0 + (act ? t : 0);
             const int len = act ? a.nl_len[i] : 0;
-            if (__any_sync(0xffffffffu, len < 0)) {  // a list overflowed
+            if (__any_sync(0xffffffffu, len < 0)) {  // no list (overflow, or too many leaves)
                 push_fallback(a, g, b0);
                 continue;
             }
@@ -187,16 +187,24 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_list_kernel(DensArgs 
                 const float hinv = 1.f / h;
                 const float R = 2.f * h;
                 const float R2 = R * R;
-                for (int e = sub; e < len; e += L) {
-                    const int j = __ldg(lst + e);
-                    const float4 pj = __ldg(&a.pos[j]);
-                    const float r2 = canon_r2(xi.x, xi.y, xi.z, pj.x, pj.y, pj.z);
-                    if (!(r2 < R2)) continue;
-                    const float4 vj = __ldg(&a.vel[j]);
-                    const float vd = (vi.x - vj.x) * (xi.x - pj.x) + (vi.y - vj.y) * (xi.y - pj.y) +
-                                     (vi.z - vj.z) * (xi.z - pj.z);
-                    ++cnt;
-                    pair_sums(r2, pj.w, vd, hinv, s0, s1, s2);
+                // Two entries per iteration, no branch on the distance: f and
+                // f' vanish for q >= 2, so entries beyond 2 h add nothing.  A
+                // missing second entry repeats the first with zero mass.
+                auto entry = [&](float4 pj, float4 vj, float mj) {
+                    const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
+                    const float r2 = dx * dx + dy * dy + dz * dz;
+                    const float vd = (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz;
+                    cnt += (mj > 0.f && r2 < R2) ? 1 : 0;
+                    pair_sums(r2, mj, vd, hinv, s0, s1, s2);
+                };
+                for (int e = sub; e < len; e += 2 * L) {
+                    const bool two = e + L < len;
+                    const int j0 = __ldcs(lst + e);
+                    const int j1 = two ? __ldcs(lst + e + L) : j0;
+                    const float4 p0 = __ldg(&a.pos[j0]), p1 = __ldg(&a.pos[j1]);
+                    const float4 v0 = __ldg(&a.vel[j0]), v1 = __ldg(&a.vel[j1]);
+                    entry(p0, v0, p0.w);
+                    entry(p1, v1, two ? p1.w : 0.f);
                 }
                 s0 = seg_sum(s0, L);
                 s1 = seg_sum(s1, L);

@@ -52,14 +52,12 @@ struct ForceArgs {
     unsigned long long *counters;
 };
 
-__device__ __forceinline__ float m4_df(float q)
+// f'(q) of the M4 kernel without branches (q >= 0; q >= 2 gives 0)
+__device__ __forceinline__ float m4_df_sel(float q)
 {
-    if (q < 1.f) return q * (-3.f + 2.25f * q);
-    if (q < 2.f) {
-        float t = 2.f - q;
-        return -0.75f * t * t;
-    }
-    return 0.f;
+    const float inner = q * (-3.f + 2.25f * q);
+    const float t = fmaxf(2.f - q, 0.f);
+    return q < 1.f ? inner : -0.75f * t * t;
 }
 
 // Per-target state of the pair sums: the target's constants and the
@@ -67,7 +65,7 @@ __device__ __forceinline__ float m4_df(float q)
 // (Eqs. 10, 14, 15) and the signal-velocity maximum (Eq. 12).
 struct ForceTarget {
     float4 xi, vi, qi;  // x, m / v, u / h, rho, A = 1/(rho Omega), c
-    float hinv_i, hinv4_i, Pi, pres_i;
+    float hinv_i, cf_i, Pi, pres_i;
     float ax, ay, az, dup, duav, duc, vsmax;
     int cnt;
 
@@ -75,7 +73,7 @@ struct ForceTarget {
     {
         xi = x; vi = v; qi = q;
         hinv_i = 1.f / qi.x;
-        hinv4_i = hinv_i * hinv_i * hinv_i * hinv_i;
+        cf_i = kCNorm * hinv_i * hinv_i * hinv_i * hinv_i;  // F_i = f'(q_i) C / h_i^4
         Pi = a.gm1 * qi.y * vi.w;
         pres_i = a.gm1 * vi.w;  // P_i / rho_i
         ax = ay = az = dup = duav = duc = 0.f;
@@ -83,37 +81,42 @@ struct ForceTarget {
         cnt = 0;
     }
 
-    __device__ __forceinline__ void pair(float4 pj, float4 vj, float4 qj, const ForceArgs &a)
+    // One pair.  `in` = j is in the pair set; all other contributions scale
+    // with mj, which callers set to 0 for a padding entry.  Square roots and
+    // quotients use the hardware approximations (a few ulp), the pair-set
+    // decision is made by the caller with the canonical distance.
+    __device__ __forceinline__ void pair(float4 pj, float4 vj, float4 qj, float mj, bool in,
+                                         const ForceArgs &a)
     {
         const float Ai = qi.z, ci = qi.w;
         const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
         const float r2 = dx * dx + dy * dy + dz * dz;
-        const float r = sqrtf(r2);
-        const float rinv = r > 0.f ? 1.f / r : 0.f;
-        const float hinv_j = 1.f / qj.x;
-        const float Fi = kCNorm * m4_df(r * hinv_i) * hinv4_i;
+        const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+        const float r = r2 * rinv;
+        const float hinv_j = __fdividef(1.f, qj.x);
         const float hinv2_j = hinv_j * hinv_j;
-        const float Fj = kCNorm * m4_df(r * hinv_j) * hinv2_j * hinv2_j;
+        const float Fi = m4_df_sel(r * hinv_i) * cf_i;
+        const float Fj = kCNorm * m4_df_sel(r * hinv_j) * hinv2_j * hinv2_j;
         const float vr = ((vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz) * rinv;
         const float avr = fabsf(vr);
         const float vsi = a.alpha * ci + a.beta * avr;
-        float avi = 0.f, avj = 0.f;
-        if (vr < 0.f) {
-            avi = -0.5f * vsi * vr;
-            avj = -0.5f * (a.alpha * qj.w + a.beta * avr) * vr;
-            duav += pj.w * vsi * vr * vr * Fi;
-        }
+        const float mu = vr < 0.f ? -0.5f * vr : 0.f;  // viscosity acts on approaching pairs
+        const float avi = mu * vsi;
+        const float avj = mu * (a.alpha * qj.w + a.beta * avr);
+        duav += mj * vsi * vr * (-2.f * mu) * Fi;
         const float Aj = qj.z;
-        const float coef = pj.w * (Ai * (pres_i + avi) * Fi + Aj * (a.gm1 * vj.w + avj) * Fj);
-        ax -= coef * dx * rinv;
-        ay -= coef * dy * rinv;
-        az -= coef * dz * rinv;
-        dup += pj.w * vr * Fi;
+        const float coef = mj * (Ai * (pres_i + avi) * Fi + Aj * (a.gm1 * vj.w + avj) * Fj);
+        const float cr = coef * rinv;
+        ax -= cr * dx;
+        ay -= cr * dy;
+        az -= cr * dz;
+        dup += mj * vr * Fi;
         const float Pj = a.gm1 * qj.y * vj.w;
-        const float vsu = sqrtf(fabsf(Pi - Pj) / (0.5f * (qi.y + qj.y)));
-        duc += pj.w * vsu * (vi.w - vj.w) * (Fi * Ai + Fj * Aj);
-        vsmax = fmaxf(vsmax, vsi);
-        ++cnt;
+        const float x = __fdividef(fabsf(Pi - Pj), 0.5f * (qi.y + qj.y));
+        const float vsu = x > 0.f ? x * rsqrtf(x) : 0.f;
+        duc += mj * vsu * (vi.w - vj.w) * (Fi * Ai + Fj * Aj);
+        vsmax = in ? fmaxf(vsmax, vsi) : vsmax;
+        cnt += in ? 1 : 0;
     }
 
     // reduce over the L lanes of each target; lane sub == 0 writes
@@ -166,15 +169,25 @@ __global__ void __launch_bounds__(kForceWarps * 32) force_list_kernel(ForceArgs 
             ForceTarget T;
             T.init(a.pos[i], a.vel[i], a.prop[i], a);
             const int *__restrict__ lst = a.nl_idx + (size_t)i * kNbrCap;
-            for (int e = sub; e < len; e += L) {
-                const int j = __ldg(lst + e);
-                if (j == i) continue;
+            // Two entries per iteration, no branch: an entry outside the pair
+            // set (or padding) gets zero mass.  The particle itself (r = 0) is
+            // left out; a distinct particle at r = 0 would add nothing either
+            // (every term carries f'(0) = 0 or v_ij.r_ij / r = 0).
+            auto entry = [&](int j, bool valid) {
                 const float4 pj = __ldg(&a.pos[j]);
                 const float4 qj = __ldg(&a.prop[j]);
+                const float4 vj = __ldg(&a.vel[j]);
                 const float r2 = canon_r2(T.xi.x, T.xi.y, T.xi.z, pj.x, pj.y, pj.z);
                 const float R = 2.0f * fmaxf(T.qi.x, qj.x);
-                if (!(r2 < R * R)) continue;
-                T.pair(pj, __ldg(&a.vel[j]), qj, a);
+                const bool in = valid && r2 > 0.f && r2 < R * R;
+                T.pair(pj, vj, qj, in ? pj.w : 0.f, in, a);
+            };
+            for (int e = sub; e < len; e += 2 * L) {
+                const bool two = e + L < len;
+                const int j0 = __ldcs(lst + e);
+                const int j1 = two ? __ldcs(lst + e + L) : j0;
+                entry(j0, true);
+                entry(j1, two);
             }
             T.finish(L, act && sub == 0, i, a);
             n_pairs += T.cnt;
@@ -237,7 +250,8 @@ __global__ void __launch_bounds__(kForceWarps * 32) force_walk_kernel(ForceArgs 
                     const int len = sm.tlen[t];
                     for (int e = sub; e < len; e += L) {
                         const int j = sm.ej[t][e];
-                        T.pair(__ldg(&a.pos[j]), __ldg(&a.vel[j]), __ldg(&a.prop[j]), a);
+                        const float4 pj = __ldg(&a.pos[j]);
+                        T.pair(pj, __ldg(&a.vel[j]), __ldg(&a.prop[j]), pj.w, true, a);
                     }
                 }
                 __syncwarp();

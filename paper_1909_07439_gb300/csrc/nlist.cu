@@ -1,34 +1,51 @@
 // Neighbour lists for the density and force passes.
 //
-// One tree walk per group (Sect. 3.2) finds, for every particle i, the
-// particles j with
+// For every particle i the list holds the particles j with
 //     r_ij < 2 (1 + pad) max(h_i, h_j)          (h at the start of the pass)
-// and stores them in i's fixed-size slot of nl_idx (curve order, walk order).
-// That set holds both pair sets of the step as long as no smoothing length
-// grows by more than the pad during the h-rho solve:
+// in i's fixed-size slot of nl_idx (curve order).  That set holds both pair
+// sets of the step as long as no smoothing length grows by more than the pad
+// during the h-rho solve:
 //   density (Eq. 1):       r_ij < 2 h_i,           h_i <= (1 + pad) h_i,in
 //   force   (Eqs. 9-15):   r_ij < 2 max(h_i, h_j), both h <= (1 + pad) h_in
 // so the density Newton sweeps and the force pass read lists instead of
 // walking; the few particles that leave the pad (and lists that overflow
-// kNbrCap) are handed to the walking kernels.
+// kNbrCap, or groups whose walk finds more than kSGLeaves leaves) are handed
+// to the walking kernels.
 //
-// The walk opens a node if its box is within max(reach of the batch,
-// 2 (1 + pad) h_max(node)) of the group box, so every j of the set is a
-// candidate.  Each 32-candidate chunk is tested against up to 16 targets
-// with the canonical FP32 squared distance (two targets per packed
-// instruction); hits go straight to the lists in global memory.
+// Candidates come from the group walk of Sect. 3.2: a leaf is opened for a
+// group if its box is within max(reach of the group, 2 (1 + pad) h_max(leaf))
+// of the group box.  Two kernels:
+//   leafwalk_kernel: runs of up to kSG consecutive groups of one instance with
+//     similar h share one tree walk for the union of their boxes and their
+//     largest h; the walk's leaves, in particle order, go to a pool in global
+//     memory.  A node that passes the opening test for a box passes it for
+//     any box containing it, so the list holds every leaf of every group of
+//     the run.  Memory-latency bound: many warps, 4 nodes per lane and step.
+//   nlist_kernel: each group picks its leaves from its run's list with its
+//     own test (so its candidates do not depend on which groups shared the
+//     walk) and tests each 32-candidate chunk against up to 16 targets with
+//     the canonical FP32 squared distance (two targets per packed
+//     instruction); hits go straight to the lists in global memory.
 #include "walk.cuh"
 
 namespace sph {
 
-constexpr int kNlTB = 16;       // targets per walk
+constexpr int kNlTB = 16;       // targets per candidate test batch
 constexpr int kNlWarps = 4;     // warps per block
+constexpr int kSG = 8;          // consecutive groups that may share one tree walk
+constexpr int kSGLeaves = 256;  // leaves one walk may find
+constexpr int kLWWide = 4;      // nodes per lane and walk step
+constexpr int kLWStack = 320;   // stack entries of a wide walk
+constexpr float kShareH = 2.f;  // groups share a walk if their h_max differ by less
 constexpr float kListSlack = 1.0f + 1e-5f;  // list radius margin over the FP32 pad checks
 
 struct NlistSmem {
-    WalkSmem w;
+    WalkSmemW<kLWWide, kLWStack> w;
+    int2 lv[kSGLeaves];        // walk output (node, first); then a group's leaves (first, count)
+    int leaves[kSGLeaves];     // the walk's leaves (nodes) in particle order
+    int2 runs[kMaxRuns + 1];   // a group's candidate runs: (first particle, first slot), sentinel
     TargetPairs<kNlTB> tc;
-    float tr[kNlTB];  // list radius factor x h_i (0 for unused slots)
+    float tr[kNlTB];           // list radius factor x h_i (0 for unused slots)
 };
 
 struct NlistArgs {
@@ -41,12 +58,91 @@ struct NlistArgs {
     WalkTree tree;
     const int *inst;
     float rscale;  // list radius = rscale * max(h_i, h_j)
-    int *idx, *len;
+    int *idx;
+    int *len;
     int *err;
     unsigned long long *counters;
 };
 
-__global__ void __launch_bounds__(kNlWarps * 32) nlist_kernel(NlistArgs a)
+// Walk for the box [blo, bhi] (h_max blo.w) and put the leaves, in particle
+// order, in sm.leaves.  Returns their number, or -1 if more than kSGLeaves.
+__device__ __forceinline__ int walk_sorted(const NlistArgs &a, NlistSmem &sm, int root, float4 blo,
+                                           float4 bhi)
+{
+    const int lane = threadIdx.x & 31;
+    const int n = walk_leaves_wide(a.tree, root, blo, bhi, 0.5f * (a.rscale * blo.w), 0.5f * a.rscale,
+                                   sm.w, sm.lv, kSGLeaves);
+    __syncwarp();
+    // rank sort by first particle (leaves hold disjoint particle ranges)
+    for (int k0 = 0; k0 < n; k0 += 32) {
+        const int k = k0 + lane;
+        const int2 me = k < n ? sm.lv[k] : make_int2(-1, 0x7fffffff);
+        int rank = 0;
+        for (int m = 0; m < n; ++m) rank += sm.lv[m].y < me.y ? 1 : 0;
+        if (k < n) sm.leaves[rank] = me.x;
+    }
+    __syncwarp();
+    return n;
+}
+
+// The group's candidates: the leaves of sm.leaves that pass the group's own
+// opening test (the test of walk_step for the group box and hgroup = rscale
+// h_max(group) / 2), in particle order, merged into maximal contiguous runs
+// of particles numbered by slot: sm.runs[m] = (first particle, first slot),
+// sm.runs[nrun] = (-1, number of slots).  A node that passes the test for a
+// box passes it for any box containing it, so when sm.leaves comes from a
+// walk shared with other groups (union box, largest h) the result is the same
+// as for the group's own walk.  Returns nrun, or -1 if more than max_runs.
+__device__ __forceinline__ int group_candidates(const NlistArgs &a, NlistSmem &sm, int nleaf,
+                                                float4 glo, float4 ghi, int max_runs)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lane_lt();
+    const float hgroup = 0.5f * (a.rscale * glo.w), node_scale = 0.5f * a.rscale;
+    int nsel = 0;
+    for (int k0 = 0; k0 < nleaf; k0 += 32) {
+        const int k = k0 + lane;
+        const int node = k < nleaf ? sm.leaves[k] : -1;
+        bool open = false;
+        int2 ref = make_int2(0, 0);
+        if (node >= 0) {
+            const float4 lo = __ldg(&a.tree.node_lo[node]);
+            const float4 hi = __ldg(&a.tree.node_hi[node]);
+            ref = __ldg(&a.tree.node_ref[node]);
+            const float d2 = box_dist2(glo, ghi, lo, hi);
+            const float R = 2.0f * fmaxf(hgroup, lo.w * node_scale);
+            open = d2 < R * R * kOpenSlack;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, open);
+        __syncwarp();
+        if (open) sm.lv[nsel + __popc(m & lt)] = ref;
+        nsel += __popc(m);
+    }
+    __syncwarp();
+    // merge: a leaf starts a run unless its particles continue the previous one's
+    int nrun = 0, slot = 0;
+    for (int k0 = 0; k0 < nsel; k0 += 32) {
+        const int k = k0 + lane;
+        const bool valid = k < nsel;
+        const int2 cur = valid ? sm.lv[k] : make_int2(0, 0);
+        const bool st = valid && (k == 0 || sm.lv[k - 1].x + sm.lv[k - 1].y != cur.x);
+        const unsigned bst = __ballot_sync(0xffffffffu, st);
+        int inc = cur.y;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const int p = nrun + __popc(bst & lt);
+        if (st && p < max_runs) sm.runs[p] = make_int2(cur.x, slot + inc - cur.y);
+        nrun += __popc(bst);
+        slot += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    if (lane == 0 && nrun <= max_runs) sm.runs[nrun] = make_int2(-1, slot);
+    __syncwarp();
+    return nrun <= max_runs ? nrun : -1;
+}
+
+__global__ void __launch_bounds__(kNlWarps * 32, 5) nlist_kernel(NlistArgs a)
 {
     __shared__ NlistSmem smv[kNlWarps];
     NlistSmem &sm = smv[threadIdx.x >> 5];
@@ -56,70 +152,109 @@ __global__ void __launch_bounds__(kNlWarps * 32) nlist_kernel(NlistArgs a)
     unsigned long long n_cand = 0, n_entries = 0, n_over = 0;
 
     while (true) {
-        int g = 0;
-        if (lane == 0) g = atomicAdd(a.work, 1);
-        g = __shfl_sync(0xffffffffu, g, 0);
-        if (g >= ng) break;
-        const int2 gr = a.grp_ref[g];
-        const float4 glo = a.grp_lo[g], ghi = a.grp_hi[g];
-        const int root = a.inst ? a.inst[gr.x] : 0;
-        for (int b0 = 0; b0 < gr.y; b0 += kNlTB) {
-            const int nt = min(kNlTB, gr.y - b0);
-            const int i0 = gr.x + b0;
-            float rt = 0.f;
-            if (lane < kNlTB) {
-                const float4 p = lane < nt ? a.pos[i0 + lane] : make_float4(1e30f, 1e30f, 1e30f, 0.f);
-                sm.tc.set(lane, p);
-                rt = lane < nt ? a.rscale * a.h[i0 + lane] : 0.f;
-                sm.tr[lane] = rt;
+        int sg = 0;
+        if (lane == 0) sg = atomicAdd(a.work, 1);
+        sg = __shfl_sync(0xffffffffu, sg, 0);
+        const int gf = sg * kSG;
+        if (gf >= ng) break;
+        const int sgn = min(kSG, ng - gf);
+        const bool have = lane < sgn;
+        const int2 grl = have ? a.grp_ref[gf + lane] : make_int2(0, 0);
+        const float4 glol = have ? a.grp_lo[gf + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 ghil = have ? a.grp_hi[gf + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int ins = a.inst && have ? a.inst[grl.x] : 0;
+        // a group starts a new run unless it is of the same instance as the
+        // previous one and their h_max agree within kShareH
+        const int ins_p = __shfl_up_sync(0xffffffffu, ins, 1);
+        const float hm_p = __shfl_up_sync(0xffffffffu, glol.w, 1);
+        const bool starts = have && (lane == 0 || ins != ins_p || glol.w > kShareH * hm_p ||
+                                     hm_p > kShareH * glol.w);
+        const unsigned bstart = __ballot_sync(0xffffffffu, starts);
+        for (int s = 0; s < sgn;) {
+            const unsigned later = bstart & ~((2u << s) - 1u);  // starts after s
+            const int e = later ? min(__ffs(later) - 1, sgn) : sgn;
+            const bool mine = lane >= s && lane < e;
+            float4 ulo = mine ? glol : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+            float4 uhi = mine ? ghil : make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
+            for (int o = 16; o > 0; o >>= 1) {
+                ulo.x = fminf(ulo.x, __shfl_xor_sync(0xffffffffu, ulo.x, o));
+                ulo.y = fminf(ulo.y, __shfl_xor_sync(0xffffffffu, ulo.y, o));
+                ulo.z = fminf(ulo.z, __shfl_xor_sync(0xffffffffu, ulo.z, o));
+                ulo.w = fmaxf(ulo.w, __shfl_xor_sync(0xffffffffu, ulo.w, o));  // h_max
+                uhi.x = fmaxf(uhi.x, __shfl_xor_sync(0xffffffffu, uhi.x, o));
+                uhi.y = fmaxf(uhi.y, __shfl_xor_sync(0xffffffffu, uhi.y, o));
+                uhi.z = fmaxf(uhi.z, __shfl_xor_sync(0xffffffffu, uhi.z, o));
             }
-            for (int o = 16; o > 0; o >>= 1) rt = fmaxf(rt, __shfl_xor_sync(0xffffffffu, rt, o));
-            __syncwarp();
-            int len[kNlTB];
-#pragma unroll
-            for (int tt = 0; tt < kNlTB; ++tt) len[tt] = 0;
-            auto chunk = [&](int j) {
-                const float4 pj = j >= 0 ? __ldg(&a.pos[j]) : make_float4(0.f, 0.f, 0.f, 0.f);
-                const float rj = j >= 0 ? a.rscale * __ldg(&a.h[j]) : 0.f;
-#pragma unroll
-                for (int q = 0; q < kNlTB / 2; ++q) {
-                    const int t0 = 2 * q, t1 = t0 + 1;
-                    if (t0 < nt) {
-                        const float2 r2 = canon_r2_x2(sm.tc.x[q], sm.tc.y[q], sm.tc.z[q], pj.x, pj.y, pj.z);
-                        const float R0 = fmaxf(sm.tr[t0], rj), R1 = fmaxf(sm.tr[t1], rj);
-                        const bool hit0 = j >= 0 && r2.x < R0 * R0;
-                        const bool hit1 = j >= 0 && t1 < nt && r2.y < R1 * R1;
-                        const unsigned m0 = __ballot_sync(0xffffffffu, hit0);
-                        const unsigned m1 = __ballot_sync(0xffffffffu, hit1);
-                        if (hit0) {
-                            const int e = len[t0] + __popc(m0 & lt);
-                            if (e < kNbrCap) a.idx[(size_t)(i0 + t0) * kNbrCap + e] = j;
-                        }
-                        if (hit1) {
-                            const int e = len[t1] + __popc(m1 & lt);
-                            if (e < kNbrCap) a.idx[(size_t)(i0 + t1) * kNbrCap + e] = j;
-                        }
-                        len[t0] += __popc(m0);
-                        len[t1] += __popc(m1);
+            const int root = __shfl_sync(0xffffffffu, ins, s);
+            // one walk for the run; if its leaves do not fit, one walk per group,
+            // so whether a group gets lists depends on the group alone
+            const int nshared = walk_sorted(a, sm, root, ulo, uhi);
+            for (int gi = s; gi < e; ++gi) {
+                const int g = gf + gi;
+                const int2 gr = a.grp_ref[g];
+                const float4 glo = a.grp_lo[g], ghi = a.grp_hi[g];
+                const int nleaf = nshared >= 0 || e - s == 1 ? nshared : walk_sorted(a, sm, root, glo, ghi);
+                const int nrun = nleaf >= 0 ? group_candidates(a, sm, nleaf, glo, ghi, kMaxRuns) : -1;
+                const bool ok = nrun >= 0;
+                const int ncand = ok ? sm.runs[nrun].y : 0;
+                for (int b0 = 0; b0 < gr.y; b0 += kNlTB) {
+                    const int nt = min(kNlTB, gr.y - b0);
+                    const int i0 = gr.x + b0;
+                    if (lane < kNlTB) {
+                        const float4 p = lane < nt ? a.pos[i0 + lane] : make_float4(1e30f, 1e30f, 1e30f, 0.f);
+                        sm.tc.set(lane, p);
+                        sm.tr[lane] = lane < nt ? a.rscale * a.h[i0 + lane] : 0.f;
                     }
-                }
-                n_cand += (unsigned long long)(nt * __popc(__ballot_sync(0xffffffffu, j >= 0)));
-            };
-            // open a node within max(rt, rscale h_max(node)) of the group box
-            const bool ok = walk_group(a.tree, root, glo, ghi, 0.f, true, 0.5f * rt, sm.w, chunk,
-                                       0.5f * a.rscale);
-            if (!ok && lane == 0) raise_error(a.err, SPH_ERR_TILE_OVERFLOW);
-            int mine = 0;
+                    __syncwarp();
+                    int len[kNlTB];
 #pragma unroll
-            for (int tt = 0; tt < kNlTB; ++tt)
-                if (lane == tt) mine = len[tt];
-            const bool fits = ok && mine <= kNbrCap;
-            if (lane < nt) {
-                a.len[i0 + lane] = fits ? mine : -1;
-                n_entries += (unsigned long long)min(mine, kNbrCap);
-                n_over += fits ? 0ull : 1ull;
+                    for (int tt = 0; tt < kNlTB; ++tt) len[tt] = 0;
+                    // chunks of 32 candidate slots, one per lane
+                    int r = 0;
+                    for (int c0 = 0; c0 < ncand; c0 += 32) {
+                        const int k = c0 + lane;
+                        const int j = k < ncand ? slot_particle(sm.runs, r, k) : -1;
+                        const float4 pj = j >= 0 ? __ldg(&a.pos[j]) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        const float rj = j >= 0 ? a.rscale * __ldg(&a.h[j]) : 0.f;
+#pragma unroll
+                        for (int q = 0; q < kNlTB / 2; ++q) {
+                            const int t0 = 2 * q, t1 = t0 + 1;
+                            if (t0 < nt) {
+                                const float2 r2 = canon_r2_x2(sm.tc.x[q], sm.tc.y[q], sm.tc.z[q], pj.x, pj.y, pj.z);
+                                const float R0 = fmaxf(sm.tr[t0], rj), R1 = fmaxf(sm.tr[t1], rj);
+                                const bool hit0 = j >= 0 && r2.x < R0 * R0;
+                                const bool hit1 = j >= 0 && t1 < nt && r2.y < R1 * R1;
+                                const unsigned m0 = __ballot_sync(0xffffffffu, hit0);
+                                const unsigned m1 = __ballot_sync(0xffffffffu, hit1);
+                                if (hit0) {
+                                    const int e2 = len[t0] + __popc(m0 & lt);
+                                    if (e2 < kNbrCap) a.idx[(size_t)(i0 + t0) * kNbrCap + e2] = j;
+                                }
+                                if (hit1) {
+                                    const int e2 = len[t1] + __popc(m1 & lt);
+                                    if (e2 < kNbrCap) a.idx[(size_t)(i0 + t1) * kNbrCap + e2] = j;
+                                }
+                                len[t0] += __popc(m0);
+                                len[t1] += __popc(m1);
+                            }
+                        }
+                        n_cand += (unsigned long long)(nt * __popc(__ballot_sync(0xffffffffu, j >= 0)));
+                    }
+                    int mlen = 0;
+#pragma unroll
+                    for (int tt = 0; tt < kNlTB; ++tt)
+                        if (lane == tt) mlen = len[tt];
+                    // a group without lists is left to the walking kernels
+                    const bool fits = ok && mlen <= kNbrCap;
+                    if (lane < nt) {
+                        a.len[i0 + lane] = fits ? mlen : -1;
+                        n_entries += (unsigned long long)min(mlen, kNbrCap);
+                        n_over += fits ? 0ull : 1ull;
+                    }
+                    __syncwarp();
+                }
             }
-            __syncwarp();
+            s = e;
         }
     }
     for (int o = 16; o > 0; o >>= 1) {

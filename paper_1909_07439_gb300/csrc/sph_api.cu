@@ -272,7 +272,8 @@ void sph_destroy(sph_ctx *h)
                     c.tree.node_nchild, c.tree.node_parent, c.tree.node_arrive, c.tree.node_lo,
                     c.tree.node_hi, c.tree.node_ref, c.tree.level_start, c.tree.grp_ref,
                     c.tree.grp_lo, c.tree.grp_hi, c.tree.lv_tree, c.tree.lv_grp, c.tree.blk_cnt,
-                    c.nl_idx, c.nl_len, c.fallback, c.tree.rec_ctl, c.tree.rec_bad,
+                    c.nl_idx, c.nl_len, c.fallback,
+                    c.tree.rec_ctl, c.tree.rec_bad,
                     c.prop, c.vhalf, c.inst, c.bbox_inst, c.dtmin_inst,
                     c.bbox, c.scan_part, c.red_f, c.red_d, c.d_err, c.d_counters,
                     c.d_sizes, c.mirror.pos, c.mirror.vel, c.mirror.acc, c.mirror.h, c.mirror.rho,

@@ -17,6 +17,7 @@ constexpr int kLevels = 22;          // levels 0..21
 constexpr int kWarp = 32;
 constexpr int kMaxInstances = 65536;  // instances in one batch
 constexpr int kNbrCap = 128;          // neighbour-list entries per particle
+constexpr int kMaxRuns = 256;         // candidate runs of one group (plus a sentinel)
 constexpr float kCNorm = 0.318309886183790671538f;  // M4, 3D: 1/pi
 
 // stage ids for the per-stage timers
@@ -102,7 +103,7 @@ struct Ctx {
     Tree tree;
 
     // Neighbour lists (curve order): particle i owns nl_idx[i * kNbrCap ...],
-    // nl_len[i] entries, -1 if they did not fit.  Entry j is in i's list if
+    // nl_len[i] entries (-1: none).  Entry j is in i's list if
     // r_ij < 2 (1 + pad) max(h_i, h_j) at the h the density pass started from.
     int *nl_idx = nullptr;
     int *nl_len = nullptr;

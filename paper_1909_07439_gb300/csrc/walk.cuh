@@ -80,19 +80,74 @@ __device__ __forceinline__ float box_dist2(float4 alo, float4 ahi, float4 blo, f
     return dx * dx + dy * dy + dz * dz;
 }
 
+// One step of a walk: pop whole stack entries from the top (at most 32
+// nodes), test the nodes one per lane, and push the child ranges of opened
+// internal nodes.  On return this lane's opened leaf, if any, is in
+// (leaf = true, ref = (first, count), node).  Sets ok = false if the stack
+// overflowed.
+//   force_mode = false: open a node if dist < sqrt(reach2 / kOpenSlack)
+//   force_mode = true : open a node if dist < 2 max(hgroup, node_scale h_max(node))
+__device__ __forceinline__ void walk_step(const WalkTree &T, float4 glo, float4 ghi, float reach2,
+                                          bool force_mode, float hgroup, float node_scale,
+                                          WalkSmem &sm, int &sp, bool &ok, bool &leaf, int2 &ref,
+                                          int &node)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lane_lt();
+    int2 e = lane < sp ? sm.stk[sp - 1 - lane] : make_int2(0, 0);
+    int sz = lane < sp ? e.y : 0;
+    int inc = sz;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    unsigned take = __ballot_sync(0xffffffffu, lane < sp && inc <= 32);
+    int k = __popc(take);
+    int total = __shfl_sync(0xffffffffu, inc, k - 1);
+    if (lane < k)
+        for (int q = 0, ex = inc - sz; q < sz; ++q) sm.nodes[ex + q] = e.x + q;
+    sp -= k;
+    __syncwarp();
+    node = lane < total ? sm.nodes[lane] : -1;
+    __syncwarp();
+    bool open = false;
+    leaf = false;
+    ref = make_int2(0, 0);
+    if (node >= 0) {
+        float4 lo = __ldg(&T.node_lo[node]);
+        float4 hi = __ldg(&T.node_hi[node]);
+        ref = __ldg(&T.node_ref[node]);
+        float d2 = box_dist2(glo, ghi, lo, hi);
+        float r2 = reach2;
+        if (force_mode) {
+            float R = 2.0f * fmaxf(hgroup, lo.w * node_scale);
+            r2 = R * R * kOpenSlack;
+        }
+        open = d2 < r2;
+        leaf = ref.y >= 0;
+    }
+    unsigned bint = __ballot_sync(0xffffffffu, open && !leaf);
+    if (open && !leaf) {
+        int p = sp + __popc(bint & lt);
+        if (p < kStack) sm.stk[p] = make_int2(ref.x, -ref.y);
+    }
+    sp += __popc(bint);
+    if (sp > kStack) {
+        ok = false;
+        sp = kStack;
+    }
+    leaf = open && leaf;
+}
+
 // Walk the tree below node `root` for a group with box [glo, ghi].
 //   force_mode = false: open a node if dist < reach (reach = 2 * padded h of the group)
-//   force_mode = true : open a node if dist < 2 max(h_group, h_max(node))
+//   force_mode = true : open a node if dist < 2 max(h_group, node_scale h_max(node))
 // chunk(j): called warp-uniformly with this lane's candidate j (-1: none).
 // Returns false if the stack overflowed (results then incomplete).
-// Opened leaves are appended, in order, to rec[0 .. *rec_n) when rec is
-// given (*rec_n = -1 once more than rec_cap were opened).  In force mode a
-// node's h_max is scaled by node_scale.
 template <class ChunkFn>
 __device__ bool walk_group(const WalkTree &T, int root, float4 glo, float4 ghi, float reach,
                            bool force_mode, float hgroup, WalkSmem &sm, ChunkFn &&chunk,
-                           float node_scale = 1.f, int2 *rec = nullptr, int *rec_n = nullptr,
-                           int rec_cap = 0)
+                           float node_scale = 1.f)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = lane_lt();
@@ -104,66 +159,14 @@ __device__ bool walk_group(const WalkTree &T, int root, float4 glo, float4 ghi, 
     __syncwarp();
     while (sp > 0 || pending > 0) {
         if (sp > 0) {
-            // pop whole entries from the top, at most 32 nodes
-            int2 e = lane < sp ? sm.stk[sp - 1 - lane] : make_int2(0, 0);
-            int sz = lane < sp ? e.y : 0;
-            int inc = sz;
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o) inc += y;
-            }
-            unsigned take = __ballot_sync(0xffffffffu, lane < sp && inc <= 32);
-            int k = __popc(take);
-            int total = __shfl_sync(0xffffffffu, inc, k - 1);
-            if (lane < k)
-                for (int q = 0, ex = inc - sz; q < sz; ++q) sm.nodes[ex + q] = e.x + q;
-            sp -= k;
-            __syncwarp();
-            int node = lane < total ? sm.nodes[lane] : -1;
-            __syncwarp();
-            bool open = false, leaf = false;
-            int2 ref = make_int2(0, 0);
-            if (node >= 0) {
-                float4 lo = __ldg(&T.node_lo[node]);
-                float4 hi = __ldg(&T.node_hi[node]);
-                ref = __ldg(&T.node_ref[node]);
-                float d2 = box_dist2(glo, ghi, lo, hi);
-                float r2 = reach2;
-                if (force_mode) {
-                    float R = 2.0f * fmaxf(hgroup, lo.w * node_scale);
-                    r2 = R * R * kOpenSlack;
-                }
-                open = d2 < r2;
-                leaf = ref.y >= 0;
-            }
-            unsigned bint = __ballot_sync(0xffffffffu, open && !leaf);
-            if (open && !leaf) {
-                int p = sp + __popc(bint & lt);
-                if (p < kStack) sm.stk[p] = make_int2(ref.x, -ref.y);
-            }
-            sp += __popc(bint);
-            if (sp > kStack) {
-                ok = false;
-                sp = kStack;
-            }
-            unsigned bleaf = __ballot_sync(0xffffffffu, open && leaf);
-            if (open && leaf) sm.rq[(rq_tail + __popc(bleaf & lt)) % kRQ] = ref;
-            if (rec) {
-                int nr = *rec_n;
-                if (nr >= 0) {
-                    if (nr + __popc(bleaf) > rec_cap) {
-                        nr = -1;
-                    } else {
-                        if (open && leaf) rec[nr + __popc(bleaf & lt)] = ref;
-                        nr += __popc(bleaf);
-                    }
-                }
-                __syncwarp();
-                if (lane == 0) *rec_n = nr;
-                __syncwarp();
-            }
+            bool leaf;
+            int2 ref;
+            int node;
+            walk_step(T, glo, ghi, reach2, force_mode, hgroup, node_scale, sm, sp, ok, leaf, ref, node);
+            unsigned bleaf = __ballot_sync(0xffffffffu, leaf);
+            if (leaf) sm.rq[(rq_tail + __popc(bleaf & lt)) % kRQ] = ref;
             rq_tail += __popc(bleaf);
-            pending += warp_sum_i(open && leaf ? ref.y : 0);
+            pending += warp_sum_i(leaf ? ref.y : 0);
             __syncwarp();
         }
         // hand out full chunks; the tail too once the stack is empty
@@ -194,30 +197,148 @@ __device__ bool walk_group(const WalkTree &T, int root, float4 glo, float4 ghi, 
     return ok;
 }
 
-// Hand the particles of recorded leaf ranges (global, in walk order) to
-// chunk() in 32-particle chunks, as walk_group would.
+// Walk the tree below `root` for the box [glo, ghi] in force mode and store
+// every opened leaf as (node, first particle) in out[0 .. cap).  Returns the
+// number of leaves, or -1 if they did not fit or the stack overflowed.
+__device__ __forceinline__ int walk_leaves(const WalkTree &T, int root, float4 glo, float4 ghi,
+                                           float hgroup, float node_scale, WalkSmem &sm, int2 *out,
+                                           int cap)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lane_lt();
+    bool ok = true;
+    int sp = 1, nout = 0;
+    if (lane == 0) sm.stk[0] = make_int2(root, 1);
+    __syncwarp();
+    while (sp > 0) {
+        bool leaf;
+        int2 ref;
+        int node;
+        walk_step(T, glo, ghi, 0.f, true, hgroup, node_scale, sm, sp, ok, leaf, ref, node);
+        const unsigned bleaf = __ballot_sync(0xffffffffu, leaf);
+        if (leaf) {
+            const int p = nout + __popc(bleaf & lt);
+            if (p < cap) out[p] = make_int2(node, ref.x);
+        }
+        nout += __popc(bleaf);
+        __syncwarp();
+    }
+    return ok && nout <= cap ? nout : -1;
+}
+
+// Shared memory of a wide walk: W nodes per lane and step.
+template <int W, int STK>
+struct WalkSmemW {
+    int2 stk[STK];
+    int nodes[32 * W];
+};
+
+// walk_leaves with W nodes tested per lane and step (fewer, wider steps: the
+// node loads of a step are independent, so a step costs about one memory
+// latency whatever W is).  Same opening test and result set as walk_leaves;
+// the order of `out` differs.
+template <int W, int STK>
+__device__ __forceinline__ int walk_leaves_wide(const WalkTree &T, int root, float4 glo, float4 ghi,
+                                                float hgroup, float node_scale, WalkSmemW<W, STK> &sm,
+                                                int2 *out, int cap)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lane_lt();
+    bool ok = true;
+    int sp = 1, nout = 0;
+    if (lane == 0) sm.stk[0] = make_int2(root, 1);
+    __syncwarp();
+    while (sp > 0) {
+        // pop whole entries from the top, at most 32 W nodes
+        const int2 e = lane < sp ? sm.stk[sp - 1 - lane] : make_int2(0, 0);
+        const int sz = lane < sp ? e.y : 0;
+        int inc = sz;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        const unsigned take = __ballot_sync(0xffffffffu, lane < sp && inc <= 32 * W);
+        const int k = __popc(take);
+        const int total = __shfl_sync(0xffffffffu, inc, k - 1);
+        if (lane < k)
+            for (int q = 0, ex = inc - sz; q < sz; ++q) sm.nodes[ex + q] = e.x + q;
+        sp -= k;
+        __syncwarp();
+        int node[W];
+        float4 lo[W], hi[W];
+        int2 ref[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            node[w] = w * 32 + lane < total ? sm.nodes[w * 32 + lane] : -1;
+            lo[w] = hi[w] = make_float4(0.f, 0.f, 0.f, 0.f);
+            ref[w] = make_int2(0, 0);
+            if (node[w] >= 0) {
+                lo[w] = __ldg(&T.node_lo[node[w]]);
+                hi[w] = __ldg(&T.node_hi[node[w]]);
+                ref[w] = __ldg(&T.node_ref[node[w]]);
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            bool open = false;
+            if (node[w] >= 0) {
+                const float d2 = box_dist2(glo, ghi, lo[w], hi[w]);
+                const float R = 2.0f * fmaxf(hgroup, lo[w].w * node_scale);
+                open = d2 < R * R * kOpenSlack;
+            }
+            const bool leaf = open && ref[w].y >= 0, inner = open && ref[w].y < 0;
+            const unsigned bint = __ballot_sync(0xffffffffu, inner);
+            if (inner) {
+                const int p = sp + __popc(bint & lt);
+                if (p < STK) sm.stk[p] = make_int2(ref[w].x, -ref[w].y);
+            }
+            sp += __popc(bint);
+            if (sp > STK) {
+                ok = false;
+                sp = STK;
+            }
+            const unsigned bleaf = __ballot_sync(0xffffffffu, leaf);
+            if (leaf) {
+                const int p = nout + __popc(bleaf & lt);
+                if (p < cap) out[p] = make_int2(node[w], ref[w].x);
+            }
+            nout += __popc(bleaf);
+        }
+        __syncwarp();
+    }
+    return ok && nout <= cap ? nout : -1;
+}
+
+// Candidate slots of a group: runs[m] = (first particle, first slot) for
+// m < nrun and runs[nrun] = (-1, number of candidates).  Slot k belongs to the
+// run r with runs[r].y <= k < runs[r + 1].y; r only moves forward, so a lane
+// visiting ascending slots keeps its r between calls.
+__device__ __forceinline__ int slot_particle(const int2 *runs, int &r, int k)
+{
+    while (runs[r + 1].y <= k) ++r;
+    return runs[r].x + (k - runs[r].y);
+}
+
+// Hand the particles of the runs (first, count) in shared memory to chunk()
+// in 32-particle chunks, as walk_group would.
 template <class ChunkFn>
-__device__ void replay_ranges(const int2 *__restrict__ ranges, int count, ChunkFn &&chunk)
+__device__ __forceinline__ void chunk_runs(const int2 *runs, int count, ChunkFn &&chunk)
 {
     const int lane = threadIdx.x & 31;
     int filled = 0, myj = -1;
-    for (int b = 0; b < count; b += 32) {
-        const int2 mine = b + lane < count ? __ldg(&ranges[b + lane]) : make_int2(0, 0);
-        const int nb = min(32, count - b);
-        for (int k = 0; k < nb; ++k) {
-            const int first = __shfl_sync(0xffffffffu, mine.x, k);
-            const int cnt = __shfl_sync(0xffffffffu, mine.y, k);
-            int off = 0;
-            while (off < cnt) {
-                const int take = min(cnt - off, 32 - filled);
-                if (lane >= filled && lane < filled + take) myj = first + off + (lane - filled);
-                filled += take;
-                off += take;
-                if (filled == 32) {
-                    chunk(myj);
-                    filled = 0;
-                    myj = -1;
-                }
+    for (int k = 0; k < count; ++k) {
+        const int2 r = runs[k];
+        int off = 0;
+        while (off < r.y) {
+            const int take = min(r.y - off, 32 - filled);
+            if (lane >= filled && lane < filled + take) myj = r.x + off + (lane - filled);
+            filled += take;
+            off += take;
+            if (filled == 32) {
+                chunk(myj);
+                filled = 0;
+                myj = -1;
             }
         }
     }
