@@ -27,6 +27,7 @@ namespace sph {
 constexpr int kTB = 8;           // targets per batch
 constexpr int kDensWarps = 4;    // warps per block
 constexpr float kPad = 0.03f;    // padded list radius, relative to h
+constexpr int kRound = 2;        // groups per warp per work grab of the list kernel
 
 template <int CAP>
 struct DensSmem {
@@ -154,87 +155,97 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_list_kernel(DensArgs 
     const bool fixed = a.fixed_iters > 0;
     const int limit = fixed ? a.fixed_iters : a.max_iter;
     unsigned long long n_pairs = 0, n_newton = 0;
+    // The block takes kRound consecutive groups per warp at a time, warp w the
+    // groups base + w + kDensWarps k: the warps of a block work on neighbouring
+    // groups together and share their candidates in L1.
+    __shared__ int s_base;
+    const int warp = threadIdx.x >> 5;
 
     while (true) {
-        int g = 0;
-        if (lane == 0) g = atomicAdd(a.work, 1);
-        g = __shfl_sync(0xffffffffu, g, 0);
-        if (g >= ng) break;
-        const int2 gr = a.grp_ref[g];
-        for (int b0 = 0; b0 < gr.y; b0 += kTB) {
-            const int nt = min(kTB, gr.y - b0);
-            const int L = nt > 4 ? 4 : nt > 2 ? 8 : nt > 1 ? 16 : 32;
-            const int t = lane / L, sub = lane % L;
-            const bool act = t < nt;
-            const int i = gr.x + b0 + (act ? t : 0);
-            const int len = act ? a.nl_len[i] : 0;
-            if (__any_sync(0xffffffffu, len < 0)) {  // no list (overflow, or too many leaves)
-                push_fallback(a, g, b0);
-                continue;
+        if (threadIdx.x == 0) s_base = atomicAdd(a.work, kDensWarps * kRound);
+        __syncthreads();
+        const int base = s_base;
+        __syncthreads();
+        if (base >= ng) break;
+        for (int kr = 0; kr < kRound; ++kr) {
+            const int g = base + warp + kDensWarps * kr;
+            if (g >= ng) break;
+            const int2 gr = a.grp_ref[g];
+            for (int b0 = 0; b0 < gr.y; b0 += kTB) {
+                const int nt = min(kTB, gr.y - b0);
+                const int L = nt > 4 ? 4 : nt > 2 ? 8 : nt > 1 ? 16 : 32;
+                const int t = lane / L, sub = lane % L;
+                const bool act = t < nt;
+                const int i = gr.x + b0 + (act ? t : 0);
+                const int len = act ? a.nl_len[i] : 0;
+                if (__any_sync(0xffffffffu, len < 0)) {  // no list (overflow, or too many leaves)
+                    push_fallback(a, g, b0);
+                    continue;
+                }
+                const int *__restrict__ lst = a.nl_idx + (size_t)i * kNbrCap;
+                const float4 xi = a.pos[i], vi = a.vel[i];
+                float h = a.h[i];
+                const float hw = h * a.h_in_scale;  // the lists hold every pair with r < 2 hw
+                const float M = xi.w * hf3;
+                float hlo = 0.f, hhi = INFINITY;
+                bool conv = !act, outside = false, final_pass = false;
+                int it = 0;
+                float s0, s1, s2;
+                while (true) {
+                    s0 = 0.f; s1 = 0.f; s2 = 0.f;
+                    int cnt = 0;
+                    const float hinv = 1.f / h;
+                    const float R = 2.f * h;
+                    const float R2 = R * R;
+                    // Two entries per iteration, no branch on the distance: f and
+                    // f' vanish for q >= 2, so entries beyond 2 h add nothing.  A
+                    // missing second entry repeats the first with zero mass.
+                    auto entry = [&](float4 pj, float4 vj, float mj) {
+                        const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
+                        const float r2 = dx * dx + dy * dy + dz * dz;
+                        const float vd = (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz;
+                        cnt += (mj > 0.f && r2 < R2) ? 1 : 0;
+                        pair_sums(r2, mj, vd, hinv, s0, s1, s2);
+                    };
+                    for (int e = sub; e < len; e += 2 * L) {
+                        const bool two = e + L < len;
+                        const int j0 = __ldcs(lst + e);
+                        const int j1 = two ? __ldcs(lst + e + L) : j0;
+                        const float4 p0 = __ldg(&a.pos[j0]), p1 = __ldg(&a.pos[j1]);
+                        const float4 v0 = __ldg(&a.vel[j0]), v1 = __ldg(&a.vel[j1]);
+                        entry(p0, v0, p0.w);
+                        entry(p1, v1, two ? p1.w : 0.f);
+                    }
+                    s0 = seg_sum(s0, L);
+                    s1 = seg_sum(s1, L);
+                    s2 = seg_sum(s2, L);
+                    const float cf = seg_sum((float)cnt, L);
+                    if (sub == 0 && act) {
+                        n_pairs += (unsigned long long)cf;
+                        ++n_newton;
+                    }
+                    if (final_pass) break;
+                    if (act && !conv) {
+                        newton_update(h, hlo, hhi, conv, s0, s1, M, fixed, a.tol);
+                        outside = h > hw;
+                    }
+                    ++it;
+                    if (__any_sync(0xffffffffu, outside)) break;  // the lists no longer cover h
+                    if (fixed) {
+                        if (it >= limit) final_pass = true;   // one more sweep at the last h
+                    } else if (__all_sync(0xffffffffu, conv)) {
+                        break;                                // every target's sums are at its h
+                    } else if (it >= limit) {
+                        if (lane == 0) raise_error(a.err, SPH_ERR_NOT_CONVERGED);
+                        final_pass = true;
+                    }
+                }
+                if (__any_sync(0xffffffffu, outside)) {  // start the batch over with walks
+                    push_fallback(a, g, b0);
+                    continue;
+                }
+                if (act && sub == 0) density_outputs(a, i, h, M, s1, s2, vi.w);
             }
-            const int *__restrict__ lst = a.nl_idx + (size_t)i * kNbrCap;
-            const float4 xi = a.pos[i], vi = a.vel[i];
-            float h = a.h[i];
-            const float hw = h * a.h_in_scale;  // the lists hold every pair with r < 2 hw
-            const float M = xi.w * hf3;
-            float hlo = 0.f, hhi = INFINITY;
-            bool conv = !act, outside = false, final_pass = false;
-            int it = 0;
-            float s0, s1, s2;
-            while (true) {
-                s0 = 0.f; s1 = 0.f; s2 = 0.f;
-                int cnt = 0;
-                const float hinv = 1.f / h;
-                const float R = 2.f * h;
-                const float R2 = R * R;
-                // Two entries per iteration, no branch on the distance: f and
-                // f' vanish for q >= 2, so entries beyond 2 h add nothing.  A
-                // missing second entry repeats the first with zero mass.
-                auto entry = [&](float4 pj, float4 vj, float mj) {
-                    const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
-                    const float r2 = dx * dx + dy * dy + dz * dz;
-                    const float vd = (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz;
-                    cnt += (mj > 0.f && r2 < R2) ? 1 : 0;
-                    pair_sums(r2, mj, vd, hinv, s0, s1, s2);
-                };
-                for (int e = sub; e < len; e += 2 * L) {
-                    const bool two = e + L < len;
-                    const int j0 = __ldcs(lst + e);
-                    const int j1 = two ? __ldcs(lst + e + L) : j0;
-                    const float4 p0 = __ldg(&a.pos[j0]), p1 = __ldg(&a.pos[j1]);
-                    const float4 v0 = __ldg(&a.vel[j0]), v1 = __ldg(&a.vel[j1]);
-                    entry(p0, v0, p0.w);
-                    entry(p1, v1, two ? p1.w : 0.f);
-                }
-                s0 = seg_sum(s0, L);
-                s1 = seg_sum(s1, L);
-                s2 = seg_sum(s2, L);
-                const float cf = seg_sum((float)cnt, L);
-                if (sub == 0 && act) {
-                    n_pairs += (unsigned long long)cf;
-                    ++n_newton;
-                }
-                if (final_pass) break;
-                if (act && !conv) {
-                    newton_update(h, hlo, hhi, conv, s0, s1, M, fixed, a.tol);
-                    outside = h > hw;
-                }
-                ++it;
-                if (__any_sync(0xffffffffu, outside)) break;  // the lists no longer cover h
-                if (fixed) {
-                    if (it >= limit) final_pass = true;   // one more sweep at the last h
-                } else if (__all_sync(0xffffffffu, conv)) {
-                    break;                                // every target's sums are at its h
-                } else if (it >= limit) {
-                    if (lane == 0) raise_error(a.err, SPH_ERR_NOT_CONVERGED);
-                    final_pass = true;
-                }
-            }
-            if (__any_sync(0xffffffffu, outside)) {  // start the batch over with walks
-                push_fallback(a, g, b0);
-                continue;
-            }
-            if (act && sub == 0) density_outputs(a, i, h, M, s1, s2, vi.w);
         }
     }
     for (int o = 16; o > 0; o >>= 1) {

@@ -20,6 +20,7 @@ namespace sph {
 
 constexpr int kFTB = 8;          // targets per batch
 constexpr int kForceWarps = 4;   // warps per block
+constexpr int kRound = 2;        // groups per warp per work grab of the list kernel
 
 template <int CAP>
 struct ForceSmem {
@@ -146,52 +147,62 @@ __global__ void __launch_bounds__(kForceWarps * 32) force_list_kernel(ForceArgs 
     const int ng = a.sizes[SZ_GROUPS];
     const bool lists_fresh = a.rec_ctl[1] == 0;
     unsigned long long n_pairs = 0, n_cand = 0;
+    // The block takes kRound consecutive groups per warp at a time, warp w the
+    // groups base + w + kForceWarps k: the warps of a block work on
+    // neighbouring groups together and share their candidates in L1.
+    __shared__ int s_base;
+    const int warp = threadIdx.x >> 5;
 
     while (true) {
-        int g = 0;
-        if (lane == 0) g = atomicAdd(a.work, 1);
-        g = __shfl_sync(0xffffffffu, g, 0);
-        if (g >= ng) break;
-        const int2 gr = a.grp_ref[g];
-        const int root = a.inst ? a.inst[gr.x] : 0;
-        const bool usable = lists_fresh && a.rec_bad[root] == 0;
-        for (int b0 = 0; b0 < gr.y; b0 += kFTB) {
-            const int nt = min(kFTB, gr.y - b0);
-            const int L = nt > 4 ? 4 : nt > 2 ? 8 : nt > 1 ? 16 : 32;
-            const int t = lane / L, sub = lane % L;
-            const bool act = t < nt;
-            const int i = gr.x + b0 + (act ? t : 0);
-            const int len = usable && act ? a.nl_len[i] : 0;
-            if (!usable || __any_sync(0xffffffffu, len < 0)) {
-                if (lane == 0) a.fallback[atomicAdd(a.n_fallback, 1)] = make_int2(g, b0);
-                continue;
+        if (threadIdx.x == 0) s_base = atomicAdd(a.work, kForceWarps * kRound);
+        __syncthreads();
+        const int base = s_base;
+        __syncthreads();
+        if (base >= ng) break;
+        for (int kr = 0; kr < kRound; ++kr) {
+            const int g = base + warp + kForceWarps * kr;
+            if (g >= ng) break;
+            const int2 gr = a.grp_ref[g];
+            const int root = a.inst ? a.inst[gr.x] : 0;
+            const bool usable = lists_fresh && a.rec_bad[root] == 0;
+            for (int b0 = 0; b0 < gr.y; b0 += kFTB) {
+                const int nt = min(kFTB, gr.y - b0);
+                const int L = nt > 4 ? 4 : nt > 2 ? 8 : nt > 1 ? 16 : 32;
+                const int t = lane / L, sub = lane % L;
+                const bool act = t < nt;
+                const int i = gr.x + b0 + (act ? t : 0);
+                const int len = usable && act ? a.nl_len[i] : 0;
+                if (!usable || __any_sync(0xffffffffu, len < 0)) {
+                    if (lane == 0) a.fallback[atomicAdd(a.n_fallback, 1)] = make_int2(g, b0);
+                    continue;
+                }
+                ForceTarget T;
+                T.init(a.pos[i], a.vel[i], a.prop[i], a);
+                const int *__restrict__ lst = a.nl_idx + (size_t)i * kNbrCap;
+                // Two entries per iteration, no branch: an entry outside the pair
+                // set (or padding) gets zero mass.  The particle itself (r = 0) is
+                // left out; a distinct particle at r = 0 would add nothing either
+                // (every term carries f'(0) = 0 or v_ij.r_ij / r = 0).
+                auto entry = [&](int j, bool valid) {
+                    const float4 pj = __ldg(&a.pos[j]);
+                    const float4 qj = __ldg(&a.prop[j]);
+                    const float4 vj = __ldg(&a.vel[j]);
+                    const float r2 = canon_r2(T.xi.x, T.xi.y, T.xi.z, pj.x, pj.y, pj.z);
+                    const float R = 2.0f * fmaxf(T.qi.x, qj.x);
+                    const bool in = valid && r2 > 0.f && r2 < R * R;
+                    T.pair(pj, vj, qj, in ? pj.w : 0.f, in, a);
+                };
+                for (int e = sub; e < len; e += 2 * L) {
+                    const bool two = e + L < len;
+                    const int j0 = __ldcs(lst + e);
+                    const int j1 = two ? __ldcs(lst + e + L) : j0;
+                    entry(j0, true);
+                    entry(j1, two);
+                }
+                T.finish(L, act && sub == 0, i, a);
+                n_pairs += T.cnt;
+                n_cand += act ? (unsigned long long)((len - sub + L - 1) / L) : 0ull;
             }
-            ForceTarget T;
-            T.init(a.pos[i], a.vel[i], a.prop[i], a);
-            const int *__restrict__ lst = a.nl_idx + (size_t)i * kNbrCap;
-            // Two entries per iteration, no branch: an entry outside the pair
-            // set (or padding) gets zero mass.  The particle itself (r = 0) is
-            // left out; a distinct particle at r = 0 would add nothing either
-            // (every term carries f'(0) = 0 or v_ij.r_ij / r = 0).
-            auto entry = [&](int j, bool valid) {
-                const float4 pj = __ldg(&a.pos[j]);
-                const float4 qj = __ldg(&a.prop[j]);
-                const float4 vj = __ldg(&a.vel[j]);
-                const float r2 = canon_r2(T.xi.x, T.xi.y, T.xi.z, pj.x, pj.y, pj.z);
-                const float R = 2.0f * fmaxf(T.qi.x, qj.x);
-                const bool in = valid && r2 > 0.f && r2 < R * R;
-                T.pair(pj, vj, qj, in ? pj.w : 0.f, in, a);
-            };
-            for (int e = sub; e < len; e += 2 * L) {
-                const bool two = e + L < len;
-                const int j0 = __ldcs(lst + e);
-                const int j1 = two ? __ldcs(lst + e + L) : j0;
-                entry(j0, true);
-                entry(j1, two);
-            }
-            T.finish(L, act && sub == 0, i, a);
-            n_pairs += T.cnt;
-            n_cand += act ? (unsigned long long)((len - sub + L - 1) / L) : 0ull;
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
