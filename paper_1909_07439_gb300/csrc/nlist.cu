@@ -45,7 +45,7 @@ struct NlistSmem {
     int leaves[kSGLeaves];     // the walk's leaves (nodes) in particle order
     int2 runs[kMaxRuns + 1];   // a group's candidate runs: (first particle, first slot), sentinel
     TargetPairs<kNlTB> tc;
-    float tr[kNlTB];           // list radius factor x h_i (0 for unused slots)
+    float tr2[kNlTB];          // (list radius factor x h_i)^2 (0 for unused slots)
 };
 
 struct NlistArgs {
@@ -142,6 +142,65 @@ __device__ __forceinline__ int group_candidates(const NlistArgs &a, NlistSmem &s
     return nrun <= max_runs ? nrun : -1;
 }
 
+// Test the group's candidate slots, 32 per chunk (one per lane), against the
+// batch's targets (TB slots, the unused ones far away: no candidate hits
+// them, and a missing candidate, also far away, hits no target) and append
+// the hits to the targets' lists.  The next chunk's candidates are loaded
+// while one is tested.  Returns the list length of target `lane` (lane < TB).
+template <int TB>
+__device__ __forceinline__ int test_chunks(const NlistArgs &a, const NlistSmem &sm, int ncand, int i0,
+                                           int nt, unsigned long long &n_cand)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lane_lt();
+    int len[TB];
+#pragma unroll
+    for (int tt = 0; tt < TB; ++tt) len[tt] = 0;
+    int r = 0;
+    int jn = lane < ncand ? slot_particle(sm.runs, r, lane) : -1;
+    float4 pn = jn >= 0 ? __ldg(&a.pos[jn]) : make_float4(1e30f, 1e30f, 1e30f, 0.f);
+    float hn = jn >= 0 ? __ldg(&a.h[jn]) : 0.f;
+    for (int c0 = 0; c0 < ncand; c0 += 32) {
+        const int k = c0 + lane;
+        const int j = jn;
+        const float4 pj = pn;
+        const float rj = a.rscale * hn;
+        const float rj2 = rj * rj;
+        if (c0 + 32 < ncand) {
+            jn = k + 32 < ncand ? slot_particle(sm.runs, r, k + 32) : -1;
+            pn = jn >= 0 ? __ldg(&a.pos[jn]) : make_float4(1e30f, 1e30f, 1e30f, 0.f);
+            hn = jn >= 0 ? __ldg(&a.h[jn]) : 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < TB / 2; ++q) {
+            const int t0 = 2 * q, t1 = t0 + 1;
+            // r < max(R_i, R_j) as r^2 < max(R_i^2, R_j^2): squaring is
+            // monotone, so both compare the same rounded values
+            const float2 r2 = canon_r2_x2(sm.tc.x[q], sm.tc.y[q], sm.tc.z[q], pj.x, pj.y, pj.z);
+            const bool hit0 = r2.x < fmaxf(sm.tr2[t0], rj2);
+            const bool hit1 = r2.y < fmaxf(sm.tr2[t1], rj2);
+            const unsigned m0 = __ballot_sync(0xffffffffu, hit0);
+            const unsigned m1 = __ballot_sync(0xffffffffu, hit1);
+            if (hit0) {
+                const int e = len[t0] + __popc(m0 & lt);
+                if (e < kNbrCap) a.idx[(size_t)(i0 + t0) * kNbrCap + e] = j;
+            }
+            if (hit1) {
+                const int e = len[t1] + __popc(m1 & lt);
+                if (e < kNbrCap) a.idx[(size_t)(i0 + t1) * kNbrCap + e] = j;
+            }
+            len[t0] += __popc(m0);
+            len[t1] += __popc(m1);
+        }
+        n_cand += (unsigned long long)(nt * __popc(__ballot_sync(0xffffffffu, j >= 0)));
+    }
+    int mine = 0;
+#pragma unroll
+    for (int tt = 0; tt < TB; ++tt)
+        if (lane == tt) mine = len[tt];
+    return mine;
+}
+
 __global__ void __launch_bounds__(kNlWarps * 32, 5) nlist_kernel(NlistArgs a)
 {
     __shared__ NlistSmem smv[kNlWarps];
@@ -203,47 +262,16 @@ __global__ void __launch_bounds__(kNlWarps * 32, 5) nlist_kernel(NlistArgs a)
                     if (lane < kNlTB) {
                         const float4 p = lane < nt ? a.pos[i0 + lane] : make_float4(1e30f, 1e30f, 1e30f, 0.f);
                         sm.tc.set(lane, p);
-                        sm.tr[lane] = lane < nt ? a.rscale * a.h[i0 + lane] : 0.f;
+                        const float rt = lane < nt ? a.rscale * a.h[i0 + lane] : 0.f;
+                        sm.tr2[lane] = rt * rt;
                     }
                     __syncwarp();
-                    int len[kNlTB];
-#pragma unroll
-                    for (int tt = 0; tt < kNlTB; ++tt) len[tt] = 0;
-                    // chunks of 32 candidate slots, one per lane
-                    int r = 0;
-                    for (int c0 = 0; c0 < ncand; c0 += 32) {
-                        const int k = c0 + lane;
-                        const int j = k < ncand ? slot_particle(sm.runs, r, k) : -1;
-                        const float4 pj = j >= 0 ? __ldg(&a.pos[j]) : make_float4(0.f, 0.f, 0.f, 0.f);
-                        const float rj = j >= 0 ? a.rscale * __ldg(&a.h[j]) : 0.f;
-#pragma unroll
-                        for (int q = 0; q < kNlTB / 2; ++q) {
-                            const int t0 = 2 * q, t1 = t0 + 1;
-                            if (t0 < nt) {
-                                const float2 r2 = canon_r2_x2(sm.tc.x[q], sm.tc.y[q], sm.tc.z[q], pj.x, pj.y, pj.z);
-                                const float R0 = fmaxf(sm.tr[t0], rj), R1 = fmaxf(sm.tr[t1], rj);
-                                const bool hit0 = j >= 0 && r2.x < R0 * R0;
-                                const bool hit1 = j >= 0 && t1 < nt && r2.y < R1 * R1;
-                                const unsigned m0 = __ballot_sync(0xffffffffu, hit0);
-                                const unsigned m1 = __ballot_sync(0xffffffffu, hit1);
-                                if (hit0) {
-                                    const int e2 = len[t0] + __popc(m0 & lt);
-                                    if (e2 < kNbrCap) a.idx[(size_t)(i0 + t0) * kNbrCap + e2] = j;
-                                }
-                                if (hit1) {
-                                    const int e2 = len[t1] + __popc(m1 & lt);
-                                    if (e2 < kNbrCap) a.idx[(size_t)(i0 + t1) * kNbrCap + e2] = j;
-                                }
-                                len[t0] += __popc(m0);
-                                len[t1] += __popc(m1);
-                            }
-                        }
-                        n_cand += (unsigned long long)(nt * __popc(__ballot_sync(0xffffffffu, j >= 0)));
-                    }
                     int mlen = 0;
-#pragma unroll
-                    for (int tt = 0; tt < kNlTB; ++tt)
-                        if (lane == tt) mlen = len[tt];
+                    if (ncand > 0) {
+                        if (nt <= 4) mlen = test_chunks<4>(a, sm, ncand, i0, nt, n_cand);
+                        else if (nt <= 8) mlen = test_chunks<8>(a, sm, ncand, i0, nt, n_cand);
+                        else mlen = test_chunks<16>(a, sm, ncand, i0, nt, n_cand);
+                    }
                     // a group without lists is left to the walking kernels
                     const bool fits = ok && mlen <= kNbrCap;
                     if (lane < nt) {
