@@ -268,6 +268,7 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_walk_kernel(DensArgs 
     const int lane = threadIdx.x & 31;
     const unsigned lt = lane_lt();
     const int nfb = *a.n_fallback;
+    if (nfb == 0) return;  // nothing handed over (the usual case): no atomics
     const float hf3 = a.hfact * a.hfact * a.hfact;
     const bool fixed = a.fixed_iters > 0;
     const int limit = fixed ? a.fixed_iters : a.max_iter;
@@ -680,7 +681,7 @@ cudaError_t density_solve(Ctx &c, const sph_state &s, const sph_params &p, cudaS
 cudaError_t density_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st,
                          const Batch *batch)
 {
-    cudaError_t e = density_lists(c, s, p, st, batch);
+    cudaError_t e = density_lists(c, s, p, st, batch, false);
     if (e != cudaSuccess) return e;
     return density_solve(c, s, p, st, batch);
 }

@@ -224,6 +224,7 @@ __global__ void __launch_bounds__(kForceWarps * 32) force_walk_kernel(ForceArgs 
     const int lane = threadIdx.x & 31;
     const unsigned lt = lane_lt();
     const int nfb = *a.n_fallback;
+    if (nfb == 0) return;  // nothing handed over (the usual case): no atomics
     unsigned long long n_pairs = 0, n_cand = 0;
 
     while (true) {

@@ -116,9 +116,12 @@ sph_status check_params(Ctx &c, const sph_params *p)
 constexpr int kTreeLaunches = 42;
 constexpr int kPrepLaunches = 3;
 
-sph_status do_density(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st)
+// hmax_fresh: the tree's node and group h_max already hold the current h (the
+// tree was just built from it)
+sph_status do_density(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st,
+                      bool hmax_fresh)
 {
-    {
+    if (!hmax_fresh) {
         // node and group h_max of the starting h, for the list walk
         StageScope sc(c, ST_PREP, st, 2);
         CK(update_hmax(c, s, p, st), "update_hmax");
@@ -308,7 +311,7 @@ sph_status sph_density(sph_ctx *h, sph_state *s, const sph_params *p, void *stre
     if (r != SPH_OK) return r;
     if ((r = check_params(c, p)) != SPH_OK) return r;
     if (s->n == 0) return SPH_OK;
-    return do_density(c, *s, *p, (cudaStream_t)stream);
+    return do_density(c, *s, *p, (cudaStream_t)stream, false);
 }
 
 sph_status sph_force(sph_ctx *h, sph_state *s, const sph_params *p, void *stream)
@@ -354,7 +357,7 @@ sph_status sph_step(sph_ctx *h, sph_state *s, const sph_params *p, float *d_dt, 
         CK(kick_drift(c, *s, d_dt, st), "kick_drift");
     }
     if ((r = do_tree(c, *s, *p, false, st)) != SPH_OK) return r;
-    if ((r = do_density(c, *s, *p, st)) != SPH_OK) return r;
+    if ((r = do_density(c, *s, *p, st, true)) != SPH_OK) return r;
     if ((r = do_force(c, *s, *p, st)) != SPH_OK) return r;
     {
         StageScope sc(c, ST_LEAPFROG, st, 1);

@@ -163,7 +163,8 @@ cudaError_t scan_exclusive_int(Ctx &c, const int *in, int *out, int n, int *tota
 cudaError_t nlist_pass(Ctx &c, const sph_state &s, const sph_params &p, float pad,
                        cudaStream_t st, const Batch *batch = nullptr);
 cudaError_t configure_nlist_kernels();
-// density.cu (density_pass = density_lists + density_solve)
+// density.cu (density_pass = density_lists + density_solve; density_pass
+// expects the node and group h_max of the current h, as build_tree leaves them)
 cudaError_t density_lists(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st,
                           const Batch *batch = nullptr, bool refresh_hmax = true);
 cudaError_t density_solve(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st,
