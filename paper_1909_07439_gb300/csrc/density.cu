@@ -46,6 +46,7 @@ struct DensSmem {
 struct DensArgs {
     const float4 *pos;
     const float4 *vel;
+    const float4 *rec;  // pos, vel side by side
     float *h, *rho, *omega, *drhodt;
     float4 *prop;  // h, rho, 1/(rho Omega), c_s  (for the force pass)
     const int2 *grp_ref;
@@ -211,8 +212,9 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_list_kernel(DensArgs 
                         const bool two = e + L < len;
                         const int j0 = __ldcs(lst + e);
                         const int j1 = two ? __ldcs(lst + e + L) : j0;
-                        const float4 p0 = __ldg(&a.pos[j0]), p1 = __ldg(&a.pos[j1]);
-                        const float4 v0 = __ldg(&a.vel[j0]), v1 = __ldg(&a.vel[j1]);
+                        float4 p0, v0, p1, v1;
+                        ld_rec(a.rec, j0, p0, v0);
+                        ld_rec(a.rec, j1, p1, v1);
                         entry(p0, v0, p0.w);
                         entry(p1, v1, two ? p1.w : 0.f);
                     }
@@ -643,6 +645,7 @@ cudaError_t density_solve(Ctx &c, const sph_state &s, const sph_params &p, cudaS
     a.rec_bad = c.tree.rec_bad;
     a.pos = (const float4 *)s.pos;
     a.vel = (const float4 *)s.vel;
+    a.rec = c.rec;
     a.h = s.h;
     a.rho = s.rho;
     a.omega = s.omega;

@@ -116,15 +116,16 @@ sph_status check_params(Ctx &c, const sph_params *p)
 constexpr int kTreeLaunches = 42;
 constexpr int kPrepLaunches = 3;
 
-// hmax_fresh: the tree's node and group h_max already hold the current h (the
-// tree was just built from it)
+// tree_fresh: the tree was just built from this state (node and group h_max
+// hold the current h, and the packed particle records the current pos, vel)
 sph_status do_density(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st,
-                      bool hmax_fresh)
+                      bool tree_fresh)
 {
-    if (!hmax_fresh) {
+    if (!tree_fresh) {
         // node and group h_max of the starting h, for the list walk
-        StageScope sc(c, ST_PREP, st, 2);
+        StageScope sc(c, ST_PREP, st, 3);
         CK(update_hmax(c, s, p, st), "update_hmax");
+        CK(pack_records(c, s, st), "pack");
     }
     {
         StageScope sc(c, ST_LISTS, st, 1);
@@ -135,11 +136,15 @@ sph_status do_density(Ctx &c, const sph_state &s, const sph_params &p, cudaStrea
     return SPH_OK;
 }
 
-sph_status do_force(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st)
+// records_fresh: the packed particle records hold the current pos, vel (the
+// density pass of the same step ran on this state)
+sph_status do_force(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st,
+                    bool records_fresh)
 {
     {
-        StageScope sc(c, ST_PREP, st, kPrepLaunches);
+        StageScope sc(c, ST_PREP, st, kPrepLaunches + (records_fresh ? 0 : 1));
         CK(force_prep(c, s, p, st), "force_prep");
+        if (!records_fresh) CK(pack_records(c, s, st), "pack");
     }
     StageScope sc(c, ST_FORCE, st, 2);
     CK(force_pass(c, s, p, st), "force");
@@ -237,6 +242,7 @@ sph_status sph_create(sph_ctx **out, int64_t max_n, int device)
     A(dalloc(t.lv_tree, n));
     A(dalloc(t.lv_grp, n));
     A(dalloc(t.blk_cnt, (size_t)kLevels * nbchop));
+    A(dalloc(c.rec, 2 * n));
     A(dalloc(c.prop, n));
     A(dalloc(c.vhalf, n));
     A(dalloc(c.inst, n));
@@ -277,7 +283,7 @@ void sph_destroy(sph_ctx *h)
                     c.tree.grp_lo, c.tree.grp_hi, c.tree.lv_tree, c.tree.lv_grp, c.tree.blk_cnt,
                     c.nl_idx, c.nl_len, c.fallback,
                     c.tree.rec_ctl, c.tree.rec_bad,
-                    c.prop, c.vhalf, c.inst, c.bbox_inst, c.dtmin_inst,
+                    c.rec, c.prop, c.vhalf, c.inst, c.bbox_inst, c.dtmin_inst,
                     c.bbox, c.scan_part, c.red_f, c.red_d, c.d_err, c.d_counters,
                     c.d_sizes, c.mirror.pos, c.mirror.vel, c.mirror.acc, c.mirror.h, c.mirror.rho,
                     c.mirror.omega, c.mirror.drhodt, c.mirror.vsigmax, c.mirror.perm,
@@ -322,7 +328,7 @@ sph_status sph_force(sph_ctx *h, sph_state *s, const sph_params *p, void *stream
     if (r != SPH_OK) return r;
     if ((r = check_params(c, p)) != SPH_OK) return r;
     if (s->n == 0) return SPH_OK;
-    return do_force(c, *s, *p, (cudaStream_t)stream);
+    return do_force(c, *s, *p, (cudaStream_t)stream, false);
 }
 
 sph_status sph_timestep(sph_ctx *h, const sph_state *s, const sph_params *p, float *d_dt,
@@ -358,7 +364,7 @@ sph_status sph_step(sph_ctx *h, sph_state *s, const sph_params *p, float *d_dt, 
     }
     if ((r = do_tree(c, *s, *p, false, st)) != SPH_OK) return r;
     if ((r = do_density(c, *s, *p, st, true)) != SPH_OK) return r;
-    if ((r = do_force(c, *s, *p, st)) != SPH_OK) return r;
+    if ((r = do_force(c, *s, *p, st, true)) != SPH_OK) return r;
     {
         StageScope sc(c, ST_LEAPFROG, st, 1);
         CK(kick_close(c, *s, d_dt, d_time, st), "kick_close");

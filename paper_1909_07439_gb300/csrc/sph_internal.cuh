@@ -110,6 +110,7 @@ struct Ctx {
     int2 *fallback = nullptr;  // (group, first batch slot) handed to the walk kernels
 
     // per-particle scratch
+    float4 *rec = nullptr;    // [2 n]: pos, vel of each particle side by side (32-byte records)
     float4 *prop = nullptr;   // h, rho, 1/(rho Omega), c_s
     float4 *vhalf = nullptr;  // half-step v, u of the leapfrog
     float *bbox = nullptr;    // [8]: lo xyz, size, then scratch
@@ -157,6 +158,8 @@ cudaError_t build_tree(Ctx &c, const sph_state &s, const sph_params &p, bool ful
                        cudaStream_t st, const Batch *batch = nullptr);
 cudaError_t instance_map(Ctx &c, const int64_t *d_offsets, int n_inst, int n, cudaStream_t st);
 cudaError_t update_hmax(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st);
+// c.rec from the state's pos and vel (build_tree writes it too)
+cudaError_t pack_records(Ctx &c, const sph_state &s, cudaStream_t st);
 cudaError_t scan_exclusive_int(Ctx &c, const int *in, int *out, int n, int *total_dev,
                                cudaStream_t st);
 // nlist.cu

@@ -336,6 +336,7 @@ struct GatherArgs {
     float *a1[5];
     float *t1[5];
     uint32_t *perm, *tperm;
+    float4 *rec;  // a4[0], a4[1] (pos, vel) side by side
     int n4, n1;
 };
 
@@ -344,8 +345,13 @@ __global__ void gather_kernel(GatherArgs g, int n)
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         uint32_t o = g.order[k];
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
-            if (a < g.n4) g.t4[a][k] = g.a4[a][o];
+        for (int a = 0; a < 4; ++a) {
+            if (a < g.n4) {
+                const float4 v = g.a4[a][o];
+                g.t4[a][k] = v;
+                if (a < 2) g.rec[2 * (size_t)k + a] = v;
+            }
+        }
 #pragma unroll
         for (int a = 0; a < 5; ++a)
             if (a < g.n1) g.t1[a][k] = g.a1[a][o];
@@ -773,6 +779,7 @@ cudaError_t build_tree(Ctx &c, const sph_state &s, const sph_params &p, bool ful
     for (int a = 0; a < n1; ++a) { g.a1[a] = arr1[a]; g.t1[a] = c.tmp1[a]; }
     g.perm = s.perm;
     g.tperm = c.tmp_perm;
+    g.rec = c.rec;
     g.n4 = n4;
     g.n1 = n1;
     gather_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(g, n);
@@ -802,6 +809,22 @@ cudaError_t build_tree(Ctx &c, const sph_state &s, const sph_params &p, bool ful
     node_finish_kernel<<<grid_for(c, t.cap_nodes, 256), 256, 0, st>>>(s.keys, inst, offs, n,
                                                                        p.n_leaf, t, c.d_sizes);
     node_bounds_kernel<<<grid_for(c, t.cap_nodes, 128), 128, 0, st>>>(pos, s.h, t, c.d_sizes, 0);
+    return cudaGetLastError();
+}
+
+__global__ void pack_records_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ vel,
+                                    float4 *__restrict__ rec, int n)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        rec[2 * (size_t)i] = pos[i];
+        rec[2 * (size_t)i + 1] = vel[i];
+    }
+}
+
+cudaError_t pack_records(Ctx &c, const sph_state &s, cudaStream_t st)
+{
+    pack_records_kernel<<<grid_for(c, s.n, 256), 256, 0, st>>>((const float4 *)s.pos,
+                                                                (const float4 *)s.vel, c.rec, (int)s.n);
     return cudaGetLastError();
 }
 

@@ -39,6 +39,15 @@ __device__ __forceinline__ int warp_sum_i(int v)
     return v;
 }
 
+// Particle i's position/mass and velocity/energy as one 32-byte record
+// (rec[2 i], rec[2 i + 1]), read with a single 256-bit load.
+__device__ __forceinline__ void ld_rec(const float4 *rec, int i, float4 &p, float4 &v)
+{
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(p.x), "=f"(p.y), "=f"(p.z), "=f"(p.w), "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+        : "l"(rec + 2 * (size_t)i));
+}
+
 // canonical FP32 squared distance: (dx*dx + dy*dy) + dz*dz, no fusion
 __device__ __forceinline__ float canon_r2(float xi, float yi, float zi, float xj, float yj, float zj)
 {
