@@ -259,7 +259,7 @@ def run_ours(args):
 def run_batched(args):
     """512 independent Sedov blasts (log-uniform sizes in [4096, 262144]),
     20 steps each with per-instance dt: one batched state, graph-replayed
-    steps with persistent walk kernels, autotuned N_group and tile; compared
+    steps with persistent list and pair kernels, autotuned N_group and N_leaf; compared
     with the same instances advanced one after another by sph_step."""
     import torch
     from paper_1909_07439_gb300 import DeviceState, autotune, inputs, native
@@ -292,7 +292,7 @@ def run_batched(args):
     # the same instances one after another through the single-instance path
     nmax = int(np.max(np.diff(off)))
     ctx = native.sph_create(nmax, 0)
-    p1 = native.sph_params_default(n_group=p.n_group, tile=p.tile)
+    p1 = native.sph_params_default(n_group=p.n_group, n_leaf=p.n_leaf)
     states = []
     for i in range(k):
         a, b = int(off[i]), int(off[i + 1])

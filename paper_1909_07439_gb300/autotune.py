@@ -1,7 +1,7 @@
-"""Autotuner for the batched step: picks the group size (N_group) and the
-neighbour-list tile width by timing a few graph-replayed steps of the actual
-batch, restoring the state between trials.  Results are cached in a JSON
-file keyed by device, particle count and instance count."""
+"""Autotuner for the batched step: picks the group size (N_group) and the leaf
+size (N_leaf) by timing a few graph-replayed steps of the actual batch,
+restoring the state between trials.  Results are cached in a JSON file keyed
+by device, particle count and instance count."""
 from __future__ import annotations
 
 import json
@@ -9,7 +9,7 @@ import os
 
 from . import native
 
-CANDIDATES = [(g, t) for g in (4, 8, 16) for t in (64, 80, 96)]
+CANDIDATES = [(g, l) for g in (4, 8, 16) for l in (8, 16)]
 
 
 def cache_path() -> str:
@@ -42,22 +42,22 @@ def _save_cache(c):
 
 def tune_batch(ctx, state, d_offsets, n_inst, base=None, steps=2, use_cache=True,
                candidates=CANDIDATES):
-    """Return (sph_params, report) with the fastest (n_group, tile) for this batch.
+    """Return (sph_params, report) with the fastest (n_group, n_leaf) for this batch.
     ``state`` (a DeviceState) is left exactly as it was on entry."""
     import torch
     base = base or native.sph_params_default()
     key = _key(torch, state.n, n_inst)
     cache = _load_cache() if use_cache else {}
-    if key in cache:
-        g, t = cache[key]["n_group"], cache[key]["tile"]
-        return native.sph_params_default(**{**_as_dict(base), "n_group": g, "tile": t}), cache[key]
+    if key in cache and "n_leaf" in cache[key]:
+        g, l = cache[key]["n_group"], cache[key]["n_leaf"]
+        return native.sph_params_default(**{**_as_dict(base), "n_group": g, "n_leaf": l}), cache[key]
     saved = {f: getattr(state, f).clone() for f in state.FIELDS4 + state.FIELDS1 + ("perm", "keys")}
     dt = torch.zeros(n_inst, dtype=torch.float32, device=state.device)
     trials = []
-    for g, t in candidates:
+    for g, l in candidates:
         for f, v in saved.items():
             getattr(state, f).copy_(v)
-        p = native.sph_params_default(**{**_as_dict(base), "n_group": g, "tile": t})
+        p = native.sph_params_default(**{**_as_dict(base), "n_group": g, "n_leaf": l})
         native.sph_batch_evaluate(ctx, state.c, d_offsets, n_inst, p, dt)
         native.sph_batch_step(ctx, state.c, d_offsets, n_inst, 1, p, dt)  # capture + warm
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -65,16 +65,16 @@ def tune_batch(ctx, state, d_offsets, n_inst, base=None, steps=2, use_cache=True
         native.sph_batch_step(ctx, state.c, d_offsets, n_inst, steps, p, dt)
         e1.record()
         native.sph_sync(ctx)
-        trials.append({"n_group": g, "tile": t, "ms_per_step": e0.elapsed_time(e1) / steps})
+        trials.append({"n_group": g, "n_leaf": l, "ms_per_step": e0.elapsed_time(e1) / steps})
     for f, v in saved.items():
         getattr(state, f).copy_(v)
     best = min(trials, key=lambda r: r["ms_per_step"])
-    report = {"n_group": best["n_group"], "tile": best["tile"], "trials": trials}
+    report = {"n_group": best["n_group"], "n_leaf": best["n_leaf"], "trials": trials}
     if use_cache:
         cache[key] = report
         _save_cache(cache)
     return native.sph_params_default(**{**_as_dict(base), "n_group": best["n_group"],
-                                        "tile": best["tile"]}), report
+                                        "n_leaf": best["n_leaf"]}), report
 
 
 def _as_dict(p):

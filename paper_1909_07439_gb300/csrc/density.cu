@@ -151,6 +151,7 @@ __device__ __forceinline__ void push_fallback(const DensArgs &a, int g, int b0)
 __global__ void __launch_bounds__(kDensWarps * 32) density_list_kernel(DensArgs a)
 {
     const int lane = threadIdx.x & 31;
+    const uint64_t keep = l2_keep_policy();
     const int ng = a.sizes[SZ_GROUPS];
     const float hf3 = a.hfact * a.hfact * a.hfact;
     const bool fixed = a.fixed_iters > 0;
@@ -213,8 +214,8 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_list_kernel(DensArgs 
                         const int j0 = __ldcs(lst + e);
                         const int j1 = two ? __ldcs(lst + e + L) : j0;
                         float4 p0, v0, p1, v1;
-                        ld_rec(a.rec, j0, p0, v0);
-                        ld_rec(a.rec, j1, p1, v1);
+                        ld_rec(a.rec, j0, keep, p0, v0);
+                        ld_rec(a.rec, j1, keep, p1, v1);
                         entry(p0, v0, p0.w);
                         entry(p1, v1, two ? p1.w : 0.f);
                     }

@@ -144,6 +144,7 @@ struct ForceTarget {
 __global__ void __launch_bounds__(kForceWarps * 32) force_list_kernel(ForceArgs a)
 {
     const int lane = threadIdx.x & 31;
+    const uint64_t keep = l2_keep_policy();
     const int ng = a.sizes[SZ_GROUPS];
     const bool lists_fresh = a.rec_ctl[1] == 0;
     unsigned long long n_pairs = 0, n_cand = 0;
@@ -184,9 +185,9 @@ __global__ void __launch_bounds__(kForceWarps * 32) force_list_kernel(ForceArgs 
                 // left out; a distinct particle at r = 0 would add nothing either
                 // (every term carries f'(0) = 0 or v_ij.r_ij / r = 0).
                 auto entry = [&](int j, bool valid) {
-                    const float4 pj = __ldg(&a.pos[j]);
-                    const float4 qj = __ldg(&a.prop[j]);
-                    const float4 vj = __ldg(&a.vel[j]);
+                    const float4 pj = ld_keep(a.pos, j, keep);
+                    const float4 qj = ld_keep(a.prop, j, keep);
+                    const float4 vj = ld_keep(a.vel, j, keep);
                     const float r2 = canon_r2(T.xi.x, T.xi.y, T.xi.z, pj.x, pj.y, pj.z);
                     const float R = 2.0f * fmaxf(T.qi.x, qj.x);
                     const bool in = valid && r2 > 0.f && r2 < R * R;

@@ -183,11 +183,11 @@ __device__ __forceinline__ int test_chunks(const NlistArgs &a, const NlistSmem &
             const unsigned m1 = __ballot_sync(0xffffffffu, hit1);
             if (hit0) {
                 const int e = len[t0] + __popc(m0 & lt);
-                if (e < kNbrCap) a.idx[(size_t)(i0 + t0) * kNbrCap + e] = j;
+                if (e < kNbrCap) __stcs(a.idx + (size_t)(i0 + t0) * kNbrCap + e, j);
             }
             if (hit1) {
                 const int e = len[t1] + __popc(m1 & lt);
-                if (e < kNbrCap) a.idx[(size_t)(i0 + t1) * kNbrCap + e] = j;
+                if (e < kNbrCap) __stcs(a.idx + (size_t)(i0 + t1) * kNbrCap + e, j);
             }
             len[t0] += __popc(m0);
             len[t1] += __popc(m1);

@@ -39,13 +39,31 @@ __device__ __forceinline__ int warp_sum_i(int v)
     return v;
 }
 
+// L2 policy for particle data that neighbouring groups read again soon: keep
+// it in L2 while the neighbour lists stream through.
+__device__ __forceinline__ uint64_t l2_keep_policy()
+{
+    uint64_t pol;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
 // Particle i's position/mass and velocity/energy as one 32-byte record
 // (rec[2 i], rec[2 i + 1]), read with a single 256-bit load.
-__device__ __forceinline__ void ld_rec(const float4 *rec, int i, float4 &p, float4 &v)
+__device__ __forceinline__ void ld_rec(const float4 *rec, int i, uint64_t pol, float4 &p, float4 &v)
 {
-    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+    asm("ld.global.nc.L2::cache_hint.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8], %9;"
         : "=f"(p.x), "=f"(p.y), "=f"(p.z), "=f"(p.w), "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-        : "l"(rec + 2 * (size_t)i));
+        : "l"(rec + 2 * (size_t)i), "l"(pol));
+}
+
+__device__ __forceinline__ float4 ld_keep(const float4 *a, int i, uint64_t pol)
+{
+    float4 v;
+    asm("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+        : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+        : "l"(a + i), "l"(pol));
+    return v;
 }
 
 // canonical FP32 squared distance: (dx*dx + dy*dy) + dz*dz, no fusion
