@@ -42,10 +42,12 @@ FLOP_DENSITY_PAIR = 24
 FLOP_FORCE_PAIR = 65
 #  neighbour-list candidate test: canonical squared distance, 3 sub 3 mul 2 add = 8
 FLOP_TEST = 8
-# DRAM bytes (read + write) per launch of the dominant kernels from one ncu
-# capture of this workload (profiles/); None until measured for the current
-# kernels.
-NCU_TRAFFIC = {}
+# DRAM bytes (read + write) per launch of the longest-stage kernels from one
+# ncu capture of this workload (profiles/list_density_force_kernels_sedov128_ncu.md);
+# to be re-measured whenever those kernels change.
+NCU_TRAFFIC = {"nlist_kernel": 127.014e6 + 597.177344e6,
+               "density_list_kernel": 1127.482e6 + 50.49472e6,
+               "force_list_kernel": 1097.806e6 + 30.43072e6}
 
 
 def peaks():
