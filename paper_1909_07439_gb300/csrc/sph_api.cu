@@ -113,7 +113,7 @@ sph_status check_params(Ctx &c, const sph_params *p)
         if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
     } while (0)
 
-constexpr int kTreeLaunches = 42;
+constexpr int kTreeLaunches = 28;
 constexpr int kPrepLaunches = 3;
 
 // tree_fresh: the tree was just built from this state (node and group h_max
@@ -214,8 +214,10 @@ sph_status sph_create(sph_ctx **out, int64_t max_n, int device)
     A(dalloc(c.keys_alt, n));
     A(dalloc(c.idx_a, n));
     A(dalloc(c.idx_b, n));
-    A(dalloc(c.hist, (size_t)256 * c.ntiles_cap));
-    A(dalloc(c.dtotal, 256));
+    A(dalloc(c.rs_ghist, 10 * 256));
+    A(dalloc(c.rs_gstart, 10 * 256));
+    A(dalloc(c.rs_status, (size_t)10 * 256 * c.ntiles_cap));
+    A(dalloc(c.rs_tiles, 10));
     for (int k = 0; k < 4; ++k) A(dalloc(c.tmp4[k], n));
     for (int k = 0; k < 5; ++k) A(dalloc(c.tmp1[k], n));
     A(dalloc(c.tmp_perm, n));
@@ -275,7 +277,7 @@ void sph_destroy(sph_ctx *h)
     Ctx &c = h->impl;
     cudaSetDevice(c.device);
     cudaDeviceSynchronize();
-    void *ptrs[] = {c.keys_alt, c.idx_a, c.idx_b, c.hist, c.dtotal, c.tmp4[0], c.tmp4[1], c.tmp4[2],
+    void *ptrs[] = {c.keys_alt, c.idx_a, c.idx_b, c.rs_ghist, c.rs_gstart, c.rs_status, c.rs_tiles, c.tmp4[0], c.tmp4[1], c.tmp4[2],
                     c.tmp4[3], c.tmp1[0], c.tmp1[1], c.tmp1[2], c.tmp1[3], c.tmp1[4], c.tmp_perm,
                     c.tree.node_first, c.tree.node_count, c.tree.node_level, c.tree.node_child,
                     c.tree.node_nchild, c.tree.node_parent, c.tree.node_arrive, c.tree.node_lo,

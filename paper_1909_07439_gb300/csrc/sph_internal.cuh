@@ -91,8 +91,10 @@ struct Ctx {
     // sort scratch
     uint64_t *keys_alt = nullptr;
     uint32_t *idx_a = nullptr, *idx_b = nullptr;
-    uint32_t *hist = nullptr;    // [256][ntiles]
-    uint32_t *dtotal = nullptr;  // [256]
+    uint32_t *rs_ghist = nullptr;   // [10][256] digit counts of every pass
+    uint32_t *rs_gstart = nullptr;  // [10][256] their exclusive scans
+    uint32_t *rs_status = nullptr;  // [10][ntiles][256] look-back words
+    int *rs_tiles = nullptr;        // [10] tile counters
     int ntiles_cap = 0;
 
     // gather scratch

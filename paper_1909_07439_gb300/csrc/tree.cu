@@ -169,37 +169,17 @@ __global__ void morton_kernel(const float4 *__restrict__ pos, const int *__restr
 
 // ------------------------------------------------------------- radix sort
 // Stable LSD radix sort of (key, index), 8-bit digits, 8 passes over the
-// 64-bit word.  Per pass: tile histograms, per-digit scan over tiles, then a
-// scatter that scans the digit totals and ranks equal digits inside a tile in
-// input order (warp match + per-warp counts), which keeps the sort stable.
+// 64-bit word (two more on the instance id in a batch).  The digit counts of
+// every pass are taken in one histogram pass up front (the multiset of keys
+// does not change between passes).  Each pass is then one kernel: tiles are
+// numbered in launch order by an atomic counter, each ranks its keys (warp
+// match + per-warp counts, in input order, so the sort is stable), publishes
+// its per-digit counts and adds up its predecessors' counts by looking back
+// through their published words (decoupled look-back), then writes its keys
+// out digit run by digit run from a digit-ordered copy in shared memory.
 constexpr int RS_T = 256, RS_I = 8, RS_TILE = RS_T * RS_I;
-
-// digit of element s: 8 bits of its key, or (inst != nullptr) of its instance id
-__device__ __forceinline__ uint32_t rs_digit(const uint64_t *__restrict__ keys,
-                                             const uint32_t *__restrict__ vals,
-                                             const int *__restrict__ inst, int s, int shift)
-{
-    if (inst) return ((uint32_t)inst[vals[s]] >> shift) & 255u;
-    return (uint32_t)((keys[s] >> shift) & 255u);
-}
-
-__global__ void __launch_bounds__(RS_T) rs_hist_kernel(const uint64_t *__restrict__ keys,
-                                                       const uint32_t *__restrict__ vals,
-                                                       const int *__restrict__ inst, int n,
-                                                       int shift, uint32_t *hist, int ntiles)
-{
-    __shared__ uint32_t h[256];
-    h[threadIdx.x] = 0;
-    __syncthreads();
-    int base = blockIdx.x * RS_TILE;
-#pragma unroll
-    for (int i = 0; i < RS_I; ++i) {
-        int s = base + i * RS_T + threadIdx.x;
-        if (s < n) atomicAdd(&h[rs_digit(keys, vals, inst, s, shift)], 1u);
-    }
-    __syncthreads();
-    hist[threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
-}
+constexpr uint32_t RS_AGG = 1u << 30, RS_INC = 2u << 30, RS_CNT = RS_AGG - 1u;
+constexpr int RS_SPIN = 1 << 22;  // look-back polls before giving up (error, no hang)
 
 // block-wide exclusive scan helper for 256 threads, returns the block total
 __device__ __forceinline__ uint32_t block_scan_256(uint32_t v, uint32_t &excl, uint32_t *ws)
@@ -228,51 +208,85 @@ __device__ __forceinline__ uint32_t block_scan_256(uint32_t v, uint32_t &excl, u
     return total;
 }
 
-__global__ void __launch_bounds__(256) rs_scan_rows_kernel(uint32_t *hist, int ntiles,
-                                                           uint32_t *dtotal)
+// digit counts of all passes: ghist[p][d] for the 8 key digits and, with
+// inst, the 2 instance-id digits.  Each thread counts RS_GE consecutive
+// keys, adding runs of one digit with one shared atomic: the keys are nearly
+// in curve order, so the high digits come in long runs.
+constexpr int RS_GE = 8;
+__global__ void __launch_bounds__(256) rs_ghist_kernel(const uint64_t *__restrict__ keys,
+                                                       const int *__restrict__ inst, int n,
+                                                       uint32_t *ghist)
 {
-    __shared__ uint32_t ws[8];
-    uint32_t *row = hist + (size_t)blockIdx.x * ntiles;
-    uint32_t carry = 0;
-    for (int b = 0; b < ntiles; b += 256) {
-        int i = b + threadIdx.x;
-        uint32_t v = i < ntiles ? row[i] : 0, ex;
-        uint32_t tot = block_scan_256(v, ex, ws);
-        if (i < ntiles) row[i] = carry + ex;
-        carry += tot;
+    __shared__ uint32_t h[10][256];
+    for (int k = threadIdx.x; k < 10 * 256; k += 256) (&h[0][0])[k] = 0;
+    __syncthreads();
+    const int np = inst ? 10 : 8;
+    for (int b = blockIdx.x * 256 * RS_GE; b < n; b += gridDim.x * 256 * RS_GE) {
+        const int s0 = b + threadIdx.x * RS_GE;
+        uint32_t cur[10], cnt[10];
+#pragma unroll
+        for (int p = 0; p < 10; ++p) { cur[p] = 0; cnt[p] = 0; }
+        for (int e = 0; e < RS_GE && s0 + e < n; ++e) {
+            const uint64_t key = keys[s0 + e];
+            const uint32_t iv = inst ? (uint32_t)inst[s0 + e] : 0u;
+#pragma unroll
+            for (int p = 0; p < 10; ++p) {
+                if (p >= np) break;
+                const uint32_t d = p < 8 ? (uint32_t)((key >> (8 * p)) & 255u) : (iv >> (8 * (p - 8))) & 255u;
+                if (cnt[p] != 0 && d != cur[p]) {
+                    atomicAdd(&h[p][cur[p]], cnt[p]);
+                    cnt[p] = 0;
+                }
+                cur[p] = d;
+                ++cnt[p];
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < 10; ++p)
+            if (cnt[p] != 0) atomicAdd(&h[p][cur[p]], cnt[p]);
     }
-    if (threadIdx.x == 0) dtotal[blockIdx.x] = carry;
+    __syncthreads();
+    for (int k = threadIdx.x; k < np * 256; k += 256) {
+        const uint32_t v = (&h[0][0])[k];
+        if (v) atomicAdd(&ghist[k], v);
+    }
 }
 
-// Stable scatter of one tile: warp w owns the contiguous keys
-// [w * 256, (w + 1) * 256) of the tile and ranks them in 8 rounds of 32 with
-// __match_any_sync and a warp-private digit counter row; one prefix over the
-// warps per digit then gives each key its place in a digit-ordered copy of
-// the tile in shared memory, which is written out digit run by digit run
-// (consecutive threads, consecutive addresses).  Tile order is
-// (warp, round, lane), so equal digits keep their input order.
-__global__ void __launch_bounds__(RS_T) rs_scatter_kernel(
+// gstart[p][d] = exclusive scan of ghist[p][.]   (block p)
+__global__ void __launch_bounds__(256) rs_gscan_kernel(const uint32_t *ghist, uint32_t *gstart)
+{
+    __shared__ uint32_t ws[8];
+    uint32_t ex;
+    block_scan_256(ghist[blockIdx.x * 256 + threadIdx.x], ex, ws);
+    gstart[blockIdx.x * 256 + threadIdx.x] = ex;
+}
+
+// One pass: warp w of a tile owns the contiguous keys [w * 256, (w + 1) * 256)
+// of the tile and ranks them in 8 rounds of 32 with __match_any_sync and a
+// warp-private digit counter row; tile order is (warp, round, lane), so equal
+// digits keep their input order.
+__global__ void __launch_bounds__(RS_T) rs_onesweep_kernel(
     const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const int *__restrict__ inst, int n, int shift,
-    const uint32_t *__restrict__ hist, const uint32_t *__restrict__ dtotal, int ntiles)
+    const uint32_t *__restrict__ gstart, uint32_t *status, int *tile_counter, int *err)
 {
-    __shared__ uint32_t gbase[256];   // first output slot of (digit, this tile)
+    __shared__ uint32_t gbase[256];   // first output slot of each digit for this tile
     __shared__ uint32_t tstart[256];  // first slot of each digit in the sorted tile
     __shared__ uint32_t wcnt[8][256];
     __shared__ uint32_t ws[8];
+    __shared__ int s_tile;
     __shared__ uint64_t skey[RS_TILE];
     __shared__ uint32_t sval[RS_TILE];
     __shared__ uint8_t sdig[RS_TILE];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    uint32_t dstart;  // exclusive scan of the digit totals
-    block_scan_256(dtotal[tid], dstart, ws);
-    gbase[tid] = hist[tid * ntiles + blockIdx.x] + dstart;
+    if (tid == 0) s_tile = atomicAdd(tile_counter, 1);
     uint32_t *flat = &wcnt[0][0];
 #pragma unroll
     for (int k = 0; k < 8; ++k) flat[k * 256 + tid] = 0;
     __syncthreads();
+    const int tile = s_tile;
     const uint32_t lt = (1u << lane) - 1u;
-    const int tile0 = blockIdx.x * RS_TILE;
+    const int tile0 = tile * RS_TILE;
     const int wbase = tile0 + w * (RS_TILE / 8);
     uint64_t key[RS_I];
     uint32_t val[RS_I], dig[RS_I], rank[RS_I];
@@ -294,8 +308,8 @@ __global__ void __launch_bounds__(RS_T) rs_scatter_kernel(
         __syncwarp();
     }
     __syncthreads();
+    uint32_t cnt;  // keys of digit tid in this tile
     {
-        // per digit: offsets of the warps inside the digit, and the tile count
         uint32_t acc = 0;
 #pragma unroll
         for (int ww = 0; ww < 8; ++ww) {
@@ -303,10 +317,32 @@ __global__ void __launch_bounds__(RS_T) rs_scatter_kernel(
             wcnt[ww][tid] = acc;
             acc += c;
         }
+        cnt = acc;
         uint32_t ex;
         block_scan_256(acc, ex, ws);  // digit starts inside the sorted tile
         tstart[tid] = ex;
     }
+    // publish this tile's count of digit tid, then add up the predecessors'
+    volatile uint32_t *st = status;
+    st[(size_t)tile * 256 + tid] = (tile == 0 ? RS_INC : RS_AGG) | cnt;
+    uint32_t excl = 0;
+    for (int t = tile - 1; t >= 0; --t) {
+        uint32_t v = st[(size_t)t * 256 + tid];
+        int spin = 0;
+        while ((v & ~RS_CNT) == 0u) {
+            if (++spin > RS_SPIN) {  // a predecessor never published: report, do not hang
+                raise_error(err, SPH_ERR_TIMEOUT);
+                v = RS_INC;
+                break;
+            }
+            __nanosleep(32);
+            v = st[(size_t)t * 256 + tid];
+        }
+        excl += v & RS_CNT;
+        if (v & RS_INC) break;
+    }
+    if (tile > 0) st[(size_t)tile * 256 + tid] = RS_INC | (excl + cnt);
+    gbase[tid] = gstart[tid] + excl;
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < RS_I; ++r) {
@@ -747,17 +783,23 @@ cudaError_t build_tree(Ctx &c, const sph_state &s, const sph_params &p, bool ful
     morton_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(pos, inst, n, bb, s.keys, c.idx_a);
     // 3. radix sort (key, slot); a batch adds stable passes on the instance id,
     //    which puts every instance back on its own slots
-    int ntiles = div_up(n, RS_TILE);
+    const int ntiles = div_up(n, RS_TILE);
     uint64_t *kin = s.keys, *kout = c.keys_alt;
     uint32_t *vin = c.idx_a, *vout = c.idx_b;
     const int npass = batch ? 10 : 8;
+    // digit counts of all passes, their scans, fresh look-back words and tile counters
+    SPH_TRY(cudaMemsetAsync(c.rs_ghist, 0, sizeof(uint32_t) * 10 * 256, st));
+    SPH_TRY(cudaMemsetAsync(c.rs_tiles, 0, sizeof(int) * 10, st));
+    SPH_TRY(cudaMemsetAsync(c.rs_status, 0, sizeof(uint32_t) * 256 * (size_t)ntiles * npass, st));
+    rs_ghist_kernel<<<grid_for(c, div_up(n, RS_GE), 256), 256, 0, st>>>(kin, inst, n, c.rs_ghist);
+    rs_gscan_kernel<<<npass, 256, 0, st>>>(c.rs_ghist, c.rs_gstart);
     for (int pass = 0; pass < npass; ++pass) {
         const int *dinst = pass >= 8 ? inst : nullptr;
         int shift = pass >= 8 ? 8 * (pass - 8) : 8 * pass;
-        rs_hist_kernel<<<ntiles, RS_T, 0, st>>>(kin, vin, dinst, n, shift, c.hist, ntiles);
-        rs_scan_rows_kernel<<<256, 256, 0, st>>>(c.hist, ntiles, c.dtotal);
-        rs_scatter_kernel<<<ntiles, RS_T, 0, st>>>(kin, vin, kout, vout, dinst, n, shift, c.hist,
-                                                   c.dtotal, ntiles);
+        rs_onesweep_kernel<<<ntiles, RS_T, 0, st>>>(kin, vin, kout, vout, dinst, n, shift,
+                                                    c.rs_gstart + 256 * pass,
+                                                    c.rs_status + (size_t)256 * ntiles * pass,
+                                                    c.rs_tiles + pass, c.d_err);
         std::swap(kin, kout);
         std::swap(vin, vout);
     }
