@@ -199,9 +199,10 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_list_kernel(DensArgs 
                     const float hinv = 1.f / h;
                     const float R = 2.f * h;
                     const float R2 = R * R;
-                    // Two entries per iteration, no branch on the distance: f and
-                    // f' vanish for q >= 2, so entries beyond 2 h add nothing.  A
-                    // missing second entry repeats the first with zero mass.
+                    // Two consecutive entries per lane and iteration (one 8-byte
+                    // load of the list), no branch on the distance: f and f' vanish
+                    // for q >= 2, so entries beyond 2 h add nothing.  A missing
+                    // second entry repeats the first with zero mass.
                     auto entry = [&](float4 pj, float4 vj, float mj) {
                         const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
                         const float r2 = dx * dx + dy * dy + dz * dz;
@@ -209,15 +210,14 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_list_kernel(DensArgs 
                         cnt += (mj > 0.f && r2 < R2) ? 1 : 0;
                         pair_sums(r2, mj, vd, hinv, s0, s1, s2);
                     };
-                    for (int e = sub; e < len; e += 2 * L) {
-                        const bool two = e + L < len;
-                        const int j0 = __ldcs(lst + e);
-                        const int j1 = two ? __ldcs(lst + e + L) : j0;
+                    for (int e = 2 * sub; e < len; e += 2 * L) {
+                        const int2 jj = __ldcs(reinterpret_cast<const int2 *>(lst + e));
+                        const bool b1 = e + 1 < len;
                         float4 p0, v0, p1, v1;
-                        ld_rec(a.rec, j0, keep, p0, v0);
-                        ld_rec(a.rec, j1, keep, p1, v1);
+                        ld_rec(a.rec, jj.x, keep, p0, v0);
+                        ld_rec(a.rec, b1 ? jj.y : jj.x, keep, p1, v1);
                         entry(p0, v0, p0.w);
-                        entry(p1, v1, two ? p1.w : 0.f);
+                        entry(p1, v1, b1 ? p1.w : 0.f);
                     }
                     s0 = seg_sum(s0, L);
                     s1 = seg_sum(s1, L);

@@ -180,8 +180,9 @@ __global__ void __launch_bounds__(kForceWarps * 32) force_list_kernel(ForceArgs 
                 ForceTarget T;
                 T.init(a.pos[i], a.vel[i], a.prop[i], a);
                 const int *__restrict__ lst = a.nl_idx + (size_t)i * kNbrCap;
-                // Four entries per iteration, no branch: an entry outside the pair
-                // set (or padding) gets zero mass.  The particle itself (r = 0) is
+                // Four consecutive entries per lane and iteration (one 16-byte
+                // load of the list), no branch: an entry outside the pair set (or
+                // padding) gets zero mass.  The particle itself (r = 0) is
                 // left out; a distinct particle at r = 0 would add nothing either
                 // (every term carries f'(0) = 0 or v_ij.r_ij / r = 0).
                 auto entry = [&](int j, bool valid) {
@@ -193,20 +194,17 @@ __global__ void __launch_bounds__(kForceWarps * 32) force_list_kernel(ForceArgs 
                     const bool in = valid && r2 > 0.f && r2 < R * R;
                     T.pair(pj, vj, qj, in ? pj.w : 0.f, in, a);
                 };
-                for (int e = sub; e < len; e += 4 * L) {
-                    const bool b1 = e + L < len, b2 = e + 2 * L < len, b3 = e + 3 * L < len;
-                    const int j0 = __ldcs(lst + e);
-                    const int j1 = b1 ? __ldcs(lst + e + L) : j0;
-                    const int j2 = b2 ? __ldcs(lst + e + 2 * L) : j0;
-                    const int j3 = b3 ? __ldcs(lst + e + 3 * L) : j0;
-                    entry(j0, true);
-                    entry(j1, b1);
-                    entry(j2, b2);
-                    entry(j3, b3);
+                for (int e = 4 * sub; e < len; e += 4 * L) {
+                    const int4 jj = __ldcs(reinterpret_cast<const int4 *>(lst + e));
+                    const bool b1 = e + 1 < len, b2 = e + 2 < len, b3 = e + 3 < len;
+                    entry(jj.x, true);
+                    entry(b1 ? jj.y : jj.x, b1);
+                    entry(b2 ? jj.z : jj.x, b2);
+                    entry(b3 ? jj.w : jj.x, b3);
                 }
                 T.finish(L, act && sub == 0, i, a);
                 n_pairs += T.cnt;
-                n_cand += act ? (unsigned long long)((len - sub + L - 1) / L) : 0ull;
+                n_cand += act && sub == 0 ? (unsigned long long)len : 0ull;
             }
         }
     }
