@@ -325,21 +325,30 @@ __global__ void __launch_bounds__(RS_T) rs_onesweep_kernel(
     // publish this tile's count of digit tid, then add up the predecessors'
     volatile uint32_t *st = status;
     st[(size_t)tile * 256 + tid] = (tile == 0 ? RS_INC : RS_AGG) | cnt;
+    // predecessors are read 8 at a time, so a long look-back costs one memory
+    // latency per 8 tiles; tiles before tile 0 count as inclusive zeros
     uint32_t excl = 0;
-    for (int t = tile - 1; t >= 0; --t) {
-        uint32_t v = st[(size_t)t * 256 + tid];
-        int spin = 0;
-        while ((v & ~RS_CNT) == 0u) {
-            if (++spin > RS_SPIN) {  // a predecessor never published: report, do not hang
-                raise_error(err, SPH_ERR_TIMEOUT);
-                v = RS_INC;
-                break;
+    bool done = tile == 0;
+    for (int t0 = tile - 1; !done; t0 -= 8) {
+        uint32_t v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = t0 - k >= 0 ? (uint32_t)st[(size_t)(t0 - k) * 256 + tid] : (uint32_t)(RS_INC + 0u);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (done) break;
+            int spin = 0;
+            while ((v[k] & ~RS_CNT) == 0u) {
+                if (++spin > RS_SPIN) {  // a predecessor never published: report, do not hang
+                    raise_error(err, SPH_ERR_TIMEOUT);
+                    v[k] = RS_INC;
+                    break;
+                }
+                __nanosleep(32);
+                v[k] = st[(size_t)(t0 - k) * 256 + tid];
             }
-            __nanosleep(32);
-            v = st[(size_t)t * 256 + tid];
+            excl += v[k] & RS_CNT;
+            done = (v[k] & RS_INC) != 0u;
         }
-        excl += v & RS_CNT;
-        if (v & RS_INC) break;
     }
     if (tile > 0) st[(size_t)tile * 256 + tid] = RS_INC | (excl + cnt);
     gbase[tid] = gstart[tid] + excl;
