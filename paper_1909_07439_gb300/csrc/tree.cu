@@ -180,6 +180,7 @@ __global__ void morton_kernel(const float4 *__restrict__ pos, const int *__restr
 constexpr int RS_T = 256, RS_I = 8, RS_TILE = RS_T * RS_I;
 constexpr uint32_t RS_AGG = 1u << 30, RS_INC = 2u << 30, RS_CNT = RS_AGG - 1u;
 constexpr int RS_SPIN = 1 << 22;  // look-back polls before giving up (error, no hang)
+constexpr int RS_LB = 8;           // predecessor tiles read together in the look-back
 
 // block-wide exclusive scan helper for 256 threads, returns the block total
 __device__ __forceinline__ uint32_t block_scan_256(uint32_t v, uint32_t &excl, uint32_t *ws)
@@ -262,9 +263,10 @@ __global__ void __launch_bounds__(256) rs_gscan_kernel(const uint32_t *ghist, ui
 }
 
 // One pass: warp w of a tile owns the contiguous keys [w * 256, (w + 1) * 256)
-// of the tile and ranks them in 8 rounds of 32 with __match_any_sync and a
-// warp-private digit counter row; tile order is (warp, round, lane), so equal
-// digits keep their input order.
+// of the tile and ranks them in 8 rounds of 32: the lanes holding the same
+// digit are found with one ballot per digit bit, and a warp-private digit
+// counter row accumulates; tile order is (warp, round, lane), so equal digits
+// keep their input order.
 __global__ void __launch_bounds__(RS_T) rs_onesweep_kernel(
     const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const int *__restrict__ inst, int n, int shift,
@@ -300,7 +302,12 @@ __global__ void __launch_bounds__(RS_T) rs_onesweep_kernel(
                                    : (uint32_t)((key[r] >> shift) & 255u))
                            : 256u + lane;
         dig[r] = d;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t peers = 0xffffffffu;
+#pragma unroll
+        for (int b = 0; b < 9; ++b) {
+            const uint32_t bb = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? bb : ~bb;
+        }
         const uint32_t old = valid ? wcnt[w][d] : 0u;
         rank[r] = old + __popc(peers & lt);
         __syncwarp();
@@ -325,16 +332,17 @@ __global__ void __launch_bounds__(RS_T) rs_onesweep_kernel(
     // publish this tile's count of digit tid, then add up the predecessors'
     volatile uint32_t *st = status;
     st[(size_t)tile * 256 + tid] = (tile == 0 ? RS_INC : RS_AGG) | cnt;
-    // predecessors are read 8 at a time, so a long look-back costs one memory
-    // latency per 8 tiles; tiles before tile 0 count as inclusive zeros
+    // predecessors are read RS_LB at a time, so a long look-back costs one
+    // memory latency per RS_LB tiles; tiles before tile 0 count as inclusive zeros
     uint32_t excl = 0;
     bool done = tile == 0;
-    for (int t0 = tile - 1; !done; t0 -= 8) {
-        uint32_t v[8];
+    for (int t0 = tile - 1; !done; t0 -= RS_LB) {
+        uint32_t v[RS_LB];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = t0 - k >= 0 ? (uint32_t)st[(size_t)(t0 - k) * 256 + tid] : (uint32_t)(RS_INC + 0u);
+        for (int k = 0; k < RS_LB; ++k)
+            v[k] = t0 - k >= 0 ? (uint32_t)st[(size_t)(t0 - k) * 256 + tid] : (uint32_t)(RS_INC + 0u);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
+        for (int k = 0; k < RS_LB; ++k) {
             if (done) break;
             int spin = 0;
             while ((v[k] & ~RS_CNT) == 0u) {
