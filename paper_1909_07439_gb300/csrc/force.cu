@@ -89,9 +89,15 @@ struct ForceTarget {
     __device__ __forceinline__ void pair(float4 pj, float4 vj, float4 qj, float mj, bool in,
                                          const ForceArgs &a)
     {
-        const float Ai = qi.z, ci = qi.w;
         const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
-        const float r2 = dx * dx + dy * dy + dz * dz;
+        pair_d(dx, dy, dz, dx * dx + dy * dy + dz * dz, vj, qj, mj, in, a);
+    }
+
+    // the same with the separation x_i - x_j and its squared length given
+    __device__ __forceinline__ void pair_d(float dx, float dy, float dz, float r2, float4 vj, float4 qj,
+                                           float mj, bool in, const ForceArgs &a)
+    {
+        const float Ai = qi.z, ci = qi.w;
         const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
         const float r = r2 * rinv;
         const float hinv_j = __fdividef(1.f, qj.x);
@@ -189,10 +195,13 @@ __global__ void __launch_bounds__(kForceWarps * 32) force_list_kernel(ForceArgs 
                     const float4 pj = ld_keep(a.pos, j, keep);
                     const float4 qj = ld_keep(a.prop, j, keep);
                     const float4 vj = ld_keep(a.vel, j, keep);
-                    const float r2 = canon_r2(T.xi.x, T.xi.y, T.xi.z, pj.x, pj.y, pj.z);
+                    // canonical separation: decides the pair set and feeds the pair terms
+                    const float dx = __fsub_rn(T.xi.x, pj.x), dy = __fsub_rn(T.xi.y, pj.y),
+                                dz = __fsub_rn(T.xi.z, pj.z);
+                    const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
                     const float R = 2.0f * fmaxf(T.qi.x, qj.x);
                     const bool in = valid && r2 > 0.f && r2 < R * R;
-                    T.pair(pj, vj, qj, in ? pj.w : 0.f, in, a);
+                    T.pair_d(dx, dy, dz, r2, vj, qj, in ? pj.w : 0.f, in, a);
                 };
                 for (int e = 4 * sub; e < len; e += 4 * L) {
                     const int4 jj = __ldcs(reinterpret_cast<const int4 *>(lst + e));
