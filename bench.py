@@ -165,6 +165,14 @@ def run_ours(args):
     for _ in range(args.warmup):
         native.sph_step(ctx, s.c, p, d_dt, d_t)
     native.sph_sync(ctx)
+    tuned = None
+    if not (args.n_leaf or args.n_group):
+        # N_group and N_leaf tuned on the warmed-up state (untimed, state restored)
+        from paper_1909_07439_gb300 import autotune
+        p, tuned = autotune.tune_step(ctx, s, d_dt, f"sedov{args.side}", base=p, steps=20)
+        for _ in range(2):
+            native.sph_step(ctx, s.c, p, d_dt, d_t)
+        native.sph_sync(ctx)
     native.sph_get_stats(ctx)          # reset counters
     native.sph_get_timing(ctx)         # reset stage timers
     native.sph_set_timing(ctx, True)
@@ -236,9 +244,11 @@ def run_ours(args):
             "config": {"workload": f"sedov_blast_lattice_{args.side}^3", "n_particles": n,
                        "step": "sph_step: KDK + tree build + density Newton + force + Courant dt",
                        "kernel": "M4", "n_leaf": p.n_leaf, "n_group": p.n_group,
+                       "tuned": tuned is not None,
                        "hfact": round(p.hfact, 4), "l2": "flushed between timed steps",
                        "parallelism": f"replicas x{ws}"},
             "pair_interactions_per_s": pair_rate,
+            "autotune": tuned,
             "clocks": clk,
             "e2e": e2e,
             "gpu_launches": int(sum(launches.values())),
@@ -357,9 +367,11 @@ def run_adjoint(args):
 
 def run_plummer(args):
     """Strongly inhomogeneous evaluation: 2^24-particle Plummer sphere,
-    tree build + density + force of one evaluation."""
+    tree build + density + force of one evaluation, N_group and N_leaf tuned
+    on the state."""
     import torch
     from paper_1909_07439_gb300 import DeviceState, inputs, native
+    from paper_1909_07439_gb300 import autotune
     w = inputs.plummer(1 << args.plummer_log2)
     ctx = native.sph_create(w.n, 0)
     s = DeviceState.from_arrays(w.pos, w.vel, w.h)
@@ -368,6 +380,10 @@ def run_plummer(args):
     native.sph_density(ctx, s.c, p)      # converges h from the analytic-density guess
     native.sph_force(ctx, s.c, p)
     native.sph_sync(ctx)
+    d_dt = torch.zeros(1, dtype=torch.float32, device="cuda")
+    p, tuned = autotune.tune_step(ctx, s, d_dt, f"plummer{args.plummer_log2}", base=p, steps=2,
+                                  evaluate_only=True,
+                                  candidates=[(g, l) for g in (8, 16, 32) for l in (16, 32, 64)])
     native.sph_get_stats(ctx)
     native.sph_get_timing(ctx)
     native.sph_set_timing(ctx, True)
@@ -392,7 +408,8 @@ def run_plummer(args):
             "stage_ms": {k: v / reps for k, v in stage.items()},
             "h_range": [float(hh.min()), float(hh.max())],
             "streamed_groups": stats["streamed_groups"] / reps,
-            "n_nodes": stats["n_nodes"], "n_groups": stats["n_groups"]}
+            "n_nodes": stats["n_nodes"], "n_groups": stats["n_groups"],
+            "n_group": p.n_group, "n_leaf": p.n_leaf, "autotune": tuned}
 
 
 def run_e2e(native, ctx, s, p, n, args, stream):

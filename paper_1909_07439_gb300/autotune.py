@@ -1,7 +1,7 @@
-"""Autotuner for the batched step: picks the group size (N_group) and the leaf
-size (N_leaf) by timing a few graph-replayed steps of the actual batch,
+"""Autotuners for the group size (N_group) and the leaf size (N_leaf): time a
+few steps of the actual state (graph-replayed for a batch) per candidate,
 restoring the state between trials.  Results are cached in a JSON file keyed
-by device, particle count and instance count."""
+by device, particle count and instance count (or workload tag)."""
 from __future__ import annotations
 
 import json
@@ -68,6 +68,57 @@ def tune_batch(ctx, state, d_offsets, n_inst, base=None, steps=2, use_cache=True
         trials.append({"n_group": g, "n_leaf": l, "ms_per_step": e0.elapsed_time(e1) / steps})
     for f, v in saved.items():
         getattr(state, f).copy_(v)
+    best = min(trials, key=lambda r: r["ms_per_step"])
+    report = {"n_group": best["n_group"], "n_leaf": best["n_leaf"], "trials": trials}
+    if use_cache:
+        cache[key] = report
+        _save_cache(cache)
+    return native.sph_params_default(**{**_as_dict(base), "n_group": best["n_group"],
+                                        "n_leaf": best["n_leaf"]}), report
+
+
+STEP_CANDIDATES = [(g, l) for g in (8, 16, 32) for l in (16, 32)]
+
+
+def tune_step(ctx, state, d_dt, tag, base=None, steps=3, use_cache=True,
+              candidates=STEP_CANDIDATES, evaluate_only=False):
+    """Return (sph_params, report) with the fastest (n_group, n_leaf) for
+    sph_step on this state (or, with evaluate_only, for one tree build +
+    density + force evaluation).  ``state`` and ``d_dt`` are left as they were."""
+    import torch
+    base = base or native.sph_params_default()
+    key = _key(torch, state.n, tag)
+    cache = _load_cache() if use_cache else {}
+    if key in cache and "n_leaf" in cache[key]:
+        g, l = cache[key]["n_group"], cache[key]["n_leaf"]
+        return native.sph_params_default(**{**_as_dict(base), "n_group": g, "n_leaf": l}), cache[key]
+    saved = {f: getattr(state, f).clone() for f in state.FIELDS4 + state.FIELDS1 + ("perm", "keys")}
+    dt0 = d_dt.clone()
+    trials = []
+    for g, l in candidates:
+        p = native.sph_params_default(**{**_as_dict(base), "n_group": g, "n_leaf": l})
+        def run(k):
+            for _ in range(k):
+                if evaluate_only:
+                    native.sph_build_tree(ctx, state.c, p)
+                    native.sph_density(ctx, state.c, p)
+                    native.sph_force(ctx, state.c, p)
+                else:
+                    native.sph_step(ctx, state.c, p, d_dt)
+        for f, v in saved.items():
+            getattr(state, f).copy_(v)
+        d_dt.copy_(dt0)
+        run(1)  # warm
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        run(steps)
+        e1.record()
+        native.sph_sync(ctx)
+        trials.append({"n_group": g, "n_leaf": l, "ms_per_step": e0.elapsed_time(e1) / steps})
+    for f, v in saved.items():
+        getattr(state, f).copy_(v)
+    d_dt.copy_(dt0)
+    native.sph_sync(ctx)
     best = min(trials, key=lambda r: r["ms_per_step"])
     report = {"n_group": best["n_group"], "n_leaf": best["n_leaf"], "trials": trials}
     if use_cache:
