@@ -541,6 +541,9 @@ cudaError_t force_bwd(Ctx &c, const sph_state &s, const sph_params &p, const flo
     op.beta = p.beta_av;
     op.alpha_u = p.alpha_u;
     op.gamma = p.gamma;
+    // the force-set walk needs node and group h_max of the current h
+    cudaError_t e = update_hmax(c, s, p, st);
+    if (e != cudaSuccess) return e;
     return launch_pairwalk<96>(c, s, false, op, st, nullptr);
 }
 

@@ -414,7 +414,8 @@ cudaError_t configure_force_kernels()
     return e;
 }
 
-cudaError_t force_prep(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st)
+cudaError_t force_prep(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st,
+                       bool hmax_now)
 {
     const int n = (int)s.n;
     int grid = (n + 255) / 256;
@@ -423,7 +424,7 @@ cudaError_t force_prep(Ctx &c, const sph_state &s, const sph_params &p, cudaStre
                                             p.gamma, c.d_err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return update_hmax(c, s, p, st);
+    return hmax_now ? update_hmax(c, s, p, st) : cudaSuccess;
 }
 
 cudaError_t force_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st,
@@ -463,6 +464,10 @@ cudaError_t force_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStre
     if (e != cudaSuccess) return e;
     force_list_kernel<<<c.num_sms * blocks, kForceWarps * 32, 0, st>>>(a);
     e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the walking kernel needs node and group h_max of the final h; refreshed
+    // only when some batch was handed over
+    e = update_hmax(c, s, p, st, a.n_fallback);
     if (e != cudaSuccess) return e;
     int cap = p.tile > 0 ? p.tile : 96;
     if (cap <= 64) return launch_force_walk<64>(c, a, st);

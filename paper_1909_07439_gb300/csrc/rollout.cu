@@ -293,7 +293,7 @@ cudaError_t evaluate(Ctx &c, sph_state &w, const sph_params &p, float *d_dt, cud
 {
     RT(build_tree(c, w, p, true, st));
     RT(density_pass(c, w, p, st));
-    RT(force_prep(c, w, p, st));
+    RT(force_prep(c, w, p, st, true));  // the adjoint walks need the final h_max
     RT(force_pass(c, w, p, st));
     return courant_dt(c, w, p, d_dt, st);
 }
@@ -305,7 +305,7 @@ cudaError_t step(Ctx &c, sph_state &w, const sph_params &p, const float *dt, boo
     RT(kick_drift(c, w, dt, st));
     RT(build_tree(c, w, p, false, st));
     RT(density_pass(c, w, p, st));
-    RT(force_prep(c, w, p, st));
+    RT(force_prep(c, w, p, st, true));  // the adjoint walks need the final h_max
     RT(force_pass(c, w, p, st));
     if (partial) return cudaSuccess;
     RT(kick_close(c, w, dt, nullptr, st));

@@ -114,7 +114,7 @@ sph_status check_params(Ctx &c, const sph_params *p)
     } while (0)
 
 constexpr int kTreeLaunches = 28;
-constexpr int kPrepLaunches = 3;
+constexpr int kPrepLaunches = 1;
 
 // tree_fresh: the tree was just built from this state (node and group h_max
 // hold the current h, and the packed particle records the current pos, vel)
@@ -146,7 +146,7 @@ sph_status do_force(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_
         CK(force_prep(c, s, p, st), "force_prep");
         if (!records_fresh) CK(pack_records(c, s, st), "pack");
     }
-    StageScope sc(c, ST_FORCE, st, 2);
+    StageScope sc(c, ST_FORCE, st, 4);
     CK(force_pass(c, s, p, st), "force");
     return SPH_OK;
 }

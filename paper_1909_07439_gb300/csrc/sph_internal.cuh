@@ -159,7 +159,9 @@ struct Ctx {
 cudaError_t build_tree(Ctx &c, const sph_state &s, const sph_params &p, bool full_permute,
                        cudaStream_t st, const Batch *batch = nullptr);
 cudaError_t instance_map(Ctx &c, const int64_t *d_offsets, int n_inst, int n, cudaStream_t st);
-cudaError_t update_hmax(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st);
+// node and group h_max of the current h; gate != nullptr: only if *gate != 0
+cudaError_t update_hmax(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st,
+                        const int *gate = nullptr);
 // c.rec from the state's pos and vel (build_tree writes it too)
 cudaError_t pack_records(Ctx &c, const sph_state &s, cudaStream_t st);
 cudaError_t scan_exclusive_int(Ctx &c, const int *in, int *out, int n, int *total_dev,
@@ -180,7 +182,10 @@ cudaError_t neighbour_lists(Ctx &c, const sph_state &s, const sph_params &p, int
                             int64_t *d_off, int32_t *d_idx, int64_t cap, int64_t *h_total,
                             cudaStream_t st);
 // force.cu
-cudaError_t force_prep(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st);
+// hmax_now: also refresh node and group h_max (force_pass refreshes them
+// itself, only when a batch falls back to a walk)
+cudaError_t force_prep(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st,
+                       bool hmax_now = false);
 cudaError_t force_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st,
                        const Batch *batch = nullptr);
 cudaError_t configure_density_kernels();

@@ -652,11 +652,13 @@ __global__ void node_finish_kernel(const uint64_t *__restrict__ keys, const int 
 }
 
 // Bottom-up bounds: leaves from particles, parents from children; the last
-// child to finish (arrival counter) computes its parent.  what = 0: AABB of
+// child to finish (arrival counter, reset by that child) computes its parent.
+// gate != nullptr: do nothing unless *gate != 0.  what = 0: AABB of
 // positions and h_max; what = 1: h_max only.
 __global__ void node_bounds_kernel(const float4 *__restrict__ pos, const float *__restrict__ h,
-                                   Tree t, const int *sizes, int what)
+                                   Tree t, const int *sizes, int what, const int *gate)
 {
+    if (gate && *gate == 0) return;
     int nn = sizes[SZ_NODES];
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nn; k += gridDim.x * blockDim.x) {
         if (t.node_nchild[k] != 0) continue;
@@ -685,6 +687,7 @@ __global__ void node_bounds_kernel(const float4 *__restrict__ pos, const float *
             __threadfence();
             int old = atomicAdd(&t.node_arrive[p], 1);
             if (old != t.node_nchild[p] - 1) break;
+            t.node_arrive[p] = 0;  // the last child: ready for the next pass
             __threadfence();
             int cf = t.node_child[p], nc = t.node_nchild[p];
             if (what == 0) {
@@ -719,8 +722,9 @@ __global__ void group_write_kernel(const int *__restrict__ lv_grp, const int *__
 
 // what = 0: count + AABB (h_max too); what = 1: h_max only
 __global__ void group_bounds_kernel(const float4 *__restrict__ pos, const float *__restrict__ h,
-                                    int n, Tree t, const int *sizes, int what)
+                                    int n, Tree t, const int *sizes, int what, const int *gate)
 {
+    if (gate && *gate == 0) return;
     int ng = sizes[SZ_GROUPS];
     for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x) {
         int s = t.grp_ref[g].x;
@@ -856,7 +860,7 @@ cudaError_t build_tree(Ctx &c, const sph_state &s, const sph_params &p, bool ful
     int *gidx = (int *)c.tmp1[1];  // scratch: tmp1[1..] are free once copied back
     SPH_TRY(scan_mode(c, t.lv_grp, gidx, n, 1, c.d_sizes + SZ_GROUPS, st));
     group_write_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(t.lv_grp, gidx, n, t);
-    group_bounds_kernel<<<grid_for(c, n, 128), 128, 0, st>>>(pos, s.h, n, t, c.d_sizes, 0);
+    group_bounds_kernel<<<grid_for(c, n, 128), 128, 0, st>>>(pos, s.h, n, t, c.d_sizes, 0, nullptr);
     // nodes
     int nb = div_up(n, kChopBlock);
     int *blk_off = (int *)c.tmp1[2];
@@ -867,7 +871,7 @@ cudaError_t build_tree(Ctx &c, const sph_state &s, const sph_params &p, bool ful
     level_start_kernel<<<1, 32, 0, st>>>(blk_off, nb, ntotal, t, c.d_sizes);
     node_finish_kernel<<<grid_for(c, t.cap_nodes, 256), 256, 0, st>>>(s.keys, inst, offs, n,
                                                                        p.n_leaf, t, c.d_sizes);
-    node_bounds_kernel<<<grid_for(c, t.cap_nodes, 128), 128, 0, st>>>(pos, s.h, t, c.d_sizes, 0);
+    node_bounds_kernel<<<grid_for(c, t.cap_nodes, 128), 128, 0, st>>>(pos, s.h, t, c.d_sizes, 0, nullptr);
     return cudaGetLastError();
 }
 
@@ -887,15 +891,15 @@ cudaError_t pack_records(Ctx &c, const sph_state &s, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t update_hmax(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st)
+cudaError_t update_hmax(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st,
+                        const int *gate)
 {
     (void)p;
     Tree &t = c.tree;
-    SPH_TRY(cudaMemsetAsync(t.node_arrive, 0, sizeof(int) * (size_t)t.cap_nodes, st));
     node_bounds_kernel<<<grid_for(c, t.cap_nodes, 128), 128, 0, st>>>((const float4 *)s.pos, s.h, t,
-                                                                       c.d_sizes, 1);
+                                                                       c.d_sizes, 1, gate);
     group_bounds_kernel<<<grid_for(c, s.n, 128), 128, 0, st>>>((const float4 *)s.pos, s.h,
-                                                               (int)s.n, t, c.d_sizes, 1);
+                                                               (int)s.n, t, c.d_sizes, 1, gate);
     return cudaGetLastError();
 }
 
