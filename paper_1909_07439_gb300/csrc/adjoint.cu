@@ -194,6 +194,9 @@ struct PairWalkArgs {
     WalkTree tree;
     const int *inst;
     int dens_set;  // 1: density set r < 2 h_i (self included); 0: force set
+    // neighbour lists of the last density pass (a superset of both pair sets
+    // while they are fresh and no h of the instance outgrew the list pad)
+    const int *nl_idx, *nl_len, *rec_ctl, *rec_bad;
     int *err;
 };
 
@@ -291,10 +294,30 @@ __global__ void __launch_bounds__(128) pairwalk_kernel(PairWalkArgs a, Op op)
                 }
                 __syncwarp();
             };
-            bool ok = a.dens_set ? walk_group(a.tree, root, glo, ghi, 2.f * hmx, false, 0.f, sm.w, chunk)
-                                 : walk_group(a.tree, root, glo, ghi, 0.f, true, hmx, sm.w, chunk);
-            if (!ok && lane == 0) raise_error(a.err, SPH_ERR_TILE_OVERFLOW);
-            flush();
+            const int len = act ? a.nl_len[i] : 0;
+            const bool lists = a.rec_ctl[1] == 0 && a.rec_bad[root] == 0 &&
+                               !__any_sync(0xffffffffu, len < 0);
+            if (lists) {
+                // the pair set from the target's list, with the same exact tests
+                if (act) {
+                    const int *__restrict__ lst = a.nl_idx + (size_t)i * kNbrCap;
+                    const float4 tp = sm.tp[t];
+                    const float ht = sm.th[t];
+                    for (int e = sub; e < len; e += L) {
+                        const int j = __ldcs(lst + e);
+                        const float4 pj = __ldg(&a.pos[j]);
+                        const float r2 = canon_r2(tp.x, tp.y, tp.z, pj.x, pj.y, pj.z);
+                        const float R = a.dens_set ? 2.0f * ht : 2.0f * fmaxf(ht, __ldg(&a.h[j]));
+                        if (r2 < R * R && (a.dens_set || j != i)) op.pair(i, j, acc);
+                    }
+                }
+                __syncwarp();
+            } else {
+                bool ok = a.dens_set ? walk_group(a.tree, root, glo, ghi, 2.f * hmx, false, 0.f, sm.w, chunk)
+                                     : walk_group(a.tree, root, glo, ghi, 0.f, true, hmx, sm.w, chunk);
+                if (!ok && lane == 0) raise_error(a.err, SPH_ERR_TILE_OVERFLOW);
+                flush();
+            }
             op.reduce(acc, L);
             if (act && sub == 0) op.store(i, acc);
             __syncwarp();
@@ -513,6 +536,10 @@ static cudaError_t launch_pairwalk(Ctx &c, const sph_state &s, bool dens_set, co
     a.tree = WalkTree{c.tree.node_lo, c.tree.node_hi, c.tree.node_ref};
     a.inst = batch ? c.inst : nullptr;
     a.dens_set = dens_set ? 1 : 0;
+    a.nl_idx = c.nl_idx;
+    a.nl_len = c.nl_len;
+    a.rec_ctl = c.tree.rec_ctl;
+    a.rec_bad = c.tree.rec_bad;
     a.err = c.d_err;
     cudaError_t e = cudaMemsetAsync(a.work, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
