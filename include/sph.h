@@ -123,7 +123,12 @@ sph_status sph_timestep(sph_ctx *ctx, const sph_state *s, const sph_params *p, f
  * kick/drift with the acc already in the state, tree build, density and force
  * at the new positions with predicted v and u, closing kick, then the next
  * Courant step is written to *d_dt.  If d_time is not NULL, *d_time += dt
- * (device double).  Nothing returns to the host inside the call. */
+ * (device double).  Nothing returns to the host inside the call.
+ * The first call for a given (state arrays, n, params, d_dt, d_time, timing
+ * on/off) records the step's kernels into a CUDA graph (the context keeps the
+ * last four); later calls with the same arguments launch that graph on
+ * `stream`.  Inside a capture that the caller records on `stream`, the kernels
+ * are enqueued directly and the stage timers skip the step. */
 sph_status sph_step(sph_ctx *ctx, sph_state *s, const sph_params *p, float *d_dt,
                     double *d_time, void *stream);
 

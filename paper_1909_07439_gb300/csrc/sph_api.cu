@@ -48,6 +48,23 @@ cudaError_t dalloc(T *&p, size_t count)
     return cudaMalloc((void **)&p, sizeof(T) * (count > 0 ? count : 1));
 }
 
+// an event pair from the pool (created when the pool is empty)
+bool take_event_pair(Ctx &c, Ctx::EvPair &ev)
+{
+    if (c.ev_free.empty()) {
+        Ctx::EvPair p{};
+        if (cudaEventCreate(&p.a) != cudaSuccess) return false;
+        if (cudaEventCreate(&p.b) != cudaSuccess) {
+            cudaEventDestroy(p.a);
+            return false;
+        }
+        c.ev_free.push_back(p);
+    }
+    ev = c.ev_free.back();
+    c.ev_free.pop_back();
+    return true;
+}
+
 struct StageScope {
     Ctx &c;
     int stage;
@@ -56,24 +73,28 @@ struct StageScope {
     bool on = false;
     StageScope(Ctx &c_, int stage_, cudaStream_t st_, int launches) : c(c_), stage(stage_), st(st_)
     {
-        c.pending_launches[stage] += launches;
+        (c.capturing ? c.capture_launches : c.pending_launches)[stage] += launches;
         if (!c.timing) return;
-        if (c.ev_free.empty()) {
-            Ctx::EvPair p{};
-            if (cudaEventCreate(&p.a) != cudaSuccess) return;
-            if (cudaEventCreate(&p.b) != cudaSuccess) return;
-            c.ev_free.push_back(p);
-        }
-        ev = c.ev_free.back();
-        c.ev_free.pop_back();
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        // a graph the caller records holds no timing events of ours
+        if (!c.capturing && (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone))
+            return;
+        if (!take_event_pair(c, ev)) return;
         ev.stage = stage;
-        on = cudaEventRecord(ev.a, st) == cudaSuccess;
+        on = record(ev.a);
+        if (!on) c.ev_free.push_back(ev);
     }
     ~StageScope()
     {
         if (!on) return;
-        cudaEventRecord(ev.b, st);
-        c.ev_pending.push_back(ev);
+        record(ev.b);
+        (c.capturing ? c.capture_ev : c.ev_pending).push_back(ev);
+    }
+    // while a step graph is recorded, as an event-record node of the graph
+    bool record(cudaEvent_t e)
+    {
+        return (c.capturing ? cudaEventRecordWithFlags(e, st, cudaEventRecordExternal)
+                            : cudaEventRecord(e, st)) == cudaSuccess;
     }
 };
 
@@ -155,6 +176,94 @@ sph_status do_tree(Ctx &c, const sph_state &s, const sph_params &p, bool full, c
 {
     StageScope sc(c, ST_TREE, st, kTreeLaunches);
     CK(build_tree(c, s, p, full, st), "build_tree");
+    return SPH_OK;
+}
+
+// one leapfrog step (kick-drift, tree, density, force, closing kick, Courant dt)
+sph_status enqueue_step(Ctx &c, const sph_state &s, const sph_params &p, float *d_dt,
+                        double *d_time, cudaStream_t st)
+{
+    sph_status r;
+    {
+        StageScope sc(c, ST_LEAPFROG, st, 1);
+        CK(kick_drift(c, s, d_dt, st), "kick_drift");
+    }
+    if ((r = do_tree(c, s, p, false, st)) != SPH_OK) return r;
+    if ((r = do_density(c, s, p, st, true)) != SPH_OK) return r;
+    if ((r = do_force(c, s, p, st, true)) != SPH_OK) return r;
+    {
+        StageScope sc(c, ST_LEAPFROG, st, 1);
+        CK(kick_close(c, s, d_dt, d_time, st), "kick_close");
+    }
+    {
+        StageScope sc(c, ST_REDUCE, st, 2);
+        CK(courant_dt(c, s, p, d_dt, st), "timestep");
+    }
+    return SPH_OK;
+}
+
+void free_step_graph(Ctx::StepGraph &g)
+{
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    g = Ctx::StepGraph{};
+}
+
+// Record one step into g (on the context's private stream: the caller's may
+// be the legacy default stream, which cannot be captured).  With timing on,
+// the stage scopes become event-record nodes; their events go back to the
+// pool, and every launch points the nodes at fresh ones.
+sph_status record_step_graph(Ctx &c, Ctx::StepGraph &g, const sph_state &s, const sph_params &p,
+                             float *d_dt, double *d_time)
+{
+    free_step_graph(g);
+    CK(configure_density_kernels(), "configure density");
+    CK(configure_force_kernels(), "configure force");
+    CK(configure_nlist_kernels(), "configure lists");
+    if (!c.capture_stream)
+        CK(cudaStreamCreateWithFlags(&c.capture_stream, cudaStreamNonBlocking), "capture stream");
+    cudaStream_t cs = c.capture_stream;
+    c.capture_ev.clear();
+    for (auto &x : c.capture_launches) x = 0;
+    CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture");
+    c.capturing = true;
+    const sph_status r = enqueue_step(c, s, p, d_dt, d_time, cs);
+    c.capturing = false;
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(cs, &graph);
+    for (auto &ev : c.capture_ev) c.ev_free.push_back(ev);
+    if (r != SPH_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        c.capture_ev.clear();
+        return r != SPH_OK ? r : cuda_fail(c, e, "end capture");
+    }
+    g.graph = graph;
+    g.ev_nodes.assign(c.capture_ev.size(), Ctx::StepGraph::EvNode{nullptr, nullptr, 0});
+    for (size_t q = 0; q < c.capture_ev.size(); ++q) g.ev_nodes[q].stage = c.capture_ev[q].stage;
+    size_t nn = 0;
+    cudaError_t e2 = cudaGraphGetNodes(graph, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (e2 == cudaSuccess && nn) e2 = cudaGraphGetNodes(graph, nodes.data(), &nn);
+    for (size_t k = 0; e2 == cudaSuccess && k < nn; ++k) {
+        cudaGraphNodeType t;
+        if ((e2 = cudaGraphNodeGetType(nodes[k], &t)) != cudaSuccess || t != cudaGraphNodeTypeEventRecord)
+            continue;
+        cudaEvent_t ev = nullptr;
+        if ((e2 = cudaGraphEventRecordNodeGetEvent(nodes[k], &ev)) != cudaSuccess) break;
+        for (size_t q = 0; q < c.capture_ev.size(); ++q) {
+            if (c.capture_ev[q].a == ev) g.ev_nodes[q].a = nodes[k];
+            if (c.capture_ev[q].b == ev) g.ev_nodes[q].b = nodes[k];
+        }
+    }
+    c.capture_ev.clear();
+    for (const auto &en : g.ev_nodes)
+        if (e2 == cudaSuccess && (!en.a || !en.b)) e2 = cudaErrorInvalidResourceHandle;
+    if (e2 == cudaSuccess) e2 = cudaGraphInstantiate(&g.exec, graph, 0);
+    if (e2 != cudaSuccess) {
+        free_step_graph(g);
+        return cuda_fail(c, e2, "step graph");
+    }
+    for (int k = 0; k < ST_N; ++k) g.launches[k] = c.capture_launches[k];
     return SPH_OK;
 }
 
@@ -294,6 +403,7 @@ void sph_destroy(sph_ctx *h)
         if (p) cudaFree(p);
     if (c.h_pinned) cudaFreeHost(c.h_pinned);
     if (c.batch_graph) cudaGraphExecDestroy(c.batch_graph);
+    for (auto &g : c.step_graph) free_step_graph(g);
     if (c.capture_stream) cudaStreamDestroy(c.capture_stream);
     for (auto &p : c.ev_free) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto &p : c.ev_pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
@@ -360,21 +470,40 @@ sph_status sph_step(sph_ctx *h, sph_state *s, const sph_params *p, float *d_dt, 
     if (!d_dt) return fail(c, SPH_ERR_INVALID_ARG, "d_dt is NULL");
     if (s->n == 0) return SPH_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    {
-        StageScope sc(c, ST_LEAPFROG, st, 1);
-        CK(kick_drift(c, *s, d_dt, st), "kick_drift");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(st, &cap), "capture query");
+    if (cap != cudaStreamCaptureStatusNone)  // the caller records a graph of its own
+        return enqueue_step(c, *s, *p, d_dt, d_time, st);
+    // the graph is valid for exactly these pointers, sizes, parameters and timing mode
+    std::vector<unsigned char> key(sizeof(sph_state) + sizeof(sph_params) + 3 * sizeof(void *));
+    unsigned char *kp = key.data();
+    memcpy(kp, s, sizeof(sph_state)); kp += sizeof(sph_state);
+    memcpy(kp, p, sizeof(sph_params)); kp += sizeof(sph_params);
+    const void *extra[3] = {d_dt, d_time, (const void *)(intptr_t)(c.timing ? 1 : 0)};
+    memcpy(kp, extra, sizeof(extra));
+    Ctx::StepGraph *g = nullptr;
+    for (auto &x : c.step_graph)
+        if (x.exec && x.key == key) g = &x;
+    if (!g) {
+        g = &c.step_graph[0];  // the least recently used slot
+        for (auto &x : c.step_graph)
+            if (x.used < g->used) g = &x;
+        if ((r = record_step_graph(c, *g, *s, *p, d_dt, d_time)) != SPH_OK) return r;
+        g->key = key;
     }
-    if ((r = do_tree(c, *s, *p, false, st)) != SPH_OK) return r;
-    if ((r = do_density(c, *s, *p, st, true)) != SPH_OK) return r;
-    if ((r = do_force(c, *s, *p, st, true)) != SPH_OK) return r;
-    {
-        StageScope sc(c, ST_LEAPFROG, st, 1);
-        CK(kick_close(c, *s, d_dt, d_time, st), "kick_close");
+    g->used = ++c.step_graph_clock;
+    if (c.timing) {
+        for (const auto &en : g->ev_nodes) {
+            Ctx::EvPair ev{};
+            if (!take_event_pair(c, ev)) return cuda_fail(c, cudaErrorMemoryAllocation, "timing events");
+            ev.stage = en.stage;
+            CK(cudaGraphExecEventRecordNodeSetEvent(g->exec, en.a, ev.a), "timing event node");
+            CK(cudaGraphExecEventRecordNodeSetEvent(g->exec, en.b, ev.b), "timing event node");
+            c.ev_pending.push_back(ev);
+        }
     }
-    {
-        StageScope sc(c, ST_REDUCE, st, 2);
-        CK(courant_dt(c, *s, *p, d_dt, st), "timestep");
-    }
+    for (int k = 0; k < ST_N; ++k) c.pending_launches[k] += g->launches[k];
+    CK(cudaGraphLaunch(g->exec, st), "step graph launch");
     return SPH_OK;
 }
 

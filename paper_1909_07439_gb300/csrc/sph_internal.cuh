@@ -150,6 +150,25 @@ struct Ctx {
     double stage_ms[ST_N] = {};
     int64_t stage_launches[ST_N] = {};
     int64_t pending_launches[ST_N] = {};
+
+    // sph_step recorded as CUDA graphs, one per (state, params, dt, time,
+    // timing) seen last; with timing on, the graph holds the stage events as
+    // event-record nodes, pointed at fresh events before every launch
+    struct StepGraph {
+        std::vector<unsigned char> key;
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        struct EvNode { cudaGraphNode_t a, b; int stage; };
+        std::vector<EvNode> ev_nodes;
+        int64_t launches[ST_N] = {};
+        uint64_t used = 0;
+    };
+    static constexpr int kStepGraphs = 4;
+    StepGraph step_graph[kStepGraphs];
+    uint64_t step_graph_clock = 0;
+    bool capturing = false;  // stage scopes record into the capture lists below
+    std::vector<EvPair> capture_ev;
+    int64_t capture_launches[ST_N] = {};
 };
 
 // ---------------------------------------------------------------------------

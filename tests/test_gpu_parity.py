@@ -274,6 +274,65 @@ def test_step_host_matches_device_step(sph):
     assert hdt.value == d_dt.item()
 
 
+def test_step_graph_matches_eager(sph):
+    """sph_step replays a recorded CUDA graph; inside a caller's own capture it
+    enqueues the kernels directly.  Both give the same state bit for bit, and
+    the stage timers of the graph (event nodes) see every stage."""
+    native, ctx, torch = sph
+    w = CASES["ragged_3001"]
+    s, p = evaluate_gpu(native, ctx, w)
+    d_dt = torch.zeros(1, dtype=torch.float32, device="cuda")
+    d_t = torch.zeros(1, dtype=torch.float64, device="cuda")
+    native.sph_timestep(ctx, s.c, p, d_dt)
+    native.sph_sync(ctx)
+    fields = s.FIELDS4 + s.FIELDS1 + ("perm", "keys")
+    snap = {k: getattr(s, k).clone() for k in fields}
+    dt0 = d_dt.clone()
+
+    def restore():
+        for k in fields:
+            getattr(s, k).copy_(snap[k])
+        d_dt.copy_(dt0)
+        d_t.zero_()
+
+    def result():
+        native.sph_sync(ctx)
+        return {k: getattr(s, k).clone() for k in fields}, d_dt.item(), d_t.item()
+
+    steps = 3
+    native.sph_get_timing(ctx)
+    for _ in range(steps):                       # graph, no timing
+        native.sph_step(ctx, s.c, p, d_dt, d_t)
+    a = result()
+    _, launches0 = native.sph_get_timing(ctx)
+    restore()
+    native.sph_set_timing(ctx, True)
+    for _ in range(steps):                       # graph with event nodes
+        native.sph_step(ctx, s.c, p, d_dt, d_t)
+    b = result()
+    ms, launches1 = native.sph_get_timing(ctx)
+    native.sph_set_timing(ctx, False)
+    restore()
+    g = torch.cuda.CUDAGraph()                   # the caller's capture: direct launches
+    cs = torch.cuda.Stream()
+    cs.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.graph(g, stream=cs):
+        native.sph_step(ctx, s.c, p, d_dt, d_t)
+    torch.cuda.current_stream().wait_stream(cs)
+    torch.cuda.synchronize()
+    native.sph_get_timing(ctx)
+    for _ in range(steps):
+        g.replay()
+    c = result()
+    for other in (b, c):
+        assert other[1] == a[1] and other[2] == a[2]
+        for k in fields:
+            assert torch.equal(other[0][k], a[0][k]), k
+    assert launches1 == launches0 and sum(launches0.values()) > 0
+    for stage in ("tree", "lists", "density", "force", "leapfrog", "reduce"):
+        assert ms[stage] > 0, stage
+
+
 # ------------------------------------------------------------------ edge cases
 def test_empty_is_noop(sph):
     native, ctx, torch = sph
