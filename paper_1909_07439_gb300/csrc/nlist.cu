@@ -14,18 +14,18 @@
 //
 // Candidates come from the group walk of Sect. 3.2: a leaf is opened for a
 // group if its box is within max(reach of the group, 2 (1 + pad) h_max(leaf))
-// of the group box.  Two kernels:
-//   leafwalk_kernel: runs of up to kSG consecutive groups of one instance with
-//     similar h share one tree walk for the union of their boxes and their
-//     largest h; the walk's leaves, in particle order, go to a pool in global
-//     memory.  A node that passes the opening test for a box passes it for
-//     any box containing it, so the list holds every leaf of every group of
-//     the run.  Memory-latency bound: many warps, 4 nodes per lane and step.
-//   nlist_kernel: each group picks its leaves from its run's list with its
-//     own test (so its candidates do not depend on which groups shared the
-//     walk) and tests each 32-candidate chunk against up to 16 targets with
-//     the canonical FP32 squared distance (two targets per packed
-//     instruction); hits go straight to the lists in global memory.
+// of the group box.  One persistent kernel, nlist_kernel: each warp takes up
+// to kSG consecutive groups at a time.  Runs of those groups of one instance
+// whose h_max agree within kShareH share one tree walk for the union of their
+// boxes and their largest h (4 nodes per lane and walk step); the walk's
+// leaves are ranked by first particle.  A node that passes the opening test
+// for a box passes it for any box containing it, so each group then picks its
+// own leaves from that list with its own test and gets the candidates its own
+// walk would give, in particle order; a shared walk that finds more than
+// kSGLeaves leaves is replaced by one walk per group.  Each 32-candidate chunk
+// is tested against up to 16 targets with the canonical FP32 squared
+// distance (two targets per packed instruction); hits go straight to the
+// lists in global memory.
 #include "walk.cuh"
 
 namespace sph {
