@@ -156,6 +156,7 @@ __device__ __forceinline__ int test_chunks(const NlistArgs &a, const NlistSmem &
     int len[TB];
 #pragma unroll
     for (int tt = 0; tt < TB; ++tt) len[tt] = 0;
+    int *const tbase = a.idx + (size_t)i0 * kNbrCap;  // the batch's first list
     int r = 0;
     int jn = lane < ncand ? slot_particle(sm.runs, r, lane) : -1;
     float4 pn = jn >= 0 ? __ldg(&a.pos[jn]) : make_float4(1e30f, 1e30f, 1e30f, 0.f);
@@ -181,14 +182,10 @@ __device__ __forceinline__ int test_chunks(const NlistArgs &a, const NlistSmem &
             const bool hit1 = r2.y < fmaxf(sm.tr2[t1], rj2);
             const unsigned m0 = __ballot_sync(0xffffffffu, hit0);
             const unsigned m1 = __ballot_sync(0xffffffffu, hit1);
-            if (hit0) {
-                const int e = len[t0] + __popc(m0 & lt);
-                if (e < kNbrCap) __stcs(a.idx + (size_t)(i0 + t0) * kNbrCap + e, j);
-            }
-            if (hit1) {
-                const int e = len[t1] + __popc(m1 & lt);
-                if (e < kNbrCap) __stcs(a.idx + (size_t)(i0 + t1) * kNbrCap + e, j);
-            }
+            // past kNbrCap hits the last entry is overwritten: such a list is
+            // discarded (its length is set to -1) anyway
+            if (hit0) __stcs(tbase + t0 * kNbrCap + min(len[t0] + __popc(m0 & lt), kNbrCap - 1), j);
+            if (hit1) __stcs(tbase + t1 * kNbrCap + min(len[t1] + __popc(m1 & lt), kNbrCap - 1), j);
             len[t0] += __popc(m0);
             len[t1] += __popc(m1);
         }
@@ -201,7 +198,7 @@ __device__ __forceinline__ int test_chunks(const NlistArgs &a, const NlistSmem &
     return mine;
 }
 
-__global__ void __launch_bounds__(kNlWarps * 32, 5) nlist_kernel(NlistArgs a)
+__global__ void __launch_bounds__(kNlWarps * 32, 6) nlist_kernel(NlistArgs a)
 {
     __shared__ NlistSmem smv[kNlWarps];
     NlistSmem &sm = smv[threadIdx.x >> 5];
