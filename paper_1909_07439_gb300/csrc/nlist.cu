@@ -21,8 +21,8 @@
 // leaves are ranked by first particle.  A node that passes the opening test
 // for a box passes it for any box containing it, so each group then picks its
 // own leaves from that list with its own test and gets the candidates its own
-// walk would give, in particle order; a shared walk that finds more than
-// kSGLeaves leaves is replaced by one walk per group.  Each 32-candidate chunk
+// walk would give, in particle order; while a shared walk finds more than
+// kSGLeaves leaves, its range of groups is halved.  Each 32-candidate chunk
 // is tested against up to 16 targets with the canonical FP32 squared
 // distance (two targets per packed instruction); hits go straight to the
 // lists in global memory.
@@ -228,28 +228,35 @@ __global__ void __launch_bounds__(kNlWarps * 32, 6) nlist_kernel(NlistArgs a)
         const unsigned bstart = __ballot_sync(0xffffffffu, starts);
         for (int s = 0; s < sgn;) {
             const unsigned later = bstart & ~((2u << s) - 1u);  // starts after s
-            const int e = later ? min(__ffs(later) - 1, sgn) : sgn;
-            const bool mine = lane >= s && lane < e;
-            float4 ulo = mine ? glol : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
-            float4 uhi = mine ? ghil : make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
-            for (int o = 16; o > 0; o >>= 1) {
-                ulo.x = fminf(ulo.x, __shfl_xor_sync(0xffffffffu, ulo.x, o));
-                ulo.y = fminf(ulo.y, __shfl_xor_sync(0xffffffffu, ulo.y, o));
-                ulo.z = fminf(ulo.z, __shfl_xor_sync(0xffffffffu, ulo.z, o));
-                ulo.w = fmaxf(ulo.w, __shfl_xor_sync(0xffffffffu, ulo.w, o));  // h_max
-                uhi.x = fmaxf(uhi.x, __shfl_xor_sync(0xffffffffu, uhi.x, o));
-                uhi.y = fmaxf(uhi.y, __shfl_xor_sync(0xffffffffu, uhi.y, o));
-                uhi.z = fmaxf(uhi.z, __shfl_xor_sync(0xffffffffu, uhi.z, o));
-            }
+            int e = later ? min(__ffs(later) - 1, sgn) : sgn;
             const int root = __shfl_sync(0xffffffffu, ins, s);
-            // one walk for the run; if its leaves do not fit, one walk per group,
-            // so whether a group gets lists depends on the group alone
-            const int nshared = walk_sorted(a, sm, root, ulo, uhi);
+            // One walk for the groups [s, e) of the run; while its leaves do
+            // not fit, the range is halved (a group alone that does not fit
+            // gets no lists), so whether a group gets lists depends on the
+            // group alone.
+            int nshared;
+            while (true) {
+                const bool mine = lane >= s && lane < e;
+                float4 ulo = mine ? glol : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+                float4 uhi = mine ? ghil : make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
+                for (int o = 16; o > 0; o >>= 1) {
+                    ulo.x = fminf(ulo.x, __shfl_xor_sync(0xffffffffu, ulo.x, o));
+                    ulo.y = fminf(ulo.y, __shfl_xor_sync(0xffffffffu, ulo.y, o));
+                    ulo.z = fminf(ulo.z, __shfl_xor_sync(0xffffffffu, ulo.z, o));
+                    ulo.w = fmaxf(ulo.w, __shfl_xor_sync(0xffffffffu, ulo.w, o));  // h_max
+                    uhi.x = fmaxf(uhi.x, __shfl_xor_sync(0xffffffffu, uhi.x, o));
+                    uhi.y = fmaxf(uhi.y, __shfl_xor_sync(0xffffffffu, uhi.y, o));
+                    uhi.z = fmaxf(uhi.z, __shfl_xor_sync(0xffffffffu, uhi.z, o));
+                }
+                nshared = walk_sorted(a, sm, root, ulo, uhi);
+                if (nshared >= 0 || e - s == 1) break;
+                e = s + (e - s + 1) / 2;
+            }
             for (int gi = s; gi < e; ++gi) {
                 const int g = gf + gi;
                 const int2 gr = a.grp_ref[g];
                 const float4 glo = a.grp_lo[g], ghi = a.grp_hi[g];
-                const int nleaf = nshared >= 0 || e - s == 1 ? nshared : walk_sorted(a, sm, root, glo, ghi);
+                const int nleaf = nshared;
                 const int nrun = nleaf >= 0 ? group_candidates(a, sm, nleaf, glo, ghi, kMaxRuns) : -1;
                 const bool ok = nrun >= 0;
                 const int ncand = ok ? sm.runs[nrun].y : 0;

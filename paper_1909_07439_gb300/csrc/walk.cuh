@@ -333,6 +333,7 @@ __device__ __forceinline__ int walk_leaves_wide(const WalkTree &T, int root, flo
             nout += __popc(bleaf);
         }
         __syncwarp();
+        if (nout > cap) break;  // the result is -1 whatever else the walk finds
     }
     return ok && nout <= cap ? nout : -1;
 }
