@@ -33,7 +33,8 @@ namespace sph {
 constexpr int kNlTB = 16;       // targets per candidate test batch
 constexpr int kNlWarps = 4;     // warps per block
 constexpr int kSG = 8;          // consecutive groups that may share one tree walk
-constexpr int kSGLeaves = 256;  // leaves one walk may find
+constexpr int kSGLeaves = 320;  // leaves one walk may find
+constexpr int kMaxRuns = 128;   // candidate runs of one group (plus a sentinel)
 constexpr int kLWWide = 4;      // nodes per lane and walk step
 constexpr int kLWStack = 320;   // stack entries of a wide walk
 constexpr float kShareH = 2.f;  // groups share a walk if their h_max differ by less
@@ -208,12 +209,16 @@ __global__ void __launch_bounds__(kNlWarps * 32, 6) nlist_kernel(NlistArgs a)
     unsigned long long n_cand = 0, n_entries = 0, n_over = 0;
 
     while (true) {
-        int sg = 0;
-        if (lane == 0) sg = atomicAdd(a.work, 1);
-        sg = __shfl_sync(0xffffffffu, sg, 0);
-        const int gf = sg * kSG;
+        // kSG groups at a time, kSG / 2 in the last quarter (shorter tail)
+        int gf = 0, grab = kSG;
+        if (lane == 0) {
+            grab = *(volatile int *)a.work < ng - (ng >> 2) ? kSG : kSG / 2;
+            gf = atomicAdd(a.work, grab);
+        }
+        gf = __shfl_sync(0xffffffffu, gf, 0);
+        grab = __shfl_sync(0xffffffffu, grab, 0);
         if (gf >= ng) break;
-        const int sgn = min(kSG, ng - gf);
+        const int sgn = min(grab, ng - gf);
         const bool have = lane < sgn;
         const int2 grl = have ? a.grp_ref[gf + lane] : make_int2(0, 0);
         const float4 glol = have ? a.grp_lo[gf + lane] : make_float4(0.f, 0.f, 0.f, 0.f);

@@ -17,7 +17,6 @@ constexpr int kLevels = 22;          // levels 0..21
 constexpr int kWarp = 32;
 constexpr int kMaxInstances = 65536;  // instances in one batch
 constexpr int kNbrCap = 128;          // neighbour-list entries per particle
-constexpr int kMaxRuns = 256;         // candidate runs of one group (plus a sentinel)
 constexpr float kCNorm = 0.318309886183790671538f;  // M4, 3D: 1/pi
 
 // stage ids for the per-stage timers
