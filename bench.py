@@ -45,9 +45,9 @@ FLOP_TEST = 8
 # DRAM bytes (read + write) per launch of the longest-stage kernels from one
 # ncu capture of this workload (profiles/list_density_force_kernels_sedov128_ncu.md);
 # to be re-measured whenever those kernels change.
-NCU_TRAFFIC = {"nlist_kernel": 126.975e6 + 597.347328e6,
-               "density_list_kernel": 1100.468e6 + 49.331712e6,
-               "force_list_kernel": 980.34e6 + 29.13664e6}
+NCU_TRAFFIC = {"nlist_kernel": 129.211e6 + 600.035584e6,
+               "density_list_kernel": 1100.968e6 + 49.730304e6,
+               "force_list_kernel": 980.119e6 + 29.17248e6}
 
 
 def peaks():
