@@ -13,12 +13,17 @@ static int grid_n(const Ctx &c, int64_t n, int block)
     return g < 1 ? 1 : (int)g;
 }
 
-// v_half = v + a dt/2, u_half = u + du dt/2 (kept in vhalf);
-// predicted v1p = v + a dt, u1p = u + du dt (Eq. 6) into vel;
-// r1 = r + v_half dt = r + v dt + a dt^2/2 (Eq. 5).
-__global__ void kick_drift_kernel(float4 *__restrict__ pos, float4 *__restrict__ vel,
-                                  const float4 *__restrict__ acc, float4 *__restrict__ vhalf,
-                                  int n, const float *d_dt, const int *__restrict__ inst)
+// v_half = v + a dt/2, u_half = u + du dt/2 (into vhalf);
+// predicted v1p = v + a dt, u1p = u + du dt (Eq. 6) into vel1;
+// r1 = r + v_half dt = r + v dt + a dt^2/2 (Eq. 5) into pos1; h and perm
+// copied along.  The outputs are the context's temporaries, from which the
+// tree build gathers the state back in the new curve order.
+__global__ void kick_drift_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ vel,
+                                  const float4 *__restrict__ acc, const float *__restrict__ h,
+                                  const uint32_t *__restrict__ perm, float4 *__restrict__ pos1,
+                                  float4 *__restrict__ vel1, float4 *__restrict__ vhalf,
+                                  float *__restrict__ h1, uint32_t *__restrict__ perm1, int n,
+                                  const float *d_dt, const int *__restrict__ inst)
 {
     float dt = *d_dt, hdt = 0.5f * dt;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -29,8 +34,10 @@ __global__ void kick_drift_kernel(float4 *__restrict__ pos, float4 *__restrict__
         float4 v = vel[i], a = acc[i], p = pos[i];
         float4 vh = make_float4(v.x + hdt * a.x, v.y + hdt * a.y, v.z + hdt * a.z, v.w + hdt * a.w);
         vhalf[i] = vh;
-        vel[i] = make_float4(v.x + dt * a.x, v.y + dt * a.y, v.z + dt * a.z, v.w + dt * a.w);
-        pos[i] = make_float4(p.x + dt * vh.x, p.y + dt * vh.y, p.z + dt * vh.z, p.w);
+        vel1[i] = make_float4(v.x + dt * a.x, v.y + dt * a.y, v.z + dt * a.z, v.w + dt * a.w);
+        pos1[i] = make_float4(p.x + dt * vh.x, p.y + dt * vh.y, p.z + dt * vh.z, p.w);
+        h1[i] = h[i];
+        perm1[i] = perm[i];
     }
 }
 
@@ -165,9 +172,9 @@ cudaError_t kick_drift(Ctx &c, const sph_state &s, const float *d_dt, cudaStream
                        const Batch *batch)
 {
     int n = (int)s.n;
-    kick_drift_kernel<<<grid_n(c, n, 256), 256, 0, st>>>((float4 *)s.pos, (float4 *)s.vel,
-                                                         (const float4 *)s.acc, c.vhalf, n, d_dt,
-                                                         batch ? c.inst : nullptr);
+    kick_drift_kernel<<<grid_n(c, n, 256), 256, 0, st>>>(
+        (const float4 *)s.pos, (const float4 *)s.vel, (const float4 *)s.acc, s.h, s.perm, c.tmp4[0],
+        c.tmp4[1], c.tmp4[2], c.tmp1[0], c.tmp_perm, n, d_dt, batch ? c.inst : nullptr);
     return cudaGetLastError();
 }
 

@@ -792,16 +792,22 @@ cudaError_t build_tree(Ctx &c, const sph_state &s, const sph_params &p, bool ful
     const int *inst = batch ? c.inst : nullptr;
     const int64_t *offs = batch ? batch->offsets : nullptr;
     int *bb = batch ? c.bbox_inst : (int *)c.bbox;
+    // Within a step (full_permute = false) kick_drift has left the kicked pos,
+    // vel, v_half, h and perm in the temporaries: keys come from there and
+    // the gather writes the state straight back in curve order.
+    const bool kicked = !full_permute;
+    float4 *pos_in = kicked ? c.tmp4[0] : pos;
+    const float *h_in = kicked ? c.tmp1[0] : s.h;
     // 1. bounding box (per instance in a batch) and input checks
     if (batch) {
         bbox_batch_init_kernel<<<div_up(6 * batch->n_inst, 256), 256, 0, st>>>(bb, batch->n_inst);
-        bbox_batch_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(pos, s.h, inst, n, bb, c.d_err);
+        bbox_batch_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(pos_in, h_in, inst, n, bb, c.d_err);
     } else {
         bbox_init_kernel<<<1, 32, 0, st>>>(bb);
-        bbox_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(pos, s.h, n, bb, c.d_err);
+        bbox_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(pos_in, h_in, n, bb, c.d_err);
     }
     // 2. keys
-    morton_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(pos, inst, n, bb, s.keys, c.idx_a);
+    morton_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(pos_in, inst, n, bb, s.keys, c.idx_a);
     // 3. radix sort (key, slot); a batch adds stable passes on the instance id,
     //    which puts every instance back on its own slots
     const int ntiles = div_up(n, RS_TILE);
@@ -828,29 +834,36 @@ cudaError_t build_tree(Ctx &c, const sph_state &s, const sph_params &p, bool ful
     // 4. permute the state into curve order
     GatherArgs g{};
     g.order = c.idx_a;
-    int n4 = 0, n1 = 0;
-    float4 *arr4[4] = {(float4 *)s.pos, (float4 *)s.vel, nullptr, nullptr};
-    n4 = 2;
-    if (full_permute) {
-        arr4[n4++] = (float4 *)s.acc;
-    } else {
-        arr4[n4++] = c.vhalf;
-    }
-    float *arr1[5] = {s.h, s.rho, s.omega, s.drhodt, s.vsigmax};
-    n1 = full_permute ? 5 : 1;
-    for (int a = 0; a < n4; ++a) { g.a4[a] = arr4[a]; g.t4[a] = c.tmp4[a]; }
-    for (int a = 0; a < n1; ++a) { g.a1[a] = arr1[a]; g.t1[a] = c.tmp1[a]; }
-    g.perm = s.perm;
-    g.tperm = c.tmp_perm;
     g.rec = c.rec;
-    g.n4 = n4;
-    g.n1 = n1;
-    gather_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(g, n);
-    for (int a = 0; a < n4; ++a)
-        SPH_TRY(cudaMemcpyAsync(arr4[a], c.tmp4[a], (size_t)n * 16, cudaMemcpyDeviceToDevice, st));
-    for (int a = 0; a < n1; ++a)
-        SPH_TRY(cudaMemcpyAsync(arr1[a], c.tmp1[a], (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
-    SPH_TRY(cudaMemcpyAsync(s.perm, c.tmp_perm, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
+    if (kicked) {
+        float4 *src4[3] = {c.tmp4[0], c.tmp4[1], c.tmp4[2]};
+        float4 *dst4[3] = {(float4 *)s.pos, (float4 *)s.vel, c.vhalf};
+        for (int a = 0; a < 3; ++a) { g.a4[a] = src4[a]; g.t4[a] = dst4[a]; }
+        g.a1[0] = c.tmp1[0];
+        g.t1[0] = s.h;
+        g.perm = c.tmp_perm;
+        g.tperm = s.perm;
+        g.n4 = 3;
+        g.n1 = 1;
+        gather_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(g, n);
+    } else {
+        // gather into the temporaries, then copy back
+        float4 *arr4[4] = {(float4 *)s.pos, (float4 *)s.vel, (float4 *)s.acc, nullptr};
+        float *arr1[5] = {s.h, s.rho, s.omega, s.drhodt, s.vsigmax};
+        const int n4 = 3, n1 = 5;
+        for (int a = 0; a < n4; ++a) { g.a4[a] = arr4[a]; g.t4[a] = c.tmp4[a]; }
+        for (int a = 0; a < n1; ++a) { g.a1[a] = arr1[a]; g.t1[a] = c.tmp1[a]; }
+        g.perm = s.perm;
+        g.tperm = c.tmp_perm;
+        g.n4 = n4;
+        g.n1 = n1;
+        gather_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(g, n);
+        for (int a = 0; a < n4; ++a)
+            SPH_TRY(cudaMemcpyAsync(arr4[a], c.tmp4[a], (size_t)n * 16, cudaMemcpyDeviceToDevice, st));
+        for (int a = 0; a < n1; ++a)
+            SPH_TRY(cudaMemcpyAsync(arr1[a], c.tmp1[a], (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
+        SPH_TRY(cudaMemcpyAsync(s.perm, c.tmp_perm, (size_t)n * 4, cudaMemcpyDeviceToDevice, st));
+    }
     // recorded leaf ranges refer to the previous tree: mark them invalid
     SPH_TRY(cudaMemsetAsync(t.rec_ctl + 1, 0xff, sizeof(int), st));
     // 5. chop: tree (n_leaf) and groups (n_group)
