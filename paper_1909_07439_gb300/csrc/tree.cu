@@ -180,7 +180,7 @@ __global__ void morton_kernel(const float4 *__restrict__ pos, const int *__restr
 constexpr int RS_T = 256, RS_I = 8, RS_TILE = RS_T * RS_I;
 constexpr uint32_t RS_AGG = 1u << 30, RS_INC = 2u << 30, RS_CNT = RS_AGG - 1u;
 constexpr int RS_SPIN = 1 << 22;  // look-back polls before giving up (error, no hang)
-constexpr int RS_LB = 8;           // predecessor tiles read together in the look-back
+constexpr int RS_LB = 4;           // predecessor tiles read together in the look-back
 
 // block-wide exclusive scan helper for 256 threads, returns the block total
 __device__ __forceinline__ uint32_t block_scan_256(uint32_t v, uint32_t &excl, uint32_t *ws)
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(256) rs_gscan_kernel(const uint32_t *ghist, ui
 // digit are found with one ballot per digit bit, and a warp-private digit
 // counter row accumulates; tile order is (warp, round, lane), so equal digits
 // keep their input order.
-__global__ void __launch_bounds__(RS_T) rs_onesweep_kernel(
+__global__ void __launch_bounds__(RS_T, 4) rs_onesweep_kernel(
     const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const int *__restrict__ inst, int n, int shift,
     const uint32_t *__restrict__ gstart, uint32_t *status, int *tile_counter, int *err)
