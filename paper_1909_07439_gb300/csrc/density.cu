@@ -90,7 +90,8 @@ __device__ __forceinline__ float seg_sum(float v, int L)
 __device__ __forceinline__ void pair_sums(float r2, float mj, float vd, float hinv, float &s0,
                                           float &s1, float &s2)
 {
-    const float rinv = r2 > 0.f ? rsqrtf(r2) : 0.f;
+    // r = 0 (the particle itself, or a padding entry) gives q = 0 and vd = 0
+    const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
     const float q = r2 * rinv * hinv;
     float f, df;
     m4_f_df(q, f, df);

@@ -75,8 +75,8 @@ struct ForceTarget {
         xi = x; vi = v; qi = q;
         hinv_i = 1.f / qi.x;
         cf_i = kCNorm * hinv_i * hinv_i * hinv_i * hinv_i;  // F_i = f'(q_i) C / h_i^4
-        Pi = a.gm1 * qi.y * vi.w;
         pres_i = a.gm1 * vi.w;  // P_i / rho_i
+        Pi = pres_i * qi.y;      // formed as P_j is
         ax = ay = az = dup = duav = duc = 0.f;
         vsmax = a.alpha * qi.w;
         cnt = 0;
@@ -112,14 +112,15 @@ struct ForceTarget {
         const float avj = mu * (a.alpha * qj.w + a.beta * avr);
         duav += mj * vsi * vr * (-2.f * mu) * Fi;
         const float Aj = qj.z;
-        const float coef = mj * (Ai * (pres_i + avi) * Fi + Aj * (a.gm1 * vj.w + avj) * Fj);
+        const float pres_j = a.gm1 * vj.w;  // P_j / rho_j
+        const float coef = mj * (Ai * (pres_i + avi) * Fi + Aj * (pres_j + avj) * Fj);
         const float cr = coef * rinv;
         ax -= cr * dx;
         ay -= cr * dy;
         az -= cr * dz;
         dup += mj * vr * Fi;
-        const float Pj = a.gm1 * qj.y * vj.w;
-        const float x = __fdividef(fabsf(Pi - Pj), 0.5f * (qi.y + qj.y));
+        const float Pj = pres_j * qj.y;
+        const float x = __fdividef(2.f * fabsf(Pi - Pj), qi.y + qj.y);
         const float vsu = x > 0.f ? x * rsqrtf(x) : 0.f;
         duc += mj * vsu * (vi.w - vj.w) * (Fi * Ai + Fj * Aj);
         vsmax = in ? fmaxf(vsmax, vsi) : vsmax;
@@ -147,7 +148,7 @@ struct ForceTarget {
     }
 };
 
-__global__ void __launch_bounds__(kForceWarps * 32) force_list_kernel(ForceArgs a)
+__global__ void __launch_bounds__(kForceWarps * 32, 8) force_list_kernel(ForceArgs a)
 {
     const int lane = threadIdx.x & 31;
     const uint64_t keep = l2_keep_policy();
