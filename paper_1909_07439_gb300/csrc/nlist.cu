@@ -149,8 +149,7 @@ __device__ __forceinline__ int group_candidates(const NlistArgs &a, NlistSmem &s
 // the hits to the targets' lists.  The next chunk's candidates are loaded
 // while one is tested.  Returns the list length of target `lane` (lane < TB).
 template <int TB>
-__device__ __forceinline__ int test_chunks(const NlistArgs &a, const NlistSmem &sm, int ncand, int i0,
-                                           int nt, unsigned long long &n_cand)
+__device__ __forceinline__ int test_chunks(const NlistArgs &a, const NlistSmem &sm, int ncand, int i0)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = lane_lt();
@@ -190,7 +189,6 @@ __device__ __forceinline__ int test_chunks(const NlistArgs &a, const NlistSmem &
             len[t0] += __popc(m0);
             len[t1] += __popc(m1);
         }
-        n_cand += (unsigned long long)(nt * __popc(__ballot_sync(0xffffffffu, j >= 0)));
     }
     int mine = 0;
 #pragma unroll
@@ -277,9 +275,10 @@ __global__ void __launch_bounds__(kNlWarps * 32, 6) nlist_kernel(NlistArgs a)
                     __syncwarp();
                     int mlen = 0;
                     if (ncand > 0) {
-                        if (nt <= 4) mlen = test_chunks<4>(a, sm, ncand, i0, nt, n_cand);
-                        else if (nt <= 8) mlen = test_chunks<8>(a, sm, ncand, i0, nt, n_cand);
-                        else mlen = test_chunks<16>(a, sm, ncand, i0, nt, n_cand);
+                        if (nt <= 4) mlen = test_chunks<4>(a, sm, ncand, i0);
+                        else if (nt <= 8) mlen = test_chunks<8>(a, sm, ncand, i0);
+                        else mlen = test_chunks<16>(a, sm, ncand, i0);
+                        n_cand += (unsigned long long)nt * (unsigned long long)ncand;
                     }
                     // a group without lists is left to the walking kernels
                     const bool fits = ok && mlen <= kNbrCap;
