@@ -333,6 +333,38 @@ def test_step_graph_matches_eager(sph):
         assert ms[stage] > 0, stage
 
 
+def test_step_graphs_of_two_states_do_not_mix(sph):
+    """Steps of two states interleaved on one context (one recorded graph
+    each) give the states that each gets alone on its own context."""
+    native, ctx, torch = sph
+    fields = ("pos", "vel", "acc", "h", "rho", "omega", "drhodt", "vsigmax", "perm", "keys")
+
+    def prepare(context, w):
+        s, p = evaluate_gpu(native, context, w)
+        d_dt = torch.zeros(1, dtype=torch.float32, device="cuda")
+        native.sph_timestep(context, s.c, p, d_dt)
+        return s, p, d_dt
+
+    a = prepare(ctx, CASES["ragged_3001"])
+    b = prepare(ctx, CASES["c1_8192"])
+    for _ in range(2):
+        for s, p, d_dt in (a, b):
+            native.sph_step(ctx, s.c, p, d_dt)
+    native.sph_sync(ctx)
+    for (s, _, d_dt), name in ((a, "ragged_3001"), (b, "c1_8192")):
+        own = native.sph_create(1 << 14, 0)
+        try:
+            s2, p2, dt2 = prepare(own, CASES[name])
+            for _ in range(2):
+                native.sph_step(own, s2.c, p2, dt2)
+            native.sph_sync(own)
+            for k in fields:
+                assert torch.equal(getattr(s, k), getattr(s2, k)), (name, k)
+            assert d_dt.item() == dt2.item()
+        finally:
+            native.sph_destroy(own)
+
+
 # ------------------------------------------------------------------ edge cases
 def test_empty_is_noop(sph):
     native, ctx, torch = sph
