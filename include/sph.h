@@ -194,7 +194,10 @@ sph_status sph_rollout(sph_ctx *ctx, const sph_state *init, const sph_params *p,
 /* Same step for a state held in HOST memory (pinned for best speed): copies
  * the state in, runs n_steps steps, copies it back; *h_dt (host) is read as
  * the first dt and receives the next one.  Allocates a device mirror on the
- * first call.  Synchronous. */
+ * first call.  With every array of *hs pinned, the last step copies each
+ * output back on a second stream as soon as it is final (pos, perm, keys
+ * after the tree build; h, rho, omega, drhodt after the density pass), so
+ * those copies overlap the rest of the step.  Synchronous. */
 sph_status sph_step_host(sph_ctx *ctx, sph_state *host_state, const sph_params *p, int n_steps,
                          float *h_dt, void *stream);
 

@@ -179,9 +179,35 @@ sph_status do_tree(Ctx &c, const sph_state &s, const sph_params &p, bool full, c
     return SPH_OK;
 }
 
+// Host buffers that receive a step's outputs (sph_step_host's last step):
+// each output is copied on the context's copy stream as soon as it is final,
+// while the rest of the step runs.
+struct HostOut {
+    const sph_state *hs;
+    float *h_dt;
+};
+
+// queue the device-to-host copies of `fields` (bit k: field k of
+// sph_state after n, in declaration order) behind what st has queued so far
+cudaError_t copy_out(Ctx &c, const sph_state &d, const HostOut &o, unsigned fields, cudaStream_t st,
+                     int ev)
+{
+    const size_t n = (size_t)d.n;
+    void *const dst[10] = {o.hs->pos, o.hs->vel, o.hs->acc, o.hs->h, o.hs->rho,
+                           o.hs->omega, o.hs->drhodt, o.hs->vsigmax, o.hs->perm, o.hs->keys};
+    const void *const src[10] = {d.pos, d.vel, d.acc, d.h, d.rho, d.omega, d.drhodt, d.vsigmax, d.perm, d.keys};
+    const size_t size[10] = {16, 16, 16, 4, 4, 4, 4, 4, 4, 8};
+    cudaError_t e = cudaEventRecord(c.copy_ev[ev], st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(c.copy_stream, c.copy_ev[ev], 0);
+    for (int k = 0; k < 10 && e == cudaSuccess; ++k)
+        if (fields & (1u << k))
+            e = cudaMemcpyAsync(dst[k], src[k], n * size[k], cudaMemcpyDeviceToHost, c.copy_stream);
+    return e;
+}
+
 // one leapfrog step (kick-drift, tree, density, force, closing kick, Courant dt)
 sph_status enqueue_step(Ctx &c, const sph_state &s, const sph_params &p, float *d_dt,
-                        double *d_time, cudaStream_t st)
+                        double *d_time, cudaStream_t st, const HostOut *out = nullptr)
 {
     sph_status r;
     {
@@ -189,7 +215,10 @@ sph_status enqueue_step(Ctx &c, const sph_state &s, const sph_params &p, float *
         CK(kick_drift(c, s, d_dt, st), "kick_drift");
     }
     if ((r = do_tree(c, s, p, false, st)) != SPH_OK) return r;
+    // final from here on: pos (the closing kick changes v only), perm, keys
+    if (out) CK(copy_out(c, s, *out, 1u | 1u << 8 | 1u << 9, st, 0), "copy out");
     if ((r = do_density(c, s, p, st, true)) != SPH_OK) return r;
+    if (out) CK(copy_out(c, s, *out, 1u << 3 | 1u << 4 | 1u << 5 | 1u << 6, st, 1), "copy out");
     if ((r = do_force(c, s, p, st, true)) != SPH_OK) return r;
     {
         StageScope sc(c, ST_LEAPFROG, st, 1);
@@ -198,6 +227,12 @@ sph_status enqueue_step(Ctx &c, const sph_state &s, const sph_params &p, float *
     {
         StageScope sc(c, ST_REDUCE, st, 2);
         CK(courant_dt(c, s, p, d_dt, st), "timestep");
+    }
+    if (out) {
+        CK(copy_out(c, s, *out, 1u << 1 | 1u << 2 | 1u << 7, st, 2), "copy out");
+        CK(cudaMemcpyAsync(out->h_dt, d_dt, sizeof(float), cudaMemcpyDeviceToHost, c.copy_stream), "copy out");
+        CK(cudaEventRecord(c.copy_ev[3], c.copy_stream), "copy join");
+        CK(cudaStreamWaitEvent(st, c.copy_ev[3], 0), "copy join");
     }
     return SPH_OK;
 }
@@ -214,7 +249,7 @@ void free_step_graph(Ctx::StepGraph &g)
 // the stage scopes become event-record nodes; their events go back to the
 // pool, and every launch points the nodes at fresh ones.
 sph_status record_step_graph(Ctx &c, Ctx::StepGraph &g, const sph_state &s, const sph_params &p,
-                             float *d_dt, double *d_time)
+                             float *d_dt, double *d_time, const HostOut *out)
 {
     free_step_graph(g);
     CK(configure_density_kernels(), "configure density");
@@ -227,7 +262,7 @@ sph_status record_step_graph(Ctx &c, Ctx::StepGraph &g, const sph_state &s, cons
     for (auto &x : c.capture_launches) x = 0;
     CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture");
     c.capturing = true;
-    const sph_status r = enqueue_step(c, s, p, d_dt, d_time, cs);
+    const sph_status r = enqueue_step(c, s, p, d_dt, d_time, cs, out);
     c.capturing = false;
     cudaGraph_t graph = nullptr;
     const cudaError_t e = cudaStreamEndCapture(cs, &graph);
@@ -404,6 +439,9 @@ void sph_destroy(sph_ctx *h)
     if (c.h_pinned) cudaFreeHost(c.h_pinned);
     if (c.batch_graph) cudaGraphExecDestroy(c.batch_graph);
     for (auto &g : c.step_graph) free_step_graph(g);
+    if (c.copy_stream) cudaStreamDestroy(c.copy_stream);
+    for (auto &ev : c.copy_ev)
+        if (ev) cudaEventDestroy(ev);
     if (c.capture_stream) cudaStreamDestroy(c.capture_stream);
     for (auto &p : c.ev_free) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto &p : c.ev_pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
@@ -459,27 +497,26 @@ sph_status sph_timestep(sph_ctx *h, const sph_state *s, const sph_params *p, flo
     return SPH_OK;
 }
 
-sph_status sph_step(sph_ctx *h, sph_state *s, const sph_params *p, float *d_dt, double *d_time,
-                    void *stream)
+namespace {
+
+// Launch one step as the recorded graph for these arguments (recorded on
+// first use; the context keeps the last kStepGraphs).
+sph_status step_launch(Ctx &c, const sph_state &s, const sph_params &p, float *d_dt, double *d_time,
+                       cudaStream_t st, const HostOut *out)
 {
-    if (!h) return SPH_ERR_INVALID_ARG;
-    Ctx &c = h->impl;
-    sph_status r = check_state(c, s, true);
-    if (r != SPH_OK) return r;
-    if ((r = check_params(c, p)) != SPH_OK) return r;
-    if (!d_dt) return fail(c, SPH_ERR_INVALID_ARG, "d_dt is NULL");
-    if (s->n == 0) return SPH_OK;
-    cudaStream_t st = (cudaStream_t)stream;
+    sph_status r;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     CK(cudaStreamIsCapturing(st, &cap), "capture query");
     if (cap != cudaStreamCaptureStatusNone)  // the caller records a graph of its own
-        return enqueue_step(c, *s, *p, d_dt, d_time, st);
+        return enqueue_step(c, s, p, d_dt, d_time, st, out);
     // the graph is valid for exactly these pointers, sizes, parameters and timing mode
-    std::vector<unsigned char> key(sizeof(sph_state) + sizeof(sph_params) + 3 * sizeof(void *));
+    std::vector<unsigned char> key(2 * sizeof(sph_state) + sizeof(sph_params) + 4 * sizeof(void *));
     unsigned char *kp = key.data();
-    memcpy(kp, s, sizeof(sph_state)); kp += sizeof(sph_state);
-    memcpy(kp, p, sizeof(sph_params)); kp += sizeof(sph_params);
-    const void *extra[3] = {d_dt, d_time, (const void *)(intptr_t)(c.timing ? 1 : 0)};
+    memcpy(kp, &s, sizeof(sph_state)); kp += sizeof(sph_state);
+    const sph_state none{};
+    memcpy(kp, out ? out->hs : &none, sizeof(sph_state)); kp += sizeof(sph_state);
+    memcpy(kp, &p, sizeof(sph_params)); kp += sizeof(sph_params);
+    const void *extra[4] = {d_dt, d_time, out ? out->h_dt : nullptr, (const void *)(intptr_t)(c.timing ? 1 : 0)};
     memcpy(kp, extra, sizeof(extra));
     Ctx::StepGraph *g = nullptr;
     for (auto &x : c.step_graph)
@@ -488,7 +525,7 @@ sph_status sph_step(sph_ctx *h, sph_state *s, const sph_params *p, float *d_dt, 
         g = &c.step_graph[0];  // the least recently used slot
         for (auto &x : c.step_graph)
             if (x.used < g->used) g = &x;
-        if ((r = record_step_graph(c, *g, *s, *p, d_dt, d_time)) != SPH_OK) return r;
+        if ((r = record_step_graph(c, *g, s, p, d_dt, d_time, out)) != SPH_OK) return r;
         g->key = key;
     }
     g->used = ++c.step_graph_clock;
@@ -505,6 +542,21 @@ sph_status sph_step(sph_ctx *h, sph_state *s, const sph_params *p, float *d_dt, 
     for (int k = 0; k < ST_N; ++k) c.pending_launches[k] += g->launches[k];
     CK(cudaGraphLaunch(g->exec, st), "step graph launch");
     return SPH_OK;
+}
+
+}  // namespace
+
+sph_status sph_step(sph_ctx *h, sph_state *s, const sph_params *p, float *d_dt, double *d_time,
+                    void *stream)
+{
+    if (!h) return SPH_ERR_INVALID_ARG;
+    Ctx &c = h->impl;
+    sph_status r = check_state(c, s, true);
+    if (r != SPH_OK) return r;
+    if ((r = check_params(c, p)) != SPH_OK) return r;
+    if (!d_dt) return fail(c, SPH_ERR_INVALID_ARG, "d_dt is NULL");
+    if (s->n == 0) return SPH_OK;
+    return step_launch(c, *s, *p, d_dt, d_time, (cudaStream_t)stream, nullptr);
 }
 
 sph_status sph_step_host(sph_ctx *h, sph_state *hs, const sph_params *p, int n_steps, float *h_dt,
@@ -554,8 +606,32 @@ sph_status sph_step_host(sph_ctx *h, sph_state *hs, const sph_params *p, int n_s
     CK(cudaMemcpyAsync(d.h, hs->h, n * 4, H2D, st), "H2D h");
     CK(cudaMemcpyAsync(d.perm, hs->perm, n * 4, H2D, st), "H2D perm");
     CK(cudaMemcpyAsync(c.mirror_dt, h_dt, sizeof(float), H2D, st), "H2D dt");
-    for (int k = 0; k < n_steps; ++k)
-        if ((r = sph_step(h, &d, p, c.mirror_dt, nullptr, stream)) != SPH_OK) return r;
+    // With all host buffers pinned, the last step copies each output back as
+    // soon as it is final, on the copy stream, while the step runs on.
+    bool pinned = true;
+    for (const void *q : {(const void *)hs->pos, (const void *)hs->vel, (const void *)hs->acc,
+                          (const void *)hs->h, (const void *)hs->rho, (const void *)hs->omega,
+                          (const void *)hs->drhodt, (const void *)hs->vsigmax, (const void *)hs->perm,
+                          (const void *)hs->keys}) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, q) != cudaSuccess || at.type != cudaMemoryTypeHost) pinned = false;
+    }
+    (void)cudaGetLastError();  // an unregistered pointer may leave an error behind
+    if (pinned && !c.copy_stream) {
+        CK(cudaStreamCreateWithFlags(&c.copy_stream, cudaStreamNonBlocking), "copy stream");
+        for (auto &ev : c.copy_ev) CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "copy events");
+    }
+    float *dt_pinned = reinterpret_cast<float *>(c.h_pinned + 8);  // the next dt, read after the sync
+    for (int k = 0; k < n_steps; ++k) {
+        const HostOut out{hs, dt_pinned};
+        const bool last = k == n_steps - 1 && pinned;
+        if ((r = step_launch(c, d, *p, c.mirror_dt, nullptr, st, last ? &out : nullptr)) != SPH_OK) return r;
+    }
+    if (n_steps > 0 && pinned) {
+        if ((r = sph_sync(h, stream)) != SPH_OK) return r;
+        *h_dt = *dt_pinned;
+        return SPH_OK;
+    }
     CK(cudaMemcpyAsync(hs->pos, d.pos, n * 16, D2H, st), "D2H pos");
     CK(cudaMemcpyAsync(hs->vel, d.vel, n * 16, D2H, st), "D2H vel");
     CK(cudaMemcpyAsync(hs->acc, d.acc, n * 16, D2H, st), "D2H acc");
