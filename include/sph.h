@@ -196,8 +196,9 @@ sph_status sph_rollout(sph_ctx *ctx, const sph_state *init, const sph_params *p,
  * the first dt and receives the next one.  Allocates a device mirror on the
  * first call.  With every array of *hs pinned, the last step copies each
  * output back on a second stream as soon as it is final (pos, perm, keys
- * after the tree build; h, rho, omega, drhodt after the density pass), so
- * those copies overlap the rest of the step.  Synchronous. */
+ * after the tree build; h, rho, omega, drhodt after the density pass; acc,
+ * vsigmax after the force pass), so those copies overlap the rest of the
+ * step.  Synchronous. */
 sph_status sph_step_host(sph_ctx *ctx, sph_state *host_state, const sph_params *p, int n_steps,
                          float *h_dt, void *stream);
 

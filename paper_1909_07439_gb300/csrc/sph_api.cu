@@ -220,6 +220,7 @@ sph_status enqueue_step(Ctx &c, const sph_state &s, const sph_params &p, float *
     if ((r = do_density(c, s, p, st, true)) != SPH_OK) return r;
     if (out) CK(copy_out(c, s, *out, 1u << 3 | 1u << 4 | 1u << 5 | 1u << 6, st, 1), "copy out");
     if ((r = do_force(c, s, p, st, true)) != SPH_OK) return r;
+    if (out) CK(copy_out(c, s, *out, 1u << 2 | 1u << 7, st, 2), "copy out");  // acc, vsigmax
     {
         StageScope sc(c, ST_LEAPFROG, st, 1);
         CK(kick_close(c, s, d_dt, d_time, st), "kick_close");
@@ -229,7 +230,7 @@ sph_status enqueue_step(Ctx &c, const sph_state &s, const sph_params &p, float *
         CK(courant_dt(c, s, p, d_dt, st), "timestep");
     }
     if (out) {
-        CK(copy_out(c, s, *out, 1u << 1 | 1u << 2 | 1u << 7, st, 2), "copy out");
+        CK(copy_out(c, s, *out, 1u << 1, st, 4), "copy out");  // vel
         CK(cudaMemcpyAsync(out->h_dt, d_dt, sizeof(float), cudaMemcpyDeviceToHost, c.copy_stream), "copy out");
         CK(cudaEventRecord(c.copy_ev[3], c.copy_stream), "copy join");
         CK(cudaStreamWaitEvent(st, c.copy_ev[3], 0), "copy join");

@@ -122,7 +122,7 @@ struct Ctx {
     cudaGraphExec_t batch_graph = nullptr;
     cudaStream_t capture_stream = nullptr;  // graphs are recorded here, launched on the caller's
     cudaStream_t copy_stream = nullptr;     // sph_step_host's output copies (inside its graph)
-    cudaEvent_t copy_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t copy_ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     std::vector<unsigned char> batch_graph_key;
 
     // scan scratch
