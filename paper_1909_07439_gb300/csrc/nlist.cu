@@ -17,7 +17,7 @@
 // of the group box.  One persistent kernel, nlist_kernel: each warp takes up
 // to kSG consecutive groups at a time.  Runs of those groups of one instance
 // whose h_max agree within kShareH share one tree walk for the union of their
-// boxes and their largest h (4 nodes per lane and walk step); the walk's
+// boxes and their largest h (2 nodes per lane and walk step); the walk's
 // leaves are ranked by first particle.  A node that passes the opening test
 // for a box passes it for any box containing it, so each group then picks its
 // own leaves from that list with its own test and gets the candidates its own
@@ -35,7 +35,7 @@ constexpr int kNlWarps = 4;     // warps per block
 constexpr int kSG = 8;          // consecutive groups that may share one tree walk
 constexpr int kSGLeaves = 320;  // leaves one walk may find
 constexpr int kMaxRuns = 128;   // candidate runs of one group (plus a sentinel)
-constexpr int kLWWide = 4;      // nodes per lane and walk step
+constexpr int kLWWide = 2;      // nodes per lane and walk step
 constexpr int kLWStack = 320;   // stack entries of a wide walk
 constexpr float kShareH = 2.f;  // groups share a walk if their h_max differ by less
 constexpr float kListSlack = 1.0f + 1e-5f;  // list radius margin over the FP32 pad checks
