@@ -197,7 +197,7 @@ __device__ __forceinline__ int test_chunks(const NlistArgs &a, const NlistSmem &
     return mine;
 }
 
-__global__ void __launch_bounds__(kNlWarps * 32, 6) nlist_kernel(NlistArgs a)
+__global__ void __launch_bounds__(kNlWarps * 32, 7) nlist_kernel(NlistArgs a)
 {
     __shared__ NlistSmem smv[kNlWarps];
     NlistSmem &sm = smv[threadIdx.x >> 5];
