@@ -134,7 +134,7 @@ sph_status check_params(Ctx &c, const sph_params *p)
         if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
     } while (0)
 
-constexpr int kTreeLaunches = 28;
+constexpr int kTreeLaunches = 34;
 constexpr int kPrepLaunches = 1;
 
 // tree_fresh: the tree was just built from this state (node and group h_max
@@ -361,8 +361,8 @@ sph_status sph_create(sph_ctx **out, int64_t max_n, int device)
     A(dalloc(c.idx_b, n));
     A(dalloc(c.rs_ghist, 10 * 256));
     A(dalloc(c.rs_gstart, 10 * 256));
-    A(dalloc(c.rs_status, (size_t)10 * 256 * c.ntiles_cap));
-    A(dalloc(c.rs_tiles, 10));
+    A(dalloc(c.rs_status, (size_t)kRsSlots * 256 * c.ntiles_cap));
+    A(dalloc(c.rs_tiles, kRsSlots + 1));
     for (int k = 0; k < 4; ++k) A(dalloc(c.tmp4[k], n));
     for (int k = 0; k < 5; ++k) A(dalloc(c.tmp1[k], n));
     A(dalloc(c.tmp_perm, n));

@@ -16,6 +16,7 @@ constexpr int kMaxLevel = 21;        // 21 bits per axis, 63-bit keys
 constexpr int kLevels = 22;          // levels 0..21
 constexpr int kWarp = 32;
 constexpr int kMaxInstances = 65536;  // instances in one batch
+constexpr int kRsSlots = 15;         // radix passes of one sort at most (5 + 8 + 2)
 constexpr int kNbrCap = 128;          // neighbour-list entries per particle
 constexpr float kCNorm = 0.318309886183790671538f;  // M4, 3D: 1/pi
 
@@ -92,8 +93,8 @@ struct Ctx {
     uint32_t *idx_a = nullptr, *idx_b = nullptr;
     uint32_t *rs_ghist = nullptr;   // [10][256] digit counts of every pass
     uint32_t *rs_gstart = nullptr;  // [10][256] their exclusive scans
-    uint32_t *rs_status = nullptr;  // [10][ntiles][256] look-back words
-    int *rs_tiles = nullptr;        // [10] tile counters
+    uint32_t *rs_status = nullptr;  // [kRsSlots][ntiles][256] look-back words, one slot per pass
+    int *rs_tiles = nullptr;        // [kRsSlots] tile counters, then the full-sort flag
     int ntiles_cap = 0;
 
     // gather scratch

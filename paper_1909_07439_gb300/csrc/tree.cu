@@ -168,8 +168,12 @@ __global__ void morton_kernel(const float4 *__restrict__ pos, const int *__restr
 }
 
 // ------------------------------------------------------------- radix sort
-// Stable LSD radix sort of (key, index), 8-bit digits, 8 passes over the
-// 64-bit word (two more on the instance id in a batch).  The digit counts of
+// Stable LSD radix sort of (key, index) with 8-bit digits.  Particles are far
+// apart in units of the key's lowest 24 bits (2^-13 of the box per axis), so
+// five passes sort by bits 24..63 and a fix-up pass orders each run of equal
+// top bits by its low 24 bits; if some run is longer than kFixRun, eight
+// passes over the whole word follow (they return at once otherwise).  Two
+// more passes on the instance id in a batch.  The digit counts of
 // every pass are taken in one histogram pass up front (the multiset of keys
 // does not change between passes).  Each pass is then one kernel: tiles are
 // numbered in launch order by an atomic counter, each ranks its keys (warp
@@ -270,8 +274,10 @@ __global__ void __launch_bounds__(256) rs_gscan_kernel(const uint32_t *ghist, ui
 __global__ void __launch_bounds__(RS_T, 4) rs_onesweep_kernel(
     const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const int *__restrict__ inst, int n, int shift,
-    const uint32_t *__restrict__ gstart, uint32_t *status, int *tile_counter, int *err)
+    const uint32_t *__restrict__ gstart, uint32_t *status, int *tile_counter, int *err,
+    const int *gate)
 {
+    if (gate && *gate == 0) return;  // a pass of the full sort that is not needed
     __shared__ uint32_t gbase[256];   // first output slot of each digit for this tile
     __shared__ uint32_t tstart[256];  // first slot of each digit in the sorted tile
     __shared__ uint32_t wcnt[8][256];
@@ -381,6 +387,39 @@ __global__ void __launch_bounds__(RS_T, 4) rs_onesweep_kernel(
     }
 }
 
+// Runs of keys with equal bits 24..63 (after the passes on those bits, in
+// input order) sorted by their low 24 bits: one thread per run, stable
+// insertion sort.  A run longer than kFixRun raises *full instead.  Threads
+// that are not at a run's start read only the top bits of their neighbours,
+// which the sort inside a run does not change.
+constexpr int kFixRun = 32;
+__global__ void rs_fixup_kernel(uint64_t *keys, uint32_t *vals, int n, int *full)
+{
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        const uint64_t top = keys[s] >> 24;
+        if (s > 0 && (keys[s - 1] >> 24) == top) continue;        // inside a run
+        if (s + 1 >= n || (keys[s + 1] >> 24) != top) continue;   // a run of one
+        int e = s + 2;
+        while (e < n && e - s <= kFixRun && (keys[e] >> 24) == top) ++e;
+        if (e - s > kFixRun) {
+            atomicOr(full, 1);
+            continue;
+        }
+        for (int i = s + 1; i < e; ++i) {
+            const uint64_t k = keys[i];
+            const uint32_t v = vals[i];
+            int j = i - 1;
+            while (j >= s && (keys[j] & 0xffffffu) > (k & 0xffffffu)) {
+                keys[j + 1] = keys[j];
+                vals[j + 1] = vals[j];
+                --j;
+            }
+            keys[j + 1] = k;
+            vals[j + 1] = v;
+        }
+    }
+}
+
 // ------------------------------------------------------------------ gather
 struct GatherArgs {
     const uint32_t *order;
@@ -390,6 +429,8 @@ struct GatherArgs {
     float *t1[5];
     uint32_t *perm, *tperm;
     float4 *rec;  // a4[0], a4[1] (pos, vel) side by side
+    const uint64_t *keys_sorted;  // if not null: copied to keys_out
+    uint64_t *keys_out;
     int n4, n1;
 };
 
@@ -409,6 +450,7 @@ __global__ void gather_kernel(GatherArgs g, int n)
         for (int a = 0; a < 5; ++a)
             if (a < g.n1) g.t1[a][k] = g.a1[a][o];
         g.tperm[k] = g.perm[o];
+        if (g.keys_sorted) g.keys_out[k] = g.keys_sorted[k];
     }
 }
 
@@ -813,28 +855,43 @@ cudaError_t build_tree(Ctx &c, const sph_state &s, const sph_params &p, bool ful
     const int ntiles = div_up(n, RS_TILE);
     uint64_t *kin = s.keys, *kout = c.keys_alt;
     uint32_t *vin = c.idx_a, *vout = c.idx_b;
-    const int npass = batch ? 10 : 8;
-    // digit counts of all passes, their scans, fresh look-back words and tile counters
+    const int ndigit = batch ? 10 : 8;  // digits 0..7 of the key, 8..9 of the instance id
+    const int nslot = 5 + 8 + (batch ? 2 : 0);
+    int *full = c.rs_tiles + kRsSlots;  // the fix-up found a long run: sort all 64 bits
+    // digit counts of all passes, their scans, fresh look-back words, tile counters, flag
     SPH_TRY(cudaMemsetAsync(c.rs_ghist, 0, sizeof(uint32_t) * 10 * 256, st));
-    SPH_TRY(cudaMemsetAsync(c.rs_tiles, 0, sizeof(int) * 10, st));
-    SPH_TRY(cudaMemsetAsync(c.rs_status, 0, sizeof(uint32_t) * 256 * (size_t)ntiles * npass, st));
+    SPH_TRY(cudaMemsetAsync(c.rs_tiles, 0, sizeof(int) * (kRsSlots + 1), st));
+    SPH_TRY(cudaMemsetAsync(c.rs_status, 0, sizeof(uint32_t) * 256 * (size_t)ntiles * nslot, st));
     rs_ghist_kernel<<<grid_for(c, div_up(n, RS_GE), 256), 256, 0, st>>>(kin, inst, n, c.rs_ghist);
-    rs_gscan_kernel<<<npass, 256, 0, st>>>(c.rs_ghist, c.rs_gstart);
-    for (int pass = 0; pass < npass; ++pass) {
-        const int *dinst = pass >= 8 ? inst : nullptr;
-        int shift = pass >= 8 ? 8 * (pass - 8) : 8 * pass;
+    rs_gscan_kernel<<<ndigit, 256, 0, st>>>(c.rs_ghist, c.rs_gstart);
+    int slot = 0;
+    auto pass = [&](int digit, const int *gate) {
+        const int *dinst = digit >= 8 ? inst : nullptr;
+        const int shift = digit >= 8 ? 8 * (digit - 8) : 8 * digit;
         rs_onesweep_kernel<<<ntiles, RS_T, 0, st>>>(kin, vin, kout, vout, dinst, n, shift,
-                                                    c.rs_gstart + 256 * pass,
-                                                    c.rs_status + (size_t)256 * ntiles * pass,
-                                                    c.rs_tiles + pass, c.d_err);
-        std::swap(kin, kout);
-        std::swap(vin, vout);
+                                                    c.rs_gstart + 256 * digit,
+                                                    c.rs_status + (size_t)256 * ntiles * slot,
+                                                    c.rs_tiles + slot, c.d_err, gate);
+        ++slot;
+        std::swap(kin, kout);  // a gated pass that returns moves nothing, but
+        std::swap(vin, vout);  // the gated passes come in an even number
+    };
+    for (int digit = 3; digit < 8; ++digit) pass(digit, nullptr);
+    rs_fixup_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(kin, vin, n, full);
+    for (int digit = 0; digit < 8; ++digit) pass(digit, full);
+    if (batch) {
+        pass(8, nullptr);
+        pass(9, nullptr);
     }
-    // after an even number of passes the sorted (key, slot) pairs are in (s.keys, idx_a)
+    // the sorted (key, slot) pairs are in (kin, vin)
     // 4. permute the state into curve order
     GatherArgs g{};
-    g.order = c.idx_a;
+    g.order = vin;
     g.rec = c.rec;
+    if (kin != s.keys) {
+        g.keys_sorted = kin;
+        g.keys_out = s.keys;
+    }
     if (kicked) {
         float4 *src4[3] = {c.tmp4[0], c.tmp4[1], c.tmp4[2]};
         float4 *dst4[3] = {(float4 *)s.pos, (float4 *)s.vel, c.vhalf};

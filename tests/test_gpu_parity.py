@@ -89,6 +89,41 @@ def test_keys_sort_perm_bit_exact(sph, n):
     assert np.array_equal(s.numpy("h"), w.h[order])
 
 
+def _tight_clusters(n, size, seed):
+    # clusters of `size` distinct particles within ~1e-6 of the box: their keys
+    # share the top 40 bits (cells of 2^-13 of the box per axis) and differ
+    # below, so the sort has to order them by the low 24 bits
+    w = inputs.unit_sphere(n, seed=seed)
+    rng = np.random.default_rng(seed)
+    bases = rng.choice(n, size=n // (2 * size), replace=False)
+    k = 0
+    for b in bases:
+        for q in range(size):
+            if k >= n:
+                break
+            if k != b:
+                w.pos[k, :3] = w.pos[b, :3] + rng.uniform(-1e-6, 1e-6, 3).astype(np.float32)
+            k += 1
+    return w
+
+
+@pytest.mark.parametrize("size", [3, 20, 40])
+def test_sort_of_keys_that_share_their_top_bits(sph, size):
+    # runs of up to 32 equal top bits are ordered by the fix-up pass, longer
+    # runs by the passes over all 64 bits
+    native, ctx, torch = sph
+    w = _tight_clusters(6000, size, seed=size)
+    s = upload(native, w)
+    native.sph_build_tree(ctx, s.c, native.sph_params_default())
+    native.sph_sync(ctx)
+    keys_o = oracle.morton_keys(w.pos)
+    order = oracle.sort_order(keys_o)
+    top = keys_o[order] >> np.uint64(24)
+    assert np.sum(top[1:] == top[:-1]) > 0          # the case has runs
+    assert np.array_equal(s.numpy("perm").astype(np.int64), order)
+    assert np.array_equal(s.numpy("keys").view(np.uint64), keys_o[order])
+
+
 def _clustered(n=20000):
     w = inputs.plummer(n, seed=11)
     # a block of exact duplicates exercises identical keys (depth-21 leaves)
