@@ -171,8 +171,9 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_list_kernel(DensArgs 
         __syncthreads();
         if (base >= ng) break;
         for (int kr = 0; kr < kRound; ++kr) {
-            const int g = base + warp + kDensWarps * kr;
-            if (g >= ng) break;
+            const int gq = base + warp + kDensWarps * kr;
+            if (gq >= ng) break;
+            const int g = ng - 1 - gq;  // last group first: its lists were written last (in L2)
             const int2 gr = a.grp_ref[g];
             for (int b0 = 0; b0 < gr.y; b0 += kTB) {
                 const int nt = min(kTB, gr.y - b0);

@@ -183,9 +183,10 @@ __device__ __forceinline__ int test_chunks(const NlistArgs &a, const NlistSmem &
             const unsigned m0 = __ballot_sync(0xffffffffu, hit0);
             const unsigned m1 = __ballot_sync(0xffffffffu, hit1);
             // past kNbrCap hits the last entry is overwritten: such a list is
-            // discarded (its length is set to -1) anyway
-            if (hit0) __stcs(tbase + t0 * kNbrCap + min(len[t0] + __popc(m0 & lt), kNbrCap - 1), j);
-            if (hit1) __stcs(tbase + t1 * kNbrCap + min(len[t1] + __popc(m1 & lt), kNbrCap - 1), j);
+            // discarded (its length is set to -1) anyway.  Stores kept in L2 (the
+            // density pass reads the last groups' lists first).
+            if (hit0) __stcg(tbase + t0 * kNbrCap + min(len[t0] + __popc(m0 & lt), kNbrCap - 1), j);
+            if (hit1) __stcg(tbase + t1 * kNbrCap + min(len[t1] + __popc(m1 & lt), kNbrCap - 1), j);
             len[t0] += __popc(m0);
             len[t1] += __popc(m1);
         }
