@@ -134,7 +134,7 @@ sph_status check_params(Ctx &c, const sph_params *p)
         if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
     } while (0)
 
-constexpr int kTreeLaunches = 34;
+constexpr int kTreeLaunches = 33;
 constexpr int kPrepLaunches = 1;
 
 // tree_fresh: the tree was just built from this state (node and group h_max

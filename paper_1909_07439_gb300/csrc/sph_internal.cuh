@@ -16,7 +16,7 @@ constexpr int kMaxLevel = 21;        // 21 bits per axis, 63-bit keys
 constexpr int kLevels = 22;          // levels 0..21
 constexpr int kWarp = 32;
 constexpr int kMaxInstances = 65536;  // instances in one batch
-constexpr int kRsSlots = 15;         // radix passes of one sort at most (5 + 8 + 2)
+constexpr int kRsSlots = 14;         // radix passes of one sort at most (4 + 8 + 2)
 constexpr int kNbrCap = 128;          // neighbour-list entries per particle
 constexpr float kCNorm = 0.318309886183790671538f;  // M4, 3D: 1/pi
 

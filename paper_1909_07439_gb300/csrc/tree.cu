@@ -168,11 +168,11 @@ __global__ void morton_kernel(const float4 *__restrict__ pos, const int *__restr
 }
 
 // ------------------------------------------------------------- radix sort
-// Stable LSD radix sort of (key, index) with 8-bit digits.  Particles are far
-// apart in units of the key's lowest 24 bits (2^-13 of the box per axis), so
-// five passes sort by bits 24..63 and a fix-up pass orders each run of equal
-// top bits by its low 24 bits; if some run is longer than kFixRun, eight
-// passes over the whole word follow (they return at once otherwise).  Two
+// Stable LSD radix sort of (key, index) with 8-bit digits.  Few particles
+// share the key's top 32 bits (a cell of 2^-10 of the box per axis), so four
+// passes sort by bits 32..63 and a fix-up pass orders each run of equal top
+// bits by its low 32 bits; if some run is longer than kFixRun, eight passes
+// over the whole word follow (they return at once otherwise).  Two
 // more passes on the instance id in a batch.  The digit counts of
 // every pass are taken in one histogram pass up front (the multiset of keys
 // does not change between passes).  Each pass is then one kernel: tiles are
@@ -387,8 +387,8 @@ __global__ void __launch_bounds__(RS_T, 4) rs_onesweep_kernel(
     }
 }
 
-// Runs of keys with equal bits 24..63 (after the passes on those bits, in
-// input order) sorted by their low 24 bits: one thread per run, stable
+// Runs of keys with equal bits 32..63 (after the passes on those bits, in
+// input order) sorted by their low 32 bits: one thread per run, stable
 // insertion sort.  A run longer than kFixRun raises *full instead.  Threads
 // that are not at a run's start read only the top bits of their neighbours,
 // which the sort inside a run does not change.
@@ -396,11 +396,11 @@ constexpr int kFixRun = 32;
 __global__ void rs_fixup_kernel(uint64_t *keys, uint32_t *vals, int n, int *full)
 {
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-        const uint64_t top = keys[s] >> 24;
-        if (s > 0 && (keys[s - 1] >> 24) == top) continue;        // inside a run
-        if (s + 1 >= n || (keys[s + 1] >> 24) != top) continue;   // a run of one
+        const uint64_t top = keys[s] >> 32;
+        if (s > 0 && (keys[s - 1] >> 32) == top) continue;        // inside a run
+        if (s + 1 >= n || (keys[s + 1] >> 32) != top) continue;   // a run of one
         int e = s + 2;
-        while (e < n && e - s <= kFixRun && (keys[e] >> 24) == top) ++e;
+        while (e < n && e - s <= kFixRun && (keys[e] >> 32) == top) ++e;
         if (e - s > kFixRun) {
             atomicOr(full, 1);
             continue;
@@ -409,7 +409,7 @@ __global__ void rs_fixup_kernel(uint64_t *keys, uint32_t *vals, int n, int *full
             const uint64_t k = keys[i];
             const uint32_t v = vals[i];
             int j = i - 1;
-            while (j >= s && (keys[j] & 0xffffffu) > (k & 0xffffffu)) {
+            while (j >= s && (uint32_t)keys[j] > (uint32_t)k) {
                 keys[j + 1] = keys[j];
                 vals[j + 1] = vals[j];
                 --j;
@@ -856,7 +856,7 @@ cudaError_t build_tree(Ctx &c, const sph_state &s, const sph_params &p, bool ful
     uint64_t *kin = s.keys, *kout = c.keys_alt;
     uint32_t *vin = c.idx_a, *vout = c.idx_b;
     const int ndigit = batch ? 10 : 8;  // digits 0..7 of the key, 8..9 of the instance id
-    const int nslot = 5 + 8 + (batch ? 2 : 0);
+    const int nslot = 4 + 8 + (batch ? 2 : 0);
     int *full = c.rs_tiles + kRsSlots;  // the fix-up found a long run: sort all 64 bits
     // digit counts of all passes, their scans, fresh look-back words, tile counters, flag
     SPH_TRY(cudaMemsetAsync(c.rs_ghist, 0, sizeof(uint32_t) * 10 * 256, st));
@@ -876,7 +876,7 @@ cudaError_t build_tree(Ctx &c, const sph_state &s, const sph_params &p, bool ful
         std::swap(kin, kout);  // a gated pass that returns moves nothing, but
         std::swap(vin, vout);  // the gated passes come in an even number
     };
-    for (int digit = 3; digit < 8; ++digit) pass(digit, nullptr);
+    for (int digit = 4; digit < 8; ++digit) pass(digit, nullptr);
     rs_fixup_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(kin, vin, n, full);
     for (int digit = 0; digit < 8; ++digit) pass(digit, full);
     if (batch) {

@@ -91,8 +91,8 @@ def test_keys_sort_perm_bit_exact(sph, n):
 
 def _tight_clusters(n, size, seed):
     # clusters of `size` distinct particles within ~1e-6 of the box: their keys
-    # share the top 40 bits (cells of 2^-13 of the box per axis) and differ
-    # below, so the sort has to order them by the low 24 bits
+    # share the top 32 bits (cells of 2^-10 of the box per axis) and differ
+    # below, so the sort has to order them by the low 32 bits
     w = inputs.unit_sphere(n, seed=seed)
     rng = np.random.default_rng(seed)
     bases = rng.choice(n, size=n // (2 * size), replace=False)
@@ -118,7 +118,7 @@ def test_sort_of_keys_that_share_their_top_bits(sph, size):
     native.sph_sync(ctx)
     keys_o = oracle.morton_keys(w.pos)
     order = oracle.sort_order(keys_o)
-    top = keys_o[order] >> np.uint64(24)
+    top = keys_o[order] >> np.uint64(32)
     assert np.sum(top[1:] == top[:-1]) > 0          # the case has runs
     assert np.array_equal(s.numpy("perm").astype(np.int64), order)
     assert np.array_equal(s.numpy("keys").view(np.uint64), keys_o[order])
