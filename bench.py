@@ -45,9 +45,9 @@ FLOP_TEST = 8
 # DRAM bytes (read + write) per launch of the longest-stage kernels from one
 # ncu capture of this workload (profiles/list_density_force_kernels_sedov128_ncu.md);
 # to be re-measured whenever those kernels change.
-NCU_TRAFFIC = {"nlist_kernel": 132.63e6 + 598.619136e6,
-               "density_list_kernel": 1097.223e6 + 48.278528e6,
-               "force_list_kernel": 992.749e6 + 30.454016e6}
+NCU_TRAFFIC = {"nlist_kernel": 132.619e6 + 598.933248e6,
+               "density_list_kernel": 1097.445e6 + 49.05984e6,
+               "force_list_kernel": 992.03e6 + 31.500544e6}
 
 
 def peaks():
