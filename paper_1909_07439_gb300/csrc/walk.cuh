@@ -348,30 +348,4 @@ __device__ __forceinline__ int slot_particle(const int2 *runs, int &r, int k)
     return runs[r].x + (k - runs[r].y);
 }
 
-// Hand the particles of the runs (first, count) in shared memory to chunk()
-// in 32-particle chunks, as walk_group would.
-template <class ChunkFn>
-__device__ __forceinline__ void chunk_runs(const int2 *runs, int count, ChunkFn &&chunk)
-{
-    const int lane = threadIdx.x & 31;
-    int filled = 0, myj = -1;
-    for (int k = 0; k < count; ++k) {
-        const int2 r = runs[k];
-        int off = 0;
-        while (off < r.y) {
-            const int take = min(r.y - off, 32 - filled);
-            if (lane >= filled && lane < filled + take) myj = r.x + off + (lane - filled);
-            filled += take;
-            off += take;
-            if (filled == 32) {
-                chunk(myj);
-                filled = 0;
-                myj = -1;
-            }
-        }
-    }
-    if (filled > 0) chunk(myj);
-    __syncwarp();
-}
-
 }  // namespace sph
