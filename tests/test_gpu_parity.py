@@ -287,7 +287,10 @@ def test_conserved_fp64(sph):
     assert np.all(np.abs(got - ref) <= 1e-12 * np.maximum(scale, 1e-30))
 
 
-def test_step_host_matches_device_step(sph):
+@pytest.mark.parametrize("pinned,steps", [(True, 1), (True, 3), (False, 2)])
+def test_step_host_matches_device_step(sph, pinned, steps):
+    # pinned buffers: the last step copies each output back while it runs
+    # (its own graph); pageable buffers: plain copies after the steps
     import ctypes
     native, ctx, torch = sph
     w = CASES["ragged_3001"]
@@ -295,18 +298,50 @@ def test_step_host_matches_device_step(sph):
     d_dt = torch.zeros(1, dtype=torch.float32, device="cuda")
     native.sph_timestep(ctx, s.c, p, d_dt)
     dt0 = d_dt.item()
-    host = {k: getattr(s, k).cpu().pin_memory() for k in s.FIELDS4 + s.FIELDS1 + ("perm", "keys")}
+    fields = s.FIELDS4 + s.FIELDS1 + ("perm", "keys")
+    host = {k: getattr(s, k).cpu() for k in fields}
+    if pinned:
+        host = {k: t.pin_memory() for k, t in host.items()}
     hs = native.sph_state()
     hs.n = s.n
     for k, t in host.items():
         setattr(hs, k, t.data_ptr())
-    native.sph_step(ctx, s.c, p, d_dt)
+    for _ in range(steps):
+        native.sph_step(ctx, s.c, p, d_dt)
     native.sph_sync(ctx)
     hdt = ctypes.c_float(dt0)
-    native.sph_step_host(ctx, hs, p, 1, hdt)
-    for k in ("pos", "vel", "acc", "h", "rho"):
+    native.sph_step_host(ctx, hs, p, steps, hdt)
+    for k in fields:
         assert torch.equal(host[k][: s.n], getattr(s, k)[: s.n].cpu()), k
     assert hdt.value == d_dt.item()
+
+
+def test_step_graph_slots_are_reused(sph):
+    # more argument sets than the context keeps graphs for: the least recently
+    # used graph is dropped and recorded again when its arguments come back
+    native, ctx, torch = sph
+    fields = ("pos", "vel", "acc", "h", "rho", "omega", "drhodt", "vsigmax", "perm", "keys")
+    states = []
+    for k in range(6):
+        w = inputs.unit_sphere(700 + 50 * k, seed=40 + k)
+        s, p = evaluate_gpu(native, ctx, w)
+        d_dt = torch.zeros(1, dtype=torch.float32, device="cuda")
+        native.sph_timestep(ctx, s.c, p, d_dt)
+        native.sph_sync(ctx)
+        states.append((w, s, p, d_dt, d_dt.clone()))
+    for _ in range(2):
+        for w, s, p, d_dt, _ in states:
+            native.sph_step(ctx, s.c, p, d_dt)
+    native.sph_sync(ctx)
+    for w, s, p, d_dt, dt0 in states:
+        s2, p2 = evaluate_gpu(native, ctx, w)
+        dt2 = dt0.clone()
+        for _ in range(2):
+            native.sph_step(ctx, s2.c, p2, dt2)
+        native.sph_sync(ctx)
+        for k in fields:
+            assert torch.equal(getattr(s, k), getattr(s2, k)), k
+        assert d_dt.item() == dt2.item()
 
 
 def test_step_graph_matches_eager(sph):
