@@ -267,3 +267,87 @@ def test_sedov_similarity_constant():
             continue
         g, xi = map(float, line.split())
         assert abs(oracle.sedov_xi0(g) - xi) < 2e-4
+
+
+# ------------------------------------------------- signal speed (Eqs. 8, 12)
+def _vsig_case():
+    # four particles; h, rho, Omega given directly (the signal speed needs no density solve)
+    x = np.array([[0.0, 0.0, 0.0],     # 0: target
+                  [0.8, -0.5, 0.0],    # 1: r = 0.943 < 2 h_0 = 1.0, approaching 0
+                  [0.0, 1.5, 0.0],     # 2: outside 2 h_0, inside 2 h_2 = 1.8, receding from 0
+                  [0.0, 0.0, 3.0]])    # 3: outside both ranges, approaching fast
+    v = np.array([[0.0, 0.0, 0.0],
+                  [-0.8 / 0.89 ** 0.5, 0.5 / 0.89 ** 0.5, 0.0],  # v_01 . rhat_01 = -1 (approach)
+                  [0.0, 3.0, 0.0],     # v_02 . rhat_02 = +3 (recession)
+                  [0.0, 0.0, -10.0]])  # would give |vr| = 10 if it were counted
+    m = np.ones(4)
+    u = np.array([0.3, 0.2, 0.5, 0.1])
+    h = np.array([0.5, 0.5, 0.9, 0.5])
+    rho = np.array([1.0, 1.2, 0.8, 1.0])
+    om = np.ones(4)
+    return x, v, m, u, h, rho, om
+
+
+def test_vsigmax_by_hand():
+    # v_sig,i = max(alpha c_i, max over the force set F_i of alpha c_i + beta |v_ij . rhat_ij|)
+    # with c_i = sqrt(gamma (gamma - 1) u_i) (adiabatic EOS): every pair of F_i counts,
+    # approaching or receding, and F_i uses max(h_i, h_j) (Sect. 3.2)
+    x, v, m, u, h, rho, om = _vsig_case()
+    g = 5.0 / 3.0
+    c = np.sqrt(g * (g - 1.0) * u)
+    for alpha, beta in ((1.0, 2.0), (0.7, 3.0)):
+        f = oracle.force(x, v, m, u, h, rho, om, alpha=alpha, beta=beta)
+        # 0: pairs 1 (|vr| = 1) and 2 (|vr| = 3, receding, only via h_2); 3 is out of range
+        assert f.vsigmax[0] == pytest.approx(alpha * c[0] + beta * 3.0, rel=1e-14)
+        # 1: its only pair is 0 (r = 0.943 < 2 max(0.5, 0.5)); 2 is at r = sqrt(4.64) > 1.8
+        assert f.vsigmax[1] == pytest.approx(alpha * c[1] + beta * 1.0, rel=1e-14)
+        # 2: its only pair is 0 (r = 1.5 < 2 max(0.9, 0.5)), |vr| = 3
+        assert f.vsigmax[2] == pytest.approx(alpha * c[2] + beta * 3.0, rel=1e-14)
+        # 3: nobody in range: the floor alpha c_3
+        assert f.vsigmax[3] == pytest.approx(alpha * c[3], rel=1e-14)
+        assert list(f.nforce) == [2, 1, 1, 0]
+
+
+def test_vsigmax_floor_without_neighbours_in_motion():
+    # all particles at rest: every pair adds beta |vr| = 0, so v_sig = alpha c_i exactly
+    x, v, m, u, h, rho, om = _vsig_case()
+    f = oracle.force(x, np.zeros_like(v), m, u, h, rho, om, alpha=1.3, beta=2.0)
+    assert np.allclose(f.vsigmax, 1.3 * np.sqrt(5.0 / 3.0 * 2.0 / 3.0 * u), rtol=1e-14, atol=0)
+
+
+# ------------------------------------------- conserved quantities (Sect. 4.5)
+def test_conserved_by_hand():
+    # E_kin = sum m v^2 / 2, E_th = sum m u, p = sum m v, L = sum m r x v
+    x = np.array([[0.0, 1.0, 0.0], [0.0, 0.0, 1.0], [1.0, 0.0, 0.0]])
+    v = np.array([[0.0, 0.0, 1.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+    m = np.array([1.0, 2.0, 3.0])
+    u = np.array([0.5, 0.25, 2.0])
+    out = oracle.conserved(x, v, m, u)
+    # y x z = +x, z x x = +y, x x y = +z: one unit of L per axis, weighted by m
+    assert out == pytest.approx([0.5 * (1 + 2 + 3), 0.5 + 0.5 + 6.0, 2.0, 3.0, 1.0, 1.0, 2.0, 3.0],
+                                rel=0, abs=1e-15)
+
+
+def test_conserved_opposite_momenta_and_rings():
+    # two bodies with opposite momenta: p = 0, E_kin by hand
+    x = np.array([[0.1, 0.2, 0.3], [-0.4, 0.5, 0.6]])
+    v = np.array([[1.0, 2.0, 3.0], [-0.5, -1.0, -1.5]])
+    m = np.array([1.0, 2.0])
+    out = oracle.conserved(x, v, m, np.zeros(2))
+    assert out[0] == pytest.approx(0.5 * 14.0 + 0.5 * 2.0 * 3.5, rel=1e-15)
+    assert np.all(np.abs(out[2:5]) < 1e-15)
+    # rigid rings of radius R, angular speed w about each axis: |L| = N m R^2 w
+    # along the axis (right-handed), p = 0
+    N, R, w = 12, 0.7, 1.9
+    th = 2 * np.pi * np.arange(N) / N
+    a, b = R * np.cos(th), R * np.sin(th)
+    zero = np.zeros(N)
+    for axis, pos, vel in ((0, (zero, a, b), (zero, -w * b, w * a)),
+                           (1, (b, zero, a), (w * a, zero, -w * b)),
+                           (2, (a, b, zero), (-w * b, w * a, zero))):
+        out = oracle.conserved(np.stack(pos, 1), np.stack(vel, 1), np.full(N, 0.5), zero)
+        L = np.zeros(3)
+        L[axis] = N * 0.5 * R * R * w
+        assert np.allclose(out[5:], L, rtol=0, atol=1e-14), (axis, out[5:])
+        assert np.all(np.abs(out[2:5]) < 1e-14)
+        assert out[0] == pytest.approx(0.5 * N * 0.5 * (R * w) ** 2, rel=1e-14)
