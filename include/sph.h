@@ -218,11 +218,15 @@ sph_status sph_conserved(sph_ctx *ctx, const sph_state *s, double *d_out8, void 
  * Its scratch is a fixed 256 KB array inside the library, held on every GPU
  * that loads the library until the process exits; no call allocates.
  * The first call on each device looks up that array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress) and keeps it for the life of the process; make
+ * that first call before any stream capture, and do not reset the device
+ * (cudaDeviceReset) while the library is loaded: the kept address would then
+ * be stale.
  * All calls share the array and it keeps the last call's partial sums: calls
  * whose kernels overlap on the GPU (unordered streams) race; calls ordered on
  * one stream are safe.  Returns SPH_ERR_INVALID_ARG if n < 0 or
- * n > SPH_CONSERVED_NOALLOC_MAX_N, for NULL or misaligned pointers, or a
+ * n > SPH_CONSERVED_NOALLOC_MAX_N, for NULL pointers, for d_pos or d_vel not
+ * 16-byte aligned or d_out8 not 8-byte aligned, or a
  * current device index >= 64; SPH_ERR_CUDA if a launch or the address
  * lookup fails.  Asynchronous otherwise. */
 #define SPH_CONSERVED_NOALLOC_MAX_N 16777216
@@ -233,6 +237,13 @@ sph_status sph_conserved_noalloc(int64_t n, const float *d_pos, const float *d_v
  * mode 0: density set {j : r2 < (2 h_i)^2} (includes i);
  * mode 1: force set {j != i : r2 < (2 max(h_i, h_j))^2};
  * r2 = (dx*dx + dy*dy) + dz*dz in FP32, round-to-nearest, no fusion.
+ * Modes 0 and 1 use a separate tree walk.  Modes 2 and 3 give the same two
+ * sets taken from the neighbour lists that sph_density and sph_force read:
+ * the list-building walk of the density pass runs at the current h (its
+ * lists replace the context's), and each list is filtered with the test
+ * above (mode 2: density set, mode 3: force set).  If a particle's list
+ * overflowed, its row is empty and the call returns SPH_ERR_TILE_OVERFLOW.
+ * The tree must be the one built from the current positions.
  * d_off: device int64 [n+1] row offsets (always written);
  * d_idx: device int32 [cap] slot indices (written if non-NULL and total <= cap).
  * *h_total receives the total (host).  Synchronous. */
@@ -252,6 +263,15 @@ sph_status sph_get_tree(sph_ctx *ctx, int32_t *h_level, int32_t *h_first, int32_
                         int32_t *h_gfirst, int32_t *h_gcount, int64_t group_cap,
                         int64_t *n_nodes, int64_t *n_groups);
 
+/* Test hook for the bounded device-side waits: enqueues one block of a
+ * radix-sort pass that waits, in its decoupled look-back, on a predecessor
+ * tile that never publishes (the real passes wait only on tiles that are
+ * already running).  After spin_cap polls (1..2^20) the block records
+ * SPH_ERR_TIMEOUT in the error word and returns, reading and writing no
+ * particle data; the next sph_sync returns SPH_ERR_TIMEOUT and clears it.
+ * Uses the context's sort scratch, so do not overlap it with a tree build. */
+sph_status sph_test_lookback_timeout(sph_ctx *ctx, int spin_cap, void *stream);
+
 /* Work counters accumulated since the last call (then reset).  Synchronous. */
 typedef struct {
     uint64_t density_pairs;       /* true-neighbour pairs summed, all Newton sweeps   */
@@ -267,6 +287,9 @@ typedef struct {
     uint64_t n_groups;            /* groups of the last build                          */
     uint64_t list_entries;        /* neighbour-list entries written                    */
     uint64_t list_overflows;      /* particles whose list exceeded its capacity        */
+    uint64_t force_rewalks;       /* target batches of the force pass solved by the
+                                     walking fallback (lists stale, overflowed, or an
+                                     h of the instance outgrew the list pad)          */
 } sph_stats;
 sph_status sph_get_stats(sph_ctx *ctx, sph_stats *out);
 

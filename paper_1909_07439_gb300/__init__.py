@@ -12,5 +12,5 @@ from .native import (NativeLibraryMissing, SphError, load, sph_batch_evaluate,  
                      sph_create, sph_density, sph_destroy, sph_force, sph_get_stats,
                      sph_get_timing, sph_get_tree, sph_last_error, sph_neighbours, sph_params,
                      sph_params_default, sph_set_timing, sph_state, sph_step, sph_step_host,
-                     sph_sync, sph_timestep)
+                     sph_sync, sph_test_lookback_timeout, sph_timestep)
 from .state import DeviceState  # noqa: F401

@@ -559,6 +559,41 @@ __global__ void scan_i64_kernel(int64_t *off, int n)
     if (threadIdx.x == 0) off[n] = carry;
 }
 
+// Test export: the density (mode 0) or force (mode 1) set of every particle
+// taken from its neighbour list with the canonical FP32 test, one thread per
+// particle.  out == nullptr: row counts into off[i] (and particles without a
+// list into *missing); otherwise the rows are written at off[i].
+__global__ void list_set_kernel(const float4 *__restrict__ pos, const float *__restrict__ h,
+                                const int *__restrict__ idx, const int *__restrict__ len, int n,
+                                int mode, int64_t *off, int32_t *out, int *missing)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int l = len[i];
+        if (l < 0) {
+            if (!out) {
+                off[i] = 0;
+                atomicAdd(missing, 1);
+            }
+            continue;
+        }
+        const float4 pi = pos[i];
+        const float hi = h[i];
+        int64_t w = out ? off[i] : 0;
+        int cnt = 0;
+        for (int e = 0; e < l; ++e) {
+            const int j = idx[(size_t)i * kNbrCap + e];
+            const float4 pj = pos[j];
+            const float r2 = canon_r2(pi.x, pi.y, pi.z, pj.x, pj.y, pj.z);
+            const float R = mode == 0 ? 2.0f * hi : 2.0f * fmaxf(hi, h[j]);
+            if (r2 < R * R && (mode == 0 || j != i)) {
+                if (out) out[w++] = j;
+                ++cnt;
+            }
+        }
+        if (!out) off[i] = cnt;
+    }
+}
+
 // ------------------------------------------------------------------ host side
 // one-time kernel attributes and occupancy (also called before graph capture)
 template <int CAP>
@@ -690,6 +725,36 @@ cudaError_t density_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaSt
     cudaError_t e = density_lists(c, s, p, st, batch, false);
     if (e != cudaSuccess) return e;
     return density_solve(c, s, p, st, batch);
+}
+
+cudaError_t list_sets(Ctx &c, const sph_state &s, const sph_params &p, int mode, int64_t *d_off,
+                      int32_t *d_idx, int64_t cap, int64_t *h_total, int *h_missing,
+                      cudaStream_t st)
+{
+    // the production lists at the current h: node and group h_max refreshed,
+    // then the list-building kernel of the density pass
+    cudaError_t e = density_lists(c, s, p, st, nullptr, true);
+    if (e != cudaSuccess) return e;
+    const int n = (int)s.n;
+    int *missing = c.d_sizes + SZ_WORK2;
+    e = cudaMemsetAsync(missing, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    const int grid = c.num_sms * 8;
+    list_set_kernel<<<grid, 256, 0, st>>>((const float4 *)s.pos, s.h, c.nl_idx, c.nl_len, n, mode,
+                                          d_off, nullptr, missing);
+    scan_i64_kernel<<<1, 1024, 0, st>>>(d_off, n);
+    e = cudaMemcpyAsync(h_total, d_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c.h_pinned + 4, missing, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return e;
+    *h_missing = c.h_pinned[4];
+    if (d_idx && *h_total <= cap) {
+        list_set_kernel<<<grid, 256, 0, st>>>((const float4 *)s.pos, s.h, c.nl_idx, c.nl_len, n, mode,
+                                              d_off, d_idx, missing);
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t neighbour_lists(Ctx &c, const sph_state &s, const sph_params &p, int mode,

@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kForceWarps * 32, 8) force_list_kernel(ForceAr
     const uint64_t keep = l2_keep_policy();
     const int ng = a.sizes[SZ_GROUPS];
     const bool lists_fresh = a.rec_ctl[1] == 0;
-    unsigned long long n_pairs = 0, n_cand = 0;
+    unsigned long long n_pairs = 0, n_cand = 0, n_fb = 0;
     // The block takes kRound consecutive groups per warp at a time, warp w the
     // groups base + w + kForceWarps k: the warps of a block work on
     // neighbouring groups together and share their candidates in L1.
@@ -182,6 +182,7 @@ __global__ void __launch_bounds__(kForceWarps * 32, 8) force_list_kernel(ForceAr
                 const int len = usable && act ? a.nl_len[i] : 0;
                 if (!usable || __any_sync(0xffffffffu, len < 0)) {
                     if (lane == 0) a.fallback[atomicAdd(a.n_fallback, 1)] = make_int2(g, b0);
+                    ++n_fb;
                     continue;
                 }
                 ForceTarget T;
@@ -225,6 +226,7 @@ __global__ void __launch_bounds__(kForceWarps * 32, 8) force_list_kernel(ForceAr
     if (lane == 0) {
         atomicAdd(&a.counters[C_FORCE_PAIRS], n_pairs);
         atomicAdd(&a.counters[C_FORCE_CAND], n_cand);
+        if (n_fb) atomicAdd(&a.counters[C_FORCE_FB], n_fb);  // warp-uniform count
     }
 }
 

@@ -100,7 +100,8 @@ extern "C" sph_status sph_conserved_noalloc(int64_t n, const float *d_pos, const
 {
     if (n < 0 || n > SPH_CONSERVED_NOALLOC_MAX_N) return SPH_ERR_INVALID_ARG;
     if (!d_out8 || (n > 0 && (!d_pos || !d_vel))) return SPH_ERR_INVALID_ARG;
-    if (((uintptr_t)d_pos & 15u) || ((uintptr_t)d_vel & 15u)) return SPH_ERR_INVALID_ARG;
+    if (((uintptr_t)d_pos & 15u) || ((uintptr_t)d_vel & 15u) || ((uintptr_t)d_out8 & 7u))
+        return SPH_ERR_INVALID_ARG;
     double *part = nullptr;
     sph_status st = na_scratch(&part);
     if (st != SPH_OK) return st;

@@ -209,29 +209,19 @@ struct RB {
     }
 };
 
-// one rollout buffer per context, kept in a side table (the context layout
-// stays unchanged for the other entry points)
-struct Entry { const sph_ctx *ctx; RB *rb; };
-std::vector<Entry> g_rb;
-
-RB *get_rb(const sph_ctx *h)
+// The context owns its rollout buffers (Ctx::rollout); sph_destroy releases
+// them through release_rollout.
+cudaError_t ensure_rb(Ctx &c, int64_t n, int n_steps, int ck, RB **out)
 {
-    for (auto &e : g_rb)
-        if (e.ctx == h) return e.rb;
-    return nullptr;
-}
-
-cudaError_t ensure_rb(Ctx &c, const sph_ctx *h, int64_t n, int n_steps, int ck, RB **out)
-{
-    RB *rb = get_rb(h);
+    RB *rb = static_cast<RB *>(c.rollout);
     int n_ckpt = (n_steps + ck - 1) / ck;
-    if (rb && rb->b.n >= n && rb->b.n_ckpt >= n_ckpt && rb->b.win >= ck) {
+    // dts holds n_steps + 1 entries, so a longer rollout needs new buffers
+    if (rb && rb->b.n >= n && rb->b.n_ckpt >= n_ckpt && rb->b.win >= ck && rb->b.n_steps >= n_steps) {
         *out = rb;
         return cudaSuccess;
     }
     if (rb) {
-        for (auto &e : g_rb)
-            if (e.ctx == h) e.ctx = nullptr;
+        c.rollout = nullptr;
         delete rb;
     }
     rb = new RB();
@@ -277,7 +267,7 @@ cudaError_t ensure_rb(Ctx &c, const sph_ctx *h, int64_t n, int n_steps, int ck, 
         delete rb;
         return e;
     }
-    g_rb.push_back(Entry{h, rb});
+    c.rollout = rb;
     *out = rb;
     return cudaSuccess;
 }
@@ -379,6 +369,12 @@ cudaError_t rollout(Ctx &c, RolloutBuf &b, const sph_state &init, const sph_para
 
 }  // namespace
 
+void sph::release_rollout(Ctx &c)
+{
+    delete static_cast<RB *>(c.rollout);
+    c.rollout = nullptr;
+}
+
 extern "C" sph_status sph_rollout(sph_ctx *h, const sph_state *init, const sph_params *p,
                                   int n_steps, int ckpt, const int64_t *d_probes, int n_probes,
                                   double *h_loss, float *d_gvel, double *h_galpha, void *stream)
@@ -391,7 +387,7 @@ extern "C" sph_status sph_rollout(sph_ctx *h, const sph_state *init, const sph_p
     if ((d_gvel == nullptr) != (h_galpha == nullptr)) return SPH_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     RB *rb = nullptr;
-    cudaError_t e = ensure_rb(c, h, init->n, n_steps, ckpt, &rb);
+    cudaError_t e = ensure_rb(c, init->n, n_steps, ckpt, &rb);
     if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? SPH_ERR_NOMEM : SPH_ERR_CUDA;
     RolloutBuf &b = rb->b;
     const bool grad = d_gvel != nullptr;

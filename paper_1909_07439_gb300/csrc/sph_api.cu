@@ -422,6 +422,7 @@ void sph_destroy(sph_ctx *h)
     Ctx &c = h->impl;
     cudaSetDevice(c.device);
     cudaDeviceSynchronize();
+    release_rollout(c);
     void *ptrs[] = {c.keys_alt, c.idx_a, c.idx_b, c.rs_ghist, c.rs_gstart, c.rs_status, c.rs_tiles, c.tmp4[0], c.tmp4[1], c.tmp4[2],
                     c.tmp4[3], c.tmp1[0], c.tmp1[1], c.tmp1[2], c.tmp1[3], c.tmp1[4], c.tmp_perm,
                     c.tree.node_first, c.tree.node_count, c.tree.node_level, c.tree.node_child,
@@ -774,13 +775,25 @@ sph_status sph_neighbours(sph_ctx *h, const sph_state *s, const sph_params *p, i
     sph_status r = check_state(c, s, false);
     if (r != SPH_OK) return r;
     if ((r = check_params(c, p)) != SPH_OK) return r;
-    if ((mode != 0 && mode != 1) || !d_off || !h_total)
-        return fail(c, SPH_ERR_INVALID_ARG, "mode must be 0 or 1; d_off and h_total required");
+    if (mode < 0 || mode > 3 || !d_off || !h_total)
+        return fail(c, SPH_ERR_INVALID_ARG, "mode must be 0..3; d_off and h_total required");
     cudaStream_t st = (cudaStream_t)stream;
     if (s->n == 0) {
         *h_total = 0;
         CK(cudaMemsetAsync(d_off, 0, sizeof(int64_t), st), "memset");
         return sph_sync(h, stream);
+    }
+    if (mode >= 2) {
+        int missing = 0;
+        CK(list_sets(c, *s, *p, mode - 2, d_off, d_idx, cap, h_total, &missing, st), "list sets");
+        sph_status r2 = sph_sync(h, stream);
+        if (r2 != SPH_OK) return r2;
+        if (missing > 0) {
+            char buf[96];
+            snprintf(buf, sizeof(buf), "%d particles have no neighbour list (overflow)", missing);
+            return fail(c, SPH_ERR_TILE_OVERFLOW, buf);
+        }
+        return SPH_OK;
     }
     // the force set needs the current h in the node/group bounds
     CK(update_hmax(c, *s, *p, st), "update_hmax");
@@ -820,6 +833,15 @@ sph_status sph_get_tree(sph_ctx *h, int32_t *h_level, int32_t *h_first, int32_t 
     return SPH_OK;
 }
 
+sph_status sph_test_lookback_timeout(sph_ctx *h, int spin_cap, void *stream)
+{
+    if (!h) return SPH_ERR_INVALID_ARG;
+    Ctx &c = h->impl;
+    if (spin_cap < 1 || spin_cap > (1 << 20)) return fail(c, SPH_ERR_INVALID_ARG, "spin_cap must be 1..2^20");
+    CK(sort_lookback_probe(c, spin_cap, (cudaStream_t)stream), "look-back probe");
+    return SPH_OK;
+}
+
 sph_status sph_get_stats(sph_ctx *h, sph_stats *out)
 {
     if (!h || !out) return SPH_ERR_INVALID_ARG;
@@ -839,6 +861,7 @@ sph_status sph_get_stats(sph_ctx *h, sph_stats *out)
     out->streamed_groups = v[C_STREAMED];
     out->list_entries = v[C_LIST_ENTRIES];
     out->list_overflows = v[C_LIST_OVERFLOW];
+    out->force_rewalks = v[C_FORCE_FB];
     out->n_nodes = (uint64_t)sz[SZ_NODES];
     out->n_groups = (uint64_t)sz[SZ_GROUPS];
     return SPH_OK;

@@ -43,6 +43,7 @@ enum Counter {
     C_STREAMED = 6,
     C_LIST_ENTRIES = 7,
     C_LIST_OVERFLOW = 8,
+    C_FORCE_FB = 9,
     C_N = 12
 };
 
@@ -140,6 +141,10 @@ struct Ctx {
     int *d_sizes = nullptr;
     int *h_pinned = nullptr;  // small pinned host buffer
 
+    // work buffers of sph_rollout (allocated on its first call, released by
+    // sph_destroy through release_rollout)
+    void *rollout = nullptr;
+
     // host-buffer mirror (sph_step_host)
     sph_state mirror{};
     float *mirror_dt = nullptr;
@@ -187,6 +192,8 @@ cudaError_t update_hmax(Ctx &c, const sph_state &s, const sph_params &p, cudaStr
 cudaError_t pack_records(Ctx &c, const sph_state &s, cudaStream_t st);
 cudaError_t scan_exclusive_int(Ctx &c, const int *in, int *out, int n, int *total_dev,
                                cudaStream_t st);
+// test hook: a sort pass whose look-back predecessor never publishes
+cudaError_t sort_lookback_probe(Ctx &c, int spin_cap, cudaStream_t st);
 // nlist.cu
 cudaError_t nlist_pass(Ctx &c, const sph_state &s, const sph_params &p, float pad,
                        cudaStream_t st, const Batch *batch = nullptr);
@@ -202,6 +209,12 @@ cudaError_t density_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaSt
 cudaError_t neighbour_lists(Ctx &c, const sph_state &s, const sph_params &p, int mode,
                             int64_t *d_off, int32_t *d_idx, int64_t cap, int64_t *h_total,
                             cudaStream_t st);
+// the same sets read from the neighbour lists that the density and force
+// passes use (built here at the current h); *h_missing = particles whose
+// list overflowed (their rows are empty)
+cudaError_t list_sets(Ctx &c, const sph_state &s, const sph_params &p, int mode, int64_t *d_off,
+                      int32_t *d_idx, int64_t cap, int64_t *h_total, int *h_missing,
+                      cudaStream_t st);
 // force.cu
 // hmax_now: also refresh node and group h_max (force_pass refreshes them
 // itself, only when a batch falls back to a walk)
@@ -220,6 +233,8 @@ cudaError_t kick_close(Ctx &c, const sph_state &s, const float *d_dt, double *d_
 cudaError_t courant_dt(Ctx &c, const sph_state &s, const sph_params &p, float *d_dt,
                        cudaStream_t st, const Batch *batch = nullptr);
 cudaError_t conserved(Ctx &c, const sph_state &s, double *d_out8, cudaStream_t st);
+// rollout.cu
+void release_rollout(Ctx &c);
 
 // helpers
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }

@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(RS_T, 4) rs_onesweep_kernel(
     const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
     uint32_t *__restrict__ vout, const int *__restrict__ inst, int n, int shift,
     const uint32_t *__restrict__ gstart, uint32_t *status, int *tile_counter, int *err,
-    const int *gate)
+    const int *gate, int spin_cap)
 {
     if (gate && *gate == 0) return;  // a pass of the full sort that is not needed
     __shared__ uint32_t gbase[256];   // first output slot of each digit for this tile
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(RS_T, 4) rs_onesweep_kernel(
             if (done) break;
             int spin = 0;
             while ((v[k] & ~RS_CNT) == 0u) {
-                if (++spin > RS_SPIN) {  // a predecessor never published: report, do not hang
+                if (++spin > spin_cap) {  // a predecessor never published: report, do not hang
                     raise_error(err, SPH_ERR_TIMEOUT);
                     v[k] = RS_INC;
                     break;
@@ -871,7 +871,7 @@ cudaError_t build_tree(Ctx &c, const sph_state &s, const sph_params &p, bool ful
         rs_onesweep_kernel<<<ntiles, RS_T, 0, st>>>(kin, vin, kout, vout, dinst, n, shift,
                                                     c.rs_gstart + 256 * digit,
                                                     c.rs_status + (size_t)256 * ntiles * slot,
-                                                    c.rs_tiles + slot, c.d_err, gate);
+                                                    c.rs_tiles + slot, c.d_err, gate, RS_SPIN);
         ++slot;
         std::swap(kin, kout);  // a gated pass that returns moves nothing, but
         std::swap(vin, vout);  // the gated passes come in an even number
@@ -970,6 +970,24 @@ cudaError_t update_hmax(Ctx &c, const sph_state &s, const sph_params &p, cudaStr
                                                                        c.d_sizes, 1, gate);
     group_bounds_kernel<<<grid_for(c, s.n, 128), 128, 0, st>>>((const float4 *)s.pos, s.h,
                                                                (int)s.n, t, c.d_sizes, 1, gate);
+    return cudaGetLastError();
+}
+
+// Test hook for the bounded look-back: one block of a sort pass that takes
+// the place of tile 1 while tile 0 never publishes its counts.  The tile
+// holds no keys (n = RS_TILE), so the block reads and writes no key; its
+// look-back polls tile 0's zeroed status word spin_cap times, raises
+// SPH_ERR_TIMEOUT in the error word and returns.
+__global__ void set_int_kernel(int *p, int v) { *p = v; }
+
+cudaError_t sort_lookback_probe(Ctx &c, int spin_cap, cudaStream_t st)
+{
+    // status words of tiles 0 and 1 (the buffer holds at least kRsSlots tiles)
+    SPH_TRY(cudaMemsetAsync(c.rs_status, 0, sizeof(uint32_t) * 256 * 2, st));
+    set_int_kernel<<<1, 1, 0, st>>>(c.rs_tiles, 1);  // the block draws tile 1
+    rs_onesweep_kernel<<<1, RS_T, 0, st>>>(c.keys_alt, c.idx_a, c.keys_alt, c.idx_b, nullptr, RS_TILE,
+                                          0, c.rs_gstart, c.rs_status, c.rs_tiles, c.d_err, nullptr,
+                                          spin_cap);
     return cudaGetLastError();
 }
 

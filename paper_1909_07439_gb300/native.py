@@ -48,7 +48,7 @@ class sph_stats(ctypes.Structure):
     _fields_ = [(k, c_uint64) for k in (
         "density_pairs", "density_candidates", "force_pairs", "force_candidates",
         "newton_iters", "density_rewalks", "streamed_groups", "n_nodes", "n_groups",
-        "list_entries", "list_overflows")]
+        "list_entries", "list_overflows", "force_rewalks")]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -60,7 +60,7 @@ EXPORTS = ("sph_params_default", "sph_create", "sph_destroy", "sph_build_tree", 
            "sph_batch_step", "sph_force_bwd", "sph_density_bwd", "sph_rollout", "sph_conserved",
            "sph_conserved_noalloc",
            "sph_neighbours", "sph_get_tree", "sph_get_stats", "sph_set_timing", "sph_get_timing", "sph_sync",
-           "sph_last_error")
+           "sph_last_error", "sph_test_lookback_timeout")
 
 
 def load():
@@ -99,6 +99,7 @@ def load():
     lib.sph_get_tree.argtypes = [P, P, P, P, P, P, c_int64, P, P, c_int64, POINTER(c_int64),
                                  POINTER(c_int64)]
     lib.sph_get_stats.argtypes = [P, POINTER(sph_stats)]
+    lib.sph_test_lookback_timeout.argtypes = [P, c_int, P]
     lib.sph_set_timing.argtypes = [P, c_int]
     lib.sph_get_timing.argtypes = [P, POINTER(c_double), POINTER(c_int64)]
     lib.sph_sync.argtypes = [P, P]
@@ -238,9 +239,11 @@ def sph_conserved_noalloc(n, d_pos, d_vel, d_out8, stream=None):
     memory (see include/sph.h); scratch is a fixed array inside the library."""
     st = load().sph_conserved_noalloc(int(n), _ptr(d_pos), _ptr(d_vel), _ptr(d_out8),
                                       _stream(stream))
+    if st == 1:
+        raise SphError(st, f"sph_conserved_noalloc rejected its arguments (n = {n}, limit "
+                           f"{CONSERVED_NOALLOC_MAX_N}; pos/vel 16-byte and out 8-byte aligned)")
     if st != SPH_OK:
-        raise SphError(st, f"sph_conserved_noalloc rejected the call (n = {n}, "
-                           f"limit {CONSERVED_NOALLOC_MAX_N})")
+        raise SphError(st, "sph_conserved_noalloc: a CUDA launch or the scratch address lookup failed")
     return st
 
 
@@ -268,6 +271,10 @@ def sph_get_tree(ctx, node_cap=1 << 26, group_cap=1 << 26):
     return ({"level": arrs[0][:n], "first": arrs[1][:n], "count": arrs[2][:n],
              "nchild": arrs[3][:n], "child": arrs[4][:n]},
             {"first": garrs[0][:g], "count": garrs[1][:g]})
+
+
+def sph_test_lookback_timeout(ctx, spin_cap, stream=None):
+    return _check(ctx, load().sph_test_lookback_timeout(ctx, int(spin_cap), _stream(stream)))
 
 
 def sph_get_stats(ctx) -> dict:

@@ -146,7 +146,116 @@ def test_sedov_100_steps(sedov):
     rs, prof, edges = oracle.shock_radius_from_profile(s.numpy("pos")[:, :3], s.numpy("rho"),
                                                        meta["centre"], nbins=80, rmax=2.0 * R)
     print(f"t={t:.4e} R_sedov={R:.4f} R_peak={rs:.4f} dE/E={abs(E1 - E0) / E0:.2e}")
-    assert abs(rs / R - 1) < 0.15
-    assert abs(E1 - E0) / E0 < 0.05
+    # measured on GB300: R_peak / R_sedov = 0.987 (the profile's bins are
+    # R / 40 wide), dE/E = 1.56e-3 after 100 steps at C_cour = 0.3 (the paper
+    # finds the Sedov energy error erratic at this Courant number)
+    assert abs(rs / R - 1) < 0.05
+    assert abs(E1 - E0) / E0 < 3e-3
     # the shell is compressed: peak density well above the ambient rho0 = 1
     assert prof.max() > 1.5
+
+
+# ------------------------------------------------ the list path in mid-blast
+@pytest.fixture(scope="module")
+def sedov_mid(sedov):
+    """The benchmark's state: initial evaluation, then 6 sph_steps (the bench's
+    warm-up), then one more step with fresh counters: the list path timed by
+    the benchmark, with no walking fallback."""
+    w, s0, p, ctx, native, torch = sedov
+    from paper_1909_07439_gb300 import DeviceState
+    s = DeviceState.from_arrays(w.pos, w.vel, w.h)
+    native.sph_build_tree(ctx, s.c, p)
+    native.sph_density(ctx, s.c, p)
+    native.sph_force(ctx, s.c, p)
+    d_dt = torch.zeros(1, dtype=torch.float32, device="cuda")
+    native.sph_timestep(ctx, s.c, p, d_dt)
+    for _ in range(6):
+        native.sph_step(ctx, s.c, p, d_dt)
+    native.sph_sync(ctx)
+    native.sph_get_stats(ctx)
+    native.sph_step(ctx, s.c, p, d_dt)
+    native.sph_sync(ctx)
+    stats = native.sph_get_stats(ctx)
+    return w, s, p, ctx, native, torch, stats
+
+
+def _mid_samples(x, rho, n, k=56, seed=7):
+    r = np.linalg.norm(x - 0.5, axis=1)
+    rng = np.random.default_rng(seed)
+    hot = np.argsort(r)[:8]                                   # rarefied hot centre
+    shell = np.where(rho > 0.8 * rho.max())[0]                # compressed shell
+    edge = np.where(np.min(np.minimum(x, 1 - x), axis=1) < 0.01)[0]
+    pick = [hot, rng.choice(shell, min(12, len(shell)), replace=False),
+            rng.choice(edge, 8, replace=False), rng.choice(n, k - 28, replace=False)]
+    return np.unique(np.concatenate(pick))
+
+
+def test_midblast_step_uses_lists_only(sedov_mid):
+    w, s, p, ctx, native, torch, st = sedov_mid
+    assert st["density_rewalks"] == 0 and st["force_rewalks"] == 0
+    assert st["list_overflows"] == 0 and st["streamed_groups"] == 0
+    assert st["density_pairs"] > 0 and st["force_pairs"] > 0
+
+
+def test_midblast_density_and_force_parity(sedov_mid):
+    # the step's own h and rho (Eqs. 1-4 at the step's positions), then
+    # sph_force on the step's lists (current v, u): element by element
+    # against the oracle on sampled targets
+    w, s, p, ctx, native, torch, _ = sedov_mid
+    pos, vel = s.numpy("pos"), s.numpy("vel")
+    x, v = pos[:, :3].astype(np.float64), vel[:, :3].astype(np.float64)
+    m, u = pos[:, 3].astype(np.float64), vel[:, 3].astype(np.float64)
+    hg, rg = s.numpy("h"), s.numpy("rho")
+    t = _mid_samples(x, rg, s.n)
+    assert len(t) >= 48
+    d = oracle.density(x, v, m, hg, targets=t)
+    assert d.failures == 0
+    assert np.max(np.abs(rg[t] / d.rho - 1)) <= 1e-5
+    assert np.max(np.abs(hg[t] / d.h - 1)) <= 1e-5 / 3
+    native.sph_get_stats(ctx)
+    native.sph_force(ctx, s.c, p)
+    native.sph_sync(ctx)
+    assert native.sph_get_stats(ctx)["force_rewalks"] == 0
+    acc = s.numpy("acc")
+    ra, ga, rd, gd = [], [], [], []
+    for i in t:
+        r = np.linalg.norm(x - x[i], axis=1)
+        near = np.where(r < 2.1 * np.maximum(hg[i], hg))[0]       # the force set, with margin
+        ball = np.where(r < r[near].max() + 2.3 * hg[near].max())[0]
+        dd = oracle.density(x[ball], v[ball], m[ball], hg[ball],
+                            targets=np.searchsorted(ball, near))
+        assert dd.failures == 0
+        hb, rb, ob = (hg[ball].astype(np.float64), rg[ball].astype(np.float64),
+                      s.numpy("omega")[ball].astype(np.float64))
+        kk = np.searchsorted(ball, near)
+        hb[kk], rb[kk], ob[kk] = dd.h, dd.rho, dd.omega
+        # every particle that reaches i under the oracle's h is in `near`
+        rr = r[ball]
+        k = int(np.searchsorted(ball, i))
+        assert np.all(np.isin(np.where(rr < 2.0 * np.maximum(hb[k], hb))[0], kk))
+        f = oracle.force(x[ball], v[ball], m[ball], u[ball], hb, rb, ob, targets=[k])
+        ra.append(f.acc[0]); ga.append(acc[i, :3]); rd.append(f.dudt[0]); gd.append(acc[i, 3])
+    ra, ga, rd, gd = map(np.array, (ra, ga, rd, gd))
+    err_a = np.max(np.abs(ga - ra)) / np.max(np.abs(ra))
+    err_d = np.max(np.abs(gd - rd)) / np.max(np.abs(rd))
+    print(f"mid-blast: {len(t)} targets, max|da|/max|a| = {err_a:.2e}, "
+          f"max|ddu|/max|du| = {err_d:.2e}")
+    assert err_a <= 1e-4 and err_d <= 1e-4
+
+
+def test_midblast_lists_bit_exact_sampled(sedov_mid):
+    # the production lists at the mid-blast state, filtered by the exact
+    # test, against the oracle's brute-force sets for sampled targets
+    w, s, p, ctx, native, torch, _ = sedov_mid
+    pos, hg = s.numpy("pos"), s.numpy("h")
+    t = _mid_samples(pos[:, :3].astype(np.float64), s.numpy("rho"), s.n, seed=11)
+    for mode in (0, 1):
+        off = torch.zeros(s.n + 1, dtype=torch.int64, device="cuda")
+        total = native.sph_neighbours(ctx, s.c, p, 2 + mode, off)
+        idx = torch.zeros(total, dtype=torch.int32, device="cuda")
+        native.sph_neighbours(ctx, s.c, p, 2 + mode, off, idx, total)
+        off, idx = off.cpu().numpy(), idx.cpu().numpy()
+        oo, oi = oracle.neighbours(pos, hg, mode, targets=t)
+        for q, i in enumerate(t):
+            got = np.sort(idx[off[i]:off[i + 1]])
+            assert np.array_equal(got, oi[oo[q]:oo[q + 1]]), (mode, i)

@@ -179,6 +179,72 @@ def test_neighbour_sets_bit_exact(sph, mode, case):
         assert np.array_equal(got, oi[oo[i]:oo[i + 1]]), (slot, i)
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+@pytest.mark.parametrize("case", ["c1_8192", "ragged_3001"])
+def test_production_lists_bit_exact(sph, mode, case):
+    # the neighbour lists the density and force passes read (list-building walk
+    # of the density pass, shared walks, leaf caps), each filtered by the exact
+    # canonical test: the density set (mode 0) or force set (mode 1) bit for bit
+    # at the converged h (the production state) and at a +-3 % perturbation of
+    # it (the lists hold at most 128 entries, so h cannot stray much further)
+    native, ctx, torch = sph
+    w = CASES[case]
+    d, _ = oracle_eval(case, w)
+    rng = np.random.default_rng(mode + 31)
+    h = (d.h * (1.0 if mode < 2 else rng.uniform(0.97, 1.03, w.n))).astype(np.float32)
+    mode &= 1
+    s = upload(native, inputs.Workload("x", w.pos, w.vel, h))
+    p = native.sph_params_default()
+    native.sph_build_tree(ctx, s.c, p)
+    native.sph_get_stats(ctx)
+    off = torch.zeros(w.n + 1, dtype=torch.int64, device="cuda")
+    total = native.sph_neighbours(ctx, s.c, p, 2 + mode, off)
+    assert native.sph_get_stats(ctx)["list_overflows"] == 0
+    idx = torch.zeros(total, dtype=torch.int32, device="cuda")
+    native.sph_neighbours(ctx, s.c, p, 2 + mode, off, idx, total)
+    off, idx = off.cpu().numpy(), idx.cpu().numpy()
+    perm = s.numpy("perm").astype(np.int64)
+    oo, oi = oracle.neighbours(w.pos, h, mode)
+    assert total == oo[-1]
+    for slot in range(w.n):
+        i = perm[slot]
+        got = perm[idx[off[slot]:off[slot + 1]]]
+        assert len(np.unique(got)) == len(got), (slot, i)        # no entry twice
+        assert np.array_equal(np.sort(got), oi[oo[i]:oo[i + 1]]), (slot, i)
+
+
+def test_list_path_after_steps(sph):
+    # a few steps, then sph_density and sph_force from the converged h: both
+    # passes read the neighbour lists (no walking fallback) and give the
+    # oracle's values for the stepped state
+    native, ctx, torch = sph
+    w = CASES["ragged_3001"]
+    s, p = evaluate_gpu(native, ctx, w)
+    d_dt = torch.zeros(1, dtype=torch.float32, device="cuda")
+    native.sph_timestep(ctx, s.c, p, d_dt)
+    for _ in range(3):
+        native.sph_step(ctx, s.c, p, d_dt)
+    native.sph_sync(ctx)
+    native.sph_get_stats(ctx)
+    native.sph_density(ctx, s.c, p)
+    native.sph_force(ctx, s.c, p)
+    native.sph_sync(ctx)
+    st = native.sph_get_stats(ctx)
+    assert st["density_rewalks"] == 0 and st["force_rewalks"] == 0 and st["list_overflows"] == 0
+    assert st["force_pairs"] > 0
+    pos = s.in_original_order("pos")
+    vel = s.in_original_order("vel")
+    x, v = pos[:, :3].astype(np.float64), vel[:, :3].astype(np.float64)
+    m, u = pos[:, 3].astype(np.float64), vel[:, 3].astype(np.float64)
+    d = oracle.density(x, v, m, s.in_original_order("h"))
+    assert d.failures == 0
+    assert np.max(np.abs(s.in_original_order("rho") / d.rho - 1)) <= RHO_TOL
+    f = oracle.force(x, v, m, u, d.h, d.rho, d.omega)
+    acc = s.in_original_order("acc")
+    assert np.max(np.abs(acc[:, :3] - f.acc)) <= ACC_TOL * np.max(np.abs(f.acc))
+    assert np.max(np.abs(acc[:, 3] - f.dudt)) <= ACC_TOL * np.max(np.abs(f.dudt))
+
+
 # ------------------------------------------------------------------ density
 @pytest.mark.parametrize("case", ["c1_8192", "ragged_3001"])
 def test_density_parity(sph, case):
@@ -205,7 +271,9 @@ def test_density_fixed_iterations(sph):
     h = s.in_original_order("h")
     # three Newton updates from the same h0; both sides take the same branch
     rel = np.abs(h / d3.h - 1)
-    assert np.quantile(rel, 0.999) <= 1e-5
+    worst = np.argsort(rel)[-5:]
+    print("fixed-3 worst rel err", rel[worst], "h0", w.h[worst], "h3", d3.h[worst])
+    assert np.max(rel) <= 1e-5
 
 
 # -------------------------------------------------------------------- force
@@ -470,6 +538,55 @@ def test_nonfinite_input_is_rejected(sph):
     with pytest.raises(native.SphError) as e:
         native.sph_sync(ctx)
     assert e.value.status == 6
+
+
+@pytest.mark.parametrize("what,status", [("u<0", 7), ("m=0", 6), ("h=0", 6), ("v=inf", 6),
+                                         ("v=-inf", 6), ("u=nan", 6)])
+def test_bad_input_is_reported(sph, what, status):
+    # host-injected bad inputs: each condition is found on the device and
+    # returned, with its own status, by the next sph_sync
+    native, ctx, torch = sph
+    w = inputs.unit_sphere(700, seed=12)
+    k = 123
+    if what == "u<0":
+        w.vel[k, 3] = -0.01
+    elif what == "m=0":
+        w.pos[k, 3] = 0.0
+    elif what == "h=0":
+        w.h[k] = 0.0
+    elif what == "v=inf":
+        w.vel[k, 1] = np.inf
+    elif what == "v=-inf":
+        w.vel[k, 0] = -np.inf
+    elif what == "u=nan":
+        w.vel[k, 3] = np.nan
+    s = upload(native, w)
+    p = native.sph_params_default()
+    with pytest.raises(native.SphError) as e:
+        native.sph_build_tree(ctx, s.c, p)
+        native.sph_sync(ctx)
+        native.sph_density(ctx, s.c, p)
+        native.sph_sync(ctx)
+        native.sph_force(ctx, s.c, p)
+        native.sph_sync(ctx)
+    assert e.value.status == status, str(e.value)
+    native.sph_sync(ctx)          # the error word was cleared
+
+
+def test_lookback_wait_times_out(sph):
+    # a sort pass whose look-back predecessor never publishes gives up after its
+    # poll limit and reports SPH_ERR_TIMEOUT; the context stays usable
+    native, ctx, torch = sph
+    native.sph_sync(ctx)
+    native.sph_test_lookback_timeout(ctx, 64)
+    with pytest.raises(native.SphError) as e:
+        native.sph_sync(ctx)
+    assert e.value.status == 8
+    native.sph_sync(ctx)
+    w = CASES["ragged_3001"]
+    s, p = evaluate_gpu(native, ctx, w)
+    keys_o = oracle.morton_keys(w.pos)
+    assert np.array_equal(s.numpy("perm").astype(np.int64), oracle.sort_order(keys_o))
 
 
 def test_invalid_arguments(sph):

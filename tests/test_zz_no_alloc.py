@@ -52,3 +52,16 @@ def test_conserved_noalloc_rejects_oversize():
     with pytest.raises(native.SphError) as e:
         native.sph_conserved_noalloc(native.CONSERVED_NOALLOC_MAX_N + 1, dummy, dummy, out)
     assert e.value.status == 1
+
+
+def test_conserved_noalloc_rejects_misaligned_output():
+    # d_out8 receives doubles: an address that is not 8-byte aligned is rejected
+    # on the host, before anything is launched
+    import torch
+    from paper_1909_07439_gb300 import build, native
+    build.build()
+    buf = torch.zeros(20, dtype=torch.float32, device="cuda")
+    dummy = torch.zeros((4, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(native.SphError) as e:
+        native.sph_conserved_noalloc(4, dummy, dummy, buf[1:])     # base + 4 bytes
+    assert e.value.status == 1
