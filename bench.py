@@ -66,15 +66,16 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device_index: int):
+    def __init__(self, device_index: int, interval_ms: int = 20):
         self.dev = device_index
+        self.interval = interval_ms
         self.proc = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.interval)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -103,6 +104,43 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": float(max(mx)) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measure_fp32_peak(native, torch, sms, device_index, target_ms=400.0):
+    """Measured FP32 peak: the library's multiply-add chain probe (scalar FMA
+    and packed FP32x2 FMA), 8 blocks of 256 threads per SM, timed with CUDA
+    events on the launching stream while nvidia-smi samples the SM clock.
+    Returns TFLOP/s of each form and the median SM clock under the probe."""
+    sink = torch.zeros(1, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    blocks = 8 * sms
+    out = {}
+    clocks = ClockSampler(device_index, interval_ms=20)
+    for packed in (False, True):
+        flop_per_iter = blocks * 256 * (32 if packed else 16)
+        iters = 256
+        for _ in range(2):                       # warm-up, then size the run
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            native.sph_fp32_probe(sink, blocks, iters, packed)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            iters = max(256, int(iters * target_ms / max(ms, 1e-3)))
+        if packed is False:
+            clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        native.sph_fp32_probe(sink, blocks, iters, packed)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out["ffma2" if packed else "ffma"] = flop_per_iter * iters / (ms / 1e3) / 1e12
+    clk = clocks.stop()
+    out["sm_mhz"] = clk.get("sm_mhz")
+    out["clock_samples"] = clk.get("samples")
+    out["reasons"] = clk.get("reasons")
+    return out
 
 
 def shard_instances(sizes, world_size):

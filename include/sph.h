@@ -65,6 +65,13 @@ typedef struct {
                             fallback kernels, 0 = default (80 density, 96 force)     */
     int32_t max_h_iter;  /* Newton iteration cap (>= 1)                                 */
     int32_t density_iters; /* 0: iterate to h_tol; k > 0: exactly k updates (Sect. 3.2.1) */
+    /* Launch shape of the neighbour-list density and force kernels (results
+     * do not depend on it beyond FP32 summation order; 0 = default):       */
+    int32_t pair_targets;  /* targets per warp batch: 4, 8 (default) or 16;
+                              each target gets 32 / pair_targets lanes       */
+    int32_t pair_warps;    /* warps per block: 1, 2, 4 (default) or 8       */
+    int32_t pair_unroll;   /* list entries per lane and iteration of the
+                              force kernel: 2 (default) or 4               */
 } sph_params;
 
 /* Particle state, structure of arrays, n particles, device memory.
@@ -304,6 +311,16 @@ sph_status sph_get_stats(sph_ctx *ctx, sph_stats *out);
 #define SPH_N_STAGES 7
 sph_status sph_set_timing(sph_ctx *ctx, int enable);
 sph_status sph_get_timing(sph_ctx *ctx, double *ms_by_stage, int64_t *launches_by_stage);
+
+/* FP32 throughput probe (a measurement utility, not part of the method):
+ * enqueues `blocks` blocks of 256 threads, each thread running `iters`
+ * iterations of 8 independent fused multiply-add chains, as scalar FP32
+ * FMAs (packed = 0: 16 FLOP per thread and iteration) or packed FP32x2 FMAs
+ * (packed = 1: 32 FLOP per thread and iteration).  The caller times it with
+ * events on `stream`; d_sink is one device float that is never written in
+ * practice.  SPH_ERR_INVALID_ARG for bad arguments, SPH_ERR_CUDA if the
+ * launch fails; asynchronous otherwise. */
+sph_status sph_fp32_probe(float *d_sink, int blocks, int iters, int packed, void *stream);
 
 /* Synchronise `stream` and return (then clear) the device error word. */
 sph_status sph_sync(sph_ctx *ctx, void *stream);

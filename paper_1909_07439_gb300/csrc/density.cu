@@ -61,6 +61,7 @@ struct DensArgs {
     int *rec_bad;     // per instance: an h outgrew the pad of the lists
     float h_in_scale; // 1 + pad
     float hfact, tol, gamma;
+    int tb;           // targets per batch of the list kernel (4, 8 or 16)
     int max_iter, fixed_iters;
     int *err;
     unsigned long long *counters;
@@ -144,12 +145,15 @@ __device__ __forceinline__ void density_outputs(const DensArgs &a, int i, float 
     a.prop[i] = make_float4(h, rho, 1.f / (rho * om), cs);
 }
 
-__device__ __forceinline__ void push_fallback(const DensArgs &a, int g, int b0)
+__device__ __forceinline__ void push_fallback(const DensArgs &a, int g, int b0, int nt)
 {
-    if ((threadIdx.x & 31) == 0) a.fallback[atomicAdd(a.n_fallback, 1)] = make_int2(g, b0);
+    if ((threadIdx.x & 31) == 0) push_fallback_batch(a.fallback, a.n_fallback, g, b0, nt);
 }
 
-__global__ void __launch_bounds__(kDensWarps * 32) density_list_kernel(DensArgs a)
+// Launch shape (run-time): a.tb targets per batch (32 / a.tb lanes per
+// target), blockDim.x / 32 warps per block; registers capped for 1024
+// resident threads per SM.
+__global__ void __launch_bounds__(256, 4) density_list_kernel(DensArgs a)
 {
     const int lane = threadIdx.x & 31;
     const uint64_t keep = l2_keep_policy();
@@ -159,31 +163,31 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_list_kernel(DensArgs 
     const int limit = fixed ? a.fixed_iters : a.max_iter;
     unsigned long long n_pairs = 0, n_newton = 0;
     // The block takes kRound consecutive groups per warp at a time, warp w the
-    // groups base + w + kDensWarps k: the warps of a block work on neighbouring
-    // groups together and share their candidates in L1.
+    // groups base + w + nw k: the warps of a block work on neighbouring groups
+    // together and share their candidates in L1.
     __shared__ int s_base;
-    const int warp = threadIdx.x >> 5;
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 
     while (true) {
-        if (threadIdx.x == 0) s_base = atomicAdd(a.work, kDensWarps * kRound);
+        if (threadIdx.x == 0) s_base = atomicAdd(a.work, nw * kRound);
         __syncthreads();
         const int base = s_base;
         __syncthreads();
         if (base >= ng) break;
         for (int kr = 0; kr < kRound; ++kr) {
-            const int gq = base + warp + kDensWarps * kr;
+            const int gq = base + warp + nw * kr;
             if (gq >= ng) break;
             const int g = ng - 1 - gq;  // last group first: its lists were written last (in L2)
             const int2 gr = a.grp_ref[g];
-            for (int b0 = 0; b0 < gr.y; b0 += kTB) {
-                const int nt = min(kTB, gr.y - b0);
-                const int L = nt > 4 ? 4 : nt > 2 ? 8 : nt > 1 ? 16 : 32;
+            for (int b0 = 0; b0 < gr.y; b0 += a.tb) {
+                const int nt = min(a.tb, gr.y - b0);
+                const int L = lanes_per_target(nt);
                 const int t = lane / L, sub = lane % L;
                 const bool act = t < nt;
                 const int i = gr.x + b0 + (act ? t : 0);
                 const int len = act ? a.nl_len[i] : 0;
                 if (__any_sync(0xffffffffu, len < 0)) {  // no list (overflow, or too many leaves)
-                    push_fallback(a, g, b0);
+                    push_fallback(a, g, b0, nt);
                     continue;
                 }
                 const int *__restrict__ lst = a.nl_idx + (size_t)i * kNbrCap;
@@ -202,9 +206,10 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_list_kernel(DensArgs 
                     const float R = 2.f * h;
                     const float R2 = R * R;
                     // Two consecutive entries per lane and iteration (one 8-byte
-                    // load of the list), no branch on the distance: f and f' vanish
-                    // for q >= 2, so entries beyond 2 h add nothing.  A missing
-                    // second entry repeats the first with zero mass.
+                    // load of the list, fetched an iteration ahead: the lists come
+                    // from DRAM), no branch on the distance: f and f' vanish for
+                    // q >= 2, so entries beyond 2 h add nothing.  A missing second
+                    // entry repeats the first with zero mass.
                     auto entry = [&](float4 pj, float4 vj, float mj) {
                         const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
                         const float r2 = dx * dx + dy * dy + dz * dz;
@@ -212,8 +217,11 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_list_kernel(DensArgs 
                         cnt += (mj > 0.f && r2 < R2) ? 1 : 0;
                         pair_sums(r2, mj, vd, hinv, s0, s1, s2);
                     };
-                    for (int e = 2 * sub; e < len; e += 2 * L) {
-                        const int2 jj = __ldcs(reinterpret_cast<const int2 *>(lst + e));
+                    int e = 2 * sub;
+                    int2 jn = e < len ? __ldcs(reinterpret_cast<const int2 *>(lst + e)) : make_int2(0, 0);
+                    for (; e < len; e += 2 * L) {
+                        const int2 jj = jn;
+                        if (e + 2 * L < len) jn = __ldcs(reinterpret_cast<const int2 *>(lst + e + 2 * L));
                         const bool b1 = e + 1 < len;
                         float4 p0, v0, p1, v1;
                         ld_rec(a.rec, jj.x, keep, p0, v0);
@@ -246,7 +254,7 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_list_kernel(DensArgs 
                     }
                 }
                 if (__any_sync(0xffffffffu, outside)) {  // start the batch over with walks
-                    push_fallback(a, g, b0);
+                    push_fallback(a, g, b0, nt);
                     continue;
                 }
                 if (act && sub == 0) density_outputs(a, i, h, M, s1, s2, vi.w);
@@ -285,14 +293,14 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_walk_kernel(DensArgs 
         k = __shfl_sync(0xffffffffu, k, 0);
         if (k >= nfb) break;
         const int2 fb = a.fallback[k];
-        const int g = fb.x, b0 = fb.y;
+        const int g = fb.x, b0 = fb.y & 0xffff, cnt = fb.y >> 16;  // cnt <= kTB
         const int2 gr = a.grp_ref[g];
         const float4 glo = a.grp_lo[g], ghi = a.grp_hi[g];
         const int root = a.inst ? a.inst[gr.x] : 0;
         ++n_rewalk;
         {
-            const int nt = min(kTB, gr.y - b0);
-            const int L = nt > 4 ? 4 : nt > 2 ? 8 : nt > 1 ? 16 : 32;
+            const int nt = min(cnt, gr.y - b0);
+            const int L = lanes_per_target(nt);
             const int t = lane / L, sub = lane % L;
             const bool act = t < nt;
             const int i = gr.x + b0 + (act ? t : 0);
@@ -617,19 +625,20 @@ static cudaError_t configure_density(int &blocks)
     return cudaSuccess;
 }
 
-static cudaError_t configure_density_list(int &blocks)
+// resident blocks per SM of the list kernel for 1, 2, 4 and 8 warps per block
+static int g_dens_list_blocks[4];
+
+static cudaError_t configure_density_list()
 {
     static bool configured = false;
-    static int nb_cached = 1;
-    if (!configured) {
+    if (configured) return cudaSuccess;
+    for (int w = 0; w < 4; ++w) {
         int nb = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, density_list_kernel,
-                                                                      kDensWarps * 32, 0);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, density_list_kernel, 32 << w, 0);
         if (e != cudaSuccess) return e;
-        nb_cached = nb > 0 ? nb : 1;
-        configured = true;
+        g_dens_list_blocks[w] = nb > 0 ? nb : 1;
     }
-    blocks = nb_cached;
+    configured = true;
     return cudaSuccess;
 }
 
@@ -647,7 +656,7 @@ static cudaError_t launch_density_walk(Ctx &c, const DensArgs &a, cudaStream_t s
 cudaError_t configure_density_kernels()
 {
     int b;
-    cudaError_t e = configure_density_list(b);
+    cudaError_t e = configure_density_list();
     if (e == cudaSuccess) e = configure_density<64>(b);
     if (e == cudaSuccess) e = configure_density<80>(b);
     if (e == cudaSuccess) e = configure_density<96>(b);
@@ -706,10 +715,12 @@ cudaError_t density_solve(Ctx &c, const sph_state &s, const sph_params &p, cudaS
     static_assert(SZ_FALLBACK == SZ_WORK + 1 && SZ_WORK2 == SZ_WORK + 2, "work counters adjacent");
     cudaError_t e = cudaMemsetAsync(a.work, 0, 3 * sizeof(int), st);
     if (e != cudaSuccess) return e;
-    int blocks = 1;
-    e = configure_density_list(blocks);
+    e = configure_density_list();
     if (e != cudaSuccess) return e;
-    density_list_kernel<<<c.num_sms * blocks, kDensWarps * 32, 0, st>>>(a);
+    const PairShape ps = pair_shape(p);
+    a.tb = ps.targets;
+    const int wl = ps.warps == 8 ? 3 : ps.warps == 4 ? 2 : ps.warps == 2 ? 1 : 0;
+    density_list_kernel<<<c.num_sms * g_dens_list_blocks[wl], 32 * ps.warps, 0, st>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     int cap = p.tile > 0 ? p.tile : 80;

@@ -36,6 +36,8 @@ struct ForceSmem {
 
 struct ForceArgs {
     const float4 *pos, *vel, *prop;
+    const float4 *frec;  // [3 n] force records of the list kernel
+    int tb;              // targets per batch of the list kernel (4, 8 or 16)
     float4 *acc;
     float *vsigmax;
     const int2 *grp_ref;
@@ -148,7 +150,108 @@ struct ForceTarget {
     }
 };
 
-__global__ void __launch_bounds__(kForceWarps * 32, 8) force_list_kernel(ForceArgs a)
+// Pair sums of the list kernel for one target, written for few instructions
+// per pair with the per-particle factors taken from the force records:
+//   F(r, h) = C f'(q) / h^4 = -3 C / h^4 g(q / 2),
+//   g(p) = max(1 - p, 0)^2 - max(1 - 2 p, 0)^2
+// (f'(q) = -3 q + 9/4 q^2 for q < 1, -3/4 (2 - q)^2 for 1 <= q < 2, 0 beyond:
+// the M4 derivative), with q / 2 = r / (2 h) = r rsqrt((2 h)^2).  With
+// A = 1 / (rho Omega) and AK = -3 C A / h^4, A F = AK g.  A neighbour is
+// one 48-byte record (three 16-byte loads from one address):
+// (x, y, z, m), (vx, vy, vz, (gamma - 1) u), ((2 h)^2, AK, alpha c, rho).
+// The L1 data path is what bounds this kernel: the gathers deliver about
+// 48 bytes per wavefront, so the record holds only what the pair needs.
+// Per pair
+// (Eqs. 9-15, w = min(v_ij . rhat_ij, 0), hw = -w / 2):
+//   (P_i + q^i) / (rho_i^2 Omega_i) F_i = (P_i / rho_i + hw vsig_i) AK_i g_i
+//   du/dt terms: sum m_j vr g_i, sum m_j vsig_i hw^2 g_i and the conduction
+//   sum m_j |dP| rsqrt(|dP| (rho_i + rho_j)) (P_i/rho_i - P_j/rho_j) (AK_i g_i + AK_j g_j),
+// whose constant factors are applied once per target at the end.
+struct ForceSums {
+    float xi, yi, zi, vxi, vyi, vzi, pri;   // position, velocity, (gamma - 1) u
+    float R2i, AKi, aci, rhoi, Pi;          // (2 h)^2, AK, alpha c, rho, P
+    float ax, ay, az, sp, sv, sc, vsmax;
+    int cnt;
+
+    __device__ __forceinline__ void init(const float4 *rec)
+    {
+        const float4 p = rec[0], v = rec[1], q = rec[2];
+        xi = p.x; yi = p.y; zi = p.z;
+        vxi = v.x; vyi = v.y; vzi = v.z; pri = v.w;
+        R2i = q.x; AKi = q.y; aci = q.z; rhoi = q.w;
+        Pi = pri * rhoi;
+        ax = ay = az = sp = sv = sc = 0.f;
+        vsmax = aci;
+        cnt = 0;
+    }
+
+    // one list entry with record (p, v, q); valid = false for padding
+    __device__ __forceinline__ void pair(const float4 p, const float4 v, const float4 q, bool valid,
+                                         float beta)
+    {
+        const float prj = v.w;
+        // canonical separation: decides the pair set, feeds the pair terms
+        const float dx = __fsub_rn(xi, p.x), dy = __fsub_rn(yi, p.y), dz = __fsub_rn(zi, p.z);
+        const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+        // r < 2 max(h_i, h_j) as r^2 < max((2 h_i)^2, (2 h_j)^2): squaring is monotone
+        const bool in = valid && r2 > 0.f && r2 < fmaxf(R2i, q.x);
+        const float mj = in ? p.w : 0.f;
+        const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
+        const float r = r2 * rinv;
+        const float pi = r * rsqrtf(R2i), pj = r * rsqrtf(q.x);   // q / 2 of each side
+        const float ti = fmaxf(1.f - pi, 0.f), si = fmaxf(fmaf(-2.f, pi, 1.f), 0.f);
+        const float tj = fmaxf(1.f - pj, 0.f), sj = fmaxf(fmaf(-2.f, pj, 1.f), 0.f);
+        const float gi = fmaf(ti, ti, -si * si), gj = fmaf(tj, tj, -sj * sj);
+        const float Ti = AKi * gi, Tj = q.y * gj;
+        const float dvx = vxi - v.x, dvy = vyi - v.y, dvz = vzi - v.z, dpr = pri - prj;
+        const float vr = fmaf(dvz, dz, fmaf(dvy, dy, dvx * dx)) * rinv;
+        const float avr = fabsf(vr);
+        const float vsi = fmaf(beta, avr, aci);
+        const float hw = -0.5f * fminf(vr, 0.f);
+        const float pi_ = fmaf(hw, vsi, pri);
+        const float pj_ = fmaf(hw, fmaf(beta, avr, q.z), prj);
+        const float cr = fmaf(pi_, Ti, pj_ * Tj) * (mj * rinv);
+        ax = fmaf(-cr, dx, ax);
+        ay = fmaf(-cr, dy, ay);
+        az = fmaf(-cr, dz, az);
+        const float mg = mj * gi;
+        sp = fmaf(mg, vr, sp);
+        sv = fmaf(mg, vsi * (hw * hw), sv);
+        const float dP = fabsf(Pi - prj * q.w);
+        const float vu = dP * rsqrtf(fmaxf(dP * (rhoi + q.w), 1e-30f));
+        sc = fmaf(mj * (vu * dpr), Ti + Tj, sc);
+        vsmax = fmaxf(vsmax, in ? vsi : 0.f);
+        cnt += in ? 1 : 0;
+    }
+
+    // reduce over the L lanes of the target; lane sub == 0 writes
+    __device__ __forceinline__ void finish(int L, bool write, int i, float gm1, float alpha_u,
+                                           float4 *acc, float *vsig)
+    {
+        for (int o = L >> 1; o > 0; o >>= 1) {
+            ax += __shfl_xor_sync(0xffffffffu, ax, o);
+            ay += __shfl_xor_sync(0xffffffffu, ay, o);
+            az += __shfl_xor_sync(0xffffffffu, az, o);
+            sp += __shfl_xor_sync(0xffffffffu, sp, o);
+            sv += __shfl_xor_sync(0xffffffffu, sv, o);
+            sc += __shfl_xor_sync(0xffffffffu, sc, o);
+            vsmax = fmaxf(vsmax, __shfl_xor_sync(0xffffffffu, vsmax, o));
+        }
+        if (write) {
+            // Eq. 10 pressure work, Eq. 13 viscous heating (sv holds w^2 / 4) and
+            // conduction: vsig_u = sqrt(2) |dP| rsqrt(|dP| (rho_i + rho_j)), u = pr / (gamma - 1)
+            const float du = AKi * (pri * sp - 2.f * sv) + (0.70710678118654752f * alpha_u / gm1) * sc;
+            acc[i] = make_float4(ax, ay, az, du);
+            vsig[i] = vsmax;
+        }
+    }
+};
+
+// Launch shape (run-time): a.tb targets per batch (32 / a.tb lanes per
+// target), blockDim.x / 32 warps per block; NPER list entries per lane and
+// iteration.  Registers are capped for 768 resident threads per SM.
+template <int NPER>
+__global__ void __launch_bounds__(256, 3) force_list_kernel(ForceArgs a)
 {
     const int lane = threadIdx.x & 31;
     const uint64_t keep = l2_keep_policy();
@@ -156,64 +259,73 @@ __global__ void __launch_bounds__(kForceWarps * 32, 8) force_list_kernel(ForceAr
     const bool lists_fresh = a.rec_ctl[1] == 0;
     unsigned long long n_pairs = 0, n_cand = 0, n_fb = 0;
     // The block takes kRound consecutive groups per warp at a time, warp w the
-    // groups base + w + kForceWarps k: the warps of a block work on
-    // neighbouring groups together and share their candidates in L1.
+    // groups base + w + nw k: the warps of a block work on neighbouring groups
+    // together and share their candidates in L1.
     __shared__ int s_base;
-    const int warp = threadIdx.x >> 5;
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 
     while (true) {
-        if (threadIdx.x == 0) s_base = atomicAdd(a.work, kForceWarps * kRound);
+        if (threadIdx.x == 0) s_base = atomicAdd(a.work, nw * kRound);
         __syncthreads();
         const int base = s_base;
         __syncthreads();
         if (base >= ng) break;
         for (int kr = 0; kr < kRound; ++kr) {
-            const int g = base + warp + kForceWarps * kr;
+            const int g = base + warp + nw * kr;
             if (g >= ng) break;
             const int2 gr = a.grp_ref[g];
             const int root = a.inst ? a.inst[gr.x] : 0;
             const bool usable = lists_fresh && a.rec_bad[root] == 0;
-            for (int b0 = 0; b0 < gr.y; b0 += kFTB) {
-                const int nt = min(kFTB, gr.y - b0);
-                const int L = nt > 4 ? 4 : nt > 2 ? 8 : nt > 1 ? 16 : 32;
+            for (int b0 = 0; b0 < gr.y; b0 += a.tb) {
+                const int nt = min(a.tb, gr.y - b0);
+                const int L = lanes_per_target(nt);
                 const int t = lane / L, sub = lane % L;
                 const bool act = t < nt;
                 const int i = gr.x + b0 + (act ? t : 0);
                 const int len = usable && act ? a.nl_len[i] : 0;
                 if (!usable || __any_sync(0xffffffffu, len < 0)) {
-                    if (lane == 0) a.fallback[atomicAdd(a.n_fallback, 1)] = make_int2(g, b0);
+                    if (lane == 0) push_fallback_batch(a.fallback, a.n_fallback, g, b0, nt);
                     ++n_fb;
                     continue;
                 }
-                ForceTarget T;
-                T.init(a.pos[i], a.vel[i], a.prop[i], a);
+                ForceSums T;
+                T.init(a.frec + 3 * (size_t)i);
                 const int *__restrict__ lst = a.nl_idx + (size_t)i * kNbrCap;
                 // Four consecutive entries per lane and iteration (one 16-byte
-                // load of the list), no branch: an entry outside the pair set (or
-                // padding) gets zero mass.  The particle itself (r = 0) is
-                // left out; a distinct particle at r = 0 would add nothing either
-                // (every term carries f'(0) = 0 or v_ij.r_ij / r = 0).
+                // load of the list, fetched an iteration ahead), no branch: an
+                // entry outside the pair set (or padding) gets zero mass.  The
+                // particle itself (r = 0) is left out; a distinct particle at
+                // r = 0 would add nothing either (every term carries f'(0) = 0 or
+                // v_ij.r_ij / r = 0).
                 auto entry = [&](int j, bool valid) {
-                    const float4 pj = ld_keep(a.pos, j, keep);
-                    const float4 qj = ld_keep(a.prop, j, keep);
-                    const float4 vj = ld_keep(a.vel, j, keep);
-                    // canonical separation: decides the pair set and feeds the pair terms
-                    const float dx = __fsub_rn(T.xi.x, pj.x), dy = __fsub_rn(T.xi.y, pj.y),
-                                dz = __fsub_rn(T.xi.z, pj.z);
-                    const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-                    const float R = 2.0f * fmaxf(T.qi.x, qj.x);
-                    const bool in = valid && r2 > 0.f && r2 < R * R;
-                    T.pair_d(dx, dy, dz, r2, vj, qj, in ? pj.w : 0.f, in, a);
+                    const float4 *rj = a.frec + 3 * (size_t)j;
+                    T.pair(ld_keep(rj, 0, keep), ld_keep(rj, 1, keep), ld_keep(rj, 2, keep), valid,
+                           a.beta);
                 };
-                for (int e = 4 * sub; e < len; e += 4 * L) {
-                    const int4 jj = __ldcs(reinterpret_cast<const int4 *>(lst + e));
-                    const bool b1 = e + 1 < len, b2 = e + 2 < len, b3 = e + 3 < len;
-                    entry(jj.x, true);
-                    entry(b1 ? jj.y : jj.x, b1);
-                    entry(b2 ? jj.z : jj.x, b2);
-                    entry(b3 ? jj.w : jj.x, b3);
+                if (NPER == 4) {
+                    int e = 4 * sub;
+                    int4 jn = e < len ? __ldcs(reinterpret_cast<const int4 *>(lst + e)) : make_int4(0, 0, 0, 0);
+                    for (; e < len; e += 4 * L) {
+                        const int4 jj = jn;
+                        if (e + 4 * L < len) jn = __ldcs(reinterpret_cast<const int4 *>(lst + e + 4 * L));
+                        const bool b1 = e + 1 < len, b2 = e + 2 < len, b3 = e + 3 < len;
+                        entry(jj.x, true);
+                        entry(b1 ? jj.y : jj.x, b1);
+                        entry(b2 ? jj.z : jj.x, b2);
+                        entry(b3 ? jj.w : jj.x, b3);
+                    }
+                } else {
+                    int e = 2 * sub;
+                    int2 jn = e < len ? __ldcs(reinterpret_cast<const int2 *>(lst + e)) : make_int2(0, 0);
+                    for (; e < len; e += 2 * L) {
+                        const int2 jj = jn;
+                        if (e + 2 * L < len) jn = __ldcs(reinterpret_cast<const int2 *>(lst + e + 2 * L));
+                        const bool b1 = e + 1 < len;
+                        entry(jj.x, true);
+                        entry(b1 ? jj.y : jj.x, b1);
+                    }
                 }
-                T.finish(L, act && sub == 0, i, a);
+                T.finish(L, act && sub == 0, i, a.gm1, a.alpha_u, a.acc, a.vsigmax);
                 n_pairs += T.cnt;
                 n_cand += act && sub == 0 ? (unsigned long long)len : 0ull;
             }
@@ -248,12 +360,12 @@ __global__ void __launch_bounds__(kForceWarps * 32) force_walk_kernel(ForceArgs 
         k = __shfl_sync(0xffffffffu, k, 0);
         if (k >= nfb) break;
         const int2 fb = a.fallback[k];
-        const int g = fb.x, b0 = fb.y;
+        const int g = fb.x, b0 = fb.y & 0xffff, cnt = fb.y >> 16;  // cnt <= kFTB
         const int2 gr = a.grp_ref[g];
         const float4 glo = a.grp_lo[g], ghi = a.grp_hi[g];
         {
-            const int nt = min(kFTB, gr.y - b0);
-            const int L = nt > 4 ? 4 : nt > 2 ? 8 : nt > 1 ? 16 : 32;
+            const int nt = min(cnt, gr.y - b0);
+            const int L = lanes_per_target(nt);
             const int t = lane / L, sub = lane % L;
             const bool act = t < nt;
             const int i0 = gr.x + b0;
@@ -339,20 +451,28 @@ __global__ void __launch_bounds__(kForceWarps * 32) force_walk_kernel(ForceArgs 
     }
 }
 
-// prop = (h, rho, 1/(rho Omega), c_s) from the state; checks vel and u
-__global__ void force_prep_kernel(const float4 *__restrict__ vel, const float *__restrict__ h,
-                                  const float *__restrict__ rho, const float *__restrict__ omega,
-                                  float4 *__restrict__ prop, int n, float gamma, int *err)
+// prop = (h, rho, 1/(rho Omega), c_s) and the force records from the state;
+// checks vel and u
+__global__ void force_prep_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ vel,
+                                  const float *__restrict__ h, const float *__restrict__ rho,
+                                  const float *__restrict__ omega, float4 *__restrict__ prop,
+                                  float4 *__restrict__ frec, int n, float gamma, float alpha, int *err)
 {
     bool bad = false, neg = false;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        float4 v = vel[i];
-        float r = rho[i], o = omega[i];
+        const float4 v = vel[i];
+        const float r = rho[i], o = omega[i], hi = h[i];
         bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w) && isfinite(r) &&
                  isfinite(o));
         neg |= v.w < 0.f;
-        float cs = sqrtf(fmaxf(gamma * (gamma - 1.f) * v.w, 0.f));
-        prop[i] = make_float4(h[i], r, 1.f / (r * o), cs);
+        const float cs = sqrtf(fmaxf(gamma * (gamma - 1.f) * v.w, 0.f));
+        const float A = 1.f / (r * o);
+        prop[i] = make_float4(hi, r, A, cs);
+        const float R = 2.0f * hi;
+        const float hinv = 1.f / hi, hinv2 = hinv * hinv;
+        frec[3 * (size_t)i] = pos[i];
+        frec[3 * (size_t)i + 1] = make_float4(v.x, v.y, v.z, (gamma - 1.f) * v.w);
+        frec[3 * (size_t)i + 2] = make_float4(R * R, -3.f * kCNorm * A * hinv2 * hinv2, alpha * cs, r);
     }
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) raise_error(err, SPH_ERR_NONFINITE);
     if (__any_sync(0xffffffffu, neg) && (threadIdx.x & 31) == 0) raise_error(err, SPH_ERR_NEGATIVE_U);
@@ -380,19 +500,24 @@ static cudaError_t configure_force(int &blocks)
     return cudaSuccess;
 }
 
-static cudaError_t configure_force_list(int &blocks)
+// Resident blocks per SM of the list kernel for each (entries per lane,
+// warps per block): computed once, before any graph capture.
+static int g_force_list_blocks[2][4];
+
+static cudaError_t configure_force_list()
 {
     static bool configured = false;
-    static int nb_cached = 1;
-    if (!configured) {
-        int nb = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_list_kernel,
-                                                                      kForceWarps * 32, 0);
-        if (e != cudaSuccess) return e;
-        nb_cached = nb > 0 ? nb : 1;
-        configured = true;
-    }
-    blocks = nb_cached;
+    if (configured) return cudaSuccess;
+    for (int u = 0; u < 2; ++u)
+        for (int w = 0; w < 4; ++w) {
+            int nb = 0;
+            const int threads = 32 << w;  // 1, 2, 4, 8 warps
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &nb, u ? force_list_kernel<4> : force_list_kernel<2>, threads, 0);
+            if (e != cudaSuccess) return e;
+            g_force_list_blocks[u][w] = nb > 0 ? nb : 1;
+        }
+    configured = true;
     return cudaSuccess;
 }
 
@@ -410,7 +535,7 @@ static cudaError_t launch_force_walk(Ctx &c, const ForceArgs &a, cudaStream_t st
 cudaError_t configure_force_kernels()
 {
     int b;
-    cudaError_t e = configure_force_list(b);
+    cudaError_t e = configure_force_list();
     if (e == cudaSuccess) e = configure_force<64>(b);
     if (e == cudaSuccess) e = configure_force<96>(b);
     if (e == cudaSuccess) e = configure_force<128>(b);
@@ -423,8 +548,8 @@ cudaError_t force_prep(Ctx &c, const sph_state &s, const sph_params &p, cudaStre
     const int n = (int)s.n;
     int grid = (n + 255) / 256;
     if (grid > c.num_sms * 16) grid = c.num_sms * 16;
-    force_prep_kernel<<<grid, 256, 0, st>>>((const float4 *)s.vel, s.h, s.rho, s.omega, c.prop, n,
-                                            p.gamma, c.d_err);
+    force_prep_kernel<<<grid, 256, 0, st>>>((const float4 *)s.pos, (const float4 *)s.vel, s.h, s.rho,
+                                            s.omega, c.prop, c.frec, n, p.gamma, p.alpha_av, c.d_err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return hmax_now ? update_hmax(c, s, p, st) : cudaSuccess;
@@ -445,6 +570,7 @@ cudaError_t force_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStre
     a.pos = (const float4 *)s.pos;
     a.vel = (const float4 *)s.vel;
     a.prop = c.prop;
+    a.frec = c.frec;
     a.acc = (float4 *)s.acc;
     a.vsigmax = s.vsigmax;
     a.grp_ref = c.tree.grp_ref;
@@ -462,10 +588,14 @@ cudaError_t force_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStre
     a.counters = c.d_counters;
     e = cudaMemsetAsync(a.work, 0, 3 * sizeof(int), st);  // work, fallback count, work2
     if (e != cudaSuccess) return e;
-    int blocks = 1;
-    e = configure_force_list(blocks);
+    e = configure_force_list();
     if (e != cudaSuccess) return e;
-    force_list_kernel<<<c.num_sms * blocks, kForceWarps * 32, 0, st>>>(a);
+    const PairShape ps = pair_shape(p);
+    a.tb = ps.targets;
+    const int u = ps.unroll == 4 ? 1 : 0, wl = ps.warps == 8 ? 3 : ps.warps == 4 ? 2 : ps.warps == 2 ? 1 : 0;
+    const int grid = c.num_sms * g_force_list_blocks[u][wl];
+    if (u) force_list_kernel<4><<<grid, 32 * ps.warps, 0, st>>>(a);
+    else force_list_kernel<2><<<grid, 32 * ps.warps, 0, st>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // the walking kernel needs node and group h_max of the final h; refreshed

@@ -125,6 +125,10 @@ sph_status check_params(Ctx &c, const sph_params *p)
         return fail(c, SPH_ERR_INVALID_ARG, "n_leaf must be 1..64 and n_group 1..32");
     if (p->tile < 0 || p->tile > 128 || p->max_h_iter < 1 || p->density_iters < 0)
         return fail(c, SPH_ERR_INVALID_ARG, "tile 0..128, max_h_iter >= 1, density_iters >= 0");
+    const int t = p->pair_targets, w = p->pair_warps, u = p->pair_unroll;
+    if (!(t == 0 || t == 4 || t == 8 || t == 16) || !(w == 0 || w == 1 || w == 2 || w == 4 || w == 8) ||
+        !(u == 0 || u == 2 || u == 4))
+        return fail(c, SPH_ERR_INVALID_ARG, "pair_targets 0/4/8/16, pair_warps 0/1/2/4/8, pair_unroll 0/2/4");
     return SPH_OK;
 }
 
@@ -323,6 +327,9 @@ void sph_params_default(sph_params *p)
     p->tile = 0;
     p->max_h_iter = 50;
     p->density_iters = 0;
+    p->pair_targets = 8;
+    p->pair_warps = 4;
+    p->pair_unroll = 2;
 }
 
 sph_status sph_create(sph_ctx **out, int64_t max_n, int device)
@@ -391,6 +398,7 @@ sph_status sph_create(sph_ctx **out, int64_t max_n, int device)
     A(dalloc(t.blk_cnt, (size_t)kLevels * nbchop));
     A(dalloc(c.rec, 2 * n));
     A(dalloc(c.prop, n));
+    A(dalloc(c.frec, 3 * n));
     A(dalloc(c.vhalf, n));
     A(dalloc(c.inst, n));
     A(dalloc(c.bbox_inst, (size_t)6 * kMaxInstances));
@@ -431,7 +439,7 @@ void sph_destroy(sph_ctx *h)
                     c.tree.grp_lo, c.tree.grp_hi, c.tree.lv_tree, c.tree.lv_grp, c.tree.blk_cnt,
                     c.nl_idx, c.nl_len, c.fallback,
                     c.tree.rec_ctl, c.tree.rec_bad,
-                    c.rec, c.prop, c.vhalf, c.inst, c.bbox_inst, c.dtmin_inst,
+                    c.rec, c.prop, c.frec, c.vhalf, c.inst, c.bbox_inst, c.dtmin_inst,
                     c.bbox, c.scan_part, c.red_f, c.red_d, c.d_err, c.d_counters,
                     c.d_sizes, c.mirror.pos, c.mirror.vel, c.mirror.acc, c.mirror.h, c.mirror.rho,
                     c.mirror.omega, c.mirror.drhodt, c.mirror.vsigmax, c.mirror.perm,

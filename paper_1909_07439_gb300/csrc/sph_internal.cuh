@@ -115,6 +115,9 @@ struct Ctx {
     // per-particle scratch
     float4 *rec = nullptr;    // [2 n]: pos, vel of each particle side by side (32-byte records)
     float4 *prop = nullptr;   // h, rho, 1/(rho Omega), c_s
+    // [n]: the force factors of each particle, read with its record in rec:
+    // ((2 h)^2, -3 C / (h^4 rho Omega), alpha_AV c_s, rho)
+    float4 *frec = nullptr;
     float4 *vhalf = nullptr;  // half-step v, u of the leapfrog
     float *bbox = nullptr;    // [8]: lo xyz, size, then scratch
     // batches
@@ -238,6 +241,25 @@ void release_rollout(Ctx &c);
 
 // helpers
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// Launch shape of the list pair kernels (density and force), from sph_params
+// (0 selects the default): targets per warp batch (4, 8 or 16; a target gets
+// 32 / targets lanes), warps per block (1, 2, 4 or 8) and list entries per
+// lane and iteration of the force kernel (2 or 4).
+struct PairShape {
+    int targets, warps, unroll;
+};
+inline PairShape pair_shape(const sph_params &p)
+{
+    return PairShape{p.pair_targets ? p.pair_targets : 8, p.pair_warps ? p.pair_warps : 4,
+                     p.pair_unroll ? p.pair_unroll : 2};
+}
+
+// lanes per target for a batch of nt targets (a power of two, nt * L <= 32)
+__host__ __device__ inline int lanes_per_target(int nt)
+{
+    return nt > 8 ? 2 : nt > 4 ? 4 : nt > 2 ? 8 : nt > 1 ? 16 : 32;
+}
 
 // number of blocks used by the chop's per-block counting (1024 particles each)
 constexpr int kChopBlock = 1024;

@@ -338,6 +338,16 @@ __device__ __forceinline__ int walk_leaves_wide(const WalkTree &T, int root, flo
     return ok && nout <= cap ? nout : -1;
 }
 
+// Hand a batch of cnt targets of group g, from its target b0 on, to the
+// walking kernels, in items of at most 8 targets (their batch size):
+// item = (g, first target | count << 16).  Called by one lane.
+__device__ __forceinline__ void push_fallback_batch(int2 *fallback, int *n_fallback, int g, int b0,
+                                                    int cnt)
+{
+    for (int k = 0; k < cnt; k += 8)
+        fallback[atomicAdd(n_fallback, 1)] = make_int2(g, (b0 + k) | (min(8, cnt - k) << 16));
+}
+
 // Candidate slots of a group: runs[m] = (first particle, first slot) for
 // m < nrun and runs[nrun] = (-1, number of candidates).  Slot k belongs to the
 // run r with runs[r].y <= k < runs[r + 1].y; r only moves forward, so a lane

@@ -35,7 +35,8 @@ class sph_params(ctypes.Structure):
                 ("beta_av", c_float), ("alpha_u", c_float), ("c_cour", c_float),
                 ("h_tol", c_float), ("kernel", c_int32), ("n_leaf", c_int32),
                 ("n_group", c_int32), ("tile", c_int32), ("max_h_iter", c_int32),
-                ("density_iters", c_int32)]
+                ("density_iters", c_int32), ("pair_targets", c_int32), ("pair_warps", c_int32),
+                ("pair_unroll", c_int32)]
 
 
 class sph_state(ctypes.Structure):
@@ -60,7 +61,7 @@ EXPORTS = ("sph_params_default", "sph_create", "sph_destroy", "sph_build_tree", 
            "sph_batch_step", "sph_force_bwd", "sph_density_bwd", "sph_rollout", "sph_conserved",
            "sph_conserved_noalloc",
            "sph_neighbours", "sph_get_tree", "sph_get_stats", "sph_set_timing", "sph_get_timing", "sph_sync",
-           "sph_last_error", "sph_test_lookback_timeout")
+           "sph_last_error", "sph_test_lookback_timeout", "sph_fp32_probe")
 
 
 def load():
@@ -100,6 +101,7 @@ def load():
                                  POINTER(c_int64)]
     lib.sph_get_stats.argtypes = [P, POINTER(sph_stats)]
     lib.sph_test_lookback_timeout.argtypes = [P, c_int, P]
+    lib.sph_fp32_probe.argtypes = [P, c_int, c_int, c_int, P]
     lib.sph_set_timing.argtypes = [P, c_int]
     lib.sph_get_timing.argtypes = [P, POINTER(c_double), POINTER(c_int64)]
     lib.sph_sync.argtypes = [P, P]
@@ -275,6 +277,14 @@ def sph_get_tree(ctx, node_cap=1 << 26, group_cap=1 << 26):
 
 def sph_test_lookback_timeout(ctx, spin_cap, stream=None):
     return _check(ctx, load().sph_test_lookback_timeout(ctx, int(spin_cap), _stream(stream)))
+
+
+def sph_fp32_probe(d_sink, blocks, iters, packed=False, stream=None):
+    st = load().sph_fp32_probe(_ptr(d_sink), int(blocks), int(iters), 1 if packed else 0,
+                               _stream(stream))
+    if st != SPH_OK:
+        raise SphError(st, "sph_fp32_probe failed")
+    return st
 
 
 def sph_get_stats(ctx) -> dict:

@@ -185,13 +185,14 @@ def test_production_lists_bit_exact(sph, mode, case):
     # the neighbour lists the density and force passes read (list-building walk
     # of the density pass, shared walks, leaf caps), each filtered by the exact
     # canonical test: the density set (mode 0) or force set (mode 1) bit for bit
-    # at the converged h (the production state) and at a +-3 % perturbation of
-    # it (the lists hold at most 128 entries, so h cannot stray much further)
+    # at the converged h (the production state) and at h shrunk by up to 5 %
+    # per particle (the lists hold at most 128 entries: a larger h could
+    # overflow them, and then the walking kernels take over)
     native, ctx, torch = sph
     w = CASES[case]
     d, _ = oracle_eval(case, w)
     rng = np.random.default_rng(mode + 31)
-    h = (d.h * (1.0 if mode < 2 else rng.uniform(0.97, 1.03, w.n))).astype(np.float32)
+    h = (d.h * (1.0 if mode < 2 else rng.uniform(0.95, 1.0, w.n))).astype(np.float32)
     mode &= 1
     s = upload(native, inputs.Workload("x", w.pos, w.vel, h))
     p = native.sph_params_default()
@@ -293,6 +294,30 @@ def test_force_parity(sph, case):
     hi = oracle.force(x, v, m, u, d.h, d.rho, d.omega, vsig_scale=1 + 1e-4).vsigmax
     vs = s.in_original_order("vsigmax")
     assert np.all(vs >= lo * (1 - 1e-5)) and np.all(vs <= hi * (1 + 1e-5))
+
+
+@pytest.mark.parametrize("shape", [(4, 2, 4), (16, 8, 2), (16, 1, 4), (8, 4, 4)])
+def test_launch_shapes_keep_parity(sph, shape):
+    # the autotuner's launch shapes of the list pair kernels (targets per batch,
+    # warps per block, entries per iteration) change only the FP32 summation order
+    native, ctx, torch = sph
+    t, wp, u = shape
+    w = CASES["ragged_3001"]
+    s, p = evaluate_gpu(native, ctx, w, pair_targets=t, pair_warps=wp, pair_unroll=u, n_group=16)
+    d, f = oracle_eval("ragged_3001", w)
+    assert np.max(np.abs(s.in_original_order("rho") / d.rho - 1)) <= RHO_TOL
+    acc = s.in_original_order("acc")
+    assert np.max(np.abs(acc[:, :3] - f.acc)) <= ACC_TOL * np.max(np.abs(f.acc))
+    assert np.max(np.abs(acc[:, 3] - f.dudt)) <= ACC_TOL * np.max(np.abs(f.dudt))
+
+
+def test_bad_launch_shape_rejected(sph):
+    native, ctx, torch = sph
+    s = upload(native, inputs.unit_sphere(64))
+    for bad in ({"pair_targets": 5}, {"pair_warps": 3}, {"pair_unroll": 8}):
+        with pytest.raises(native.SphError) as e:
+            native.sph_build_tree(ctx, s.c, native.sph_params_default(**bad))
+        assert e.value.status == 1
 
 
 def test_force_invariants(sph):
