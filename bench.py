@@ -32,22 +32,37 @@ sys.path.insert(0, ROOT)
 METRIC = "SPH particle-updates/s & pair-interactions/s (1 GB300); batched/adjoint vs plain"
 UNIT = "particle-updates/s"
 SIDE = 128
-# Algorithmic FP32 operations per pair (FMA = 2, add/mul = 1; sqrt, rcp and
-# divide are special-function ops, not counted), from the plain definition:
-#  density sweep pair: distance 8, kernel f and f' 9, sums 7            = 24
-#  force pair: distance 8, two kernel gradients 14, v_ij.rhat 9,
-#  signal speed 2, pressure/viscosity coefficient 9, acceleration 7,
-#  pressure work 3, conduction 11, P_j 2 (viscous branch not counted)   = 65
-FLOP_DENSITY_PAIR = 24
-FLOP_FORCE_PAIR = 65
-#  neighbour-list candidate test: canonical squared distance, 3 sub 3 mul 2 add = 8
+# Algorithmic FP32 operations per pair, counted on the oracle's operation
+# list (the plain definition, Eqs. 1-15, as oracle/sph_oracle.c writes it:
+# FMA = 2, add / sub / mul / div = 1, sqrt not counted):
+#  force pair in the force set (orc_force): separation 3, r^2 5, 2 h_max 1,
+#  v_ij . rhat 9 (with the divide), signal speed 3, F(r, h_i) 10 and
+#  F(r, h_j) 10 (q = r/h, f'(q) 4, C f' / h^4 5), P_j 3, c_j 2, coefficient
+#  12, acceleration 9, pressure work 3, conduction speed 4, conduction 12 = 86;
+#  the viscous terms of approaching pairs (q^i, q^j, heating: 21 more) are
+#  not counted, so 86 is a lower bound.
+#  density sweep pair (density_sums): separation 3, r^2 5, W 12, dW/dh 21,
+#  the two sums 4 = 45.
+#  neighbour-list candidate test: canonical squared distance 3 sub 3 mul 2 add = 8.
+FLOP_FORCE_PAIR = 86
+FLOP_DENSITY_PAIR = 45
 FLOP_TEST = 8
-# DRAM bytes (read + write) per launch of the longest-stage kernels from one
-# ncu capture of this workload (profiles/list_density_force_kernels_sedov128_ncu.md);
-# to be re-measured whenever those kernels change.
+# Executed FP32 operations per force pair of the list kernel
+# (2 FFMA + FADD + FMUL from ncu's sass instruction counters over one launch
+# of the 128^3 step, 2.71e9 FFMA, 2.05e9 FADD, 3.54e9 FMUL, divided by that
+# launch's 1.3107e8 pairs; the count includes the list entries outside the
+# pair set, which the kernel evaluates with zero mass).
+EXEC_FLOP_FORCE_PAIR = 84.0
+# DRAM bytes (read + write) per launch of the pair kernels from one ncu capture
+# of the 128^3 step; None where the kernel changed after the capture.
 NCU_TRAFFIC = {"nlist_kernel": 132.619e6 + 598.933248e6,
-               "density_list_kernel": 1097.445e6 + 49.05984e6,
-               "force_list_kernel": 992.03e6 + 31.500544e6}
+               "density_list_kernel": None,
+               "force_list_kernel": 1007.506e6 + 28.696064e6}
+# Algorithmic bytes per particle of the tree build (bbox 20, keys 28, four
+# 12-byte-key passes of the sort read and written 96, run fix-up 8, gather of
+# pos, vel, half-step vel, h and perm read and written 112 plus the 32-byte
+# record and 8-byte key 40, chop and node bounds 28).
+TREE_BYTES_PER_PARTICLE = 332
 
 
 def peaks():
@@ -143,6 +158,44 @@ def measure_fp32_peak(native, torch, sms, device_index, target_ms=400.0):
     return out
 
 
+def roofline(stage_ms, stats, reps, fp32_peak, peak_basis, hbm_peak, n):
+    """Roofline of the pair-kernel stages (FP32 ALU bound) and of the tree
+    build (HBM bound), from the library's stage timers (CUDA events on the
+    launching stream) summed over `reps` launches and the work counters."""
+    work = {"lists": ("nlist_kernel", stats["density_candidates"] * FLOP_TEST, None),
+            "density": ("density_list_kernel", stats["density_pairs"] * FLOP_DENSITY_PAIR, None),
+            "force": ("force_list_kernel", stats["force_pairs"] * FLOP_FORCE_PAIR,
+                      stats["force_pairs"] * EXEC_FLOP_FORCE_PAIR)}
+    stages = {}
+    for st, (kern, flop, exe) in work.items():
+        ms = stage_ms[st] / reps
+        if ms <= 0:
+            continue
+        ach = flop / reps / (ms / 1e3) / 1e12
+        stages[st] = {"kernel": kern, "launch_ms": round(ms, 4), "achieved": round(ach, 3),
+                      "frac": round(ach / fp32_peak, 4)}
+        if exe is not None:
+            stages[st]["achieved_executed"] = round(exe / reps / (ms / 1e3) / 1e12, 3)
+    dom = max(stages, key=lambda k: stages[k]["launch_ms"])
+    d = stages[dom]
+    roof = {"kernel": d["kernel"], "bound": "alu", "achieved": d["achieved"],
+            "peak": round(fp32_peak, 2), "unit": "TFLOP/s", "frac": d["frac"],
+            "traffic": NCU_TRAFFIC.get(d["kernel"]), "peak_basis": peak_basis,
+            "launch_ms": d["launch_ms"], "flop_per_pair": FLOP_FORCE_PAIR if dom == "force" else None,
+            "stages": stages}
+    if "achieved_executed" in d:
+        roof["achieved_executed"] = d["achieved_executed"]
+        roof["frac_executed"] = round(d["achieved_executed"] / fp32_peak, 4)
+    tree_ms = stage_ms["tree"] / reps
+    if tree_ms > 0:
+        gbs = TREE_BYTES_PER_PARTICLE * n / (tree_ms / 1e3) / 1e9
+        roof["tree_build"] = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm_peak,
+                              "unit": "GB/s", "frac": round(gbs / hbm_peak, 4),
+                              "bytes_per_particle": TREE_BYTES_PER_PARTICLE,
+                              "launch_ms": round(tree_ms, 4)}
+    return roof
+
+
 def shard_instances(sizes, world_size):
     """Split independent instances over ranks, balancing particle counts
     (largest first onto the least-loaded rank); deterministic."""
@@ -211,17 +264,20 @@ def run_ours(args):
         for _ in range(2):
             native.sph_step(ctx, s.c, p, d_dt, d_t)
         native.sph_sync(ctx)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32 = measure_fp32_peak(native, torch, sms, local)
     native.sph_get_stats(ctx)          # reset counters
     native.sph_get_timing(ctx)         # reset stage timers
     native.sph_set_timing(ctx, True)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 129 MB L2
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(args.steps)]
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local, interval_ms=10)
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    time.sleep(0.05)                   # the sampler's first sample lands in the region
     for k in range(args.steps):
         flush.zero_()                  # L2 flushed between timed steps (outside the events)
         evs[k][0].record(stream)
@@ -246,31 +302,27 @@ def run_ours(args):
     pairs = stats["density_pairs"] + stats["force_pairs"]
     pair_rate = pairs * ws / (total_ms / 1e3)
 
-    # roofline of the dominant kernel (ALU-bound pair passes)
+    # roofline: the longest pair-kernel stage against the measured FP32 peak,
+    # the tree build against the measured HBM copy bandwidth
     pk, pk_kind = peaks()
-    sms = torch.cuda.get_device_properties(local).multi_processor_count
-    peak_tflops = 2 * 128 * sms * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    # stage -> (its main kernel, algorithmic FLOPs); each of these stages is
-    # that kernel plus a fallback kernel with (normally) no work
-    work = {"lists": ("nlist_kernel", stats["density_candidates"] * FLOP_TEST),
-            "density": ("density_list_kernel", stats["density_pairs"] * FLOP_DENSITY_PAIR),
-            "force": ("force_list_kernel", stats["force_pairs"] * FLOP_FORCE_PAIR)}
-    dstage = max(work, key=lambda k: stage_ms[k])
-    (dom, dflop), dms = work[dstage], stage_ms[dstage]
-    achieved = dflop / args.steps / (dms / args.steps / 1e3) / 1e12
-    roof = {"kernel": dom, "bound": "alu", "achieved": round(achieved, 3),
-            "peak": round(peak_tflops, 2), "unit": "TFLOP/s",
-            "frac": round(achieved / peak_tflops, 4), "traffic": NCU_TRAFFIC.get(dom),
-            "peak_basis": f"FP32 FMA 2 x 128 lanes x {sms} SMs x {pk.get('sm_max_mhz', 2070.0)} MHz "
-                          f"(sm_max_mhz {pk_kind})",
-            "launch_ms": round(dms / args.steps, 4)}
+    fp32_peak = max(fp32["ffma"], fp32["ffma2"])
+    basis = (f"measured: FP32 multiply-add chain probe, {8 * sms} blocks of 256 threads, "
+             f"scalar FMA {fp32['ffma']:.1f} and packed FP32x2 FMA {fp32['ffma2']:.1f} TFLOP/s at "
+             f"median SM clock {fp32['sm_mhz']} MHz (nominal 2 x 128 lanes x {sms} SMs x "
+             f"{pk.get('sm_max_mhz', 2070.0)} MHz = "
+             f"{2 * 128 * sms * pk.get('sm_max_mhz', 2070.0) / 1e6:.2f})")
+    roof = roofline(stage_ms, stats, args.steps, fp32_peak, basis, pk.get("hbm_gbs", 6800.0), n)
+    roof["hbm_peak_basis"] = f"hbm_gbs of MEASURED_PEAKS.json ({pk_kind})"
+    hold = clock_hold(native, ctx, s, p, d_dt, local) if rank == 0 else None
+    clk["after_region"] = hold
 
     e2e = run_e2e(native, ctx, s, p, n, args, stream) if rank == 0 and not args.skip_e2e else None
     native.sph_destroy(ctx)
     del s
     batched = run_batched(args) if rank == 0 and args.batch_instances > 0 else None
     adjoint = run_adjoint(args) if rank == 0 and args.adjoint_side > 0 else None
-    plummer = run_plummer(args) if rank == 0 and args.plummer_log2 > 0 else None
+    plummer = (run_plummer(args, fp32_peak, basis, pk.get("hbm_gbs", 6800.0))
+               if rank == 0 and args.plummer_log2 > 0 else None)
     out = None
     if rank == 0:
         cpu = run_cpu_baseline(w, args.cpu_seconds) if args.cpu_seconds > 0 else None
@@ -303,6 +355,31 @@ def run_ours(args):
         }
     if ws > 1:
         torch.distributed.destroy_process_group()
+    return out
+
+
+def clock_hold(native, ctx, s, p, d_dt, device_index, seconds=0.6):
+    """SM clocks while the same step runs back to back for `seconds` right
+    after the timed region (the timed region itself holds few samples).  The
+    state and dt are restored afterwards, so later legs see the timed state."""
+    import torch
+    saved = {f: getattr(s, f).clone() for f in s.FIELDS4 + s.FIELDS1 + ("perm", "keys")}
+    dt0 = d_dt.clone()
+    c = ClockSampler(device_index, interval_ms=10)
+    c.start()
+    t0 = time.perf_counter()
+    k = 0
+    while time.perf_counter() - t0 < seconds:
+        for _ in range(20):
+            native.sph_step(ctx, s.c, p, d_dt)
+        torch.cuda.synchronize()
+        k += 20
+    out = c.stop()
+    out["steps"] = k
+    for f, v in saved.items():
+        getattr(s, f).copy_(v)
+    d_dt.copy_(dt0)
+    torch.cuda.synchronize()
     return out
 
 
@@ -403,10 +480,11 @@ def run_adjoint(args):
             "grad_norm_u": float(torch.linalg.vector_norm(g[:, 3])), "dL_dalpha": ga}
 
 
-def run_plummer(args):
+def run_plummer(args, fp32_peak, basis, hbm_peak):
     """Strongly inhomogeneous evaluation: 2^24-particle Plummer sphere,
-    tree build + density + force of one evaluation, N_group and N_leaf tuned
-    on the state."""
+    tree build + density + force of one evaluation, tree sizes and launch
+    shape tuned on the state; roofline of its stages and the oracle timed on
+    a sample of the same workload."""
     import torch
     from paper_1909_07439_gb300 import DeviceState, inputs, native
     from paper_1909_07439_gb300 import autotune
@@ -440,7 +518,10 @@ def run_plummer(args):
     stats = native.sph_get_stats(ctx)
     native.sph_destroy(ctx)
     hh = s.numpy("h")
+    roof = roofline(stage, stats, reps, fp32_peak, basis, hbm_peak, w.n)
+    cpu = run_cpu_baseline(w, args.cpu_seconds) if args.cpu_seconds > 0 else None
     return {"workload": f"Plummer sphere a = 0.1 truncated at r = 1, {w.n} particles",
+            "roofline": roof, "cpu_baseline": cpu,
             "ms_per_evaluation": ms, "value": w.n / (ms / 1e3), "unit": UNIT,
             "pair_interactions_per_s": (stats["density_pairs"] + stats["force_pairs"]) / reps / (ms / 1e3),
             "stage_ms": {k: v / reps for k, v in stage.items()},
@@ -537,7 +618,11 @@ def run_reference(args):
     value = total_k / total_t
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * w.n / value, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 * total_t / args.steps,
+            "ms_per_step_basis": "measured wall time of one sample step (a bounded sample of "
+                                 "target particles, not the whole workload)",
+            "extrapolated_ms_per_full_step": 1e3 * w.n / value,
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded Sedov lattice)",
             "config": {"workload": f"sedov_blast_lattice_{args.side}^3", "n_particles": w.n},
             "cpu_baseline": {"kind": "oracle", "cores": os.cpu_count(), "value": value,
