@@ -1,0 +1,115 @@
+"""Domain decomposition of one problem over CPU ranks (gloo, world size 2):
+equal-count Morton ranges, halo selection and the halo refresh after the
+density pass (paper_1909_07439_gb300.partition), checked against the
+oracle: every force-set neighbour of an owned particle is owned or in the
+halo, and the oracle evaluated on each rank's owned + halo particles gives
+the single-rank oracle's values for the owned particles."""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+import oracle  # noqa: E402
+from paper_1909_07439_gb300 import inputs, partition  # noqa: E402
+
+
+def test_host_keys_equal_the_oracle_keys():
+    # the partition's host keys use the tree build's quantisation; with the
+    # global box of all particles they are the oracle's keys bit for bit
+    for w in (inputs.unit_sphere(5000, seed=3), inputs.plummer(4000, seed=2)):
+        x = w.pos[:, :3]
+        lo = x.min(0).astype(np.float32)
+        size = np.float32(np.max((x.max(0) - x.min(0)).astype(np.float32)))
+        assert np.array_equal(partition.morton_keys(w.pos, lo, size), oracle.morton_keys(w.pos))
+
+
+def test_box_distance():
+    lo, hi = np.zeros(3), np.ones(3)
+    x = np.array([[0.5, 0.5, 0.5], [2.0, 0.5, 0.5], [2.0, 3.0, 0.5], [-1.0, -1.0, -1.0]])
+    assert np.allclose(partition.box_distance(x, lo, hi), [0.0, 1.0, np.sqrt(5.0), np.sqrt(3.0)])
+
+
+def _case():
+    w = inputs.unit_sphere(3000, seed=21, sigma_v=0.2)
+    rng = np.random.default_rng(5)
+    w.vel[:, 3] *= rng.uniform(0.5, 2.0, w.n).astype(np.float32)
+    return w
+
+
+def _f64(a):
+    return np.asarray(a, np.float64)
+
+
+def _worker(rank, ws, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        w = _case()
+        gid = np.arange(w.n)
+        mine = gid % ws == rank                       # an arbitrary initial split
+        dom = partition.decompose(w.pos[mine], w.vel[mine], w.h[mine], gid[mine], pad=0.03)
+        n_own = dom.n_own
+        rounds = 0
+        while True:                                   # density, halo refresh, re-exchange rule
+            rounds += 1
+            x, v, m = _f64(dom.pos[:, :3]), _f64(dom.vel[:, :3]), _f64(dom.pos[:, 3])
+            h_start = dom.h.astype(np.float64)
+            d = oracle.density(x, v, m, h_start, targets=np.arange(n_own))
+            assert d.failures == 0
+            halo, outgrew = partition.refresh_halo(
+                dom, {"h": d.h, "rho": d.rho, "omega": d.omega}, h_start)
+            if not outgrew:
+                break
+            own = slice(0, n_own)
+            dom = partition.attach_halo(dom.pos[own], dom.vel[own], d.h.astype(np.float32),
+                                        dom.gid[own], dom.keys, pad=dom.pad)
+            assert rounds < 6
+        h = np.concatenate([d.h, halo["h"]])
+        rho = np.concatenate([d.rho, halo["rho"]])
+        om = np.concatenate([d.omega, halo["omega"]])
+        u = _f64(dom.vel[:, 3])
+        f = oracle.force(x, v, m, u, h, rho, om, targets=np.arange(n_own))
+        out[rank] = dict(gid=dom.gid[:n_own].copy(), halo=dom.gid[n_own:].copy(),
+                         keys=dom.keys.copy(), h=d.h, rho=d.rho, acc=f.acc, dudt=f.dudt,
+                         vsig=f.vsigmax, rounds=rounds)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("ws", [2, 3])
+def test_decomposition_matches_single_rank_oracle(ws):
+    oracle.build()
+    port = 29600 + 10 * ws + os.getpid() % 500
+    mgr = mp.Manager()
+    out = mgr.dict()
+    mp.spawn(_worker, args=(ws, port, out), nprocs=ws, join=True)
+    w = _case()
+    x, v, m, u = _f64(w.pos[:, :3]), _f64(w.vel[:, :3]), _f64(w.pos[:, 3]), _f64(w.vel[:, 3])
+    d = oracle.density(x, v, m, w.h)
+    f = oracle.force(x, v, m, u, d.h, d.rho, d.omega)
+    off, idx = oracle.neighbours(w.pos, d.h.astype(np.float32), 1)
+    rs = [out[r] for r in range(ws)]
+    # equal-count contiguous ranges of the global (key, id) order, in rank order
+    sizes = [len(r["gid"]) for r in rs]
+    assert max(sizes) - min(sizes) <= 1
+    assert sorted(np.concatenate([r["gid"] for r in rs])) == list(range(w.n))
+    for a, b in zip(rs[:-1], rs[1:]):
+        assert (int(a["keys"][-1]), int(a["gid"][-1])) < (int(b["keys"][0]), int(b["gid"][0]))
+    for r in rs:
+        assert np.all(np.diff(r["keys"].astype(np.float64)) >= 0)
+        have = set(r["gid"].tolist()) | set(r["halo"].tolist())
+        for g in r["gid"]:
+            assert set(idx[off[g]:off[g + 1]].tolist()) <= have, g
+        g = r["gid"]
+        assert np.max(np.abs(r["h"] / d.h[g] - 1)) < 1e-12
+        assert np.max(np.abs(r["rho"] / d.rho[g] - 1)) < 1e-12
+        assert np.max(np.abs(r["acc"] - f.acc[g])) <= 1e-12 * np.max(np.abs(f.acc))
+        assert np.max(np.abs(r["dudt"] - f.dudt[g])) <= 1e-12 * np.max(np.abs(f.dudt))
+        assert np.max(np.abs(r["vsig"] / f.vsigmax[g] - 1)) < 1e-12
+    # the starting h (the uniform-density guess) moves past the 3 % pad at the
+    # sphere's edge, so the halo had to be selected again at least once
+    assert max(r["rounds"] for r in rs) >= 2
