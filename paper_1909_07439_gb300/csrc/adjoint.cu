@@ -8,10 +8,10 @@
 // its own equations and from its neighbours' equations.  No atomics, so the
 // results are deterministic.
 //
-// Force backward: the pair term T_ij (the contribution of j to a_i and du_i)
-// is written once as a template over the scalar type; forward-mode dual
-// numbers give its derivatives with respect to one particle's inputs
-// (x, v, u, h, rho, Omega) and alpha_AV, in passes of 4 derivative slots.
+// Force backward: the vector-Jacobian product of the pair term T_ij (the
+// contribution of j to a_i and du_i/dt, Eqs. 9-15 as the force pass computes
+// them) is a hand-written reverse sweep (force_pair_vjp), one sweep per pair
+// and side, in FP32 only (this GPU's FP64 rate is a small fraction of FP32's).
 //
 // Density backward (implicit-function theorem): h_i solves
 // g_i = sum_j m_j W(r_ij, h_i) - M_i / h_i^3 = 0, M_i = m_i hfact^3, with
@@ -22,165 +22,15 @@
 
 namespace sph {
 
-// ------------------------------------------------------------ dual numbers
-template <int N>
-struct Dual {
-    float v;
-    float d[N];
-    __device__ __forceinline__ Dual() {}
-    __device__ __forceinline__ Dual(float x) : v(x)
-    {
-#pragma unroll
-        for (int k = 0; k < N; ++k) d[k] = 0.f;
-    }
-};
-
-template <int N>
-__device__ __forceinline__ Dual<N> operator+(const Dual<N> &a, const Dual<N> &b)
-{
-    Dual<N> r;
-    r.v = a.v + b.v;
-#pragma unroll
-    for (int k = 0; k < N; ++k) r.d[k] = a.d[k] + b.d[k];
-    return r;
-}
-template <int N>
-__device__ __forceinline__ Dual<N> operator-(const Dual<N> &a, const Dual<N> &b)
-{
-    Dual<N> r;
-    r.v = a.v - b.v;
-#pragma unroll
-    for (int k = 0; k < N; ++k) r.d[k] = a.d[k] - b.d[k];
-    return r;
-}
-template <int N>
-__device__ __forceinline__ Dual<N> operator*(const Dual<N> &a, const Dual<N> &b)
-{
-    Dual<N> r;
-    r.v = a.v * b.v;
-#pragma unroll
-    for (int k = 0; k < N; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
-    return r;
-}
-template <int N>
-__device__ __forceinline__ Dual<N> operator/(const Dual<N> &a, const Dual<N> &b)
-{
-    Dual<N> r;
-    float inv = 1.f / b.v;
-    r.v = a.v * inv;
-#pragma unroll
-    for (int k = 0; k < N; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) * inv;
-    return r;
-}
-template <int N>
-__device__ __forceinline__ Dual<N> operator*(float s, const Dual<N> &a)
-{
-    Dual<N> r;
-    r.v = s * a.v;
-#pragma unroll
-    for (int k = 0; k < N; ++k) r.d[k] = s * a.d[k];
-    return r;
-}
-template <int N>
-__device__ __forceinline__ Dual<N> operator-(const Dual<N> &a)
-{
-    return (-1.f) * a;
-}
-template <int N>
-__device__ __forceinline__ Dual<N> dsqrt(const Dual<N> &a)
-{
-    Dual<N> r;
-    r.v = sqrtf(a.v);
-    // sqrt at 0: zero derivative (the only places this happens are the
-    // conduction speed of two particles at equal pressure, times u_i - u_j)
-    float g = r.v > 0.f ? 0.5f / r.v : 0.f;
-#pragma unroll
-    for (int k = 0; k < N; ++k) r.d[k] = g * a.d[k];
-    return r;
-}
-template <int N>
-__device__ __forceinline__ Dual<N> dabs(const Dual<N> &a)
-{
-    return a.v < 0.f ? -a : a;
-}
-
-__device__ __forceinline__ float dsqrt(float a) { return sqrtf(a); }
-__device__ __forceinline__ float dabs(float a) { return fabsf(a); }
-__device__ __forceinline__ float val(float a) { return a; }
-template <int N>
-__device__ __forceinline__ float val(const Dual<N> &a) { return a.v; }
-
-// (gamma-1)(rho_i u_i - rho_j u_j): the value in FP64, because the two
-// pressures are often nearly equal and the conduction speed's derivative
-// carries 1 / sqrt(|P_i - P_j|)
-__device__ __forceinline__ float pdiff(float gm1, float ri, float ui, float rj, float uj)
-{
-    return (float)((double)gm1 * ((double)ri * (double)ui - (double)rj * (double)uj));
-}
-template <int N>
-__device__ __forceinline__ Dual<N> pdiff(float gm1, const Dual<N> &ri, const Dual<N> &ui,
-                                         const Dual<N> &rj, const Dual<N> &uj)
-{
-    Dual<N> r;
-    r.v = pdiff(gm1, ri.v, ui.v, rj.v, uj.v);
-#pragma unroll
-    for (int k = 0; k < N; ++k)
-        r.d[k] = gm1 * (ri.d[k] * ui.v + ri.v * ui.d[k] - rj.d[k] * uj.v - rj.v * uj.d[k]);
-    return r;
-}
-
 // M4 f'(q), piecewise on the value of q
-template <class S>
-__device__ __forceinline__ S m4_dfq(const S &q)
+__device__ __forceinline__ float m4_dfq(float q)
 {
-    if (val(q) < 1.f) return q * (S(-3.f) + 2.25f * q);
-    if (val(q) < 2.f) {
-        S t = S(2.f) - q;
-        return (-0.75f) * (t * t);
+    if (q < 1.f) return q * (-3.f + 2.25f * q);
+    if (q < 2.f) {
+        const float t = 2.f - q;
+        return -0.75f * (t * t);
     }
-    return S(0.f);
-}
-
-// Contribution of neighbour j to a_i (xyz) and du_i/dt (Eqs. 9-15), the same
-// arithmetic as the force pass.
-template <class S>
-__device__ __forceinline__ void force_pair(const S xi[3], const S vi[3], const S &ui, const S &hi,
-                                           const S &rhoi, const S &omi, const S xj[3],
-                                           const S vj[3], const S &uj, const S &hj,
-                                           const S &rhoj, const S &omj, float mj, const S &alpha,
-                                           float beta, float alpha_u, float gamma, S out[4])
-{
-    const float gm1 = gamma - 1.f;
-    S dx = xi[0] - xj[0], dy = xi[1] - xj[1], dz = xi[2] - xj[2];
-    S r = dsqrt(dx * dx + dy * dy + dz * dz);
-    if (!(val(r) > 0.f)) {
-        out[0] = out[1] = out[2] = out[3] = S(0.f);
-        return;
-    }
-    S rinv = S(1.f) / r;
-    S h2i = hi * hi, h2j = hj * hj;
-    S Fi = (kCNorm * m4_dfq(r / hi)) / (h2i * h2i);
-    S Fj = (kCNorm * m4_dfq(r / hj)) / (h2j * h2j);
-    S vr = ((vi[0] - vj[0]) * dx + (vi[1] - vj[1]) * dy + (vi[2] - vj[2]) * dz) * rinv;
-    S avr = dabs(vr);
-    S ci = dsqrt(gamma * gm1 * ui), cj = dsqrt(gamma * gm1 * uj);
-    S vsi = alpha * ci + beta * avr;
-    S avi(0.f), avj(0.f), duav(0.f);
-    if (val(vr) < 0.f) {
-        S vsj = alpha * cj + beta * avr;
-        avi = (-0.5f) * (vsi * vr);
-        avj = (-0.5f) * (vsj * vr);
-        duav = 0.5f * (vsi * vr * vr * Fi);
-    }
-    S Ai = S(1.f) / (rhoi * omi), Aj = S(1.f) / (rhoj * omj);
-    S coef = mj * (Ai * (gm1 * ui + avi) * Fi + Aj * (gm1 * uj + avj) * Fj);
-    S cr = coef * rinv;
-    out[0] = -(cr * dx);
-    out[1] = -(cr * dy);
-    out[2] = -(cr * dz);
-    S vsu = dsqrt(dabs(pdiff(gm1, rhoi, ui, rhoj, uj)) / (0.5f * (rhoi + rhoj)));
-    out[3] = mj * (gm1 * (ui * Ai * vr * Fi) - Ai * duav +
-                   0.5f * alpha_u * (vsu * (ui - uj) * (Fi * Ai + Fj * Aj)));
+    return 0.f;
 }
 
 // ------------------------------------------------------- generic pair walk
@@ -326,6 +176,203 @@ __global__ void __launch_bounds__(128) pairwalk_kernel(PairWalkArgs a, Op op)
 }
 
 // ------------------------------------------------------------ force backward
+// Inputs of one particle in a pair term.
+struct PairIn {
+    float x[3], v[3], u, h, rho, om;
+};
+
+// M4 f''(q) on the same pieces as m4_dfq
+__device__ __forceinline__ float m4_d2fq(float q)
+{
+    if (q < 1.f) return -3.f + 4.5f * q;
+    if (q < 2.f) return 1.5f * (2.f - q);
+    return 0.f;
+}
+
+// P_i - P_j = (gamma - 1)(rho_i u_i - rho_j u_j) without FP64 (whose rate is
+// a small fraction of FP32's on this GPU): each product's rounding error is
+// recovered exactly with an FMA, and when the pressures are close the
+// difference of the rounded products is exact (Sterbenz), so the difference
+// keeps about twice FP32's precision.  The conduction speed's derivative
+// carries 1 / sqrt(|P_i - P_j|), so the difference must not be swamped by
+// the rounding of the two pressures.
+__device__ __forceinline__ float pressure_diff(float gm1, float ri, float ui, float rj, float uj)
+{
+    const float a = ri * ui, b = rj * uj;
+    const float ea = fmaf(ri, ui, -a), eb = fmaf(rj, uj, -b);
+    return gm1 * ((a - b) + (ea - eb));
+}
+
+// sqrt(x) for x >= 0 through the hardware reciprocal square root (0 at 0)
+__device__ __forceinline__ float fast_sqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+
+// Reverse-mode derivative of the pair term T_ij (particle I in the role of
+// i, J in the role of j, the same operations as the force pass): given the
+// cotangent w of (a_i xyz, du_i/dt), adds w . dT_ij / d(inputs of I) to g
+// and w . dT_ij / d alpha to *galpha (WANT_I), or w . dT_ij / d(inputs of J)
+// to g (otherwise).  r = 0 gives no term, the viscous terms act for vr < 0
+// only, |x| has derivative +1 at 0, and sqrt has derivative 0 at 0 (at equal
+// pressures the conduction term carries u_i - u_j times a zero speed).
+// Quotients and roots use the hardware approximations (a few ulp).
+template <bool WANT_I>
+__device__ __forceinline__ void force_pair_vjp(const PairIn &I, const PairIn &J, float mj, float alpha,
+                                               float beta, float alpha_u, float gamma, float4 w,
+                                               PairIn &g, float &galpha)
+{
+    const float gm1 = gamma - 1.f;
+    const float dx = I.x[0] - J.x[0], dy = I.x[1] - J.x[1], dz = I.x[2] - J.x[2];
+    const float r2 = dx * dx + dy * dy + dz * dz;
+    if (!(r2 > 0.f)) return;
+    const float rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    // ---- forward values
+    const float hiinv = __fdividef(1.f, I.h), hjinv = __fdividef(1.f, J.h);
+    const float qi = r * hiinv, qj = r * hjinv;
+    const float dfi = m4_dfq(qi), dfj = m4_dfq(qj);
+    const float h2i = hiinv * hiinv, h2j = hjinv * hjinv;
+    const float Ki = kCNorm * h2i * h2i, Kj = kCNorm * h2j * h2j;  // C / h^4
+    const float Fi = dfi * Ki, Fj = dfj * Kj;
+    const float dvx = I.v[0] - J.v[0], dvy = I.v[1] - J.v[1], dvz = I.v[2] - J.v[2];
+    const float sd = dvx * dx + dvy * dy + dvz * dz;
+    const float vr = sd * rinv;
+    const float avr = fabsf(vr);
+    const float ci = fast_sqrt(gamma * gm1 * I.u), cj = fast_sqrt(gamma * gm1 * J.u);
+    const float vsi = alpha * ci + beta * avr;
+    const bool visc = vr < 0.f;
+    const float vsj = alpha * cj + beta * avr;
+    const float avi = visc ? -0.5f * (vsi * vr) : 0.f;
+    const float avj = visc ? -0.5f * (vsj * vr) : 0.f;
+    const float duav = visc ? 0.5f * (vsi * vr * vr * Fi) : 0.f;
+    const float rhoinv_i = __fdividef(1.f, I.rho), rhoinv_j = __fdividef(1.f, J.rho);
+    const float Ai = rhoinv_i * __fdividef(1.f, I.om), Aj = rhoinv_j * __fdividef(1.f, J.om);
+    const float pi_ = gm1 * I.u + avi, pj_ = gm1 * J.u + avj;
+    const float Ti = Ai * pi_ * Fi, Tj = Aj * pj_ * Fj;
+    const float coef = mj * (Ti + Tj);
+    const float PD = pressure_diff(gm1, I.rho, I.u, J.rho, J.u);
+    const float APD = fabsf(PD);
+    const float Sinv = __fdividef(2.f, I.rho + J.rho);   // 1 / (rho_i + rho_j) / 2
+    const float X = APD * Sinv;
+    const float vsu = fast_sqrt(X);
+    const float du = I.u - J.u;
+    const float AF = Fi * Ai + Fj * Aj;
+    // ---- reverse sweep
+    float bui = 0.f, bhi = 0.f, brhoi = 0.f, bomi = 0.f;
+    float buj = 0.f, bhj = 0.f, brhoj = 0.f, bomj = 0.f;
+    float bal = 0.f;
+    // out_a = -coef rinv d
+    const float Wd = w.x * dx + w.y * dy + w.z * dz;
+    const float bcr = -Wd;
+    const float cri = -coef * rinv;
+    float bdx = cri * w.x, bdy = cri * w.y, bdz = cri * w.z;
+    float brinv = bcr * coef;
+    const float bcoef = bcr * rinv;
+    // out_u = mj E, E = gm1 u_i A_i vr F_i - A_i duav + 0.5 alpha_u vsu (u_i - u_j) AF
+    const float bE = w.w * mj;
+    const float hau = 0.5f * alpha_u * bE;
+    bui += bE * gm1 * Ai * vr * Fi + hau * vsu * AF;
+    buj += -hau * vsu * AF;
+    float bAi = bE * (gm1 * I.u * vr * Fi - duav);
+    float bvr = bE * gm1 * I.u * Ai * Fi;
+    float bFi = bE * gm1 * I.u * Ai * vr;
+    const float bduav = -bE * Ai;
+    const float bvsu = hau * du * AF;
+    const float bAF = hau * vsu * du;
+    // AF = F_i A_i + F_j A_j
+    bFi += bAF * Ai;
+    bAi += bAF * Fi;
+    float bFj = bAF * Aj;
+    float bAj = bAF * Fj;
+    // vsu = sqrt(|PD| / Srho), Srho = (rho_i + rho_j) / 2
+    const float bX = vsu > 0.f ? __fdividef(0.5f * bvsu, vsu) : 0.f;
+    const float bAPD = bX * Sinv;
+    const float bSrho = -bX * X * Sinv;
+    const float bPD = PD < 0.f ? -bAPD : bAPD;
+    brhoi += bPD * gm1 * I.u + 0.5f * bSrho;
+    bui += bPD * gm1 * I.rho;
+    brhoj += -bPD * gm1 * J.u + 0.5f * bSrho;
+    buj += -bPD * gm1 * J.rho;
+    // coef = mj (T_i + T_j), T = A p F
+    const float bT = bcoef * mj;
+    bAi += bT * pi_ * Fi;
+    bFi += bT * Ai * pi_;
+    const float bpi = bT * Ai * Fi;
+    bAj += bT * pj_ * Fj;
+    bFj += bT * Aj * pj_;
+    const float bpj = bT * Aj * Fj;
+    bui += bpi * gm1;
+    buj += bpj * gm1;
+    float bavr = 0.f, bci = 0.f, bcj = 0.f;
+    if (visc) {
+        // avi = -vsi vr / 2, avj = -vsj vr / 2, duav = vsi vr^2 F_i / 2
+        const float bvsi = bpi * (-0.5f * vr) + bduav * 0.5f * vr * vr * Fi;
+        const float bvsj = bpj * (-0.5f * vr);
+        bvr += bpi * (-0.5f * vsi) + bpj * (-0.5f * vsj) + bduav * vsi * vr * Fi;
+        bFi += bduav * 0.5f * vsi * vr * vr;
+        bal += bvsi * ci + bvsj * cj;
+        bci += bvsi * alpha;
+        bcj += bvsj * alpha;
+        bavr += (bvsi + bvsj) * beta;
+    }
+    // A = 1 / (rho Omega)
+    brhoi += -bAi * Ai * rhoinv_i;
+    bomi += -bAi * Ai * __fdividef(1.f, I.om);
+    brhoj += -bAj * Aj * rhoinv_j;
+    bomj += -bAj * Aj * __fdividef(1.f, J.om);
+    // c = sqrt(gamma gm1 u)
+    bui += ci > 0.f ? __fdividef(bci * gamma * gm1 * 0.5f, ci) : 0.f;
+    buj += cj > 0.f ? __fdividef(bcj * gamma * gm1 * 0.5f, cj) : 0.f;
+    // avr = |vr| (derivative +1 at 0)
+    bvr += vr < 0.f ? -bavr : bavr;
+    // vr = sd rinv
+    const float bsd = bvr * rinv;
+    brinv += bvr * sd;
+    bdx += bsd * dvx;
+    bdy += bsd * dvy;
+    bdz += bsd * dvz;
+    // F = C f'(q) / h^4, q = r / h
+    float br = 0.f;
+    {
+        const float bq = bFi * Ki * m4_d2fq(qi);
+        bhi += -4.f * bFi * Fi * hiinv - bq * qi * hiinv;
+        br += bq * hiinv;
+    }
+    {
+        const float bq = bFj * Kj * m4_d2fq(qj);
+        bhj += -4.f * bFj * Fj * hjinv - bq * qj * hjinv;
+        br += bq * hjinv;
+    }
+    // rinv = 1 / r, r = |d|
+    br += -brinv * rinv * rinv;
+    bdx += br * rinv * dx;
+    bdy += br * rinv * dy;
+    bdz += br * rinv * dz;
+    if (WANT_I) {
+        g.x[0] += bdx;
+        g.x[1] += bdy;
+        g.x[2] += bdz;
+        g.v[0] += bsd * dx;
+        g.v[1] += bsd * dy;
+        g.v[2] += bsd * dz;
+        g.u += bui;
+        g.h += bhi;
+        g.rho += brhoi;
+        g.om += bomi;
+        galpha += bal;
+    } else {
+        // d = x_i - x_j, dv = v_i - v_j
+        g.x[0] -= bdx;
+        g.x[1] -= bdy;
+        g.x[2] -= bdz;
+        g.v[0] -= bsd * dx;
+        g.v[1] -= bsd * dy;
+        g.v[2] -= bsd * dz;
+        g.u += buj;
+        g.h += bhj;
+        g.rho += brhoj;
+        g.om += bomj;
+    }
+}
+
 struct ForceBwdOp {
     const float4 *pos, *vel, *gacc;  // gacc: (dL/da xyz, dL/d(du/dt))
     const float *h, *rho, *omega;
@@ -334,74 +381,57 @@ struct ForceBwdOp {
     double *galpha;                  // out: accumulated (one atomic per target)
     float alpha, beta, alpha_u, gamma;
     struct Acc {
-        float g[10];  // x0 x1 x2 v0 v1 v2 u h rho om
+        PairIn K;     // the target's own inputs, loaded once
+        float mk;
+        float4 wk;    // the target's cotangent
+        PairIn g;
         float ga;
     };
-    __device__ void init(int, Acc &c) const
+    __device__ PairIn load(int k) const
     {
-#pragma unroll
-        for (int k = 0; k < 10; ++k) c.g[k] = 0.f;
+        const float4 p = pos[k], v = vel[k];
+        return PairIn{{p.x, p.y, p.z}, {v.x, v.y, v.z}, v.w, h[k], rho[k], omega[k]};
+    }
+    __device__ void init(int k, Acc &c) const
+    {
+        c.K = load(k);
+        c.mk = pos[k].w;
+        c.wk = gacc[k];
+        c.g = PairIn{{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, 0.f, 0.f, 0.f, 0.f};
         c.ga = 0.f;
     }
-    // side: 0 -> derivatives of T_kj w.r.t. k's inputs (k = "i" of the pair);
-    //       1 -> derivatives of T_jk w.r.t. k's inputs (k = "j" of the pair)
-    template <int P>
-    __device__ void pass(int k, int j, int side, Acc &c) const
-    {
-        typedef Dual<4> D;
-        const int base = 4 * P;  // input slots base .. base+3 of (x0..om, alpha)
-        float4 pk = pos[k], vk = vel[k], pj = pos[j], vj = vel[j];
-        float fk[11] = {pk.x, pk.y, pk.z, vk.x, vk.y, vk.z, vk.w, h[k], rho[k], omega[k], alpha};
-        float fj[10] = {pj.x, pj.y, pj.z, vj.x, vj.y, vj.z, vj.w, h[j], rho[j], omega[j]};
-        D dk[11], dj[10];
-#pragma unroll
-        for (int s = 0; s < 11; ++s) {
-            dk[s] = D(fk[s]);
-            if (s >= base && s < base + 4 && (s < 10 || side == 0)) dk[s].d[s - base] = 1.f;
-        }
-#pragma unroll
-        for (int s = 0; s < 10; ++s) dj[s] = D(fj[s]);
-        D out[4];
-        const D al = dk[10];
-        if (side == 0)
-            force_pair(dk, dk + 3, dk[6], dk[7], dk[8], dk[9], dj, dj + 3, dj[6], dj[7], dj[8], dj[9],
-                       pj.w, al, beta, alpha_u, gamma, out);
-        else
-            force_pair(dj, dj + 3, dj[6], dj[7], dj[8], dj[9], dk, dk + 3, dk[6], dk[7], dk[8], dk[9],
-                       pk.w, D(alpha), beta, alpha_u, gamma, out);
-        const float4 w = gacc[side == 0 ? k : j];
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            float v = w.x * out[0].d[s] + w.y * out[1].d[s] + w.z * out[2].d[s] + w.w * out[3].d[s];
-            int slot = base + s;
-            if (slot < 10) c.g[slot] += v;
-            else if (slot == 10 && side == 0) c.ga += v;
-        }
-    }
+    // the terms that land on k's inputs: from k's own equations (T_kj with
+    // cotangent gacc[k]) and from j's (T_jk with cotangent gacc[j])
     __device__ void pair(int k, int j, Acc &c) const
     {
-        pass<0>(k, j, 0, c);
-        pass<1>(k, j, 0, c);
-        pass<2>(k, j, 0, c);
-        pass<0>(k, j, 1, c);
-        pass<1>(k, j, 1, c);
-        pass<2>(k, j, 1, c);
+        (void)k;
+        const PairIn J = load(j);
+        force_pair_vjp<true>(c.K, J, pos[j].w, alpha, beta, alpha_u, gamma, c.wk, c.g, c.ga);
+        float unused = 0.f;
+        force_pair_vjp<false>(J, c.K, c.mk, alpha, beta, alpha_u, gamma, gacc[j], c.g, unused);
     }
     __device__ void reduce(Acc &c, int L) const
     {
         for (int o = L >> 1; o > 0; o >>= 1) {
 #pragma unroll
-            for (int k = 0; k < 10; ++k) c.g[k] += __shfl_xor_sync(0xffffffffu, c.g[k], o);
+            for (int a = 0; a < 3; ++a) {
+                c.g.x[a] += __shfl_xor_sync(0xffffffffu, c.g.x[a], o);
+                c.g.v[a] += __shfl_xor_sync(0xffffffffu, c.g.v[a], o);
+            }
+            c.g.u += __shfl_xor_sync(0xffffffffu, c.g.u, o);
+            c.g.h += __shfl_xor_sync(0xffffffffu, c.g.h, o);
+            c.g.rho += __shfl_xor_sync(0xffffffffu, c.g.rho, o);
+            c.g.om += __shfl_xor_sync(0xffffffffu, c.g.om, o);
             c.ga += __shfl_xor_sync(0xffffffffu, c.ga, o);
         }
     }
     __device__ void store(int k, Acc &c) const
     {
-        gpos[k] = make_float4(c.g[0], c.g[1], c.g[2], 0.f);
-        gvel[k] = make_float4(c.g[3], c.g[4], c.g[5], c.g[6]);
-        gh[k] = c.g[7];
-        grho[k] = c.g[8];
-        gom[k] = c.g[9];
+        gpos[k] = make_float4(c.g.x[0], c.g.x[1], c.g.x[2], 0.f);
+        gvel[k] = make_float4(c.g.v[0], c.g.v[1], c.g.v[2], c.g.u);
+        gh[k] = c.g.h;
+        grho[k] = c.g.rho;
+        gom[k] = c.g.om;
         atomicAdd(galpha, (double)c.ga);
     }
 };
@@ -438,8 +468,8 @@ struct DensBwd1Op {
     {
         float4 pi = pos[i], pj = pos[j];
         float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
-        float r = sqrtf(dx * dx + dy * dy + dz * dz);
-        float hi = h[i], hinv = 1.f / hi;
+        float r = fast_sqrt(dx * dx + dy * dy + dz * dz);
+        float hi = h[i], hinv = __fdividef(1.f, hi);
         float q = r * hinv, f, df, d2f;
         m4_all(q, f, df, d2f);
         float h4 = hinv * hinv * hinv * hinv;
@@ -475,7 +505,7 @@ struct DensBwd2Op {
     __device__ void init(int, Acc &c) const { c.g[0] = c.g[1] = c.g[2] = 0.f; }
     __device__ static float cterm(float r, float hh, float lam, float w, float m)
     {
-        float hinv = 1.f / hh, q = r * hinv, f, df, d2f;
+        float hinv = __fdividef(1.f, hh), q = r * hinv, f, df, d2f;
         m4_all(q, f, df, d2f);
         float h4 = hinv * hinv * hinv * hinv;
         float F = kCNorm * df * h4;
@@ -486,10 +516,11 @@ struct DensBwd2Op {
     {
         float4 pk = pos[k], pj = pos[j];
         float dx = pk.x - pj.x, dy = pk.y - pj.y, dz = pk.z - pj.z;
-        float r = sqrtf(dx * dx + dy * dy + dz * dz);
-        if (!(r > 0.f)) return;
+        float r2 = dx * dx + dy * dy + dz * dz;
+        if (!(r2 > 0.f)) return;
+        float rinv = rsqrtf(r2), r = r2 * rinv;
         float2 ck = coef[k], cj = coef[j];
-        float s = (cterm(r, h[k], ck.x, ck.y, pj.w) + cterm(r, h[j], cj.x, cj.y, pk.w)) / r;
+        float s = (cterm(r, h[k], ck.x, ck.y, pj.w) + cterm(r, h[j], cj.x, cj.y, pk.w)) * rinv;
         c.g[0] += s * dx;
         c.g[1] += s * dy;
         c.g[2] += s * dz;
@@ -576,7 +607,7 @@ cudaError_t force_bwd(Ctx &c, const sph_state &s, const sph_params &p, const flo
 
 cudaError_t density_bwd(Ctx &c, const sph_state &s, const sph_params &p, const float *gh,
                         const float *grho, const float *gom, float4 *gpos, float2 *coef,
-                        cudaStream_t st)
+                        cudaStream_t st, bool refresh_hmax)
 {
     DensBwd1Op op1;
     op1.pos = (const float4 *)s.pos;
@@ -588,8 +619,9 @@ cudaError_t density_bwd(Ctx &c, const sph_state &s, const sph_params &p, const f
     op1.gom = gom;
     op1.coef = coef;
     op1.hf3 = p.hfact * p.hfact * p.hfact;
-    // pass 2 opens nodes by their h_max (force set): refresh it for the current h
-    cudaError_t e = update_hmax(c, s, p, st);
+    // pass 2 opens nodes by their h_max (force set) where it walks: refresh it
+    // for the current h (unless the caller just did)
+    cudaError_t e = refresh_hmax ? update_hmax(c, s, p, st) : cudaSuccess;
     if (e != cudaSuccess) return e;
     e = launch_pairwalk<96>(c, s, true, op1, st, nullptr);
     if (e != cudaSuccess) return e;

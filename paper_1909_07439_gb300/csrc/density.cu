@@ -26,7 +26,7 @@ namespace sph {
 
 constexpr int kTB = 8;           // targets per batch
 constexpr int kDensWarps = 4;    // warps per block
-constexpr float kPad = 0.03f;    // padded list radius, relative to h
+constexpr float kPad = kListPad; // padded list radius, relative to h
 constexpr int kRound = 2;        // groups per warp per work grab of the list kernel
 
 template <int CAP>
@@ -59,6 +59,7 @@ struct DensArgs {
     int2 *fallback;   // batches handed to the walking kernel
     int *n_fallback;
     int *rec_bad;     // per instance: an h outgrew the pad of the lists
+    int *rec_any;     // set with rec_bad: some instance outgrew its pad
     float h_in_scale; // 1 + pad
     float hfact, tol, gamma;
     int tb;           // targets per batch of the list kernel (4, 8 or 16)
@@ -447,8 +448,10 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_walk_kernel(DensArgs 
             }
             if (act && sub == 0) density_outputs(a, i, h, M, s1, s2, sm.tv[t].w);
             // the neighbour lists hold while no h grew beyond their pad
-            if (__any_sync(0xffffffffu, act && h > a.h_in_scale * h_in) && lane == 0)
+            if (__any_sync(0xffffffffu, act && h > a.h_in_scale * h_in) && lane == 0) {
                 atomicOr(a.rec_bad + root, 1);  // root = this group's instance
+                atomicOr(a.rec_any, 1);
+            }
             __syncwarp();
         }
     }
@@ -690,6 +693,7 @@ cudaError_t density_solve(Ctx &c, const sph_state &s, const sph_params &p, cudaS
     a.fallback = c.fallback;
     a.n_fallback = c.d_sizes + SZ_FALLBACK;
     a.rec_bad = c.tree.rec_bad;
+    a.rec_any = c.tree.rec_ctl;
     a.pos = (const float4 *)s.pos;
     a.vel = (const float4 *)s.vel;
     a.rec = c.rec;

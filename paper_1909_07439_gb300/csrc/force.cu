@@ -586,6 +586,9 @@ cudaError_t force_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStre
     a.alpha_u = p.alpha_u;
     a.err = c.d_err;
     a.counters = c.d_counters;
+    // lists of instances where an h outgrew the pad are rebuilt at the final h
+    e = relist_pass(c, s, p, kListPad, st, batch);
+    if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(a.work, 0, 3 * sizeof(int), st);  // work, fallback count, work2
     if (e != cudaSuccess) return e;
     e = configure_force_list();

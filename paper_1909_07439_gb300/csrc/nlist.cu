@@ -61,6 +61,9 @@ struct NlistArgs {
     float rscale;  // list radius = rscale * max(h_i, h_j)
     int *idx;
     int *len;
+    // relist mode: the kernel returns at once unless *gate != 0, and builds the
+    // lists only of groups whose instance k has only_bad[k] != 0
+    const int *gate, *only_bad;
     int *err;
     unsigned long long *counters;
 };
@@ -205,6 +208,7 @@ __global__ void __launch_bounds__(kNlWarps * 32, 7) nlist_kernel(NlistArgs a)
     const int lane = threadIdx.x & 31;
     const unsigned lt = lane_lt();
     const int ng = a.sizes[SZ_GROUPS];
+    if (a.gate && *a.gate == 0) return;  // relist mode, nothing outgrew its pad
     unsigned long long n_cand = 0, n_entries = 0, n_over = 0;
 
     while (true) {
@@ -234,6 +238,10 @@ __global__ void __launch_bounds__(kNlWarps * 32, 7) nlist_kernel(NlistArgs a)
             const unsigned later = bstart & ~((2u << s) - 1u);  // starts after s
             int e = later ? min(__ffs(later) - 1, sgn) : sgn;
             const int root = __shfl_sync(0xffffffffu, ins, s);
+            if (a.only_bad && a.only_bad[root] == 0) {  // relist mode: this instance's lists hold
+                s = e;
+                continue;
+            }
             // One walk for the groups [s, e) of the run; while its leaves do
             // not fit, the range is halved (a group alone that does not fit
             // gets no lists), so whether a group gets lists depends on the
@@ -326,13 +334,8 @@ cudaError_t configure_nlist_kernels()
     return configure_nlist(b);
 }
 
-cudaError_t nlist_pass(Ctx &c, const sph_state &s, const sph_params &p, float pad, cudaStream_t st,
-                       const Batch *batch)
+static NlistArgs nlist_args(Ctx &c, const sph_state &s, float pad, const Batch *batch)
 {
-    (void)p;
-    int blocks = 1;
-    cudaError_t e = configure_nlist(blocks);
-    if (e != cudaSuccess) return e;
     NlistArgs a{};
     a.pos = (const float4 *)s.pos;
     a.h = s.h;
@@ -348,10 +351,45 @@ cudaError_t nlist_pass(Ctx &c, const sph_state &s, const sph_params &p, float pa
     a.len = c.nl_len;
     a.err = c.d_err;
     a.counters = c.d_counters;
+    return a;
+}
+
+cudaError_t nlist_pass(Ctx &c, const sph_state &s, const sph_params &p, float pad, cudaStream_t st,
+                       const Batch *batch)
+{
+    (void)p;
+    int blocks = 1;
+    cudaError_t e = configure_nlist(blocks);
+    if (e != cudaSuccess) return e;
+    NlistArgs a = nlist_args(c, s, pad, batch);
     e = cudaMemsetAsync(a.work, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     nlist_kernel<<<c.num_sms * blocks, kNlWarps * 32, 0, st>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t relist_pass(Ctx &c, const sph_state &s, const sph_params &p, float pad, cudaStream_t st,
+                        const Batch *batch)
+{
+    int blocks = 1;
+    cudaError_t e = configure_nlist(blocks);
+    if (e != cudaSuccess) return e;
+    int *any = c.tree.rec_ctl;  // rec_ctl[0]: some instance outgrew its pad
+    // node and group h_max of the final h (the list walk's opening test)
+    e = update_hmax(c, s, p, st, any);
+    if (e != cudaSuccess) return e;
+    NlistArgs a = nlist_args(c, s, pad, batch);
+    a.gate = any;
+    a.only_bad = c.tree.rec_bad;
+    e = cudaMemsetAsync(a.work, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    nlist_kernel<<<c.num_sms * blocks, kNlWarps * 32, 0, st>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the rebuilt lists cover the pair sets at the final h
+    e = cudaMemsetAsync(c.tree.rec_bad, 0, sizeof(int) * (batch ? batch->n_inst : 1), st);
+    if (e != cudaSuccess) return e;
+    return cudaMemsetAsync(any, 0, sizeof(int), st);
 }
 
 }  // namespace sph

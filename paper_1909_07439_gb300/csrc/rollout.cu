@@ -27,7 +27,7 @@ cudaError_t force_bwd(Ctx &c, const sph_state &s, const sph_params &p, const flo
                       double *galpha, cudaStream_t st);
 cudaError_t density_bwd(Ctx &c, const sph_state &s, const sph_params &p, const float *gh,
                         const float *grho, const float *gom, float4 *gpos, float2 *coef,
-                        cudaStream_t st);
+                        cudaStream_t st, bool refresh_hmax = true);
 
 static int grid_r(const Ctx &c, int64_t n)
 {
@@ -283,7 +283,7 @@ cudaError_t evaluate(Ctx &c, sph_state &w, const sph_params &p, float *d_dt, cud
 {
     RT(build_tree(c, w, p, true, st));
     RT(density_pass(c, w, p, st));
-    RT(force_prep(c, w, p, st, true));  // the adjoint walks need the final h_max
+    RT(force_prep(c, w, p, st));
     RT(force_pass(c, w, p, st));
     return courant_dt(c, w, p, d_dt, st);
 }
@@ -295,7 +295,7 @@ cudaError_t step(Ctx &c, sph_state &w, const sph_params &p, const float *dt, boo
     RT(kick_drift(c, w, dt, st));
     RT(build_tree(c, w, p, false, st));
     RT(density_pass(c, w, p, st));
-    RT(force_prep(c, w, p, st, true));  // the adjoint walks need the final h_max
+    RT(force_prep(c, w, p, st));
     RT(force_pass(c, w, p, st));
     if (partial) return cudaSuccess;
     RT(kick_close(c, w, dt, nullptr, st));
@@ -355,7 +355,8 @@ cudaError_t rollout(Ctx &c, RolloutBuf &b, const sph_state &init, const sph_para
                          b.d_galpha, st));
             if (k == K - 1)
                 loss_grho_kernel<<<nb, 256, 0, st>>>(w.rho, w.perm, b.flag, n, np, b.grho_s);
-            RT(density_bwd(c, w, p, b.gh_s, b.grho_s, b.gom_s, b.gpos_s, b.coef, st));
+            // force_bwd refreshed node and group h_max for this h
+            RT(density_bwd(c, w, p, b.gh_s, b.grho_s, b.gom_s, b.gpos_s, b.coef, st, false));
             scatter_cot_kernel<<<nb, 256, 0, st>>>(w.perm, b.gpos_s, b.gvel_s, b.dts, k, n, b.gx,
                                                    b.gv, b.ga);
         }

@@ -171,7 +171,8 @@ sph_status do_force(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_
         CK(force_prep(c, s, p, st), "force_prep");
         if (!records_fresh) CK(pack_records(c, s, st), "pack");
     }
-    StageScope sc(c, ST_FORCE, st, 4);
+    // relist (h_max refresh 2, list kernel 1), list kernel, h_max refresh 2, walking fallback
+    StageScope sc(c, ST_FORCE, st, 7);
     CK(force_pass(c, s, p, st), "force");
     return SPH_OK;
 }

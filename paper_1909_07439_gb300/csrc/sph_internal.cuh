@@ -19,6 +19,7 @@ constexpr int kMaxInstances = 65536;  // instances in one batch
 constexpr int kRsSlots = 14;         // radix passes of one sort at most (4 + 8 + 2)
 constexpr int kNbrCap = 128;          // neighbour-list entries per particle
 constexpr float kCNorm = 0.318309886183790671538f;  // M4, 3D: 1/pi
+constexpr float kListPad = 0.03f;    // neighbour-list radius margin, relative to h
 
 // stage ids for the per-stage timers
 enum Stage {
@@ -69,7 +70,8 @@ struct Tree {
     float4 *grp_hi = nullptr;
     // Validity of the neighbour lists built by the density pass:
     // rec_ctl[1] != 0: lists stale (tree rebuilt since the density pass);
-    // rec_bad[k] != 0: an h of instance k (0 without a batch) outgrew its pad.
+    // rec_bad[k] != 0: an h of instance k (0 without a batch) outgrew its pad;
+    // rec_ctl[0] != 0: some rec_bad[k] is set (the relist pass's gate).
     int *rec_ctl = nullptr;
     int *rec_bad = nullptr;
     // chop scratch
@@ -200,6 +202,12 @@ cudaError_t sort_lookback_probe(Ctx &c, int spin_cap, cudaStream_t st);
 // nlist.cu
 cudaError_t nlist_pass(Ctx &c, const sph_state &s, const sph_params &p, float pad,
                        cudaStream_t st, const Batch *batch = nullptr);
+// After the density pass: rebuild, at the final h, the lists of the
+// instances where an h outgrew the list pad (rec_bad), so the force pass and
+// the adjoint passes read lists instead of walking; returns at once (gated
+// launches) when no h outgrew its pad.
+cudaError_t relist_pass(Ctx &c, const sph_state &s, const sph_params &p, float pad,
+                        cudaStream_t st, const Batch *batch = nullptr);
 cudaError_t configure_nlist_kernels();
 // density.cu (density_pass = density_lists + density_solve; density_pass
 // expects the node and group h_max of the current h, as build_tree leaves them)

@@ -204,3 +204,48 @@ def test_rollout_buffers_reused_across_lengths(lib):
     assert loss == loss2
     assert torch.equal(g, g2)
     assert abs(ga - ga2) <= 1e-12 * abs(ga2)
+
+
+def test_single_evaluation_user_loss_matches_fp64_autograd(lib):
+    # a loss of the caller's own making over every differentiable output of one
+    # evaluation (h, rho, Omega, a, du/dt); gradients w.r.t. positions,
+    # velocities, internal energies and alpha_AV against FP64 torch autograd
+    native, ctx = lib
+    from paper_1909_07439_gb300.adjoint import evaluate
+    w = _cloud(1500, seed=11)
+    x, v, m, u = (w.pos[:, :3].astype(np.float64), w.vel[:, :3].astype(np.float64),
+                  w.pos[:, 3].astype(np.float64), w.vel[:, 3].astype(np.float64))
+    d = oracle.density(x, v, m, w.h)
+    h0 = d.h.astype(np.float32) * np.float32(1.01)        # a starting guess near the root
+    rng = np.random.default_rng(12)
+    c = {k: rng.normal(size=sh) for k, sh in (("rho", w.n), ("h", w.n), ("om", w.n),
+                                             ("a", (w.n, 3)), ("du", w.n))}
+
+    def loss(h, rho, om, a, du, lib_):
+        t = lambda k: lib_.tensor(c[k], dtype=h.dtype, device=h.device)
+        return ((t("rho") * rho * rho).sum() + (t("h") * h).sum() * 10.0 + (t("om") * om).sum() +
+                (t("a") * a).sum() * 1e-3 + (t("du") * du).sum() * 1e-3)
+
+    pos = torch.tensor(w.pos, device="cuda", requires_grad=True)
+    velu = torch.tensor(w.vel, device="cuda", requires_grad=True)
+    al = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    p = native.sph_params_default()
+    hg, rg, og, acc = evaluate(ctx, pos, velu, torch.tensor(h0, device="cuda"), al, p)
+    L = loss(hg.double(), rg.double(), og.double(), acc[:, :3].double(), acc[:, 3].double(), torch)
+    L.backward()
+    tx = torch.tensor(x, dtype=T, requires_grad=True)
+    tv = torch.tensor(v, dtype=T, requires_grad=True)
+    tu = torch.tensor(u, dtype=T, requires_grad=True)
+    ta = torch.tensor(1.0, dtype=T, requires_grad=True)
+    tm = torch.tensor(m, dtype=T)
+    i, j = R.pair_list(tx.detach(), torch.tensor(d.h, dtype=T), 1.05)
+    hh, rr, oo = R.density(tx, tm, torch.tensor(h0, dtype=T), i, j, iters=40)
+    ar, dr = R.force(tx, tv, tu, tm, hh, rr, oo, i, j, alpha=ta)
+    Lr = loss(hh, rr, oo, ar, dr, torch)
+    Lr.backward()
+    assert abs(float(L) / float(Lr) - 1) < 1e-4
+    _check("evaluate dL/dx", pos.grad[:, :3].cpu().numpy(), tx.grad.numpy())
+    _check("evaluate dL/dv", velu.grad[:, :3].cpu().numpy(), tv.grad.numpy())
+    _check("evaluate dL/du", velu.grad[:, 3].cpu().numpy(), tu.grad.numpy())
+    assert abs(float(al.grad) / float(ta.grad) - 1) < 1e-3
+    assert torch.all(pos.grad[:, 3] == 0)
