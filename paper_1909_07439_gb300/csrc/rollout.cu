@@ -4,14 +4,19 @@
 // Forward: initial evaluation, then n_steps sph_step-equivalent steps with
 // the Courant dt of each step recorded (the dt sequence is held fixed in the
 // gradient: no derivative through the minimum of Eq. 8).  The state before
-// every ckpt-th step is kept (checkpoint).  Loss L = mean over probe
-// particles (by the caller's index) of rho^2 after the last step.
+// every ckpt-th step is kept (checkpoint); with gradients, the states of the
+// last window after their force passes are kept too.  Loss L = mean over
+// probe particles (by the caller's index) of rho^2 after the last step.
 //
-// Backward, window by window from the last checkpoint: the pre-step states
-// of the window are recomputed from its checkpoint, then each step is rerun
-// up to its force pass (same tree, same neighbour sets: the forward is
-// deterministic) and differentiated: closing kick, force (adjoint kernels),
-// density (implicit-function theorem), opening kick and drift.  Between steps
+// Backward, window by window from the last checkpoint: the window's steps
+// are recomputed from its checkpoint (deterministic: the same trees and
+// neighbour sets; the last window's were kept by the forward) and each
+// step's state after its force pass is kept; then,
+// from the last step of the window down, a step's state is restored, its
+// tree and neighbour lists are rebuilt (the state is in that tree's order, so
+// the sort is the identity) and the step is differentiated: closing kick,
+// force (adjoint kernels), density (implicit-function theorem), opening kick
+// and drift.  Between steps
 // the cotangents live in the caller's particle order; each step gathers them
 // into its own curve order through perm and scatters them back, so the sort
 // permutations need no bookkeeping.  Finally the initial force evaluation is
@@ -128,7 +133,7 @@ __global__ void final_grad_kernel(const uint32_t *perm, const float4 *gv, const 
 // ------------------------------------------------------------ buffers
 struct StateBuf {
     float4 *pos = nullptr, *vel = nullptr, *acc = nullptr;
-    float *h = nullptr;
+    float *h = nullptr, *rho = nullptr, *omega = nullptr;
     uint32_t *perm = nullptr;
 };
 
@@ -138,6 +143,8 @@ static cudaError_t alloc_sb(StateBuf &b, size_t n)
     if (e == cudaSuccess) e = cudaMalloc(&b.vel, n * 16);
     if (e == cudaSuccess) e = cudaMalloc(&b.acc, n * 16);
     if (e == cudaSuccess) e = cudaMalloc(&b.h, n * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&b.rho, n * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&b.omega, n * 4);
     if (e == cudaSuccess) e = cudaMalloc(&b.perm, n * 4);
     return e;
 }
@@ -148,6 +155,8 @@ static void free_sb(StateBuf &b)
     cudaFree(b.vel);
     cudaFree(b.acc);
     cudaFree(b.h);
+    cudaFree(b.rho);
+    cudaFree(b.omega);
     cudaFree(b.perm);
     b = StateBuf{};
 }
@@ -158,6 +167,8 @@ static cudaError_t save(const sph_state &w, StateBuf &b, size_t n, cudaStream_t 
     if (e == cudaSuccess) e = cudaMemcpyAsync(b.vel, w.vel, n * 16, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b.acc, w.acc, n * 16, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b.h, w.h, n * 4, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.rho, w.rho, n * 4, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.omega, w.omega, n * 4, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(b.perm, w.perm, n * 4, cudaMemcpyDeviceToDevice, st);
     return e;
 }
@@ -168,6 +179,8 @@ static cudaError_t restore(sph_state &w, const StateBuf &b, size_t n, cudaStream
     if (e == cudaSuccess) e = cudaMemcpyAsync(w.vel, b.vel, n * 16, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(w.acc, b.acc, n * 16, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(w.h, b.h, n * 4, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(w.rho, b.rho, n * 4, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(w.omega, b.omega, n * 4, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(w.perm, b.perm, n * 4, cudaMemcpyDeviceToDevice, st);
     return e;
 }
@@ -320,13 +333,23 @@ cudaError_t rollout(Ctx &c, RolloutBuf &b, const sph_state &init, const sph_para
     sph_state w = b.w;
     w.n = n;
     const int nb = grid_r(c, n);
-    // ---- forward
+    // ---- forward (with gradients, the last window's states after their
+    // force passes are kept on the way: its backward needs no recompute)
+    const int nwin = (K + ck - 1) / ck;
+    const int k_last = (nwin - 1) * ck;
     RT(load_init(c, w, init, st));
     RT(evaluate(c, w, p, b.d_dt, st));
     for (int k = 0; k < K; ++k) {
         if (k % ck == 0) RT(save(w, b.ckpt[k / ck], n, st));
         RT(cudaMemcpyAsync(b.dts + k, b.d_dt, sizeof(float), cudaMemcpyDeviceToDevice, st));
-        RT(step(c, w, p, b.dts + k, false, b.d_dt, st));
+        if (grad && k >= k_last) {
+            RT(step(c, w, p, b.dts + k, true, nullptr, st));
+            RT(save(w, b.window[k - k_last], n, st));
+            RT(kick_close(c, w, b.dts + k, nullptr, st));
+            RT(courant_dt(c, w, p, b.d_dt, st));
+        } else {
+            RT(step(c, w, p, b.dts + k, false, b.d_dt, st));
+        }
     }
     RT(cudaMemsetAsync(b.flag, 0, n, st));
     probe_flag_kernel<<<grid_r(c, np), 256, 0, st>>>(probes, np, n, b.flag);
@@ -338,18 +361,25 @@ cudaError_t rollout(Ctx &c, RolloutBuf &b, const sph_state &init, const sph_para
     RT(cudaMemsetAsync(b.gv, 0, (size_t)n * 16, st));
     RT(cudaMemsetAsync(b.ga, 0, (size_t)n * 16, st));
     RT(cudaMemsetAsync(b.d_galpha, 0, sizeof(double), st));
-    const int nwin = (K + ck - 1) / ck;
     for (int cw = nwin - 1; cw >= 0; --cw) {
         const int k0 = cw * ck, k1 = std::min(k0 + ck, K);
-        RT(restore(w, b.ckpt[cw], n, st));
-        RT(save(w, b.window[0], n, st));
-        for (int k = k0; k < k1 - 1; ++k) {
-            RT(step(c, w, p, b.dts + k, false, b.d_dt, st));
-            RT(save(w, b.window[k - k0 + 1], n, st));
+        const bool kept = cw == nwin - 1;  // the forward kept this window's states
+        if (!kept) {
+            // recompute the window from its checkpoint, keeping each step's state
+            // after its force pass (what the step's backward differentiates)
+            RT(restore(w, b.ckpt[cw], n, st));
+            for (int k = k0; k < k1; ++k) {
+                RT(step(c, w, p, b.dts + k, true, nullptr, st));
+                RT(save(w, b.window[k - k0], n, st));
+                if (k < k1 - 1) RT(kick_close(c, w, b.dts + k, nullptr, st));
+            }
         }
         for (int k = k1 - 1; k >= k0; --k) {
-            RT(restore(w, b.window[k - k0], n, st));
-            RT(step(c, w, p, b.dts + k, true, nullptr, st));
+            if (k < k1 - 1 || kept) RT(restore(w, b.window[k - k0], n, st));
+            // the step's tree (the state is already in its curve order: the
+            // permutation is the identity) and its neighbour lists at the final h
+            RT(build_tree(c, w, p, true, st));
+            RT(density_lists(c, w, p, st, nullptr, false));
             gather_cot_kernel<<<nb, 256, 0, st>>>(w.perm, b.ga, b.gv, b.dts, k, n, b.gacc_s);
             RT(force_bwd(c, w, p, b.gacc_s, b.gpos_s, b.gvel_s, b.gh_s, b.grho_s, b.gom_s,
                          b.d_galpha, st));
