@@ -56,20 +56,20 @@ def _load():
             lib = ctypes.CDLL(_LIB_PATH)
             P = ctypes.c_void_p
             i64, i32, f64 = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
-            lib.orc_kernel_eval.argtypes = [P, P, i64, P, P, P]
+            lib.orc_kernel_eval.argtypes = [P, P, i64, P, P, P, ctypes.c_int]
             lib.orc_bbox.argtypes = [P, i64, P]
             lib.orc_morton_keys.argtypes = [P, i64, P]
             lib.orc_sort_order.argtypes = [P, i64, P]
             lib.orc_sort_order.restype = ctypes.c_int
             lib.orc_chop.argtypes = [P, i64, i32, P, P, P, P, P, i64]
             lib.orc_chop.restype = i64
-            lib.orc_neighbour_counts.argtypes = [P, P, i64, ctypes.c_int, P, i64, P]
-            lib.orc_neighbour_lists.argtypes = [P, P, i64, ctypes.c_int, P, i64, P, P]
+            lib.orc_neighbour_counts.argtypes = [P, P, i64, ctypes.c_int, P, i64, P, ctypes.c_int]
+            lib.orc_neighbour_lists.argtypes = [P, P, i64, ctypes.c_int, P, i64, P, P, ctypes.c_int]
             lib.orc_density.argtypes = [P, P, P, i64, P, i64, P, f64, f64, i32, i32,
-                                        P, P, P, P, P, P]
+                                        P, P, P, P, P, P, ctypes.c_int]
             lib.orc_density.restype = i64
             lib.orc_force.argtypes = [P, P, P, P, P, P, P, i64, P, i64, f64, f64, f64,
-                                      f64, f64, P, P, P, P]
+                                      f64, f64, P, P, P, P, ctypes.c_int]
             lib.orc_conserved.argtypes = [P, P, P, P, i64, P]
             _lib = lib
     return _lib
@@ -97,14 +97,19 @@ def _targets(targets, n):
 
 
 # --------------------------------------------------------------------------
-# M4 kernel (Sect. 2.3, Eq. 14)
+# Smoothing kernels (Sect. 2.3, Eq. 14): 0 = M4 cubic, 1 = M6 quintic,
+# 2 = Wendland C6; SUPPORT[k] = support radius in units of h
 # --------------------------------------------------------------------------
-def kernel_eval(r, h):
-    """Return (W, F = dW/dr, dW/dh) of the 3D M4 cubic spline at (r, h)."""
+M4, M6, WC6 = 0, 1, 2
+SUPPORT = {M4: 2.0, M6: 3.0, WC6: 2.0}
+
+
+def kernel_eval(r, h, kernel=M4):
+    """Return (W, F = dW/dr, dW/dh) of the 3D kernel at (r, h)."""
     r, h = np.broadcast_arrays(_f64(r), _f64(h))
     r, h = _f64(r.ravel()), _f64(h.ravel())
     w, F, dh = (np.empty_like(r) for _ in range(3))
-    _load().orc_kernel_eval(_ptr(r), _ptr(h), r.size, _ptr(w), _ptr(F), _ptr(dh))
+    _load().orc_kernel_eval(_ptr(r), _ptr(h), r.size, _ptr(w), _ptr(F), _ptr(dh), int(kernel))
     return w, F, dh
 
 
@@ -163,7 +168,7 @@ def chop(sorted_keys, thresh):
 # --------------------------------------------------------------------------
 # Neighbour sets (Sect. 3.2), canonical FP32
 # --------------------------------------------------------------------------
-def neighbours(pos4, h, mode, targets=None):
+def neighbours(pos4, h, mode, targets=None, kernel=M4):
     """CSR (offsets, indices) of the density (mode 0) or force (mode 1) sets."""
     pos4 = _f32(pos4, 4)
     h = _f32(h)
@@ -171,12 +176,13 @@ def neighbours(pos4, h, mode, targets=None):
     t = _targets(targets, n)
     cnt = np.zeros(t.size, np.int64)
     lib = _load()
-    lib.orc_neighbour_counts(_ptr(pos4), _ptr(h), n, int(mode), _ptr(t), t.size, _ptr(cnt))
+    lib.orc_neighbour_counts(_ptr(pos4), _ptr(h), n, int(mode), _ptr(t), t.size, _ptr(cnt),
+                             int(kernel))
     off = np.zeros(t.size + 1, np.int64)
     np.cumsum(cnt, out=off[1:])
     idx = np.zeros(max(1, int(off[-1])), np.int64)
     lib.orc_neighbour_lists(_ptr(pos4), _ptr(h), n, int(mode), _ptr(t), t.size, _ptr(off),
-                            _ptr(idx))
+                            _ptr(idx), int(kernel))
     return off, idx[: off[-1]]
 
 
@@ -194,7 +200,8 @@ class Density:
     failures: int
 
 
-def density(x, v, m, h0, targets=None, hfact=1.2, tol=1e-12, max_iter=200, fixed_iters=0):
+def density(x, v, m, h0, targets=None, hfact=1.2, tol=1e-12, max_iter=200, fixed_iters=0,
+            kernel=M4):
     """Solve the h-rho fixed point for each target (FP64, brute force)."""
     x, v, m, h0 = _f64(x), _f64(v), _f64(m), _f64(h0)
     n = m.size
@@ -206,7 +213,7 @@ def density(x, v, m, h0, targets=None, hfact=1.2, tol=1e-12, max_iter=200, fixed
     fails = _load().orc_density(_ptr(x), _ptr(v), _ptr(m), n, _ptr(t), t.size, _ptr(h0),
                                 float(hfact), float(tol), int(max_iter), int(fixed_iters),
                                 _ptr(h), _ptr(rho), _ptr(om), _ptr(dr), _ptr(nngb),
-                                _ptr(iters))
+                                _ptr(iters), int(kernel))
     return Density(h, rho, om, dr, nngb, iters, int(fails))
 
 
@@ -219,7 +226,7 @@ class Force:
 
 
 def force(x, v, m, u, h, rho, omega, targets=None, gamma=5.0 / 3.0, alpha=1.0, beta=2.0,
-          alpha_u=1.0, vsig_scale=1.0):
+          alpha_u=1.0, vsig_scale=1.0, kernel=M4):
     """Accelerations, du/dt and max signal speed for each target (FP64)."""
     x, v, m, u, h, rho, omega = (_f64(a) for a in (x, v, m, u, h, rho, omega))
     n = m.size
@@ -230,7 +237,7 @@ def force(x, v, m, u, h, rho, omega, targets=None, gamma=5.0 / 3.0, alpha=1.0, b
     _load().orc_force(_ptr(x), _ptr(v), _ptr(m), _ptr(u), _ptr(h), _ptr(rho), _ptr(omega), n,
                       _ptr(t), t.size, float(gamma), float(alpha), float(beta),
                       float(alpha_u), float(vsig_scale), _ptr(acc), _ptr(dudt), _ptr(vsig),
-                      _ptr(nf))
+                      _ptr(nf), int(kernel))
     return Force(acc, dudt, vsig, nf)
 
 
@@ -255,6 +262,7 @@ class Params:
     c_cour: float = 0.3
     tol: float = 1e-12
     max_iter: int = 200
+    kernel: int = M4
 
 
 @dataclass
@@ -274,12 +282,12 @@ class SphState:
 
 def evaluate(s: SphState, p: Params = Params()):
     """Density solve then force pass at the current state (in place)."""
-    d = density(s.x, s.v, s.m, s.h, hfact=p.hfact, tol=p.tol, max_iter=p.max_iter)
+    d = density(s.x, s.v, s.m, s.h, hfact=p.hfact, tol=p.tol, max_iter=p.max_iter, kernel=p.kernel)
     if d.failures:
         raise RuntimeError(f"oracle density: {d.failures} targets did not converge")
     s.h, s.rho, s.omega, s.drhodt = d.h, d.rho, d.omega, d.drhodt
     f = force(s.x, s.v, s.m, s.u, s.h, s.rho, s.omega, gamma=p.gamma, alpha=p.alpha,
-              beta=p.beta, alpha_u=p.alpha_u)
+              beta=p.beta, alpha_u=p.alpha_u, kernel=p.kernel)
     s.acc, s.dudt, s.vsigmax = f.acc, f.dudt, f.vsigmax
     return s
 

@@ -26,43 +26,91 @@
 #define ORC_API __attribute__((visibility("default")))
 
 /* ------------------------------------------------------------------------- */
-/* M4 cubic spline, 3D (Sect. 2.3 and Eq. 14).  q = r/h, support radius 2h,  */
-/* W = C f(q) / h^3 with C = 1/pi so that 4 pi int_0^2 C f(q) q^2 dq = 1.     */
+/* Smoothing kernels, 3D (Sect. 2.3 and Eq. 14): W(r, h) = C f(q) / h^3 with */
+/* q = r/h, zero for q >= R (the support radius in units of h), C such that  */
+/* 4 pi int_0^R C f(q) q^2 dq = 1.  The paper names the kernels and leaves   */
+/* their formulas to the literature; these are the standard forms:          */
+/*   0  M4 cubic spline, R = 2, C = 1/pi:                                    */
+/*        f = 1 - 3/2 q^2 + 3/4 q^3 (q < 1), 1/4 (2 - q)^3 (1 <= q < 2)       */
+/*   1  M6 quintic spline, R = 3, C = 1/(120 pi):                            */
+/*        f = (3-q)^5 - 6 (2-q)^5 + 15 (1-q)^5 (q < 1),                       */
+/*            (3-q)^5 - 6 (2-q)^5 (1 <= q < 2), (3-q)^5 (2 <= q < 3)          */
+/*   2  Wendland C6, R = 2, C = 1365/(512 pi):                               */
+/*        f = (1 - q/2)^8 (4 q^3 + 25/4 q^2 + 4 q + 1) (q < 2)                */
 /* ------------------------------------------------------------------------- */
-static const double C_NORM = 0.318309886183790671537767526745; /* 1/pi */
+static const double PI_D = 3.14159265358979323846264338327950288;
 
-static double m4_f(double q)
+static double kern_support(int kernel) { return kernel == 1 ? 3.0 : 2.0; }
+
+static double kern_norm(int kernel)
 {
+    if (kernel == 1) return 1.0 / (120.0 * PI_D);
+    if (kernel == 2) return 1365.0 / (512.0 * PI_D);
+    return 1.0 / PI_D;
+}
+
+static double shape_f(int kernel, double q)
+{
+    if (kernel == 1) {
+        double a = 3.0 - q, b = 2.0 - q, c = 1.0 - q;
+        if (q < 1.0) return a * a * a * a * a - 6.0 * b * b * b * b * b + 15.0 * c * c * c * c * c;
+        if (q < 2.0) return a * a * a * a * a - 6.0 * b * b * b * b * b;
+        if (q < 3.0) return a * a * a * a * a;
+        return 0.0;
+    }
+    if (kernel == 2) {
+        if (q >= 2.0) return 0.0;
+        double s = 1.0 - 0.5 * q, s2 = s * s, s4 = s2 * s2, s8 = s4 * s4;
+        return s8 * (4.0 * q * q * q + 6.25 * q * q + 4.0 * q + 1.0);
+    }
     if (q < 1.0) return 1.0 - 1.5 * q * q + 0.75 * q * q * q;
     if (q < 2.0) { double t = 2.0 - q; return 0.25 * t * t * t; }
     return 0.0;
 }
 
-static double m4_df(double q) /* df/dq */
+static double shape_df(int kernel, double q) /* df/dq */
 {
+    if (kernel == 1) {
+        double a = 3.0 - q, b = 2.0 - q, c = 1.0 - q;
+        if (q < 1.0) return -5.0 * a * a * a * a + 30.0 * b * b * b * b - 75.0 * c * c * c * c;
+        if (q < 2.0) return -5.0 * a * a * a * a + 30.0 * b * b * b * b;
+        if (q < 3.0) return -5.0 * a * a * a * a;
+        return 0.0;
+    }
+    if (kernel == 2) {
+        /* product rule on s^8 P(q), s = 1 - q/2, P = 4 q^3 + 25/4 q^2 + 4 q + 1 */
+        if (q >= 2.0) return 0.0;
+        double s = 1.0 - 0.5 * q, s2 = s * s, s4 = s2 * s2, s7 = s4 * s2 * s, s8 = s7 * s;
+        double P = 4.0 * q * q * q + 6.25 * q * q + 4.0 * q + 1.0;
+        double dP = 12.0 * q * q + 12.5 * q + 4.0;
+        return 8.0 * s7 * (-0.5) * P + s8 * dP;
+    }
     if (q < 1.0) return -3.0 * q + 2.25 * q * q;
     if (q < 2.0) { double t = 2.0 - q; return -0.75 * t * t; }
     return 0.0;
 }
 
 /* W(r, h) */
-static double kern_w(double r, double h) { return C_NORM * m4_f(r / h) / (h * h * h); }
+static double kern_w(int k, double r, double h) { return kern_norm(k) * shape_f(k, r / h) / (h * h * h); }
 /* F(r, h) = C f'(q) / h^4 = dW/dr (Eq. 14); grad_i W_ij(h) = rhat_ij F(r_ij, h) */
-static double kern_F(double r, double h) { return C_NORM * m4_df(r / h) / (h * h * h * h); }
+static double kern_F(int k, double r, double h)
+{
+    return kern_norm(k) * shape_df(k, r / h) / (h * h * h * h);
+}
 /* dW/dh at fixed r: -C (3 f(q) + q f'(q)) / h^4 */
-static double kern_dwdh(double r, double h)
+static double kern_dwdh(int k, double r, double h)
 {
     double q = r / h;
-    return -C_NORM * (3.0 * m4_f(q) + q * m4_df(q)) / (h * h * h * h);
+    return -kern_norm(k) * (3.0 * shape_f(k, q) + q * shape_df(k, q)) / (h * h * h * h);
 }
 
 ORC_API void orc_kernel_eval(const double *r, const double *h, int64_t n,
-                             double *w, double *F, double *dwdh)
+                             double *w, double *F, double *dwdh, int kernel)
 {
     for (int64_t i = 0; i < n; ++i) {
-        if (w) w[i] = kern_w(r[i], h[i]);
-        if (F) F[i] = kern_F(r[i], h[i]);
-        if (dwdh) dwdh[i] = kern_dwdh(r[i], h[i]);
+        if (w) w[i] = kern_w(kernel, r[i], h[i]);
+        if (F) F[i] = kern_F(kernel, r[i], h[i]);
+        if (dwdh) dwdh[i] = kern_dwdh(kernel, r[i], h[i]);
     }
 }
 
@@ -186,8 +234,10 @@ ORC_API int64_t orc_chop(const uint64_t *skeys, int64_t n, int32_t thresh,
 /* ------------------------------------------------------------------------- */
 /* Neighbour sets (Sect. 3.2), canonical FP32 membership test:               */
 /*   dx = x_i - x_j (per axis), r2 = (dx*dx + dy*dy) + dz*dz                 */
-/*   density set  D_i = { j : r2 < (2 h_i)*(2 h_i) }        (includes i)     */
-/*   force set    F_i = { j != i : r2 < (2 m)*(2 m) }, m = max(h_i, h_j)     */
+/*   density set  D_i = { j : r2 < (R h_i)*(R h_i) }        (includes i)     */
+/*   force set    F_i = { j != i : r2 < (R m)*(R m) }, m = max(h_i, h_j)     */
+/* with R the kernel's support radius in units of h (2, or 3 for M6) and     */
+/* R h one FP32 multiplication.                                              */
 /* The force set uses the larger smoothing length of the pair so that a pair */
 /* interacts if either particle lies inside the other's range.               */
 /* ------------------------------------------------------------------------- */
@@ -204,29 +254,30 @@ static float canon_r2(const float *pi, const float *pj)
     return s;
 }
 
-static int canon_in_set(int mode, int64_t i, int64_t j, const float *pos4, const float *h)
+static int canon_in_set(int mode, int kernel, int64_t i, int64_t j, const float *pos4, const float *h)
 {
+    const float kr = kernel == 1 ? 3.0f : 2.0f; /* support radius in units of h */
     float r2 = canon_r2(pos4 + 4 * i, pos4 + 4 * j);
     if (mode == 0) {
-        float R = 2.0f * h[i];
+        float R = kr * h[i];
         float R2 = R * R;
         return r2 < R2;
     }
     if (i == j) return 0;
     float m = h[i] > h[j] ? h[i] : h[j];
-    float R = 2.0f * m;
+    float R = kr * m;
     float R2 = R * R;
     return r2 < R2;
 }
 
 /* Row counts for the given targets (cnt[t]). */
 ORC_API void orc_neighbour_counts(const float *pos4, const float *h, int64_t n, int mode,
-                                  const int64_t *targets, int64_t nt, int64_t *cnt)
+                                  const int64_t *targets, int64_t nt, int64_t *cnt, int kernel)
 {
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t t = 0; t < nt; ++t) {
         int64_t i = targets[t], c = 0;
-        for (int64_t j = 0; j < n; ++j) c += canon_in_set(mode, i, j, pos4, h);
+        for (int64_t j = 0; j < n; ++j) c += canon_in_set(mode, kernel, i, j, pos4, h);
         cnt[t] = c;
     }
 }
@@ -234,13 +285,13 @@ ORC_API void orc_neighbour_counts(const float *pos4, const float *h, int64_t n, 
 /* Rows written at off[t] (caller computed from the counts), ascending j. */
 ORC_API void orc_neighbour_lists(const float *pos4, const float *h, int64_t n, int mode,
                                  const int64_t *targets, int64_t nt, const int64_t *off,
-                                 int64_t *idx)
+                                 int64_t *idx, int kernel)
 {
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t t = 0; t < nt; ++t) {
         int64_t i = targets[t], c = off[t];
         for (int64_t j = 0; j < n; ++j)
-            if (canon_in_set(mode, i, j, pos4, h)) idx[c++] = j;
+            if (canon_in_set(mode, kernel, i, j, pos4, h)) idx[c++] = j;
     }
 }
 
@@ -258,17 +309,18 @@ ORC_API void orc_neighbour_lists(const float *pos4, const float *h, int64_t n, i
 /* fixed_iters > 0 runs exactly that many updates and skips the tolerance.   */
 /* Returns the number of targets that did not converge.                      */
 /* ------------------------------------------------------------------------- */
-static void density_sums(int64_t i, double h, const double *x, const double *m, int64_t n,
+static void density_sums(int k, int64_t i, double h, const double *x, const double *m, int64_t n,
                          double *rho_sum, double *dwdh_sum)
 {
     double s0 = 0.0, s1 = 0.0;
+    const double R = kern_support(k);
     for (int64_t j = 0; j < n; ++j) {
         double dx = x[3 * i] - x[3 * j], dy = x[3 * i + 1] - x[3 * j + 1],
                dz = x[3 * i + 2] - x[3 * j + 2];
         double r = sqrt(dx * dx + dy * dy + dz * dz);
-        if (r >= 2.0 * h) continue;
-        s0 += m[j] * kern_w(r, h);
-        s1 += m[j] * kern_dwdh(r, h);
+        if (r >= R * h) continue;
+        s0 += m[j] * kern_w(k, r, h);
+        s1 += m[j] * kern_dwdh(k, r, h);
     }
     *rho_sum = s0;
     *dwdh_sum = s1;
@@ -278,8 +330,9 @@ ORC_API int64_t orc_density(const double *x, const double *v, const double *m, i
                             const int64_t *targets, int64_t nt, const double *h0,
                             double hfact, double tol, int32_t max_iter, int32_t fixed_iters,
                             double *h_out, double *rho, double *omega, double *drhodt,
-                            int32_t *nngb, int32_t *iters)
+                            int32_t *nngb, int32_t *iters, int kernel)
 {
+    const double R = kern_support(kernel);
     int64_t failures = 0;
     double hf3 = hfact * hfact * hfact;
 #pragma omp parallel for schedule(dynamic, 4) reduction(+ : failures)
@@ -290,7 +343,7 @@ ORC_API int64_t orc_density(const double *x, const double *v, const double *m, i
         int limit = fixed_iters > 0 ? fixed_iters : max_iter;
         while (it < limit) {
             double rs, ds;
-            density_sums(i, h, x, m, n, &rs, &ds);
+            density_sums(kernel, i, h, x, m, n, &rs, &ds);
             double rho_h = m[i] * hf3 / (h * h * h);
             double g = rs - rho_h;
             double gp = ds + 3.0 * rho_h / h;
@@ -312,7 +365,7 @@ ORC_API int64_t orc_density(const double *x, const double *v, const double *m, i
         if (!converged) failures += 1;
         /* final quantities at the accepted h */
         double rs, ds;
-        density_sums(i, h, x, m, n, &rs, &ds);
+        density_sums(kernel, i, h, x, m, n, &rs, &ds);
         double rho_h = m[i] * hf3 / (h * h * h);
         double om = 1.0 + h / (3.0 * rho_h) * ds;
         double div = 0.0;
@@ -321,12 +374,12 @@ ORC_API int64_t orc_density(const double *x, const double *v, const double *m, i
             double dx = x[3 * i] - x[3 * j], dy = x[3 * i + 1] - x[3 * j + 1],
                    dz = x[3 * i + 2] - x[3 * j + 2];
             double r = sqrt(dx * dx + dy * dy + dz * dz);
-            if (r >= 2.0 * h) continue;
+            if (r >= R * h) continue;
             ++cnt;
             if (r <= 0.0) continue;
             double vr = ((v[3 * i] - v[3 * j]) * dx + (v[3 * i + 1] - v[3 * j + 1]) * dy +
                          (v[3 * i + 2] - v[3 * j + 2]) * dz) / r;
-            div += m[j] * vr * kern_F(r, h);
+            div += m[j] * vr * kern_F(kernel, r, h);
         }
         h_out[t] = h;
         rho[t] = rho_h;
@@ -352,8 +405,8 @@ ORC_API int64_t orc_density(const double *x, const double *v, const double *m, i
 /*               * 1/2 [F(r,h_i)/(Om_i rho_i) + F(r,h_j)/(Om_j rho_j)]  (13)  */
 /*   vsig_u = sqrt(|P_i - P_j| / (1/2 (rho_i + rho_j)))                 (15)  */
 /*   vsigmax_i = max(alpha c_i, max_{j in F_i} alpha c_i + beta |vr|)   (8)   */
-/* vr = (v_i - v_j) . rhat_ij.  F(r, h) vanishes for r >= 2h, so the sums    */
-/* run over every j != i.  The set for vsigmax is r < 2 max(h_i,h_j) * vsig_scale */
+/* vr = (v_i - v_j) . rhat_ij.  F(r, h) vanishes for r >= R h, so the sums   */
+/* run over every j != i.  The set for vsigmax is r < R max(h_i,h_j) * vsig_scale */
 /* (vsig_scale = 1 is the definition; other values give the bracketing sets  */
 /* the parity tests use).                                                     */
 /* ------------------------------------------------------------------------- */
@@ -361,8 +414,9 @@ ORC_API void orc_force(const double *x, const double *v, const double *m, const 
                        const double *h, const double *rho, const double *omega, int64_t n,
                        const int64_t *targets, int64_t nt, double gamma, double alpha,
                        double beta, double alpha_u, double vsig_scale, double *acc,
-                       double *dudt, double *vsigmax, int32_t *nforce)
+                       double *dudt, double *vsigmax, int32_t *nforce, int kernel)
 {
+    const double R = kern_support(kernel);
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t t = 0; t < nt; ++t) {
         int64_t i = targets[t];
@@ -378,7 +432,7 @@ ORC_API void orc_force(const double *x, const double *v, const double *m, const 
                    dz = x[3 * i + 2] - x[3 * j + 2];
             double r2 = dx * dx + dy * dy + dz * dz;
             double hm = h[i] > h[j] ? h[i] : h[j];
-            double rad = 2.0 * hm * vsig_scale;
+            double rad = R * hm * vsig_scale;
             double r = sqrt(r2);
             double vr = 0.0;
             if (r > 0.0)
@@ -388,11 +442,11 @@ ORC_API void orc_force(const double *x, const double *v, const double *m, const 
                 double s = alpha * ci + beta * fabs(vr);
                 if (s > vs) vs = s;
             }
-            if (r >= 2.0 * hm) continue;
+            if (r >= R * hm) continue;
             ++cnt;
             if (r <= 0.0) continue;
-            double Fi = kern_F(r, h[i]);
-            double Fj = kern_F(r, h[j]);
+            double Fi = kern_F(kernel, r, h[i]);
+            double Fj = kern_F(kernel, r, h[j]);
             double Pj = (gamma - 1.0) * rho[j] * u[j];
             double cj = sqrt(gamma * Pj / rho[j]);
             double qi = 0.0, qj = 0.0;

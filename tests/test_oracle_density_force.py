@@ -351,3 +351,52 @@ def test_conserved_opposite_momenta_and_rings():
         assert np.allclose(out[5:], L, rtol=0, atol=1e-14), (axis, out[5:])
         assert np.all(np.abs(out[2:5]) < 1e-14)
         assert out[0] == pytest.approx(0.5 * N * 0.5 * (R * w) ** 2, rel=1e-14)
+
+
+# ------------------------------------------------------- other kernels (Sect. 2.3)
+@pytest.mark.parametrize("k,hfact", [(oracle.M6, 0.9), (oracle.WC6, 1.3)])
+def test_conservation_and_root_other_kernels(k, hfact):
+    x, v, m, u, h0 = small_cloud()
+    d = oracle.density(x, v, m, h0 * hfact / 1.2, hfact=hfact, kernel=k)
+    assert d.failures == 0
+    for t in range(0, 300, 61):
+        r = np.linalg.norm(x - x[t], axis=1)
+        rs = np.sum(m * oracle.kernel_eval(r, np.full_like(r, d.h[t]), k)[0])
+        assert abs(rs - m[t] * (hfact / d.h[t]) ** 3) < 1e-12 * rs
+    f = oracle.force(x, v, m, u, d.h, d.rho, d.omega, kernel=k)
+    ma = m[:, None] * f.acc
+    assert np.max(np.abs(ma.sum(0))) < 1e-13 * np.sum(np.abs(ma))
+    assert np.max(np.abs(np.cross(x, ma).sum(0))) < 1e-13 * np.sum(np.abs(np.cross(x, ma)))
+    de = m * (np.sum(v * f.acc, 1) + f.dudt)
+    assert abs(de.sum()) < 1e-12 * np.sum(m * (np.abs(np.sum(v * f.acc, 1)) + np.abs(f.dudt)))
+    # support radius in the sets: every force-set partner lies within R max(h_i, h_j)
+    R = oracle.SUPPORT[k]
+    off, idx = oracle.neighbours(np.c_[x, m].astype(np.float32), d.h.astype(np.float32), 1, kernel=k)
+    for i in (0, 100, 200):
+        js = idx[off[i]:off[i + 1]]
+        r = np.linalg.norm(x[js] - x[i], axis=1)
+        assert np.all(r < R * np.maximum(d.h[i], d.h[js]) * (1 + 1e-6))
+        assert len(js) == f.nforce[i]
+
+
+def test_variational_pressure_force_m6():
+    # grad-h consistency holds for any kernel: m_i a_i = -dU/dx_i (alpha = beta = alpha_u = 0)
+    x, v, m, u, h0 = small_cloud(160, seed=21)
+    gam = 5.0 / 3.0
+    k = oracle.M6
+    d = oracle.density(x, v, m, h0 * 0.9 / 1.2, hfact=0.9, kernel=k)
+    f = oracle.force(x, v, m, u, d.h, d.rho, d.omega, alpha=0.0, beta=0.0, alpha_u=0.0, kernel=k)
+    A = (gam - 1) * u / d.rho ** (gam - 1)
+
+    def U(xx):
+        dd = oracle.density(xx, v, m, d.h, hfact=0.9, kernel=k)
+        return np.sum(m * A * dd.rho ** (gam - 1) / (gam - 1))
+
+    e = 1e-6
+    for i in (0, 57):
+        for a in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[i, a] += e
+            xm[i, a] -= e
+            grad = (U(xp) - U(xm)) / (2 * e)
+            assert abs(m[i] * f.acc[i, a] + grad) < 1e-6 * np.max(np.abs(m[:, None] * f.acc))
