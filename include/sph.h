@@ -41,7 +41,7 @@ typedef enum {
     SPH_ERR_CUDA = 2,          /* a CUDA runtime call failed                         */
     SPH_ERR_NOMEM = 3,         /* allocation failed, or tree capacity exceeded       */
     SPH_ERR_NOT_CONVERGED = 4, /* h-rho Newton did not reach h_tol in max_h_iter     */
-    SPH_ERR_TILE_OVERFLOW = 5, /* a tree-walk list overflowed its shared-memory tile */
+    SPH_ERR_TILE_OVERFLOW = 5, /* a tree-walk stack or a neighbour list overflowed  */
     SPH_ERR_NONFINITE = 6,     /* non-finite position, velocity, mass or h; m<=0; h<=0 */
     SPH_ERR_NEGATIVE_U = 7,    /* internal energy became negative                    */
     SPH_ERR_TIMEOUT = 8        /* a bounded device-side wait gave up                 */
@@ -58,11 +58,16 @@ typedef struct {
     float alpha_u;       /* alpha_u, artificial conductivity (Eq. 13)                   */
     float c_cour;        /* Courant factor (Eq. 8)                                      */
     float h_tol;         /* Newton stops when |dh| < h_tol h (decided exactly)         */
-    int32_t kernel;      /* smoothing kernel: 0 = M4 cubic spline (the only one built)  */
+    int32_t kernel;      /* smoothing kernel (Sect. 2.3), support radius R in units of h:
+                            0 = M4 cubic spline (R = 2), 1 = M6 quintic spline
+                            (R = 3), 2 = Wendland C6 (R = 2); other values are
+                            SPH_ERR_INVALID_ARG.  hfact should suit the kernel
+                            (about 1.2, 0.9 and 1.3 respectively)             */
     int32_t n_leaf;      /* max particles per tree leaf  (1..64)                        */
     int32_t n_group;     /* max particles per walk group (1..32)                        */
     int32_t tile;        /* shared-memory list capacity per target of the walking
-                            fallback kernels, 0 = default (80 density, 96 force)     */
+                            fallback kernels, 0 = default (80 density, 96 force
+                            for M4; 128 for the other kernels)                 */
     int32_t max_h_iter;  /* Newton iteration cap (>= 1)                                 */
     int32_t density_iters; /* 0: iterate to h_tol; k > 0: exactly k updates (Sect. 3.2.1) */
     /* Launch shape of the neighbour-list density and force kernels (results
@@ -119,7 +124,8 @@ sph_status sph_density(sph_ctx *ctx, sph_state *s, const sph_params *p, void *st
 
 /* Hydro force pass (Eqs. 9-15), no gravity: writes acc (xyz and du/dt) and
  * vsigmax.  Needs h, rho, omega from sph_density and the current vel.
- * A pair interacts if r < 2 max(h_i, h_j) (Sect. 3.2). */
+ * A pair interacts if r < R max(h_i, h_j), R the kernel's support radius
+ * in units of h (Sect. 3.2). */
 sph_status sph_force(sph_ctx *ctx, sph_state *s, const sph_params *p, void *stream);
 
 /* Courant step (Eq. 8): *d_dt = c_cour * min_i h_i / vsigmax_i (device float). */
@@ -241,8 +247,10 @@ sph_status sph_conserved_noalloc(int64_t n, const float *d_pos, const float *d_v
                                  double *d_out8, void *stream);
 
 /* Neighbour sets of the current tree/state (Sect. 3.2), for testing.
- * mode 0: density set {j : r2 < (2 h_i)^2} (includes i);
- * mode 1: force set {j != i : r2 < (2 max(h_i, h_j))^2};
+ * mode 0: density set {j : r2 < (R h_i)^2} (includes i);
+ * mode 1: force set {j != i : r2 < (R max(h_i, h_j))^2};
+ * R the support radius of p->kernel (2 M4, 3 M6, 2 Wendland C6) and R h
+ * rounded to FP32;
  * r2 = (dx*dx + dy*dy) + dz*dz in FP32, round-to-nearest, no fusion.
  * Modes 0 and 1 use a separate tree walk.  Modes 2 and 3 give the same two
  * sets taken from the neighbour lists that sph_density and sph_force read:

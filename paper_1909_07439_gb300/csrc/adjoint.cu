@@ -18,20 +18,13 @@
 // dg_i/dh_i = 3 rho_i Omega_i / h_i and dg_i/dr_ij = m_j F(r_ij, h_i);
 // rho_i = M_i / h_i^3 and Omega_i = 1 + h_i^4 S_i / (3 M_i),
 // S_i = sum_j m_j dW/dh(r_ij, h_i).
+//
+// The pair operations are templates on the smoothing kernel K (SphKernel<K>:
+// f, f', f'' and the support radius R).
+#include "kernels.cuh"
 #include "walk.cuh"
 
 namespace sph {
-
-// M4 f'(q), piecewise on the value of q
-__device__ __forceinline__ float m4_dfq(float q)
-{
-    if (q < 1.f) return q * (-3.f + 2.25f * q);
-    if (q < 2.f) {
-        const float t = 2.f - q;
-        return -0.75f * (t * t);
-    }
-    return 0.f;
-}
 
 // ------------------------------------------------------- generic pair walk
 struct PairWalkArgs {
@@ -43,7 +36,8 @@ struct PairWalkArgs {
     int *work;
     WalkTree tree;
     const int *inst;
-    int dens_set;  // 1: density set r < 2 h_i (self included); 0: force set
+    int dens_set;  // 1: density set r < R h_i (self included); 0: force set r < R max(h_i, h_j)
+    float kr;      // R, the kernel's support radius in units of h
     // neighbour lists of the last density pass (a superset of both pair sets
     // while they are fresh and no h of the instance outgrew the list pad)
     const int *nl_idx, *nl_len, *rec_ctl, *rec_bad;
@@ -119,10 +113,10 @@ __global__ void __launch_bounds__(128) pairwalk_kernel(PairWalkArgs a, Op op)
                         const float r2 = canon_r2(tp.x, tp.y, tp.z, pj.x, pj.y, pj.z);
                         bool hit;
                         if (a.dens_set) {
-                            const float R = 2.0f * sm.th[tt];
+                            const float R = a.kr * sm.th[tt];
                             hit = j >= 0 && r2 < R * R;
                         } else {
-                            const float R = 2.0f * fmaxf(sm.th[tt], hj);
+                            const float R = a.kr * fmaxf(sm.th[tt], hj);
                             hit = j >= 0 && j != i0 + tt && r2 < R * R;
                         }
                         bs[tt] = __ballot_sync(0xffffffffu, hit);
@@ -157,14 +151,15 @@ __global__ void __launch_bounds__(128) pairwalk_kernel(PairWalkArgs a, Op op)
                         const int j = __ldcs(lst + e);
                         const float4 pj = __ldg(&a.pos[j]);
                         const float r2 = canon_r2(tp.x, tp.y, tp.z, pj.x, pj.y, pj.z);
-                        const float R = a.dens_set ? 2.0f * ht : 2.0f * fmaxf(ht, __ldg(&a.h[j]));
+                        const float R = a.dens_set ? a.kr * ht : a.kr * fmaxf(ht, __ldg(&a.h[j]));
                         if (r2 < R * R && (a.dens_set || j != i)) op.pair(i, j, acc);
                     }
                 }
                 __syncwarp();
             } else {
-                bool ok = a.dens_set ? walk_group(a.tree, root, glo, ghi, 2.f * hmx, false, 0.f, sm.w, chunk)
-                                     : walk_group(a.tree, root, glo, ghi, 0.f, true, hmx, sm.w, chunk);
+                const float hr = 0.5f * a.kr;
+                bool ok = a.dens_set ? walk_group(a.tree, root, glo, ghi, a.kr * hmx, false, 0.f, sm.w, chunk)
+                                     : walk_group(a.tree, root, glo, ghi, 0.f, true, hr * hmx, sm.w, chunk, hr);
                 if (!ok && lane == 0) raise_error(a.err, SPH_ERR_TILE_OVERFLOW);
                 flush();
             }
@@ -180,14 +175,6 @@ __global__ void __launch_bounds__(128) pairwalk_kernel(PairWalkArgs a, Op op)
 struct PairIn {
     float x[3], v[3], u, h, rho, om;
 };
-
-// M4 f''(q) on the same pieces as m4_dfq
-__device__ __forceinline__ float m4_d2fq(float q)
-{
-    if (q < 1.f) return -3.f + 4.5f * q;
-    if (q < 2.f) return 1.5f * (2.f - q);
-    return 0.f;
-}
 
 // P_i - P_j = (gamma - 1)(rho_i u_i - rho_j u_j) without FP64 (whose rate is
 // a small fraction of FP32's on this GPU): each product's rounding error is
@@ -214,7 +201,7 @@ __device__ __forceinline__ float fast_sqrt(float x) { return x > 0.f ? x * rsqrt
 // only, |x| has derivative +1 at 0, and sqrt has derivative 0 at 0 (at equal
 // pressures the conduction term carries u_i - u_j times a zero speed).
 // Quotients and roots use the hardware approximations (a few ulp).
-template <bool WANT_I>
+template <bool WANT_I, int K>
 __device__ __forceinline__ void force_pair_vjp(const PairIn &I, const PairIn &J, float mj, float alpha,
                                                float beta, float alpha_u, float gamma, float4 w,
                                                PairIn &g, float &galpha)
@@ -228,9 +215,9 @@ __device__ __forceinline__ void force_pair_vjp(const PairIn &I, const PairIn &J,
     // ---- forward values
     const float hiinv = __fdividef(1.f, I.h), hjinv = __fdividef(1.f, J.h);
     const float qi = r * hiinv, qj = r * hjinv;
-    const float dfi = m4_dfq(qi), dfj = m4_dfq(qj);
+    const float dfi = SphKernel<K>::df(qi), dfj = SphKernel<K>::df(qj);
     const float h2i = hiinv * hiinv, h2j = hjinv * hjinv;
-    const float Ki = kCNorm * h2i * h2i, Kj = kCNorm * h2j * h2j;  // C / h^4
+    const float Ki = SphKernel<K>::C * h2i * h2i, Kj = SphKernel<K>::C * h2j * h2j;  // C / h^4
     const float Fi = dfi * Ki, Fj = dfj * Kj;
     const float dvx = I.v[0] - J.v[0], dvy = I.v[1] - J.v[1], dvz = I.v[2] - J.v[2];
     const float sd = dvx * dx + dvy * dy + dvz * dz;
@@ -332,12 +319,12 @@ __device__ __forceinline__ void force_pair_vjp(const PairIn &I, const PairIn &J,
     // F = C f'(q) / h^4, q = r / h
     float br = 0.f;
     {
-        const float bq = bFi * Ki * m4_d2fq(qi);
+        const float bq = bFi * Ki * SphKernel<K>::d2f(qi);
         bhi += -4.f * bFi * Fi * hiinv - bq * qi * hiinv;
         br += bq * hiinv;
     }
     {
-        const float bq = bFj * Kj * m4_d2fq(qj);
+        const float bq = bFj * Kj * SphKernel<K>::d2f(qj);
         bhj += -4.f * bFj * Fj * hjinv - bq * qj * hjinv;
         br += bq * hjinv;
     }
@@ -373,6 +360,7 @@ __device__ __forceinline__ void force_pair_vjp(const PairIn &I, const PairIn &J,
     }
 }
 
+template <int KER>
 struct ForceBwdOp {
     const float4 *pos, *vel, *gacc;  // gacc: (dL/da xyz, dL/d(du/dt))
     const float *h, *rho, *omega;
@@ -406,9 +394,9 @@ struct ForceBwdOp {
     {
         (void)k;
         const PairIn J = load(j);
-        force_pair_vjp<true>(c.K, J, pos[j].w, alpha, beta, alpha_u, gamma, c.wk, c.g, c.ga);
+        force_pair_vjp<true, KER>(c.K, J, pos[j].w, alpha, beta, alpha_u, gamma, c.wk, c.g, c.ga);
         float unused = 0.f;
-        force_pair_vjp<false>(J, c.K, c.mk, alpha, beta, alpha_u, gamma, gacc[j], c.g, unused);
+        force_pair_vjp<false, KER>(J, c.K, c.mk, alpha, beta, alpha_u, gamma, gacc[j], c.g, unused);
     }
     __device__ void reduce(Acc &c, int L) const
     {
@@ -437,25 +425,17 @@ struct ForceBwdOp {
 };
 
 // --------------------------------------------------------- density backward
-// M4 pieces: f, f', f''
-__device__ __forceinline__ void m4_all(float q, float &f, float &df, float &d2f)
+// kernel pieces f, f', f'' at q (all 0 beyond the support)
+template <int K>
+__device__ __forceinline__ void kernel_all(float q, float &f, float &df, float &d2f)
 {
-    if (q < 1.f) {
-        f = 1.f + q * q * (-1.5f + 0.75f * q);
-        df = q * (-3.f + 2.25f * q);
-        d2f = -3.f + 4.5f * q;
-    } else if (q < 2.f) {
-        float t = 2.f - q;
-        f = 0.25f * t * t * t;
-        df = -0.75f * t * t;
-        d2f = 1.5f * t;
-    } else {
-        f = df = d2f = 0.f;
-    }
+    SphKernel<K>::f_df(q, f, df);
+    d2f = SphKernel<K>::d2f(q);
 }
 
 // pass 1: per target, S = sum m dW/dh and S2 = sum m d2W/dh2 over the density
 // set; then lambda (the IFT multiplier) and omega-coefficient per particle.
+template <int K>
 struct DensBwd1Op {
     const float4 *pos;
     const float *h, *rho, *omega;
@@ -471,10 +451,11 @@ struct DensBwd1Op {
         float r = fast_sqrt(dx * dx + dy * dy + dz * dz);
         float hi = h[i], hinv = __fdividef(1.f, hi);
         float q = r * hinv, f, df, d2f;
-        m4_all(q, f, df, d2f);
+        kernel_all<K>(q, f, df, d2f);
         float h4 = hinv * hinv * hinv * hinv;
-        c.S += pj.w * (-kCNorm * (3.f * f + q * df) * h4);
-        c.S2 += pj.w * (kCNorm * (12.f * f + 8.f * q * df + q * q * d2f) * h4 * hinv);
+        constexpr float C = SphKernel<K>::C;
+        c.S += pj.w * (-C * (3.f * f + q * df) * h4);
+        c.S2 += pj.w * (C * (12.f * f + 8.f * q * df + q * q * d2f) * h4 * hinv);
     }
     __device__ void reduce(Acc &c, int L) const
     {
@@ -496,6 +477,7 @@ struct DensBwd1Op {
 
 // pass 2 (force set): gx_k += sum_j (c_kj + c_jk) rhat_kj,
 // c_ij = -lambda_i m_j F(r, h_i) + w_i m_j d2W/dh dr(r, h_i)
+template <int K>
 struct DensBwd2Op {
     const float4 *pos;
     const float *h;
@@ -506,10 +488,11 @@ struct DensBwd2Op {
     __device__ static float cterm(float r, float hh, float lam, float w, float m)
     {
         float hinv = __fdividef(1.f, hh), q = r * hinv, f, df, d2f;
-        m4_all(q, f, df, d2f);
+        kernel_all<K>(q, f, df, d2f);
         float h4 = hinv * hinv * hinv * hinv;
-        float F = kCNorm * df * h4;
-        float Whr = -kCNorm * (4.f * df + q * d2f) * h4 * hinv;
+        constexpr float C = SphKernel<K>::C;
+        float F = C * df * h4;
+        float Whr = -C * (4.f * df + q * d2f) * h4 * hinv;
         return m * (-lam * F + w * Whr);
     }
     __device__ void pair(int k, int j, Acc &c) const
@@ -540,7 +523,7 @@ struct DensBwd2Op {
 
 // ------------------------------------------------------------------ launch
 template <int CAP, class Op>
-static cudaError_t launch_pairwalk(Ctx &c, const sph_state &s, bool dens_set, const Op &op,
+static cudaError_t launch_pairwalk(Ctx &c, const sph_state &s, bool dens_set, float kr, const Op &op,
                                    cudaStream_t st, const Batch *batch)
 {
     size_t smem = sizeof(PairWalkSmem<CAP>) * 4;
@@ -567,6 +550,7 @@ static cudaError_t launch_pairwalk(Ctx &c, const sph_state &s, bool dens_set, co
     a.tree = WalkTree{c.tree.node_lo, c.tree.node_hi, c.tree.node_ref};
     a.inst = batch ? c.inst : nullptr;
     a.dens_set = dens_set ? 1 : 0;
+    a.kr = kr;
     a.nl_idx = c.nl_idx;
     a.nl_len = c.nl_len;
     a.rec_ctl = c.tree.rec_ctl;
@@ -578,11 +562,12 @@ static cudaError_t launch_pairwalk(Ctx &c, const sph_state &s, bool dens_set, co
     return cudaGetLastError();
 }
 
-cudaError_t force_bwd(Ctx &c, const sph_state &s, const sph_params &p, const float4 *gacc,
-                      float4 *gpos, float4 *gvel, float *gh, float *grho, float *gom,
-                      double *galpha, cudaStream_t st)
+template <int K>
+static cudaError_t force_bwd_k(Ctx &c, const sph_state &s, const sph_params &p, const float4 *gacc,
+                               float4 *gpos, float4 *gvel, float *gh, float *grho, float *gom,
+                               double *galpha, cudaStream_t st)
 {
-    ForceBwdOp op;
+    ForceBwdOp<K> op;
     op.pos = (const float4 *)s.pos;
     op.vel = (const float4 *)s.vel;
     op.gacc = gacc;
@@ -602,14 +587,24 @@ cudaError_t force_bwd(Ctx &c, const sph_state &s, const sph_params &p, const flo
     // the force-set walk needs node and group h_max of the current h
     cudaError_t e = update_hmax(c, s, p, st);
     if (e != cudaSuccess) return e;
-    return launch_pairwalk<96>(c, s, false, op, st, nullptr);
+    return launch_pairwalk<96>(c, s, false, SphKernel<K>::R, op, st, nullptr);
 }
 
-cudaError_t density_bwd(Ctx &c, const sph_state &s, const sph_params &p, const float *gh,
-                        const float *grho, const float *gom, float4 *gpos, float2 *coef,
-                        cudaStream_t st, bool refresh_hmax)
+cudaError_t force_bwd(Ctx &c, const sph_state &s, const sph_params &p, const float4 *gacc,
+                      float4 *gpos, float4 *gvel, float *gh, float *grho, float *gom,
+                      double *galpha, cudaStream_t st)
 {
-    DensBwd1Op op1;
+    if (p.kernel == 1) return force_bwd_k<1>(c, s, p, gacc, gpos, gvel, gh, grho, gom, galpha, st);
+    if (p.kernel == 2) return force_bwd_k<2>(c, s, p, gacc, gpos, gvel, gh, grho, gom, galpha, st);
+    return force_bwd_k<0>(c, s, p, gacc, gpos, gvel, gh, grho, gom, galpha, st);
+}
+
+template <int K>
+static cudaError_t density_bwd_k(Ctx &c, const sph_state &s, const sph_params &p, const float *gh,
+                                 const float *grho, const float *gom, float4 *gpos, float2 *coef,
+                                 cudaStream_t st, bool refresh_hmax)
+{
+    DensBwd1Op<K> op1;
     op1.pos = (const float4 *)s.pos;
     op1.h = s.h;
     op1.rho = s.rho;
@@ -623,14 +618,23 @@ cudaError_t density_bwd(Ctx &c, const sph_state &s, const sph_params &p, const f
     // for the current h (unless the caller just did)
     cudaError_t e = refresh_hmax ? update_hmax(c, s, p, st) : cudaSuccess;
     if (e != cudaSuccess) return e;
-    e = launch_pairwalk<96>(c, s, true, op1, st, nullptr);
+    e = launch_pairwalk<96>(c, s, true, SphKernel<K>::R, op1, st, nullptr);
     if (e != cudaSuccess) return e;
-    DensBwd2Op op2;
+    DensBwd2Op<K> op2;
     op2.pos = (const float4 *)s.pos;
     op2.h = s.h;
     op2.coef = coef;
     op2.gpos = gpos;
-    return launch_pairwalk<96>(c, s, false, op2, st, nullptr);
+    return launch_pairwalk<96>(c, s, false, SphKernel<K>::R, op2, st, nullptr);
+}
+
+cudaError_t density_bwd(Ctx &c, const sph_state &s, const sph_params &p, const float *gh,
+                        const float *grho, const float *gom, float4 *gpos, float2 *coef,
+                        cudaStream_t st, bool refresh_hmax)
+{
+    if (p.kernel == 1) return density_bwd_k<1>(c, s, p, gh, grho, gom, gpos, coef, st, refresh_hmax);
+    if (p.kernel == 2) return density_bwd_k<2>(c, s, p, gh, grho, gom, gpos, coef, st, refresh_hmax);
+    return density_bwd_k<0>(c, s, p, gh, grho, gom, gpos, coef, st, refresh_hmax);
 }
 
 }  // namespace sph

@@ -20,6 +20,7 @@
 // lane = t * L + sub; partial sums are reduced across the L lanes with xor
 // shuffles, so every lane of a target holds the full sums and takes the
 // same Newton step.
+#include "kernels.cuh"
 #include "walk.cuh"
 
 namespace sph {
@@ -68,27 +69,17 @@ struct DensArgs {
     unsigned long long *counters;
 };
 
-// M4 shape f(q) and f'(q) without branches (q >= 0; q >= 2 gives 0)
-__device__ __forceinline__ void m4_f_df(float q, float &f, float &df)
-{
-    float fi = 1.f + q * q * (-1.5f + 0.75f * q);
-    float dfi = q * (-3.f + 2.25f * q);
-    float t = fmaxf(2.f - q, 0.f);
-    float t2 = t * t;
-    bool in = q < 1.f;
-    f = in ? fi : 0.25f * t2 * t;
-    df = in ? dfi : -0.75f * t2;
-}
-
 __device__ __forceinline__ float seg_sum(float v, int L)
 {
     for (int o = L >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
-// Sums of one pair at smoothing length 1/hinv:
+// Sums of one pair at smoothing length 1/hinv (kernel K, whose f and f'
+// vanish beyond its support):
 //   s0 += m_j f(q), s1 += m_j (3 f + q f'), s2 += m_j vd f' / r
 // (h^3 rho = C s0, -h^4 d(rho)/dh = C s1, Eq. 3 numerator x h^4 / C = s2).
+template <int K>
 __device__ __forceinline__ void pair_sums(float r2, float mj, float vd, float hinv, float &s0,
                                           float &s1, float &s2)
 {
@@ -96,7 +87,7 @@ __device__ __forceinline__ void pair_sums(float r2, float mj, float vd, float hi
     const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
     const float q = r2 * rinv * hinv;
     float f, df;
-    m4_f_df(q, f, df);
+    SphKernel<K>::f_df(q, f, df);
     s0 += mj * f;
     s1 += mj * (3.f * f + q * df);
     s2 += mj * vd * df * rinv;
@@ -107,10 +98,11 @@ __device__ __forceinline__ void pair_sums(float r2, float mj, float vd, float hi
 // is decided exactly: h_new - h is exact in FP32 for h_new in [h/2, 2h] and
 // the rounding error of tol h is recovered with an FMA.
 __device__ __forceinline__ void newton_update(float &h, float &hlo, float &hhi, bool &conv,
-                                              float s0, float s1, float M, bool fixed, float tol)
+                                              float s0, float s1, float M, bool fixed, float tol,
+                                              float C)
 {
-    const float gt = kCNorm * s0 - M;
-    const float gp = 3.f * M - kCNorm * s1;
+    const float gt = C * s0 - M;
+    const float gp = 3.f * M - C * s1;
     if (gt == 0.f) {
         conv = !fixed;
         return;
@@ -132,12 +124,12 @@ __device__ __forceinline__ void newton_update(float &h, float &hlo, float &hhi, 
 
 // outputs at the accepted h (Eqs. 1-4) and the force pass's per-particle terms
 __device__ __forceinline__ void density_outputs(const DensArgs &a, int i, float h, float M, float s1,
-                                                float s2, float u)
+                                                float s2, float u, float C)
 {
     const float hinv = 1.f / h;
     const float rho = M * hinv * hinv * hinv;
-    const float om = 1.f - kCNorm * s1 / (3.f * M);
-    const float F4 = kCNorm * hinv * hinv * hinv * hinv;
+    const float om = 1.f - C * s1 / (3.f * M);
+    const float F4 = C * hinv * hinv * hinv * hinv;
     a.h[i] = h;
     a.rho[i] = rho;
     a.omega[i] = om;
@@ -154,6 +146,7 @@ __device__ __forceinline__ void push_fallback(const DensArgs &a, int g, int b0, 
 // Launch shape (run-time): a.tb targets per batch (32 / a.tb lanes per
 // target), blockDim.x / 32 warps per block; registers capped for 1024
 // resident threads per SM.
+template <int K>
 __global__ void __launch_bounds__(256, 4) density_list_kernel(DensArgs a)
 {
     const int lane = threadIdx.x & 31;
@@ -194,7 +187,7 @@ __global__ void __launch_bounds__(256, 4) density_list_kernel(DensArgs a)
                 const int *__restrict__ lst = a.nl_idx + (size_t)i * kNbrCap;
                 const float4 xi = a.pos[i], vi = a.vel[i];
                 float h = a.h[i];
-                const float hw = h * a.h_in_scale;  // the lists hold every pair with r < 2 hw
+                const float hw = h * a.h_in_scale;  // the lists hold every pair with r < R hw
                 const float M = xi.w * hf3;
                 float hlo = 0.f, hhi = INFINITY;
                 bool conv = !act, outside = false, final_pass = false;
@@ -204,7 +197,7 @@ __global__ void __launch_bounds__(256, 4) density_list_kernel(DensArgs a)
                     s0 = 0.f; s1 = 0.f; s2 = 0.f;
                     int cnt = 0;
                     const float hinv = 1.f / h;
-                    const float R = 2.f * h;
+                    const float R = SphKernel<K>::R * h;
                     const float R2 = R * R;
                     // Two consecutive entries per lane and iteration (one 8-byte
                     // load of the list, fetched an iteration ahead: the lists come
@@ -216,7 +209,7 @@ __global__ void __launch_bounds__(256, 4) density_list_kernel(DensArgs a)
                         const float r2 = dx * dx + dy * dy + dz * dz;
                         const float vd = (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz;
                         cnt += (mj > 0.f && r2 < R2) ? 1 : 0;
-                        pair_sums(r2, mj, vd, hinv, s0, s1, s2);
+                        pair_sums<K>(r2, mj, vd, hinv, s0, s1, s2);
                     };
                     int e = 2 * sub;
                     int2 jn = e < len ? __ldcs(reinterpret_cast<const int2 *>(lst + e)) : make_int2(0, 0);
@@ -240,7 +233,7 @@ __global__ void __launch_bounds__(256, 4) density_list_kernel(DensArgs a)
                     }
                     if (final_pass) break;
                     if (act && !conv) {
-                        newton_update(h, hlo, hhi, conv, s0, s1, M, fixed, a.tol);
+                        newton_update(h, hlo, hhi, conv, s0, s1, M, fixed, a.tol, SphKernel<K>::C);
                         outside = h > hw;
                     }
                     ++it;
@@ -258,7 +251,7 @@ __global__ void __launch_bounds__(256, 4) density_list_kernel(DensArgs a)
                     push_fallback(a, g, b0, nt);
                     continue;
                 }
-                if (act && sub == 0) density_outputs(a, i, h, M, s1, s2, vi.w);
+                if (act && sub == 0) density_outputs(a, i, h, M, s1, s2, vi.w, SphKernel<K>::C);
             }
         }
     }
@@ -274,7 +267,7 @@ __global__ void __launch_bounds__(256, 4) density_list_kernel(DensArgs a)
 
 // Batches the list kernel handed over, each solved from its starting h with
 // tree walks.
-template <int CAP>
+template <int CAP, int K>
 __global__ void __launch_bounds__(kDensWarps * 32) density_walk_kernel(DensArgs a)
 {
     extern __shared__ __align__(16) unsigned char dsm_raw[];
@@ -316,7 +309,7 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_walk_kernel(DensArgs 
             const float h_in = h;
             const float M = sm.tp[act ? t : 0].w * hf3;  // m_i hfact^3
             float hlo = 0.f, hhi = INFINITY;
-            float hw = h * (1.f + kPad);  // list radius is 2 hw
+            float hw = h * (1.f + kPad);  // list radius is R hw
             bool valid = false;           // lists cover the current h
             bool streamed = false;        // batch overflowed the tile
             bool conv = !act;
@@ -328,7 +321,7 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_walk_kernel(DensArgs 
                 s0 = 0.f; s1 = 0.f; s2 = 0.f;
                 int cnt = 0;
                 const float hinv = 1.f / h;
-                const float R = 2.f * h;
+                const float R = SphKernel<K>::R * h;
                 const float R2 = R * R;
                 auto list_sums = [&]() {
                     if (act) {
@@ -337,14 +330,14 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_walk_kernel(DensArgs 
                             const float r2 = sm.er2[t][e];
                             if (!(r2 < R2)) continue;
                             ++cnt;
-                            pair_sums(r2, sm.em[t][e], sm.evd[t][e], hinv, s0, s1, s2);
+                            pair_sums<K>(r2, sm.em[t][e], sm.evd[t][e], hinv, s0, s1, s2);
                         }
                     }
                     __syncwarp();
                 };
                 if (!valid) {
                     // (re)build the candidate lists with a walk
-                    const float myr = streamed ? R : 2.f * hw;  // padded unless streaming
+                    const float myr = streamed ? R : SphKernel<K>::R * hw;  // padded unless streaming
                     if (act && sub == 0) sm.tr2[t] = myr * myr;
                     if (lane < kTB) sm.tlen[lane] = 0;
                     float reach = act ? myr : 0.f;
@@ -428,7 +421,7 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_walk_kernel(DensArgs 
                 }
                 if (final_pass) break;
                 if (act && !conv) {
-                    newton_update(h, hlo, hhi, conv, s0, s1, M, fixed, a.tol);
+                    newton_update(h, hlo, hhi, conv, s0, s1, M, fixed, a.tol, SphKernel<K>::C);
                     if (h > hw) {  // outgrew the padded list
                         hw = h * (1.f + kPad);
                         valid = false;
@@ -446,7 +439,7 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_walk_kernel(DensArgs 
                 }
                 __syncwarp();
             }
-            if (act && sub == 0) density_outputs(a, i, h, M, s1, s2, sm.tv[t].w);
+            if (act && sub == 0) density_outputs(a, i, h, M, s1, s2, sm.tv[t].w, SphKernel<K>::C);
             // the neighbour lists hold while no h grew beyond their pad
             if (__any_sync(0xffffffffu, act && h > a.h_in_scale * h_in) && lane == 0) {
                 atomicOr(a.rec_bad + root, 1);  // root = this group's instance
@@ -480,6 +473,7 @@ struct NbrArgs {
     WalkTree tree;
     const int *inst;
     int mode;          // 0 density set, 1 force set
+    float kr;          // support radius in units of h
     int64_t *off;      // [n+1]
     int32_t *idx;      // nullptr: count pass
     int *err;
@@ -524,7 +518,7 @@ __global__ void __launch_bounds__(128) neighbour_kernel(NbrArgs a)
                     float ht = sm.th[tt];
                     int it = gr.x + b0 + tt;
                     float r2 = canon_r2(tq.x, tq.y, tq.z, pj.x, pj.y, pj.z);
-                    float Rr = a.mode == 0 ? 2.0f * ht : 2.0f * fmaxf(ht, hj);
+                    float Rr = a.mode == 0 ? a.kr * ht : a.kr * fmaxf(ht, hj);
                     bool hit = j >= 0 && r2 < Rr * Rr && (a.mode == 0 || j != it);
                     unsigned b = __ballot_sync(0xffffffffu, hit);
                     int base = sm.tcnt[tt];
@@ -534,8 +528,8 @@ __global__ void __launch_bounds__(128) neighbour_kernel(NbrArgs a)
                     __syncwarp();
                 }
             };
-            bool ok = walk_group(a.tree, a.inst ? a.inst[gr.x] : 0, glo, ghi, 2.f * hmx, a.mode == 1,
-                                 hmx, sm.w, chunk);
+            bool ok = walk_group(a.tree, a.inst ? a.inst[gr.x] : 0, glo, ghi, a.kr * hmx, a.mode == 1,
+                                 0.5f * a.kr * hmx, sm.w, chunk, 0.5f * a.kr);
             if (!ok && lane == 0) raise_error(a.err, SPH_ERR_TILE_OVERFLOW);
             if (lane < nt && !a.idx) a.off[gr.x + b0 + lane] = sm.tcnt[lane];
             __syncwarp();
@@ -576,7 +570,7 @@ __global__ void scan_i64_kernel(int64_t *off, int n)
 // list into *missing); otherwise the rows are written at off[i].
 __global__ void list_set_kernel(const float4 *__restrict__ pos, const float *__restrict__ h,
                                 const int *__restrict__ idx, const int *__restrict__ len, int n,
-                                int mode, int64_t *off, int32_t *out, int *missing)
+                                int mode, float kr, int64_t *off, int32_t *out, int *missing)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int l = len[i];
@@ -595,7 +589,7 @@ __global__ void list_set_kernel(const float4 *__restrict__ pos, const float *__r
             const int j = idx[(size_t)i * kNbrCap + e];
             const float4 pj = pos[j];
             const float r2 = canon_r2(pi.x, pi.y, pi.z, pj.x, pj.y, pj.z);
-            const float R = mode == 0 ? 2.0f * hi : 2.0f * fmaxf(hi, h[j]);
+            const float R = mode == 0 ? kr * hi : kr * fmaxf(hi, h[j]);
             if (r2 < R * R && (mode == 0 || j != i)) {
                 if (out) out[w++] = j;
                 ++cnt;
@@ -607,19 +601,19 @@ __global__ void list_set_kernel(const float4 *__restrict__ pos, const float *__r
 
 // ------------------------------------------------------------------ host side
 // one-time kernel attributes and occupancy (also called before graph capture)
-template <int CAP>
+template <int CAP, int K>
 static cudaError_t configure_density(int &blocks)
 {
     static bool configured = false;
     static int nb_cached = 1;
     if (!configured) {
         size_t smem = sizeof(DensSmem<CAP>) * kDensWarps;
-        cudaError_t e = cudaFuncSetAttribute(density_walk_kernel<CAP>,
+        cudaError_t e = cudaFuncSetAttribute(density_walk_kernel<CAP, K>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, density_walk_kernel<CAP>, kDensWarps * 32,
-                                                          smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, density_walk_kernel<CAP, K>,
+                                                          kDensWarps * 32, smem);
         if (e != cudaSuccess) return e;
         nb_cached = nb > 0 ? nb : 1;
         configured = true;
@@ -629,42 +623,74 @@ static cudaError_t configure_density(int &blocks)
 }
 
 // resident blocks per SM of the list kernel for 1, 2, 4 and 8 warps per block
-static int g_dens_list_blocks[4];
-
-static cudaError_t configure_density_list()
+template <int K>
+static cudaError_t configure_density_list(int blocks[4])
 {
     static bool configured = false;
-    if (configured) return cudaSuccess;
-    for (int w = 0; w < 4; ++w) {
-        int nb = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, density_list_kernel, 32 << w, 0);
-        if (e != cudaSuccess) return e;
-        g_dens_list_blocks[w] = nb > 0 ? nb : 1;
+    static int nb_cached[4];
+    if (!configured) {
+        for (int w = 0; w < 4; ++w) {
+            int nb = 0;
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, density_list_kernel<K>,
+                                                                          32 << w, 0);
+            if (e != cudaSuccess) return e;
+            nb_cached[w] = nb > 0 ? nb : 1;
+        }
+        configured = true;
     }
-    configured = true;
+    for (int w = 0; w < 4; ++w) blocks[w] = nb_cached[w];
     return cudaSuccess;
 }
 
-template <int CAP>
+template <int CAP, int K>
 static cudaError_t launch_density_walk(Ctx &c, const DensArgs &a, cudaStream_t st)
 {
     int blocks = 1;
-    cudaError_t e = configure_density<CAP>(blocks);
+    cudaError_t e = configure_density<CAP, K>(blocks);
     if (e != cudaSuccess) return e;
     size_t smem = sizeof(DensSmem<CAP>) * kDensWarps;
-    density_walk_kernel<CAP><<<c.num_sms * blocks, kDensWarps * 32, smem, st>>>(a);
+    density_walk_kernel<CAP, K><<<c.num_sms * blocks, kDensWarps * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t configure_density_kernels()
+template <int K>
+static cudaError_t configure_density_k()
 {
-    int b;
-    cudaError_t e = configure_density_list();
-    if (e == cudaSuccess) e = configure_density<64>(b);
-    if (e == cudaSuccess) e = configure_density<80>(b);
-    if (e == cudaSuccess) e = configure_density<96>(b);
-    if (e == cudaSuccess) e = configure_density<128>(b);
+    int b, bl[4];
+    cudaError_t e = configure_density_list<K>(bl);
+    if (e == cudaSuccess) e = configure_density<64, K>(b);
+    if (e == cudaSuccess) e = configure_density<80, K>(b);
+    if (e == cudaSuccess) e = configure_density<96, K>(b);
+    if (e == cudaSuccess) e = configure_density<128, K>(b);
     return e;
+}
+
+cudaError_t configure_density_kernels(int kernel)
+{
+    return kernel == 1 ? configure_density_k<1>() : kernel == 2 ? configure_density_k<2>()
+                                                                : configure_density_k<0>();
+}
+
+// the list kernel, then the walking kernel for the batches it handed over
+template <int K>
+static cudaError_t density_solve_k(Ctx &c, DensArgs &a, const sph_params &p, cudaStream_t st)
+{
+    int bl[4];
+    cudaError_t e = configure_density_list<K>(bl);
+    if (e != cudaSuccess) return e;
+    const PairShape ps = pair_shape(p);
+    a.tb = ps.targets;
+    const int wl = ps.warps == 8 ? 3 : ps.warps == 4 ? 2 : ps.warps == 2 ? 1 : 0;
+    density_list_kernel<K><<<c.num_sms * bl[wl], 32 * ps.warps, 0, st>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // default tile: the mean density set (about 58 for M4 at hfact 1.2, 82 for
+    // M6 at 0.9, 74 for Wendland C6 at 1.3) with room to spare
+    int cap = p.tile > 0 ? p.tile : K == 0 ? 80 : 128;
+    if (cap <= 64) return launch_density_walk<64, K>(c, a, st);
+    if (cap <= 80) return launch_density_walk<80, K>(c, a, st);
+    if (cap <= 96) return launch_density_walk<96, K>(c, a, st);
+    return launch_density_walk<128, K>(c, a, st);
 }
 
 cudaError_t density_lists(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st,
@@ -719,19 +745,9 @@ cudaError_t density_solve(Ctx &c, const sph_state &s, const sph_params &p, cudaS
     static_assert(SZ_FALLBACK == SZ_WORK + 1 && SZ_WORK2 == SZ_WORK + 2, "work counters adjacent");
     cudaError_t e = cudaMemsetAsync(a.work, 0, 3 * sizeof(int), st);
     if (e != cudaSuccess) return e;
-    e = configure_density_list();
-    if (e != cudaSuccess) return e;
-    const PairShape ps = pair_shape(p);
-    a.tb = ps.targets;
-    const int wl = ps.warps == 8 ? 3 : ps.warps == 4 ? 2 : ps.warps == 2 ? 1 : 0;
-    density_list_kernel<<<c.num_sms * g_dens_list_blocks[wl], 32 * ps.warps, 0, st>>>(a);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    int cap = p.tile > 0 ? p.tile : 80;
-    if (cap <= 64) return launch_density_walk<64>(c, a, st);
-    if (cap <= 80) return launch_density_walk<80>(c, a, st);
-    if (cap <= 96) return launch_density_walk<96>(c, a, st);
-    return launch_density_walk<128>(c, a, st);
+    if (p.kernel == 1) return density_solve_k<1>(c, a, p, st);
+    if (p.kernel == 2) return density_solve_k<2>(c, a, p, st);
+    return density_solve_k<0>(c, a, p, st);
 }
 
 cudaError_t density_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st,
@@ -755,7 +771,8 @@ cudaError_t list_sets(Ctx &c, const sph_state &s, const sph_params &p, int mode,
     e = cudaMemsetAsync(missing, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     const int grid = c.num_sms * 8;
-    list_set_kernel<<<grid, 256, 0, st>>>((const float4 *)s.pos, s.h, c.nl_idx, c.nl_len, n, mode,
+    const float kr = kernel_support(p.kernel);
+    list_set_kernel<<<grid, 256, 0, st>>>((const float4 *)s.pos, s.h, c.nl_idx, c.nl_len, n, mode, kr,
                                           d_off, nullptr, missing);
     scan_i64_kernel<<<1, 1024, 0, st>>>(d_off, n);
     e = cudaMemcpyAsync(h_total, d_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
@@ -765,7 +782,7 @@ cudaError_t list_sets(Ctx &c, const sph_state &s, const sph_params &p, int mode,
     *h_missing = c.h_pinned[4];
     if (d_idx && *h_total <= cap) {
         list_set_kernel<<<grid, 256, 0, st>>>((const float4 *)s.pos, s.h, c.nl_idx, c.nl_len, n, mode,
-                                              d_off, d_idx, missing);
+                                              kr, d_off, d_idx, missing);
         e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return e;
     }
@@ -776,8 +793,8 @@ cudaError_t neighbour_lists(Ctx &c, const sph_state &s, const sph_params &p, int
                             int64_t *d_off, int32_t *d_idx, int64_t cap, int64_t *h_total,
                             cudaStream_t st)
 {
-    (void)p;
     NbrArgs a{};
+    a.kr = kernel_support(p.kernel);
     a.pos = (const float4 *)s.pos;
     a.h = s.h;
     a.grp_ref = c.tree.grp_ref;

@@ -1,7 +1,9 @@
 // Hydro force pass (Sect. 2.4-2.6, Eqs. 9-15), no gravity.
 //
-// The pair set of a particle is every j with r_ij < 2 max(h_i, h_j): a pair is
-// found whenever either particle reaches the other (Sect. 3.2).
+// The pair set of a particle is every j with r_ij < R max(h_i, h_j), R the
+// support radius of the kernel in units of h: a pair is found whenever either
+// particle reaches the other (Sect. 3.2).  The pair kernels are templates on
+// the smoothing kernel K (SphKernel<K>).
 //
 // force_list_kernel: one warp per batch of up to 8 targets of a group, L
 // lanes per target, reading each target's neighbour list from the density
@@ -9,11 +11,12 @@
 // applying the exact test with the canonical FP32 distance.  Batches whose
 // lists are unusable (overflowed, stale, or an h of the instance outgrew the
 // pad) go to force_walk_kernel, which walks the tree: it opens a node if its
-// box is within 2 max(h_max(group), h_max(node)) of the group box, tests
+// box is within R max(h_max(group), h_max(node)) of the group box, tests
 // each candidate chunk against every target and compacts the hits with
 // ballots into per-target lists in shared memory; the pair arithmetic then
 // runs over those lists with L lanes per target, flushing whenever a list
 // could overflow.
+#include "kernels.cuh"
 #include "walk.cuh"
 
 namespace sph {
@@ -55,17 +58,10 @@ struct ForceArgs {
     unsigned long long *counters;
 };
 
-// f'(q) of the M4 kernel without branches (q >= 0; q >= 2 gives 0)
-__device__ __forceinline__ float m4_df_sel(float q)
-{
-    const float inner = q * (-3.f + 2.25f * q);
-    const float t = fmaxf(2.f - q, 0.f);
-    return q < 1.f ? inner : -0.75f * t * t;
-}
-
 // Per-target state of the pair sums: the target's constants and the
 // accumulated acceleration (Eq. 9 with Eq. 13), the three du/dt terms
 // (Eqs. 10, 14, 15) and the signal-velocity maximum (Eq. 12).
+template <int K>
 struct ForceTarget {
     float4 xi, vi, qi;  // x, m / v, u / h, rho, A = 1/(rho Omega), c
     float hinv_i, cf_i, Pi, pres_i;
@@ -76,7 +72,7 @@ struct ForceTarget {
     {
         xi = x; vi = v; qi = q;
         hinv_i = 1.f / qi.x;
-        cf_i = kCNorm * hinv_i * hinv_i * hinv_i * hinv_i;  // F_i = f'(q_i) C / h_i^4
+        cf_i = SphKernel<K>::C * hinv_i * hinv_i * hinv_i * hinv_i;  // F_i = f'(q_i) C / h_i^4
         pres_i = a.gm1 * vi.w;  // P_i / rho_i
         Pi = pres_i * qi.y;      // formed as P_j is
         ax = ay = az = dup = duav = duc = 0.f;
@@ -104,8 +100,8 @@ struct ForceTarget {
         const float r = r2 * rinv;
         const float hinv_j = __fdividef(1.f, qj.x);
         const float hinv2_j = hinv_j * hinv_j;
-        const float Fi = m4_df_sel(r * hinv_i) * cf_i;
-        const float Fj = kCNorm * m4_df_sel(r * hinv_j) * hinv2_j * hinv2_j;
+        const float Fi = SphKernel<K>::df(r * hinv_i) * cf_i;
+        const float Fj = SphKernel<K>::C * SphKernel<K>::df(r * hinv_j) * hinv2_j * hinv2_j;
         const float vr = ((vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz) * rinv;
         const float avr = fabsf(vr);
         const float vsi = a.alpha * ci + a.beta * avr;
@@ -152,13 +148,12 @@ struct ForceTarget {
 
 // Pair sums of the list kernel for one target, written for few instructions
 // per pair with the per-particle factors taken from the force records:
-//   F(r, h) = C f'(q) / h^4 = -3 C / h^4 g(q / 2),
-//   g(p) = max(1 - p, 0)^2 - max(1 - 2 p, 0)^2
-// (f'(q) = -3 q + 9/4 q^2 for q < 1, -3/4 (2 - q)^2 for 1 <= q < 2, 0 beyond:
-// the M4 derivative), with q / 2 = r / (2 h) = r rsqrt((2 h)^2).  With
-// A = 1 / (rho Omega) and AK = -3 C A / h^4, A F = AK g.  A neighbour is
-// one 48-byte record (three 16-byte loads from one address):
-// (x, y, z, m), (vx, vy, vz, (gamma - 1) u), ((2 h)^2, AK, alpha c, rho).
+//   F(r, h) = C f'(q) / h^4 = G C / h^4 g_p(p),  p = q / R = r rsqrt((R h)^2)
+// (for M4, G = -3 and g_p(p) = max(1 - p, 0)^2 - max(1 - 2 p, 0)^2: the
+// derivative -3 q + 9/4 q^2 for q < 1, -3/4 (2 - q)^2 for 1 <= q < 2, 0
+// beyond).  With A = 1 / (rho Omega) and AK = G C A / h^4, A F = AK g_p.  A
+// neighbour is one 48-byte record (three 16-byte loads from one address):
+// (x, y, z, m), (vx, vy, vz, (gamma - 1) u), ((R h)^2, AK, alpha c, rho).
 // The L1 data path is what bounds this kernel: the gathers deliver about
 // 48 bytes per wavefront, so the record holds only what the pair needs.
 // Per pair
@@ -167,9 +162,10 @@ struct ForceTarget {
 //   du/dt terms: sum m_j vr g_i, sum m_j vsig_i hw^2 g_i and the conduction
 //   sum m_j |dP| rsqrt(|dP| (rho_i + rho_j)) (P_i/rho_i - P_j/rho_j) (AK_i g_i + AK_j g_j),
 // whose constant factors are applied once per target at the end.
+template <int K>
 struct ForceSums {
     float xi, yi, zi, vxi, vyi, vzi, pri;   // position, velocity, (gamma - 1) u
-    float R2i, AKi, aci, rhoi, Pi;          // (2 h)^2, AK, alpha c, rho, P
+    float R2i, AKi, aci, rhoi, Pi;          // (R h)^2, AK, alpha c, rho, P
     float ax, ay, az, sp, sv, sc, vsmax;
     int cnt;
 
@@ -193,15 +189,13 @@ struct ForceSums {
         // canonical separation: decides the pair set, feeds the pair terms
         const float dx = __fsub_rn(xi, p.x), dy = __fsub_rn(yi, p.y), dz = __fsub_rn(zi, p.z);
         const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
-        // r < 2 max(h_i, h_j) as r^2 < max((2 h_i)^2, (2 h_j)^2): squaring is monotone
+        // r < R max(h_i, h_j) as r^2 < max((R h_i)^2, (R h_j)^2): squaring is monotone
         const bool in = valid && r2 > 0.f && r2 < fmaxf(R2i, q.x);
         const float mj = in ? p.w : 0.f;
         const float rinv = rsqrtf(fmaxf(r2, 1e-30f));
         const float r = r2 * rinv;
-        const float pi = r * rsqrtf(R2i), pj = r * rsqrtf(q.x);   // q / 2 of each side
-        const float ti = fmaxf(1.f - pi, 0.f), si = fmaxf(fmaf(-2.f, pi, 1.f), 0.f);
-        const float tj = fmaxf(1.f - pj, 0.f), sj = fmaxf(fmaf(-2.f, pj, 1.f), 0.f);
-        const float gi = fmaf(ti, ti, -si * si), gj = fmaf(tj, tj, -sj * sj);
+        const float pi = r * rsqrtf(R2i), pj = r * rsqrtf(q.x);   // q / R of each side
+        const float gi = SphKernel<K>::g_p(pi), gj = SphKernel<K>::g_p(pj);
         const float Ti = AKi * gi, Tj = q.y * gj;
         const float dvx = vxi - v.x, dvy = vyi - v.y, dvz = vzi - v.z, dpr = pri - prj;
         const float vr = fmaf(dvz, dz, fmaf(dvy, dy, dvx * dx)) * rinv;
@@ -250,7 +244,7 @@ struct ForceSums {
 // Launch shape (run-time): a.tb targets per batch (32 / a.tb lanes per
 // target), blockDim.x / 32 warps per block; NPER list entries per lane and
 // iteration.  Registers are capped for 768 resident threads per SM.
-template <int NPER>
+template <int NPER, int K>
 __global__ void __launch_bounds__(256, 3) force_list_kernel(ForceArgs a)
 {
     const int lane = threadIdx.x & 31;
@@ -288,7 +282,7 @@ __global__ void __launch_bounds__(256, 3) force_list_kernel(ForceArgs a)
                     ++n_fb;
                     continue;
                 }
-                ForceSums T;
+                ForceSums<K> T;
                 T.init(a.frec + 3 * (size_t)i);
                 const int *__restrict__ lst = a.nl_idx + (size_t)i * kNbrCap;
                 // Four consecutive entries per lane and iteration (one 16-byte
@@ -343,7 +337,7 @@ __global__ void __launch_bounds__(256, 3) force_list_kernel(ForceArgs a)
 }
 
 // Batches the list kernel handed over, with tree walks.
-template <int CAP>
+template <int CAP, int K>
 __global__ void __launch_bounds__(kForceWarps * 32) force_walk_kernel(ForceArgs a)
 {
     extern __shared__ __align__(16) unsigned char fsm_raw[];
@@ -381,7 +375,7 @@ __global__ void __launch_bounds__(kForceWarps * 32) force_walk_kernel(ForceArgs 
                 }
             }
             __syncwarp();
-            ForceTarget T;
+            ForceTarget<K> T;
             T.init(sm.tp[act ? t : 0], sm.tv[act ? t : 0], sm.tq[act ? t : 0], a);
 
             auto flush = [&]() {
@@ -410,8 +404,8 @@ __global__ void __launch_bounds__(kForceWarps * 32) force_walk_kernel(ForceArgs 
                     base[t0] = base[t1] = 0;
                     if (t0 < nt) {
                         const float2 r2 = canon_r2_x2(sm.tc.x[q], sm.tc.y[q], sm.tc.z[q], pj.x, pj.y, pj.z);
-                        const float R0 = 2.0f * fmaxf(sm.th[t0], hj);
-                        const float R1 = 2.0f * fmaxf(sm.th[t1], hj);
+                        const float R0 = SphKernel<K>::R * fmaxf(sm.th[t0], hj);
+                        const float R1 = SphKernel<K>::R * fmaxf(sm.th[t1], hj);
                         bs[t0] = __ballot_sync(0xffffffffu, j >= 0 && j != i0 + t0 && r2.x < R0 * R0);
                         bs[t1] = __ballot_sync(0xffffffffu, j >= 0 && t1 < nt && j != i0 + t1 && r2.y < R1 * R1);
                         base[t0] = sm.tlen[t0];
@@ -436,7 +430,9 @@ __global__ void __launch_bounds__(kForceWarps * 32) force_walk_kernel(ForceArgs 
                 n_cand += (unsigned long long)nt;
             };
             const int root = a.inst ? a.inst[gr.x] : 0;
-            bool ok = walk_group(a.tree, root, glo, ghi, 0.f, true, glo.w, sm.w, chunk);
+            // opens a node within R max(h_max(group), h_max(node)) of the group box
+            constexpr float hr = 0.5f * SphKernel<K>::R;
+            bool ok = walk_group(a.tree, root, glo, ghi, 0.f, true, hr * glo.w, sm.w, chunk, hr);
             if (!ok && lane == 0) raise_error(a.err, SPH_ERR_TILE_OVERFLOW);
             flush();
             T.finish(L, act && sub == 0, i0 + t, a);
@@ -451,12 +447,13 @@ __global__ void __launch_bounds__(kForceWarps * 32) force_walk_kernel(ForceArgs 
     }
 }
 
-// prop = (h, rho, 1/(rho Omega), c_s) and the force records from the state;
-// checks vel and u
+// prop = (h, rho, 1/(rho Omega), c_s) and the force records from the state
+// (kr = R, gc = G C of the kernel); checks vel and u
 __global__ void force_prep_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ vel,
                                   const float *__restrict__ h, const float *__restrict__ rho,
                                   const float *__restrict__ omega, float4 *__restrict__ prop,
-                                  float4 *__restrict__ frec, int n, float gamma, float alpha, int *err)
+                                  float4 *__restrict__ frec, int n, float gamma, float alpha, float kr,
+                                  float gc, int *err)
 {
     bool bad = false, neg = false;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -468,29 +465,29 @@ __global__ void force_prep_kernel(const float4 *__restrict__ pos, const float4 *
         const float cs = sqrtf(fmaxf(gamma * (gamma - 1.f) * v.w, 0.f));
         const float A = 1.f / (r * o);
         prop[i] = make_float4(hi, r, A, cs);
-        const float R = 2.0f * hi;
+        const float R = kr * hi;
         const float hinv = 1.f / hi, hinv2 = hinv * hinv;
         frec[3 * (size_t)i] = pos[i];
         frec[3 * (size_t)i + 1] = make_float4(v.x, v.y, v.z, (gamma - 1.f) * v.w);
-        frec[3 * (size_t)i + 2] = make_float4(R * R, -3.f * kCNorm * A * hinv2 * hinv2, alpha * cs, r);
+        frec[3 * (size_t)i + 2] = make_float4(R * R, gc * A * hinv2 * hinv2, alpha * cs, r);
     }
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) raise_error(err, SPH_ERR_NONFINITE);
     if (__any_sync(0xffffffffu, neg) && (threadIdx.x & 31) == 0) raise_error(err, SPH_ERR_NEGATIVE_U);
 }
 
 // one-time kernel attributes and occupancy (also called before graph capture)
-template <int CAP>
+template <int CAP, int K>
 static cudaError_t configure_force(int &blocks)
 {
     static bool configured = false;
     static int nb_cached = 1;
     if (!configured) {
         size_t smem = sizeof(ForceSmem<CAP>) * kForceWarps;
-        cudaError_t e = cudaFuncSetAttribute(force_walk_kernel<CAP>,
+        cudaError_t e = cudaFuncSetAttribute(force_walk_kernel<CAP, K>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_walk_kernel<CAP>, kForceWarps * 32,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, force_walk_kernel<CAP, K>, kForceWarps * 32,
                                                           smem);
         if (e != cudaSuccess) return e;
         nb_cached = nb > 0 ? nb : 1;
@@ -502,44 +499,54 @@ static cudaError_t configure_force(int &blocks)
 
 // Resident blocks per SM of the list kernel for each (entries per lane,
 // warps per block): computed once, before any graph capture.
-static int g_force_list_blocks[2][4];
-
-static cudaError_t configure_force_list()
+template <int K>
+static cudaError_t configure_force_list(int blocks[2][4])
 {
     static bool configured = false;
-    if (configured) return cudaSuccess;
+    static int nb_cached[2][4];
+    if (!configured) {
+        for (int u = 0; u < 2; ++u)
+            for (int w = 0; w < 4; ++w) {
+                int nb = 0;
+                const int threads = 32 << w;  // 1, 2, 4, 8 warps
+                cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &nb, u ? force_list_kernel<4, K> : force_list_kernel<2, K>, threads, 0);
+                if (e != cudaSuccess) return e;
+                nb_cached[u][w] = nb > 0 ? nb : 1;
+            }
+        configured = true;
+    }
     for (int u = 0; u < 2; ++u)
-        for (int w = 0; w < 4; ++w) {
-            int nb = 0;
-            const int threads = 32 << w;  // 1, 2, 4, 8 warps
-            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &nb, u ? force_list_kernel<4> : force_list_kernel<2>, threads, 0);
-            if (e != cudaSuccess) return e;
-            g_force_list_blocks[u][w] = nb > 0 ? nb : 1;
-        }
-    configured = true;
+        for (int w = 0; w < 4; ++w) blocks[u][w] = nb_cached[u][w];
     return cudaSuccess;
 }
 
-template <int CAP>
+template <int CAP, int K>
 static cudaError_t launch_force_walk(Ctx &c, const ForceArgs &a, cudaStream_t st)
 {
     int blocks = 1;
-    cudaError_t e = configure_force<CAP>(blocks);
+    cudaError_t e = configure_force<CAP, K>(blocks);
     if (e != cudaSuccess) return e;
     size_t smem = sizeof(ForceSmem<CAP>) * kForceWarps;
-    force_walk_kernel<CAP><<<c.num_sms * blocks, kForceWarps * 32, smem, st>>>(a);
+    force_walk_kernel<CAP, K><<<c.num_sms * blocks, kForceWarps * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t configure_force_kernels()
+template <int K>
+static cudaError_t configure_force_k()
 {
-    int b;
-    cudaError_t e = configure_force_list();
-    if (e == cudaSuccess) e = configure_force<64>(b);
-    if (e == cudaSuccess) e = configure_force<96>(b);
-    if (e == cudaSuccess) e = configure_force<128>(b);
+    int b, bl[2][4];
+    cudaError_t e = configure_force_list<K>(bl);
+    if (e == cudaSuccess) e = configure_force<64, K>(b);
+    if (e == cudaSuccess) e = configure_force<96, K>(b);
+    if (e == cudaSuccess) e = configure_force<128, K>(b);
     return e;
+}
+
+cudaError_t configure_force_kernels(int kernel)
+{
+    return kernel == 1 ? configure_force_k<1>() : kernel == 2 ? configure_force_k<2>()
+                                                              : configure_force_k<0>();
 }
 
 cudaError_t force_prep(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st,
@@ -549,10 +556,37 @@ cudaError_t force_prep(Ctx &c, const sph_state &s, const sph_params &p, cudaStre
     int grid = (n + 255) / 256;
     if (grid > c.num_sms * 16) grid = c.num_sms * 16;
     force_prep_kernel<<<grid, 256, 0, st>>>((const float4 *)s.pos, (const float4 *)s.vel, s.h, s.rho,
-                                            s.omega, c.prop, c.frec, n, p.gamma, p.alpha_av, c.d_err);
+                                            s.omega, c.prop, c.frec, n, p.gamma, p.alpha_av,
+                                            kernel_support(p.kernel), kernel_gc(p.kernel), c.d_err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return hmax_now ? update_hmax(c, s, p, st) : cudaSuccess;
+}
+
+// the list kernel, then the walking kernel for the batches it handed over
+template <int K>
+static cudaError_t force_launch_k(Ctx &c, ForceArgs &a, const sph_params &p, const sph_state &s,
+                                  cudaStream_t st)
+{
+    int bl[2][4];
+    cudaError_t e = configure_force_list<K>(bl);
+    if (e != cudaSuccess) return e;
+    const PairShape ps = pair_shape(p);
+    a.tb = ps.targets;
+    const int u = ps.unroll == 4 ? 1 : 0, wl = ps.warps == 8 ? 3 : ps.warps == 4 ? 2 : ps.warps == 2 ? 1 : 0;
+    const int grid = c.num_sms * bl[u][wl];
+    if (u) force_list_kernel<4, K><<<grid, 32 * ps.warps, 0, st>>>(a);
+    else force_list_kernel<2, K><<<grid, 32 * ps.warps, 0, st>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // the walking kernel needs node and group h_max of the final h; refreshed
+    // only when some batch was handed over
+    e = update_hmax(c, s, p, st, a.n_fallback);
+    if (e != cudaSuccess) return e;
+    int cap = p.tile > 0 ? p.tile : K == 0 ? 96 : 128;
+    if (cap <= 64) return launch_force_walk<64, K>(c, a, st);
+    if (cap <= 96) return launch_force_walk<96, K>(c, a, st);
+    return launch_force_walk<128, K>(c, a, st);
 }
 
 cudaError_t force_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st,
@@ -591,24 +625,9 @@ cudaError_t force_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStre
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(a.work, 0, 3 * sizeof(int), st);  // work, fallback count, work2
     if (e != cudaSuccess) return e;
-    e = configure_force_list();
-    if (e != cudaSuccess) return e;
-    const PairShape ps = pair_shape(p);
-    a.tb = ps.targets;
-    const int u = ps.unroll == 4 ? 1 : 0, wl = ps.warps == 8 ? 3 : ps.warps == 4 ? 2 : ps.warps == 2 ? 1 : 0;
-    const int grid = c.num_sms * g_force_list_blocks[u][wl];
-    if (u) force_list_kernel<4><<<grid, 32 * ps.warps, 0, st>>>(a);
-    else force_list_kernel<2><<<grid, 32 * ps.warps, 0, st>>>(a);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    // the walking kernel needs node and group h_max of the final h; refreshed
-    // only when some batch was handed over
-    e = update_hmax(c, s, p, st, a.n_fallback);
-    if (e != cudaSuccess) return e;
-    int cap = p.tile > 0 ? p.tile : 96;
-    if (cap <= 64) return launch_force_walk<64>(c, a, st);
-    if (cap <= 96) return launch_force_walk<96>(c, a, st);
-    return launch_force_walk<128>(c, a, st);
+    if (p.kernel == 1) return force_launch_k<1>(c, a, p, s, st);
+    if (p.kernel == 2) return force_launch_k<2>(c, a, p, s, st);
+    return force_launch_k<0>(c, a, p, s, st);
 }
 
 }  // namespace sph

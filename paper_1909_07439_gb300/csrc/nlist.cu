@@ -26,6 +26,7 @@
 // is tested against up to 16 targets with the canonical FP32 squared
 // distance (two targets per packed instruction); hits go straight to the
 // lists in global memory.
+#include "kernels.cuh"
 #include "walk.cuh"
 
 namespace sph {
@@ -334,7 +335,8 @@ cudaError_t configure_nlist_kernels()
     return configure_nlist(b);
 }
 
-static NlistArgs nlist_args(Ctx &c, const sph_state &s, float pad, const Batch *batch)
+static NlistArgs nlist_args(Ctx &c, const sph_state &s, const sph_params &p, float pad,
+                            const Batch *batch)
 {
     NlistArgs a{};
     a.pos = (const float4 *)s.pos;
@@ -346,7 +348,7 @@ static NlistArgs nlist_args(Ctx &c, const sph_state &s, float pad, const Batch *
     a.work = c.d_sizes + SZ_WORK;
     a.tree = WalkTree{c.tree.node_lo, c.tree.node_hi, c.tree.node_ref};
     a.inst = batch ? c.inst : nullptr;
-    a.rscale = 2.f * (1.f + pad) * kListSlack;
+    a.rscale = kernel_support(p.kernel) * (1.f + pad) * kListSlack;
     a.idx = c.nl_idx;
     a.len = c.nl_len;
     a.err = c.d_err;
@@ -357,11 +359,10 @@ static NlistArgs nlist_args(Ctx &c, const sph_state &s, float pad, const Batch *
 cudaError_t nlist_pass(Ctx &c, const sph_state &s, const sph_params &p, float pad, cudaStream_t st,
                        const Batch *batch)
 {
-    (void)p;
     int blocks = 1;
     cudaError_t e = configure_nlist(blocks);
     if (e != cudaSuccess) return e;
-    NlistArgs a = nlist_args(c, s, pad, batch);
+    NlistArgs a = nlist_args(c, s, p, pad, batch);
     e = cudaMemsetAsync(a.work, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
     nlist_kernel<<<c.num_sms * blocks, kNlWarps * 32, 0, st>>>(a);
@@ -378,7 +379,7 @@ cudaError_t relist_pass(Ctx &c, const sph_state &s, const sph_params &p, float p
     // node and group h_max of the final h (the list walk's opening test)
     e = update_hmax(c, s, p, st, any);
     if (e != cudaSuccess) return e;
-    NlistArgs a = nlist_args(c, s, pad, batch);
+    NlistArgs a = nlist_args(c, s, p, pad, batch);
     a.gate = any;
     a.only_bad = c.tree.rec_bad;
     e = cudaMemsetAsync(a.work, 0, sizeof(int), st);

@@ -18,7 +18,7 @@ const char *status_text(sph_status s)
     case SPH_ERR_CUDA: return "CUDA error";
     case SPH_ERR_NOMEM: return "out of memory or tree capacity exceeded";
     case SPH_ERR_NOT_CONVERGED: return "h-rho Newton iteration did not converge";
-    case SPH_ERR_TILE_OVERFLOW: return "tree-walk stack overflow";
+    case SPH_ERR_TILE_OVERFLOW: return "tree-walk stack or neighbour-list overflow";
     case SPH_ERR_NONFINITE: return "non-finite or non-positive input (pos, vel, m, h)";
     case SPH_ERR_NEGATIVE_U: return "negative internal energy";
     case SPH_ERR_TIMEOUT: return "device wait timed out";
@@ -120,7 +120,8 @@ sph_status check_params(Ctx &c, const sph_params *p)
     if (!(p->gamma > 1.f) || !(p->hfact > 0.f) || !(p->h_tol > 0.f) || !(p->c_cour > 0.f) ||
         !(p->alpha_av >= 0.f) || !(p->beta_av >= 0.f) || !(p->alpha_u >= 0.f))
         return fail(c, SPH_ERR_INVALID_ARG, "parameter out of range");
-    if (p->kernel != 0) return fail(c, SPH_ERR_INVALID_ARG, "only the M4 kernel (0) is built");
+    if (p->kernel < 0 || p->kernel > 2)
+        return fail(c, SPH_ERR_INVALID_ARG, "kernel must be 0 (M4), 1 (M6) or 2 (Wendland C6)");
     if (p->n_leaf < 1 || p->n_leaf > 64 || p->n_group < 1 || p->n_group > 32)
         return fail(c, SPH_ERR_INVALID_ARG, "n_leaf must be 1..64 and n_group 1..32");
     if (p->tile < 0 || p->tile > 128 || p->max_h_iter < 1 || p->density_iters < 0)
@@ -258,8 +259,8 @@ sph_status record_step_graph(Ctx &c, Ctx::StepGraph &g, const sph_state &s, cons
                              float *d_dt, double *d_time, const HostOut *out)
 {
     free_step_graph(g);
-    CK(configure_density_kernels(), "configure density");
-    CK(configure_force_kernels(), "configure force");
+    CK(configure_density_kernels(p.kernel), "configure density");
+    CK(configure_force_kernels(p.kernel), "configure force");
     CK(configure_nlist_kernels(), "configure lists");
     if (!c.capture_stream)
         CK(cudaStreamCreateWithFlags(&c.capture_stream, cudaStreamNonBlocking), "capture stream");
@@ -388,7 +389,7 @@ sph_status sph_create(sph_ctx **out, int64_t max_n, int device)
     A(dalloc(t.grp_ref, t.cap_groups));
     A(dalloc(t.grp_lo, t.cap_groups));
     A(dalloc(t.grp_hi, t.cap_groups));
-    A(dalloc(c.nl_idx, n * kNbrCap));  // 512 B per particle
+    A(dalloc(c.nl_idx, n * kNbrCap));  // 768 B per particle
     A(dalloc(c.nl_len, n));
     A(dalloc(c.fallback, n));
     A(dalloc(t.rec_ctl, 2));
@@ -732,8 +733,8 @@ sph_status sph_batch_step(sph_ctx *h, sph_state *s, const int64_t *d_offsets, in
             cudaGraphExecDestroy(c.batch_graph);
             c.batch_graph = nullptr;
         }
-        CK(configure_density_kernels(), "configure density");
-        CK(configure_force_kernels(), "configure force");
+        CK(configure_density_kernels(p->kernel), "configure density");
+        CK(configure_force_kernels(p->kernel), "configure force");
         CK(configure_nlist_kernels(), "configure lists");
         // record on a private stream: the caller's may be the legacy default
         // stream, which cannot be captured

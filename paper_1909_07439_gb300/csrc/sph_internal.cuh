@@ -17,8 +17,11 @@ constexpr int kLevels = 22;          // levels 0..21
 constexpr int kWarp = 32;
 constexpr int kMaxInstances = 65536;  // instances in one batch
 constexpr int kRsSlots = 14;         // radix passes of one sort at most (4 + 8 + 2)
-constexpr int kNbrCap = 128;          // neighbour-list entries per particle
-constexpr float kCNorm = 0.318309886183790671538f;  // M4, 3D: 1/pi
+// Neighbour-list entries per particle: about twice the mean list length of
+// every kernel at its usual hfact (list radius (1 + pad) R max(h_i, h_j):
+// about 63 entries for M4 at hfact 1.2, 90 for M6 at 0.9, 80 for Wendland C6
+// at 1.3); a multiple of 4 for the 16-byte list loads
+constexpr int kNbrCap = 192;
 constexpr float kListPad = 0.03f;    // neighbour-list radius margin, relative to h
 
 // stage ids for the per-stage timers
@@ -233,8 +236,10 @@ cudaError_t force_prep(Ctx &c, const sph_state &s, const sph_params &p, cudaStre
                        bool hmax_now = false);
 cudaError_t force_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st,
                        const Batch *batch = nullptr);
-cudaError_t configure_density_kernels();
-cudaError_t configure_force_kernels();
+// kernel attributes and occupancy of the pair kernels of smoothing kernel
+// `kernel` (before any graph capture)
+cudaError_t configure_density_kernels(int kernel);
+cudaError_t configure_force_kernels(int kernel);
 // integrate.cu
 // with a batch, d_dt and d_time hold one value per instance
 cudaError_t kick_drift(Ctx &c, const sph_state &s, const float *d_dt, cudaStream_t st,

@@ -15,11 +15,12 @@ interact with one of its own:
    each round one all-reduce of P - 1 counts;
 3. particles move to their owners by point-to-point messages;
 4. halo selection: particle j of rank r goes to rank q if
-   dist(x_j, box_q) < 2 max(h_max,q, h_j) (1 + pad), box_q and h_max,q the
-   bounding box and largest h of q's own particles.  Every j with
-   |x_i - x_j| < 2 max(h_i, h_j) for some i of q satisfies it, since
+   dist(x_j, box_q) < R max(h_max,q, h_j) (1 + pad), box_q and h_max,q the
+   bounding box and largest h of q's own particles, R the kernel's support
+   radius in units of h (2 for M4 and Wendland C6, 3 for M6).  Every j with
+   |x_i - x_j| < R max(h_i, h_j) for some i of q satisfies it, since
    dist(x_j, box_q) <= |x_i - x_j|: the halo holds the density sets
-   (r < 2 h_i, Eq. 1) and the force sets (r < 2 max(h_i, h_j), Sect. 3.2) of
+   (r < R h_i, Eq. 1) and the force sets (r < R max(h_i, h_j), Sect. 3.2) of
    q's particles as long as no h grows by more than the pad;
 5. after the density pass the owners send h, rho and Omega of their halo
    particles (the force pass needs them, Eqs. 9-15), and an all-reduced flag
@@ -183,6 +184,7 @@ class Domain:
     box_hi: np.ndarray
     h_max: float
     pad: float
+    support: float = 2.0
 
 
 def _pack(pos, vel, h, gid):
@@ -202,9 +204,10 @@ def box_distance(x: np.ndarray, lo: np.ndarray, hi: np.ndarray) -> np.ndarray:
     return np.sqrt(np.sum(d * d, axis=1))
 
 
-def decompose(pos, vel, h, gid, pad=0.03, group=None) -> Domain:
+def decompose(pos, vel, h, gid, pad=0.03, group=None, support=2.0) -> Domain:
     """Redistribute this rank's particles (any initial split) into the
-    equal-count Morton ranges and attach the halo."""
+    equal-count Morton ranges and attach the halo (support: the kernel's
+    support radius in units of h)."""
     import torch.distributed as dist
     rank, size = dist.get_rank(group), dist.get_world_size(group)
     pos = np.asarray(pos, np.float32)
@@ -223,10 +226,10 @@ def decompose(pos, vel, h, gid, pad=0.03, group=None) -> Domain:
     keys = morton_keys(pos, lo, ext)
     order = np.lexsort((gid, keys))
     pos, vel, h, gid, keys = pos[order], vel[order], h[order], gid[order], keys[order]
-    return attach_halo(pos, vel, h, gid, keys, pad, group)
+    return attach_halo(pos, vel, h, gid, keys, pad, group, support)
 
 
-def attach_halo(pos, vel, h, gid, keys, pad=0.03, group=None) -> Domain:
+def attach_halo(pos, vel, h, gid, keys, pad=0.03, group=None, support=2.0) -> Domain:
     """Select and exchange the halo of owned particles (pos ... keys) with
     the rule of the module docstring."""
     import torch
@@ -245,7 +248,7 @@ def attach_halo(pos, vel, h, gid, keys, pad=0.03, group=None) -> Domain:
             send.append(np.zeros(0))
             continue
         b = allb[q].numpy()
-        reach = 2.0 * np.maximum(b[6], h.astype(np.float64)) * (1.0 + pad)
+        reach = support * np.maximum(b[6], h.astype(np.float64)) * (1.0 + pad)
         sel = box_distance(x, b[0:3], b[3:6]) < reach
         send.append(_pack(pos[sel], vel[sel], h[sel], gid[sel]).ravel())
     recv = _exchange(send, group)
@@ -258,7 +261,7 @@ def attach_halo(pos, vel, h, gid, keys, pad=0.03, group=None) -> Domain:
     cat = lambda own, extra: np.concatenate([own] + extra) if extra else own
     return Domain(pos=cat(pos, hp), vel=cat(vel, hv), h=cat(h, hh), gid=cat(gid, hg), keys=keys,
                   n_own=len(pos), halo_from=cat(np.zeros(0, np.int64), hf), box_lo=box_lo,
-                  box_hi=box_hi, h_max=h_max, pad=pad)
+                  box_hi=box_hi, h_max=h_max, pad=pad, support=support)
 
 
 def refresh_halo(dom: Domain, fields: dict, h_start: np.ndarray, group=None):

@@ -14,6 +14,8 @@ torch = pytest.importorskip("torch")
 from oracle import adjoint_ref as R  # noqa: E402
 
 T = torch.float64
+HFACT = {R.M4: 1.2, R.M6: 0.9, R.WC6: 1.3}
+KERNELS = [R.M4, R.M6, R.WC6]
 
 
 @pytest.fixture(scope="module")
@@ -26,8 +28,8 @@ def lib():
     native.sph_destroy(ctx)
 
 
-def _cloud(n=1500, seed=3):
-    w = inputs.unit_sphere(n, seed=seed, sigma_v=0.3)
+def _cloud(n=1500, seed=3, kernel=R.M4):
+    w = inputs.unit_sphere(n, seed=seed, sigma_v=0.3, hfact=HFACT[kernel])
     rng = np.random.default_rng(seed)
     w.vel[:, 3] *= rng.uniform(0.5, 2.0, n).astype(np.float32)
     return w
@@ -49,17 +51,18 @@ def _check(name, got, ref, tol=1e-3, elem_tol=1e-3):
     assert e_elem < elem_tol, name
 
 
-def test_force_bwd_matches_autograd(lib):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_force_bwd_matches_autograd(lib, kernel):
     native, ctx = lib
     from paper_1909_07439_gb300 import DeviceState
-    w = _cloud()
+    w = _cloud(kernel=kernel)
     x, v, m, u = (w.pos[:, :3].astype(np.float64), w.vel[:, :3].astype(np.float64),
                   w.pos[:, 3].astype(np.float64), w.vel[:, 3].astype(np.float64))
-    d = oracle.density(x, v, m, w.h)
+    d = oracle.density(x, v, m, w.h, hfact=HFACT[kernel], kernel=kernel)
     # both sides use the oracle's h, rho, Omega (rounded to float32) as inputs
     h32, r32, o32 = (d.h.astype(np.float32), d.rho.astype(np.float32), d.omega.astype(np.float32))
     s = DeviceState.from_arrays(w.pos, w.vel, h32)
-    p = native.sph_params_default()
+    p = native.sph_params_default(kernel=kernel, hfact=HFACT[kernel])
     native.sph_build_tree(ctx, s.c, p)
     perm = s.numpy("perm").astype(np.int64)
     s.rho[: s.n] = torch.as_tensor(r32[perm], device="cuda")
@@ -88,8 +91,8 @@ def test_force_bwd_matches_autograd(lib):
     to = torch.tensor(o32, dtype=T, requires_grad=True)
     ta = torch.tensor(1.0, dtype=T, requires_grad=True)
     tm = torch.tensor(w.pos[:, 3], dtype=T)
-    i, j = R.pair_list(tx.detach(), th.detach(), 1.0001)
-    acc, du = R.force(tx, tv, tu, tm, th, tr, to, i, j, alpha=ta)
+    i, j = R.pair_list(tx.detach(), th.detach(), 1.0001, kernel=kernel)
+    acc, du = R.force(tx, tv, tu, tm, th, tr, to, i, j, alpha=ta, kernel=kernel)
     L = (torch.tensor(wgt[:, :3], dtype=T) * acc).sum() + (torch.tensor(wgt[:, 3], dtype=T) * du).sum()
     L.backward()
     _check("dL/dx", orig(gpos)[:, :3], tx.grad.numpy())
@@ -101,12 +104,13 @@ def test_force_bwd_matches_autograd(lib):
     assert abs(gal.item() - float(ta.grad)) <= 1e-3 * abs(float(ta.grad))
 
 
-def test_density_bwd_matches_autograd(lib):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_density_bwd_matches_autograd(lib, kernel):
     native, ctx = lib
     from paper_1909_07439_gb300 import DeviceState
-    w = _cloud(1200, seed=8)
+    w = _cloud(1200, seed=8, kernel=kernel)
     s = DeviceState.from_arrays(w.pos, w.vel, w.h)
-    p = native.sph_params_default()
+    p = native.sph_params_default(kernel=kernel, hfact=HFACT[kernel])
     native.sph_build_tree(ctx, s.c, p)
     native.sph_density(ctx, s.c, p)
     perm = s.numpy("perm").astype(np.int64)
@@ -123,25 +127,26 @@ def test_density_bwd_matches_autograd(lib):
     tx = torch.tensor(w.pos[:, :3], dtype=T, requires_grad=True)
     tm = torch.tensor(w.pos[:, 3], dtype=T)
     h0 = torch.tensor(w.h, dtype=T)
-    i, j = R.pair_list(tx.detach(), h0, 2.6)
-    h, rho, om = R.density(tx, tm, h0, i, j, iters=40)
+    i, j = R.pair_list(tx.detach(), h0, 2.6, kernel=kernel)
+    h, rho, om = R.density(tx, tm, h0, i, j, hfact=HFACT[kernel], iters=40, kernel=kernel)
     L = (torch.tensor(cg[0], dtype=T) * h + torch.tensor(cg[1], dtype=T) * rho +
          torch.tensor(cg[2], dtype=T) * om).sum()
     L.backward()
     _check("density dL/dx", got[:, :3], tx.grad.numpy())
 
 
-def _sedov16():
-    w = inputs.sedov_lattice(16, seed=6)
+def _sedov16(kernel=R.M4):
+    w = inputs.sedov_lattice(16, seed=6, hfact=HFACT[kernel])
     return w, inputs.probe_indices(w.n, 256, seed=7)
 
 
-def test_rollout_gradient_matches_fp64_reference(lib):
+@pytest.mark.parametrize("kernel", [R.M4, R.M6])
+def test_rollout_gradient_matches_fp64_reference(lib, kernel):
     native, ctx = lib
     from paper_1909_07439_gb300 import DeviceState
-    w, probes = _sedov16()
+    w, probes = _sedov16(kernel)
     s = DeviceState.from_arrays(w.pos, w.vel, w.h)
-    p = native.sph_params_default()
+    p = native.sph_params_default(kernel=kernel, hfact=HFACT[kernel])
     d_probes = torch.as_tensor(probes, device="cuda")
     gvel = torch.zeros((w.n, 4), dtype=torch.float32, device="cuda")
     loss, galpha = native.sph_rollout(ctx, s.c, p, 20, 5, d_probes, len(probes), gvel)
@@ -151,7 +156,8 @@ def test_rollout_gradient_matches_fp64_reference(lib):
     u = torch.tensor(w.vel[:, 3], dtype=T, requires_grad=True)
     m = torch.tensor(w.pos[:, 3], dtype=T)
     al = torch.tensor(1.0, dtype=T, requires_grad=True)
-    Lr, dts, _ = R.rollout(x, v, u, m, torch.tensor(w.h, dtype=T), al, 20, torch.tensor(probes))
+    Lr, dts, _ = R.rollout(x, v, u, m, torch.tensor(w.h, dtype=T), al, 20, torch.tensor(probes),
+                           hfact=HFACT[kernel], kernel=kernel)
     Lr.backward()
     assert abs(loss / float(Lr) - 1) < 1e-4
     _check("rollout dL/dv0", g[:, :3], v.grad.numpy())

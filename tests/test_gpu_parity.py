@@ -186,7 +186,7 @@ def test_production_lists_bit_exact(sph, mode, case):
     # of the density pass, shared walks, leaf caps), each filtered by the exact
     # canonical test: the density set (mode 0) or force set (mode 1) bit for bit
     # at the converged h (the production state) and at h shrunk by up to 5 %
-    # per particle (the lists hold at most 128 entries: a larger h could
+    # per particle (the lists hold at most 192 entries: a larger h could
     # overflow them, and then the walking kernels take over)
     native, ctx, torch = sph
     w = CASES[case]

@@ -44,21 +44,24 @@ def _f64(a):
     return np.asarray(a, np.float64)
 
 
-def _worker(rank, ws, port, out):
+def _worker(rank, ws, port, out, kernel):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=ws)
     try:
         w = _case()
         gid = np.arange(w.n)
         mine = gid % ws == rank                       # an arbitrary initial split
-        dom = partition.decompose(w.pos[mine], w.vel[mine], w.h[mine], gid[mine], pad=0.03)
+        hf = HFACT[kernel]
+        h0 = w.h[mine] * np.float32(hf / 1.2)
+        dom = partition.decompose(w.pos[mine], w.vel[mine], h0, gid[mine], pad=0.03,
+                                  support=oracle.SUPPORT[kernel])
         n_own = dom.n_own
         rounds = 0
         while True:                                   # density, halo refresh, re-exchange rule
             rounds += 1
             x, v, m = _f64(dom.pos[:, :3]), _f64(dom.vel[:, :3]), _f64(dom.pos[:, 3])
             h_start = dom.h.astype(np.float64)
-            d = oracle.density(x, v, m, h_start, targets=np.arange(n_own))
+            d = oracle.density(x, v, m, h_start, targets=np.arange(n_own), hfact=hf, kernel=kernel)
             assert d.failures == 0
             halo, outgrew = partition.refresh_halo(
                 dom, {"h": d.h, "rho": d.rho, "omega": d.omega}, h_start)
@@ -66,13 +69,13 @@ def _worker(rank, ws, port, out):
                 break
             own = slice(0, n_own)
             dom = partition.attach_halo(dom.pos[own], dom.vel[own], d.h.astype(np.float32),
-                                        dom.gid[own], dom.keys, pad=dom.pad)
+                                        dom.gid[own], dom.keys, pad=dom.pad, support=dom.support)
             assert rounds < 6
         h = np.concatenate([d.h, halo["h"]])
         rho = np.concatenate([d.rho, halo["rho"]])
         om = np.concatenate([d.omega, halo["omega"]])
         u = _f64(dom.vel[:, 3])
-        f = oracle.force(x, v, m, u, h, rho, om, targets=np.arange(n_own))
+        f = oracle.force(x, v, m, u, h, rho, om, targets=np.arange(n_own), kernel=kernel)
         out[rank] = dict(gid=dom.gid[:n_own].copy(), halo=dom.gid[n_own:].copy(),
                          keys=dom.keys.copy(), h=d.h, rho=d.rho, acc=f.acc, dudt=f.dudt,
                          vsig=f.vsigmax, rounds=rounds)
@@ -80,18 +83,23 @@ def _worker(rank, ws, port, out):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("ws", [2, 3])
-def test_decomposition_matches_single_rank_oracle(ws):
+# smoothing-length factor per kernel: M4, M6 (support 3 h), Wendland C6
+HFACT = {oracle.M4: 1.2, oracle.M6: 0.9, oracle.WC6: 1.3}
+
+
+@pytest.mark.parametrize("ws,kernel", [(2, oracle.M4), (3, oracle.M4), (2, oracle.M6)])
+def test_decomposition_matches_single_rank_oracle(ws, kernel):
     oracle.build()
-    port = 29600 + 10 * ws + os.getpid() % 500
+    port = 29600 + 10 * ws + kernel + os.getpid() % 500
     mgr = mp.Manager()
     out = mgr.dict()
-    mp.spawn(_worker, args=(ws, port, out), nprocs=ws, join=True)
+    mp.spawn(_worker, args=(ws, port, out, kernel), nprocs=ws, join=True)
     w = _case()
+    hf = HFACT[kernel]
     x, v, m, u = _f64(w.pos[:, :3]), _f64(w.vel[:, :3]), _f64(w.pos[:, 3]), _f64(w.vel[:, 3])
-    d = oracle.density(x, v, m, w.h)
-    f = oracle.force(x, v, m, u, d.h, d.rho, d.omega)
-    off, idx = oracle.neighbours(w.pos, d.h.astype(np.float32), 1)
+    d = oracle.density(x, v, m, w.h * np.float32(hf / 1.2), hfact=hf, kernel=kernel)
+    f = oracle.force(x, v, m, u, d.h, d.rho, d.omega, kernel=kernel)
+    off, idx = oracle.neighbours(w.pos, d.h.astype(np.float32), 1, kernel=kernel)
     rs = [out[r] for r in range(ws)]
     # equal-count contiguous ranges of the global (key, id) order, in rank order
     sizes = [len(r["gid"]) for r in rs]
