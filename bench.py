@@ -244,6 +244,8 @@ def run_ours(args):
         p.n_group = args.n_group
     if args.tile:
         p.tile = args.tile
+    if args.pair_shape:
+        p.pair_targets, p.pair_warps, p.pair_unroll = (int(x) for x in args.pair_shape.split(","))
     stream = torch.cuda.current_stream()
     d_dt = torch.zeros(1, dtype=torch.float32, device="cuda")
     d_t = torch.zeros(1, dtype=torch.float64, device="cuda")
@@ -645,6 +647,9 @@ def main():
     ap.add_argument("--n-leaf", type=int, default=0, help="override N_leaf (paper: 16)")
     ap.add_argument("--n-group", type=int, default=0, help="override N_group (paper: 8)")
     ap.add_argument("--tile", type=int, default=0, help="override the neighbour-list tile")
+    ap.add_argument("--pair-shape", default="",
+                    help="override the pair kernels' launch shape: targets,warps,unroll "
+                         "(with --n-leaf/--n-group it replaces the autotuner's choice)")
     ap.add_argument("--batch-instances", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--adjoint-side", type=int, default=64)

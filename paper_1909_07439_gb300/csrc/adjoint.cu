@@ -41,6 +41,7 @@ struct PairWalkArgs {
     // neighbour lists of the last density pass (a superset of both pair sets
     // while they are fresh and no h of the instance outgrew the list pad)
     const int *nl_idx, *nl_len, *rec_ctl, *rec_bad;
+    int nl_stride;
     int *err;
 };
 
@@ -144,7 +145,7 @@ __global__ void __launch_bounds__(128) pairwalk_kernel(PairWalkArgs a, Op op)
             if (lists) {
                 // the pair set from the target's list, with the same exact tests
                 if (act) {
-                    const int *__restrict__ lst = a.nl_idx + (size_t)i * kNbrCap;
+                    const int *__restrict__ lst = a.nl_idx + (size_t)i * a.nl_stride;
                     const float4 tp = sm.tp[t];
                     const float ht = sm.th[t];
                     for (int e = sub; e < len; e += L) {
@@ -553,6 +554,7 @@ static cudaError_t launch_pairwalk(Ctx &c, const sph_state &s, bool dens_set, fl
     a.kr = kr;
     a.nl_idx = c.nl_idx;
     a.nl_len = c.nl_len;
+    a.nl_stride = c.nl_stride;
     a.rec_ctl = c.tree.rec_ctl;
     a.rec_bad = c.tree.rec_bad;
     a.err = c.d_err;
@@ -585,7 +587,8 @@ static cudaError_t force_bwd_k(Ctx &c, const sph_state &s, const sph_params &p, 
     op.alpha_u = p.alpha_u;
     op.gamma = p.gamma;
     // the force-set walk needs node and group h_max of the current h
-    cudaError_t e = update_hmax(c, s, p, st);
+    cudaError_t e = check_list_kernel(c, p, st);
+    if (e == cudaSuccess) e = update_hmax(c, s, p, st);
     if (e != cudaSuccess) return e;
     return launch_pairwalk<96>(c, s, false, SphKernel<K>::R, op, st, nullptr);
 }
@@ -616,7 +619,8 @@ static cudaError_t density_bwd_k(Ctx &c, const sph_state &s, const sph_params &p
     op1.hf3 = p.hfact * p.hfact * p.hfact;
     // pass 2 opens nodes by their h_max (force set) where it walks: refresh it
     // for the current h (unless the caller just did)
-    cudaError_t e = refresh_hmax ? update_hmax(c, s, p, st) : cudaSuccess;
+    cudaError_t e = check_list_kernel(c, p, st);
+    if (e == cudaSuccess && refresh_hmax) e = update_hmax(c, s, p, st);
     if (e != cudaSuccess) return e;
     e = launch_pairwalk<96>(c, s, true, SphKernel<K>::R, op1, st, nullptr);
     if (e != cudaSuccess) return e;

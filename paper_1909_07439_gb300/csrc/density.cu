@@ -57,6 +57,7 @@ struct DensArgs {
     WalkTree tree;
     const int *inst;  // instance of each slot (batches), or nullptr
     const int *nl_idx, *nl_len;
+    int nl_stride;
     int2 *fallback;   // batches handed to the walking kernel
     int *n_fallback;
     int *rec_bad;     // per instance: an h outgrew the pad of the lists
@@ -184,7 +185,7 @@ __global__ void __launch_bounds__(256, 4) density_list_kernel(DensArgs a)
                     push_fallback(a, g, b0, nt);
                     continue;
                 }
-                const int *__restrict__ lst = a.nl_idx + (size_t)i * kNbrCap;
+                const int *__restrict__ lst = a.nl_idx + (size_t)i * a.nl_stride;
                 const float4 xi = a.pos[i], vi = a.vel[i];
                 float h = a.h[i];
                 const float hw = h * a.h_in_scale;  // the lists hold every pair with r < R hw
@@ -570,7 +571,8 @@ __global__ void scan_i64_kernel(int64_t *off, int n)
 // list into *missing); otherwise the rows are written at off[i].
 __global__ void list_set_kernel(const float4 *__restrict__ pos, const float *__restrict__ h,
                                 const int *__restrict__ idx, const int *__restrict__ len, int n,
-                                int mode, float kr, int64_t *off, int32_t *out, int *missing)
+                                int stride, int mode, float kr, int64_t *off, int32_t *out,
+                                int *missing)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int l = len[i];
@@ -586,7 +588,7 @@ __global__ void list_set_kernel(const float4 *__restrict__ pos, const float *__r
         int64_t w = out ? off[i] : 0;
         int cnt = 0;
         for (int e = 0; e < l; ++e) {
-            const int j = idx[(size_t)i * kNbrCap + e];
+            const int j = idx[(size_t)i * stride + e];
             const float4 pj = pos[j];
             const float r2 = canon_r2(pi.x, pi.y, pi.z, pj.x, pj.y, pj.z);
             const float R = mode == 0 ? kr * hi : kr * fmaxf(hi, h[j]);
@@ -705,6 +707,8 @@ cudaError_t density_lists(Ctx &c, const sph_state &s, const sph_params &p, cudaS
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(c.tree.rec_bad, 0, sizeof(int) * (batch ? batch->n_inst : 1), st);
     if (e != cudaSuccess) return e;
+    c.nl_kernel = p.kernel;
+    c.nl_stride = list_cap(p.kernel);
     return nlist_pass(c, s, p, kPad, st, batch);
 }
 
@@ -716,6 +720,7 @@ cudaError_t density_solve(Ctx &c, const sph_state &s, const sph_params &p, cudaS
     a.h_in_scale = 1.f + kPad;
     a.nl_idx = c.nl_idx;
     a.nl_len = c.nl_len;
+    a.nl_stride = c.nl_stride;
     a.fallback = c.fallback;
     a.n_fallback = c.d_sizes + SZ_FALLBACK;
     a.rec_bad = c.tree.rec_bad;
@@ -772,7 +777,8 @@ cudaError_t list_sets(Ctx &c, const sph_state &s, const sph_params &p, int mode,
     if (e != cudaSuccess) return e;
     const int grid = c.num_sms * 8;
     const float kr = kernel_support(p.kernel);
-    list_set_kernel<<<grid, 256, 0, st>>>((const float4 *)s.pos, s.h, c.nl_idx, c.nl_len, n, mode, kr,
+    list_set_kernel<<<grid, 256, 0, st>>>((const float4 *)s.pos, s.h, c.nl_idx, c.nl_len, n,
+                                          c.nl_stride, mode, kr,
                                           d_off, nullptr, missing);
     scan_i64_kernel<<<1, 1024, 0, st>>>(d_off, n);
     e = cudaMemcpyAsync(h_total, d_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
@@ -781,7 +787,8 @@ cudaError_t list_sets(Ctx &c, const sph_state &s, const sph_params &p, int mode,
     if (e != cudaSuccess) return e;
     *h_missing = c.h_pinned[4];
     if (d_idx && *h_total <= cap) {
-        list_set_kernel<<<grid, 256, 0, st>>>((const float4 *)s.pos, s.h, c.nl_idx, c.nl_len, n, mode,
+        list_set_kernel<<<grid, 256, 0, st>>>((const float4 *)s.pos, s.h, c.nl_idx, c.nl_len, n,
+                                              c.nl_stride, mode,
                                               kr, d_off, d_idx, missing);
         e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return e;

@@ -50,6 +50,7 @@ struct ForceArgs {
     WalkTree tree;
     const int *inst;  // instance of each slot (batches), or nullptr
     const int *nl_idx, *nl_len;
+    int nl_stride;
     const int *rec_ctl, *rec_bad;
     int2 *fallback;
     int *n_fallback;
@@ -284,7 +285,7 @@ __global__ void __launch_bounds__(256, 3) force_list_kernel(ForceArgs a)
                 }
                 ForceSums<K> T;
                 T.init(a.frec + 3 * (size_t)i);
-                const int *__restrict__ lst = a.nl_idx + (size_t)i * kNbrCap;
+                const int *__restrict__ lst = a.nl_idx + (size_t)i * a.nl_stride;
                 // Four consecutive entries per lane and iteration (one 16-byte
                 // load of the list, fetched an iteration ahead), no branch: an
                 // entry outside the pair set (or padding) gets zero mass.  The
@@ -597,6 +598,7 @@ cudaError_t force_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStre
     a.inst = batch ? c.inst : nullptr;
     a.nl_idx = c.nl_idx;
     a.nl_len = c.nl_len;
+    a.nl_stride = c.nl_stride;
     a.rec_ctl = c.tree.rec_ctl;
     a.rec_bad = c.tree.rec_bad;
     a.fallback = c.fallback;
@@ -620,6 +622,8 @@ cudaError_t force_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStre
     a.alpha_u = p.alpha_u;
     a.err = c.d_err;
     a.counters = c.d_counters;
+    e = check_list_kernel(c, p, st);
+    if (e != cudaSuccess) return e;
     // lists of instances where an h outgrew the pad are rebuilt at the final h
     e = relist_pass(c, s, p, kListPad, st, batch);
     if (e != cudaSuccess) return e;

@@ -9,7 +9,7 @@
 //   force   (Eqs. 9-15):   r_ij < 2 max(h_i, h_j), both h <= (1 + pad) h_in
 // so the density Newton sweeps and the force pass read lists instead of
 // walking; the few particles that leave the pad (and lists that overflow
-// kNbrCap, or groups whose walk finds more than kSGLeaves leaves) are handed
+// their capacity, or groups whose walk finds more than kSGLeaves leaves) are handed
 // to the walking kernels.
 //
 // Candidates come from the group walk of Sect. 3.2: a leaf is opened for a
@@ -60,6 +60,7 @@ struct NlistArgs {
     WalkTree tree;
     const int *inst;
     float rscale;  // list radius = rscale * max(h_i, h_j)
+    int cap;       // entries per list (and the lists' stride)
     int *idx;
     int *len;
     // relist mode: the kernel returns at once unless *gate != 0, and builds the
@@ -160,7 +161,7 @@ __device__ __forceinline__ int test_chunks(const NlistArgs &a, const NlistSmem &
     int len[TB];
 #pragma unroll
     for (int tt = 0; tt < TB; ++tt) len[tt] = 0;
-    int *const tbase = a.idx + (size_t)i0 * kNbrCap;  // the batch's first list
+    int *const tbase = a.idx + (size_t)i0 * a.cap;  // the batch's first list
     int r = 0;
     int jn = lane < ncand ? slot_particle(sm.runs, r, lane) : -1;
     float4 pn = jn >= 0 ? __ldg(&a.pos[jn]) : make_float4(1e30f, 1e30f, 1e30f, 0.f);
@@ -186,11 +187,11 @@ __device__ __forceinline__ int test_chunks(const NlistArgs &a, const NlistSmem &
             const bool hit1 = r2.y < fmaxf(sm.tr2[t1], rj2);
             const unsigned m0 = __ballot_sync(0xffffffffu, hit0);
             const unsigned m1 = __ballot_sync(0xffffffffu, hit1);
-            // past kNbrCap hits the last entry is overwritten: such a list is
+            // past a.cap hits the last entry is overwritten: such a list is
             // discarded (its length is set to -1) anyway.  Stores kept in L2 (the
             // density pass reads the last groups' lists first).
-            if (hit0) __stcg(tbase + t0 * kNbrCap + min(len[t0] + __popc(m0 & lt), kNbrCap - 1), j);
-            if (hit1) __stcg(tbase + t1 * kNbrCap + min(len[t1] + __popc(m1 & lt), kNbrCap - 1), j);
+            if (hit0) __stcg(tbase + t0 * a.cap + min(len[t0] + __popc(m0 & lt), a.cap - 1), j);
+            if (hit1) __stcg(tbase + t1 * a.cap + min(len[t1] + __popc(m1 & lt), a.cap - 1), j);
             len[t0] += __popc(m0);
             len[t1] += __popc(m1);
         }
@@ -291,10 +292,10 @@ __global__ void __launch_bounds__(kNlWarps * 32, 7) nlist_kernel(NlistArgs a)
                         n_cand += (unsigned long long)nt * (unsigned long long)ncand;
                     }
                     // a group without lists is left to the walking kernels
-                    const bool fits = ok && mlen <= kNbrCap;
+                    const bool fits = ok && mlen <= a.cap;
                     if (lane < nt) {
                         a.len[i0 + lane] = fits ? mlen : -1;
-                        n_entries += (unsigned long long)min(mlen, kNbrCap);
+                        n_entries += (unsigned long long)min(mlen, a.cap);
                         n_over += fits ? 0ull : 1ull;
                     }
                     __syncwarp();
@@ -348,7 +349,9 @@ static NlistArgs nlist_args(Ctx &c, const sph_state &s, const sph_params &p, flo
     a.work = c.d_sizes + SZ_WORK;
     a.tree = WalkTree{c.tree.node_lo, c.tree.node_hi, c.tree.node_ref};
     a.inst = batch ? c.inst : nullptr;
-    a.rscale = kernel_support(p.kernel) * (1.f + pad) * kListSlack;
+    // the radius and capacity of the lists' kernel (a relist keeps them)
+    a.rscale = kernel_support(c.nl_kernel >= 0 ? c.nl_kernel : p.kernel) * (1.f + pad) * kListSlack;
+    a.cap = c.nl_stride;
     a.idx = c.nl_idx;
     a.len = c.nl_len;
     a.err = c.d_err;
@@ -367,6 +370,12 @@ cudaError_t nlist_pass(Ctx &c, const sph_state &s, const sph_params &p, float pa
     if (e != cudaSuccess) return e;
     nlist_kernel<<<c.num_sms * blocks, kNlWarps * 32, 0, st>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t check_list_kernel(Ctx &c, const sph_params &p, cudaStream_t st)
+{
+    if (c.nl_kernel == p.kernel) return cudaSuccess;
+    return cudaMemsetAsync(c.tree.rec_ctl + 1, 0xff, sizeof(int), st);
 }
 
 cudaError_t relist_pass(Ctx &c, const sph_state &s, const sph_params &p, float pad, cudaStream_t st,

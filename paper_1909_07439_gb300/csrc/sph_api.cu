@@ -389,7 +389,7 @@ sph_status sph_create(sph_ctx **out, int64_t max_n, int device)
     A(dalloc(t.grp_ref, t.cap_groups));
     A(dalloc(t.grp_lo, t.cap_groups));
     A(dalloc(t.grp_hi, t.cap_groups));
-    A(dalloc(c.nl_idx, n * kNbrCap));  // 768 B per particle
+    A(dalloc(c.nl_idx, n * kNbrCapMax));  // 768 B per particle
     A(dalloc(c.nl_len, n));
     A(dalloc(c.fallback, n));
     A(dalloc(t.rec_ctl, 2));
@@ -553,6 +553,9 @@ sph_status step_launch(Ctx &c, const sph_state &s, const sph_params &p, float *d
     }
     for (int k = 0; k < ST_N; ++k) c.pending_launches[k] += g->launches[k];
     CK(cudaGraphLaunch(g->exec, st), "step graph launch");
+    // the graph rebuilt the lists for p.kernel
+    c.nl_kernel = p.kernel;
+    c.nl_stride = list_cap(p.kernel);
     return SPH_OK;
 }
 
@@ -756,6 +759,9 @@ sph_status sph_batch_step(sph_ctx *h, sph_state *s, const int64_t *d_offsets, in
         c.batch_graph_key = key;
     }
     for (int k = 0; k < n_steps; ++k) CK(cudaGraphLaunch(c.batch_graph, st), "graph launch");
+    // the graph rebuilt the lists for p->kernel
+    c.nl_kernel = p->kernel;
+    c.nl_stride = list_cap(p->kernel);
     return SPH_OK;
 }
 

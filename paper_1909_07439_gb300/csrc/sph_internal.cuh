@@ -17,11 +17,13 @@ constexpr int kLevels = 22;          // levels 0..21
 constexpr int kWarp = 32;
 constexpr int kMaxInstances = 65536;  // instances in one batch
 constexpr int kRsSlots = 14;         // radix passes of one sort at most (4 + 8 + 2)
-// Neighbour-list entries per particle: about twice the mean list length of
-// every kernel at its usual hfact (list radius (1 + pad) R max(h_i, h_j):
-// about 63 entries for M4 at hfact 1.2, 90 for M6 at 0.9, 80 for Wendland C6
-// at 1.3); a multiple of 4 for the 16-byte list loads
-constexpr int kNbrCap = 192;
+// Neighbour-list entries per particle (also the lists' stride): at least
+// twice the mean list length of the kernel at its usual hfact (list radius
+// (1 + pad) R max(h_i, h_j): about 63 entries for M4 at hfact 1.2, 80 for
+// Wendland C6 at 1.3, 90 for M6 at 0.9); multiples of 4 for the 16-byte list
+// loads.  The list array is allocated for the largest.
+constexpr int kNbrCapMax = 192;
+inline int list_cap(int kernel) { return kernel == 0 ? 128 : 192; }
 constexpr float kListPad = 0.03f;    // neighbour-list radius margin, relative to h
 
 // stage ids for the per-stage timers
@@ -110,18 +112,23 @@ struct Ctx {
 
     Tree tree;
 
-    // Neighbour lists (curve order): particle i owns nl_idx[i * kNbrCap ...],
+    // Neighbour lists (curve order): particle i owns nl_idx[i * nl_stride ...],
     // nl_len[i] entries (-1: none).  Entry j is in i's list if
-    // r_ij < 2 (1 + pad) max(h_i, h_j) at the h the density pass started from.
+    // r_ij < R (1 + pad) max(h_i, h_j) at the h the density pass started from,
+    // R the support radius of kernel nl_kernel, the kernel of the last full
+    // build (-1: none); nl_stride = list_cap(nl_kernel).  A pass with another
+    // kernel treats the lists as stale.
     int *nl_idx = nullptr;
     int *nl_len = nullptr;
+    int nl_stride = 128;
+    int nl_kernel = -1;
     int2 *fallback = nullptr;  // (group, first batch slot) handed to the walk kernels
 
     // per-particle scratch
     float4 *rec = nullptr;    // [2 n]: pos, vel of each particle side by side (32-byte records)
     float4 *prop = nullptr;   // h, rho, 1/(rho Omega), c_s
-    // [n]: the force factors of each particle, read with its record in rec:
-    // ((2 h)^2, -3 C / (h^4 rho Omega), alpha_AV c_s, rho)
+    // [3 n]: the force record of each particle: (x, m), (v, (gamma - 1) u),
+    // ((R h)^2, G C / (h^4 rho Omega), alpha_AV c_s, rho)
     float4 *frec = nullptr;
     float4 *vhalf = nullptr;  // half-step v, u of the leapfrog
     float *bbox = nullptr;    // [8]: lo xyz, size, then scratch
@@ -211,6 +218,9 @@ cudaError_t nlist_pass(Ctx &c, const sph_state &s, const sph_params &p, float pa
 // launches) when no h outgrew its pad.
 cudaError_t relist_pass(Ctx &c, const sph_state &s, const sph_params &p, float pad,
                         cudaStream_t st, const Batch *batch = nullptr);
+// lists built for another kernel than p.kernel are marked stale (the passes
+// then walk the tree)
+cudaError_t check_list_kernel(Ctx &c, const sph_params &p, cudaStream_t st);
 cudaError_t configure_nlist_kernels();
 // density.cu (density_pass = density_lists + density_solve; density_pass
 // expects the node and group h_max of the current h, as build_tree leaves them)

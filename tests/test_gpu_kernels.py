@@ -215,6 +215,33 @@ def test_negative_energy_reported_like_the_oracle(sph):
     native.sph_sync(ctx)          # the error word was cleared
 
 
+def test_lists_of_another_kernel_are_not_used(sph):
+    # density with M4 builds M4 lists (radius 2 h (1 + pad), 128 per row);
+    # a force pass with M6 then walks the tree instead of reading them, and
+    # gives the oracle's M6 force for the state's h, rho, Omega
+    native, ctx, torch = sph
+    w, _, _ = _oracle(oracle.M6)
+    from paper_1909_07439_gb300 import DeviceState
+    s = DeviceState.from_arrays(w.pos, w.vel, w.h)
+    p4 = native.sph_params_default(kernel=oracle.M4, hfact=HFACT[oracle.M6])
+    native.sph_build_tree(ctx, s.c, p4)
+    native.sph_density(ctx, s.c, p4)
+    native.sph_sync(ctx)
+    native.sph_get_stats(ctx)
+    native.sph_force(ctx, s.c, _params(native, oracle.M6))
+    native.sph_sync(ctx)
+    st = native.sph_get_stats(ctx)
+    assert st["force_rewalks"] > 0
+    x, v, m, u = _f64(w)
+    h = s.in_original_order("h").astype(np.float64)
+    rho = s.in_original_order("rho").astype(np.float64)
+    om = s.in_original_order("omega").astype(np.float64)
+    f = oracle.force(x, v, m, u, h, rho, om, kernel=oracle.M6)
+    acc = s.in_original_order("acc")
+    assert np.max(np.abs(acc[:, :3] - f.acc)) <= ACC_TOL * np.max(np.abs(f.acc))
+    assert np.max(np.abs(acc[:, 3] - f.dudt)) <= ACC_TOL * np.max(np.abs(f.dudt))
+
+
 def test_kernel_out_of_range_rejected(sph):
     native, ctx, torch = sph
     w, _, _ = _oracle(oracle.M6)
