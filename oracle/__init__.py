@@ -63,13 +63,14 @@ def _load():
             lib.orc_sort_order.restype = ctypes.c_int
             lib.orc_chop.argtypes = [P, i64, i32, P, P, P, P, P, i64]
             lib.orc_chop.restype = i64
-            lib.orc_neighbour_counts.argtypes = [P, P, i64, ctypes.c_int, P, i64, P, ctypes.c_int]
-            lib.orc_neighbour_lists.argtypes = [P, P, i64, ctypes.c_int, P, i64, P, P, ctypes.c_int]
+            lib.orc_neighbour_counts.argtypes = [P, P, i64, ctypes.c_int, P, i64, P, ctypes.c_int, P]
+            lib.orc_neighbour_lists.argtypes = [P, P, i64, ctypes.c_int, P, i64, P, P, ctypes.c_int,
+                                                P]
             lib.orc_density.argtypes = [P, P, P, i64, P, i64, P, f64, f64, i32, i32,
-                                        P, P, P, P, P, P, ctypes.c_int]
+                                        P, P, P, P, P, P, ctypes.c_int, P]
             lib.orc_density.restype = i64
             lib.orc_force.argtypes = [P, P, P, P, P, P, P, i64, P, i64, f64, f64, f64,
-                                      f64, f64, P, P, P, P, ctypes.c_int]
+                                      f64, f64, P, P, P, P, ctypes.c_int, P]
             lib.orc_conserved.argtypes = [P, P, P, P, i64, P]
             _lib = lib
     return _lib
@@ -77,6 +78,18 @@ def _load():
 
 def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _box(box, dtype):
+    """Periods (Lx, Ly, Lz), 0 for an open axis, as a C array; None: all open."""
+    if box is None:
+        return None
+    b = np.ascontiguousarray(np.asarray(box, dtype).reshape(3))
+    return b if np.any(b > 0) else None
+
+
+def _bptr(b):
+    return None if b is None else _ptr(b)
 
 
 def _f32(a, shape_last=None):
@@ -168,21 +181,23 @@ def chop(sorted_keys, thresh):
 # --------------------------------------------------------------------------
 # Neighbour sets (Sect. 3.2), canonical FP32
 # --------------------------------------------------------------------------
-def neighbours(pos4, h, mode, targets=None, kernel=M4):
-    """CSR (offsets, indices) of the density (mode 0) or force (mode 1) sets."""
+def neighbours(pos4, h, mode, targets=None, kernel=M4, box=None):
+    """CSR (offsets, indices) of the density (mode 0) or force (mode 1) sets;
+    box: periods of the periodic axes (0: open), compared in FP32."""
     pos4 = _f32(pos4, 4)
     h = _f32(h)
+    b = _box(box, np.float32)
     n = pos4.shape[0]
     t = _targets(targets, n)
     cnt = np.zeros(t.size, np.int64)
     lib = _load()
     lib.orc_neighbour_counts(_ptr(pos4), _ptr(h), n, int(mode), _ptr(t), t.size, _ptr(cnt),
-                             int(kernel))
+                             int(kernel), _bptr(b))
     off = np.zeros(t.size + 1, np.int64)
     np.cumsum(cnt, out=off[1:])
     idx = np.zeros(max(1, int(off[-1])), np.int64)
     lib.orc_neighbour_lists(_ptr(pos4), _ptr(h), n, int(mode), _ptr(t), t.size, _ptr(off),
-                            _ptr(idx), int(kernel))
+                            _ptr(idx), int(kernel), _bptr(b))
     return off, idx[: off[-1]]
 
 
@@ -201,9 +216,11 @@ class Density:
 
 
 def density(x, v, m, h0, targets=None, hfact=1.2, tol=1e-12, max_iter=200, fixed_iters=0,
-            kernel=M4):
-    """Solve the h-rho fixed point for each target (FP64, brute force)."""
+            kernel=M4, box=None):
+    """Solve the h-rho fixed point for each target (FP64, brute force);
+    box: periods of the periodic axes (0: open)."""
     x, v, m, h0 = _f64(x), _f64(v), _f64(m), _f64(h0)
+    b = _box(box, np.float64)
     n = m.size
     assert x.shape == (n, 3) and v.shape == (n, 3) and h0.shape == (n,)
     t = _targets(targets, n)
@@ -213,7 +230,7 @@ def density(x, v, m, h0, targets=None, hfact=1.2, tol=1e-12, max_iter=200, fixed
     fails = _load().orc_density(_ptr(x), _ptr(v), _ptr(m), n, _ptr(t), t.size, _ptr(h0),
                                 float(hfact), float(tol), int(max_iter), int(fixed_iters),
                                 _ptr(h), _ptr(rho), _ptr(om), _ptr(dr), _ptr(nngb),
-                                _ptr(iters), int(kernel))
+                                _ptr(iters), int(kernel), _bptr(b))
     return Density(h, rho, om, dr, nngb, iters, int(fails))
 
 
@@ -226,9 +243,11 @@ class Force:
 
 
 def force(x, v, m, u, h, rho, omega, targets=None, gamma=5.0 / 3.0, alpha=1.0, beta=2.0,
-          alpha_u=1.0, vsig_scale=1.0, kernel=M4):
-    """Accelerations, du/dt and max signal speed for each target (FP64)."""
+          alpha_u=1.0, vsig_scale=1.0, kernel=M4, box=None):
+    """Accelerations, du/dt and max signal speed for each target (FP64);
+    box: periods of the periodic axes (0: open)."""
     x, v, m, u, h, rho, omega = (_f64(a) for a in (x, v, m, u, h, rho, omega))
+    b = _box(box, np.float64)
     n = m.size
     t = _targets(targets, n)
     acc = np.zeros((t.size, 3))
@@ -237,7 +256,7 @@ def force(x, v, m, u, h, rho, omega, targets=None, gamma=5.0 / 3.0, alpha=1.0, b
     _load().orc_force(_ptr(x), _ptr(v), _ptr(m), _ptr(u), _ptr(h), _ptr(rho), _ptr(omega), n,
                       _ptr(t), t.size, float(gamma), float(alpha), float(beta),
                       float(alpha_u), float(vsig_scale), _ptr(acc), _ptr(dudt), _ptr(vsig),
-                      _ptr(nf), int(kernel))
+                      _ptr(nf), int(kernel), _bptr(b))
     return Force(acc, dudt, vsig, nf)
 
 
@@ -263,6 +282,8 @@ class Params:
     tol: float = 1e-12
     max_iter: int = 200
     kernel: int = M4
+    box: tuple = None       # periods (Lx, Ly, Lz), 0 for an open axis
+    box_lo: tuple = None    # lower corner of the periodic box (positions wrap into it)
 
 
 @dataclass
@@ -282,12 +303,13 @@ class SphState:
 
 def evaluate(s: SphState, p: Params = Params()):
     """Density solve then force pass at the current state (in place)."""
-    d = density(s.x, s.v, s.m, s.h, hfact=p.hfact, tol=p.tol, max_iter=p.max_iter, kernel=p.kernel)
+    d = density(s.x, s.v, s.m, s.h, hfact=p.hfact, tol=p.tol, max_iter=p.max_iter, kernel=p.kernel,
+                box=p.box)
     if d.failures:
         raise RuntimeError(f"oracle density: {d.failures} targets did not converge")
     s.h, s.rho, s.omega, s.drhodt = d.h, d.rho, d.omega, d.drhodt
     f = force(s.x, s.v, s.m, s.u, s.h, s.rho, s.omega, gamma=p.gamma, alpha=p.alpha,
-              beta=p.beta, alpha_u=p.alpha_u, kernel=p.kernel)
+              beta=p.beta, alpha_u=p.alpha_u, kernel=p.kernel, box=p.box)
     s.acc, s.dudt, s.vsigmax = f.acc, f.dudt, f.vsigmax
     return s
 
@@ -306,7 +328,7 @@ def kdk_step(s: SphState, dt: float, p: Params = Params()):
     """
     vh = s.v + 0.5 * dt * s.acc
     uh = s.u + 0.5 * dt * s.dudt
-    x1 = s.x + dt * vh
+    x1 = wrap_positions(s.x + dt * vh, p)
     v1p = s.v + dt * s.acc
     u1p = s.u + dt * s.dudt
     n = SphState(x=x1, v=v1p, u=u1p, m=s.m, h=s.h)
@@ -314,6 +336,21 @@ def kdk_step(s: SphState, dt: float, p: Params = Params()):
     n.v = vh + 0.5 * dt * n.acc
     n.u = uh + 0.5 * dt * n.dudt
     return n
+
+
+def wrap_positions(x, p: Params):
+    """Positions moved back into the periodic box [lo, lo + L) on each
+    periodic axis (x - L above it, x + L below it)."""
+    if p.box is None:
+        return x
+    x = np.array(x, np.float64, copy=True)
+    for a in range(3):
+        L = float(p.box[a])
+        if L > 0:
+            lo = float(p.box_lo[a]) if p.box_lo is not None else 0.0
+            x[:, a] = np.where(x[:, a] >= lo + L, x[:, a] - L, x[:, a])
+            x[:, a] = np.where(x[:, a] < lo, x[:, a] + L, x[:, a])
+    return x
 
 
 def total_energy(s: SphState):

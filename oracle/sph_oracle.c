@@ -17,6 +17,13 @@
  *
  * Targets are processed independently (OpenMP over targets); each target's
  * sum runs over j = 0..n-1 in ascending order.
+ *
+ * Periodic boundaries (the Sod and blast tube tests of Sect. 4.1-4.2 are
+ * periodic in y and z): `box` gives the period L of each axis, 0 for an open
+ * axis (box = NULL: all open).  A pair's separation along a periodic axis is
+ * the nearest image: d = x_i - x_j, then d - L if d > L/2, d + L if d < -L/2
+ * (positions lie in one period, so |d| < L and one correction suffices; the
+ * support radius must stay below L/2 so that a pair meets one image only).
  */
 #include <math.h>
 #include <stdint.h>
@@ -91,6 +98,35 @@ static double shape_df(int kernel, double q) /* df/dq */
 }
 
 /* W(r, h) */
+/* nearest-image separation along one axis (L = 0: open axis) */
+static double wrap_d(double d, double L)
+{
+    if (L > 0.0) {
+        if (d > 0.5 * L) d -= L;
+        else if (d < -0.5 * L) d += L;
+    }
+    return d;
+}
+
+/* the same in FP32: with L/2 <= |d| < L the correction is exact (Sterbenz) */
+static float wrap_f(float d, float L)
+{
+    if (L > 0.0f) {
+        if (d > 0.5f * L) d = d - L;
+        else if (d < -0.5f * L) d = d + L;
+    }
+    return d;
+}
+
+/* separation x_i - x_j (3 components) with nearest images */
+static void sep3(const double *x, int64_t i, int64_t j, const double *box, double *d)
+{
+    for (int a = 0; a < 3; ++a) {
+        d[a] = x[3 * i + a] - x[3 * j + a];
+        if (box) d[a] = wrap_d(d[a], box[a]);
+    }
+}
+
 static double kern_w(int k, double r, double h) { return kern_norm(k) * shape_f(k, r / h) / (h * h * h); }
 /* F(r, h) = C f'(q) / h^4 = dW/dr (Eq. 14); grad_i W_ij(h) = rhat_ij F(r_ij, h) */
 static double kern_F(int k, double r, double h)
@@ -233,7 +269,8 @@ ORC_API int64_t orc_chop(const uint64_t *skeys, int64_t n, int32_t thresh,
 
 /* ------------------------------------------------------------------------- */
 /* Neighbour sets (Sect. 3.2), canonical FP32 membership test:               */
-/*   dx = x_i - x_j (per axis), r2 = (dx*dx + dy*dy) + dz*dz                 */
+/*   dx = x_i - x_j (per axis, then the nearest image on a periodic axis),    */
+/*   r2 = (dx*dx + dy*dy) + dz*dz                                            */
 /*   density set  D_i = { j : r2 < (R h_i)*(R h_i) }        (includes i)     */
 /*   force set    F_i = { j != i : r2 < (R m)*(R m) }, m = max(h_i, h_j)     */
 /* with R the kernel's support radius in units of h (2, or 3 for M6) and     */
@@ -241,11 +278,16 @@ ORC_API int64_t orc_chop(const uint64_t *skeys, int64_t n, int32_t thresh,
 /* The force set uses the larger smoothing length of the pair so that a pair */
 /* interacts if either particle lies inside the other's range.               */
 /* ------------------------------------------------------------------------- */
-static float canon_r2(const float *pi, const float *pj)
+static float canon_r2(const float *pi, const float *pj, const float *box)
 {
     float dx = pi[0] - pj[0];
     float dy = pi[1] - pj[1];
     float dz = pi[2] - pj[2];
+    if (box) {
+        dx = wrap_f(dx, box[0]);
+        dy = wrap_f(dy, box[1]);
+        dz = wrap_f(dz, box[2]);
+    }
     float xx = dx * dx;
     float yy = dy * dy;
     float zz = dz * dz;
@@ -254,10 +296,11 @@ static float canon_r2(const float *pi, const float *pj)
     return s;
 }
 
-static int canon_in_set(int mode, int kernel, int64_t i, int64_t j, const float *pos4, const float *h)
+static int canon_in_set(int mode, int kernel, int64_t i, int64_t j, const float *pos4, const float *h,
+                        const float *box)
 {
     const float kr = kernel == 1 ? 3.0f : 2.0f; /* support radius in units of h */
-    float r2 = canon_r2(pos4 + 4 * i, pos4 + 4 * j);
+    float r2 = canon_r2(pos4 + 4 * i, pos4 + 4 * j, box);
     if (mode == 0) {
         float R = kr * h[i];
         float R2 = R * R;
@@ -272,12 +315,13 @@ static int canon_in_set(int mode, int kernel, int64_t i, int64_t j, const float 
 
 /* Row counts for the given targets (cnt[t]). */
 ORC_API void orc_neighbour_counts(const float *pos4, const float *h, int64_t n, int mode,
-                                  const int64_t *targets, int64_t nt, int64_t *cnt, int kernel)
+                                  const int64_t *targets, int64_t nt, int64_t *cnt, int kernel,
+                                  const float *box)
 {
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t t = 0; t < nt; ++t) {
         int64_t i = targets[t], c = 0;
-        for (int64_t j = 0; j < n; ++j) c += canon_in_set(mode, kernel, i, j, pos4, h);
+        for (int64_t j = 0; j < n; ++j) c += canon_in_set(mode, kernel, i, j, pos4, h, box);
         cnt[t] = c;
     }
 }
@@ -285,13 +329,13 @@ ORC_API void orc_neighbour_counts(const float *pos4, const float *h, int64_t n, 
 /* Rows written at off[t] (caller computed from the counts), ascending j. */
 ORC_API void orc_neighbour_lists(const float *pos4, const float *h, int64_t n, int mode,
                                  const int64_t *targets, int64_t nt, const int64_t *off,
-                                 int64_t *idx, int kernel)
+                                 int64_t *idx, int kernel, const float *box)
 {
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t t = 0; t < nt; ++t) {
         int64_t i = targets[t], c = off[t];
         for (int64_t j = 0; j < n; ++j)
-            if (canon_in_set(mode, kernel, i, j, pos4, h)) idx[c++] = j;
+            if (canon_in_set(mode, kernel, i, j, pos4, h, box)) idx[c++] = j;
     }
 }
 
@@ -310,14 +354,14 @@ ORC_API void orc_neighbour_lists(const float *pos4, const float *h, int64_t n, i
 /* Returns the number of targets that did not converge.                      */
 /* ------------------------------------------------------------------------- */
 static void density_sums(int k, int64_t i, double h, const double *x, const double *m, int64_t n,
-                         double *rho_sum, double *dwdh_sum)
+                         const double *box, double *rho_sum, double *dwdh_sum)
 {
     double s0 = 0.0, s1 = 0.0;
     const double R = kern_support(k);
     for (int64_t j = 0; j < n; ++j) {
-        double dx = x[3 * i] - x[3 * j], dy = x[3 * i + 1] - x[3 * j + 1],
-               dz = x[3 * i + 2] - x[3 * j + 2];
-        double r = sqrt(dx * dx + dy * dy + dz * dz);
+        double d[3];
+        sep3(x, i, j, box, d);
+        double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         if (r >= R * h) continue;
         s0 += m[j] * kern_w(k, r, h);
         s1 += m[j] * kern_dwdh(k, r, h);
@@ -330,7 +374,7 @@ ORC_API int64_t orc_density(const double *x, const double *v, const double *m, i
                             const int64_t *targets, int64_t nt, const double *h0,
                             double hfact, double tol, int32_t max_iter, int32_t fixed_iters,
                             double *h_out, double *rho, double *omega, double *drhodt,
-                            int32_t *nngb, int32_t *iters, int kernel)
+                            int32_t *nngb, int32_t *iters, int kernel, const double *box)
 {
     const double R = kern_support(kernel);
     int64_t failures = 0;
@@ -343,7 +387,7 @@ ORC_API int64_t orc_density(const double *x, const double *v, const double *m, i
         int limit = fixed_iters > 0 ? fixed_iters : max_iter;
         while (it < limit) {
             double rs, ds;
-            density_sums(kernel, i, h, x, m, n, &rs, &ds);
+            density_sums(kernel, i, h, x, m, n, box, &rs, &ds);
             double rho_h = m[i] * hf3 / (h * h * h);
             double g = rs - rho_h;
             double gp = ds + 3.0 * rho_h / h;
@@ -365,14 +409,15 @@ ORC_API int64_t orc_density(const double *x, const double *v, const double *m, i
         if (!converged) failures += 1;
         /* final quantities at the accepted h */
         double rs, ds;
-        density_sums(kernel, i, h, x, m, n, &rs, &ds);
+        density_sums(kernel, i, h, x, m, n, box, &rs, &ds);
         double rho_h = m[i] * hf3 / (h * h * h);
         double om = 1.0 + h / (3.0 * rho_h) * ds;
         double div = 0.0;
         int32_t cnt = 0;
         for (int64_t j = 0; j < n; ++j) {
-            double dx = x[3 * i] - x[3 * j], dy = x[3 * i + 1] - x[3 * j + 1],
-                   dz = x[3 * i + 2] - x[3 * j + 2];
+            double d[3];
+            sep3(x, i, j, box, d);
+            double dx = d[0], dy = d[1], dz = d[2];
             double r = sqrt(dx * dx + dy * dy + dz * dz);
             if (r >= R * h) continue;
             ++cnt;
@@ -414,7 +459,8 @@ ORC_API void orc_force(const double *x, const double *v, const double *m, const 
                        const double *h, const double *rho, const double *omega, int64_t n,
                        const int64_t *targets, int64_t nt, double gamma, double alpha,
                        double beta, double alpha_u, double vsig_scale, double *acc,
-                       double *dudt, double *vsigmax, int32_t *nforce, int kernel)
+                       double *dudt, double *vsigmax, int32_t *nforce, int kernel,
+                       const double *box)
 {
     const double R = kern_support(kernel);
 #pragma omp parallel for schedule(dynamic, 4)
@@ -428,8 +474,9 @@ ORC_API void orc_force(const double *x, const double *v, const double *m, const 
         int32_t cnt = 0;
         for (int64_t j = 0; j < n; ++j) {
             if (j == i) continue;
-            double dx = x[3 * i] - x[3 * j], dy = x[3 * i + 1] - x[3 * j + 1],
-                   dz = x[3 * i + 2] - x[3 * j + 2];
+            double d[3];
+            sep3(x, i, j, box, d);
+            double dx = d[0], dy = d[1], dz = d[2];
             double r2 = dx * dx + dy * dy + dz * dz;
             double hm = h[i] > h[j] ? h[i] : h[j];
             double rad = R * hm * vsig_scale;
