@@ -77,6 +77,17 @@ typedef struct {
     int32_t pair_warps;    /* warps per block: 1, 2, 4 (default) or 8       */
     int32_t pair_unroll;   /* list entries per lane and iteration of the
                               force kernel: 2 (default) or 4               */
+    /* Periodic boundaries (the tube tests of Sect. 4.1-4.2 are periodic in y
+     * and z).  box_len[a] > 0 makes axis a periodic with period box_len[a]
+     * (0 = open axis, the default): positions must lie in
+     * [box_lo[a], box_lo[a] + box_len[a]) (sph_build_tree checks this,
+     * SPH_ERR_INVALID_ARG), every pair separation along the axis is the
+     * nearest image (d - L if d > L/2, d + L if d < -L/2, exact in FP32),
+     * and sph_step wraps drifted positions back into the box.  The support
+     * R h of every particle must stay below box_len[a] / 2 (the force pass
+     * reports SPH_ERR_INVALID_ARG otherwise).                              */
+    float box_lo[3];
+    float box_len[3];
 } sph_params;
 
 /* Particle state, structure of arrays, n particles, device memory.

@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(128) pairwalk_kernel(PairWalkArgs a, Op op)
                     base[tt] = 0;
                     if (tt < nt) {
                         const float4 tp = sm.tp[tt];
-                        const float r2 = canon_r2(tp.x, tp.y, tp.z, pj.x, pj.y, pj.z);
+                        const float r2 = canon_r2p(tp.x, tp.y, tp.z, pj.x, pj.y, pj.z, a.tree.per);
                         bool hit;
                         if (a.dens_set) {
                             const float R = a.kr * sm.th[tt];
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(128) pairwalk_kernel(PairWalkArgs a, Op op)
                     for (int e = sub; e < len; e += L) {
                         const int j = __ldcs(lst + e);
                         const float4 pj = __ldg(&a.pos[j]);
-                        const float r2 = canon_r2(tp.x, tp.y, tp.z, pj.x, pj.y, pj.z);
+                        const float r2 = canon_r2p(tp.x, tp.y, tp.z, pj.x, pj.y, pj.z, a.tree.per);
                         const float R = a.dens_set ? a.kr * ht : a.kr * fmaxf(ht, __ldg(&a.h[j]));
                         if (r2 < R * R && (a.dens_set || j != i)) op.pair(i, j, acc);
                     }
@@ -205,10 +205,12 @@ __device__ __forceinline__ float fast_sqrt(float x) { return x > 0.f ? x * rsqrt
 template <bool WANT_I, int K>
 __device__ __forceinline__ void force_pair_vjp(const PairIn &I, const PairIn &J, float mj, float alpha,
                                                float beta, float alpha_u, float gamma, float4 w,
-                                               PairIn &g, float &galpha)
+                                               const Period &P, PairIn &g, float &galpha)
 {
     const float gm1 = gamma - 1.f;
-    const float dx = I.x[0] - J.x[0], dy = I.x[1] - J.x[1], dz = I.x[2] - J.x[2];
+    // nearest images on the periodic axes (the wrap's derivative is 1)
+    const float dx = wrap_sep(I.x[0] - J.x[0], P.x), dy = wrap_sep(I.x[1] - J.x[1], P.y),
+                dz = wrap_sep(I.x[2] - J.x[2], P.z);
     const float r2 = dx * dx + dy * dy + dz * dz;
     if (!(r2 > 0.f)) return;
     const float rinv = rsqrtf(r2);
@@ -369,6 +371,7 @@ struct ForceBwdOp {
     float *gh, *grho, *gom;          // out
     double *galpha;                  // out: accumulated (one atomic per target)
     float alpha, beta, alpha_u, gamma;
+    Period per;
     struct Acc {
         PairIn K;     // the target's own inputs, loaded once
         float mk;
@@ -395,9 +398,9 @@ struct ForceBwdOp {
     {
         (void)k;
         const PairIn J = load(j);
-        force_pair_vjp<true, KER>(c.K, J, pos[j].w, alpha, beta, alpha_u, gamma, c.wk, c.g, c.ga);
+        force_pair_vjp<true, KER>(c.K, J, pos[j].w, alpha, beta, alpha_u, gamma, c.wk, per, c.g, c.ga);
         float unused = 0.f;
-        force_pair_vjp<false, KER>(J, c.K, c.mk, alpha, beta, alpha_u, gamma, gacc[j], c.g, unused);
+        force_pair_vjp<false, KER>(J, c.K, c.mk, alpha, beta, alpha_u, gamma, gacc[j], per, c.g, unused);
     }
     __device__ void reduce(Acc &c, int L) const
     {
@@ -443,12 +446,14 @@ struct DensBwd1Op {
     const float *gh, *grho, *gom;  // cotangents of h, rho, Omega
     float2 *coef;                  // out: (lambda, w)
     float hf3;
+    Period per;
     struct Acc { float S, S2; };
     __device__ void init(int, Acc &c) const { c.S = 0.f; c.S2 = 0.f; }
     __device__ void pair(int i, int j, Acc &c) const
     {
         float4 pi = pos[i], pj = pos[j];
-        float dx = pi.x - pj.x, dy = pi.y - pj.y, dz = pi.z - pj.z;
+        float dx = wrap_sep(pi.x - pj.x, per.x), dy = wrap_sep(pi.y - pj.y, per.y),
+              dz = wrap_sep(pi.z - pj.z, per.z);
         float r = fast_sqrt(dx * dx + dy * dy + dz * dz);
         float hi = h[i], hinv = __fdividef(1.f, hi);
         float q = r * hinv, f, df, d2f;
@@ -484,6 +489,7 @@ struct DensBwd2Op {
     const float *h;
     const float2 *coef;
     float4 *gpos;  // accumulated (+=)
+    Period per;
     struct Acc { float g[3]; };
     __device__ void init(int, Acc &c) const { c.g[0] = c.g[1] = c.g[2] = 0.f; }
     __device__ static float cterm(float r, float hh, float lam, float w, float m)
@@ -499,7 +505,8 @@ struct DensBwd2Op {
     __device__ void pair(int k, int j, Acc &c) const
     {
         float4 pk = pos[k], pj = pos[j];
-        float dx = pk.x - pj.x, dy = pk.y - pj.y, dz = pk.z - pj.z;
+        float dx = wrap_sep(pk.x - pj.x, per.x), dy = wrap_sep(pk.y - pj.y, per.y),
+              dz = wrap_sep(pk.z - pj.z, per.z);
         float r2 = dx * dx + dy * dy + dz * dz;
         if (!(r2 > 0.f)) return;
         float rinv = rsqrtf(r2), r = r2 * rinv;
@@ -524,8 +531,8 @@ struct DensBwd2Op {
 
 // ------------------------------------------------------------------ launch
 template <int CAP, class Op>
-static cudaError_t launch_pairwalk(Ctx &c, const sph_state &s, bool dens_set, float kr, const Op &op,
-                                   cudaStream_t st, const Batch *batch)
+static cudaError_t launch_pairwalk(Ctx &c, const sph_state &s, bool dens_set, float kr, Period per,
+                                   const Op &op, cudaStream_t st, const Batch *batch)
 {
     size_t smem = sizeof(PairWalkSmem<CAP>) * 4;
     static bool configured = false;
@@ -548,7 +555,7 @@ static cudaError_t launch_pairwalk(Ctx &c, const sph_state &s, bool dens_set, fl
     a.grp_hi = c.tree.grp_hi;
     a.sizes = c.d_sizes;
     a.work = c.d_sizes + SZ_WORK;
-    a.tree = WalkTree{c.tree.node_lo, c.tree.node_hi, c.tree.node_ref};
+    a.tree = WalkTree{c.tree.node_lo, c.tree.node_hi, c.tree.node_ref, per};
     a.inst = batch ? c.inst : nullptr;
     a.dens_set = dens_set ? 1 : 0;
     a.kr = kr;
@@ -586,11 +593,12 @@ static cudaError_t force_bwd_k(Ctx &c, const sph_state &s, const sph_params &p, 
     op.beta = p.beta_av;
     op.alpha_u = p.alpha_u;
     op.gamma = p.gamma;
+    op.per = period_of(p);
     // the force-set walk needs node and group h_max of the current h
     cudaError_t e = check_list_kernel(c, p, st);
     if (e == cudaSuccess) e = update_hmax(c, s, p, st);
     if (e != cudaSuccess) return e;
-    return launch_pairwalk<96>(c, s, false, SphKernel<K>::R, op, st, nullptr);
+    return launch_pairwalk<96>(c, s, false, SphKernel<K>::R, op.per, op, st, nullptr);
 }
 
 cudaError_t force_bwd(Ctx &c, const sph_state &s, const sph_params &p, const float4 *gacc,
@@ -617,19 +625,21 @@ static cudaError_t density_bwd_k(Ctx &c, const sph_state &s, const sph_params &p
     op1.gom = gom;
     op1.coef = coef;
     op1.hf3 = p.hfact * p.hfact * p.hfact;
+    op1.per = period_of(p);
     // pass 2 opens nodes by their h_max (force set) where it walks: refresh it
     // for the current h (unless the caller just did)
     cudaError_t e = check_list_kernel(c, p, st);
     if (e == cudaSuccess && refresh_hmax) e = update_hmax(c, s, p, st);
     if (e != cudaSuccess) return e;
-    e = launch_pairwalk<96>(c, s, true, SphKernel<K>::R, op1, st, nullptr);
+    e = launch_pairwalk<96>(c, s, true, SphKernel<K>::R, op1.per, op1, st, nullptr);
     if (e != cudaSuccess) return e;
     DensBwd2Op<K> op2;
     op2.pos = (const float4 *)s.pos;
     op2.h = s.h;
     op2.coef = coef;
     op2.gpos = gpos;
-    return launch_pairwalk<96>(c, s, false, SphKernel<K>::R, op2, st, nullptr);
+    op2.per = op1.per;
+    return launch_pairwalk<96>(c, s, false, SphKernel<K>::R, op2.per, op2, st, nullptr);
 }
 
 cudaError_t density_bwd(Ctx &c, const sph_state &s, const sph_params &p, const float *gh,

@@ -147,7 +147,7 @@ __device__ __forceinline__ void push_fallback(const DensArgs &a, int g, int b0, 
 // Launch shape (run-time): a.tb targets per batch (32 / a.tb lanes per
 // target), blockDim.x / 32 warps per block; registers capped for 1024
 // resident threads per SM.
-template <int K>
+template <int K, bool PER>
 __global__ void __launch_bounds__(256, 4) density_list_kernel(DensArgs a)
 {
     const int lane = threadIdx.x & 31;
@@ -206,7 +206,12 @@ __global__ void __launch_bounds__(256, 4) density_list_kernel(DensArgs a)
                     // q >= 2, so entries beyond 2 h add nothing.  A missing second
                     // entry repeats the first with zero mass.
                     auto entry = [&](float4 pj, float4 vj, float mj) {
-                        const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
+                        float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
+                        if (PER) {  // nearest images on the periodic axes
+                            dx = wrap_sep(dx, a.tree.per.x);
+                            dy = wrap_sep(dy, a.tree.per.y);
+                            dz = wrap_sep(dz, a.tree.per.z);
+                        }
                         const float r2 = dx * dx + dy * dy + dz * dz;
                         const float vd = (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz;
                         cnt += (mj > 0.f && r2 < R2) ? 1 : 0;
@@ -359,8 +364,8 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_walk_kernel(DensArgs 
                             base[t0] = base[t1] = 0;
                             r2s[t0] = r2s[t1] = 0.f;
                             if (t0 < nt) {
-                                const float2 r2 = canon_r2_x2(sm.tq.x[q], sm.tq.y[q], sm.tq.z[q], pj.x,
-                                                              pj.y, pj.z);
+                                const float2 r2 = canon_r2_x2p(sm.tq.x[q], sm.tq.y[q], sm.tq.z[q], pj.x,
+                                                               pj.y, pj.z, a.tree.per);
                                 r2s[t0] = r2.x;
                                 r2s[t1] = r2.y;
                                 bs[t0] = __ballot_sync(0xffffffffu, j >= 0 && r2.x < sm.tr2[t0]);
@@ -385,9 +390,9 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_walk_kernel(DensArgs 
                             if (tt < nt) {
                                 if ((bs[tt] >> lane) & 1u) {
                                     const float4 tq = sm.tp[tt], tv = sm.tv[tt];
-                                    const float vdot = (tv.x - vj.x) * (tq.x - pj.x) +
-                                                       (tv.y - vj.y) * (tq.y - pj.y) +
-                                                       (tv.z - vj.z) * (tq.z - pj.z);
+                                    const float vdot = (tv.x - vj.x) * wrap_sep(tq.x - pj.x, a.tree.per.x) +
+                                                       (tv.y - vj.y) * wrap_sep(tq.y - pj.y, a.tree.per.y) +
+                                                       (tv.z - vj.z) * wrap_sep(tq.z - pj.z, a.tree.per.z);
                                     const int pe = base[tt] + __popc(bs[tt] & lt);
                                     sm.er2[tt][pe] = r2s[tt];
                                     sm.em[tt][pe] = pj.w;
@@ -518,7 +523,7 @@ __global__ void __launch_bounds__(128) neighbour_kernel(NbrArgs a)
                     float4 tq = sm.tp[tt];
                     float ht = sm.th[tt];
                     int it = gr.x + b0 + tt;
-                    float r2 = canon_r2(tq.x, tq.y, tq.z, pj.x, pj.y, pj.z);
+                    float r2 = canon_r2p(tq.x, tq.y, tq.z, pj.x, pj.y, pj.z, a.tree.per);
                     float Rr = a.mode == 0 ? a.kr * ht : a.kr * fmaxf(ht, hj);
                     bool hit = j >= 0 && r2 < Rr * Rr && (a.mode == 0 || j != it);
                     unsigned b = __ballot_sync(0xffffffffu, hit);
@@ -571,8 +576,8 @@ __global__ void scan_i64_kernel(int64_t *off, int n)
 // list into *missing); otherwise the rows are written at off[i].
 __global__ void list_set_kernel(const float4 *__restrict__ pos, const float *__restrict__ h,
                                 const int *__restrict__ idx, const int *__restrict__ len, int n,
-                                int stride, int mode, float kr, int64_t *off, int32_t *out,
-                                int *missing)
+                                int stride, int mode, float kr, Period per, int64_t *off,
+                                int32_t *out, int *missing)
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int l = len[i];
@@ -590,7 +595,7 @@ __global__ void list_set_kernel(const float4 *__restrict__ pos, const float *__r
         for (int e = 0; e < l; ++e) {
             const int j = idx[(size_t)i * stride + e];
             const float4 pj = pos[j];
-            const float r2 = canon_r2(pi.x, pi.y, pi.z, pj.x, pj.y, pj.z);
+            const float r2 = canon_r2p(pi.x, pi.y, pi.z, pj.x, pj.y, pj.z, per);
             const float R = mode == 0 ? kr * hi : kr * fmaxf(hi, h[j]);
             if (r2 < R * R && (mode == 0 || j != i)) {
                 if (out) out[w++] = j;
@@ -633,9 +638,13 @@ static cudaError_t configure_density_list(int blocks[4])
     if (!configured) {
         for (int w = 0; w < 4; ++w) {
             int nb = 0;
-            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, density_list_kernel<K>,
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, density_list_kernel<K, false>,
                                                                           32 << w, 0);
+            int nbp = 0;
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbp, density_list_kernel<K, true>, 32 << w, 0);
             if (e != cudaSuccess) return e;
+            nb = nbp < nb ? nbp : nb;
             nb_cached[w] = nb > 0 ? nb : 1;
         }
         configured = true;
@@ -683,7 +692,8 @@ static cudaError_t density_solve_k(Ctx &c, DensArgs &a, const sph_params &p, cud
     const PairShape ps = pair_shape(p);
     a.tb = ps.targets;
     const int wl = ps.warps == 8 ? 3 : ps.warps == 4 ? 2 : ps.warps == 2 ? 1 : 0;
-    density_list_kernel<K><<<c.num_sms * bl[wl], 32 * ps.warps, 0, st>>>(a);
+    if (a.tree.per.any()) density_list_kernel<K, true><<<c.num_sms * bl[wl], 32 * ps.warps, 0, st>>>(a);
+    else density_list_kernel<K, false><<<c.num_sms * bl[wl], 32 * ps.warps, 0, st>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // default tile: the mean density set (about 58 for M4 at hfact 1.2, 82 for
@@ -739,7 +749,7 @@ cudaError_t density_solve(Ctx &c, const sph_state &s, const sph_params &p, cudaS
     a.sizes = c.d_sizes;
     a.work = c.d_sizes + SZ_WORK;
     a.work2 = c.d_sizes + SZ_WORK2;
-    a.tree = WalkTree{c.tree.node_lo, c.tree.node_hi, c.tree.node_ref};
+    a.tree = WalkTree{c.tree.node_lo, c.tree.node_hi, c.tree.node_ref, period_of(p)};
     a.hfact = p.hfact;
     a.tol = p.h_tol;
     a.gamma = p.gamma;
@@ -778,7 +788,7 @@ cudaError_t list_sets(Ctx &c, const sph_state &s, const sph_params &p, int mode,
     const int grid = c.num_sms * 8;
     const float kr = kernel_support(p.kernel);
     list_set_kernel<<<grid, 256, 0, st>>>((const float4 *)s.pos, s.h, c.nl_idx, c.nl_len, n,
-                                          c.nl_stride, mode, kr,
+                                          c.nl_stride, mode, kr, period_of(p),
                                           d_off, nullptr, missing);
     scan_i64_kernel<<<1, 1024, 0, st>>>(d_off, n);
     e = cudaMemcpyAsync(h_total, d_off + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
@@ -789,7 +799,7 @@ cudaError_t list_sets(Ctx &c, const sph_state &s, const sph_params &p, int mode,
     if (d_idx && *h_total <= cap) {
         list_set_kernel<<<grid, 256, 0, st>>>((const float4 *)s.pos, s.h, c.nl_idx, c.nl_len, n,
                                               c.nl_stride, mode,
-                                              kr, d_off, d_idx, missing);
+                                              kr, period_of(p), d_off, d_idx, missing);
         e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return e;
     }
@@ -809,7 +819,7 @@ cudaError_t neighbour_lists(Ctx &c, const sph_state &s, const sph_params &p, int
     a.grp_hi = c.tree.grp_hi;
     a.sizes = c.d_sizes;
     a.work = c.d_sizes + SZ_WORK;
-    a.tree = WalkTree{c.tree.node_lo, c.tree.node_hi, c.tree.node_ref};
+    a.tree = WalkTree{c.tree.node_lo, c.tree.node_hi, c.tree.node_ref, period_of(p)};
     a.mode = mode;
     a.off = d_off;
     a.idx = nullptr;

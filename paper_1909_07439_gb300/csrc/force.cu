@@ -88,7 +88,9 @@ struct ForceTarget {
     __device__ __forceinline__ void pair(float4 pj, float4 vj, float4 qj, float mj, bool in,
                                          const ForceArgs &a)
     {
-        const float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
+        // nearest images on the periodic axes (open axes: unchanged)
+        const float dx = wrap_sep(xi.x - pj.x, a.tree.per.x), dy = wrap_sep(xi.y - pj.y, a.tree.per.y),
+                    dz = wrap_sep(xi.z - pj.z, a.tree.per.z);
         pair_d(dx, dy, dz, dx * dx + dy * dy + dz * dz, vj, qj, mj, in, a);
     }
 
@@ -163,7 +165,7 @@ struct ForceTarget {
 //   du/dt terms: sum m_j vr g_i, sum m_j vsig_i hw^2 g_i and the conduction
 //   sum m_j |dP| rsqrt(|dP| (rho_i + rho_j)) (P_i/rho_i - P_j/rho_j) (AK_i g_i + AK_j g_j),
 // whose constant factors are applied once per target at the end.
-template <int K>
+template <int K, bool PER>
 struct ForceSums {
     float xi, yi, zi, vxi, vyi, vzi, pri;   // position, velocity, (gamma - 1) u
     float R2i, AKi, aci, rhoi, Pi;          // (R h)^2, AK, alpha c, rho, P
@@ -182,13 +184,19 @@ struct ForceSums {
         cnt = 0;
     }
 
-    // one list entry with record (p, v, q); valid = false for padding
+    // one list entry with record (p, v, q); valid = false for padding; PER:
+    // nearest images on the periodic axes of P
     __device__ __forceinline__ void pair(const float4 p, const float4 v, const float4 q, bool valid,
-                                         float beta)
+                                         float beta, const Period &P)
     {
         const float prj = v.w;
         // canonical separation: decides the pair set, feeds the pair terms
-        const float dx = __fsub_rn(xi, p.x), dy = __fsub_rn(yi, p.y), dz = __fsub_rn(zi, p.z);
+        float dx = __fsub_rn(xi, p.x), dy = __fsub_rn(yi, p.y), dz = __fsub_rn(zi, p.z);
+        if (PER) {
+            dx = wrap_sep(dx, P.x);
+            dy = wrap_sep(dy, P.y);
+            dz = wrap_sep(dz, P.z);
+        }
         const float r2 = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
         // r < R max(h_i, h_j) as r^2 < max((R h_i)^2, (R h_j)^2): squaring is monotone
         const bool in = valid && r2 > 0.f && r2 < fmaxf(R2i, q.x);
@@ -245,7 +253,7 @@ struct ForceSums {
 // Launch shape (run-time): a.tb targets per batch (32 / a.tb lanes per
 // target), blockDim.x / 32 warps per block; NPER list entries per lane and
 // iteration.  Registers are capped for 768 resident threads per SM.
-template <int NPER, int K>
+template <int NPER, int K, bool PER>
 __global__ void __launch_bounds__(256, 3) force_list_kernel(ForceArgs a)
 {
     const int lane = threadIdx.x & 31;
@@ -283,7 +291,7 @@ __global__ void __launch_bounds__(256, 3) force_list_kernel(ForceArgs a)
                     ++n_fb;
                     continue;
                 }
-                ForceSums<K> T;
+                ForceSums<K, PER> T;
                 T.init(a.frec + 3 * (size_t)i);
                 const int *__restrict__ lst = a.nl_idx + (size_t)i * a.nl_stride;
                 // Four consecutive entries per lane and iteration (one 16-byte
@@ -295,7 +303,7 @@ __global__ void __launch_bounds__(256, 3) force_list_kernel(ForceArgs a)
                 auto entry = [&](int j, bool valid) {
                     const float4 *rj = a.frec + 3 * (size_t)j;
                     T.pair(ld_keep(rj, 0, keep), ld_keep(rj, 1, keep), ld_keep(rj, 2, keep), valid,
-                           a.beta);
+                           a.beta, a.tree.per);
                 };
                 if (NPER == 4) {
                     int e = 4 * sub;
@@ -404,7 +412,8 @@ __global__ void __launch_bounds__(kForceWarps * 32) force_walk_kernel(ForceArgs 
                     bs[t0] = bs[t1] = 0u;
                     base[t0] = base[t1] = 0;
                     if (t0 < nt) {
-                        const float2 r2 = canon_r2_x2(sm.tc.x[q], sm.tc.y[q], sm.tc.z[q], pj.x, pj.y, pj.z);
+                        const float2 r2 = canon_r2_x2p(sm.tc.x[q], sm.tc.y[q], sm.tc.z[q], pj.x, pj.y, pj.z,
+                                                       a.tree.per);
                         const float R0 = SphKernel<K>::R * fmaxf(sm.th[t0], hj);
                         const float R1 = SphKernel<K>::R * fmaxf(sm.th[t1], hj);
                         bs[t0] = __ballot_sync(0xffffffffu, j >= 0 && j != i0 + t0 && r2.x < R0 * R0);
@@ -454,15 +463,16 @@ __global__ void force_prep_kernel(const float4 *__restrict__ pos, const float4 *
                                   const float *__restrict__ h, const float *__restrict__ rho,
                                   const float *__restrict__ omega, float4 *__restrict__ prop,
                                   float4 *__restrict__ frec, int n, float gamma, float alpha, float kr,
-                                  float gc, int *err)
+                                  float gc, float h_lim, int *err)
 {
-    bool bad = false, neg = false;
+    bool bad = false, neg = false, wide = false;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float4 v = vel[i];
         const float r = rho[i], o = omega[i], hi = h[i];
         bad |= !(isfinite(v.x) && isfinite(v.y) && isfinite(v.z) && isfinite(v.w) && isfinite(r) &&
                  isfinite(o));
         neg |= v.w < 0.f;
+        wide |= !(hi < h_lim);  // the support would reach a second periodic image
         const float cs = sqrtf(fmaxf(gamma * (gamma - 1.f) * v.w, 0.f));
         const float A = 1.f / (r * o);
         prop[i] = make_float4(hi, r, A, cs);
@@ -474,6 +484,7 @@ __global__ void force_prep_kernel(const float4 *__restrict__ pos, const float4 *
     }
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) raise_error(err, SPH_ERR_NONFINITE);
     if (__any_sync(0xffffffffu, neg) && (threadIdx.x & 31) == 0) raise_error(err, SPH_ERR_NEGATIVE_U);
+    if (__any_sync(0xffffffffu, wide) && (threadIdx.x & 31) == 0) raise_error(err, SPH_ERR_INVALID_ARG);
 }
 
 // one-time kernel attributes and occupancy (also called before graph capture)
@@ -511,8 +522,13 @@ static cudaError_t configure_force_list(int blocks[2][4])
                 int nb = 0;
                 const int threads = 32 << w;  // 1, 2, 4, 8 warps
                 cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                    &nb, u ? force_list_kernel<4, K> : force_list_kernel<2, K>, threads, 0);
+                    &nb, u ? force_list_kernel<4, K, false> : force_list_kernel<2, K, false>, threads, 0);
+                int nbp = 0;
+                if (e == cudaSuccess)
+                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                        &nbp, u ? force_list_kernel<4, K, true> : force_list_kernel<2, K, true>, threads, 0);
                 if (e != cudaSuccess) return e;
+                nb = nbp < nb ? nbp : nb;
                 nb_cached[u][w] = nb > 0 ? nb : 1;
             }
         configured = true;
@@ -558,7 +574,8 @@ cudaError_t force_prep(Ctx &c, const sph_state &s, const sph_params &p, cudaStre
     if (grid > c.num_sms * 16) grid = c.num_sms * 16;
     force_prep_kernel<<<grid, 256, 0, st>>>((const float4 *)s.pos, (const float4 *)s.vel, s.h, s.rho,
                                             s.omega, c.prop, c.frec, n, p.gamma, p.alpha_av,
-                                            kernel_support(p.kernel), kernel_gc(p.kernel), c.d_err);
+                                            kernel_support(p.kernel), kernel_gc(p.kernel),
+                                            periodic_h_limit(p), c.d_err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     return hmax_now ? update_hmax(c, s, p, st) : cudaSuccess;
@@ -576,8 +593,11 @@ static cudaError_t force_launch_k(Ctx &c, ForceArgs &a, const sph_params &p, con
     a.tb = ps.targets;
     const int u = ps.unroll == 4 ? 1 : 0, wl = ps.warps == 8 ? 3 : ps.warps == 4 ? 2 : ps.warps == 2 ? 1 : 0;
     const int grid = c.num_sms * bl[u][wl];
-    if (u) force_list_kernel<4, K><<<grid, 32 * ps.warps, 0, st>>>(a);
-    else force_list_kernel<2, K><<<grid, 32 * ps.warps, 0, st>>>(a);
+    const bool per = a.tree.per.any();
+    if (u && per) force_list_kernel<4, K, true><<<grid, 32 * ps.warps, 0, st>>>(a);
+    else if (u) force_list_kernel<4, K, false><<<grid, 32 * ps.warps, 0, st>>>(a);
+    else if (per) force_list_kernel<2, K, true><<<grid, 32 * ps.warps, 0, st>>>(a);
+    else force_list_kernel<2, K, false><<<grid, 32 * ps.warps, 0, st>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // the walking kernel needs node and group h_max of the final h; refreshed
@@ -615,7 +635,7 @@ cudaError_t force_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStre
     a.sizes = c.d_sizes;
     a.work = c.d_sizes + SZ_WORK;
     a.work2 = c.d_sizes + SZ_WORK2;
-    a.tree = WalkTree{c.tree.node_lo, c.tree.node_hi, c.tree.node_ref};
+    a.tree = WalkTree{c.tree.node_lo, c.tree.node_hi, c.tree.node_ref, period_of(p)};
     a.gm1 = p.gamma - 1.f;
     a.alpha = p.alpha_av;
     a.beta = p.beta_av;

@@ -15,16 +15,27 @@ static int grid_n(const Ctx &c, int64_t n, int block)
 
 // v_half = v + a dt/2, u_half = u + du dt/2 (into vhalf);
 // predicted v1p = v + a dt, u1p = u + du dt (Eq. 6) into vel1;
-// r1 = r + v_half dt = r + v dt + a dt^2/2 (Eq. 5) into pos1; h and perm
-// copied along.  The outputs are the context's temporaries, from which the
-// tree build gathers the state back in the new curve order.
+// r1 = r + v_half dt = r + v dt + a dt^2/2 (Eq. 5) into pos1, moved back
+// into [lo, lo + L) on the periodic axes (by -L or +L; should rounding leave
+// it outside, it becomes lo, its image within an ulp); h and perm copied
+// along.  The outputs are the context's temporaries, from which the tree
+// build gathers the state back in the new curve order.
 __global__ void kick_drift_kernel(const float4 *__restrict__ pos, const float4 *__restrict__ vel,
                                   const float4 *__restrict__ acc, const float *__restrict__ h,
                                   const uint32_t *__restrict__ perm, float4 *__restrict__ pos1,
                                   float4 *__restrict__ vel1, float4 *__restrict__ vhalf,
                                   float *__restrict__ h1, uint32_t *__restrict__ perm1, int n,
-                                  const float *d_dt, const int *__restrict__ inst)
+                                  const float *d_dt, const int *__restrict__ inst, Period per,
+                                  float3 plo)
 {
+    auto wrap = [](float x, float L, float lo) {
+        if (L > 0.f) {
+            const float hi = lo + L;
+            x = x >= hi ? x - L : x < lo ? x + L : x;
+            x = (x >= lo && x < hi) ? x : lo;
+        }
+        return x;
+    };
     float dt = *d_dt, hdt = 0.5f * dt;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         if (inst) {
@@ -35,7 +46,8 @@ __global__ void kick_drift_kernel(const float4 *__restrict__ pos, const float4 *
         float4 vh = make_float4(v.x + hdt * a.x, v.y + hdt * a.y, v.z + hdt * a.z, v.w + hdt * a.w);
         vhalf[i] = vh;
         vel1[i] = make_float4(v.x + dt * a.x, v.y + dt * a.y, v.z + dt * a.z, v.w + dt * a.w);
-        pos1[i] = make_float4(p.x + dt * vh.x, p.y + dt * vh.y, p.z + dt * vh.z, p.w);
+        pos1[i] = make_float4(wrap(p.x + dt * vh.x, per.x, plo.x), wrap(p.y + dt * vh.y, per.y, plo.y),
+                              wrap(p.z + dt * vh.z, per.z, plo.z), p.w);
         h1[i] = h[i];
         perm1[i] = perm[i];
     }
@@ -168,13 +180,14 @@ __global__ void conserved_final_kernel(const double *part, int nb, double *out8)
     }
 }
 
-cudaError_t kick_drift(Ctx &c, const sph_state &s, const float *d_dt, cudaStream_t st,
-                       const Batch *batch)
+cudaError_t kick_drift(Ctx &c, const sph_state &s, const sph_params &p, const float *d_dt,
+                       cudaStream_t st, const Batch *batch)
 {
     int n = (int)s.n;
     kick_drift_kernel<<<grid_n(c, n, 256), 256, 0, st>>>(
         (const float4 *)s.pos, (const float4 *)s.vel, (const float4 *)s.acc, s.h, s.perm, c.tmp4[0],
-        c.tmp4[1], c.tmp4[2], c.tmp1[0], c.tmp_perm, n, d_dt, batch ? c.inst : nullptr);
+        c.tmp4[1], c.tmp4[2], c.tmp1[0], c.tmp_perm, n, d_dt, batch ? c.inst : nullptr,
+        period_of(p), box_lo_of(p));
     return cudaGetLastError();
 }
 

@@ -134,6 +134,17 @@ inline float kernel_norm(int k)
 {
     return k == 1 ? SphKernel<1>::C : k == 2 ? SphKernel<2>::C : SphKernel<0>::C;
 }
+// largest h whose support R h stays below half of every periodic period
+// (INFINITY without periodic axes)
+inline float periodic_h_limit(const sph_params &p)
+{
+    float lim = INFINITY;
+    const float R = kernel_support(p.kernel);
+    for (int a = 0; a < 3; ++a)
+        if (p.box_len[a] > 0.f) lim = fminf(lim, 0.5f * p.box_len[a] / R);
+    return lim;
+}
+
 inline float kernel_gc(int k)
 {
     return k == 1 ? SphKernel<1>::G * SphKernel<1>::C

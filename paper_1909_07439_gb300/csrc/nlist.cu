@@ -115,7 +115,7 @@ __device__ __forceinline__ int group_candidates(const NlistArgs &a, NlistSmem &s
             const float4 lo = __ldg(&a.tree.node_lo[node]);
             const float4 hi = __ldg(&a.tree.node_hi[node]);
             ref = __ldg(&a.tree.node_ref[node]);
-            const float d2 = box_dist2(glo, ghi, lo, hi);
+            const float d2 = box_dist2_t(a.tree, glo, ghi, lo, hi);
             const float R = 2.0f * fmaxf(hgroup, lo.w * node_scale);
             open = d2 < R * R * kOpenSlack;
         }
@@ -153,7 +153,8 @@ __device__ __forceinline__ int group_candidates(const NlistArgs &a, NlistSmem &s
 // them, and a missing candidate, also far away, hits no target) and append
 // the hits to the targets' lists.  The next chunk's candidates are loaded
 // while one is tested.  Returns the list length of target `lane` (lane < TB).
-template <int TB>
+// PER: nearest images on the periodic axes.
+template <int TB, bool PER>
 __device__ __forceinline__ int test_chunks(const NlistArgs &a, const NlistSmem &sm, int ncand, int i0)
 {
     const int lane = threadIdx.x & 31;
@@ -182,7 +183,8 @@ __device__ __forceinline__ int test_chunks(const NlistArgs &a, const NlistSmem &
             const int t0 = 2 * q, t1 = t0 + 1;
             // r < max(R_i, R_j) as r^2 < max(R_i^2, R_j^2): squaring is
             // monotone, so both compare the same rounded values
-            const float2 r2 = canon_r2_x2(sm.tc.x[q], sm.tc.y[q], sm.tc.z[q], pj.x, pj.y, pj.z);
+            const float2 r2 = PER ? canon_r2_x2p(sm.tc.x[q], sm.tc.y[q], sm.tc.z[q], pj.x, pj.y, pj.z, a.tree.per)
+                                  : canon_r2_x2(sm.tc.x[q], sm.tc.y[q], sm.tc.z[q], pj.x, pj.y, pj.z);
             const bool hit0 = r2.x < fmaxf(sm.tr2[t0], rj2);
             const bool hit1 = r2.y < fmaxf(sm.tr2[t1], rj2);
             const unsigned m0 = __ballot_sync(0xffffffffu, hit0);
@@ -203,6 +205,7 @@ __device__ __forceinline__ int test_chunks(const NlistArgs &a, const NlistSmem &
     return mine;
 }
 
+template <bool PER>
 __global__ void __launch_bounds__(kNlWarps * 32, 7) nlist_kernel(NlistArgs a)
 {
     __shared__ NlistSmem smv[kNlWarps];
@@ -286,9 +289,9 @@ __global__ void __launch_bounds__(kNlWarps * 32, 7) nlist_kernel(NlistArgs a)
                     __syncwarp();
                     int mlen = 0;
                     if (ncand > 0) {
-                        if (nt <= 4) mlen = test_chunks<4>(a, sm, ncand, i0);
-                        else if (nt <= 8) mlen = test_chunks<8>(a, sm, ncand, i0);
-                        else mlen = test_chunks<16>(a, sm, ncand, i0);
+                        if (nt <= 4) mlen = test_chunks<4, PER>(a, sm, ncand, i0);
+                        else if (nt <= 8) mlen = test_chunks<8, PER>(a, sm, ncand, i0);
+                        else mlen = test_chunks<16, PER>(a, sm, ncand, i0);
                         n_cand += (unsigned long long)nt * (unsigned long long)ncand;
                     }
                     // a group without lists is left to the walking kernels
@@ -321,7 +324,12 @@ static cudaError_t configure_nlist(int &blocks)
     static int nb_cached = 1;
     if (!configured) {
         int nb = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, nlist_kernel, kNlWarps * 32, 0);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, nlist_kernel<true>,
+                                                                      kNlWarps * 32, 0);
+        int nb0 = 0;
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb0, nlist_kernel<false>, kNlWarps * 32, 0);
+        nb = nb0 < nb ? nb0 : nb;
         if (e != cudaSuccess) return e;
         nb_cached = nb > 0 ? nb : 1;
         configured = true;
@@ -347,7 +355,7 @@ static NlistArgs nlist_args(Ctx &c, const sph_state &s, const sph_params &p, flo
     a.grp_hi = c.tree.grp_hi;
     a.sizes = c.d_sizes;
     a.work = c.d_sizes + SZ_WORK;
-    a.tree = WalkTree{c.tree.node_lo, c.tree.node_hi, c.tree.node_ref};
+    a.tree = WalkTree{c.tree.node_lo, c.tree.node_hi, c.tree.node_ref, period_of(p)};
     a.inst = batch ? c.inst : nullptr;
     // the radius and capacity of the lists' kernel (a relist keeps them)
     a.rscale = kernel_support(c.nl_kernel >= 0 ? c.nl_kernel : p.kernel) * (1.f + pad) * kListSlack;
@@ -368,7 +376,8 @@ cudaError_t nlist_pass(Ctx &c, const sph_state &s, const sph_params &p, float pa
     NlistArgs a = nlist_args(c, s, p, pad, batch);
     e = cudaMemsetAsync(a.work, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    nlist_kernel<<<c.num_sms * blocks, kNlWarps * 32, 0, st>>>(a);
+    if (a.tree.per.any()) nlist_kernel<true><<<c.num_sms * blocks, kNlWarps * 32, 0, st>>>(a);
+    else nlist_kernel<false><<<c.num_sms * blocks, kNlWarps * 32, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -393,7 +402,8 @@ cudaError_t relist_pass(Ctx &c, const sph_state &s, const sph_params &p, float p
     a.only_bad = c.tree.rec_bad;
     e = cudaMemsetAsync(a.work, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    nlist_kernel<<<c.num_sms * blocks, kNlWarps * 32, 0, st>>>(a);
+    if (a.tree.per.any()) nlist_kernel<true><<<c.num_sms * blocks, kNlWarps * 32, 0, st>>>(a);
+    else nlist_kernel<false><<<c.num_sms * blocks, kNlWarps * 32, 0, st>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // the rebuilt lists cover the pair sets at the final h

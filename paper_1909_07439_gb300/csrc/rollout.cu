@@ -305,7 +305,7 @@ cudaError_t evaluate(Ctx &c, sph_state &w, const sph_params &p, float *d_dt, cud
 cudaError_t step(Ctx &c, sph_state &w, const sph_params &p, const float *dt, bool partial,
                  float *d_dt_next, cudaStream_t st)
 {
-    RT(kick_drift(c, w, dt, st));
+    RT(kick_drift(c, w, p, dt, st));
     RT(build_tree(c, w, p, false, st));
     RT(density_pass(c, w, p, st));
     RT(force_prep(c, w, p, st));

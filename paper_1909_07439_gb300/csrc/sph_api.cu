@@ -1,5 +1,6 @@
 // C ABI entry points (include/sph.h): context, argument checks, stage timing,
 // error word, and the step driver.
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -130,6 +131,9 @@ sph_status check_params(Ctx &c, const sph_params *p)
     if (!(t == 0 || t == 4 || t == 8 || t == 16) || !(w == 0 || w == 1 || w == 2 || w == 4 || w == 8) ||
         !(u == 0 || u == 2 || u == 4))
         return fail(c, SPH_ERR_INVALID_ARG, "pair_targets 0/4/8/16, pair_warps 0/1/2/4/8, pair_unroll 0/2/4");
+    for (int a = 0; a < 3; ++a)
+        if (!(p->box_len[a] >= 0.f) || !std::isfinite(p->box_len[a]) || !std::isfinite(p->box_lo[a]))
+            return fail(c, SPH_ERR_INVALID_ARG, "box_len must be finite and >= 0, box_lo finite");
     return SPH_OK;
 }
 
@@ -218,7 +222,7 @@ sph_status enqueue_step(Ctx &c, const sph_state &s, const sph_params &p, float *
     sph_status r;
     {
         StageScope sc(c, ST_LEAPFROG, st, 1);
-        CK(kick_drift(c, s, d_dt, st), "kick_drift");
+        CK(kick_drift(c, s, p, d_dt, st), "kick_drift");
     }
     if ((r = do_tree(c, s, p, false, st)) != SPH_OK) return r;
     // final from here on: pos (the closing kick changes v only), perm, keys
@@ -332,6 +336,10 @@ void sph_params_default(sph_params *p)
     p->pair_targets = 8;
     p->pair_warps = 4;
     p->pair_unroll = 2;
+    for (int a = 0; a < 3; ++a) {
+        p->box_lo[a] = 0.f;
+        p->box_len[a] = 0.f;
+    }
 }
 
 sph_status sph_create(sph_ctx **out, int64_t max_n, int device)
@@ -676,7 +684,7 @@ sph_status check_batch(Ctx &c, const sph_state *s, const int64_t *d_offsets, int
 cudaError_t enqueue_batch_step(Ctx &c, const sph_state &s, const sph_params &p, const Batch &b,
                                float *d_dt, double *d_time, cudaStream_t st)
 {
-    cudaError_t e = kick_drift(c, s, d_dt, st, &b);
+    cudaError_t e = kick_drift(c, s, p, d_dt, st, &b);
     if (e == cudaSuccess) e = build_tree(c, s, p, false, st, &b);
     if (e == cudaSuccess) e = density_pass(c, s, p, st, &b);
     if (e == cudaSuccess) e = force_prep(c, s, p, st);

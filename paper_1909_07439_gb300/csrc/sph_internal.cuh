@@ -193,6 +193,15 @@ struct Ctx {
     int64_t capture_launches[ST_N] = {};
 };
 
+// Periods of the axes for periodic boundaries (0: open axis), and the lower
+// corner of the periodic box.
+struct Period {
+    float x, y, z;
+    __host__ __device__ bool any() const { return x > 0.f || y > 0.f || z > 0.f; }
+};
+inline Period period_of(const sph_params &p) { return Period{p.box_len[0], p.box_len[1], p.box_len[2]}; }
+inline float3 box_lo_of(const sph_params &p) { return make_float3(p.box_lo[0], p.box_lo[1], p.box_lo[2]); }
+
 // ---------------------------------------------------------------------------
 // launchers (host functions) implemented in the .cu files
 // ---------------------------------------------------------------------------
@@ -252,8 +261,9 @@ cudaError_t configure_density_kernels(int kernel);
 cudaError_t configure_force_kernels(int kernel);
 // integrate.cu
 // with a batch, d_dt and d_time hold one value per instance
-cudaError_t kick_drift(Ctx &c, const sph_state &s, const float *d_dt, cudaStream_t st,
-                       const Batch *batch = nullptr);
+// (drifted positions wrap into the periodic box of p)
+cudaError_t kick_drift(Ctx &c, const sph_state &s, const sph_params &p, const float *d_dt,
+                       cudaStream_t st, const Batch *batch = nullptr);
 cudaError_t kick_close(Ctx &c, const sph_state &s, const float *d_dt, double *d_time,
                        cudaStream_t st, const Batch *batch = nullptr);
 cudaError_t courant_dt(Ctx &c, const sph_state &s, const sph_params &p, float *d_dt,

@@ -147,15 +147,21 @@ __device__ __forceinline__ void box_scale(const int *bb, float lo[3], float &s)
     s = size > 0.f ? __fdiv_rn(2097152.0f, size) : 0.f;
 }
 
+// (also checks that positions lie in [plo, plo + L) on the periodic axes)
 __global__ void morton_kernel(const float4 *__restrict__ pos, const int *__restrict__ inst, int n,
-                              const int *bb, uint64_t *__restrict__ keys, uint32_t *__restrict__ idx)
+                              const int *bb, uint64_t *__restrict__ keys, uint32_t *__restrict__ idx,
+                              Period per, float3 plo, int *err)
 {
     float lo[3], s;
     box_scale(bb, lo, s);
+    const float L[3] = {per.x, per.y, per.z}, pl[3] = {plo.x, plo.y, plo.z};
+    bool outside = false;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         if (inst) box_scale(bb + 6 * inst[i], lo, s);
         float4 p = pos[i];
         float x[3] = {p.x, p.y, p.z};
+        for (int a = 0; a < 3; ++a)
+            outside |= L[a] > 0.f && !(x[a] >= pl[a] && x[a] < pl[a] + L[a]);
         uint32_t c[3];
         for (int a = 0; a < 3; ++a) {
             float t = __fmul_rn(__fsub_rn(x[a], lo[a]), s);
@@ -165,6 +171,7 @@ __global__ void morton_kernel(const float4 *__restrict__ pos, const int *__restr
         keys[i] = (spread21(c[0]) << 2) | (spread21(c[1]) << 1) | spread21(c[2]);
         idx[i] = (uint32_t)i;
     }
+    if (__any_sync(0xffffffffu, outside) && (threadIdx.x & 31) == 0) raise_error(err, SPH_ERR_INVALID_ARG);
 }
 
 // ------------------------------------------------------------- radix sort
@@ -849,7 +856,8 @@ cudaError_t build_tree(Ctx &c, const sph_state &s, const sph_params &p, bool ful
         bbox_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(pos_in, h_in, n, bb, c.d_err);
     }
     // 2. keys
-    morton_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(pos_in, inst, n, bb, s.keys, c.idx_a);
+    morton_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(pos_in, inst, n, bb, s.keys, c.idx_a,
+                                                      period_of(p), box_lo_of(p), c.d_err);
     // 3. radix sort (key, slot); a batch adds stable passes on the instance id,
     //    which puts every instance back on its own slots
     const int ntiles = div_up(n, RS_TILE);

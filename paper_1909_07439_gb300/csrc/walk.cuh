@@ -19,10 +19,21 @@ constexpr int kStack = 224;  // node-range stack entries per warp
 constexpr int kRQ = 64;      // leaf-range queue entries per warp
 constexpr float kOpenSlack = 1.0f + 1e-5f;  // keeps FP32 box tests conservative
 
+// Nearest-image separation along one axis: d - L if d > L/2, d + L if
+// d < -L/2.  Positions lie in one period, so |d| < L and, with
+// L/2 <= |d| < L, the correction is exact; L = 0 (open axis) leaves d as it is.
+__device__ __forceinline__ float wrap_sep(float d, float L)
+{
+    const float hL = 0.5f * L;
+    d = d > hL ? __fsub_rn(d, L) : d;
+    return d < -hL ? __fadd_rn(d, L) : d;
+}
+
 struct WalkTree {
     const float4 *__restrict__ node_lo;   // x, y, z, h_max
     const float4 *__restrict__ node_hi;
     const int2 *__restrict__ node_ref;    // leaf (first, count) / internal (child, -nchild)
+    Period per;                           // periodic axes (box distances over images)
 };
 
 struct WalkSmem {
@@ -73,6 +84,15 @@ __device__ __forceinline__ float canon_r2(float xi, float yi, float zi, float xj
     return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
 }
 
+// the same with the nearest image on the periodic axes of P
+__device__ __forceinline__ float canon_r2p(float xi, float yi, float zi, float xj, float yj, float zj,
+                                           const Period &P)
+{
+    float dx = wrap_sep(__fsub_rn(xi, xj), P.x), dy = wrap_sep(__fsub_rn(yi, yj), P.y),
+          dz = wrap_sep(__fsub_rn(zi, zj), P.z);
+    return __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+}
+
 // The same canonical squared distance for two targets at once with the
 // packed FP32x2 instructions: every element is rounded to nearest exactly as
 // in canon_r2 (x - y is formed as x + (-y), which is the same operation).
@@ -82,6 +102,19 @@ __device__ __forceinline__ float2 canon_r2_x2(float2 tx, float2 ty, float2 tz, f
     const float2 dx = __fadd2_rn(tx, make_float2(-xj, -xj));
     const float2 dy = __fadd2_rn(ty, make_float2(-yj, -yj));
     const float2 dz = __fadd2_rn(tz, make_float2(-zj, -zj));
+    return __fadd2_rn(__fadd2_rn(__fmul2_rn(dx, dx), __fmul2_rn(dy, dy)), __fmul2_rn(dz, dz));
+}
+
+// canon_r2_x2 with the nearest image on the periodic axes of P
+__device__ __forceinline__ float2 canon_r2_x2p(float2 tx, float2 ty, float2 tz, float xj, float yj,
+                                               float zj, const Period &P)
+{
+    float2 dx = __fadd2_rn(tx, make_float2(-xj, -xj));
+    float2 dy = __fadd2_rn(ty, make_float2(-yj, -yj));
+    float2 dz = __fadd2_rn(tz, make_float2(-zj, -zj));
+    dx = make_float2(wrap_sep(dx.x, P.x), wrap_sep(dx.y, P.x));
+    dy = make_float2(wrap_sep(dy.x, P.y), wrap_sep(dy.y, P.y));
+    dz = make_float2(wrap_sep(dz.x, P.z), wrap_sep(dz.y, P.z));
     return __fadd2_rn(__fadd2_rn(__fmul2_rn(dx, dx), __fmul2_rn(dy, dy)), __fmul2_rn(dz, dz));
 }
 
@@ -104,6 +137,31 @@ __device__ __forceinline__ float box_dist2(float4 alo, float4 ahi, float4 blo, f
     float dx = fmaxf(0.f, fmaxf(blo.x - ahi.x, alo.x - bhi.x));
     float dy = fmaxf(0.f, fmaxf(blo.y - ahi.y, alo.y - bhi.y));
     float dz = fmaxf(0.f, fmaxf(blo.z - ahi.z, alo.z - bhi.z));
+    return dx * dx + dy * dy + dz * dz;
+}
+
+// Gap along one axis between [alo, ahi] and the nearest of the images of
+// [blo, bhi] shifted by 0, +L, -L (L > 0).  The shifted gaps are lower
+// bounds (rounded down), so a box test on them stays conservative.
+__device__ __forceinline__ float gap_periodic(float alo, float ahi, float blo, float bhi, float L)
+{
+    const float g0 = fmaxf(0.f, fmaxf(blo - ahi, alo - bhi));
+    const float gp = fmaxf(0.f, fmaxf(__fsub_rd(__fadd_rd(blo, L), ahi), __fsub_rd(alo, __fadd_ru(bhi, L))));
+    const float gm = fmaxf(0.f, fmaxf(__fsub_rd(__fsub_rd(blo, L), ahi), __fsub_rd(alo, __fsub_ru(bhi, L))));
+    return fminf(g0, fminf(gp, gm));
+}
+
+// box_dist2 over the nearest images on the periodic axes of the walk's tree
+__device__ __forceinline__ float box_dist2_t(const WalkTree &T, float4 alo, float4 ahi, float4 blo,
+                                             float4 bhi)
+{
+    if (!T.per.any()) return box_dist2(alo, ahi, blo, bhi);
+    float dx = T.per.x > 0.f ? gap_periodic(alo.x, ahi.x, blo.x, bhi.x, T.per.x)
+                             : fmaxf(0.f, fmaxf(blo.x - ahi.x, alo.x - bhi.x));
+    float dy = T.per.y > 0.f ? gap_periodic(alo.y, ahi.y, blo.y, bhi.y, T.per.y)
+                             : fmaxf(0.f, fmaxf(blo.y - ahi.y, alo.y - bhi.y));
+    float dz = T.per.z > 0.f ? gap_periodic(alo.z, ahi.z, blo.z, bhi.z, T.per.z)
+                             : fmaxf(0.f, fmaxf(blo.z - ahi.z, alo.z - bhi.z));
     return dx * dx + dy * dy + dz * dz;
 }
 
@@ -144,7 +202,7 @@ __device__ __forceinline__ void walk_step(const WalkTree &T, float4 glo, float4 
         float4 lo = __ldg(&T.node_lo[node]);
         float4 hi = __ldg(&T.node_hi[node]);
         ref = __ldg(&T.node_ref[node]);
-        float d2 = box_dist2(glo, ghi, lo, hi);
+        float d2 = box_dist2_t(T, glo, ghi, lo, hi);
         float r2 = reach2;
         if (force_mode) {
             float R = 2.0f * fmaxf(hgroup, lo.w * node_scale);
@@ -310,7 +368,7 @@ __device__ __forceinline__ int walk_leaves_wide(const WalkTree &T, int root, flo
         for (int w = 0; w < W; ++w) {
             bool open = false;
             if (node[w] >= 0) {
-                const float d2 = box_dist2(glo, ghi, lo[w], hi[w]);
+                const float d2 = box_dist2_t(T, glo, ghi, lo[w], hi[w]);
                 const float R = 2.0f * fmaxf(hgroup, lo[w].w * node_scale);
                 open = d2 < R * R * kOpenSlack;
             }

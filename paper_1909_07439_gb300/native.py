@@ -36,7 +36,7 @@ class sph_params(ctypes.Structure):
                 ("h_tol", c_float), ("kernel", c_int32), ("n_leaf", c_int32),
                 ("n_group", c_int32), ("tile", c_int32), ("max_h_iter", c_int32),
                 ("density_iters", c_int32), ("pair_targets", c_int32), ("pair_warps", c_int32),
-                ("pair_unroll", c_int32)]
+                ("pair_unroll", c_int32), ("box_lo", c_float * 3), ("box_len", c_float * 3)]
 
 
 class sph_state(ctypes.Structure):
@@ -144,6 +144,8 @@ def sph_params_default(**overrides) -> sph_params:
     for k, v in overrides.items():
         if not hasattr(p, k):
             raise KeyError(k)
+        if k in ("box_lo", "box_len"):
+            v = (c_float * 3)(*[float(x) for x in v])
         setattr(p, k, v)
     return p
 

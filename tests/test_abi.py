@@ -48,7 +48,7 @@ def test_struct_layout_matches_c(tmp_path):
     src.write_text('#include "sph.h"\n#include <stdio.h>\n#include <stddef.h>\n'
                    'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(sph_params),'
                    ' sizeof(sph_state), sizeof(sph_stats), offsetof(sph_state, keys),'
-                   ' offsetof(sph_params, pair_unroll));return 0;}\n')
+                   ' offsetof(sph_params, box_len));return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
                    check=True)
@@ -56,7 +56,7 @@ def test_struct_layout_matches_c(tmp_path):
                                        check=True).stdout.split()))
     assert got == [ctypes.sizeof(native.sph_params), ctypes.sizeof(native.sph_state),
                    ctypes.sizeof(native.sph_stats), native.sph_state.keys.offset,
-                   native.sph_params.pair_unroll.offset]
+                   native.sph_params.box_len.offset]
 
 
 def test_params_default_are_the_papers(lib):
