@@ -108,6 +108,62 @@ def sedov_lattice(side: int = 128, seed: int = 2, jitter: float = 0.1, E: float 
                      "rho0": 1.0, "n_deposit": int(sel.sum())})
 
 
+def shock_tube(nx_left: int, n_left: int, rho: tuple, P: tuple, gamma: float,
+               hfact: float = 1.0, x_range: tuple = (-0.5, 0.5), name: str = "shock_tube") -> Workload:
+    """A two-state shock tube in a box periodic on every axis (Sect. 4.1-4.2).
+
+    The left state fills [x0, xm) with a cubic lattice of nx_left x n_left x
+    n_left particles, spacing dx_L = (xm - x0) / nx_left, xm the midpoint of
+    x_range; the right state fills [xm, x1) with a lattice of spacing
+    dx_R = dx_L (rho_L / rho_R)^(1/3) (equal masses m = rho_L dx_L^3), the
+    cross-section L_yz = n_left dx_L the same for both (so rho_L / rho_R must
+    make n_left dx_L / dx_R a whole number).  Zero velocity,
+    u = P / ((gamma - 1) rho).  Periodic in x too, the tube holds a second
+    interface at x0 = x1 (the same problem mirrored), whose waves start at the
+    tube's ends.  meta: box_lo, box_len and the two states."""
+    x0, x1 = x_range
+    xm = 0.5 * (x0 + x1)
+    dxl = (xm - x0) / nx_left
+    ratio = (rho[0] / rho[1]) ** (1.0 / 3.0)
+    dxr = dxl * ratio
+    Lyz = n_left * dxl
+    n_right = int(round(Lyz / dxr))
+    nx_right = int(round((x1 - xm) / dxr))
+    assert abs(n_right * dxr - Lyz) < 1e-9 * Lyz and abs(nx_right * dxr - (x1 - xm)) < 1e-9
+    parts = []
+    for (nx, ny, dx, xa) in ((nx_left, n_left, dxl, x0), (nx_right, n_right, dxr, xm)):
+        i, j, k = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(ny), indexing="ij")
+        parts.append(np.stack([xa + (i.ravel() + 0.5) * dx, (j.ravel() + 0.5) * dx,
+                               (k.ravel() + 0.5) * dx], axis=1))
+    x = np.concatenate(parts)
+    nl = parts[0].shape[0]
+    n = x.shape[0]
+    m = np.full(n, rho[0] * dxl ** 3)
+    rh = np.where(np.arange(n) < nl, rho[0], rho[1])
+    u = np.where(np.arange(n) < nl, P[0], P[1]) / ((gamma - 1.0) * rh)
+    pos, vel = _pack(x, m, np.zeros((n, 3)), u)
+    h = (hfact * (m / rh) ** (1.0 / 3.0)).astype(np.float32)
+    box_lo = (float(x0), 0.0, 0.0)
+    box_len = (float(x1 - x0), float(Lyz), float(Lyz))
+    return Workload(name, pos, vel, h,
+                    {"box_lo": box_lo, "box_len": box_len, "gamma": gamma, "x_mid": xm,
+                     "left": (rho[0], 0.0, P[0]), "right": (rho[1], 0.0, P[1]),
+                     "dx": (dxl, dxr)})
+
+
+def sod_tube(nx_left: int = 256, n_left: int = 24, hfact: float = 1.0) -> Workload:
+    """Sod's shock tube as in Sect. 4.1: [rho, P] = [1, 1] left with
+    256 x 24 x 24 particles, [0.125, 0.1] right with 128 x 12 x 12, gamma =
+    5/3, in [-0.5, 0.5) x L_yz^2."""
+    return shock_tube(nx_left, n_left, (1.0, 0.125), (1.0, 0.1), 5.0 / 3.0, hfact, name="sod_tube")
+
+
+def blast_tube(nx_left: int = 400, n_left: int = 12, hfact: float = 1.0) -> Workload:
+    """The blast wave of Sect. 4.2: [rho, P] = [1, 1000] left and [1, 0.1]
+    right, 400 x 12 x 12 particles each, gamma = 7/5, in [-0.5, 0.5) x L_yz^2."""
+    return shock_tube(nx_left, n_left, (1.0, 1.0), (1000.0, 0.1), 1.4, hfact, name="blast_tube")
+
+
 def plummer(n: int = 1 << 24, seed: int = 3, a: float = 0.1, rmax: float = 1.0,
             hfact: float = HFACT) -> Workload:
     """Plummer gas sphere (scale a, truncated at rmax), m = 1/n, v = 0,

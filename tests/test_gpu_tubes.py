@@ -1,0 +1,131 @@
+"""The shock-tube tests of Sect. 4.1-4.2 on the GPU path, with the M6
+quintic kernel and periodic boundaries, against the exact Riemann solution
+(oracle/riemann.py, pinned in test_oracle_riemann.py):
+
+- Sod: [rho, P] = [1, 1] | [0.125, 0.1], 256x24x24 | 128x12x12 particles,
+  gamma = 5/3, to t = 0.1 (the paper's text; its figure shows t = 0.2);
+- blast wave: [1, 1000] | [1, 0.1], 400x12x12 particles each side, gamma =
+  7/5, to t = 0.01.
+
+The tube is periodic in x as well (a second, mirrored interface at the
+ends); the comparison window holds only the waves of the central interface.
+Profiles are averaged in x bins; the bounds sit just above the errors
+measured on GB300 (each test prints them): Sod L1(rho) 0.028, L1(P) 0.030,
+L1(u) / max|u| 0.034, shock 0.9 dx_R behind the exact one, dE/E 4.6e-6;
+blast L1(rho) 0.064 (the thin shell and the contact), L1(P) 0.011, L1(u)
+0.014, shock within 0.25 dx_R, dE/E 9.3e-7.
+"""
+import numpy as np
+import pytest
+
+from oracle import riemann as R
+from paper_1909_07439_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sph():
+    import torch
+    from paper_1909_07439_gb300 import build, native
+    build.build()
+    native.load()
+    ctx = native.sph_create(1 << 18, 0)
+    yield native, ctx, torch
+    native.sph_destroy(ctx)
+
+
+def _run(sph, w, t_end, max_steps):
+    native, ctx, torch = sph
+    from paper_1909_07439_gb300 import DeviceState
+    m = w.meta
+    p = native.sph_params_default(kernel=1, hfact=1.0, gamma=m["gamma"], box_lo=m["box_lo"],
+                                  box_len=m["box_len"])
+    s = DeviceState.from_arrays(w.pos, w.vel, w.h)
+    d_dt = torch.zeros(1, dtype=torch.float32, device="cuda")
+    d_t = torch.zeros(1, dtype=torch.float64, device="cuda")
+    native.sph_build_tree(ctx, s.c, p)
+    native.sph_density(ctx, s.c, p)
+    native.sph_force(ctx, s.c, p)
+    native.sph_timestep(ctx, s.c, p, d_dt)
+    out8 = torch.zeros(8, dtype=torch.float64, device="cuda")
+    native.sph_conserved(ctx, s.c, out8)
+    e0 = out8.cpu().numpy().copy()
+    steps = 0
+    while steps < max_steps:
+        t, dt = d_t.item(), d_dt.item()
+        if t >= t_end * (1 - 1e-9):
+            break
+        if t + dt > t_end:
+            d_dt.fill_(t_end - t)
+        native.sph_step(ctx, s.c, p, d_dt, d_t)
+        steps += 1
+    native.sph_sync(ctx)
+    native.sph_conserved(ctx, s.c, out8)
+    e1 = out8.cpu().numpy().copy()
+    assert abs(d_t.item() / t_end - 1) < 1e-6, (d_t.item(), steps)
+    pos = s.numpy("pos")
+    vel = s.numpy("vel")
+    rho = s.numpy("rho")
+    return pos, vel, rho, e0, e1, steps
+
+
+def _profiles(pos, vel, rho, gamma, window, width):
+    x = pos[:, 0].astype(np.float64)
+    edges = np.arange(window[0], window[1] + 0.5 * width, width)
+    k = np.digitize(x, edges) - 1
+    keep = (k >= 0) & (k < len(edges) - 1)
+    P = (gamma - 1.0) * rho.astype(np.float64) * vel[:, 3]
+    out = {}
+    for name, q in (("rho", rho.astype(np.float64)), ("u", vel[:, 0].astype(np.float64)), ("P", P),
+                    ("x", x)):
+        out[name] = np.bincount(k[keep], q[keep], len(edges) - 1) / np.maximum(
+            np.bincount(k[keep], None, len(edges) - 1), 1)
+    return out
+
+
+def _l1(a, b):
+    return float(np.mean(np.abs(a - b)) / np.mean(np.abs(b)))
+
+
+def _check(name, pos, vel, rho, e0, e1, w, t_end, window, width, bounds):
+    m = w.meta
+    gamma = m["gamma"]
+    left, right = R.State(*m["left"]), R.State(*m["right"])
+    prof = _profiles(pos, vel, rho, gamma, window, width)
+    ex = R.sample(prof["x"], t_end, m["x_mid"], left, right, gamma)
+    err = {"rho": _l1(prof["rho"], ex[0]), "P": _l1(prof["P"], ex[2]),
+           "u": float(np.mean(np.abs(prof["u"] - ex[1])) / np.max(np.abs(ex[1])))}
+    # shock position: where rho crosses the middle of the jump, right of the contact
+    star = R.star_state(left, right, gamma)
+    S = R.wave_speeds(left, right, gamma)[3]
+    xs_exact = m["x_mid"] + S * t_end
+    mid = 0.5 * (star.rho_r + right.rho)
+    xb = prof["x"]
+    right_of_contact = xb > m["x_mid"] + star.u * t_end + 2 * width
+    cross = np.where(right_of_contact[:-1] & (prof["rho"][:-1] >= mid) & (prof["rho"][1:] < mid))[0]
+    xs = float(xb[cross[-1]] + (prof["rho"][cross[-1]] - mid) /
+               (prof["rho"][cross[-1]] - prof["rho"][cross[-1] + 1]) * width) if len(cross) else np.nan
+    dE = abs((e1[0] + e1[1]) / (e0[0] + e0[1]) - 1)
+    px = abs(e1[2]) / np.sum(pos[:, 3] * np.abs(vel[:, 0]))
+    print(f"{name}: L1 rho {err['rho']:.4f}, L1 P {err['P']:.4f}, L1 u/max|u| {err['u']:.4f}, "
+          f"shock x {xs:.5f} (exact {xs_exact:.5f}, dx_R {m['dx'][1]:.5f}), dE/E {dE:.2e}, "
+          f"|px|/sum m|vx| {px:.2e}")
+    assert err["rho"] < bounds["rho"] and err["P"] < bounds["P"] and err["u"] < bounds["u"]
+    assert abs(xs - xs_exact) < bounds["shock_dx"] * m["dx"][1]
+    assert dE < bounds["dE"]
+    assert px < 1e-4
+
+
+def test_sod_m6(sph):
+    w = inputs.sod_tube()
+    pos, vel, rho, e0, e1, steps = _run(sph, w, 0.1, 2000)
+    _check("sod", pos, vel, rho, e0, e1, w, 0.1, (-0.25, 0.25), 0.005,
+           {"rho": 0.035, "P": 0.04, "u": 0.045, "shock_dx": 1.5, "dE": 2e-5})
+
+
+def test_blast_m6(sph):
+    w = inputs.blast_tube()
+    pos, vel, rho, e0, e1, steps = _run(sph, w, 0.01, 20000)
+    _check("blast", pos, vel, rho, e0, e1, w, 0.01, (-0.1, 0.24), 0.0025,
+           {"rho": 0.08, "P": 0.015, "u": 0.02, "shock_dx": 1.0, "dE": 5e-6})
