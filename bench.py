@@ -47,6 +47,11 @@ SIDE = 128
 FLOP_FORCE_PAIR = 86
 FLOP_DENSITY_PAIR = 45
 FLOP_TEST = 8
+# The same counts for the other kernels: the branch-free shape functions cost
+# more than M4's (f: M4 6, M6 16, Wendland C6 12; f': M4 4, M6 14, Wendland
+# C6 13 operations), and a force pair evaluates f' twice, a density pair f
+# twice (W and dW/dh) and f' once.
+FLOP_PAIR = {0: (FLOP_FORCE_PAIR, FLOP_DENSITY_PAIR), 1: (106, 75), 2: (104, 66)}
 # Executed FP32 operations per force pair of the list kernel
 # (2 FFMA + FADD + FMUL from ncu's sass instruction counters over one launch
 # of the 128^3 step, 2.71e9 FFMA, 2.05e9 FADD, 3.54e9 FMUL, divided by that
@@ -158,14 +163,15 @@ def measure_fp32_peak(native, torch, sms, device_index, target_ms=400.0):
     return out
 
 
-def roofline(stage_ms, stats, reps, fp32_peak, peak_basis, hbm_peak, n):
+def roofline(stage_ms, stats, reps, fp32_peak, peak_basis, hbm_peak, n, kernel=0):
     """Roofline of the pair-kernel stages (FP32 ALU bound) and of the tree
     build (HBM bound), from the library's stage timers (CUDA events on the
     launching stream) summed over `reps` launches and the work counters."""
+    f_force, f_dens = FLOP_PAIR[kernel]
     work = {"lists": ("nlist_kernel", stats["density_candidates"] * FLOP_TEST, None),
-            "density": ("density_list_kernel", stats["density_pairs"] * FLOP_DENSITY_PAIR, None),
-            "force": ("force_list_kernel", stats["force_pairs"] * FLOP_FORCE_PAIR,
-                      stats["force_pairs"] * EXEC_FLOP_FORCE_PAIR)}
+            "density": ("density_list_kernel", stats["density_pairs"] * f_dens, None),
+            "force": ("force_list_kernel", stats["force_pairs"] * f_force,
+                      stats["force_pairs"] * EXEC_FLOP_FORCE_PAIR if kernel == 0 else None)}
     stages = {}
     for st, (kern, flop, exe) in work.items():
         ms = stage_ms[st] / reps
@@ -181,7 +187,7 @@ def roofline(stage_ms, stats, reps, fp32_peak, peak_basis, hbm_peak, n):
     roof = {"kernel": d["kernel"], "bound": "alu", "achieved": d["achieved"],
             "peak": round(fp32_peak, 2), "unit": "TFLOP/s", "frac": d["frac"],
             "traffic": NCU_TRAFFIC.get(d["kernel"]), "peak_basis": peak_basis,
-            "launch_ms": d["launch_ms"], "flop_per_pair": FLOP_FORCE_PAIR if dom == "force" else None,
+            "launch_ms": d["launch_ms"], "flop_per_pair": f_force if dom == "force" else None,
             "stages": stages}
     if "achieved_executed" in d:
         roof["achieved_executed"] = d["achieved_executed"]
@@ -325,6 +331,8 @@ def run_ours(args):
     adjoint = run_adjoint(args) if rank == 0 and args.adjoint_side > 0 else None
     plummer = (run_plummer(args, fp32_peak, basis, pk.get("hbm_gbs", 6800.0))
                if rank == 0 and args.plummer_log2 > 0 else None)
+    tube = (run_tube(args, fp32_peak, basis, pk.get("hbm_gbs", 6800.0))
+            if rank == 0 and args.tube_scale > 0 else None)
     out = None
     if rank == 0:
         cpu = run_cpu_baseline(w, args.cpu_seconds) if args.cpu_seconds > 0 else None
@@ -354,6 +362,7 @@ def run_ours(args):
             "batched": batched,
             "adjoint": adjoint,
             "plummer": plummer,
+            "tube": tube,
         }
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -533,6 +542,59 @@ def run_plummer(args, fp32_peak, basis, hbm_peak):
             "n_group": p.n_group, "n_leaf": p.n_leaf, "autotune": tuned}
 
 
+def run_tube(args, fp32_peak, basis, hbm_peak):
+    """Sod shock tube (Sect. 4.1) with the M6 kernel and periodic boundaries,
+    the paper's setup scaled by --tube-scale per axis: untimed steps until
+    the waves have formed, then timed steps with CUDA events."""
+    import torch
+    from paper_1909_07439_gb300 import DeviceState, inputs, native
+    k = args.tube_scale
+    w = inputs.sod_tube(256 * k, 24 * k)
+    m = w.meta
+    ctx = native.sph_create(w.n, 0)
+    s = DeviceState.from_arrays(w.pos, w.vel, w.h)
+    p = native.sph_params_default(kernel=1, hfact=1.0, gamma=m["gamma"], box_lo=m["box_lo"],
+                                  box_len=m["box_len"], n_group=16)
+    d_dt = torch.zeros(1, dtype=torch.float32, device="cuda")
+    d_t = torch.zeros(1, dtype=torch.float64, device="cuda")
+    native.sph_build_tree(ctx, s.c, p)
+    native.sph_density(ctx, s.c, p)
+    native.sph_force(ctx, s.c, p)
+    native.sph_timestep(ctx, s.c, p, d_dt)
+    for _ in range(30):
+        native.sph_step(ctx, s.c, p, d_dt, d_t)
+    native.sph_sync(ctx)
+    native.sph_get_stats(ctx)
+    native.sph_get_timing(ctx)
+    native.sph_set_timing(ctx, True)
+    reps = 40
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        native.sph_step(ctx, s.c, p, d_dt, d_t)
+    e1.record()
+    torch.cuda.synchronize()
+    native.sph_sync(ctx)
+    ms = e0.elapsed_time(e1) / reps
+    stage, _ = native.sph_get_timing(ctx)
+    native.sph_set_timing(ctx, False)
+    stats = native.sph_get_stats(ctx)
+    t = d_t.item()
+    native.sph_destroy(ctx)
+    roof = roofline(stage, stats, reps, fp32_peak, basis, hbm_peak, w.n, kernel=1)
+    return {"workload": f"Sod shock tube, M6 kernel, periodic box, {256 * k}x{24 * k}^2 | "
+                        f"{128 * k}x{12 * k}^2 particles ({w.n})",
+            "value": w.n / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": reps,
+            "sim_time_after": t,
+            "pair_interactions_per_s": (stats["density_pairs"] + stats["force_pairs"]) / reps / (ms / 1e3),
+            "stage_ms": {kk: v / reps for kk, v in stage.items()},
+            "work_per_step": {kk: v / reps for kk, v in stats.items()
+                              if kk in ("density_pairs", "force_pairs", "newton_iters",
+                                        "density_rewalks", "force_rewalks", "list_overflows")},
+            "roofline": roof}
+
+
 def run_e2e(native, ctx, s, p, n, args, stream):
     """Same metric through the C ABI with the state in pinned HOST memory:
     every step copies the inputs in and the whole state back."""
@@ -654,6 +716,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--adjoint-side", type=int, default=64)
     ap.add_argument("--plummer-log2", type=int, default=24)
+    ap.add_argument("--tube-scale", type=int, default=2,
+                    help="Sod/M6/periodic leg: the paper's tube scaled per axis (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -97,7 +97,6 @@ static double shape_df(int kernel, double q) /* df/dq */
     return 0.0;
 }
 
-/* W(r, h) */
 /* nearest-image separation along one axis (L = 0: open axis) */
 static double wrap_d(double d, double L)
 {
@@ -127,6 +126,7 @@ static void sep3(const double *x, int64_t i, int64_t j, const double *box, doubl
     }
 }
 
+/* W(r, h) */
 static double kern_w(int k, double r, double h) { return kern_norm(k) * shape_f(k, r / h) / (h * h * h); }
 /* F(r, h) = C f'(q) / h^4 = dW/dr (Eq. 14); grad_i W_ij(h) = rhat_ij F(r_ij, h) */
 static double kern_F(int k, double r, double h)
