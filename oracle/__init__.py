@@ -72,6 +72,7 @@ def _load():
             lib.orc_force.argtypes = [P, P, P, P, P, P, P, i64, P, i64, f64, f64, f64,
                                       f64, f64, P, P, P, P, ctypes.c_int, P]
             lib.orc_conserved.argtypes = [P, P, P, P, i64, P]
+            lib.orc_gravity.argtypes = [P, P, i64, P, i64, f64, f64, P]
             _lib = lib
     return _lib
 
@@ -258,6 +259,17 @@ def force(x, v, m, u, h, rho, omega, targets=None, gamma=5.0 / 3.0, alpha=1.0, b
                       float(alpha_u), float(vsig_scale), _ptr(acc), _ptr(dudt), _ptr(vsig),
                       _ptr(nf), int(kernel), _bptr(b))
     return Force(acc, dudt, vsig, nf)
+
+
+def gravity(x, m, G=1.0, eps=0.01, targets=None):
+    """Softened self-gravity by direct summation (the a_grav of Eq. 9):
+    returns (acc [nt, 3], phi [nt]) for the targets."""
+    x, m = _f64(x), _f64(m)
+    n = m.size
+    t = _targets(targets, n)
+    out = np.zeros((t.size, 4))
+    _load().orc_gravity(_ptr(x), _ptr(m), n, _ptr(t), t.size, float(G), float(eps), _ptr(out))
+    return out[:, :3].copy(), out[:, 3].copy()
 
 
 def conserved(x, v, m, u):

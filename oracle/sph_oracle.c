@@ -542,3 +542,39 @@ ORC_API void orc_conserved(const double *x, const double *v, const double *m, co
     }
     memcpy(out8, e, sizeof(e));
 }
+
+/* ------------------------------------------------------------------------- */
+/* Self-gravity (the a_grav term of Eq. 9), the plain definition: a direct   */
+/* sum over every other particle with Plummer softening eps,                 */
+/*   a_i   = -G sum_{j != i} m_j (x_i - x_j) / (|x_i - x_j|^2 + eps^2)^(3/2) */
+/*   phi_i = -G sum_{j != i} m_j / (|x_i - x_j|^2 + eps^2)^(1/2)            */
+/* (the tree code of the paper approximates this sum with the Barnes-Hut    */
+/* walk; the potential energy is 1/2 sum_i m_i phi_i).                       */
+/* out4[4 t .. 4 t + 3] = (a_x, a_y, a_z, phi) of target t.                  */
+/* ------------------------------------------------------------------------- */
+ORC_API void orc_gravity(const double *x, const double *m, int64_t n, const int64_t *targets,
+                         int64_t nt, double G, double eps, double *out4)
+{
+    const double e2 = eps * eps;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t t = 0; t < nt; ++t) {
+        int64_t i = targets[t];
+        double ax = 0.0, ay = 0.0, az = 0.0, phi = 0.0;
+        for (int64_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double dx = x[3 * i] - x[3 * j], dy = x[3 * i + 1] - x[3 * j + 1],
+                   dz = x[3 * i + 2] - x[3 * j + 2];
+            double r2 = dx * dx + dy * dy + dz * dz + e2;
+            double rinv = 1.0 / sqrt(r2);
+            double mr3 = m[j] * rinv * rinv * rinv;
+            ax -= mr3 * dx;
+            ay -= mr3 * dy;
+            az -= mr3 * dz;
+            phi -= m[j] * rinv;
+        }
+        out4[4 * t] = G * ax;
+        out4[4 * t + 1] = G * ay;
+        out4[4 * t + 2] = G * az;
+        out4[4 * t + 3] = G * phi;
+    }
+}
