@@ -88,6 +88,19 @@ typedef struct {
      * reports SPH_ERR_INVALID_ARG otherwise).                              */
     float box_lo[3];
     float box_len[3];
+    /* Self-gravity, the a_grav term of Eq. 9 (Sect. 2.4): grav_G > 0 adds the
+     * Newtonian acceleration of every particle, with Plummer softening
+     * grav_eps, to acc in every force pass, by a Barnes-Hut walk of the same
+     * tree (a node whose centre of mass lies farther than
+     * l / grav_theta + delta from a group's box acts on the group through its
+     * monopole and quadrupole; l its longest edge, delta the offset of its
+     * centre of mass from its box centre).  grav_G = 0 (default): no gravity.
+     * With grav_G > 0: grav_eps > 0, 0 < grav_theta <= 0.57 (no node that
+     * holds a target is ever accepted), and no periodic axis; the adjoint
+     * entry points reject it (gravity is not differentiated).             */
+    float grav_G;
+    float grav_eps;
+    float grav_theta;
 } sph_params;
 
 /* Particle state, structure of arrays, n particles, device memory.
@@ -257,6 +270,16 @@ sph_status sph_conserved(sph_ctx *ctx, const sph_state *s, double *d_out8, void 
 sph_status sph_conserved_noalloc(int64_t n, const float *d_pos, const float *d_vel,
                                  double *d_out8, void *stream);
 
+/* Self-gravity alone (the a_grav term of Eq. 9, see sph_params.grav_G):
+ * d_out4[4 k .. 4 k + 3] = (a_x, a_y, a_z, phi) of slot k, G included, by
+ * the Barnes-Hut walk of the tree built by the last sph_build_tree on this
+ * state (positions unchanged since).  The potential energy is
+ * 1/2 sum_k m_k phi_k.  d_out4: device, 16-byte aligned, n float4.
+ * SPH_ERR_INVALID_ARG unless grav_G > 0 and the gravity parameters are
+ * valid.  Asynchronous. */
+sph_status sph_gravity(sph_ctx *ctx, const sph_state *s, const sph_params *p, float *d_out4,
+                       void *stream);
+
 /* Neighbour sets of the current tree/state (Sect. 3.2), for testing.
  * mode 0: density set {j : r2 < (R h_i)^2} (includes i);
  * mode 1: force set {j != i : r2 < (R max(h_i, h_j))^2};
@@ -316,6 +339,8 @@ typedef struct {
     uint64_t force_rewalks;       /* target batches of the force pass solved by the
                                      walking fallback (lists stale, overflowed, or an
                                      h of the instance outgrew the list pad)          */
+    uint64_t gravity_cells;       /* target-node (multipole) gravity interactions      */
+    uint64_t gravity_particles;   /* target-particle gravity interactions             */
 } sph_stats;
 sph_status sph_get_stats(sph_ctx *ctx, sph_stats *out);
 
@@ -323,11 +348,12 @@ sph_status sph_get_stats(sph_ctx *ctx, sph_stats *out);
  * Stages: 0 tree build, 1 density (h-rho solve), 2 force, 3 reductions
  * (dt, conserved), 4 leapfrog kicks/drift, 5 force preparation (per-particle
  * sound speed and node/group h_max, also refreshed before the density pass),
- * 6 neighbour lists (the list-building tree walk of the density pass).
+ * 6 neighbour lists (the list-building tree walk of the density pass),
+ * 7 self-gravity (multipole moments and the Barnes-Hut walk).
  * sph_get_timing synchronises and returns the milliseconds summed since the
  * last call, and the number of kernels launched per stage (also counted when
  * timing is off); both arrays hold SPH_N_STAGES entries. */
-#define SPH_N_STAGES 7
+#define SPH_N_STAGES 8
 sph_status sph_set_timing(sph_ctx *ctx, int enable);
 sph_status sph_get_timing(sph_ctx *ctx, double *ms_by_stage, int64_t *launches_by_stage);
 

@@ -406,6 +406,13 @@ void sph::release_rollout(Ctx &c)
     c.rollout = nullptr;
 }
 
+// parameters the adjoint passes take: a built kernel, no gravity (its
+// a_grav term is not differentiated)
+static bool adjoint_params_ok(const sph_params *p)
+{
+    return p->kernel >= 0 && p->kernel <= 2 && p->grav_G == 0.f;
+}
+
 extern "C" sph_status sph_rollout(sph_ctx *h, const sph_state *init, const sph_params *p,
                                   int n_steps, int ckpt, const int64_t *d_probes, int n_probes,
                                   double *h_loss, float *d_gvel, double *h_galpha, void *stream)
@@ -414,7 +421,7 @@ extern "C" sph_status sph_rollout(sph_ctx *h, const sph_state *init, const sph_p
     Ctx &c = h->impl;
     if (init->n < 1 || init->n > c.max_n || !init->pos || !init->vel || !init->h)
         return SPH_ERR_INVALID_ARG;
-    if (n_steps < 1 || ckpt < 1 || n_probes < 1) return SPH_ERR_INVALID_ARG;
+    if (n_steps < 1 || ckpt < 1 || n_probes < 1 || !adjoint_params_ok(p)) return SPH_ERR_INVALID_ARG;
     if ((d_gvel == nullptr) != (h_galpha == nullptr)) return SPH_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     RB *rb = nullptr;
@@ -454,7 +461,7 @@ extern "C" sph_status sph_force_bwd(sph_ctx *h, const sph_state *s, const sph_pa
         !d_galpha)
         return SPH_ERR_INVALID_ARG;
     Ctx &c = h->impl;
-    if (s->n < 1 || s->n > c.max_n) return SPH_ERR_INVALID_ARG;
+    if (s->n < 1 || s->n > c.max_n || !adjoint_params_ok(p)) return SPH_ERR_INVALID_ARG;
     cudaError_t e = force_bwd(c, *s, *p, (const float4 *)d_gacc, (float4 *)d_gpos, (float4 *)d_gvel,
                               d_gh, d_grho, d_gomega, d_galpha, (cudaStream_t)stream);
     return e == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
@@ -466,7 +473,7 @@ extern "C" sph_status sph_density_bwd(sph_ctx *h, const sph_state *s, const sph_
 {
     if (!h || !s || !p || !d_gh || !d_grho || !d_gomega || !d_gpos) return SPH_ERR_INVALID_ARG;
     Ctx &c = h->impl;
-    if (s->n < 1 || s->n > c.max_n) return SPH_ERR_INVALID_ARG;
+    if (s->n < 1 || s->n > c.max_n || !adjoint_params_ok(p)) return SPH_ERR_INVALID_ARG;
     // the per-particle multipliers use context scratch (one float2 per particle)
     cudaError_t e = density_bwd(c, *s, *p, d_gh, d_grho, d_gomega, (float4 *)d_gpos,
                                 reinterpret_cast<float2 *>(c.tmp4[3]), (cudaStream_t)stream);

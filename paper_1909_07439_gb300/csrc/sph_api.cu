@@ -134,6 +134,15 @@ sph_status check_params(Ctx &c, const sph_params *p)
     for (int a = 0; a < 3; ++a)
         if (!(p->box_len[a] >= 0.f) || !std::isfinite(p->box_len[a]) || !std::isfinite(p->box_lo[a]))
             return fail(c, SPH_ERR_INVALID_ARG, "box_len must be finite and >= 0, box_lo finite");
+    if (!(p->grav_G >= 0.f) || !std::isfinite(p->grav_G))
+        return fail(c, SPH_ERR_INVALID_ARG, "grav_G must be finite and >= 0");
+    if (p->grav_G > 0.f) {
+        if (!(p->grav_eps > 0.f) || !std::isfinite(p->grav_eps) || !(p->grav_theta > 0.f) ||
+            !(p->grav_theta <= 0.57f))
+            return fail(c, SPH_ERR_INVALID_ARG, "gravity needs grav_eps > 0 and 0 < grav_theta <= 0.57");
+        if (p->box_len[0] > 0.f || p->box_len[1] > 0.f || p->box_len[2] > 0.f)
+            return fail(c, SPH_ERR_INVALID_ARG, "gravity with periodic boundaries is not built");
+    }
     return SPH_OK;
 }
 
@@ -176,9 +185,15 @@ sph_status do_force(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_
         CK(force_prep(c, s, p, st), "force_prep");
         if (!records_fresh) CK(pack_records(c, s, st), "pack");
     }
-    // relist (h_max refresh 2, list kernel 1), list kernel, h_max refresh 2, walking fallback
-    StageScope sc(c, ST_FORCE, st, 7);
-    CK(force_pass(c, s, p, st), "force");
+    {
+        // relist (h_max refresh 2, list kernel 1), list kernel, h_max refresh 2, walking fallback
+        StageScope sc(c, ST_FORCE, st, 7);
+        CK(force_pass(c, s, p, st), "force");
+    }
+    if (p.grav_G > 0.f) {
+        StageScope sc(c, ST_GRAVITY, st, 2);  // moments, walk
+        CK(gravity_pass(c, s, p, (float4 *)s.acc, nullptr, st), "gravity");
+    }
     return SPH_OK;
 }
 
@@ -266,6 +281,7 @@ sph_status record_step_graph(Ctx &c, Ctx::StepGraph &g, const sph_state &s, cons
     CK(configure_density_kernels(p.kernel), "configure density");
     CK(configure_force_kernels(p.kernel), "configure force");
     CK(configure_nlist_kernels(), "configure lists");
+    CK(configure_gravity_kernels(), "configure gravity");
     if (!c.capture_stream)
         CK(cudaStreamCreateWithFlags(&c.capture_stream, cudaStreamNonBlocking), "capture stream");
     cudaStream_t cs = c.capture_stream;
@@ -340,6 +356,9 @@ void sph_params_default(sph_params *p)
         p->box_lo[a] = 0.f;
         p->box_len[a] = 0.f;
     }
+    p->grav_G = 0.f;
+    p->grav_eps = 0.01f;
+    p->grav_theta = 0.5f;
 }
 
 sph_status sph_create(sph_ctx **out, int64_t max_n, int device)
@@ -410,6 +429,9 @@ sph_status sph_create(sph_ctx **out, int64_t max_n, int device)
     A(dalloc(c.prop, n));
     A(dalloc(c.frec, 3 * n));
     A(dalloc(c.vhalf, n));
+    A(dalloc(c.g_com, t.cap_nodes));
+    A(dalloc(c.g_q0, t.cap_nodes));
+    A(dalloc(c.g_q1, t.cap_nodes));
     A(dalloc(c.inst, n));
     A(dalloc(c.bbox_inst, (size_t)6 * kMaxInstances));
     A(dalloc(c.dtmin_inst, kMaxInstances));
@@ -449,7 +471,8 @@ void sph_destroy(sph_ctx *h)
                     c.tree.grp_lo, c.tree.grp_hi, c.tree.lv_tree, c.tree.lv_grp, c.tree.blk_cnt,
                     c.nl_idx, c.nl_len, c.fallback,
                     c.tree.rec_ctl, c.tree.rec_bad,
-                    c.rec, c.prop, c.frec, c.vhalf, c.inst, c.bbox_inst, c.dtmin_inst,
+                    c.rec, c.prop, c.frec, c.vhalf, c.g_com, c.g_q0, c.g_q1, c.inst, c.bbox_inst,
+                    c.dtmin_inst,
                     c.bbox, c.scan_part, c.red_f, c.red_d, c.d_err, c.d_counters,
                     c.d_sizes, c.mirror.pos, c.mirror.vel, c.mirror.acc, c.mirror.h, c.mirror.rho,
                     c.mirror.omega, c.mirror.drhodt, c.mirror.vsigmax, c.mirror.perm,
@@ -499,6 +522,23 @@ sph_status sph_force(sph_ctx *h, sph_state *s, const sph_params *p, void *stream
     if ((r = check_params(c, p)) != SPH_OK) return r;
     if (s->n == 0) return SPH_OK;
     return do_force(c, *s, *p, (cudaStream_t)stream, false);
+}
+
+sph_status sph_gravity(sph_ctx *h, const sph_state *s, const sph_params *p, float *d_out4,
+                       void *stream)
+{
+    if (!h) return SPH_ERR_INVALID_ARG;
+    Ctx &c = h->impl;
+    sph_status r = check_state(c, s, false);
+    if (r != SPH_OK) return r;
+    if ((r = check_params(c, p)) != SPH_OK) return r;
+    if (!(p->grav_G > 0.f)) return fail(c, SPH_ERR_INVALID_ARG, "sph_gravity needs grav_G > 0");
+    if (!d_out4 || ((uintptr_t)d_out4 & 15)) return fail(c, SPH_ERR_INVALID_ARG, "d_out4 NULL or not 16-byte aligned");
+    if (s->n == 0) return SPH_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    StageScope sc(c, ST_GRAVITY, st, 2);
+    CK(gravity_pass(c, *s, *p, nullptr, (float4 *)d_out4, st), "gravity");
+    return SPH_OK;
 }
 
 sph_status sph_timestep(sph_ctx *h, const sph_state *s, const sph_params *p, float *d_dt,
@@ -689,6 +729,7 @@ cudaError_t enqueue_batch_step(Ctx &c, const sph_state &s, const sph_params &p, 
     if (e == cudaSuccess) e = density_pass(c, s, p, st, &b);
     if (e == cudaSuccess) e = force_prep(c, s, p, st);
     if (e == cudaSuccess) e = force_pass(c, s, p, st, &b);
+    if (e == cudaSuccess && p.grav_G > 0.f) e = gravity_pass(c, s, p, (float4 *)s.acc, nullptr, st, &b);
     if (e == cudaSuccess) e = kick_close(c, s, d_dt, d_time, st, &b);
     if (e == cudaSuccess) e = courant_dt(c, s, p, d_dt, st, &b);
     return e;
@@ -747,6 +788,7 @@ sph_status sph_batch_step(sph_ctx *h, sph_state *s, const int64_t *d_offsets, in
         CK(configure_density_kernels(p->kernel), "configure density");
         CK(configure_force_kernels(p->kernel), "configure force");
         CK(configure_nlist_kernels(), "configure lists");
+        CK(configure_gravity_kernels(), "configure gravity");
         // record on a private stream: the caller's may be the legacy default
         // stream, which cannot be captured
         if (!c.capture_stream)
@@ -886,6 +928,8 @@ sph_status sph_get_stats(sph_ctx *h, sph_stats *out)
     out->list_entries = v[C_LIST_ENTRIES];
     out->list_overflows = v[C_LIST_OVERFLOW];
     out->force_rewalks = v[C_FORCE_FB];
+    out->gravity_cells = v[C_GRAV_CELLS];
+    out->gravity_particles = v[C_GRAV_PARTS];
     out->n_nodes = (uint64_t)sz[SZ_NODES];
     out->n_groups = (uint64_t)sz[SZ_GROUPS];
     return SPH_OK;

@@ -29,7 +29,7 @@ constexpr float kListPad = 0.03f;    // neighbour-list radius margin, relative t
 // stage ids for the per-stage timers
 enum Stage {
     ST_TREE = 0, ST_DENSITY = 1, ST_FORCE = 2, ST_REDUCE = 3, ST_LEAPFROG = 4, ST_PREP = 5, ST_LISTS = 6,
-    ST_N = 7
+    ST_GRAVITY = 7, ST_N = 8
 };
 
 // device error word: bit (1 << status) per condition seen
@@ -50,6 +50,8 @@ enum Counter {
     C_LIST_ENTRIES = 7,
     C_LIST_OVERFLOW = 8,
     C_FORCE_FB = 9,
+    C_GRAV_CELLS = 10,
+    C_GRAV_PARTS = 11,
     C_N = 12
 };
 
@@ -131,6 +133,9 @@ struct Ctx {
     // ((R h)^2, G C / (h^4 rho Omega), alpha_AV c_s, rho)
     float4 *frec = nullptr;
     float4 *vhalf = nullptr;  // half-step v, u of the leapfrog
+    // [cap_nodes] gravity moments: (centre of mass, M), (Qxx, Qyy, Qzz, r_open^2),
+    // (Qxy, Qxz, Qyz, -)
+    float4 *g_com = nullptr, *g_q0 = nullptr, *g_q1 = nullptr;
     float *bbox = nullptr;    // [8]: lo xyz, size, then scratch
     // batches
     int *inst = nullptr;       // [max_n] instance of each slot
@@ -259,6 +264,11 @@ cudaError_t force_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStre
 // `kernel` (before any graph capture)
 cudaError_t configure_density_kernels(int kernel);
 cudaError_t configure_force_kernels(int kernel);
+// gravity.cu: the moments pass and the Barnes-Hut walk; adds G a to acc.xyz
+// and/or writes (G a, G phi) to out (either may be null)
+cudaError_t gravity_pass(Ctx &c, const sph_state &s, const sph_params &p, float4 *acc, float4 *out,
+                         cudaStream_t st, const Batch *batch = nullptr);
+cudaError_t configure_gravity_kernels();
 // integrate.cu
 // with a batch, d_dt and d_time hold one value per instance
 // (drifted positions wrap into the periodic box of p)

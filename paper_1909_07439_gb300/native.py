@@ -17,7 +17,7 @@ SPH_OK = 0
 STATUS = {0: "SPH_OK", 1: "SPH_ERR_INVALID_ARG", 2: "SPH_ERR_CUDA", 3: "SPH_ERR_NOMEM",
           4: "SPH_ERR_NOT_CONVERGED", 5: "SPH_ERR_TILE_OVERFLOW", 6: "SPH_ERR_NONFINITE",
           7: "SPH_ERR_NEGATIVE_U", 8: "SPH_ERR_TIMEOUT"}
-STAGES = ("tree", "density", "force", "reduce", "leapfrog", "prep", "lists")
+STAGES = ("tree", "density", "force", "reduce", "leapfrog", "prep", "lists", "gravity")
 
 
 class NativeLibraryMissing(RuntimeError):
@@ -36,7 +36,8 @@ class sph_params(ctypes.Structure):
                 ("h_tol", c_float), ("kernel", c_int32), ("n_leaf", c_int32),
                 ("n_group", c_int32), ("tile", c_int32), ("max_h_iter", c_int32),
                 ("density_iters", c_int32), ("pair_targets", c_int32), ("pair_warps", c_int32),
-                ("pair_unroll", c_int32), ("box_lo", c_float * 3), ("box_len", c_float * 3)]
+                ("pair_unroll", c_int32), ("box_lo", c_float * 3), ("box_len", c_float * 3),
+                ("grav_G", c_float), ("grav_eps", c_float), ("grav_theta", c_float)]
 
 
 class sph_state(ctypes.Structure):
@@ -49,7 +50,7 @@ class sph_stats(ctypes.Structure):
     _fields_ = [(k, c_uint64) for k in (
         "density_pairs", "density_candidates", "force_pairs", "force_candidates",
         "newton_iters", "density_rewalks", "streamed_groups", "n_nodes", "n_groups",
-        "list_entries", "list_overflows", "force_rewalks")]
+        "list_entries", "list_overflows", "force_rewalks", "gravity_cells", "gravity_particles")]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_}
@@ -57,7 +58,7 @@ class sph_stats(ctypes.Structure):
 
 _lib = None
 EXPORTS = ("sph_params_default", "sph_create", "sph_destroy", "sph_build_tree", "sph_density",
-           "sph_force", "sph_timestep", "sph_step", "sph_step_host", "sph_batch_evaluate",
+           "sph_force", "sph_gravity", "sph_timestep", "sph_step", "sph_step_host", "sph_batch_evaluate",
            "sph_batch_step", "sph_force_bwd", "sph_density_bwd", "sph_rollout", "sph_conserved",
            "sph_conserved_noalloc",
            "sph_neighbours", "sph_get_tree", "sph_get_stats", "sph_set_timing", "sph_get_timing", "sph_sync",
@@ -82,6 +83,7 @@ def load():
     for name in ("sph_build_tree", "sph_density", "sph_force"):
         getattr(lib, name).argtypes = [P, POINTER(sph_state), POINTER(sph_params), P]
     lib.sph_timestep.argtypes = [P, POINTER(sph_state), POINTER(sph_params), P, P]
+    lib.sph_gravity.argtypes = [P, POINTER(sph_state), POINTER(sph_params), P, P]
     lib.sph_step.argtypes = [P, POINTER(sph_state), POINTER(sph_params), P, P, P]
     lib.sph_step_host.argtypes = [P, POINTER(sph_state), POINTER(sph_params), c_int,
                                   POINTER(c_float), P]
@@ -175,6 +177,12 @@ def sph_density(ctx, state, params, stream=None):
 def sph_force(ctx, state, params, stream=None):
     return _check(ctx, load().sph_force(ctx, ctypes.byref(state), ctypes.byref(params),
                                         _stream(stream)))
+
+
+def sph_gravity(ctx, state, params, d_out4, stream=None):
+    """Self-gravity alone: d_out4 (n x 4 float32 on the device) = (a, phi), G included."""
+    return _check(ctx, load().sph_gravity(ctx, ctypes.byref(state), ctypes.byref(params),
+                                          _ptr(d_out4), _stream(stream)))
 
 
 def sph_timestep(ctx, state, params, d_dt, stream=None):
