@@ -63,6 +63,12 @@ EXEC_FLOP_FORCE_PAIR = 84.0
 NCU_TRAFFIC = {"nlist_kernel": 132.619e6 + 598.933248e6,
                "density_list_kernel": None,
                "force_list_kernel": 1007.506e6 + 28.696064e6}
+# Self-gravity FP32 operations per interaction (softened pair: separation 3,
+# r^2 + eps^2 6, the inverse powers 3, m/r and m/r^3 2, acceleration 6,
+# potential 1 = 21; quadrupole cell: the same 20 plus Q d 15, d.Q.d 5, the
+# cell terms 20 = 60; the reciprocal square root counted as one operation).
+FLOP_GRAV_PART = 21
+FLOP_GRAV_CELL = 60
 # Algorithmic bytes per particle of the tree build (bbox 20, keys 28, four
 # 12-byte-key passes of the sort read and written 96, run fix-up 8, gather of
 # pos, vel, half-step vel, h and perm read and written 112 plus the 32-byte
@@ -527,6 +533,7 @@ def run_plummer(args, fp32_peak, basis, hbm_peak):
     ms = e0.elapsed_time(e1) / reps
     stage, _ = native.sph_get_timing(ctx)
     stats = native.sph_get_stats(ctx)
+    grav = run_gravity(native, ctx, s, w, fp32_peak)
     native.sph_destroy(ctx)
     hh = s.numpy("h")
     roof = roofline(stage, stats, reps, fp32_peak, basis, hbm_peak, w.n)
@@ -539,7 +546,39 @@ def run_plummer(args, fp32_peak, basis, hbm_peak):
             "h_range": [float(hh.min()), float(hh.max())],
             "streamed_groups": stats["streamed_groups"] / reps,
             "n_nodes": stats["n_nodes"], "n_groups": stats["n_groups"],
-            "n_group": p.n_group, "n_leaf": p.n_leaf, "autotune": tuned}
+            "n_group": p.n_group, "n_leaf": p.n_leaf, "autotune": tuned, "gravity": grav}
+
+
+def run_gravity(native, ctx, s, w, fp32_peak, theta=0.5, eps=0.01):
+    """Self-gravity (Barnes-Hut, quadrupole cells) on the built tree of the
+    Plummer state: moments pass + walk, timed with CUDA events."""
+    import torch
+    p = native.sph_params_default(grav_G=1.0, grav_eps=eps, grav_theta=theta, n_group=16)
+    out = torch.zeros((w.n, 4), dtype=torch.float32, device="cuda")
+    native.sph_build_tree(ctx, s.c, p)
+    native.sph_gravity(ctx, s.c, p, out)          # warm-up
+    native.sph_sync(ctx)
+    native.sph_get_stats(ctx)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record()
+    for _ in range(reps):
+        native.sph_gravity(ctx, s.c, p, out)
+    e1.record()
+    torch.cuda.synchronize()
+    native.sph_sync(ctx)
+    st = native.sph_get_stats(ctx)
+    ms = e0.elapsed_time(e1) / reps
+    cells, parts = st["gravity_cells"] / reps, st["gravity_particles"] / reps
+    flop = cells * FLOP_GRAV_CELL + parts * FLOP_GRAV_PART
+    ach = flop / (ms / 1e3) / 1e12
+    return {"theta": theta, "eps": eps, "n_group": 16, "ms_per_evaluation": ms,
+            "value": w.n / (ms / 1e3), "unit": "particle gravity evaluations/s",
+            "interactions_per_particle": (cells + parts) / w.n,
+            "interactions_per_s": (cells + parts) / (ms / 1e3),
+            "roofline": {"bound": "alu", "achieved": round(ach, 3), "peak": round(fp32_peak, 2),
+                         "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4),
+                         "flop_per_interaction": {"cell": FLOP_GRAV_CELL, "particle": FLOP_GRAV_PART}}}
 
 
 def run_tube(args, fp32_peak, basis, hbm_peak):
