@@ -365,6 +365,62 @@ def wrap_positions(x, p: Params):
     return x
 
 
+def block_step(s: SphState, levels, dt_min: float, max_level: int, p: Params = Params()):
+    """One block step of individual (power-of-two) time steps, the block-time-step
+    form of the leapfrog the paper leaves unused (footnote in Sect. 2.4), in the
+    same kick-drift-kick form as kdk_step.
+
+    Particle i steps with dt_i = dt_min 2^levels[i] (levels fixed for the block);
+    the block lasts dt_min 2^max_level, in substeps of dt_min.  In substep k
+    (k = 0 .. 2^max_level - 1) a particle whose step starts (k mod 2^levels[i]
+    = 0) gets its opening half kick from its last acceleration; every
+    particle drifts with its half-step velocity; every particle's velocity and
+    u are predicted to the substep's end (half-step value plus acceleration
+    times the time past the step's middle); the particles whose step ends
+    there ((k + 1) mod 2^levels[i] = 0) get their density solved (from their
+    last h) and their force computed, against all particles at their
+    predicted velocities and last h, rho, Omega, then the closing half kick.
+    The state must hold the accelerations of its positions (an evaluate)."""
+    lv = np.asarray(levels, np.int64)
+    x, v, u = s.x.copy(), s.v.copy(), s.u.copy()
+    h, rho, om, drho = s.h.copy(), s.rho.copy(), s.omega.copy(), s.drhodt.copy()
+    acc, dudt, vs = s.acc.copy(), s.dudt.copy(), s.vsigmax.copy()
+    dti = dt_min * 2.0 ** lv
+    vh, uh = v.copy(), u.copy()
+    for k in range(2 ** max_level):
+        period = 2 ** lv
+        start = (k % period) == 0
+        vh[start] = v[start] + 0.5 * dti[start, None] * acc[start]
+        uh[start] = u[start] + 0.5 * dti[start] * dudt[start]
+        x = wrap_positions(x + dt_min * vh, p)
+        into = ((k % period) + 1) * dt_min - 0.5 * dti
+        v = vh + into[:, None] * acc
+        u = uh + into * dudt
+        end = np.where(((k + 1) % period) == 0)[0]
+        d = density(x, v, s.m, h, targets=end, hfact=p.hfact, tol=p.tol, max_iter=p.max_iter,
+                    kernel=p.kernel, box=p.box)
+        if d.failures:
+            raise RuntimeError(f"oracle density: {d.failures} targets did not converge")
+        h[end], rho[end], om[end], drho[end] = d.h, d.rho, d.omega, d.drhodt
+        f = force(x, v, s.m, u, h, rho, om, targets=end, gamma=p.gamma, alpha=p.alpha,
+                  beta=p.beta, alpha_u=p.alpha_u, kernel=p.kernel, box=p.box)
+        acc[end], dudt[end], vs[end] = f.acc, f.dudt, f.vsigmax
+        v[end] = vh[end] + 0.5 * dti[end, None] * acc[end]
+        u[end] = uh[end] + 0.5 * dti[end] * dudt[end]
+    return SphState(x=x, v=v, u=u, m=s.m, h=h, rho=rho, omega=om, drhodt=drho, acc=acc,
+                    dudt=dudt, vsigmax=vs)
+
+
+def block_levels(s: SphState, dt_min: float, max_level: int, p: Params = Params()):
+    """Level of each particle for a block step: the largest k <= max_level with
+    dt_min 2^k <= C_cour h_i / vsigmax_i (Eq. 8 per particle)."""
+    dtc = p.c_cour * s.h / s.vsigmax
+    k = np.zeros(len(dtc), np.int64)
+    for j in range(1, max_level + 1):
+        k = np.where(dt_min * 2.0 ** j <= dtc, j, k)
+    return k
+
+
 def total_energy(s: SphState):
     c = conserved(s.x, s.v, s.m, s.u)
     return c[0] + c[1]
