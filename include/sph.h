@@ -270,6 +270,38 @@ sph_status sph_conserved(sph_ctx *ctx, const sph_state *s, double *d_out8, void 
 sph_status sph_conserved_noalloc(int64_t n, const float *d_pos, const float *d_vel,
                                  double *d_out8, void *stream);
 
+/* Block (individual) time steps: the kick-drift-kick leapfrog of sph_step
+ * with a step of its own per particle, dt_i = dt_min 2^L_i (the paper's code
+ * has such steps and leaves them unused, Sect. 2.4).
+ *
+ * sph_block_levels: *d_dt_min = c_cour min_i h_i / vsigmax_i (Eq. 8, as
+ * sph_timestep) and d_level[i] (caller order, int32, device) = the largest
+ * L <= max_level with dt_min 2^L <= c_cour min(h_i / vsigmax_i, u_i / |du_i/dt|)
+ * (FP32; the second term keeps a long step from driving u negative).  Needs
+ * h, vsigmax, u and du/dt of the current state.
+ *
+ * sph_step_block: one block of 2^max_level substeps of *d_dt_min (device
+ * float) with the levels d_level (caller order, each in [0, max_level],
+ * fixed for the block).  It first sorts the state into curve order (as
+ * sph_build_tree: acc, h, rho, omega, drhodt, vsigmax move along), then per
+ * substep j: particles whose step starts (j mod 2^L = 0) get their opening
+ * half kick from their last acceleration; all drift with their half-step
+ * velocity (wrapped into a periodic box) and have velocity and u predicted
+ * to the substep's end; the tree's boxes are refitted to the new positions
+ * (no re-sort); the particles whose step ends ((j + 1) mod 2^L = 0) get the
+ * density pass (Newton from their last h) and the force pass against all
+ * particles at their predicted velocities and last h, rho, Omega, then
+ * their closing half kick.  After the block every particle is synchronised
+ * with fresh forces.  *d_time (device double, may be NULL) advances by
+ * dt_min per substep.  Needs acc, vsigmax, h, rho, omega of the current
+ * state (after sph_force, sph_step or sph_step_block).  0 <= max_level <= 16;
+ * not with gravity (SPH_ERR_INVALID_ARG).  Asynchronous. */
+sph_status sph_block_levels(sph_ctx *ctx, const sph_state *s, const sph_params *p, int max_level,
+                            float *d_dt_min, int32_t *d_level, void *stream);
+sph_status sph_step_block(sph_ctx *ctx, sph_state *s, const sph_params *p, int max_level,
+                          const int32_t *d_level, const float *d_dt_min, double *d_time,
+                          void *stream);
+
 /* Self-gravity alone (the a_grav term of Eq. 9, see sph_params.grav_G):
  * d_out4[4 k .. 4 k + 3] = (a_x, a_y, a_z, phi) of slot k, G included, by
  * the Barnes-Hut walk of the tree built by the last sph_build_tree on this

@@ -413,8 +413,12 @@ def block_step(s: SphState, levels, dt_min: float, max_level: int, p: Params = P
 
 def block_levels(s: SphState, dt_min: float, max_level: int, p: Params = Params()):
     """Level of each particle for a block step: the largest k <= max_level with
-    dt_min 2^k <= C_cour h_i / vsigmax_i (Eq. 8 per particle)."""
-    dtc = p.c_cour * s.h / s.vsigmax
+    dt_min 2^k <= C_cour min(h_i / vsigmax_i, u_i / |du_i/dt|) (Eq. 8 per
+    particle, and the same fraction of the time in which u changes by
+    itself, which keeps a long step from driving u negative)."""
+    with np.errstate(divide="ignore"):
+        tu = np.where(s.dudt != 0.0, s.u / np.abs(s.dudt), np.inf)
+    dtc = p.c_cour * np.minimum(s.h / s.vsigmax, tu)
     k = np.zeros(len(dtc), np.int64)
     for j in range(1, max_level + 1):
         k = np.where(dt_min * 2.0 ** j <= dtc, j, k)

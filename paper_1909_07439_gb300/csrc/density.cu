@@ -58,6 +58,7 @@ struct DensArgs {
     const int *inst;  // instance of each slot (batches), or nullptr
     const int *nl_idx, *nl_len;
     int nl_stride;
+    const uint8_t *active;  // only these targets are solved and written (nullptr: all)
     int2 *fallback;   // batches handed to the walking kernel
     int *n_fallback;
     int *rec_bad;     // per instance: an h outgrew the pad of the lists
@@ -180,6 +181,8 @@ __global__ void __launch_bounds__(256, 4) density_list_kernel(DensArgs a)
                 const int t = lane / L, sub = lane % L;
                 const bool act = t < nt;
                 const int i = gr.x + b0 + (act ? t : 0);
+                const bool on = act && (!a.active || a.active[i]);
+                if (!__any_sync(0xffffffffu, on)) continue;  // no target of the batch is due
                 const int len = act ? a.nl_len[i] : 0;
                 if (__any_sync(0xffffffffu, len < 0)) {  // no list (overflow, or too many leaves)
                     push_fallback(a, g, b0, nt);
@@ -191,7 +194,7 @@ __global__ void __launch_bounds__(256, 4) density_list_kernel(DensArgs a)
                 const float hw = h * a.h_in_scale;  // the lists hold every pair with r < R hw
                 const float M = xi.w * hf3;
                 float hlo = 0.f, hhi = INFINITY;
-                bool conv = !act, outside = false, final_pass = false;
+                bool conv = !on, outside = false, final_pass = false;
                 int it = 0;
                 float s0, s1, s2;
                 while (true) {
@@ -233,12 +236,12 @@ __global__ void __launch_bounds__(256, 4) density_list_kernel(DensArgs a)
                     s1 = seg_sum(s1, L);
                     s2 = seg_sum(s2, L);
                     const float cf = seg_sum((float)cnt, L);
-                    if (sub == 0 && act) {
+                    if (sub == 0 && on) {
                         n_pairs += (unsigned long long)cf;
                         ++n_newton;
                     }
                     if (final_pass) break;
-                    if (act && !conv) {
+                    if (on && !conv) {
                         newton_update(h, hlo, hhi, conv, s0, s1, M, fixed, a.tol, SphKernel<K>::C);
                         outside = h > hw;
                     }
@@ -257,7 +260,7 @@ __global__ void __launch_bounds__(256, 4) density_list_kernel(DensArgs a)
                     push_fallback(a, g, b0, nt);
                     continue;
                 }
-                if (act && sub == 0) density_outputs(a, i, h, M, s1, s2, vi.w, SphKernel<K>::C);
+                if (on && sub == 0) density_outputs(a, i, h, M, s1, s2, vi.w, SphKernel<K>::C);
             }
         }
     }
@@ -304,6 +307,7 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_walk_kernel(DensArgs 
             const int t = lane / L, sub = lane % L;
             const bool act = t < nt;
             const int i = gr.x + b0 + (act ? t : 0);
+            const bool on = act && (!a.active || a.active[i]);
             if (lane < kTB) {
                 const float4 p = lane < nt ? a.pos[gr.x + b0 + lane] : make_float4(1e30f, 1e30f, 1e30f, 0.f);
                 sm.tp[lane] = p;
@@ -318,7 +322,7 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_walk_kernel(DensArgs 
             float hw = h * (1.f + kPad);  // list radius is R hw
             bool valid = false;           // lists cover the current h
             bool streamed = false;        // batch overflowed the tile
-            bool conv = !act;
+            bool conv = !on;
             bool final_pass = false;
             int it = 0;
             float s0, s1, s2;
@@ -421,12 +425,12 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_walk_kernel(DensArgs 
                 s1 = seg_sum(s1, L);
                 s2 = seg_sum(s2, L);
                 const float cf = seg_sum((float)cnt, L);
-                if (sub == 0 && act) {
+                if (sub == 0 && on) {
                     n_pairs += (unsigned long long)cf;
                     ++n_newton;
                 }
                 if (final_pass) break;
-                if (act && !conv) {
+                if (on && !conv) {
                     newton_update(h, hlo, hhi, conv, s0, s1, M, fixed, a.tol, SphKernel<K>::C);
                     if (h > hw) {  // outgrew the padded list
                         hw = h * (1.f + kPad);
@@ -445,9 +449,9 @@ __global__ void __launch_bounds__(kDensWarps * 32) density_walk_kernel(DensArgs 
                 }
                 __syncwarp();
             }
-            if (act && sub == 0) density_outputs(a, i, h, M, s1, s2, sm.tv[t].w, SphKernel<K>::C);
+            if (on && sub == 0) density_outputs(a, i, h, M, s1, s2, sm.tv[t].w, SphKernel<K>::C);
             // the neighbour lists hold while no h grew beyond their pad
-            if (__any_sync(0xffffffffu, act && h > a.h_in_scale * h_in) && lane == 0) {
+            if (__any_sync(0xffffffffu, on && h > a.h_in_scale * h_in) && lane == 0) {
                 atomicOr(a.rec_bad + root, 1);  // root = this group's instance
                 atomicOr(a.rec_any, 1);
             }
@@ -731,6 +735,7 @@ cudaError_t density_solve(Ctx &c, const sph_state &s, const sph_params &p, cudaS
     a.nl_idx = c.nl_idx;
     a.nl_len = c.nl_len;
     a.nl_stride = c.nl_stride;
+    a.active = c.mask;
     a.fallback = c.fallback;
     a.n_fallback = c.d_sizes + SZ_FALLBACK;
     a.rec_bad = c.tree.rec_bad;

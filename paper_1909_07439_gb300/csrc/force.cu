@@ -51,6 +51,7 @@ struct ForceArgs {
     const int *inst;  // instance of each slot (batches), or nullptr
     const int *nl_idx, *nl_len;
     int nl_stride;
+    const uint8_t *active;  // only these targets are computed and written (nullptr: all)
     const int *rec_ctl, *rec_bad;
     int2 *fallback;
     int *n_fallback;
@@ -285,6 +286,8 @@ __global__ void __launch_bounds__(256, 3) force_list_kernel(ForceArgs a)
                 const int t = lane / L, sub = lane % L;
                 const bool act = t < nt;
                 const int i = gr.x + b0 + (act ? t : 0);
+                const bool on = act && (!a.active || a.active[i]);
+                if (!__any_sync(0xffffffffu, on)) continue;  // no target of the batch is due
                 const int len = usable && act ? a.nl_len[i] : 0;
                 if (!usable || __any_sync(0xffffffffu, len < 0)) {
                     if (lane == 0) push_fallback_batch(a.fallback, a.n_fallback, g, b0, nt);
@@ -328,9 +331,9 @@ __global__ void __launch_bounds__(256, 3) force_list_kernel(ForceArgs a)
                         entry(b1 ? jj.y : jj.x, b1);
                     }
                 }
-                T.finish(L, act && sub == 0, i, a.gm1, a.alpha_u, a.acc, a.vsigmax);
-                n_pairs += T.cnt;
-                n_cand += act && sub == 0 ? (unsigned long long)len : 0ull;
+                T.finish(L, on && sub == 0, i, a.gm1, a.alpha_u, a.acc, a.vsigmax);
+                n_pairs += on ? T.cnt : 0;
+                n_cand += on && sub == 0 ? (unsigned long long)len : 0ull;
             }
         }
     }
@@ -445,8 +448,9 @@ __global__ void __launch_bounds__(kForceWarps * 32) force_walk_kernel(ForceArgs 
             bool ok = walk_group(a.tree, root, glo, ghi, 0.f, true, hr * glo.w, sm.w, chunk, hr);
             if (!ok && lane == 0) raise_error(a.err, SPH_ERR_TILE_OVERFLOW);
             flush();
-            T.finish(L, act && sub == 0, i0 + t, a);
-            n_pairs += T.cnt;
+            const bool on = act && (!a.active || a.active[i0 + t]);
+            T.finish(L, on && sub == 0, i0 + t, a);
+            n_pairs += on ? T.cnt : 0;
             __syncwarp();
         }
     }
@@ -619,6 +623,7 @@ cudaError_t force_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStre
     a.nl_idx = c.nl_idx;
     a.nl_len = c.nl_len;
     a.nl_stride = c.nl_stride;
+    a.active = c.mask;
     a.rec_ctl = c.tree.rec_ctl;
     a.rec_bad = c.tree.rec_bad;
     a.fallback = c.fallback;

@@ -180,6 +180,129 @@ __global__ void conserved_final_kernel(const double *part, int nb, double *out8)
     }
 }
 
+// ------------------------------------------------------------ block steps
+// Individual power-of-two time steps: particle i (slot k, caller index
+// perm[k]) steps with dt_i = dt_min 2^L_i, L_i = level[perm[k]]; substep j of
+// the block spans [j, j + 1) dt_min.
+//
+// Substep j, before the passes: a particle whose step starts (j mod 2^L = 0)
+// gets its opening half kick from its last acceleration (v_half = v + a dt/2,
+// also u); every particle drifts with its half-step velocity (wrapped into a
+// periodic box) and its velocity and u are predicted to the substep's end,
+// v = v_half + a ((j mod 2^L + 1) dt_min - dt/2); the particles whose step ends
+// there ((j + 1) mod 2^L = 0) are flagged for the density and force passes;
+// the packed records take the new position and velocity.
+__global__ void block_substep_kernel(float4 *__restrict__ pos, float4 *__restrict__ vel,
+                                     const float4 *__restrict__ acc, float4 *__restrict__ vhalf,
+                                     float4 *__restrict__ rec, uint8_t *__restrict__ due,
+                                     const uint32_t *__restrict__ perm, const int *__restrict__ level,
+                                     int n, int j, const float *d_dt_min, Period per, float3 plo)
+{
+    const float dtm = *d_dt_min;
+    auto wrap = [](float x, float L, float lo) {
+        if (L > 0.f) {
+            const float hi = lo + L;
+            x = x >= hi ? x - L : x < lo ? x + L : x;
+            x = (x >= lo && x < hi) ? x : lo;
+        }
+        return x;
+    };
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int L = level[perm[i]];
+        const int mask = (1 << L) - 1;
+        const float dt = dtm * (float)(1 << L);
+        const float4 a = acc[i];
+        float4 vh;
+        if ((j & mask) == 0) {
+            const float4 v = vel[i];
+            const float hdt = 0.5f * dt;
+            vh = make_float4(v.x + hdt * a.x, v.y + hdt * a.y, v.z + hdt * a.z, v.w + hdt * a.w);
+            vhalf[i] = vh;
+        } else {
+            vh = vhalf[i];
+        }
+        const float4 p = pos[i];
+        const float4 q = make_float4(wrap(p.x + dtm * vh.x, per.x, plo.x), wrap(p.y + dtm * vh.y, per.y, plo.y),
+                                     wrap(p.z + dtm * vh.z, per.z, plo.z), p.w);
+        const float into = (float)((j & mask) + 1) * dtm - 0.5f * dt;
+        const float4 w = make_float4(vh.x + into * a.x, vh.y + into * a.y, vh.z + into * a.z, vh.w + into * a.w);
+        pos[i] = q;
+        vel[i] = w;
+        rec[2 * (size_t)i] = q;
+        rec[2 * (size_t)i + 1] = w;
+        due[i] = ((j + 1) & mask) == 0 ? 1 : 0;
+    }
+}
+
+// the closing half kick of the particles whose step ended: v = v_half + a dt/2
+__global__ void block_close_kernel(float4 *__restrict__ vel, const float4 *__restrict__ acc,
+                                   const float4 *__restrict__ vhalf, const uint8_t *__restrict__ due,
+                                   const uint32_t *__restrict__ perm, const int *__restrict__ level,
+                                   int n, const float *d_dt_min, double *d_time, int *err)
+{
+    const float dtm = *d_dt_min;
+    bool neg = false;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        if (!due[i]) continue;
+        const float hdt = 0.5f * dtm * (float)(1 << level[perm[i]]);
+        const float4 vh = vhalf[i], a = acc[i];
+        const float4 v = make_float4(vh.x + hdt * a.x, vh.y + hdt * a.y, vh.z + hdt * a.z, vh.w + hdt * a.w);
+        neg |= !(v.w >= 0.f);
+        vel[i] = v;
+    }
+    if (__any_sync(0xffffffffu, neg) && (threadIdx.x & 31) == 0) raise_error(err, SPH_ERR_NEGATIVE_U);
+    if (d_time && blockIdx.x == 0 && threadIdx.x == 0) *d_time += (double)dtm;
+}
+
+// level of each particle (caller order): the largest L <= max_level with
+// dt_min 2^L <= c_cour min(h / vsigmax, u / |du/dt|) (Eq. 8 per particle and
+// the same fraction of the time in which u changes by itself; FP32)
+__global__ void block_levels_kernel(const float *__restrict__ h, const float *__restrict__ vs,
+                                    const float4 *__restrict__ vel, const float4 *__restrict__ acc,
+                                    const uint32_t *__restrict__ perm, int n, float c_cour,
+                                    int max_level, const float *d_dt_min, int *level)
+{
+    const float dtm = *d_dt_min;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float du = fabsf(acc[i].w);
+        const float tu = du > 0.f ? vel[i].w / du : INFINITY;
+        const float dtc = c_cour * fminf(h[i] / vs[i], tu);
+        int L = 0;
+        while (L < max_level && dtm * (float)(2 << L) <= dtc) ++L;
+        level[perm[i]] = L;
+    }
+}
+
+cudaError_t block_substep(Ctx &c, const sph_state &s, const sph_params &p, const int *d_level, int j,
+                          const float *d_dt_min, cudaStream_t st)
+{
+    const int n = (int)s.n;
+    block_substep_kernel<<<grid_n(c, n, 256), 256, 0, st>>>(
+        (float4 *)s.pos, (float4 *)s.vel, (const float4 *)s.acc, c.vhalf, c.rec, c.active, s.perm,
+        d_level, n, j, d_dt_min, period_of(p), box_lo_of(p));
+    return cudaGetLastError();
+}
+
+cudaError_t block_close(Ctx &c, const sph_state &s, const int *d_level, const float *d_dt_min,
+                        double *d_time, cudaStream_t st)
+{
+    const int n = (int)s.n;
+    block_close_kernel<<<grid_n(c, n, 256), 256, 0, st>>>((float4 *)s.vel, (const float4 *)s.acc,
+                                                          c.vhalf, c.active, s.perm, d_level, n,
+                                                          d_dt_min, d_time, c.d_err);
+    return cudaGetLastError();
+}
+
+cudaError_t block_levels(Ctx &c, const sph_state &s, const sph_params &p, int max_level,
+                         const float *d_dt_min, int *d_level, cudaStream_t st)
+{
+    const int n = (int)s.n;
+    block_levels_kernel<<<grid_n(c, n, 256), 256, 0, st>>>(s.h, s.vsigmax, (const float4 *)s.vel,
+                                                           (const float4 *)s.acc, s.perm, n, p.c_cour,
+                                                           max_level, d_dt_min, d_level);
+    return cudaGetLastError();
+}
+
 cudaError_t kick_drift(Ctx &c, const sph_state &s, const sph_params &p, const float *d_dt,
                        cudaStream_t st, const Batch *batch)
 {

@@ -61,6 +61,7 @@ struct NlistArgs {
     const int *inst;
     float rscale;  // list radius = rscale * max(h_i, h_j)
     int cap;       // entries per list (and the lists' stride)
+    const uint8_t *active;  // lists only for groups holding one of these targets (nullptr: all)
     int *idx;
     int *len;
     // relist mode: the kernel returns at once unless *gate != 0, and builds the
@@ -272,6 +273,8 @@ __global__ void __launch_bounds__(kNlWarps * 32, 7) nlist_kernel(NlistArgs a)
             for (int gi = s; gi < e; ++gi) {
                 const int g = gf + gi;
                 const int2 gr = a.grp_ref[g];
+                if (a.active && !__any_sync(0xffffffffu, lane < gr.y && a.active[gr.x + lane]))
+                    continue;  // no target of the group is due: its lists are not read
                 const float4 glo = a.grp_lo[g], ghi = a.grp_hi[g];
                 const int nleaf = nshared;
                 const int nrun = nleaf >= 0 ? group_candidates(a, sm, nleaf, glo, ghi, kMaxRuns) : -1;
@@ -360,6 +363,7 @@ static NlistArgs nlist_args(Ctx &c, const sph_state &s, const sph_params &p, flo
     // the radius and capacity of the lists' kernel (a relist keeps them)
     a.rscale = kernel_support(c.nl_kernel >= 0 ? c.nl_kernel : p.kernel) * (1.f + pad) * kListSlack;
     a.cap = c.nl_stride;
+    a.active = c.mask;
     a.idx = c.nl_idx;
     a.len = c.nl_len;
     a.err = c.d_err;

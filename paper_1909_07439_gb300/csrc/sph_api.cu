@@ -429,6 +429,7 @@ sph_status sph_create(sph_ctx **out, int64_t max_n, int device)
     A(dalloc(c.prop, n));
     A(dalloc(c.frec, 3 * n));
     A(dalloc(c.vhalf, n));
+    A(dalloc(c.active, n));
     A(dalloc(c.g_com, t.cap_nodes));
     A(dalloc(c.g_q0, t.cap_nodes));
     A(dalloc(c.g_q1, t.cap_nodes));
@@ -471,7 +472,7 @@ void sph_destroy(sph_ctx *h)
                     c.tree.grp_lo, c.tree.grp_hi, c.tree.lv_tree, c.tree.lv_grp, c.tree.blk_cnt,
                     c.nl_idx, c.nl_len, c.fallback,
                     c.tree.rec_ctl, c.tree.rec_bad,
-                    c.rec, c.prop, c.frec, c.vhalf, c.g_com, c.g_q0, c.g_q1, c.inst, c.bbox_inst,
+                    c.rec, c.prop, c.frec, c.vhalf, c.active, c.g_com, c.g_q0, c.g_q1, c.inst, c.bbox_inst,
                     c.dtmin_inst,
                     c.bbox, c.scan_part, c.red_f, c.red_d, c.d_err, c.d_counters,
                     c.d_sizes, c.mirror.pos, c.mirror.vel, c.mirror.acc, c.mirror.h, c.mirror.rho,
@@ -538,6 +539,61 @@ sph_status sph_gravity(sph_ctx *h, const sph_state *s, const sph_params *p, floa
     cudaStream_t st = (cudaStream_t)stream;
     StageScope sc(c, ST_GRAVITY, st, 2);
     CK(gravity_pass(c, *s, *p, nullptr, (float4 *)d_out4, st), "gravity");
+    return SPH_OK;
+}
+
+sph_status sph_block_levels(sph_ctx *h, const sph_state *s, const sph_params *p, int max_level,
+                            float *d_dt_min, int32_t *d_level, void *stream)
+{
+    if (!h) return SPH_ERR_INVALID_ARG;
+    Ctx &c = h->impl;
+    sph_status r = check_state(c, s, true);
+    if (r != SPH_OK) return r;
+    if ((r = check_params(c, p)) != SPH_OK) return r;
+    if (max_level < 0 || max_level > kMaxBlockLevel)
+        return fail(c, SPH_ERR_INVALID_ARG, "max_level out of range [0, 16]");
+    if (!d_dt_min || !d_level) return fail(c, SPH_ERR_INVALID_ARG, "d_dt_min or d_level is NULL");
+    if (s->n == 0) return SPH_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    StageScope sc(c, ST_REDUCE, st, 3);
+    CK(courant_dt(c, *s, *p, d_dt_min, st), "block levels: dt");
+    CK(block_levels(c, *s, *p, max_level, d_dt_min, d_level, st), "block levels");
+    return SPH_OK;
+}
+
+sph_status sph_step_block(sph_ctx *h, sph_state *s, const sph_params *p, int max_level,
+                          const int32_t *d_level, const float *d_dt_min, double *d_time, void *stream)
+{
+    if (!h) return SPH_ERR_INVALID_ARG;
+    Ctx &c = h->impl;
+    sph_status r = check_state(c, s, true);
+    if (r != SPH_OK) return r;
+    if ((r = check_params(c, p)) != SPH_OK) return r;
+    if (max_level < 0 || max_level > kMaxBlockLevel)
+        return fail(c, SPH_ERR_INVALID_ARG, "max_level out of range [0, 16]");
+    if (!d_level || !d_dt_min) return fail(c, SPH_ERR_INVALID_ARG, "d_level or d_dt_min is NULL");
+    if (p->grav_G > 0.f) return fail(c, SPH_ERR_INVALID_ARG, "block time steps with gravity are not built");
+    if (s->n == 0) return SPH_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the block starts from a sorted tree: every per-particle array in curve order
+    if ((r = do_tree(c, *s, *p, true, st)) != SPH_OK) return r;
+    for (int j = 0; j < (1 << max_level); ++j) {
+        {
+            StageScope sc(c, ST_LEAPFROG, st, 1);
+            CK(block_substep(c, *s, *p, d_level, j, d_dt_min, st), "block substep");
+        }
+        {
+            StageScope sc(c, ST_TREE, st, 2);
+            CK(refit_tree(c, *s, st), "refit");
+        }
+        c.mask = c.active;
+        r = do_density(c, *s, *p, st, true);
+        if (r == SPH_OK) r = do_force(c, *s, *p, st, true);
+        c.mask = nullptr;
+        if (r != SPH_OK) return r;
+        StageScope sc(c, ST_LEAPFROG, st, 1);
+        CK(block_close(c, *s, d_level, d_dt_min, d_time, st), "block close");
+    }
     return SPH_OK;
 }
 

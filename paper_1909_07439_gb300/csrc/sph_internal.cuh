@@ -23,6 +23,7 @@ constexpr int kRsSlots = 14;         // radix passes of one sort at most (4 + 8 
 // Wendland C6 at 1.3, 90 for M6 at 0.9); multiples of 4 for the 16-byte list
 // loads.  The list array is allocated for the largest.
 constexpr int kNbrCapMax = 192;
+constexpr int kMaxBlockLevel = 16;  // deepest level of the block time steps
 inline int list_cap(int kernel) { return kernel == 0 ? 128 : 192; }
 constexpr float kListPad = 0.03f;    // neighbour-list radius margin, relative to h
 
@@ -133,6 +134,11 @@ struct Ctx {
     // ((R h)^2, G C / (h^4 rho Omega), alpha_AV c_s, rho)
     float4 *frec = nullptr;
     float4 *vhalf = nullptr;  // half-step v, u of the leapfrog
+    // [n] block time steps: per-slot flag of the particles whose step ends in
+    // the current substep; mask points at it while the passes run for those
+    // particles only (nullptr otherwise)
+    uint8_t *active = nullptr;
+    const uint8_t *mask = nullptr;
     // [cap_nodes] gravity moments: (centre of mass, M), (Qxx, Qyy, Qzz, r_open^2),
     // (Qxy, Qxz, Qyz, -)
     float4 *g_com = nullptr, *g_q0 = nullptr, *g_q1 = nullptr;
@@ -274,6 +280,17 @@ cudaError_t configure_gravity_kernels();
 // (drifted positions wrap into the periodic box of p)
 cudaError_t kick_drift(Ctx &c, const sph_state &s, const sph_params &p, const float *d_dt,
                        cudaStream_t st, const Batch *batch = nullptr);
+// block time steps (integrate.cu): substep j's kicks, drift, prediction and
+// due flags; the closing kicks of the due particles; the levels from Eq. 8
+cudaError_t block_substep(Ctx &c, const sph_state &s, const sph_params &p, const int *d_level, int j,
+                          const float *d_dt_min, cudaStream_t st);
+cudaError_t block_close(Ctx &c, const sph_state &s, const int *d_level, const float *d_dt_min,
+                        double *d_time, cudaStream_t st);
+cudaError_t block_levels(Ctx &c, const sph_state &s, const sph_params &p, int max_level,
+                         const float *d_dt_min, int *d_level, cudaStream_t st);
+// node and group boxes and h_max from the current positions and h, without
+// re-sorting (tree.cu)
+cudaError_t refit_tree(Ctx &c, const sph_state &s, cudaStream_t st);
 cudaError_t kick_close(Ctx &c, const sph_state &s, const float *d_dt, double *d_time,
                        cudaStream_t st, const Batch *batch = nullptr);
 cudaError_t courant_dt(Ctx &c, const sph_state &s, const sph_params &p, float *d_dt,

@@ -832,6 +832,16 @@ cudaError_t instance_map(Ctx &c, const int64_t *d_offsets, int n_inst, int n, cu
     return cudaGetLastError();
 }
 
+cudaError_t refit_tree(Ctx &c, const sph_state &s, cudaStream_t st)
+{
+    const int n = (int)s.n;
+    Tree &t = c.tree;
+    const float4 *pos = (const float4 *)s.pos;
+    group_bounds_kernel<<<grid_for(c, n, 128), 128, 0, st>>>(pos, s.h, n, t, c.d_sizes, 0, nullptr);
+    node_bounds_kernel<<<grid_for(c, t.cap_nodes, 128), 128, 0, st>>>(pos, s.h, t, c.d_sizes, 0, nullptr);
+    return cudaGetLastError();
+}
+
 cudaError_t build_tree(Ctx &c, const sph_state &s, const sph_params &p, bool full_permute,
                        cudaStream_t st, const Batch *batch)
 {

@@ -58,7 +58,7 @@ class sph_stats(ctypes.Structure):
 
 _lib = None
 EXPORTS = ("sph_params_default", "sph_create", "sph_destroy", "sph_build_tree", "sph_density",
-           "sph_force", "sph_gravity", "sph_timestep", "sph_step", "sph_step_host", "sph_batch_evaluate",
+           "sph_force", "sph_gravity", "sph_timestep", "sph_step", "sph_block_levels", "sph_step_block", "sph_step_host", "sph_batch_evaluate",
            "sph_batch_step", "sph_force_bwd", "sph_density_bwd", "sph_rollout", "sph_conserved",
            "sph_conserved_noalloc",
            "sph_neighbours", "sph_get_tree", "sph_get_stats", "sph_set_timing", "sph_get_timing", "sph_sync",
@@ -84,6 +84,8 @@ def load():
         getattr(lib, name).argtypes = [P, POINTER(sph_state), POINTER(sph_params), P]
     lib.sph_timestep.argtypes = [P, POINTER(sph_state), POINTER(sph_params), P, P]
     lib.sph_gravity.argtypes = [P, POINTER(sph_state), POINTER(sph_params), P, P]
+    lib.sph_block_levels.argtypes = [P, POINTER(sph_state), POINTER(sph_params), c_int, P, P, P]
+    lib.sph_step_block.argtypes = [P, POINTER(sph_state), POINTER(sph_params), c_int, P, P, P, P]
     lib.sph_step.argtypes = [P, POINTER(sph_state), POINTER(sph_params), P, P, P]
     lib.sph_step_host.argtypes = [P, POINTER(sph_state), POINTER(sph_params), c_int,
                                   POINTER(c_float), P]
@@ -177,6 +179,20 @@ def sph_density(ctx, state, params, stream=None):
 def sph_force(ctx, state, params, stream=None):
     return _check(ctx, load().sph_force(ctx, ctypes.byref(state), ctypes.byref(params),
                                         _stream(stream)))
+
+
+def sph_block_levels(ctx, state, params, max_level, d_dt_min, d_level, stream=None):
+    """Courant dt_min (device float[1]) and per-particle levels (device int32[n], caller order)."""
+    return _check(ctx, load().sph_block_levels(ctx, ctypes.byref(state), ctypes.byref(params),
+                                               int(max_level), _ptr(d_dt_min), _ptr(d_level),
+                                               _stream(stream)))
+
+
+def sph_step_block(ctx, state, params, max_level, d_level, d_dt_min, d_time=None, stream=None):
+    """One block of 2^max_level substeps of dt_min with individual levels."""
+    return _check(ctx, load().sph_step_block(ctx, ctypes.byref(state), ctypes.byref(params),
+                                             int(max_level), _ptr(d_level), _ptr(d_dt_min),
+                                             _ptr(d_time), _stream(stream)))
 
 
 def sph_gravity(ctx, state, params, d_out4, stream=None):

@@ -68,11 +68,13 @@ def test_separated_clouds_on_two_levels():
     _close(part(r, slice(500, 900)), rb, 1e-10)
 
 
-def test_levels_follow_the_courant_rule():
+def test_levels_follow_the_courant_and_energy_rule():
     s = _state(inputs.sedov_lattice(10, seed=2))
     dt_min = oracle.courant_dt(s)
     lv = oracle.block_levels(s, dt_min, 3)
-    dtc = 0.3 * s.h / s.vsigmax
-    assert np.all(dt_min * 2.0 ** lv <= dtc * (1 + 1e-12))
+    dtc = 0.3 * np.minimum(s.h / s.vsigmax, s.u / np.abs(s.dudt))
+    # level 0 also takes the particles whose energy time is below dt_min
+    assert np.all((lv == 0) | (dt_min * 2.0 ** lv <= dtc * (1 + 1e-12)))
+    assert np.any(dtc < dt_min)
     assert np.all((lv == 3) | (dt_min * 2.0 ** (lv + 1) > dtc))
     assert lv.min() == 0 and lv.max() > 0
