@@ -339,6 +339,7 @@ def run_ours(args):
                if rank == 0 and args.plummer_log2 > 0 else None)
     tube = (run_tube(args, fp32_peak, basis, pk.get("hbm_gbs", 6800.0))
             if rank == 0 and args.tube_scale > 0 else None)
+    block = run_block(args) if rank == 0 and args.block_levels > 0 else None
     out = None
     if rank == 0:
         cpu = run_cpu_baseline(w, args.cpu_seconds) if args.cpu_seconds > 0 else None
@@ -369,6 +370,7 @@ def run_ours(args):
             "adjoint": adjoint,
             "plummer": plummer,
             "tube": tube,
+            "block": block,
         }
     if ws > 1:
         torch.distributed.destroy_process_group()
@@ -634,6 +636,73 @@ def run_tube(args, fp32_peak, basis, hbm_peak):
             "roofline": roof}
 
 
+def run_block(args):
+    """Block (individual) time steps on the Sedov blast: from the state after
+    20 global steps, the same span of time as one block of 2^L substeps of
+    the Courant dt_min, taken (a) as 2^L global steps of dt_min and (b) as one
+    block step with each particle on its own level; both timed with CUDA
+    events from the same saved state."""
+    import torch
+    from paper_1909_07439_gb300 import DeviceState, inputs, native
+    L = args.block_levels
+    w = inputs.sedov_lattice(args.side)
+    ctx = native.sph_create(w.n, 0)
+    s = DeviceState.from_arrays(w.pos, w.vel, w.h)
+    p = native.sph_params_default(n_group=16)
+    d_dt = torch.zeros(1, dtype=torch.float32, device="cuda")
+    native.sph_build_tree(ctx, s.c, p)
+    native.sph_density(ctx, s.c, p)
+    native.sph_force(ctx, s.c, p)
+    native.sph_timestep(ctx, s.c, p, d_dt)
+    for _ in range(20):
+        native.sph_step(ctx, s.c, p, d_dt)
+    native.sph_sync(ctx)
+    saved = {f: getattr(s, f).clone() for f in s.FIELDS4 + s.FIELDS1 + ("perm", "keys")}
+    d_level = torch.zeros(w.n, dtype=torch.int32, device="cuda")
+    native.sph_block_levels(ctx, s.c, p, L, d_dt, d_level)
+    native.sph_sync(ctx)
+    dt0 = d_dt.item()
+    levels = np.bincount(d_level.cpu().numpy(), minlength=L + 1).tolist()
+
+    def restore():
+        for f, t in saved.items():
+            getattr(s, f).copy_(t)
+        torch.cuda.synchronize()
+
+    out = {}
+    for mode in ("global", "block"):
+        best = None
+        for rep in range(3):
+            restore()
+            native.sph_get_stats(ctx)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            if mode == "global":
+                for _ in range(1 << L):
+                    d_dt.fill_(dt0)
+                    native.sph_step(ctx, s.c, p, d_dt)
+            else:
+                d_dt.fill_(dt0)
+                native.sph_step_block(ctx, s.c, p, L, d_level, d_dt)
+            e1.record()
+            torch.cuda.synchronize()
+            native.sph_sync(ctx)
+            st = native.sph_get_stats(ctx)
+            ms = e0.elapsed_time(e1)
+            if best is None or ms < best[0]:
+                best = (ms, st["force_pairs"], st["density_pairs"])
+        out[mode] = {"ms": best[0], "force_pairs": best[1], "density_pairs": best[2]}
+    native.sph_destroy(ctx)
+    span = (1 << L) * dt0
+    return {"workload": f"Sedov lattice {args.side}^3 after 20 steps, {1 << L} x dt_min "
+                        f"({span:.3e} of simulated time)",
+            "levels": levels, "global_ms": out["global"]["ms"], "block_ms": out["block"]["ms"],
+            "speedup": out["global"]["ms"] / out["block"]["ms"],
+            "force_pairs": {"global": out["global"]["force_pairs"], "block": out["block"]["force_pairs"]},
+            "value": w.n * (1 << L) / (out["block"]["ms"] / 1e3),
+            "unit": "particle-updates/s at dt_min resolution (block steps)"}
+
+
 def run_e2e(native, ctx, s, p, n, args, stream):
     """Same metric through the C ABI with the state in pinned HOST memory:
     every step copies the inputs in and the whole state back."""
@@ -755,6 +824,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--adjoint-side", type=int, default=64)
     ap.add_argument("--plummer-log2", type=int, default=24)
+    ap.add_argument("--block-levels", type=int, default=3,
+                    help="block time step leg: levels below dt_min 2^L (0: skip)")
     ap.add_argument("--tube-scale", type=int, default=2,
                     help="Sod/M6/periodic leg: the paper's tube scaled per axis (0: skip)")
     args = ap.parse_args()
