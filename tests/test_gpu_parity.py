@@ -614,6 +614,24 @@ def test_lookback_wait_times_out(sph):
     assert np.array_equal(s.numpy("perm").astype(np.int64), oracle.sort_order(keys_o))
 
 
+def test_list_overflow_is_reported(sph):
+    # h doubled: about 8x the neighbours, past the 128-entry lists; the list
+    # sets cannot be returned (status 5) and the context stays usable
+    native, ctx, torch = sph
+    w = CASES["c1_8192"]
+    d, _ = oracle_eval("c1_8192", w)
+    h = (2.0 * d.h).astype(np.float32)
+    s = upload(native, inputs.Workload("x", w.pos, w.vel, h))
+    p = native.sph_params_default()
+    native.sph_build_tree(ctx, s.c, p)
+    off = torch.zeros(w.n + 1, dtype=torch.int64, device="cuda")
+    with pytest.raises(native.SphError) as e:
+        native.sph_neighbours(ctx, s.c, p, 2, off)
+    assert e.value.status == 5
+    native.sph_sync(ctx)
+    assert native.sph_get_stats(ctx)["list_overflows"] > 0
+
+
 def test_invalid_arguments(sph):
     native, ctx, torch = sph
     s = upload(native, inputs.unit_sphere(64))
