@@ -157,6 +157,7 @@ __global__ void __launch_bounds__(kGWarps * 32) gravity_kernel(GravArgs a)
 
         auto eval_cells = [&](int nc) {
             __syncwarp();
+#pragma unroll 4
             for (int e = sub; e < nc; e += L) {
                 const float4 c = sm.c_com[e], qa = sm.c_q0[e], qb = sm.c_q1[e];
                 const float dx = xt.x - c.x, dy = xt.y - c.y, dz = xt.z - c.z;
@@ -177,6 +178,7 @@ __global__ void __launch_bounds__(kGWarps * 32) gravity_kernel(GravArgs a)
         };
         auto eval_parts = [&](int np) {
             __syncwarp();
+#pragma unroll 4
             for (int e = sub; e < np; e += L) {
                 const float4 pj = sm.p_pos[e];
                 const bool self = sm.p_idx[e] == i;
