@@ -681,6 +681,8 @@ def run_block(args):
         for rep in range(3):
             restore()
             native.sph_get_stats(ctx)
+            native.sph_get_timing(ctx)
+            native.sph_set_timing(ctx, True)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             if mode == "global":
@@ -694,10 +696,13 @@ def run_block(args):
             torch.cuda.synchronize()
             native.sph_sync(ctx)
             st = native.sph_get_stats(ctx)
+            stage, _ = native.sph_get_timing(ctx)
+            native.sph_set_timing(ctx, False)
             ms = e0.elapsed_time(e1)
             if best is None or ms < best[0]:
-                best = (ms, st["force_pairs"], st["density_pairs"])
-        out[mode] = {"ms": best[0], "force_pairs": best[1], "density_pairs": best[2]}
+                best = (ms, st["force_pairs"], st["density_pairs"], stage)
+        out[mode] = {"ms": best[0], "force_pairs": best[1], "density_pairs": best[2],
+                     "stage_ms": {k: round(v, 4) for k, v in best[3].items()}}
     native.sph_destroy(ctx)
     span = (1 << L) * dt0
     return {"workload": f"Sedov lattice {args.side}^3 after 20 steps, {1 << L} x dt_min "
@@ -705,6 +710,7 @@ def run_block(args):
             "levels": levels, "global_ms": out["global"]["ms"], "block_ms": out["block"]["ms"],
             "speedup": out["global"]["ms"] / out["block"]["ms"],
             "force_pairs": {"global": out["global"]["force_pairs"], "block": out["block"]["force_pairs"]},
+            "stage_ms": {"global": out["global"]["stage_ms"], "block": out["block"]["stage_ms"]},
             "value": w.n * (1 << L) / (out["block"]["ms"] / 1e3),
             "unit": "particle-updates/s at dt_min resolution (block steps)"}
 

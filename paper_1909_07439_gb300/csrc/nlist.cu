@@ -240,11 +240,24 @@ __global__ void __launch_bounds__(kNlWarps * 32, 7) nlist_kernel(NlistArgs a)
         const bool starts = have && (lane == 0 || ins != ins_p || glol.w > kShareH * hm_p ||
                                      hm_p > kShareH * glol.w);
         const unsigned bstart = __ballot_sync(0xffffffffu, starts);
+        // with a due-target mask (block steps): the groups holding a due target
+        unsigned bdue = 0xffffffffu;
+        if (a.active) {
+            bool due = false;
+            if (have)
+                for (int k = 0; k < grl.y && !due; ++k) due = a.active[grl.x + k] != 0;
+            bdue = __ballot_sync(0xffffffffu, due);
+        }
         for (int s = 0; s < sgn;) {
             const unsigned later = bstart & ~((2u << s) - 1u);  // starts after s
             int e = later ? min(__ffs(later) - 1, sgn) : sgn;
             const int root = __shfl_sync(0xffffffffu, ins, s);
             if (a.only_bad && a.only_bad[root] == 0) {  // relist mode: this instance's lists hold
+                s = e;
+                continue;
+            }
+            const unsigned run = (e >= 32 ? 0xffffffffu : ((1u << e) - 1u)) & ~((1u << s) - 1u);
+            if ((bdue & run) == 0) {  // no group of the run is due: no walk
                 s = e;
                 continue;
             }
