@@ -76,7 +76,7 @@ typedef struct {
                               each target gets 32 / pair_targets lanes       */
     int32_t pair_warps;    /* warps per block: 1, 2, 4 (default) or 8       */
     int32_t pair_unroll;   /* list entries per lane and iteration of the
-                              force kernel: 2 (default) or 4               */
+                              density and force kernels: 2 (default) or 4 */
     /* Periodic boundaries (the tube tests of Sect. 4.1-4.2 are periodic in y
      * and z).  box_len[a] > 0 makes axis a periodic with period box_len[a]
      * (0 = open axis, the default): positions must lie in

@@ -146,9 +146,9 @@ __device__ __forceinline__ void push_fallback(const DensArgs &a, int g, int b0, 
 }
 
 // Launch shape (run-time): a.tb targets per batch (32 / a.tb lanes per
-// target), blockDim.x / 32 warps per block; registers capped for 1024
-// resident threads per SM.
-template <int K, bool PER>
+// target), blockDim.x / 32 warps per block; NPER list entries per lane and
+// iteration; registers capped for 1024 resident threads per SM.
+template <int NPER, int K, bool PER>
 __global__ void __launch_bounds__(256, 4) density_list_kernel(DensArgs a)
 {
     const int lane = threadIdx.x & 31;
@@ -203,11 +203,11 @@ __global__ void __launch_bounds__(256, 4) density_list_kernel(DensArgs a)
                     const float hinv = 1.f / h;
                     const float R = SphKernel<K>::R * h;
                     const float R2 = R * R;
-                    // Two consecutive entries per lane and iteration (one 8-byte
-                    // load of the list, fetched an iteration ahead: the lists come
-                    // from DRAM), no branch on the distance: f and f' vanish for
-                    // q >= 2, so entries beyond 2 h add nothing.  A missing second
-                    // entry repeats the first with zero mass.
+                    // NPER consecutive entries per lane and iteration (one 8- or
+                    // 16-byte load of the list, fetched an iteration ahead: the
+                    // lists come from DRAM), no branch on the distance: f and f'
+                    // vanish for q >= R, so entries beyond R h add nothing.  A
+                    // missing entry repeats the first with zero mass.
                     auto entry = [&](float4 pj, float4 vj, float mj) {
                         float dx = xi.x - pj.x, dy = xi.y - pj.y, dz = xi.z - pj.z;
                         if (PER) {  // nearest images on the periodic axes
@@ -220,17 +220,36 @@ __global__ void __launch_bounds__(256, 4) density_list_kernel(DensArgs a)
                         cnt += (mj > 0.f && r2 < R2) ? 1 : 0;
                         pair_sums<K>(r2, mj, vd, hinv, s0, s1, s2);
                     };
-                    int e = 2 * sub;
-                    int2 jn = e < len ? __ldcs(reinterpret_cast<const int2 *>(lst + e)) : make_int2(0, 0);
-                    for (; e < len; e += 2 * L) {
-                        const int2 jj = jn;
-                        if (e + 2 * L < len) jn = __ldcs(reinterpret_cast<const int2 *>(lst + e + 2 * L));
-                        const bool b1 = e + 1 < len;
-                        float4 p0, v0, p1, v1;
-                        ld_rec(a.rec, jj.x, keep, p0, v0);
-                        ld_rec(a.rec, b1 ? jj.y : jj.x, keep, p1, v1);
-                        entry(p0, v0, p0.w);
-                        entry(p1, v1, b1 ? p1.w : 0.f);
+                    if (NPER == 4) {
+                        int e = 4 * sub;
+                        int4 jn = e < len ? __ldcs(reinterpret_cast<const int4 *>(lst + e)) : make_int4(0, 0, 0, 0);
+                        for (; e < len; e += 4 * L) {
+                            const int4 jj = jn;
+                            if (e + 4 * L < len) jn = __ldcs(reinterpret_cast<const int4 *>(lst + e + 4 * L));
+                            const bool b1 = e + 1 < len, b2 = e + 2 < len, b3 = e + 3 < len;
+                            float4 p0, v0, p1, v1, p2, v2, p3, v3;
+                            ld_rec(a.rec, jj.x, keep, p0, v0);
+                            ld_rec(a.rec, b1 ? jj.y : jj.x, keep, p1, v1);
+                            ld_rec(a.rec, b2 ? jj.z : jj.x, keep, p2, v2);
+                            ld_rec(a.rec, b3 ? jj.w : jj.x, keep, p3, v3);
+                            entry(p0, v0, p0.w);
+                            entry(p1, v1, b1 ? p1.w : 0.f);
+                            entry(p2, v2, b2 ? p2.w : 0.f);
+                            entry(p3, v3, b3 ? p3.w : 0.f);
+                        }
+                    } else {
+                        int e = 2 * sub;
+                        int2 jn = e < len ? __ldcs(reinterpret_cast<const int2 *>(lst + e)) : make_int2(0, 0);
+                        for (; e < len; e += 2 * L) {
+                            const int2 jj = jn;
+                            if (e + 2 * L < len) jn = __ldcs(reinterpret_cast<const int2 *>(lst + e + 2 * L));
+                            const bool b1 = e + 1 < len;
+                            float4 p0, v0, p1, v1;
+                            ld_rec(a.rec, jj.x, keep, p0, v0);
+                            ld_rec(a.rec, b1 ? jj.y : jj.x, keep, p1, v1);
+                            entry(p0, v0, p0.w);
+                            entry(p1, v1, b1 ? p1.w : 0.f);
+                        }
                     }
                     s0 = seg_sum(s0, L);
                     s1 = seg_sum(s1, L);
@@ -634,21 +653,25 @@ static cudaError_t configure_density(int &blocks)
 }
 
 // resident blocks per SM of the list kernel for 1, 2, 4 and 8 warps per block
+// (the smallest over its variants)
 template <int K>
 static cudaError_t configure_density_list(int blocks[4])
 {
     static bool configured = false;
     static int nb_cached[4];
     if (!configured) {
+        const void *fns[4] = {(const void *)density_list_kernel<2, K, false>,
+                              (const void *)density_list_kernel<2, K, true>,
+                              (const void *)density_list_kernel<4, K, false>,
+                              (const void *)density_list_kernel<4, K, true>};
         for (int w = 0; w < 4; ++w) {
-            int nb = 0;
-            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, density_list_kernel<K, false>,
-                                                                          32 << w, 0);
-            int nbp = 0;
-            if (e == cudaSuccess)
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nbp, density_list_kernel<K, true>, 32 << w, 0);
-            if (e != cudaSuccess) return e;
-            nb = nbp < nb ? nbp : nb;
+            int nb = 1 << 30;
+            for (const void *f : fns) {
+                int b = 0;
+                cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, 32 << w, 0);
+                if (e != cudaSuccess) return e;
+                nb = b < nb ? b : nb;
+            }
             nb_cached[w] = nb > 0 ? nb : 1;
         }
         configured = true;
@@ -696,8 +719,12 @@ static cudaError_t density_solve_k(Ctx &c, DensArgs &a, const sph_params &p, cud
     const PairShape ps = pair_shape(p);
     a.tb = ps.targets;
     const int wl = ps.warps == 8 ? 3 : ps.warps == 4 ? 2 : ps.warps == 2 ? 1 : 0;
-    if (a.tree.per.any()) density_list_kernel<K, true><<<c.num_sms * bl[wl], 32 * ps.warps, 0, st>>>(a);
-    else density_list_kernel<K, false><<<c.num_sms * bl[wl], 32 * ps.warps, 0, st>>>(a);
+    const dim3 grid(c.num_sms * bl[wl]), block(32 * ps.warps);
+    const bool per = a.tree.per.any();
+    if (ps.unroll == 4 && per) density_list_kernel<4, K, true><<<grid, block, 0, st>>>(a);
+    else if (ps.unroll == 4) density_list_kernel<4, K, false><<<grid, block, 0, st>>>(a);
+    else if (per) density_list_kernel<2, K, true><<<grid, block, 0, st>>>(a);
+    else density_list_kernel<2, K, false><<<grid, block, 0, st>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // default tile: the mean density set (about 58 for M4 at hfact 1.2, 82 for

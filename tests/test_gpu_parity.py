@@ -299,12 +299,20 @@ def test_force_parity(sph, case):
 @pytest.mark.parametrize("shape", [(4, 2, 4), (16, 8, 2), (16, 1, 4), (8, 4, 4)])
 def test_launch_shapes_keep_parity(sph, shape):
     # the autotuner's launch shapes of the list pair kernels (targets per batch,
-    # warps per block, entries per iteration) change only the FP32 summation order
+    # warps per block, entries per iteration) change only the FP32 summation
+    # order, on the walking first evaluation and on the list path after it
     native, ctx, torch = sph
     t, wp, u = shape
     w = CASES["ragged_3001"]
     s, p = evaluate_gpu(native, ctx, w, pair_targets=t, pair_warps=wp, pair_unroll=u, n_group=16)
     d, f = oracle_eval("ragged_3001", w)
+    # then both passes again from the converged h: every batch on the list kernels
+    native.sph_get_stats(ctx)
+    native.sph_density(ctx, s.c, p)
+    native.sph_force(ctx, s.c, p)
+    native.sph_sync(ctx)
+    st = native.sph_get_stats(ctx)
+    assert st["density_rewalks"] == 0 and st["force_rewalks"] == 0 and st["list_overflows"] == 0
     assert np.max(np.abs(s.in_original_order("rho") / d.rho - 1)) <= RHO_TOL
     acc = s.in_original_order("acc")
     assert np.max(np.abs(acc[:, :3] - f.acc)) <= ACC_TOL * np.max(np.abs(f.acc))
