@@ -60,8 +60,8 @@ FLOP_PAIR = {0: (FLOP_FORCE_PAIR, FLOP_DENSITY_PAIR), 1: (106, 75), 2: (104, 66)
 EXEC_FLOP_FORCE_PAIR = 84.0
 # DRAM bytes (read + write) per launch of the pair kernels from one ncu capture
 # of the 128^3 step; None where the kernel changed after the capture.
-NCU_TRAFFIC = {"nlist_kernel": None,
-               "density_list_kernel": None,
+NCU_TRAFFIC = {"nlist_kernel": 132.78464e6 + 587.955712e6,
+               "density_list_kernel": 1.07383e9 + 49.421568e6,
                "force_list_kernel": 967.37024e6 + 28.055296e6}
 # Self-gravity FP32 operations per interaction (softened pair: separation 3,
 # r^2 + eps^2 6, the inverse powers 3, m/r and m/r^3 2, acceleration 6,
