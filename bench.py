@@ -62,7 +62,7 @@ EXEC_FLOP_FORCE_PAIR = 84.0
 # of the 128^3 step; None where the kernel changed after the capture.
 NCU_TRAFFIC = {"nlist_kernel": 132.78464e6 + 587.955712e6,
                "density_list_kernel": 1.07383e9 + 49.421568e6,
-               "force_list_kernel": 967.37024e6 + 28.055296e6}
+               "force_list_kernel": 1.00118e9 + 29.120512e6}
 # Self-gravity FP32 operations per interaction (softened pair: separation 3,
 # r^2 + eps^2 6, the inverse powers 3, m/r and m/r^3 2, acceleration 6,
 # potential 1 = 21; quadrupole cell: the same 20 plus Q d 15, d.Q.d 5, the

@@ -22,16 +22,17 @@
 // for a box passes it for any box containing it, so each group then picks its
 // own leaves from that list with its own test and gets the candidates its own
 // walk would give, in particle order; while a shared walk finds more than
-// kSGLeaves leaves, its range of groups is halved.  Each 32-candidate chunk
-// is tested against up to 16 targets with the canonical FP32 squared
-// distance (two targets per packed instruction); hits go straight to the
-// lists in global memory.
+// kSGLeaves leaves, its range of groups is halved.  A group's targets are
+// taken in batches of up to kNlTB; the candidates within reach of a batch's
+// box are queued, and every 32 queued candidates are tested against the
+// batch's targets with the canonical FP32 squared distance (two targets per
+// packed instruction); hits go straight to the lists in global memory.
 #include "kernels.cuh"
 #include "walk.cuh"
 
 namespace sph {
 
-constexpr int kNlTB = 16;       // targets per candidate test batch
+constexpr int kNlTB = 8;        // targets per candidate test batch
 constexpr int kNlWarps = 4;     // warps per block
 constexpr int kSG = 8;          // consecutive groups that may share one tree walk
 constexpr int kSGLeaves = 320;  // leaves one walk may find
@@ -41,13 +42,29 @@ constexpr int kLWStack = 320;   // stack entries of a wide walk
 constexpr float kShareH = 2.f;  // groups share a walk if their h_max differ by less
 constexpr float kListSlack = 1.0f + 1e-5f;  // list radius margin over the FP32 pad checks
 
-struct NlistSmem {
+struct NlistWalkPart {
     WalkSmemW<kLWWide, kLWStack> w;
     int2 lv[kSGLeaves];        // walk output (node, first); then a group's leaves (first, count)
+};
+
+// A batch's candidates that pass its box test, waiting to be tested against
+// its targets in chunks of 32 (in slot order)
+struct NlistQueue {
+    float4 p[64];              // x, y, z, (list radius factor x h_j)^2
+    int j[64];
+};
+
+struct NlistSmem {
+    // the walk's scratch is free while a group's batches are tested
+    union {
+        NlistWalkPart wp;
+        NlistQueue q;
+    } u;
     int leaves[kSGLeaves];     // the walk's leaves (nodes) in particle order
     int2 runs[kMaxRuns + 1];   // a group's candidate runs: (first particle, first slot), sentinel
     TargetPairs<kNlTB> tc;
     float tr2[kNlTB];          // (list radius factor x h_i)^2 (0 for unused slots)
+    float4 blo, bhi;           // the batch's box; bhi.w: its largest tr2
 };
 
 struct NlistArgs {
@@ -78,14 +95,14 @@ __device__ __forceinline__ int walk_sorted(const NlistArgs &a, NlistSmem &sm, in
 {
     const int lane = threadIdx.x & 31;
     const int n = walk_leaves_wide(a.tree, root, blo, bhi, 0.5f * (a.rscale * blo.w), 0.5f * a.rscale,
-                                   sm.w, sm.lv, kSGLeaves);
+                                   sm.u.wp.w, sm.u.wp.lv, kSGLeaves);
     __syncwarp();
     // rank sort by first particle (leaves hold disjoint particle ranges)
     for (int k0 = 0; k0 < n; k0 += 32) {
         const int k = k0 + lane;
-        const int2 me = k < n ? sm.lv[k] : make_int2(-1, 0x7fffffff);
+        const int2 me = k < n ? sm.u.wp.lv[k] : make_int2(-1, 0x7fffffff);
         int rank = 0;
-        for (int m = 0; m < n; ++m) rank += sm.lv[m].y < me.y ? 1 : 0;
+        for (int m = 0; m < n; ++m) rank += sm.u.wp.lv[m].y < me.y ? 1 : 0;
         if (k < n) sm.leaves[rank] = me.x;
     }
     __syncwarp();
@@ -122,7 +139,7 @@ __device__ __forceinline__ int group_candidates(const NlistArgs &a, NlistSmem &s
         }
         const unsigned m = __ballot_sync(0xffffffffu, open);
         __syncwarp();
-        if (open) sm.lv[nsel + __popc(m & lt)] = ref;
+        if (open) sm.u.wp.lv[nsel + __popc(m & lt)] = ref;
         nsel += __popc(m);
     }
     __syncwarp();
@@ -131,8 +148,8 @@ __device__ __forceinline__ int group_candidates(const NlistArgs &a, NlistSmem &s
     for (int k0 = 0; k0 < nsel; k0 += 32) {
         const int k = k0 + lane;
         const bool valid = k < nsel;
-        const int2 cur = valid ? sm.lv[k] : make_int2(0, 0);
-        const bool st = valid && (k == 0 || sm.lv[k - 1].x + sm.lv[k - 1].y != cur.x);
+        const int2 cur = valid ? sm.u.wp.lv[k] : make_int2(0, 0);
+        const bool st = valid && (k == 0 || sm.u.wp.lv[k - 1].x + sm.u.wp.lv[k - 1].y != cur.x);
         const unsigned bst = __ballot_sync(0xffffffffu, st);
         int inc = cur.y;
         for (int o = 1; o < 32; o <<= 1) {
@@ -149,14 +166,54 @@ __device__ __forceinline__ int group_candidates(const NlistArgs &a, NlistSmem &s
     return nrun <= max_runs ? nrun : -1;
 }
 
-// Test the group's candidate slots, 32 per chunk (one per lane), against the
-// batch's targets (TB slots, the unused ones far away: no candidate hits
-// them, and a missing candidate, also far away, hits no target) and append
-// the hits to the targets' lists.  The next chunk's candidates are loaded
-// while one is tested.  Returns the list length of target `lane` (lane < TB).
-// PER: nearest images on the periodic axes.
+// Test up to 32 queued candidates (entries [0, cnt) of sm.u.q, one per lane)
+// against the batch's targets (TB slots, the unused ones far away: no
+// candidate hits them, and a missing candidate, also far away, hits no
+// target) and append the hits to the targets' lists.
 template <int TB, bool PER>
-__device__ __forceinline__ int test_chunks(const NlistArgs &a, const NlistSmem &sm, int ncand, int i0)
+__device__ __forceinline__ void test_queued(const NlistArgs &a, const NlistSmem &sm, int cnt, int *tbase,
+                                            int (&len)[TB])
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = lane_lt();
+    const bool v = lane < cnt;
+    const float4 pj = v ? sm.u.q.p[lane] : make_float4(1e30f, 1e30f, 1e30f, 0.f);
+    const int j = v ? sm.u.q.j[lane] : -1;
+#pragma unroll
+    for (int q = 0; q < TB / 2; ++q) {
+        const int t0 = 2 * q, t1 = t0 + 1;
+        // r < max(R_i, R_j) as r^2 < max(R_i^2, R_j^2): squaring is
+        // monotone, so both compare the same rounded values
+        const float2 r2 = PER ? canon_r2_x2p(sm.tc.x[q], sm.tc.y[q], sm.tc.z[q], pj.x, pj.y, pj.z, a.tree.per)
+                              : canon_r2_x2(sm.tc.x[q], sm.tc.y[q], sm.tc.z[q], pj.x, pj.y, pj.z);
+        const bool hit0 = r2.x < fmaxf(sm.tr2[t0], pj.w);
+        const bool hit1 = r2.y < fmaxf(sm.tr2[t1], pj.w);
+        const unsigned m0 = __ballot_sync(0xffffffffu, hit0);
+        const unsigned m1 = __ballot_sync(0xffffffffu, hit1);
+        // past a.cap hits the last entry is overwritten: such a list is
+        // discarded (its length is set to -1) anyway.  Stores kept in L2 (the
+        // density pass reads the last groups' lists first).
+        if (hit0) __stcg(tbase + t0 * a.cap + min(len[t0] + __popc(m0 & lt), a.cap - 1), j);
+        if (hit1) __stcg(tbase + t1 * a.cap + min(len[t1] + __popc(m1 & lt), a.cap - 1), j);
+        len[t0] += __popc(m0);
+        len[t1] += __popc(m1);
+    }
+}
+
+// The lists of a batch of targets (sm.tc, sm.tr2, box [sm.blo, sm.bhi],
+// largest (list radius factor x h_i)^2 sm.bhi.w) from the group's candidate slots,
+// 32 per chunk (one per lane; the next chunk's candidates are loaded while
+// one is handled).  A candidate enters the queue only if it is within
+// max(its own list radius, the batch's largest) of the batch box: a
+// candidate that hits a target is always that close (the box test rounds to
+// the conservative side within kOpenSlack), so the lists are the same as
+// from testing every candidate against every target, with fewer tests when
+// the batch is smaller than the group or h varies across the group.  Every
+// 32 queued candidates are tested against the batch's targets.  Returns the
+// list length of target `lane` (lane < TB).  PER: nearest images on the
+// periodic axes.
+template <int TB, bool PER>
+__device__ __forceinline__ int test_chunks(const NlistArgs &a, NlistSmem &sm, int ncand, int i0)
 {
     const int lane = threadIdx.x & 31;
     const unsigned lt = lane_lt();
@@ -164,40 +221,56 @@ __device__ __forceinline__ int test_chunks(const NlistArgs &a, const NlistSmem &
 #pragma unroll
     for (int tt = 0; tt < TB; ++tt) len[tt] = 0;
     int *const tbase = a.idx + (size_t)i0 * a.cap;  // the batch's first list
+    int qn = 0;  // queued candidates
     int r = 0;
     int jn = lane < ncand ? slot_particle(sm.runs, r, lane) : -1;
     float4 pn = jn >= 0 ? __ldg(&a.pos[jn]) : make_float4(1e30f, 1e30f, 1e30f, 0.f);
     float hn = jn >= 0 ? __ldg(&a.h[jn]) : 0.f;
-    for (int c0 = 0; c0 < ncand; c0 += 32) {
-        const int k = c0 + lane;
-        const int j = jn;
-        const float4 pj = pn;
-        const float rj = a.rscale * hn;
-        const float rj2 = rj * rj;
-        if (c0 + 32 < ncand) {
-            jn = k + 32 < ncand ? slot_particle(sm.runs, r, k + 32) : -1;
-            pn = jn >= 0 ? __ldg(&a.pos[jn]) : make_float4(1e30f, 1e30f, 1e30f, 0.f);
-            hn = jn >= 0 ? __ldg(&a.h[jn]) : 0.f;
+    for (int c0 = 0;;) {
+        if (c0 < ncand) {  // the chunk's candidates near the batch box into the queue
+            const int k = c0 + lane;
+            const int j = jn;
+            const float4 pj = pn;
+            const float rj = a.rscale * hn;
+            const float rj2 = rj * rj;
+            if (c0 + 32 < ncand) {
+                jn = k + 32 < ncand ? slot_particle(sm.runs, r, k + 32) : -1;
+                pn = jn >= 0 ? __ldg(&a.pos[jn]) : make_float4(1e30f, 1e30f, 1e30f, 0.f);
+                hn = jn >= 0 ? __ldg(&a.h[jn]) : 0.f;
+            }
+            const float4 blo = sm.blo, bhi = sm.bhi;
+            const bool keep = j >= 0 && box_dist2_t(a.tree, blo, bhi, pj, pj) < fmaxf(bhi.w, rj2) * kOpenSlack;
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            if (keep) {
+                const int slot = qn + __popc(m & lt);
+                sm.u.q.p[slot] = make_float4(pj.x, pj.y, pj.z, rj2);
+                sm.u.q.j[slot] = j;
+            }
+            qn += __popc(m);
+            c0 += 32;
+            __syncwarp();
         }
-#pragma unroll
-        for (int q = 0; q < TB / 2; ++q) {
-            const int t0 = 2 * q, t1 = t0 + 1;
-            // r < max(R_i, R_j) as r^2 < max(R_i^2, R_j^2): squaring is
-            // monotone, so both compare the same rounded values
-            const float2 r2 = PER ? canon_r2_x2p(sm.tc.x[q], sm.tc.y[q], sm.tc.z[q], pj.x, pj.y, pj.z, a.tree.per)
-                                  : canon_r2_x2(sm.tc.x[q], sm.tc.y[q], sm.tc.z[q], pj.x, pj.y, pj.z);
-            const bool hit0 = r2.x < fmaxf(sm.tr2[t0], rj2);
-            const bool hit1 = r2.y < fmaxf(sm.tr2[t1], rj2);
-            const unsigned m0 = __ballot_sync(0xffffffffu, hit0);
-            const unsigned m1 = __ballot_sync(0xffffffffu, hit1);
-            // past a.cap hits the last entry is overwritten: such a list is
-            // discarded (its length is set to -1) anyway.  Stores kept in L2 (the
-            // density pass reads the last groups' lists first).
-            if (hit0) __stcg(tbase + t0 * a.cap + min(len[t0] + __popc(m0 & lt), a.cap - 1), j);
-            if (hit1) __stcg(tbase + t1 * a.cap + min(len[t1] + __popc(m1 & lt), a.cap - 1), j);
-            len[t0] += __popc(m0);
-            len[t1] += __popc(m1);
+        const bool last = c0 >= ncand;
+        if (qn >= 32 || (last && qn > 0)) {
+            const int cnt = min(qn, 32);
+            test_queued<TB, PER>(a, sm, cnt, tbase, len);
+            // the rest (fewer than 32) to the front of the queue
+            const int rest = qn - cnt;
+            float4 pv = make_float4(0.f, 0.f, 0.f, 0.f);
+            int jv = 0;
+            if (lane < rest) {
+                pv = sm.u.q.p[32 + lane];
+                jv = sm.u.q.j[32 + lane];
+            }
+            __syncwarp();
+            if (lane < rest) {
+                sm.u.q.p[lane] = pv;
+                sm.u.q.j[lane] = jv;
+            }
+            __syncwarp();
+            qn = rest;
         }
+        if (last && qn == 0) break;
     }
     int mine = 0;
 #pragma unroll
@@ -215,7 +288,8 @@ __global__ void __launch_bounds__(kNlWarps * 32, 7) nlist_kernel(NlistArgs a)
     const unsigned lt = lane_lt();
     const int ng = a.sizes[SZ_GROUPS];
     if (a.gate && *a.gate == 0) return;  // relist mode, nothing outgrew its pad
-    unsigned long long n_cand = 0, n_entries = 0, n_over = 0;
+    // per-warp tallies (32 bits: a warp's share of a launch stays far below 2^32)
+    unsigned n_cand = 0, n_entries = 0, n_over = 0;
 
     while (true) {
         // kSG groups at a time, kSG / 2 in the last quarter (shorter tail)
@@ -230,15 +304,14 @@ __global__ void __launch_bounds__(kNlWarps * 32, 7) nlist_kernel(NlistArgs a)
         const int sgn = min(grab, ng - gf);
         const bool have = lane < sgn;
         const int2 grl = have ? a.grp_ref[gf + lane] : make_int2(0, 0);
-        const float4 glol = have ? a.grp_lo[gf + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 ghil = have ? a.grp_hi[gf + lane] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float hml = have ? a.grp_lo[gf + lane].w : 0.f;  // the group's h_max
         const int ins = a.inst && have ? a.inst[grl.x] : 0;
         // a group starts a new run unless it is of the same instance as the
         // previous one and their h_max agree within kShareH
         const int ins_p = __shfl_up_sync(0xffffffffu, ins, 1);
-        const float hm_p = __shfl_up_sync(0xffffffffu, glol.w, 1);
-        const bool starts = have && (lane == 0 || ins != ins_p || glol.w > kShareH * hm_p ||
-                                     hm_p > kShareH * glol.w);
+        const float hm_p = __shfl_up_sync(0xffffffffu, hml, 1);
+        const bool starts = have && (lane == 0 || ins != ins_p || hml > kShareH * hm_p ||
+                                     hm_p > kShareH * hml);
         const unsigned bstart = __ballot_sync(0xffffffffu, starts);
         // with a due-target mask (block steps): the groups holding a due target
         unsigned bdue = 0xffffffffu;
@@ -268,8 +341,8 @@ __global__ void __launch_bounds__(kNlWarps * 32, 7) nlist_kernel(NlistArgs a)
             int nshared;
             while (true) {
                 const bool mine = lane >= s && lane < e;
-                float4 ulo = mine ? glol : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
-                float4 uhi = mine ? ghil : make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
+                float4 ulo = mine ? a.grp_lo[gf + lane] : make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+                float4 uhi = mine ? a.grp_hi[gf + lane] : make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
                 for (int o = 16; o > 0; o >>= 1) {
                     ulo.x = fminf(ulo.x, __shfl_xor_sync(0xffffffffu, ulo.x, o));
                     ulo.y = fminf(ulo.y, __shfl_xor_sync(0xffffffffu, ulo.y, o));
@@ -296,26 +369,48 @@ __global__ void __launch_bounds__(kNlWarps * 32, 7) nlist_kernel(NlistArgs a)
                 for (int b0 = 0; b0 < gr.y; b0 += kNlTB) {
                     const int nt = min(kNlTB, gr.y - b0);
                     const int i0 = gr.x + b0;
+                    // the batch's targets, their box and largest list radius
+                    float4 blo = make_float4(INFINITY, INFINITY, INFINITY, 0.f);
+                    float4 bhi = make_float4(-INFINITY, -INFINITY, -INFINITY, 0.f);
+                    float tr2max = 0.f;
                     if (lane < kNlTB) {
                         const float4 p = lane < nt ? a.pos[i0 + lane] : make_float4(1e30f, 1e30f, 1e30f, 0.f);
                         sm.tc.set(lane, p);
                         const float rt = lane < nt ? a.rscale * a.h[i0 + lane] : 0.f;
                         sm.tr2[lane] = rt * rt;
+                        if (lane < nt) {
+                            blo = make_float4(p.x, p.y, p.z, 0.f);
+                            bhi = blo;
+                            tr2max = rt * rt;
+                        }
+                    }
+                    for (int o = 16; o > 0; o >>= 1) {
+                        blo.x = fminf(blo.x, __shfl_xor_sync(0xffffffffu, blo.x, o));
+                        blo.y = fminf(blo.y, __shfl_xor_sync(0xffffffffu, blo.y, o));
+                        blo.z = fminf(blo.z, __shfl_xor_sync(0xffffffffu, blo.z, o));
+                        bhi.x = fmaxf(bhi.x, __shfl_xor_sync(0xffffffffu, bhi.x, o));
+                        bhi.y = fmaxf(bhi.y, __shfl_xor_sync(0xffffffffu, bhi.y, o));
+                        bhi.z = fmaxf(bhi.z, __shfl_xor_sync(0xffffffffu, bhi.z, o));
+                        tr2max = fmaxf(tr2max, __shfl_xor_sync(0xffffffffu, tr2max, o));
+                    }
+                    if (lane == 0) {
+                        sm.blo = blo;
+                        sm.bhi = make_float4(bhi.x, bhi.y, bhi.z, tr2max);
                     }
                     __syncwarp();
                     int mlen = 0;
                     if (ncand > 0) {
                         if (nt <= 4) mlen = test_chunks<4, PER>(a, sm, ncand, i0);
                         else if (nt <= 8) mlen = test_chunks<8, PER>(a, sm, ncand, i0);
-                        else mlen = test_chunks<16, PER>(a, sm, ncand, i0);
-                        n_cand += (unsigned long long)nt * (unsigned long long)ncand;
+                        else mlen = test_chunks<kNlTB, PER>(a, sm, ncand, i0);
+                        n_cand += (unsigned)nt * (unsigned)ncand;
                     }
                     // a group without lists is left to the walking kernels
                     const bool fits = ok && mlen <= a.cap;
                     if (lane < nt) {
                         a.len[i0 + lane] = fits ? mlen : -1;
-                        n_entries += (unsigned long long)min(mlen, a.cap);
-                        n_over += fits ? 0ull : 1ull;
+                        n_entries += (unsigned)min(mlen, a.cap);
+                        n_over += fits ? 0u : 1u;
                     }
                     __syncwarp();
                 }
@@ -328,9 +423,9 @@ __global__ void __launch_bounds__(kNlWarps * 32, 7) nlist_kernel(NlistArgs a)
         n_over += __shfl_xor_sync(0xffffffffu, n_over, o);
     }
     if (lane == 0) {
-        atomicAdd(&a.counters[C_DENS_CAND], n_cand);  // candidate x target tests
-        atomicAdd(&a.counters[C_LIST_ENTRIES], n_entries);
-        atomicAdd(&a.counters[C_LIST_OVERFLOW], n_over);
+        atomicAdd(&a.counters[C_DENS_CAND], (unsigned long long)n_cand);  // candidate x target tests
+        atomicAdd(&a.counters[C_LIST_ENTRIES], (unsigned long long)n_entries);
+        atomicAdd(&a.counters[C_LIST_OVERFLOW], (unsigned long long)n_over);
     }
 }
 
