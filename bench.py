@@ -60,7 +60,7 @@ FLOP_PAIR = {0: (FLOP_FORCE_PAIR, FLOP_DENSITY_PAIR), 1: (106, 75), 2: (104, 66)
 EXEC_FLOP_FORCE_PAIR = 84.0
 # DRAM bytes (read + write) per launch of the pair kernels from one ncu capture
 # of the 128^3 step; None where the kernel changed after the capture.
-NCU_TRAFFIC = {"nlist_kernel": 132.78464e6 + 587.955712e6,
+NCU_TRAFFIC = {"nlist_kernel": 135.363328e6 + 602.912256e6,
                "density_list_kernel": 1.07383e9 + 49.421568e6,
                "force_list_kernel": 1.00118e9 + 29.120512e6}
 # Self-gravity FP32 operations per interaction (softened pair: separation 3,
