@@ -172,7 +172,9 @@ sph_status sph_step(sph_ctx *ctx, sph_state *s, const sph_params *p, float *d_dt
 /* Batched form (not in the paper): n_inst independent SPH problems packed
  * back to back in one state; instance k owns slots [d_offsets[k],
  * d_offsets[k+1]) (device int64 [n_inst+1], ascending, d_offsets[0] = 0,
- * d_offsets[n_inst] = n, every instance non-empty, n_inst <= 65536).  Each
+ * d_offsets[n_inst] = n, every instance non-empty, n_inst <= 65536; other
+ * offsets are reported as SPH_ERR_INVALID_ARG through the error word, and
+ * no kernel then reads or writes outside the state's n slots).  Each
  * instance gets its own bounding box, keys, tree and groups (the sort keeps
  * every instance on its own slots), its own Courant step and its own time:
  * d_dt is a device float [n_inst], d_time a device double [n_inst] (or NULL).
@@ -282,7 +284,8 @@ sph_status sph_conserved_noalloc(int64_t n, const float *d_pos, const float *d_v
  *
  * sph_step_block: one block of 2^max_level substeps of *d_dt_min (device
  * float) with the levels d_level (caller order, each in [0, max_level],
- * fixed for the block).  It first sorts the state into curve order (as
+ * fixed for the block; a level outside that range counts as 0 and is
+ * reported as SPH_ERR_INVALID_ARG through the error word).  It first sorts the state into curve order (as
  * sph_build_tree: acc, h, rho, omega, drhodt, vsigmax move along), then per
  * substep j: particles whose step starts (j mod 2^L = 0) get their opening
  * half kick from their last acceleration; all drift with their half-step

@@ -535,6 +535,8 @@ static cudaError_t launch_pairwalk(Ctx &c, const sph_state &s, bool dens_set, fl
                                    const Op &op, cudaStream_t st, const Batch *batch)
 {
     size_t smem = sizeof(PairWalkSmem<CAP>) * 4;
+    static std::mutex mu;  // first calls may come from several host threads
+    std::lock_guard<std::mutex> lock(mu);
     static bool configured = false;
     static int blocks = 1;
     if (!configured) {

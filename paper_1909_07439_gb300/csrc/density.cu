@@ -634,6 +634,8 @@ __global__ void list_set_kernel(const float4 *__restrict__ pos, const float *__r
 template <int CAP, int K>
 static cudaError_t configure_density(int &blocks)
 {
+    static std::mutex mu;  // first calls may come from several host threads
+    std::lock_guard<std::mutex> lock(mu);
     static bool configured = false;
     static int nb_cached = 1;
     if (!configured) {
@@ -657,6 +659,8 @@ static cudaError_t configure_density(int &blocks)
 template <int K>
 static cudaError_t configure_density_list(int blocks[4])
 {
+    static std::mutex mu;  // first calls may come from several host threads
+    std::lock_guard<std::mutex> lock(mu);
     static bool configured = false;
     static int nb_cached[4];
     if (!configured) {

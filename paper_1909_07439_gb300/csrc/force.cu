@@ -495,6 +495,8 @@ __global__ void force_prep_kernel(const float4 *__restrict__ pos, const float4 *
 template <int CAP, int K>
 static cudaError_t configure_force(int &blocks)
 {
+    static std::mutex mu;  // first calls may come from several host threads
+    std::lock_guard<std::mutex> lock(mu);
     static bool configured = false;
     static int nb_cached = 1;
     if (!configured) {
@@ -518,6 +520,8 @@ static cudaError_t configure_force(int &blocks)
 template <int K>
 static cudaError_t configure_force_list(int blocks[2][4])
 {
+    static std::mutex mu;  // first calls may come from several host threads
+    std::lock_guard<std::mutex> lock(mu);
     static bool configured = false;
     static int nb_cached[2][4];
     if (!configured) {

@@ -322,6 +322,8 @@ __global__ void __launch_bounds__(kGWarps * 32) gravity_kernel(GravArgs a)
 
 static cudaError_t configure_gravity(int &blocks)
 {
+    static std::mutex mu;  // first calls may come from several host threads
+    std::lock_guard<std::mutex> lock(mu);
     static bool configured = false;
     static int nb_cached = 1;
     if (!configured) {

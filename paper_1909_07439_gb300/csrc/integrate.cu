@@ -192,12 +192,24 @@ __global__ void conserved_final_kernel(const double *part, int nb, double *out8)
 // v = v_half + a ((j mod 2^L + 1) dt_min - dt/2); the particles whose step ends
 // there ((j + 1) mod 2^L = 0) are flagged for the density and force passes;
 // the packed records take the new position and velocity.
+// a particle's level, checked: outside [0, max_level] it counts as 0 (and
+// the substep kernel reports SPH_ERR_INVALID_ARG)
+__device__ __forceinline__ int block_level(const int *level, const uint32_t *perm, int i, int max_level,
+                                           bool &bad)
+{
+    const int L = level[perm[i]];
+    bad = L < 0 || L > max_level;
+    return bad ? 0 : L;
+}
+
 __global__ void block_substep_kernel(float4 *__restrict__ pos, float4 *__restrict__ vel,
                                      const float4 *__restrict__ acc, float4 *__restrict__ vhalf,
                                      float4 *__restrict__ rec, uint8_t *__restrict__ due,
                                      const uint32_t *__restrict__ perm, const int *__restrict__ level,
-                                     int n, int j, const float *d_dt_min, Period per, float3 plo)
+                                     int n, int j, int max_level, const float *d_dt_min, Period per,
+                                     float3 plo, int *err)
 {
+    bool any_bad = false;
     const float dtm = *d_dt_min;
     auto wrap = [](float x, float L, float lo) {
         if (L > 0.f) {
@@ -208,7 +220,9 @@ __global__ void block_substep_kernel(float4 *__restrict__ pos, float4 *__restric
         return x;
     };
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int L = level[perm[i]];
+        bool bad;
+        const int L = block_level(level, perm, i, max_level, bad);
+        any_bad |= bad;
         const int mask = (1 << L) - 1;
         const float dt = dtm * (float)(1 << L);
         const float4 a = acc[i];
@@ -232,19 +246,21 @@ __global__ void block_substep_kernel(float4 *__restrict__ pos, float4 *__restric
         rec[2 * (size_t)i + 1] = w;
         due[i] = ((j + 1) & mask) == 0 ? 1 : 0;
     }
+    if (__any_sync(0xffffffffu, any_bad) && (threadIdx.x & 31) == 0) raise_error(err, SPH_ERR_INVALID_ARG);
 }
 
 // the closing half kick of the particles whose step ended: v = v_half + a dt/2
 __global__ void block_close_kernel(float4 *__restrict__ vel, const float4 *__restrict__ acc,
                                    const float4 *__restrict__ vhalf, const uint8_t *__restrict__ due,
                                    const uint32_t *__restrict__ perm, const int *__restrict__ level,
-                                   int n, const float *d_dt_min, double *d_time, int *err)
+                                   int n, int max_level, const float *d_dt_min, double *d_time, int *err)
 {
     const float dtm = *d_dt_min;
     bool neg = false;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         if (!due[i]) continue;
-        const float hdt = 0.5f * dtm * (float)(1 << level[perm[i]]);
+        bool bad;
+        const float hdt = 0.5f * dtm * (float)(1 << block_level(level, perm, i, max_level, bad));
         const float4 vh = vhalf[i], a = acc[i];
         const float4 v = make_float4(vh.x + hdt * a.x, vh.y + hdt * a.y, vh.z + hdt * a.z, vh.w + hdt * a.w);
         neg |= !(v.w >= 0.f);
@@ -274,22 +290,22 @@ __global__ void block_levels_kernel(const float *__restrict__ h, const float *__
 }
 
 cudaError_t block_substep(Ctx &c, const sph_state &s, const sph_params &p, const int *d_level, int j,
-                          const float *d_dt_min, cudaStream_t st)
+                          int max_level, const float *d_dt_min, cudaStream_t st)
 {
     const int n = (int)s.n;
     block_substep_kernel<<<grid_n(c, n, 256), 256, 0, st>>>(
         (float4 *)s.pos, (float4 *)s.vel, (const float4 *)s.acc, c.vhalf, c.rec, c.active, s.perm,
-        d_level, n, j, d_dt_min, period_of(p), box_lo_of(p));
+        d_level, n, j, max_level, d_dt_min, period_of(p), box_lo_of(p), c.d_err);
     return cudaGetLastError();
 }
 
-cudaError_t block_close(Ctx &c, const sph_state &s, const int *d_level, const float *d_dt_min,
-                        double *d_time, cudaStream_t st)
+cudaError_t block_close(Ctx &c, const sph_state &s, const int *d_level, int max_level,
+                        const float *d_dt_min, double *d_time, cudaStream_t st)
 {
     const int n = (int)s.n;
     block_close_kernel<<<grid_n(c, n, 256), 256, 0, st>>>((float4 *)s.vel, (const float4 *)s.acc,
                                                           c.vhalf, c.active, s.perm, d_level, n,
-                                                          d_dt_min, d_time, c.d_err);
+                                                          max_level, d_dt_min, d_time, c.d_err);
     return cudaGetLastError();
 }
 

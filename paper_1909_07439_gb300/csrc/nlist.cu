@@ -431,6 +431,8 @@ __global__ void __launch_bounds__(kNlWarps * 32, 7) nlist_kernel(NlistArgs a)
 
 static cudaError_t configure_nlist(int &blocks)
 {
+    static std::mutex mu;  // first calls may come from several host threads
+    std::lock_guard<std::mutex> lock(mu);
     static bool configured = false;
     static int nb_cached = 1;
     if (!configured) {

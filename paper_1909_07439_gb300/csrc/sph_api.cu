@@ -580,7 +580,7 @@ sph_status sph_step_block(sph_ctx *h, sph_state *s, const sph_params *p, int max
     for (int j = 0; j < (1 << max_level); ++j) {
         {
             StageScope sc(c, ST_LEAPFROG, st, 1);
-            CK(block_substep(c, *s, *p, d_level, j, d_dt_min, st), "block substep");
+            CK(block_substep(c, *s, *p, d_level, j, max_level, d_dt_min, st), "block substep");
         }
         {
             StageScope sc(c, ST_TREE, st, 2);
@@ -592,7 +592,7 @@ sph_status sph_step_block(sph_ctx *h, sph_state *s, const sph_params *p, int max
         c.mask = nullptr;
         if (r != SPH_OK) return r;
         StageScope sc(c, ST_LEAPFROG, st, 1);
-        CK(block_close(c, *s, d_level, d_dt_min, d_time, st), "block close");
+        CK(block_close(c, *s, d_level, max_level, d_dt_min, d_time, st), "block close");
     }
     return SPH_OK;
 }

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -58,8 +59,9 @@ enum Counter {
 
 // tree-size scalars on the device (Ctx::d_sizes)
 // SZ_WORK / SZ_WORK2: work counters of the persistent kernels; SZ_FALLBACK:
-// entries in Ctx::fallback
-enum Size { SZ_NODES = 0, SZ_GROUPS = 1, SZ_WORK = 3, SZ_FALLBACK = 4, SZ_WORK2 = 5, SZ_N = 8 };
+// entries in Ctx::fallback; SZ_BAD_OFFSETS: the batch offsets failed their check
+enum Size { SZ_NODES = 0, SZ_GROUPS = 1, SZ_WORK = 3, SZ_FALLBACK = 4, SZ_WORK2 = 5, SZ_BAD_OFFSETS = 6,
+            SZ_N = 8 };
 
 struct Tree {
     int cap_nodes = 0;
@@ -283,9 +285,9 @@ cudaError_t kick_drift(Ctx &c, const sph_state &s, const sph_params &p, const fl
 // block time steps (integrate.cu): substep j's kicks, drift, prediction and
 // due flags; the closing kicks of the due particles; the levels from Eq. 8
 cudaError_t block_substep(Ctx &c, const sph_state &s, const sph_params &p, const int *d_level, int j,
-                          const float *d_dt_min, cudaStream_t st);
-cudaError_t block_close(Ctx &c, const sph_state &s, const int *d_level, const float *d_dt_min,
-                        double *d_time, cudaStream_t st);
+                          int max_level, const float *d_dt_min, cudaStream_t st);
+cudaError_t block_close(Ctx &c, const sph_state &s, const int *d_level, int max_level,
+                        const float *d_dt_min, double *d_time, cudaStream_t st);
 cudaError_t block_levels(Ctx &c, const sph_state &s, const sph_params &p, int max_level,
                          const float *d_dt_min, int *d_level, cudaStream_t st);
 // node and group boxes and h_max from the current positions and h, without

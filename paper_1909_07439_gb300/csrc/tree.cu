@@ -652,11 +652,14 @@ __global__ void level_start_kernel(const int *blk_off, int nb, const int *total,
     }
 }
 
-// end of the run at level L that starts at s (galloping search)
-__device__ int run_end(const uint64_t *__restrict__ keys, const int *__restrict__ inst,
-                       const int64_t *__restrict__ offs, int n, int s, int L)
+// end of the run at level L that starts at s (galloping search).  The
+// root run of a batch instance is its slots (the sort keeps each instance's
+// slots together), found from the instance ids, so the tree stays inside
+// [0, n) whatever the caller's offsets hold.
+__device__ int run_end(const uint64_t *__restrict__ keys, const int *__restrict__ inst, int n, int s,
+                       int L)
 {
-    if (L == 0) return inst ? (int)offs[inst[s] + 1] : n;
+    if (L == 0 && !inst) return n;
     int step = 1, lo = s;  // slot lo is in the run
     while (s + step < n && cd_slots(keys, inst, s + step, s) >= L) {
         lo = s + step;
@@ -671,13 +674,12 @@ __device__ int run_end(const uint64_t *__restrict__ keys, const int *__restrict_
 }
 
 __global__ void node_finish_kernel(const uint64_t *__restrict__ keys, const int *__restrict__ inst,
-                                   const int64_t *__restrict__ offs, int n, int T, Tree t,
-                                   const int *sizes)
+                                   int n, int T, Tree t, const int *sizes)
 {
     int nn = sizes[SZ_NODES];
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nn; k += gridDim.x * blockDim.x) {
         int L = t.node_level[k], s = t.node_first[k];
-        int cnt = run_end(keys, inst, offs, n, s, L) - s;
+        int cnt = run_end(keys, inst, n, s, L) - s;
         t.node_count[k] = cnt;
         if (L == 0) t.node_parent[k] = -1;
         int cf = -1, nc = 0;
@@ -799,9 +801,36 @@ __global__ void group_bounds_kernel(const float4 *__restrict__ pos, const float 
 }
 
 // inst[k] = instance owning slot k (offsets ascending, every instance non-empty)
-__global__ void instance_map_kernel(const int64_t *__restrict__ offs, int n_inst, int n, int *inst)
+// *bad = 1 (and SPH_ERR_INVALID_ARG) unless 0 = offs[0] < offs[1] < ... <
+// offs[n_inst] = n (one block)
+__global__ void offsets_check_kernel(const int64_t *__restrict__ offs, int n_inst, int n, int *bad, int *err)
 {
+    bool b = false;
+    for (int k = threadIdx.x; k <= n_inst; k += blockDim.x)
+        b |= k == 0 ? offs[0] != 0
+           : k == n_inst ? offs[k] != (int64_t)n || offs[k - 1] >= offs[k]
+                         : offs[k - 1] >= offs[k];
+    b = __syncthreads_or(b);
+    if (threadIdx.x == 0) {
+        *bad = b ? 1 : 0;
+        if (b) raise_error(err, SPH_ERR_INVALID_ARG);
+    }
+}
+
+// inst[k] = the instance of particle k (caller order).  With offsets that
+// failed their check, instance i < n_inst - 1 gets particle i alone and the
+// last one the rest (n >= n_inst): every instance keeps a particle, so the
+// instances' roots are the first n_inst nodes as the walks assume, and no
+// kernel leaves the state's slots.
+__global__ void instance_map_kernel(const int64_t *__restrict__ offs, int n_inst, int n, const int *bad,
+                                    int *inst)
+{
+    const bool valid = *bad == 0;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        if (!valid) {
+            inst[k] = min(k, n_inst - 1);
+            continue;
+        }
         int lo = 0, hi = n_inst - 1;  // largest i with offs[i] <= k
         while (lo < hi) {
             int mid = (lo + hi + 1) >> 1;
@@ -828,7 +857,9 @@ static int grid_for(const Ctx &c, int64_t n, int block)
 
 cudaError_t instance_map(Ctx &c, const int64_t *d_offsets, int n_inst, int n, cudaStream_t st)
 {
-    instance_map_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(d_offsets, n_inst, n, c.inst);
+    int *bad = c.d_sizes + SZ_BAD_OFFSETS;
+    offsets_check_kernel<<<1, 1024, 0, st>>>(d_offsets, n_inst, n, bad, c.d_err);
+    instance_map_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(d_offsets, n_inst, n, bad, c.inst);
     return cudaGetLastError();
 }
 
@@ -849,7 +880,6 @@ cudaError_t build_tree(Ctx &c, const sph_state &s, const sph_params &p, bool ful
     Tree &t = c.tree;
     float4 *pos = (float4 *)s.pos;
     const int *inst = batch ? c.inst : nullptr;
-    const int64_t *offs = batch ? batch->offsets : nullptr;
     int *bb = batch ? c.bbox_inst : (int *)c.bbox;
     // Within a step (full_permute = false) kick_drift has left the kicked pos,
     // vel, v_half, h and perm in the temporaries: keys come from there and
@@ -957,8 +987,8 @@ cudaError_t build_tree(Ctx &c, const sph_state &s, const sph_params &p, bool ful
     SPH_TRY(scan_mode(c, t.blk_cnt, blk_off, kLevels * nb, 0, ntotal, st));
     chop_write_kernel<<<nb, 256, 0, st>>>(t.lv_tree, n, blk_off, nb, t, c.d_err);
     level_start_kernel<<<1, 32, 0, st>>>(blk_off, nb, ntotal, t, c.d_sizes);
-    node_finish_kernel<<<grid_for(c, t.cap_nodes, 256), 256, 0, st>>>(s.keys, inst, offs, n,
-                                                                       p.n_leaf, t, c.d_sizes);
+    node_finish_kernel<<<grid_for(c, t.cap_nodes, 256), 256, 0, st>>>(s.keys, inst, n, p.n_leaf, t,
+                                                                       c.d_sizes);
     node_bounds_kernel<<<grid_for(c, t.cap_nodes, 128), 128, 0, st>>>(pos, s.h, t, c.d_sizes, 0, nullptr);
     return cudaGetLastError();
 }

@@ -123,3 +123,35 @@ def test_batch_rejects_bad_offsets(lib):
             native.sph_batch_evaluate(ctx, s.c, d_off, 0, native.sph_params_default(), dt)
     finally:
         native.sph_destroy(ctx)
+
+
+@pytest.mark.parametrize("case", ["past_n", "not_increasing", "not_from_zero"])
+def test_batch_reports_inconsistent_offsets(lib, case):
+    # offsets are device data: the library checks them on the device and
+    # reports SPH_ERR_INVALID_ARG through the error word; the pass itself
+    # stays inside the state's slots, and the context stays usable
+    native, torch = lib
+    from paper_1909_07439_gb300 import DeviceState
+    w, off = _batch(n_inst=4)
+    bad = off.copy()
+    if case == "past_n":
+        bad[-1] = w.n + 1000
+    elif case == "not_increasing":
+        bad[2] = bad[1]
+    else:
+        bad[0] = 5
+    ctx = native.sph_create(w.n, 0)
+    try:
+        s = DeviceState.from_arrays(w.pos, w.vel, w.h)
+        p = native.sph_params_default()
+        dt = torch.zeros(4, dtype=torch.float32, device="cuda")
+        native.sph_batch_evaluate(ctx, s.c, torch.as_tensor(bad, device="cuda"), 4, p, dt)
+        with pytest.raises(native.SphError) as e:
+            native.sph_sync(ctx)
+        assert e.value.status == 1  # SPH_ERR_INVALID_ARG
+        s = DeviceState.from_arrays(w.pos, w.vel, w.h)
+        native.sph_batch_evaluate(ctx, s.c, torch.as_tensor(off, device="cuda"), 4, p, dt)
+        native.sph_sync(ctx)
+        assert np.all(np.isfinite(s.numpy("acc")))
+    finally:
+        native.sph_destroy(ctx)

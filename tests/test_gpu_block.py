@@ -167,3 +167,30 @@ def test_block_step_saves_work(sph):
         pairs.append(native.sph_get_stats(ctx)["force_pairs"])
     print("force pairs: 8 global steps", pairs[0], "one block", pairs[1])
     assert pairs[1] < 0.5 * pairs[0]
+
+
+def test_block_level_out_of_range_is_reported(sph):
+    # a level outside [0, max_level] is device data: the substep kernel
+    # reports it through the error word (read by sph_sync) and steps the
+    # particle as level 0
+    native, ctx, torch = sph
+    from paper_1909_07439_gb300 import DeviceState
+    w = inputs.unit_sphere(3000, seed=11, sigma_v=0.1)
+    s = DeviceState.from_arrays(w.pos, w.vel, w.h)
+    p = native.sph_params_default()
+    native.sph_build_tree(ctx, s.c, p)
+    native.sph_density(ctx, s.c, p)
+    native.sph_force(ctx, s.c, p)
+    native.sph_sync(ctx)
+    d_dt = torch.zeros(1, dtype=torch.float32, device="cuda")
+    d_level = torch.zeros(w.n, dtype=torch.int32, device="cuda")
+    native.sph_block_levels(ctx, s.c, p, 2, d_dt, d_level)
+    d_level[17] = 3                         # above max_level = 2
+    native.sph_step_block(ctx, s.c, p, 2, d_level, d_dt)
+    with pytest.raises(native.SphError) as e:
+        native.sph_sync(ctx)
+    assert e.value.status == 1  # SPH_ERR_INVALID_ARG
+    # the context stays usable
+    native.sph_build_tree(ctx, s.c, p)
+    native.sph_density(ctx, s.c, p)
+    native.sph_sync(ctx)
