@@ -159,7 +159,10 @@ sph_status sph_timestep(sph_ctx *ctx, const sph_state *s, const sph_params *p, f
 /* One leapfrog step (Eqs. 5-7 in kick-drift-kick form) with dt = *d_dt:
  * kick/drift with the acc already in the state, tree build, density and force
  * at the new positions with predicted v and u, closing kick, then the next
- * Courant step is written to *d_dt.  If d_time is not NULL, *d_time += dt
+ * Courant step is written to *d_dt.  Inside a step drhodt comes from the
+ * force pass (Eq. 3 is, up to the factor rho_i A_i, the pair sum of the
+ * energy equation's pressure work), so the density pass gathers positions
+ * only.  If d_time is not NULL, *d_time += dt
  * (device double).  Nothing returns to the host inside the call.
  * The first call for a given (state arrays, n, params, d_dt, d_time, timing
  * on/off) records the step's kernels into a CUDA graph (the context keeps the
@@ -235,7 +238,7 @@ sph_status sph_rollout(sph_ctx *ctx, const sph_state *init, const sph_params *p,
  * the first dt and receives the next one.  Allocates a device mirror on the
  * first call.  With every array of *hs pinned, the last step copies each
  * output back on a second stream as soon as it is final (pos, perm, keys
- * after the tree build; h, rho, omega, drhodt after the density pass; acc,
+ * after the tree build; h, rho, omega after the density pass; acc, drhodt,
  * vsigmax after the force pass), so those copies overlap the rest of the
  * step.  Synchronous. */
 sph_status sph_step_host(sph_ctx *ctx, sph_state *host_state, const sph_params *p, int n_steps,

@@ -66,6 +66,7 @@ struct DensArgs {
     float h_in_scale; // 1 + pad
     float hfact, tol, gamma;
     int tb;           // targets per batch of the list kernel (4, 8 or 16)
+    int vd;           // 1: drho/dt here (Eq. 3); 0: the force pass of the step writes it
     int max_iter, fixed_iters;
     int *err;
     unsigned long long *counters;
@@ -81,7 +82,7 @@ __device__ __forceinline__ float seg_sum(float v, int L)
 // vanish beyond its support):
 //   s0 += m_j f(q), s1 += m_j (3 f + q f'), s2 += m_j vd f' / r
 // (h^3 rho = C s0, -h^4 d(rho)/dh = C s1, Eq. 3 numerator x h^4 / C = s2).
-template <int K>
+template <int K, bool VD = true>
 __device__ __forceinline__ void pair_sums(float r2, float mj, float vd, float hinv, float &s0,
                                           float &s1, float &s2)
 {
@@ -92,7 +93,7 @@ __device__ __forceinline__ void pair_sums(float r2, float mj, float vd, float hi
     SphKernel<K>::f_df(q, f, df);
     s0 += mj * f;
     s1 += mj * (3.f * f + q * df);
-    s2 += mj * vd * df * rinv;
+    if (VD) s2 += mj * vd * df * rinv;
 }
 
 // One bracketed Newton update of h from the sums at h; g h^3 = C s0 - M,
@@ -125,8 +126,9 @@ __device__ __forceinline__ void newton_update(float &h, float &hlo, float &hhi, 
 }
 
 // outputs at the accepted h (Eqs. 1-4) and the force pass's per-particle terms
+// (drho/dt only with vd: otherwise the force pass of the step writes it)
 __device__ __forceinline__ void density_outputs(const DensArgs &a, int i, float h, float M, float s1,
-                                                float s2, float u, float C)
+                                                float s2, float u, float C, bool vd = true)
 {
     const float hinv = 1.f / h;
     const float rho = M * hinv * hinv * hinv;
@@ -135,7 +137,7 @@ __device__ __forceinline__ void density_outputs(const DensArgs &a, int i, float 
     a.h[i] = h;
     a.rho[i] = rho;
     a.omega[i] = om;
-    a.drhodt[i] = F4 * s2 / om;
+    if (vd) a.drhodt[i] = F4 * s2 / om;
     const float cs = sqrtf(fmaxf(a.gamma * (a.gamma - 1.f) * u, 0.f));
     a.prop[i] = make_float4(h, rho, 1.f / (rho * om), cs);
 }
@@ -147,8 +149,10 @@ __device__ __forceinline__ void push_fallback(const DensArgs &a, int g, int b0, 
 
 // Launch shape (run-time): a.tb targets per batch (32 / a.tb lanes per
 // target), blockDim.x / 32 warps per block; NPER list entries per lane and
-// iteration; registers capped for 1024 resident threads per SM.
-template <int NPER, int K, bool PER>
+// iteration; registers capped for 1024 resident threads per SM.  VD: the
+// sums of drho/dt too, over 32-byte records (position, velocity); without,
+// the neighbours' 16-byte positions alone are gathered.
+template <int NPER, int K, bool PER, bool VD>
 __global__ void __launch_bounds__(256, 4) density_list_kernel(DensArgs a)
 {
     const int lane = threadIdx.x & 31;
@@ -216,9 +220,15 @@ __global__ void __launch_bounds__(256, 4) density_list_kernel(DensArgs a)
                             dz = wrap_sep(dz, a.tree.per.z);
                         }
                         const float r2 = dx * dx + dy * dy + dz * dz;
-                        const float vd = (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz;
+                        const float vd =
+                            VD ? (vi.x - vj.x) * dx + (vi.y - vj.y) * dy + (vi.z - vj.z) * dz : 0.f;
                         cnt += (mj > 0.f && r2 < R2) ? 1 : 0;
-                        pair_sums<K>(r2, mj, vd, hinv, s0, s1, s2);
+                        pair_sums<K, VD>(r2, mj, vd, hinv, s0, s1, s2);
+                    };
+                    // neighbour j's position (and velocity with VD)
+                    auto load = [&](int j, float4 &pj, float4 &vj) {
+                        if (VD) ld_rec(a.rec, j, keep, pj, vj);
+                        else pj = ld_keep(a.pos, j, keep);
                     };
                     if (NPER == 4) {
                         int e = 4 * sub;
@@ -228,10 +238,10 @@ __global__ void __launch_bounds__(256, 4) density_list_kernel(DensArgs a)
                             if (e + 4 * L < len) jn = __ldcs(reinterpret_cast<const int4 *>(lst + e + 4 * L));
                             const bool b1 = e + 1 < len, b2 = e + 2 < len, b3 = e + 3 < len;
                             float4 p0, v0, p1, v1, p2, v2, p3, v3;
-                            ld_rec(a.rec, jj.x, keep, p0, v0);
-                            ld_rec(a.rec, b1 ? jj.y : jj.x, keep, p1, v1);
-                            ld_rec(a.rec, b2 ? jj.z : jj.x, keep, p2, v2);
-                            ld_rec(a.rec, b3 ? jj.w : jj.x, keep, p3, v3);
+                            load(jj.x, p0, v0);
+                            load(b1 ? jj.y : jj.x, p1, v1);
+                            load(b2 ? jj.z : jj.x, p2, v2);
+                            load(b3 ? jj.w : jj.x, p3, v3);
                             entry(p0, v0, p0.w);
                             entry(p1, v1, b1 ? p1.w : 0.f);
                             entry(p2, v2, b2 ? p2.w : 0.f);
@@ -245,8 +255,8 @@ __global__ void __launch_bounds__(256, 4) density_list_kernel(DensArgs a)
                             if (e + 2 * L < len) jn = __ldcs(reinterpret_cast<const int2 *>(lst + e + 2 * L));
                             const bool b1 = e + 1 < len;
                             float4 p0, v0, p1, v1;
-                            ld_rec(a.rec, jj.x, keep, p0, v0);
-                            ld_rec(a.rec, b1 ? jj.y : jj.x, keep, p1, v1);
+                            load(jj.x, p0, v0);
+                            load(b1 ? jj.y : jj.x, p1, v1);
                             entry(p0, v0, p0.w);
                             entry(p1, v1, b1 ? p1.w : 0.f);
                         }
@@ -279,7 +289,7 @@ __global__ void __launch_bounds__(256, 4) density_list_kernel(DensArgs a)
                     push_fallback(a, g, b0, nt);
                     continue;
                 }
-                if (on && sub == 0) density_outputs(a, i, h, M, s1, s2, vi.w, SphKernel<K>::C);
+                if (on && sub == 0) density_outputs(a, i, h, M, s1, s2, vi.w, SphKernel<K>::C, VD);
             }
         }
     }
@@ -664,10 +674,14 @@ static cudaError_t configure_density_list(int blocks[4])
     static bool configured = false;
     static int nb_cached[4];
     if (!configured) {
-        const void *fns[4] = {(const void *)density_list_kernel<2, K, false>,
-                              (const void *)density_list_kernel<2, K, true>,
-                              (const void *)density_list_kernel<4, K, false>,
-                              (const void *)density_list_kernel<4, K, true>};
+        const void *fns[8] = {(const void *)density_list_kernel<2, K, false, true>,
+                              (const void *)density_list_kernel<2, K, true, true>,
+                              (const void *)density_list_kernel<4, K, false, true>,
+                              (const void *)density_list_kernel<4, K, true, true>,
+                              (const void *)density_list_kernel<2, K, false, false>,
+                              (const void *)density_list_kernel<2, K, true, false>,
+                              (const void *)density_list_kernel<4, K, false, false>,
+                              (const void *)density_list_kernel<4, K, true, false>};
         for (int w = 0; w < 4; ++w) {
             int nb = 1 << 30;
             for (const void *f : fns) {
@@ -725,10 +739,17 @@ static cudaError_t density_solve_k(Ctx &c, DensArgs &a, const sph_params &p, cud
     const int wl = ps.warps == 8 ? 3 : ps.warps == 4 ? 2 : ps.warps == 2 ? 1 : 0;
     const dim3 grid(c.num_sms * bl[wl]), block(32 * ps.warps);
     const bool per = a.tree.per.any();
-    if (ps.unroll == 4 && per) density_list_kernel<4, K, true><<<grid, block, 0, st>>>(a);
-    else if (ps.unroll == 4) density_list_kernel<4, K, false><<<grid, block, 0, st>>>(a);
-    else if (per) density_list_kernel<2, K, true><<<grid, block, 0, st>>>(a);
-    else density_list_kernel<2, K, false><<<grid, block, 0, st>>>(a);
+    if (a.vd) {
+        if (ps.unroll == 4 && per) density_list_kernel<4, K, true, true><<<grid, block, 0, st>>>(a);
+        else if (ps.unroll == 4) density_list_kernel<4, K, false, true><<<grid, block, 0, st>>>(a);
+        else if (per) density_list_kernel<2, K, true, true><<<grid, block, 0, st>>>(a);
+        else density_list_kernel<2, K, false, true><<<grid, block, 0, st>>>(a);
+    } else {
+        if (ps.unroll == 4 && per) density_list_kernel<4, K, true, false><<<grid, block, 0, st>>>(a);
+        else if (ps.unroll == 4) density_list_kernel<4, K, false, false><<<grid, block, 0, st>>>(a);
+        else if (per) density_list_kernel<2, K, true, false><<<grid, block, 0, st>>>(a);
+        else density_list_kernel<2, K, false, false><<<grid, block, 0, st>>>(a);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // default tile: the mean density set (about 58 for M4 at hfact 1.2, 82 for
@@ -774,6 +795,7 @@ cudaError_t density_solve(Ctx &c, const sph_state &s, const sph_params &p, cudaS
     a.pos = (const float4 *)s.pos;
     a.vel = (const float4 *)s.vel;
     a.rec = c.rec;
+    a.vd = c.drhodt_in_force ? 0 : 1;
     a.h = s.h;
     a.rho = s.rho;
     a.omega = s.omega;

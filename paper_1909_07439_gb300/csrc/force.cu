@@ -43,6 +43,7 @@ struct ForceArgs {
     int tb;              // targets per batch of the list kernel (4, 8 or 16)
     float4 *acc;
     float *vsigmax;
+    float *drhodt;  // written too (Eq. 3, the pressure-work sum over m_j F_i), or nullptr
     const int2 *grp_ref;
     const float4 *grp_lo, *grp_hi;
     const int *sizes;
@@ -146,6 +147,8 @@ struct ForceTarget {
             const float du = pres_i * Ai * dup - 0.5f * Ai * duav + 0.5f * a.alpha_u * duc;
             a.acc[i] = make_float4(ax, ay, az, du);
             a.vsigmax[i] = vsmax;
+            // drho/dt = (1 / Omega) sum m_j v_ij.rhat_ij F(r, h_i) = rho A dup
+            if (a.drhodt) a.drhodt[i] = qi.y * Ai * dup;
         }
     }
 };
@@ -230,7 +233,7 @@ struct ForceSums {
 
     // reduce over the L lanes of the target; lane sub == 0 writes
     __device__ __forceinline__ void finish(int L, bool write, int i, float gm1, float alpha_u,
-                                           float4 *acc, float *vsig)
+                                           float4 *acc, float *vsig, float *drhodt)
     {
         for (int o = L >> 1; o > 0; o >>= 1) {
             ax += __shfl_xor_sync(0xffffffffu, ax, o);
@@ -247,6 +250,8 @@ struct ForceSums {
             const float du = AKi * (pri * sp - 2.f * sv) + (0.70710678118654752f * alpha_u / gm1) * sc;
             acc[i] = make_float4(ax, ay, az, du);
             vsig[i] = vsmax;
+            // drho/dt = (1 / Omega) sum m_j v_ij.rhat_ij F(r, h_i) = rho AK sp
+            if (drhodt) drhodt[i] = rhoi * AKi * sp;
         }
     }
 };
@@ -331,7 +336,7 @@ __global__ void __launch_bounds__(256, 3) force_list_kernel(ForceArgs a)
                         entry(b1 ? jj.y : jj.x, b1);
                     }
                 }
-                T.finish(L, on && sub == 0, i, a.gm1, a.alpha_u, a.acc, a.vsigmax);
+                T.finish(L, on && sub == 0, i, a.gm1, a.alpha_u, a.acc, a.vsigmax, a.drhodt);
                 n_pairs += on ? T.cnt : 0;
                 n_cand += on && sub == 0 ? (unsigned long long)len : 0ull;
             }
@@ -638,6 +643,7 @@ cudaError_t force_pass(Ctx &c, const sph_state &s, const sph_params &p, cudaStre
     a.frec = c.frec;
     a.acc = (float4 *)s.acc;
     a.vsigmax = s.vsigmax;
+    a.drhodt = c.drhodt_in_force ? s.drhodt : nullptr;
     a.grp_ref = c.tree.grp_ref;
     a.grp_lo = c.tree.grp_lo;
     a.grp_hi = c.tree.grp_hi;

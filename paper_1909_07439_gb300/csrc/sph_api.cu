@@ -230,6 +230,13 @@ cudaError_t copy_out(Ctx &c, const sph_state &d, const HostOut &o, unsigned fiel
     return e;
 }
 
+// drho/dt from the force pass while in scope (the density and force passes of a step)
+struct DrhodtInForce {
+    Ctx &c;
+    explicit DrhodtInForce(Ctx &cc) : c(cc) { c.drhodt_in_force = true; }
+    ~DrhodtInForce() { c.drhodt_in_force = false; }
+};
+
 // one leapfrog step (kick-drift, tree, density, force, closing kick, Courant dt)
 sph_status enqueue_step(Ctx &c, const sph_state &s, const sph_params &p, float *d_dt,
                         double *d_time, cudaStream_t st, const HostOut *out = nullptr)
@@ -242,10 +249,14 @@ sph_status enqueue_step(Ctx &c, const sph_state &s, const sph_params &p, float *
     if ((r = do_tree(c, s, p, false, st)) != SPH_OK) return r;
     // final from here on: pos (the closing kick changes v only), perm, keys
     if (out) CK(copy_out(c, s, *out, 1u | 1u << 8 | 1u << 9, st, 0), "copy out");
-    if ((r = do_density(c, s, p, st, true)) != SPH_OK) return r;
-    if (out) CK(copy_out(c, s, *out, 1u << 3 | 1u << 4 | 1u << 5 | 1u << 6, st, 1), "copy out");
-    if ((r = do_force(c, s, p, st, true)) != SPH_OK) return r;
-    if (out) CK(copy_out(c, s, *out, 1u << 2 | 1u << 7, st, 2), "copy out");  // acc, vsigmax
+    {
+        DrhodtInForce fused(c);
+        if ((r = do_density(c, s, p, st, true)) != SPH_OK) return r;
+        if (out) CK(copy_out(c, s, *out, 1u << 3 | 1u << 4 | 1u << 5, st, 1), "copy out");
+        if ((r = do_force(c, s, p, st, true)) != SPH_OK) return r;
+    }
+    // acc, drhodt, vsigmax
+    if (out) CK(copy_out(c, s, *out, 1u << 2 | 1u << 6 | 1u << 7, st, 2), "copy out");
     {
         StageScope sc(c, ST_LEAPFROG, st, 1);
         CK(kick_close(c, s, d_dt, d_time, st), "kick_close");
@@ -587,8 +598,11 @@ sph_status sph_step_block(sph_ctx *h, sph_state *s, const sph_params *p, int max
             CK(refit_tree(c, *s, st), "refit");
         }
         c.mask = c.active;
-        r = do_density(c, *s, *p, st, true);
-        if (r == SPH_OK) r = do_force(c, *s, *p, st, true);
+        {
+            DrhodtInForce fused(c);
+            r = do_density(c, *s, *p, st, true);
+            if (r == SPH_OK) r = do_force(c, *s, *p, st, true);
+        }
         c.mask = nullptr;
         if (r != SPH_OK) return r;
         StageScope sc(c, ST_LEAPFROG, st, 1);
@@ -782,9 +796,12 @@ cudaError_t enqueue_batch_step(Ctx &c, const sph_state &s, const sph_params &p, 
 {
     cudaError_t e = kick_drift(c, s, p, d_dt, st, &b);
     if (e == cudaSuccess) e = build_tree(c, s, p, false, st, &b);
-    if (e == cudaSuccess) e = density_pass(c, s, p, st, &b);
-    if (e == cudaSuccess) e = force_prep(c, s, p, st);
-    if (e == cudaSuccess) e = force_pass(c, s, p, st, &b);
+    {
+        DrhodtInForce fused(c);
+        if (e == cudaSuccess) e = density_pass(c, s, p, st, &b);
+        if (e == cudaSuccess) e = force_prep(c, s, p, st);
+        if (e == cudaSuccess) e = force_pass(c, s, p, st, &b);
+    }
     if (e == cudaSuccess && p.grav_G > 0.f) e = gravity_pass(c, s, p, (float4 *)s.acc, nullptr, st, &b);
     if (e == cudaSuccess) e = kick_close(c, s, d_dt, d_time, st, &b);
     if (e == cudaSuccess) e = courant_dt(c, s, p, d_dt, st, &b);

@@ -127,6 +127,10 @@ struct Ctx {
     int *nl_len = nullptr;
     int nl_stride = 128;
     int nl_kernel = -1;
+    // Inside a step the force pass writes drho/dt (its pressure-work sum is
+    // the same sum up to a per-particle factor) and the density pass gathers
+    // positions only; standalone density passes write drho/dt themselves.
+    bool drhodt_in_force = false;
     int2 *fallback = nullptr;  // (group, first batch slot) handed to the walk kernels
 
     // per-particle scratch
