@@ -61,7 +61,7 @@ EXEC_FLOP_FORCE_PAIR = 84.0
 # DRAM bytes (read + write) per launch of the pair kernels from one ncu capture
 # of the 128^3 step; None where the kernel changed after the capture.
 NCU_TRAFFIC = {"nlist_kernel": 135.363328e6 + 602.912256e6,
-               "density_list_kernel": 1.07383e9 + 49.421568e6,
+               "density_list_kernel": 918.412544e6 + 34.043392e6,
                "force_list_kernel": 1.00118e9 + 29.120512e6}
 # Self-gravity FP32 operations per interaction (softened pair: separation 3,
 # r^2 + eps^2 6, the inverse powers 3, m/r and m/r^3 2, acceleration 6,
