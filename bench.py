@@ -63,6 +63,10 @@ EXEC_FLOP_FORCE_PAIR = 84.0
 NCU_TRAFFIC = {"nlist_kernel": 135.363328e6 + 602.912256e6,
                "density_list_kernel": 918.412544e6 + 34.043392e6,
                "force_list_kernel": 1.00118e9 + 29.120512e6}
+# Issue slots busy (smsp__issue_active, fraction of the active cycles) in the
+# same ncu captures: the list build is bound by instruction issue, which its
+# FP32 fraction (8 FLOP per candidate test) does not show.
+NCU_ISSUE_ACTIVE = {"nlist_kernel": 0.768, "density_list_kernel": 0.682, "force_list_kernel": 0.656}
 # Self-gravity FP32 operations per interaction (softened pair: separation 3,
 # r^2 + eps^2 6, the inverse powers 3, m/r and m/r^3 2, acceleration 6,
 # potential 1 = 21; quadrupole cell: the same 20 plus Q d 15, d.Q.d 5, the
@@ -185,14 +189,15 @@ def roofline(stage_ms, stats, reps, fp32_peak, peak_basis, hbm_peak, n, kernel=0
             continue
         ach = flop / reps / (ms / 1e3) / 1e12
         stages[st] = {"kernel": kern, "launch_ms": round(ms, 4), "achieved": round(ach, 3),
-                      "frac": round(ach / fp32_peak, 4)}
+                      "frac": round(ach / fp32_peak, 4), "issue_active_ncu": NCU_ISSUE_ACTIVE.get(kern)}
         if exe is not None:
             stages[st]["achieved_executed"] = round(exe / reps / (ms / 1e3) / 1e12, 3)
     dom = max(stages, key=lambda k: stages[k]["launch_ms"])
     d = stages[dom]
     roof = {"kernel": d["kernel"], "bound": "alu", "achieved": d["achieved"],
             "peak": round(fp32_peak, 2), "unit": "TFLOP/s", "frac": d["frac"],
-            "traffic": NCU_TRAFFIC.get(d["kernel"]), "peak_basis": peak_basis,
+            "traffic": NCU_TRAFFIC.get(d["kernel"]), "issue_active_ncu": NCU_ISSUE_ACTIVE.get(d["kernel"]),
+            "peak_basis": peak_basis,
             "launch_ms": d["launch_ms"], "flop_per_pair": f_force if dom == "force" else None,
             "stages": stages}
     if "achieved_executed" in d:
