@@ -80,6 +80,9 @@ def _compare(s, ref, span, box=None):
     acc = s.in_original_order("acc")
     assert np.max(np.abs(acc[:, :3] - ref.acc)) <= ACC_TOL * np.max(np.abs(ref.acc))
     assert np.max(np.abs(acc[:, 3] - ref.dudt)) <= ACC_TOL * np.max(np.abs(ref.dudt))
+    # drho/dt of each particle's last substep, written by the force pass
+    dr = s.in_original_order("drhodt")
+    assert np.max(np.abs(dr - ref.drhodt)) <= ACC_TOL * np.max(np.abs(ref.drhodt))
 
 
 def test_block_step_sedov(sph):

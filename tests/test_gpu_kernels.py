@@ -189,6 +189,9 @@ def test_step_parity(sph, kernel):
     acc = s.in_original_order("acc")
     assert np.max(np.abs(acc[:, :3] - n1.acc)) <= ACC_TOL * np.max(np.abs(n1.acc))
     assert np.max(np.abs(acc[:, 3] - n1.dudt)) <= ACC_TOL * np.max(np.abs(n1.dudt))
+    # drho/dt of the step, written by its force pass
+    dr = s.in_original_order("drhodt")
+    assert np.max(np.abs(dr - n1.drhodt)) <= ACC_TOL * np.max(np.abs(n1.drhodt))
 
 
 def test_negative_energy_reported_like_the_oracle(sph):

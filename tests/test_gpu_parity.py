@@ -370,6 +370,9 @@ def test_timestep_and_step_parity(sph):
     assert np.max(np.abs(rho / n1.rho - 1)) <= RHO_TOL
     assert np.max(np.abs(acc[:, :3] - n1.acc)) <= ACC_TOL * np.max(np.abs(n1.acc))
     assert np.max(np.abs(acc[:, 3] - n1.dudt)) <= ACC_TOL * np.max(np.abs(n1.dudt))
+    # drho/dt of the step (written by its force pass) at the predicted velocities
+    dr = s.in_original_order("drhodt")
+    assert np.max(np.abs(dr - n1.drhodt)) <= ACC_TOL * np.max(np.abs(n1.drhodt))
     # the step wrote the next Courant dt
     n1.vsigmax = n1.vsigmax
     assert abs(d_dt.item() / oracle.courant_dt(n1) - 1) <= 1e-3

@@ -163,6 +163,9 @@ def test_periodic_step_parity(sph, kernel):
     acc = s.in_original_order("acc")
     assert np.max(np.abs(acc[:, :3] - n1.acc)) <= ACC_TOL * np.max(np.abs(n1.acc))
     assert np.max(np.abs(acc[:, 3] - n1.dudt)) <= ACC_TOL * np.max(np.abs(n1.dudt))
+    # drho/dt of the step, written by its force pass (nearest-image separations)
+    dr = s.in_original_order("drhodt")
+    assert np.max(np.abs(dr - n1.drhodt)) <= ACC_TOL * np.max(np.abs(n1.drhodt))
 
 
 def test_uniform_periodic_lattice(sph):
