@@ -21,6 +21,7 @@
 //              a   = -M d / r^3 + Q d / r^5 - 5 (d.Q.d) d / (2 r^7)
 //   particle:  phi = -m/r,  a = -m d / r^3
 // with d = x_i - X (or x_i - x_j) and r^2 = |d|^2 + eps^2.  FP32 throughout.
+#include "kernels.cuh"
 #include "walk.cuh"
 
 namespace sph {
@@ -30,16 +31,28 @@ constexpr int kGStack = 256;   // node-range stack entries per warp
 constexpr int kGRQ = 64;       // leaf-range queue entries per warp
 constexpr int kGCell = 64;     // cell list entries per warp
 
+// Staged cells and particles are stored in pairs, component by component
+// (element 2k and 2k + 1 of the list side by side), so that a lane evaluates
+// two of them against its target with the packed FP32x2 instructions.
 struct GravSmem {
     int2 stk[kGStack];
     int nodes[32];
     int2 rq[kGRQ];
-    float4 c_com[kGCell];   // X, M
-    float4 c_q0[kGCell];    // Qxx, Qyy, Qzz, unused
-    float4 c_q1[kGCell];    // Qxy, Qxz, Qyz, unused
-    float4 p_pos[32];
-    int p_idx[32];
+    float4 c0[kGCell / 2];  // (X_a, X_b, Y_a, Y_b)
+    float4 c1[kGCell / 2];  // (Z_a, Z_b, M_a, M_b)
+    float4 c2[kGCell / 2];  // (Qxx_a, Qxx_b, Qyy_a, Qyy_b)
+    float4 c3[kGCell / 2];  // (Qzz_a, Qzz_b, Qxy_a, Qxy_b)
+    float4 c4[kGCell / 2];  // (Qxz_a, Qxz_b, Qyz_a, Qyz_b)
+    float4 p0[16];          // (x_a, x_b, y_a, y_b)
+    float4 p1[16];          // (z_a, z_b, m_a, m_b)
+    int pidx[32];           // slot of each staged particle (the target's own is skipped)
 };
+
+// element e of a pair-staged list: component c (0..1 of a float4) of slot e
+__device__ __forceinline__ void put_pair(float4 *arr, int e, int c, float v)
+{
+    reinterpret_cast<float *>(&arr[e >> 1])[2 * c + (e & 1)] = v;
+}
 
 struct GravArgs {
     const float4 *pos;
@@ -153,43 +166,76 @@ __global__ void __launch_bounds__(kGWarps * 32) gravity_kernel(GravArgs a)
         const bool act = t < nt;
         const int i = gr.x + (act ? t : 0);
         const float4 xt = a.pos[i];
-        float ax = 0.f, ay = 0.f, az = 0.f, phi = 0.f;
 
+        // Two staged entries per lane and iteration in FP32x2 (element 0 the
+        // even entry, 1 the odd one), with d' = X - x_i = -d: the potential is
+        // even in d, and
+        //   a = d' (M / r^3 + 5/2 (d'.Q.d') / r^7) - Q d' / r^5.
+        // The sums are combined (and phi negated) at the end.
+        const float2 tx = f2(xt.x), ty = f2(xt.y), tz = f2(xt.z), e2 = f2(a.eps2);
+        float2 ax2 = f2(0.f), ay2 = f2(0.f), az2 = f2(0.f), nphi2 = f2(0.f);  // nphi2: -phi
         auto eval_cells = [&](int nc) {
+            if ((nc & 1) && lane == 0) {  // an odd list gets a massless partner far away
+                put_pair(sm.c0, nc, 0, 1e18f); put_pair(sm.c0, nc, 1, 1e18f);
+                put_pair(sm.c1, nc, 0, 1e18f); put_pair(sm.c1, nc, 1, 0.f);
+                put_pair(sm.c2, nc, 0, 0.f); put_pair(sm.c2, nc, 1, 0.f);
+                put_pair(sm.c3, nc, 0, 0.f); put_pair(sm.c3, nc, 1, 0.f);
+                put_pair(sm.c4, nc, 0, 0.f); put_pair(sm.c4, nc, 1, 0.f);
+            }
             __syncwarp();
-#pragma unroll 4
-            for (int e = sub; e < nc; e += L) {
-                const float4 c = sm.c_com[e], qa = sm.c_q0[e], qb = sm.c_q1[e];
-                const float dx = xt.x - c.x, dy = xt.y - c.y, dz = xt.z - c.z;
-                const float rinv = rsqrtf(dx * dx + dy * dy + dz * dz + a.eps2);
-                const float rinv2 = rinv * rinv, rinv3 = rinv * rinv2, rinv5 = rinv3 * rinv2;
-                const float qx = qa.x * dx + qb.x * dy + qb.y * dz;
-                const float qy = qb.x * dx + qa.y * dy + qb.z * dz;
-                const float qz = qb.y * dx + qb.z * dy + qa.z * dz;
-                const float dqd = dx * qx + dy * qy + dz * qz;
-                const float s = -c.w * rinv3 - 2.5f * dqd * rinv5 * rinv2;
-                ax += s * dx + qx * rinv5;
-                ay += s * dy + qy * rinv5;
-                az += s * dz + qz * rinv5;
-                phi -= c.w * rinv + 0.5f * dqd * rinv5;
+            const int np2 = (nc + 1) >> 1;
+#pragma unroll 2
+            for (int e = sub; e < np2; e += L) {
+                const float4 A = sm.c0[e], B = sm.c1[e], Q0 = sm.c2[e], Q1 = sm.c3[e], Q2 = sm.c4[e];
+                const float2 dx = add2(make_float2(A.x, A.y), mul2(tx, f2(-1.f)));
+                const float2 dy = add2(make_float2(A.z, A.w), mul2(ty, f2(-1.f)));
+                const float2 dz = add2(make_float2(B.x, B.y), mul2(tz, f2(-1.f)));
+                const float2 M = make_float2(B.z, B.w);
+                const float2 qxx = make_float2(Q0.x, Q0.y), qyy = make_float2(Q0.z, Q0.w);
+                const float2 qzz = make_float2(Q1.x, Q1.y), qxy = make_float2(Q1.z, Q1.w);
+                const float2 qxz = make_float2(Q2.x, Q2.y), qyz = make_float2(Q2.z, Q2.w);
+                const float2 r2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, e2)));
+                const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+                const float2 rinv2 = mul2(rinv, rinv), rinv3 = mul2(rinv, rinv2), rinv5 = mul2(rinv3, rinv2);
+                const float2 qx = fma2(qxx, dx, fma2(qxy, dy, mul2(qxz, dz)));
+                const float2 qy = fma2(qxy, dx, fma2(qyy, dy, mul2(qyz, dz)));
+                const float2 qz = fma2(qxz, dx, fma2(qyz, dy, mul2(qzz, dz)));
+                const float2 dqd = fma2(dx, qx, fma2(dy, qy, mul2(dz, qz)));
+                const float2 s = fma2(M, rinv3, mul2(mul2(f2(2.5f), dqd), mul2(rinv5, rinv2)));
+                const float2 nr5 = mul2(rinv5, f2(-1.f));
+                ax2 = fma2(s, dx, fma2(qx, nr5, ax2));
+                ay2 = fma2(s, dy, fma2(qy, nr5, ay2));
+                az2 = fma2(s, dz, fma2(qz, nr5, az2));
+                nphi2 = fma2(M, rinv, fma2(mul2(f2(0.5f), dqd), rinv5, nphi2));
             }
             if (act && sub == 0) n_cell += (unsigned long long)nc;
             __syncwarp();
         };
+        // particles: a = m d' / r^3, phi = -m / r (the target's own slot gets m = 0)
         auto eval_parts = [&](int np) {
+            if ((np & 1) && lane == 0) {
+                put_pair(sm.p0, np, 0, 1e18f); put_pair(sm.p0, np, 1, 1e18f);
+                put_pair(sm.p1, np, 0, 1e18f); put_pair(sm.p1, np, 1, 0.f);
+                sm.pidx[np] = -1;
+            }
             __syncwarp();
-#pragma unroll 4
-            for (int e = sub; e < np; e += L) {
-                const float4 pj = sm.p_pos[e];
-                const bool self = sm.p_idx[e] == i;
-                const float dx = xt.x - pj.x, dy = xt.y - pj.y, dz = xt.z - pj.z;
-                const float rinv = rsqrtf(dx * dx + dy * dy + dz * dz + a.eps2);
-                const float mr = self ? 0.f : pj.w * rinv;
-                const float mr3 = mr * rinv * rinv;
-                ax -= mr3 * dx;
-                ay -= mr3 * dy;
-                az -= mr3 * dz;
-                phi -= mr;
+            const int np2 = (np + 1) >> 1;
+#pragma unroll 2
+            for (int e = sub; e < np2; e += L) {
+                const float4 A = sm.p0[e], B = sm.p1[e];
+                const int2 js = reinterpret_cast<const int2 *>(sm.pidx)[e];
+                const float2 m = make_float2(js.x == i ? 0.f : B.z, js.y == i ? 0.f : B.w);
+                const float2 dx = add2(make_float2(A.x, A.y), mul2(tx, f2(-1.f)));
+                const float2 dy = add2(make_float2(A.z, A.w), mul2(ty, f2(-1.f)));
+                const float2 dz = add2(make_float2(B.x, B.y), mul2(tz, f2(-1.f)));
+                const float2 r2 = fma2(dx, dx, fma2(dy, dy, fma2(dz, dz, e2)));
+                const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+                const float2 mr = mul2(m, rinv);
+                const float2 mr3 = mul2(mr, mul2(rinv, rinv));
+                ax2 = fma2(mr3, dx, ax2);
+                ay2 = fma2(mr3, dy, ay2);
+                az2 = fma2(mr3, dz, az2);
+                nphi2 = add2(nphi2, mr);
             }
             if (act && sub == 0) n_part += (unsigned long long)np;
             __syncwarp();
@@ -247,9 +293,11 @@ __global__ void __launch_bounds__(kGWarps * 32) gravity_kernel(GravArgs a)
                 const unsigned bcell = __ballot_sync(0xffffffffu, cell);
                 if (cell) {
                     const int p = ncell + __popc(bcell & lt);
-                    sm.c_com[p] = c;
-                    sm.c_q0[p] = qa;
-                    sm.c_q1[p] = qb;
+                    put_pair(sm.c0, p, 0, c.x); put_pair(sm.c0, p, 1, c.y);
+                    put_pair(sm.c1, p, 0, c.z); put_pair(sm.c1, p, 1, c.w);
+                    put_pair(sm.c2, p, 0, qa.x); put_pair(sm.c2, p, 1, qa.y);
+                    put_pair(sm.c3, p, 0, qa.z); put_pair(sm.c3, p, 1, qb.x);
+                    put_pair(sm.c4, p, 0, qb.y); put_pair(sm.c4, p, 1, qb.z);
                 }
                 ncell += __popc(bcell);
                 const unsigned bleaf = __ballot_sync(0xffffffffu, leaf);
@@ -285,13 +333,17 @@ __global__ void __launch_bounds__(kGWarps * 32) gravity_kernel(GravArgs a)
                 }
                 __syncwarp();
                 if (lane < filled) {
-                    sm.p_pos[lane] = __ldg(&a.pos[myj]);
-                    sm.p_idx[lane] = myj;
+                    const float4 pj = __ldg(&a.pos[myj]);
+                    put_pair(sm.p0, lane, 0, pj.x); put_pair(sm.p0, lane, 1, pj.y);
+                    put_pair(sm.p1, lane, 0, pj.z);
+                    put_pair(sm.p1, lane, 1, pj.w);
+                    sm.pidx[lane] = myj;
                 }
                 eval_parts(filled);
             }
         }
         if (!ok && lane == 0) raise_error(a.err, SPH_ERR_TILE_OVERFLOW);
+        float ax = ax2.x + ax2.y, ay = ay2.x + ay2.y, az = az2.x + az2.y, phi = -(nphi2.x + nphi2.y);
         for (int o = L >> 1; o > 0; o >>= 1) {
             ax += __shfl_xor_sync(0xffffffffu, ax, o);
             ay += __shfl_xor_sync(0xffffffffu, ay, o);

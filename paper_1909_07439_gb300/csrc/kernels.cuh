@@ -21,6 +21,13 @@
 
 namespace sph {
 
+// Two-lane FP32 arithmetic in the packed FP32x2 instructions (add, multiply,
+// fused multiply-add, each rounded to nearest per element).
+__device__ __forceinline__ float2 f2(float s) { return make_float2(s, s); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
 template <int K>
 struct SphKernel;
 
