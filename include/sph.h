@@ -183,8 +183,9 @@ sph_status sph_step(sph_ctx *ctx, sph_state *s, const sph_params *p, float *d_dt
  * d_dt is a device float [n_inst], d_time a device double [n_inst] (or NULL).
  * The results for an instance equal those of the single-instance calls on
  * that instance alone.
- * sph_batch_evaluate: tree build, density, force and Courant step of every
- * instance (the initial evaluation before stepping).
+ * sph_batch_evaluate: tree build, density, force (with self-gravity when
+ * grav_G > 0, as sph_force) and Courant step of every instance (the initial
+ * evaluation before stepping).
  * sph_batch_step: n_steps leapfrog steps of every instance.  The first call
  * for a given (state, offsets, params, d_dt, d_time) records one step into a
  * CUDA graph (stream capture); every step is a replay of that graph, whose

@@ -828,6 +828,8 @@ sph_status sph_batch_evaluate(sph_ctx *h, sph_state *s, const int64_t *d_offsets
     CK(density_pass(c, *s, *p, st, &b), "batch density");
     CK(force_prep(c, *s, *p, st), "batch force_prep");
     CK(force_pass(c, *s, *p, st, &b), "batch force");
+    // with self-gravity on, acc takes its term as in sph_force and the batched step
+    if (p->grav_G > 0.f) CK(gravity_pass(c, *s, *p, (float4 *)s->acc, nullptr, st, &b), "batch gravity");
     CK(courant_dt(c, *s, *p, d_dt, st, &b), "batch timestep");
     return SPH_OK;
 }

@@ -46,12 +46,16 @@ def _plain_run(native, torch, ctx, w, a, b, nsteps, p):
     return s, dt.item(), t.item(), dts[0]
 
 
+@pytest.mark.parametrize("grav", [False, True])
 @pytest.mark.parametrize("nsteps", [0, 3])
-def test_batch_equals_single_instance_runs(lib, nsteps):
+def test_batch_equals_single_instance_runs(lib, nsteps, grav):
+    # with self-gravity on too: the evaluation and the steps add each
+    # instance's own Barnes-Hut term to acc
     native, torch = lib
     from paper_1909_07439_gb300 import DeviceState
     w, off = _batch()
-    p = native.sph_params_default()
+    p = (native.sph_params_default(grav_G=1.0, grav_eps=0.01, grav_theta=0.5) if grav
+         else native.sph_params_default())
     ctx = native.sph_create(w.n, 0)
     try:
         s = DeviceState.from_arrays(w.pos, w.vel, w.h)
