@@ -440,37 +440,48 @@ def run_batched(args):
     stats = native.sph_get_stats(ctx)
     native.sph_destroy(ctx)
     del s
-    # the same instances one after another through the single-instance path
+    # the same instances one after another through the single-instance path,
+    # with the batch's tuned parameters and with the single-instance step's
+    # (N_group = N_leaf = 16, 16 targets per batch, 4 warps, 2 entries): the
+    # faster of the two is the baseline
     nmax = int(np.max(np.diff(off)))
     ctx = native.sph_create(nmax, 0)
-    p1 = native.sph_params_default(n_group=p.n_group, n_leaf=p.n_leaf)
-    states = []
-    for i in range(k):
-        a, b = int(off[i]), int(off[i + 1])
-        si = DeviceState.from_arrays(w.pos[a:b], w.vel[a:b], w.h[a:b])
-        di = torch.zeros(1, dtype=torch.float32, device="cuda")
-        native.sph_build_tree(ctx, si.c, p1)
-        native.sph_density(ctx, si.c, p1)
-        native.sph_force(ctx, si.c, p1)
-        native.sph_timestep(ctx, si.c, p1, di)
-        native.sph_step(ctx, si.c, p1, di)
-        states.append((si, di))
-    native.sph_sync(ctx)
-    torch.cuda.synchronize()
-    e0.record()
-    for si, di in states:
-        for _ in range(args.batch_steps):
+    seq = {}
+    for name, p1 in (("batch_params", native.sph_params_default(
+                         n_group=p.n_group, n_leaf=p.n_leaf, pair_targets=p.pair_targets,
+                         pair_warps=p.pair_warps, pair_unroll=p.pair_unroll)),
+                     ("plain_params", native.sph_params_default(
+                         n_group=16, n_leaf=16, pair_targets=16, pair_warps=4, pair_unroll=2))):
+        states = []
+        for i in range(k):
+            a, b = int(off[i]), int(off[i + 1])
+            si = DeviceState.from_arrays(w.pos[a:b], w.vel[a:b], w.h[a:b])
+            di = torch.zeros(1, dtype=torch.float32, device="cuda")
+            native.sph_build_tree(ctx, si.c, p1)
+            native.sph_density(ctx, si.c, p1)
+            native.sph_force(ctx, si.c, p1)
+            native.sph_timestep(ctx, si.c, p1, di)
             native.sph_step(ctx, si.c, p1, di)
-    e1.record()
-    torch.cuda.synchronize()
-    native.sph_sync(ctx)
-    t_seq = e0.elapsed_time(e1) / 1e3
+            states.append((si, di))
+        native.sph_sync(ctx)
+        torch.cuda.synchronize()
+        e0.record()
+        for si, di in states:
+            for _ in range(args.batch_steps):
+                native.sph_step(ctx, si.c, p1, di)
+        e1.record()
+        torch.cuda.synchronize()
+        native.sph_sync(ctx)
+        seq[name] = e0.elapsed_time(e1) / 1e3
+        del states
+    t_seq = min(seq.values())
     native.sph_destroy(ctx)
     updates = w.n * args.batch_steps
     return {"workload": f"{k} Sedov blasts, sizes log-uniform in [4096, 262144] (seeded), "
                         f"{w.n} particles", "steps": args.batch_steps,
             "value": updates / t_batch, "unit": UNIT,
             "plain_sequential_value": updates / t_seq, "batched_over_plain": t_seq / t_batch,
+            "plain_sequential_ms": {k2: 1e3 * v / args.batch_steps for k2, v in seq.items()},
             "pair_interactions_per_s": (stats["density_pairs"] + stats["force_pairs"]) / t_batch,
             "autotune": report, "ms_per_step": 1e3 * t_batch / args.batch_steps}
 

@@ -14,7 +14,7 @@ import os
 
 from . import native
 
-CANDIDATES = [(g, l) for g in (4, 8, 16) for l in (8, 16)]
+CANDIDATES = [(g, l) for g in (8, 16, 32) for l in (8, 16, 32)]
 # launch shapes of the pair kernels: (targets per batch, warps per block, entries per iteration)
 SHAPES = [(t, w, u) for t in (4, 8, 16) for w in (2, 4, 8) for u in (2, 4)]
 TUNED = ("n_group", "n_leaf", "pair_targets", "pair_warps", "pair_unroll")
