@@ -627,6 +627,9 @@ def run_tube(args, fp32_peak, basis, hbm_peak):
     for _ in range(30):
         native.sph_step(ctx, s.c, p, d_dt, d_t)
     native.sph_sync(ctx)
+    # tree sizes and launch shape tuned on this state (untimed, state restored)
+    from paper_1909_07439_gb300 import autotune
+    p, tuned = autotune.tune_step(ctx, s, d_dt, f"sod_m6_{k}", base=p, steps=2)
     native.sph_get_stats(ctx)
     native.sph_get_timing(ctx)
     native.sph_set_timing(ctx, True)
@@ -655,7 +658,7 @@ def run_tube(args, fp32_peak, basis, hbm_peak):
             "work_per_step": {kk: v / reps for kk, v in stats.items()
                               if kk in ("density_pairs", "force_pairs", "newton_iters",
                                         "density_rewalks", "force_rewalks", "list_overflows")},
-            "roofline": roof}
+            "autotune": tuned, "roofline": roof}
 
 
 def run_block(args):
