@@ -292,10 +292,12 @@ __global__ void __launch_bounds__(kNlWarps * 32, 7) nlist_kernel(NlistArgs a)
     unsigned n_cand = 0, n_entries = 0, n_over = 0;
 
     while (true) {
-        // kSG groups at a time, kSG / 2 in the last quarter (shorter tail)
+        // kSG groups at a time, kSG / 2 in the last quarter (shorter tail);
+        // with a due mask (block steps) kSG / 2 throughout: the due groups are
+        // few and clustered, and smaller grabs spread them over more warps
         int gf = 0, grab = kSG;
         if (lane == 0) {
-            grab = *(volatile int *)a.work < ng - (ng >> 2) ? kSG : kSG / 2;
+            grab = a.active || *(volatile int *)a.work >= ng - (ng >> 2) ? kSG / 2 : kSG;
             gf = atomicAdd(a.work, grab);
         }
         gf = __shfl_sync(0xffffffffu, gf, 0);
