@@ -227,8 +227,12 @@ __global__ void __launch_bounds__(256, 4) density_list_kernel(DensArgs a)
                     };
                     // neighbour j's position (and velocity with VD)
                     auto load = [&](int j, float4 &pj, float4 &vj) {
-                        if (VD) ld_rec(a.rec, j, keep, pj, vj);
-                        else pj = ld_keep(a.pos, j, keep);
+                        if (VD) {
+                            ld_rec(a.rec, j, keep, pj, vj);
+                        } else {
+                            pj = ld_keep(a.pos, j, keep);
+                            vj = make_float4(0.f, 0.f, 0.f, 0.f);  // not read without VD
+                        }
                     };
                     if (NPER == 4) {
                         int e = 4 * sub;
