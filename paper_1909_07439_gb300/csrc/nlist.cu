@@ -170,7 +170,7 @@ __device__ __forceinline__ int group_candidates(const NlistArgs &a, NlistSmem &s
 // against the batch's targets (TB slots, the unused ones far away: no
 // candidate hits them, and a missing candidate, also far away, hits no
 // target) and append the hits to the targets' lists.
-template <int TB, bool PER>
+template <int TB, bool PER, int CAP>
 __device__ __forceinline__ void test_queued(const NlistArgs &a, const NlistSmem &sm, int cnt, int *tbase,
                                             int (&len)[TB])
 {
@@ -190,11 +190,11 @@ __device__ __forceinline__ void test_queued(const NlistArgs &a, const NlistSmem 
         const bool hit1 = r2.y < fmaxf(sm.tr2[t1], pj.w);
         const unsigned m0 = __ballot_sync(0xffffffffu, hit0);
         const unsigned m1 = __ballot_sync(0xffffffffu, hit1);
-        // past a.cap hits the last entry is overwritten: such a list is
+        // past CAP hits the last entry is overwritten: such a list is
         // discarded (its length is set to -1) anyway.  Stores kept in L2 (the
         // density pass reads the last groups' lists first).
-        if (hit0) __stcg(tbase + t0 * a.cap + min(len[t0] + __popc(m0 & lt), a.cap - 1), j);
-        if (hit1) __stcg(tbase + t1 * a.cap + min(len[t1] + __popc(m1 & lt), a.cap - 1), j);
+        if (hit0) __stcg(tbase + t0 * CAP + min(len[t0] + __popc(m0 & lt), CAP - 1), j);
+        if (hit1) __stcg(tbase + t1 * CAP + min(len[t1] + __popc(m1 & lt), CAP - 1), j);
         len[t0] += __popc(m0);
         len[t1] += __popc(m1);
     }
@@ -212,7 +212,7 @@ __device__ __forceinline__ void test_queued(const NlistArgs &a, const NlistSmem 
 // 32 queued candidates are tested against the batch's targets.  Returns the
 // list length of target `lane` (lane < TB).  PER: nearest images on the
 // periodic axes.
-template <int TB, bool PER>
+template <int TB, bool PER, int CAP>
 __device__ __forceinline__ int test_chunks(const NlistArgs &a, NlistSmem &sm, int ncand, int i0)
 {
     const int lane = threadIdx.x & 31;
@@ -220,7 +220,7 @@ __device__ __forceinline__ int test_chunks(const NlistArgs &a, NlistSmem &sm, in
     int len[TB];
 #pragma unroll
     for (int tt = 0; tt < TB; ++tt) len[tt] = 0;
-    int *const tbase = a.idx + (size_t)i0 * a.cap;  // the batch's first list
+    int *const tbase = a.idx + (size_t)i0 * CAP;  // the batch's first list
     int qn = 0;  // queued candidates
     int r = 0;
     int jn = lane < ncand ? slot_particle(sm.runs, r, lane) : -1;
@@ -253,7 +253,7 @@ __device__ __forceinline__ int test_chunks(const NlistArgs &a, NlistSmem &sm, in
         const bool last = c0 >= ncand;
         if (qn >= 32 || (last && qn > 0)) {
             const int cnt = min(qn, 32);
-            test_queued<TB, PER>(a, sm, cnt, tbase, len);
+            test_queued<TB, PER, CAP>(a, sm, cnt, tbase, len);
             // the rest (fewer than 32) to the front of the queue
             const int rest = qn - cnt;
             float4 pv = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -279,7 +279,9 @@ __device__ __forceinline__ int test_chunks(const NlistArgs &a, NlistSmem &sm, in
     return mine;
 }
 
-template <bool PER>
+// CAP: the lists' stride (list_cap of their kernel), a constant so that the
+// hit stores' addresses need no multiplication
+template <bool PER, int CAP>
 __global__ void __launch_bounds__(kNlWarps * 32, 7) nlist_kernel(NlistArgs a)
 {
     __shared__ NlistSmem smv[kNlWarps];
@@ -402,16 +404,16 @@ __global__ void __launch_bounds__(kNlWarps * 32, 7) nlist_kernel(NlistArgs a)
                     __syncwarp();
                     int mlen = 0;
                     if (ncand > 0) {
-                        if (nt <= 4) mlen = test_chunks<4, PER>(a, sm, ncand, i0);
-                        else if (nt <= 8) mlen = test_chunks<8, PER>(a, sm, ncand, i0);
-                        else mlen = test_chunks<kNlTB, PER>(a, sm, ncand, i0);
+                        if (nt <= 4) mlen = test_chunks<4, PER, CAP>(a, sm, ncand, i0);
+                        else if (nt <= 8) mlen = test_chunks<8, PER, CAP>(a, sm, ncand, i0);
+                        else mlen = test_chunks<kNlTB, PER, CAP>(a, sm, ncand, i0);
                         n_cand += (unsigned)nt * (unsigned)ncand;
                     }
                     // a group without lists is left to the walking kernels
-                    const bool fits = ok && mlen <= a.cap;
+                    const bool fits = ok && mlen <= CAP;
                     if (lane < nt) {
                         a.len[i0 + lane] = fits ? mlen : -1;
-                        n_entries += (unsigned)min(mlen, a.cap);
+                        n_entries += (unsigned)min(mlen, CAP);
                         n_over += fits ? 0u : 1u;
                     }
                     __syncwarp();
@@ -437,15 +439,16 @@ static cudaError_t configure_nlist(int &blocks)
     std::lock_guard<std::mutex> lock(mu);
     static bool configured = false;
     static int nb_cached = 1;
-    if (!configured) {
-        int nb = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, nlist_kernel<true>,
-                                                                      kNlWarps * 32, 0);
-        int nb0 = 0;
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb0, nlist_kernel<false>, kNlWarps * 32, 0);
-        nb = nb0 < nb ? nb0 : nb;
-        if (e != cudaSuccess) return e;
+    if (!configured) {  // the smallest over the variants
+        const void *fns[4] = {(const void *)nlist_kernel<false, 128>, (const void *)nlist_kernel<true, 128>,
+                              (const void *)nlist_kernel<false, 192>, (const void *)nlist_kernel<true, 192>};
+        int nb = 1 << 30;
+        for (const void *f : fns) {
+            int b = 0;
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, f, kNlWarps * 32, 0);
+            if (e != cudaSuccess) return e;
+            nb = b < nb ? b : nb;
+        }
         nb_cached = nb > 0 ? nb : 1;
         configured = true;
     }
@@ -457,6 +460,24 @@ cudaError_t configure_nlist_kernels()
 {
     int b;
     return configure_nlist(b);
+}
+
+// the variant for the lists' stride and the periodicity
+static cudaError_t launch_nlist(Ctx &c, const NlistArgs &a, int blocks, cudaStream_t st)
+{
+    static_assert(kNbrCapMax == 192, "list strides are 128 and 192");
+    const dim3 grid(c.num_sms * blocks), block(kNlWarps * 32);
+    const bool per = a.tree.per.any();
+    if (a.cap == 128) {
+        if (per) nlist_kernel<true, 128><<<grid, block, 0, st>>>(a);
+        else nlist_kernel<false, 128><<<grid, block, 0, st>>>(a);
+    } else if (a.cap == 192) {
+        if (per) nlist_kernel<true, 192><<<grid, block, 0, st>>>(a);
+        else nlist_kernel<false, 192><<<grid, block, 0, st>>>(a);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 static NlistArgs nlist_args(Ctx &c, const sph_state &s, const sph_params &p, float pad,
@@ -492,9 +513,7 @@ cudaError_t nlist_pass(Ctx &c, const sph_state &s, const sph_params &p, float pa
     NlistArgs a = nlist_args(c, s, p, pad, batch);
     e = cudaMemsetAsync(a.work, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    if (a.tree.per.any()) nlist_kernel<true><<<c.num_sms * blocks, kNlWarps * 32, 0, st>>>(a);
-    else nlist_kernel<false><<<c.num_sms * blocks, kNlWarps * 32, 0, st>>>(a);
-    return cudaGetLastError();
+    return launch_nlist(c, a, blocks, st);
 }
 
 cudaError_t check_list_kernel(Ctx &c, const sph_params &p, cudaStream_t st)
@@ -518,9 +537,7 @@ cudaError_t relist_pass(Ctx &c, const sph_state &s, const sph_params &p, float p
     a.only_bad = c.tree.rec_bad;
     e = cudaMemsetAsync(a.work, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;
-    if (a.tree.per.any()) nlist_kernel<true><<<c.num_sms * blocks, kNlWarps * 32, 0, st>>>(a);
-    else nlist_kernel<false><<<c.num_sms * blocks, kNlWarps * 32, 0, st>>>(a);
-    e = cudaGetLastError();
+    e = launch_nlist(c, a, blocks, st);
     if (e != cudaSuccess) return e;
     // the rebuilt lists cover the pair sets at the final h
     e = cudaMemsetAsync(c.tree.rec_bad, 0, sizeof(int) * (batch ? batch->n_inst : 1), st);
