@@ -90,11 +90,12 @@ struct NlistArgs {
 
 // Walk for the box [blo, bhi] (h_max blo.w) and put the leaves, in particle
 // order, in sm.leaves.  Returns their number, or -1 if more than kSGLeaves.
+template <bool PER>
 __device__ __forceinline__ int walk_sorted(const NlistArgs &a, NlistSmem &sm, int root, float4 blo,
                                            float4 bhi)
 {
     const int lane = threadIdx.x & 31;
-    const int n = walk_leaves_wide(a.tree, root, blo, bhi, 0.5f * (a.rscale * blo.w), 0.5f * a.rscale,
+    const int n = walk_leaves_wide<kLWWide, kLWStack, PER>(a.tree, root, blo, bhi, 0.5f * (a.rscale * blo.w), 0.5f * a.rscale,
                                    sm.u.wp.w, sm.u.wp.lv, kSGLeaves);
     __syncwarp();
     // rank sort by first particle (leaves hold disjoint particle ranges)
@@ -117,6 +118,7 @@ __device__ __forceinline__ int walk_sorted(const NlistArgs &a, NlistSmem &sm, in
 // box passes it for any box containing it, so when sm.leaves comes from a
 // walk shared with other groups (union box, largest h) the result is the same
 // as for the group's own walk.  Returns nrun, or -1 if more than max_runs.
+template <bool PER>
 __device__ __forceinline__ int group_candidates(const NlistArgs &a, NlistSmem &sm, int nleaf,
                                                 float4 glo, float4 ghi, int max_runs)
 {
@@ -133,7 +135,7 @@ __device__ __forceinline__ int group_candidates(const NlistArgs &a, NlistSmem &s
             const float4 lo = __ldg(&a.tree.node_lo[node]);
             const float4 hi = __ldg(&a.tree.node_hi[node]);
             ref = __ldg(&a.tree.node_ref[node]);
-            const float d2 = box_dist2_t(a.tree, glo, ghi, lo, hi);
+            const float d2 = box_dist2_c<PER>(a.tree, glo, ghi, lo, hi);
             const float R = 2.0f * fmaxf(hgroup, lo.w * node_scale);
             open = d2 < R * R * kOpenSlack;
         }
@@ -239,7 +241,7 @@ __device__ __forceinline__ int test_chunks(const NlistArgs &a, NlistSmem &sm, in
                 hn = jn >= 0 ? __ldg(&a.h[jn]) : 0.f;
             }
             const float4 blo = sm.blo, bhi = sm.bhi;
-            const bool keep = j >= 0 && box_dist2_t(a.tree, blo, bhi, pj, pj) < fmaxf(bhi.w, rj2) * kOpenSlack;
+            const bool keep = j >= 0 && box_dist2_c<PER>(a.tree, blo, bhi, pj, pj) < fmaxf(bhi.w, rj2) * kOpenSlack;
             const unsigned m = __ballot_sync(0xffffffffu, keep);
             if (keep) {
                 const int slot = qn + __popc(m & lt);
@@ -356,7 +358,7 @@ __global__ void __launch_bounds__(kNlWarps * 32, 7) nlist_kernel(NlistArgs a)
                     uhi.y = fmaxf(uhi.y, __shfl_xor_sync(0xffffffffu, uhi.y, o));
                     uhi.z = fmaxf(uhi.z, __shfl_xor_sync(0xffffffffu, uhi.z, o));
                 }
-                nshared = walk_sorted(a, sm, root, ulo, uhi);
+                nshared = walk_sorted<PER>(a, sm, root, ulo, uhi);
                 if (nshared >= 0 || e - s == 1) break;
                 e = s + (e - s + 1) / 2;
             }
@@ -367,7 +369,7 @@ __global__ void __launch_bounds__(kNlWarps * 32, 7) nlist_kernel(NlistArgs a)
                     continue;  // no target of the group is due: its lists are not read
                 const float4 glo = a.grp_lo[g], ghi = a.grp_hi[g];
                 const int nleaf = nshared;
-                const int nrun = nleaf >= 0 ? group_candidates(a, sm, nleaf, glo, ghi, kMaxRuns) : -1;
+                const int nrun = nleaf >= 0 ? group_candidates<PER>(a, sm, nleaf, glo, ghi, kMaxRuns) : -1;
                 const bool ok = nrun >= 0;
                 const int ncand = ok ? sm.runs[nrun].y : 0;
                 for (int b0 = 0; b0 < gr.y; b0 += kNlTB) {

@@ -165,6 +165,14 @@ __device__ __forceinline__ float box_dist2_t(const WalkTree &T, float4 alo, floa
     return dx * dx + dy * dy + dz * dz;
 }
 
+// box_dist2_t with the periodicity known at compile time: PER = false takes
+// the open-box distance without the run-time check (the same value then)
+template <bool PER>
+__device__ __forceinline__ float box_dist2_c(const WalkTree &T, float4 alo, float4 ahi, float4 blo, float4 bhi)
+{
+    return PER ? box_dist2_t(T, alo, ahi, blo, bhi) : box_dist2(alo, ahi, blo, bhi);
+}
+
 // One step of a walk: pop whole stack entries from the top (at most 32
 // nodes), test the nodes one per lane, and push the child ranges of opened
 // internal nodes.  On return this lane's opened leaf, if any, is in
@@ -322,7 +330,7 @@ struct WalkSmemW {
 // node loads of a step are independent, so a step costs about one memory
 // latency whatever W is).  Same opening test and result set as walk_leaves;
 // the order of `out` differs.
-template <int W, int STK>
+template <int W, int STK, bool PER = true>
 __device__ __forceinline__ int walk_leaves_wide(const WalkTree &T, int root, float4 glo, float4 ghi,
                                                 float hgroup, float node_scale, WalkSmemW<W, STK> &sm,
                                                 int2 *out, int cap)
@@ -368,7 +376,7 @@ __device__ __forceinline__ int walk_leaves_wide(const WalkTree &T, int root, flo
         for (int w = 0; w < W; ++w) {
             bool open = false;
             if (node[w] >= 0) {
-                const float d2 = box_dist2_t(T, glo, ghi, lo[w], hi[w]);
+                const float d2 = box_dist2_c<PER>(T, glo, ghi, lo[w], hi[w]);
                 const float R = 2.0f * fmaxf(hgroup, lo[w].w * node_scale);
                 open = d2 < R * R * kOpenSlack;
             }
