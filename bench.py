@@ -60,13 +60,13 @@ FLOP_PAIR = {0: (FLOP_FORCE_PAIR, FLOP_DENSITY_PAIR), 1: (106, 75), 2: (104, 66)
 EXEC_FLOP_FORCE_PAIR = 84.0
 # DRAM bytes (read + write) per launch of the pair kernels from one ncu capture
 # of the 128^3 step; None where the kernel changed after the capture.
-NCU_TRAFFIC = {"nlist_kernel": 135.363328e6 + 602.912256e6,
+NCU_TRAFFIC = {"nlist_kernel": 135.070208e6 + 602.764288e6,
                "density_list_kernel": 918.412544e6 + 34.043392e6,
                "force_list_kernel": 1.00118e9 + 29.120512e6}
 # Issue slots busy (smsp__issue_active, fraction of the active cycles) in the
 # same ncu captures: the list build is bound by instruction issue, which its
 # FP32 fraction (8 FLOP per candidate test) does not show.
-NCU_ISSUE_ACTIVE = {"nlist_kernel": 0.768, "density_list_kernel": 0.682, "force_list_kernel": 0.656}
+NCU_ISSUE_ACTIVE = {"nlist_kernel": 0.756, "density_list_kernel": 0.682, "force_list_kernel": 0.656}
 # Self-gravity FP32 operations per interaction (softened pair: separation 3,
 # r^2 + eps^2 6, the inverse powers 3, m/r and m/r^3 2, acceleration 6,
 # potential 1 = 21; quadrupole cell: the same 20 plus Q d 15, d.Q.d 5, the
