@@ -307,9 +307,12 @@ cudaError_t step(Ctx &c, sph_state &w, const sph_params &p, const float *dt, boo
 {
     RT(kick_drift(c, w, p, dt, st));
     RT(build_tree(c, w, p, false, st));
-    RT(density_pass(c, w, p, st));
-    RT(force_prep(c, w, p, st));
-    RT(force_pass(c, w, p, st));
+    {
+        DrhodtInForce fused(c);  // as in sph_step: drho/dt from the force pass
+        RT(density_pass(c, w, p, st));
+        RT(force_prep(c, w, p, st));
+        RT(force_pass(c, w, p, st));
+    }
     if (partial) return cudaSuccess;
     RT(kick_close(c, w, dt, nullptr, st));
     return courant_dt(c, w, p, d_dt_next, st);

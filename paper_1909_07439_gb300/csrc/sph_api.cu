@@ -230,13 +230,6 @@ cudaError_t copy_out(Ctx &c, const sph_state &d, const HostOut &o, unsigned fiel
     return e;
 }
 
-// drho/dt from the force pass while in scope (the density and force passes of a step)
-struct DrhodtInForce {
-    Ctx &c;
-    explicit DrhodtInForce(Ctx &cc) : c(cc) { c.drhodt_in_force = true; }
-    ~DrhodtInForce() { c.drhodt_in_force = false; }
-};
-
 // one leapfrog step (kick-drift, tree, density, force, closing kick, Courant dt)
 sph_status enqueue_step(Ctx &c, const sph_state &s, const sph_params &p, float *d_dt,
                         double *d_time, cudaStream_t st, const HostOut *out = nullptr)

@@ -321,6 +321,13 @@ inline PairShape pair_shape(const sph_params &p)
                      p.pair_unroll ? p.pair_unroll : 2};
 }
 
+// drho/dt from the force pass while in scope (the density and force passes of a step)
+struct DrhodtInForce {
+    Ctx &c;
+    explicit DrhodtInForce(Ctx &cc) : c(cc) { c.drhodt_in_force = true; }
+    ~DrhodtInForce() { c.drhodt_in_force = false; }
+};
+
 // lanes per target for a batch of nt targets (a power of two, nt * L <= 32)
 __host__ __device__ inline int lanes_per_target(int nt)
 {
