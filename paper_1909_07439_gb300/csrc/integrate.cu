@@ -190,8 +190,8 @@ __global__ void conserved_final_kernel(const double *part, int nb, double *out8)
 // also u); every particle drifts with its half-step velocity (wrapped into a
 // periodic box) and its velocity and u are predicted to the substep's end,
 // v = v_half + a ((j mod 2^L + 1) dt_min - dt/2); the particles whose step ends
-// there ((j + 1) mod 2^L = 0) are flagged for the density and force passes;
-// the packed records take the new position and velocity.
+// there ((j + 1) mod 2^L = 0) are flagged for the density and force passes.
+
 // a particle's level, checked: outside [0, max_level] it counts as 0 (and
 // the substep kernel reports SPH_ERR_INVALID_ARG)
 __device__ __forceinline__ int block_level(const int *level, const uint32_t *perm, int i, int max_level,
@@ -204,7 +204,7 @@ __device__ __forceinline__ int block_level(const int *level, const uint32_t *per
 
 __global__ void block_substep_kernel(float4 *__restrict__ pos, float4 *__restrict__ vel,
                                      const float4 *__restrict__ acc, float4 *__restrict__ vhalf,
-                                     float4 *__restrict__ rec, uint8_t *__restrict__ due,
+                                     uint8_t *__restrict__ due,
                                      const uint32_t *__restrict__ perm, const int *__restrict__ level,
                                      int n, int j, int max_level, const float *d_dt_min, Period per,
                                      float3 plo, int *err)
@@ -242,8 +242,6 @@ __global__ void block_substep_kernel(float4 *__restrict__ pos, float4 *__restric
         const float4 w = make_float4(vh.x + into * a.x, vh.y + into * a.y, vh.z + into * a.z, vh.w + into * a.w);
         pos[i] = q;
         vel[i] = w;
-        rec[2 * (size_t)i] = q;
-        rec[2 * (size_t)i + 1] = w;
         due[i] = ((j + 1) & mask) == 0 ? 1 : 0;
     }
     if (__any_sync(0xffffffffu, any_bad) && (threadIdx.x & 31) == 0) raise_error(err, SPH_ERR_INVALID_ARG);
@@ -294,7 +292,7 @@ cudaError_t block_substep(Ctx &c, const sph_state &s, const sph_params &p, const
 {
     const int n = (int)s.n;
     block_substep_kernel<<<grid_n(c, n, 256), 256, 0, st>>>(
-        (float4 *)s.pos, (float4 *)s.vel, (const float4 *)s.acc, c.vhalf, c.rec, c.active, s.perm,
+        (float4 *)s.pos, (float4 *)s.vel, (const float4 *)s.acc, c.vhalf, c.active, s.perm,
         d_level, n, j, max_level, d_dt_min, period_of(p), box_lo_of(p), c.d_err);
     return cudaGetLastError();
 }

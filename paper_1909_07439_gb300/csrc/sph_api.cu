@@ -156,7 +156,8 @@ constexpr int kTreeLaunches = 33;
 constexpr int kPrepLaunches = 1;
 
 // tree_fresh: the tree was just built from this state (node and group h_max
-// hold the current h, and the packed particle records the current pos, vel)
+// hold the current h); inside a step (c.drhodt_in_force) the density pass
+// reads positions only, so the packed records need not be current
 sph_status do_density(Ctx &c, const sph_state &s, const sph_params &p, cudaStream_t st,
                       bool tree_fresh)
 {

@@ -435,7 +435,7 @@ struct GatherArgs {
     float *a1[5];
     float *t1[5];
     uint32_t *perm, *tperm;
-    float4 *rec;  // a4[0], a4[1] (pos, vel) side by side
+    float4 *rec;  // a4[0], a4[1] (pos, vel) side by side, or nullptr
     const uint64_t *keys_sorted;  // if not null: copied to keys_out
     uint64_t *keys_out;
     int n4, n1;
@@ -450,7 +450,7 @@ __global__ void gather_kernel(GatherArgs g, int n)
             if (a < g.n4) {
                 const float4 v = g.a4[a][o];
                 g.t4[a][k] = v;
-                if (a < 2) g.rec[2 * (size_t)k + a] = v;
+                if (a < 2 && g.rec) g.rec[2 * (size_t)k + a] = v;
             }
         }
 #pragma unroll
@@ -935,7 +935,9 @@ cudaError_t build_tree(Ctx &c, const sph_state &s, const sph_params &p, bool ful
     // 4. permute the state into curve order
     GatherArgs g{};
     g.order = vin;
-    g.rec = c.rec;
+    // the packed (pos, vel) records serve the standalone density pass after a
+    // full build; the density pass of a step gathers positions alone
+    g.rec = kicked ? nullptr : c.rec;
     if (kin != s.keys) {
         g.keys_sorted = kin;
         g.keys_out = s.keys;
