@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(128) pairwalk_kernel(PairWalkArgs a, Op op)
         for (int b0 = 0; b0 < gr.y; b0 += kPW_TB) {
             const int nt = min(kPW_TB, gr.y - b0);
             const int L = nt > 4 ? 4 : nt > 2 ? 8 : nt > 1 ? 16 : 32;
-            const int t = lane / L, sub = lane % L;
+            const int t = lane >> (__ffs(L) - 1), sub = lane & (L - 1);  // L a power of two
             const bool act = t < nt;
             const int i0 = gr.x + b0;
             const int i = i0 + (act ? t : 0);

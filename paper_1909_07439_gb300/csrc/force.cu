@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(256, 3) force_list_kernel(ForceArgs a)
             for (int b0 = 0; b0 < gr.y; b0 += a.tb) {
                 const int nt = min(a.tb, gr.y - b0);
                 const int L = lanes_per_target(nt);
-                const int t = lane / L, sub = lane % L;
+                const int t = lane >> (__ffs(L) - 1), sub = lane & (L - 1);  // L a power of two
                 const bool act = t < nt;
                 const int i = gr.x + b0 + (act ? t : 0);
                 const bool on = act && (!a.active || a.active[i]);
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(kForceWarps * 32) force_walk_kernel(ForceArgs 
         {
             const int nt = min(cnt, gr.y - b0);
             const int L = lanes_per_target(nt);
-            const int t = lane / L, sub = lane % L;
+            const int t = lane >> (__ffs(L) - 1), sub = lane & (L - 1);  // L a power of two
             const bool act = t < nt;
             const int i0 = gr.x + b0;
             if (lane < kFTB) {

@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(kGWarps * 32) gravity_kernel(GravArgs a)
         const float4 glo = a.grp_lo[g], ghi = a.grp_hi[g];
         const int nt = min(gr.y, 32);
         const int L = nt > 16 ? 1 : nt > 8 ? 2 : nt > 4 ? 4 : nt > 2 ? 8 : nt > 1 ? 16 : 32;
-        const int t = lane / L, sub = lane % L;
+        const int t = lane >> (__ffs(L) - 1), sub = lane & (L - 1);  // L a power of two
         const bool act = t < nt;
         const int i = gr.x + (act ? t : 0);
         const float4 xt = a.pos[i];
