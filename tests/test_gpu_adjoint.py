@@ -16,6 +16,16 @@ from oracle import adjoint_ref as R  # noqa: E402
 T = torch.float64
 HFACT = {R.M4: 1.2, R.M6: 0.9, R.WC6: 1.3}
 KERNELS = [R.M4, R.M6, R.WC6]
+KNAME = {R.M4: "M4", R.M6: "M6", R.WC6: "Wendland C6"}
+_rec = {}
+
+
+@pytest.fixture(autouse=True)
+def _bind_parity(parity, request):
+    # the error recorder and the test's kernel, for _check
+    cs = getattr(request.node, "callspec", None)
+    _rec["parity"] = parity
+    _rec["kernel"] = KNAME[cs.params.get("kernel", R.M4)] if cs else "M4"
 
 
 @pytest.fixture(scope="module")
@@ -47,8 +57,9 @@ def _elem(a, b):
 def _check(name, got, ref, tol=1e-3, elem_tol=1e-3):
     e_norm, e_elem = _rel(got, ref), _elem(got, ref)
     print(f"{name}: rel L2 {e_norm:.2e}, max elem {e_elem:.2e}")
-    assert e_norm < tol, name
-    assert e_elem < elem_tol, name
+    par, k = _rec["parity"], _rec["kernel"]
+    assert par(f"adjoint {name} ({k}): |d|_2 / |ref|_2", e_norm, tol), name
+    assert par(f"adjoint {name} ({k}): max |d| / max |ref|", e_elem, elem_tol), name
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
@@ -101,7 +112,8 @@ def test_force_bwd_matches_autograd(lib, kernel):
     _check("dL/dh", orig(gh), th.grad.numpy())
     _check("dL/drho", orig(grho), tr.grad.numpy())
     _check("dL/dOmega", orig(gom), to.grad.numpy())
-    assert abs(gal.item() - float(ta.grad)) <= 1e-3 * abs(float(ta.grad))
+    assert _rec["parity"](f"adjoint force dL/dalpha ({_rec['kernel']}): relative",
+                          abs(gal.item() - float(ta.grad)) / abs(float(ta.grad)), 1e-3)
 
 
 @pytest.mark.parametrize("kernel", KERNELS)
@@ -159,10 +171,11 @@ def test_rollout_gradient_matches_fp64_reference(lib, kernel):
     Lr, dts, _ = R.rollout(x, v, u, m, torch.tensor(w.h, dtype=T), al, 20, torch.tensor(probes),
                            hfact=HFACT[kernel], kernel=kernel)
     Lr.backward()
-    assert abs(loss / float(Lr) - 1) < 1e-4
+    par, k = _rec["parity"], _rec["kernel"]
+    assert par(f"adjoint rollout loss ({k}): |L/L_ref - 1|", abs(loss / float(Lr) - 1), 1e-4)
     _check("rollout dL/dv0", g[:, :3], v.grad.numpy())
     _check("rollout dL/du0", g[:, 3], u.grad.numpy())
-    assert abs(galpha / float(al.grad) - 1) < 1e-3
+    assert par(f"adjoint rollout dL/dalpha ({k}): relative", abs(galpha / float(al.grad) - 1), 1e-3)
 
 
 def test_autograd_function_and_no_grad_path(lib):

@@ -83,7 +83,7 @@ def test_batch_equals_single_instance_runs(lib, nsteps, grav):
         native.sph_destroy(ctx)
 
 
-def test_batch_instance_against_oracle(lib):
+def test_batch_instance_against_oracle(lib, parity):
     native, torch = lib
     from paper_1909_07439_gb300 import DeviceState
     w, off = _batch(n_inst=4, seed=5)
@@ -107,9 +107,12 @@ def test_batch_instance_against_oracle(lib):
         order = np.argsort(perm[sel])
         rho = s.numpy("rho")[sel][order]
         acc = s.numpy("acc")[sel][order]
-        assert np.max(np.abs(rho / d.rho - 1)) <= 1e-5
-        assert np.max(np.abs(acc[:, :3] - f.acc)) <= 1e-4 * np.max(np.abs(f.acc))
-        assert np.max(np.abs(acc[:, 3] - f.dudt)) <= 1e-4 * np.max(np.abs(f.dudt))
+        lab = f"batch of 4 instances, instance 2 ({b - a} particles)"
+        assert parity(f"density {lab}: max |rho/rho_o - 1|", np.max(np.abs(rho / d.rho - 1)), 1e-5)
+        assert parity(f"force {lab}: max |da| / max |a|",
+                      np.max(np.abs(acc[:, :3] - f.acc)) / np.max(np.abs(f.acc)), 1e-4)
+        assert parity(f"force {lab}: max |d du/dt| / max |du/dt|",
+                      np.max(np.abs(acc[:, 3] - f.dudt)) / np.max(np.abs(f.dudt)), 1e-4)
     finally:
         native.sph_destroy(ctx)
 

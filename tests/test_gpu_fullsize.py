@@ -51,13 +51,14 @@ def _samples(w, k=48, seed=99):
                                      rng.choice(w.n, k - 16, replace=False)]))
 
 
-def test_fullsize_keys_sort_tree_exact(sedov):
+def test_fullsize_keys_sort_tree_exact(sedov, parity):
     w, s, p, ctx, native, torch = sedov
     keys = oracle.morton_keys(w.pos)
     order = oracle.sort_order(keys)
-    assert np.array_equal(s.numpy("perm").astype(np.int64), order)
     sk = keys[order]
-    assert np.array_equal(s.numpy("keys").view(np.uint64), sk)
+    assert parity("keys/sort Sedov 128^3: mismatching keys and perm entries",
+                  np.sum(s.numpy("perm").astype(np.int64) != order)
+                  + np.sum(s.numpy("keys").view(np.uint64) != sk), 0)
     nodes, groups = native.sph_get_tree(ctx)
     ch = oracle.chop(sk, p.n_leaf)
     for f, ref in (("level", ch.level), ("first", ch.first), ("count", ch.count),
@@ -70,7 +71,7 @@ def test_fullsize_keys_sort_tree_exact(sedov):
     assert np.array_equal(groups["count"], cg.count[term][o])
 
 
-def test_fullsize_density_sampled(sedov):
+def test_fullsize_density_sampled(sedov, parity):
     w, s, p, ctx, native, torch = sedov
     x, v, m, u = _f64(w)
     t = _samples(w)
@@ -78,11 +79,13 @@ def test_fullsize_density_sampled(sedov):
     assert d.failures == 0
     rho = s.in_original_order("rho")[t]
     h = s.in_original_order("h")[t]
-    assert np.max(np.abs(rho / d.rho - 1)) <= 1e-5
-    assert np.max(np.abs(h / d.h - 1)) <= 1e-5 / 3
+    assert parity("density Sedov 128^3 initial (48 sampled): max |rho/rho_o - 1|",
+                  np.max(np.abs(rho / d.rho - 1)), 1e-5)
+    assert parity("density Sedov 128^3 initial (48 sampled): max |h/h_o - 1|",
+                  np.max(np.abs(h / d.h - 1)), 1e-5 / 3)
 
 
-def test_fullsize_force_sampled(sedov):
+def test_fullsize_force_sampled(sedov, parity):
     w, s, p, ctx, native, torch = sedov
     x, v, m, u = _f64(w)
     t = _samples(w, k=24, seed=5)
@@ -103,8 +106,10 @@ def test_fullsize_force_sampled(sedov):
         ref_du.append(f.dudt[0]); got_du.append(acc[i, 3])
     ref_a, got_a = np.array(ref_a), np.array(got_a)
     ref_du, got_du = np.array(ref_du), np.array(got_du)
-    assert np.max(np.abs(got_a - ref_a)) <= 1e-4 * np.max(np.abs(ref_a))
-    assert np.max(np.abs(got_du - ref_du)) <= 1e-4 * np.max(np.abs(ref_du))
+    assert parity("force Sedov 128^3 initial (24 sampled): max |da| / max |a|",
+                  np.max(np.abs(got_a - ref_a)) / np.max(np.abs(ref_a)), 1e-4)
+    assert parity("force Sedov 128^3 initial (24 sampled): max |d du/dt| / max |du/dt|",
+                  np.max(np.abs(got_du - ref_du)) / np.max(np.abs(ref_du)), 1e-4)
 
 
 def test_fullsize_invariants(sedov):
@@ -122,7 +127,7 @@ def test_fullsize_invariants(sedov):
     assert abs(de.sum()) <= 2e-6 * np.sum(np.abs(m * acc[:, 3]))
 
 
-def test_sedov_100_steps(sedov):
+def test_sedov_100_steps(sedov, parity):
     w, s0, p, ctx, native, torch = sedov
     from paper_1909_07439_gb300 import DeviceState
     s = DeviceState.from_arrays(w.pos, w.vel, w.h)
@@ -149,8 +154,8 @@ def test_sedov_100_steps(sedov):
     # measured on GB300: R_peak / R_sedov = 0.987 (the profile's bins are
     # R / 40 wide), dE/E = 1.56e-3 after 100 steps at C_cour = 0.3 (the paper
     # finds the Sedov energy error erratic at this Courant number)
-    assert abs(rs / R - 1) < 0.05
-    assert abs(E1 - E0) / E0 < 3e-3
+    assert parity("Sedov 128^3, 100 steps: |R_shock / R_similarity - 1|", abs(rs / R - 1), 0.05)
+    assert parity("Sedov 128^3, 100 steps: |dE/E|", abs(E1 - E0) / E0, 3e-3)
     # the shell is compressed: peak density well above the ambient rho0 = 1
     assert prof.max() > 1.5
 
@@ -197,7 +202,7 @@ def test_midblast_step_uses_lists_only(sedov_mid):
     assert st["density_pairs"] > 0 and st["force_pairs"] > 0
 
 
-def test_midblast_density_and_force_parity(sedov_mid):
+def test_midblast_density_and_force_parity(sedov_mid, parity):
     # the step's own h and rho (Eqs. 1-4 at the step's positions), then
     # sph_force on the step's lists (current v, u): element by element
     # against the oracle on sampled targets
@@ -210,8 +215,10 @@ def test_midblast_density_and_force_parity(sedov_mid):
     assert len(t) >= 48
     d = oracle.density(x, v, m, hg, targets=t)
     assert d.failures == 0
-    assert np.max(np.abs(rg[t] / d.rho - 1)) <= 1e-5
-    assert np.max(np.abs(hg[t] / d.h - 1)) <= 1e-5 / 3
+    assert parity("density Sedov 128^3 mid-blast step (sampled): max |rho/rho_o - 1|",
+                  np.max(np.abs(rg[t] / d.rho - 1)), 1e-5)
+    assert parity("density Sedov 128^3 mid-blast step (sampled): max |h/h_o - 1|",
+                  np.max(np.abs(hg[t] / d.h - 1)), 1e-5 / 3)
     native.sph_get_stats(ctx)
     native.sph_force(ctx, s.c, p)
     native.sph_sync(ctx)
@@ -240,16 +247,18 @@ def test_midblast_density_and_force_parity(sedov_mid):
     err_d = np.max(np.abs(gd - rd)) / np.max(np.abs(rd))
     print(f"mid-blast: {len(t)} targets, max|da|/max|a| = {err_a:.2e}, "
           f"max|ddu|/max|du| = {err_d:.2e}")
-    assert err_a <= 1e-4 and err_d <= 1e-4
+    assert parity("force Sedov 128^3 mid-blast lists (sampled): max |da| / max |a|", err_a, 1e-4)
+    assert parity("force Sedov 128^3 mid-blast lists (sampled): max |d du/dt| / max |du/dt|", err_d, 1e-4)
 
 
-def test_midblast_lists_bit_exact_sampled(sedov_mid):
+def test_midblast_lists_bit_exact_sampled(sedov_mid, parity):
     # the production lists at the mid-blast state, filtered by the exact
     # test, against the oracle's brute-force sets for sampled targets
     w, s, p, ctx, native, torch, _ = sedov_mid
     pos, hg = s.numpy("pos"), s.numpy("h")
     t = _mid_samples(pos[:, :3].astype(np.float64), s.numpy("rho"), s.n, seed=11)
     for mode in (0, 1):
+        bad = 0
         off = torch.zeros(s.n + 1, dtype=torch.int64, device="cuda")
         total = native.sph_neighbours(ctx, s.c, p, 2 + mode, off)
         idx = torch.zeros(total, dtype=torch.int32, device="cuda")
@@ -258,4 +267,6 @@ def test_midblast_lists_bit_exact_sampled(sedov_mid):
         oo, oi = oracle.neighbours(pos, hg, mode, targets=t)
         for q, i in enumerate(t):
             got = np.sort(idx[off[i]:off[i + 1]])
-            assert np.array_equal(got, oi[oo[q]:oo[q + 1]]), (mode, i)
+            bad += not np.array_equal(got, oi[oo[q]:oo[q + 1]])
+        assert parity(f"neighbour lists Sedov 128^3 mid-blast (sampled) mode {mode}: "
+                      "targets with a different set", bad, 0)

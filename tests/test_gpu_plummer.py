@@ -41,7 +41,7 @@ def mid():
     native.sph_destroy(ctx)
 
 
-def test_plummer_density_and_force_sampled(mid):
+def test_plummer_density_and_force_sampled(mid, parity):
     w, s, p, ctx, native = mid
     x = w.pos[:, :3].astype(np.float64)
     v = w.vel[:, :3].astype(np.float64)
@@ -51,7 +51,8 @@ def test_plummer_density_and_force_sampled(mid):
     d = oracle.density(x, v, m, w.h, targets=t)
     assert d.failures == 0
     rho = s.in_original_order("rho")[t]
-    assert np.max(np.abs(rho / d.rho - 1)) <= 1e-5
+    assert parity("density Plummer 2^18 (32 stratified): max |rho/rho_o - 1|",
+                  np.max(np.abs(rho / d.rho - 1)), 1e-5)
     hg = s.in_original_order("h")
     acc = s.in_original_order("acc")
     ra, ga, rd, gd = [], [], [], []
@@ -70,8 +71,11 @@ def test_plummer_density_and_force_sampled(mid):
         f = oracle.force(x[ball], v[ball], m[ball], u[ball], dd.h, dd.rho, dd.omega, targets=[k])
         ra.append(f.acc[0]); ga.append(acc[i, :3]); rd.append(f.dudt[0]); gd.append(acc[i, 3])
         # each sampled target's own scale: accelerations vary by decades across the sphere
-        assert np.max(np.abs(acc[i, :3] - f.acc[0])) <= 1e-4 * np.max(np.abs(f.acc[0]))
-        assert abs(acc[i, 3] - f.dudt[0]) <= 1e-4 * abs(f.dudt[0]) + 1e-6 * np.max(np.abs(rd))
+        assert parity("force Plummer 2^18 (12 stratified): max over targets of |da_i| / max |a_i|",
+                      np.max(np.abs(acc[i, :3] - f.acc[0])) / np.max(np.abs(f.acc[0])), 1e-4)
+        assert parity("force Plummer 2^18 (12 stratified): max over targets of "
+                      "|d du_i| / (|du_i| + 0.01 max |du|)",
+                      abs(acc[i, 3] - f.dudt[0]) / (abs(f.dudt[0]) + 1e-2 * np.max(np.abs(rd))), 1e-4)
 
 
 def test_plummer_invariants(mid):
@@ -87,14 +91,15 @@ def test_plummer_invariants(mid):
     assert h.max() / h.min() > 20       # the workload really spans a wide range of h
 
 
-def test_plummer_full_size_exact_and_sampled():
+def test_plummer_full_size_exact_and_sampled(parity):
     w, s, p, ctx, native = _run(1 << 24)
     try:
         keys = oracle.morton_keys(w.pos)
         order = oracle.sort_order(keys)
-        assert np.array_equal(s.numpy("perm").astype(np.int64), order)
         sk = keys[order]
-        assert np.array_equal(s.numpy("keys").view(np.uint64), sk)
+        assert parity("keys/sort Plummer 2^24: mismatching keys and perm entries",
+                      np.sum(s.numpy("perm").astype(np.int64) != order)
+                      + np.sum(s.numpy("keys").view(np.uint64) != sk), 0)
         nodes, groups = native.sph_get_tree(ctx)
         ch = oracle.chop(sk, p.n_leaf)
         for f, ref in (("level", ch.level), ("first", ch.first), ("count", ch.count)):
@@ -104,6 +109,7 @@ def test_plummer_full_size_exact_and_sampled():
         d = oracle.density(x, w.vel[:, :3].astype(np.float64), w.pos[:, 3].astype(np.float64),
                            w.h, targets=t)
         assert d.failures == 0
-        assert np.max(np.abs(s.in_original_order("rho")[t] / d.rho - 1)) <= 1e-5
+        assert parity("density Plummer 2^24 (24 stratified): max |rho/rho_o - 1|",
+                      np.max(np.abs(s.in_original_order("rho")[t] / d.rho - 1)), 1e-5)
     finally:
         native.sph_destroy(ctx)
