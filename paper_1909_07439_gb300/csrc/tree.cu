@@ -223,7 +223,9 @@ __device__ __forceinline__ uint32_t block_scan_256(uint32_t v, uint32_t &excl, u
 // digit counts of all passes: ghist[p][d] for the 8 key digits and, with
 // inst, the 2 instance-id digits.  Each thread counts RS_GE consecutive
 // keys, adding runs of one digit with one shared atomic: the keys are nearly
-// in curve order, so the high digits come in long runs.
+// in curve order, so the high digits come in long runs, and a run that spans
+// the whole warp is added once for the warp.  Four blocks per SM: each adds
+// its shared counts to ghist once, which keeps the global atomics few.
 constexpr int RS_GE = 8;
 __global__ void __launch_bounds__(256) rs_ghist_kernel(const uint64_t *__restrict__ keys,
                                                        const int *__restrict__ inst, int n,
@@ -254,8 +256,16 @@ __global__ void __launch_bounds__(256) rs_ghist_kernel(const uint64_t *__restric
             }
         }
 #pragma unroll
-        for (int p = 0; p < 10; ++p)
-            if (cnt[p] != 0) atomicAdd(&h[p][cur[p]], cnt[p]);
+        for (int p = 0; p < 10; ++p) {
+            if (p >= np) break;
+            const uint32_t c0 = __shfl_sync(0xffffffffu, cur[p], 0);
+            if (__all_sync(0xffffffffu, cnt[p] == 0 || cur[p] == c0)) {
+                const uint32_t tot = __reduce_add_sync(0xffffffffu, cnt[p]);
+                if ((threadIdx.x & 31) == 0 && tot != 0) atomicAdd(&h[p][c0], tot);
+            } else if (cnt[p] != 0) {
+                atomicAdd(&h[p][cur[p]], cnt[p]);
+            }
+        }
     }
     __syncthreads();
     for (int k = threadIdx.x; k < np * 256; k += 256) {
@@ -543,37 +553,110 @@ __device__ __forceinline__ int cd_slots(const uint64_t *__restrict__ keys,
     return common_digits(keys[a], keys[b]);
 }
 
-// lv[s] = d | (Lmax << 8) if nodes start at s, else -1 (for threshold T)
-__device__ __forceinline__ int chop_levels(const uint64_t *__restrict__ keys,
-                                           const int *__restrict__ inst, int n, int s, int T)
+// Node starts of the chop with threshold T: lv[s] = d | (Lmax << 8) if the
+// nodes of levels d..Lmax start at slot s, else -1.  With
+//   b[z] = cd(z - 1, z)    (-1 at slot 0, at an instance boundary and past
+//                           the last slot),
+// sorted keys give cd(x, y) = min(b[x+1 .. y]) for x < y, so
+//   q[x] = cd(x, x + T) = min(b[x+1 .. x+T])      (-1 if x + T >= n).
+// Slot s with 0 <= b[s] < kMaxLevel starts a cell of level d = b[s] + 1
+// inside the cell P of level b[s] that holds s - 1 and s; the cell is a node
+// iff P has more than T slots (P is split), i.e. iff q[x] >= b[s] for some x
+// in [s - T, s] (then x and x + T lie in one cell of level b[s], which holds
+// s, so it is P; conversely the first slot of P, or s - T, is such an x).
+// Its descendants starting at s are nodes down to the first one with at most
+// T slots: Lmax = max(d, min(q[s] + 1, kMaxLevel)).  b[s] = -1 is a root
+// (d = 0), b[s] = kMaxLevel a key equal to the previous one (no node).
+//
+// One block per tile of kCfTile slots, with halos of kCfHalo > T slots on
+// both sides in shared memory (one byte per slot); the window minima and
+// maxima by doubling.
+constexpr int kCfTile = 2048, kCfHalo = 65, kCfR = kCfTile + 2 * kCfHalo;
+
+// dst[i] = min (or max) of src[i + off .. i + off + len - 1] for i in [lo, hi);
+// needs lo + off >= 0 and hi + off + len <= kCfR.  t0, t1: scratch.
+template <bool MAX>
+__device__ __forceinline__ void cf_window(const signed char *src, signed char *dst, signed char *t0,
+                                          signed char *t1, int lo, int hi, int off, int len)
 {
-    int d;
-    if (s == 0 || (inst && inst[s] != inst[s - 1])) {
-        d = 0;  // root of the (instance's) tree
-    } else {
-        int c = cd_slots(keys, inst, s, s - 1);
-        if (c == kMaxLevel) return -1;  // same key as the previous particle
-        d = c + 1;
-        int l = d - 1;
-        int lo = max(0, s - T), hi = s;
-        while (lo < hi) {
-            int mid = (lo + hi) >> 1;
-            if (cd_slots(keys, inst, mid, s) >= l) hi = mid; else lo = mid + 1;
+    const signed char *cur = src;  // cur[j] = op(src[j .. j + w - 1]) for j + w <= kCfR
+    signed char *out = t0;
+    int w = 1;
+    while (2 * w <= len) {
+        for (int j = threadIdx.x; j + 2 * w <= kCfR; j += blockDim.x) {
+            const int a = cur[j], b = cur[j + w];
+            out[j] = (signed char)(MAX ? max(a, b) : min(a, b));
         }
-        if (!(lo + T <= n - 1 && cd_slots(keys, inst, lo + T, s) >= l)) return -1;
+        __syncthreads();
+        cur = out;
+        out = out == t0 ? t1 : t0;
+        w *= 2;
     }
-    int c2 = (s + T <= n - 1) ? cd_slots(keys, inst, s, s + T) : -1;
-    int lmax = max(d, min(c2 + 1, kMaxLevel));
-    return d | (lmax << 8);
+    for (int i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const int a = cur[i + off], b = cur[i + off + len - w];  // two windows of w cover len
+        dst[i] = (signed char)(MAX ? max(a, b) : min(a, b));
+    }
+    __syncthreads();
 }
 
-__global__ void chop_flags_kernel(const uint64_t *__restrict__ keys, const int *__restrict__ inst,
-                                  int n, int t_leaf, int t_group, int *lv_tree, int *lv_grp)
+__global__ void __launch_bounds__(256) chop_flags_kernel(const uint64_t *__restrict__ keys,
+                                                         const int *__restrict__ inst, int n,
+                                                         int t_leaf, int t_group, int *lv_tree,
+                                                         int *lv_grp)
 {
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-        lv_tree[s] = chop_levels(keys, inst, n, s, t_leaf);
-        lv_grp[s] = chop_levels(keys, inst, n, s, t_group);
+    // local index i <-> slot t0 - kCfHalo + i
+    __shared__ signed char sb[kCfR], sq[kCfR], sm[kCfR], s0[kCfR], s1[kCfR];
+    const int ntile = (n + kCfTile - 1) / kCfTile;
+    for (int tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+        const int t0 = tile * kCfTile;
+        for (int i = threadIdx.x; i < kCfR; i += blockDim.x) {
+            const int x = t0 - kCfHalo + i;
+            sb[i] = (signed char)(x <= 0 || x >= n ? -1 : cd_slots(keys, inst, x - 1, x));
+        }
+        __syncthreads();
+        for (int pass = 0; pass < 2; ++pass) {
+            const int T = pass == 0 ? t_leaf : t_group;
+            int *lv = pass == 0 ? lv_tree : lv_grp;
+            if (pass == 0 || t_group != t_leaf) {
+                // q over [-T, kCfTile) relative to t0, then the maxima over [s - T, s]
+                cf_window<false>(sb, sq, s0, s1, kCfHalo - T, kCfHalo + kCfTile, 1, T);
+                cf_window<true>(sq, sm, s0, s1, kCfHalo, kCfHalo + kCfTile, -T, T + 1);
+            }
+            for (int k = threadIdx.x; k < kCfTile && t0 + k < n; k += blockDim.x) {
+                const int i = kCfHalo + k;
+                const int bs = sb[i], qs = sq[i];
+                int v;
+                if (bs < 0) v = max(0, min(qs + 1, kMaxLevel)) << 8;  // root
+                else if (bs == kMaxLevel || sm[i] < bs) v = -1;
+                else v = (bs + 1) | (max(bs + 1, min(qs + 1, kMaxLevel)) << 8);
+                lv[t0 + k] = v;
+            }
+            __syncthreads();  // sq, sm and (next tile) sb are rewritten next
+        }
     }
+}
+
+// The node levels [d, lm] that start at the slots of warp w of a 256-thread
+// block: warp w owns the block's slots [w * 128, (w + 1) * 128), 4 per lane,
+// slot base + 32 r + lane for r = 0..3 (no node: an empty range).  Returns
+// the range of levels over the warp in [wlo, whi] (wlo > whi if none).
+constexpr int kCwR = kChopBlock / 256;
+__device__ __forceinline__ int chop_warp_levels(const int *__restrict__ lv, int n, int base,
+                                                int (&d)[kCwR], int (&lm)[kCwR], int &whi)
+{
+    const int lane = threadIdx.x & 31;
+    int dmin = kLevels, lmx = -1;
+#pragma unroll
+    for (int r = 0; r < kCwR; ++r) {
+        const int s = base + 32 * r + lane;
+        const int v = s < n ? lv[s] : -1;
+        d[r] = v >= 0 ? (v & 0xff) : kLevels;
+        lm[r] = v >= 0 ? (v >> 8) : -1;
+        dmin = min(dmin, d[r]);
+        lmx = max(lmx, lm[r]);
+    }
+    whi = __reduce_max_sync(0xffffffffu, lmx);
+    return __reduce_min_sync(0xffffffffu, dmin);
 }
 
 // per block of kChopBlock particles: number of nodes per level
@@ -583,61 +666,68 @@ __global__ void __launch_bounds__(256) chop_count_kernel(const int *__restrict__
     __shared__ int cnt[kLevels];
     if (threadIdx.x < kLevels) cnt[threadIdx.x] = 0;
     __syncthreads();
-    for (int r = 0; r < kChopBlock / 256; ++r) {
-        int s = blockIdx.x * kChopBlock + r * 256 + threadIdx.x;
-        if (s < n) {
-            int v = lv[s];
-            if (v >= 0)
-                for (int L = v & 0xff; L <= (v >> 8); ++L) atomicAdd(&cnt[L], 1);
-        }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int d[kCwR], lm[kCwR], whi;
+    const int wlo = chop_warp_levels(lv, n, blockIdx.x * kChopBlock + w * 32 * kCwR, d, lm, whi);
+    for (int L = wlo; L <= whi; ++L) {
+        int c = 0;
+#pragma unroll
+        for (int r = 0; r < kCwR; ++r) c += __popc(__ballot_sync(0xffffffffu, d[r] <= L && L <= lm[r]));
+        if (lane == 0 && c != 0) atomicAdd(&cnt[L], c);
     }
     __syncthreads();
     if (threadIdx.x < kLevels) blk_cnt[threadIdx.x * nb + blockIdx.x] = cnt[threadIdx.x];
 }
 
+// Node k of level L gets index level offset + its rank among the level-L
+// nodes in slot order: per warp and level the count, one scan over the
+// warps, then per warp and level the ballots again for the ranks.
 __global__ void __launch_bounds__(256) chop_write_kernel(const int *__restrict__ lv, int n,
                                                          const int *__restrict__ blk_off, int nb,
                                                          Tree t, int *err)
 {
     __shared__ int wcnt[kLevels][8];
-    __shared__ int run[kLevels];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (threadIdx.x < kLevels) run[threadIdx.x] = blk_off[threadIdx.x * nb + blockIdx.x];
-    __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
-    for (int r = 0; r < kChopBlock / 256; ++r) {
-        int s = blockIdx.x * kChopBlock + r * 256 + threadIdx.x;
-        int v = s < n ? lv[s] : -1;
-        int d = v >= 0 ? (v & 0xff) : 99, lm = v >= 0 ? (v >> 8) : -1;
-        unsigned ranks[kLevels];
+    const int base = blockIdx.x * kChopBlock + w * 32 * kCwR;
+    int d[kCwR], lm[kCwR], whi;
+    const int wlo = chop_warp_levels(lv, n, base, d, lm, whi);
+    if (lane < kLevels) wcnt[lane][w] = 0;
+    __syncwarp();
+    for (int L = wlo; L <= whi; ++L) {
+        int c = 0;
 #pragma unroll
-        for (int L = 0; L < kLevels; ++L) {
-            unsigned b = __ballot_sync(0xffffffffu, d <= L && L <= lm);
-            ranks[L] = __popc(b & lt);
-            if (lane == 0) wcnt[L][w] = __popc(b);
+        for (int r = 0; r < kCwR; ++r) c += __popc(__ballot_sync(0xffffffffu, d[r] <= L && L <= lm[r]));
+        if (lane == 0) wcnt[L][w] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x < kLevels) {  // exclusive scan over the warps from the block's offset
+        int acc = blk_off[threadIdx.x * nb + blockIdx.x];
+        for (int ww = 0; ww < 8; ++ww) {
+            const int cc = wcnt[threadIdx.x][ww];
+            wcnt[threadIdx.x][ww] = acc;
+            acc += cc;
         }
-        __syncthreads();
-        if (threadIdx.x < kLevels) {
-            int acc = run[threadIdx.x];
-            for (int ww = 0; ww < 8; ++ww) {
-                int cc = wcnt[threadIdx.x][ww];
-                wcnt[threadIdx.x][ww] = acc;
-                acc += cc;
+    }
+    __syncthreads();
+    for (int L = wlo; L <= whi; ++L) {
+        int off = wcnt[L][w];
+#pragma unroll
+        for (int r = 0; r < kCwR; ++r) {
+            const bool on = d[r] <= L && L <= lm[r];
+            const unsigned b = __ballot_sync(0xffffffffu, on);
+            if (on) {
+                const int idx = off + __popc(b & lt);
+                if (idx < t.cap_nodes) {
+                    t.node_first[idx] = base + 32 * r + lane;
+                    t.node_level[idx] = L;
+                    t.node_arrive[idx] = 0;
+                } else {
+                    raise_error(err, SPH_ERR_NOMEM);
+                }
             }
-            run[threadIdx.x] = acc;
+            off += __popc(b);
         }
-        __syncthreads();
-        for (int L = d; L <= lm; ++L) {
-            int idx = wcnt[L][w] + (int)ranks[L];
-            if (idx < t.cap_nodes) {
-                t.node_first[idx] = s;
-                t.node_level[idx] = L;
-                t.node_arrive[idx] = 0;
-            } else {
-                raise_error(err, SPH_ERR_NOMEM);
-            }
-        }
-        __syncthreads();
     }
 }
 
@@ -910,7 +1000,8 @@ cudaError_t build_tree(Ctx &c, const sph_state &s, const sph_params &p, bool ful
     SPH_TRY(cudaMemsetAsync(c.rs_ghist, 0, sizeof(uint32_t) * 10 * 256, st));
     SPH_TRY(cudaMemsetAsync(c.rs_tiles, 0, sizeof(int) * (kRsSlots + 1), st));
     SPH_TRY(cudaMemsetAsync(c.rs_status, 0, sizeof(uint32_t) * 256 * (size_t)ntiles * nslot, st));
-    rs_ghist_kernel<<<grid_for(c, div_up(n, RS_GE), 256), 256, 0, st>>>(kin, inst, n, c.rs_ghist);
+    const int gh_grid = (int)std::max<int64_t>(1, std::min<int64_t>(div_up(n, 256 * RS_GE), 4 * (int64_t)c.num_sms));
+    rs_ghist_kernel<<<gh_grid, 256, 0, st>>>(kin, inst, n, c.rs_ghist);
     rs_gscan_kernel<<<ndigit, 256, 0, st>>>(c.rs_ghist, c.rs_gstart);
     int slot = 0;
     auto pass = [&](int digit, const int *gate) {
@@ -974,8 +1065,8 @@ cudaError_t build_tree(Ctx &c, const sph_state &s, const sph_params &p, bool ful
     // recorded leaf ranges refer to the previous tree: mark them invalid
     SPH_TRY(cudaMemsetAsync(t.rec_ctl + 1, 0xff, sizeof(int), st));
     // 5. chop: tree (n_leaf) and groups (n_group)
-    chop_flags_kernel<<<grid_for(c, n, 256), 256, 0, st>>>(s.keys, inst, n, p.n_leaf, p.n_group,
-                                                            t.lv_tree, t.lv_grp);
+    chop_flags_kernel<<<grid_for(c, n, kCfTile), 256, 0, st>>>(s.keys, inst, n, p.n_leaf, p.n_group,
+                                                                t.lv_tree, t.lv_grp);
     // groups
     int *gidx = (int *)c.tmp1[1];  // scratch: tmp1[1..] are free once copied back
     SPH_TRY(scan_mode(c, t.lv_grp, gidx, n, 1, c.d_sizes + SZ_GROUPS, st));
