@@ -574,16 +574,18 @@ __device__ __forceinline__ int cd_slots(const uint64_t *__restrict__ keys,
 constexpr int kCfTile = 2048, kCfHalo = 65, kCfR = kCfTile + 2 * kCfHalo;
 
 // dst[i] = min (or max) of src[i + off .. i + off + len - 1] for i in [lo, hi);
-// needs lo + off >= 0 and hi + off + len <= kCfR.  t0, t1: scratch.
+// needs lo + off >= 0 and hi + off + len <= kCfR, and reads src only there.
+// t0, t1: scratch.
 template <bool MAX>
 __device__ __forceinline__ void cf_window(const signed char *src, signed char *dst, signed char *t0,
                                           signed char *t1, int lo, int hi, int off, int len)
 {
-    const signed char *cur = src;  // cur[j] = op(src[j .. j + w - 1]) for j + w <= kCfR
+    // cur[j] = op(src[j .. j + w - 1]) for j in [lo + off, hi + off + len - w)
+    const signed char *cur = src;
     signed char *out = t0;
     int w = 1;
     while (2 * w <= len) {
-        for (int j = threadIdx.x; j + 2 * w <= kCfR; j += blockDim.x) {
+        for (int j = lo + off + threadIdx.x; j < hi + off + len - 2 * w; j += blockDim.x) {
             const int a = cur[j], b = cur[j + w];
             out[j] = (signed char)(MAX ? max(a, b) : min(a, b));
         }
