@@ -3,7 +3,7 @@
 //
 // Chop: the paper builds the tree level by level, splitting every curve
 // section with more than N_leaf particles.  Here the same node set is found
-// with O(1) work per particle instead of one pass per level.  With d(s) the
+// with O(log T) work per particle instead of one pass per level.  With d(s) the
 // first level at which key[s] differs from key[s-1] (s starts a run at every
 // level >= d(s)), the nodes that start at particle s are the levels
 // d(s) .. Lmax(s), provided the run containing s at level d(s)-1 holds more
@@ -12,7 +12,9 @@
 // holds more than T particles exactly at the levels <= c).  A node is terminal
 // at Lmax(s), so the terminal nodes (the groups, for T = N_group) start at the
 // particles with any node at all.  Nodes are numbered level by level and by
-// first particle inside a level, the order of the level-by-level chop.
+// first particle inside a level, the order of the level-by-level chop.  Both
+// tests reduce to window minima and maxima of the shared prefixes of
+// neighbouring keys (chop_flags_kernel).
 #include "sph_internal.cuh"
 
 namespace sph {
